@@ -1,0 +1,200 @@
+"""FP64 CPU oracle for the Deep Radiance Caching hot path (arXiv 1910.02480).
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  The product path
+(the CUDA library and its Python binding) never imports, links or runs it,
+and the two share no code: the oracle is ``drc_oracle.c``, direct loops in
+double precision, compiled with gcc into ``_drc_oracle.so`` and called here
+through ctypes on numpy arrays.
+
+Functions (each cites the passage its C routine follows, see drc_oracle.c):
+  conv3x3s2, convT3x3s2   the encoder / decoder layers (Sec. 3.3)
+  forward                 the autoencoder with skip connections (Sec. 3.3)
+  payload                 cosine-weighted hemisphere integral (Eq. 2, Sec. 3.3)
+  interpolate             kNN + weights w = w_p w_n + w_p + eps (Sec. 3.2)
+  l1_backward             L1 loss (Sec. 3.3, Eq. 7) and its exact gradient
+
+Pins (the tests under ``tests/test_oracle_*.py``) tie every function to
+values fixed by the paper or by mathematics; the one function without such a
+pin is marked "parity unpinned" below.  None is unpinned at present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "drc_oracle.c")
+_SO = os.path.join(_HERE, "_drc_oracle.so")
+
+F_ENCODE_INPUT = 1
+F_DECODE_OUTPUT = 2
+METRIC_IMAGE, METRIC_WORLD = 0, 1
+WP_INVERSE, WP_LINEAR = 0, 1
+INTERP_IRRADIANCE, INTERP_LOOKUP = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile drc_oracle.c with gcc (OpenMP, strict IEEE double)."""
+    if (not force and os.path.exists(_SO)
+            and os.path.getmtime(_SO) >= os.path.getmtime(_SRC)):
+        return _SO
+    tmp = _SO + ".tmp%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-ffp-contract=off",
+           "-fno-fast-math", "-std=c11", "-o", tmp, _SRC, "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i, l, d, u = ctypes.c_int, ctypes.c_long, ctypes.c_double, ctypes.c_uint
+        lib.orc_conv3x3s2.argtypes = [P, i, i, i, i, P, P, i, P]
+        lib.orc_convT3x3s2.argtypes = [P, i, i, i, i, P, P, i, P]
+        lib.orc_weight_count.argtypes = [i, P, i, i]
+        lib.orc_weight_count.restype = l
+        lib.orc_forward.argtypes = [i, P, i, i, i, d, u, P, l, P, i, i, i, P]
+        lib.orc_forward.restype = i
+        lib.orc_payload.argtypes = [P, i, i, i, i, P]
+        lib.orc_interp.argtypes = [i, i, i, P, P, P, P, P, i, i, P, P, P,
+                                   i, i, i, i, d, d, d, l, l, P, P, P]
+        lib.orc_interp.restype = i
+        lib.orc_l1_backward.argtypes = [i, P, i, i, i, d, u, P, l, P, P, i, i,
+                                        i, i, P, P, P]
+        lib.orc_l1_backward.restype = d
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def weight_count(widths, cin=7, cout=3) -> int:
+    w = np.asarray(widths, dtype=np.int32)
+    return int(_load().orc_weight_count(len(w), _ptr(w), cin, cout))
+
+
+def conv3x3s2(x, w, b=None):
+    """3x3 conv, stride 2, pad 1.  x [N,Cin,H,W], w [Cout,Cin,3,3]."""
+    x, w = _f64(x), _f64(w)
+    N, Cin, H, W = x.shape
+    Cout = w.shape[0]
+    assert w.shape == (Cout, Cin, 3, 3) and H % 2 == 0 and W % 2 == 0
+    y = np.empty((N, Cout, H // 2, W // 2))
+    bb = None if b is None else _f64(b)
+    _load().orc_conv3x3s2(_ptr(x), N, Cin, H, W, _ptr(w), _ptr(bb), Cout, _ptr(y))
+    return y
+
+
+def convT3x3s2(x, w, b=None):
+    """3x3 transposed conv, stride 2, pad 1, output pad 1.  w [Cin,Cout,3,3]."""
+    x, w = _f64(x), _f64(w)
+    N, Cin, H, W = x.shape
+    Cout = w.shape[1]
+    assert w.shape == (Cin, Cout, 3, 3)
+    y = np.empty((N, Cout, 2 * H, 2 * W))
+    bb = None if b is None else _f64(b)
+    _load().orc_convT3x3s2(_ptr(x), N, Cin, H, W, _ptr(w), _ptr(bb), Cout, _ptr(y))
+    return y
+
+
+def forward(weights, x, widths, cin=7, cout=3, out_relu=False, exposure=1.0,
+            flags=0):
+    """Denoise [N,cin,H,W] float32 maps -> [N,cout,H,W] float64."""
+    w = _f32(weights)
+    x = _f32(x)
+    wd = np.asarray(widths, dtype=np.int32)
+    N, C, H, W = x.shape
+    assert C == cin
+    out = np.empty((N, cout, H, W))
+    rc = _load().orc_forward(len(wd), _ptr(wd), cin, cout, int(out_relu),
+                             float(exposure), flags, _ptr(w), w.size, _ptr(x),
+                             N, H, W, _ptr(out))
+    if rc:
+        raise ValueError("oracle forward: bad network description (%d)" % rc)
+    return out
+
+
+def payload(L):
+    """E/pi per map and channel from linear radiance maps [N,C,H,W]."""
+    L = _f64(L)
+    N, C, H, W = L.shape
+    out = np.empty((N, C))
+    _load().orc_payload(_ptr(L), N, C, H, W, _ptr(out))
+    return out
+
+
+def interpolate(caches, gbuf, k, metric, wp_form, mode, r, eps=1e-6,
+                delta_rel=1e-3, p_range=None, want_neighbors=False):
+    """Blend cached values at every G-buffer pixel (Sec. 3.2).
+
+    caches: dict with 'payload' [n,3], 'pos' [n,3], 'nrm' [n,3], 'pix' [n,2]
+            int32 (x, y), and 'maps' [n,3,H,W] linear radiance for LOOKUP.
+    gbuf:   dict with 'width', 'height', 'pos' [P,3], 'nrm' [P,3],
+            'dir' [P,3] (LOOKUP only).
+    Returns out [p1-p0, 3] (and neighbour indices [.,k], the k+1 smallest
+    squared distances [.,k+1] when want_neighbors).
+    """
+    n = caches["pos"].shape[0]
+    maps = caches.get("maps")
+    mH = mW = 0
+    if maps is not None:
+        maps = _f32(maps)
+        mH, mW = maps.shape[2], maps.shape[3]
+    pay = _f32(caches["payload"]) if caches.get("payload") is not None else None
+    cpos, cnrm = _f32(caches["pos"]), _f32(caches["nrm"])
+    cpix = np.ascontiguousarray(caches["pix"], dtype=np.int32)
+    width, height = int(gbuf["width"]), int(gbuf["height"])
+    gpos, gnrm = _f32(gbuf["pos"]), _f32(gbuf["nrm"])
+    gdir = _f32(gbuf["dir"]) if gbuf.get("dir") is not None else None
+    p0, p1 = (0, width * height) if p_range is None else p_range
+    out = np.empty((p1 - p0, 3))
+    idx = np.empty((p1 - p0, k), dtype=np.int32) if want_neighbors else None
+    d2 = np.empty((p1 - p0, k + 1)) if want_neighbors else None
+    rc = _load().orc_interp(n, mH, mW, _ptr(maps), _ptr(pay), _ptr(cpos),
+                            _ptr(cnrm), _ptr(cpix), width, height, _ptr(gpos),
+                            _ptr(gnrm), _ptr(gdir), k, metric, wp_form, mode,
+                            float(r), float(eps), float(delta_rel), p0, p1,
+                            _ptr(out), _ptr(idx), _ptr(d2))
+    if rc:
+        raise ValueError("oracle interpolate: bad arguments (%d)" % rc)
+    if want_neighbors:
+        return out, idx, d2
+    return out
+
+
+def l1_backward(weights, x, target, widths, cin=7, cout=3, out_relu=False,
+                exposure=1.0, flags=0, grad_out=False):
+    """Loss and gradients: returns (loss, dweights [n_floats], dinput)."""
+    w, x, t = _f32(weights), _f32(x), _f32(target)
+    wd = np.asarray(widths, dtype=np.int32)
+    N, C, H, W = x.shape
+    dw = np.empty(w.size)
+    dx = np.empty(x.shape)
+    rc = ctypes.c_int(0)
+    loss = _load().orc_l1_backward(len(wd), _ptr(wd), cin, cout, int(out_relu),
+                                   float(exposure), flags, _ptr(w), w.size,
+                                   _ptr(x), _ptr(t), N, H, W, int(grad_out),
+                                   _ptr(dw), _ptr(dx), ctypes.byref(rc))
+    if rc.value:
+        raise ValueError("oracle backward: bad network description (%d)" % rc.value)
+    return loss, dw, dx

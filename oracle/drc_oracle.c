@@ -1,0 +1,749 @@
+/*
+ * drc_oracle.c -- FP64 CPU oracle for the Deep Radiance Caching hot path
+ * (Jiang & Kainz, "Deep Radiance Caching: Convolutional Autoencoders Deeper
+ * in Ray Tracing", arXiv 1910.02480).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file; only the tests, the package's smoke check and the CPU
+ * baseline leg of the benchmark use it.  It shares no code, header, table or
+ * helper with the CUDA library: it is a plain, slow, direct-loop restatement
+ * of what the method computes, in double precision, so that a reader can
+ * check it against the paper by eye.
+ *
+ * Every tensor handed in is float32 (the exact bytes the GPU path consumes);
+ * every computation is carried out in double.
+ *
+ * Functions and the passages they follow:
+ *   orc_conv3x3s2     3x3 convolution, stride 2, pad 1 (the encoder stages of
+ *                     the autoencoder, Sec. 3.3 "Neural network").
+ *   orc_convT3x3s2    3x3 transposed convolution, stride 2, pad 1, output
+ *                     padding 1 (the decoder "deconvolutions", Sec. 3.3).
+ *   orc_forward       encoder / decoder with skip connections (Sec. 3.3),
+ *                     optional log encode / decode of the radiance channels.
+ *   orc_payload       cosine-weighted integral of a hemispherical lat-long
+ *                     radiance map over the upper hemisphere (Eq. 2 for a
+ *                     diffuse BRDF; map encoding of Sec. 3.3).
+ *   orc_interp        k-nearest cache selection, the weight heuristic
+ *                     w = w_p*w_n + w_p + eps and its normalisation, and the
+ *                     blend of the cached values (Sec. 3.2, Eqs. 4-6).
+ *   orc_l1_backward   L1 loss (Sec. 3.3, Sec. 5.1 Eq. 7) and its exact
+ *                     gradient through the network (reverse mode).
+ * Readings of passages the paper leaves open are listed beside each function.
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_F_ENCODE_INPUT 1u
+#define ORC_F_DECODE_OUTPUT 2u
+
+#define ORC_METRIC_IMAGE 0
+#define ORC_METRIC_WORLD 1
+#define ORC_WP_INVERSE 0
+#define ORC_WP_LINEAR 1
+#define ORC_INTERP_IRRADIANCE 0
+#define ORC_INTERP_LOOKUP 1
+
+static const double ORC_PI = 3.14159265358979323846;
+
+/* ------------------------------------------------------------------------ */
+/* Convolutions (Sec. 3.3).  Layouts: x [N][C][H][W]; conv weights          */
+/* [Cout][Cin][3][3]; transposed-conv weights [Cin][Cout][3][3].            */
+/* ------------------------------------------------------------------------ */
+
+/* y[n,o,i,j] = b[o] + sum_{c,u,v} W[o,c,u,v] * x[n,c,2i+u-1,2j+v-1],
+ * x taken as zero outside the map.  Output is (H/2) x (W/2). */
+void orc_conv3x3s2(const double *x, int N, int Cin, int H, int W,
+                   const double *Wt, const double *b, int Cout, double *y)
+{
+    int Ho = H / 2, Wo = W / 2;
+#pragma omp parallel for schedule(static)
+    for (int n = 0; n < N; n++)
+        for (int o = 0; o < Cout; o++)
+            for (int i = 0; i < Ho; i++)
+                for (int j = 0; j < Wo; j++) {
+                    double acc = b ? b[o] : 0.0;
+                    for (int c = 0; c < Cin; c++)
+                        for (int u = 0; u < 3; u++)
+                            for (int v = 0; v < 3; v++) {
+                                int yy = 2 * i + u - 1, xx = 2 * j + v - 1;
+                                if (yy < 0 || yy >= H || xx < 0 || xx >= W)
+                                    continue;
+                                acc += Wt[((o * Cin + c) * 3 + u) * 3 + v] *
+                                       x[(((long)n * Cin + c) * H + yy) * W + xx];
+                            }
+                    y[(((long)n * Cout + o) * Ho + i) * Wo + j] = acc;
+                }
+}
+
+/* y[n,o,p,q] = b[o] + sum over (c,i,j,u,v) with 2i+u-1 = p, 2j+v-1 = q of
+ * W[c,o,u,v] * x[n,c,i,j].  Output is (2H) x (2W): written exactly as the
+ * scatter of every input pixel through every tap, dropping taps that land
+ * outside the output. */
+void orc_convT3x3s2(const double *x, int N, int Cin, int H, int W,
+                    const double *Wt, const double *b, int Cout, double *y)
+{
+    int Ho = 2 * H, Wo = 2 * W;
+#pragma omp parallel for schedule(static)
+    for (int n = 0; n < N; n++) {
+        for (int o = 0; o < Cout; o++)
+            for (int p = 0; p < Ho * Wo; p++)
+                y[((long)n * Cout + o) * Ho * Wo + p] = b ? b[o] : 0.0;
+        for (int c = 0; c < Cin; c++)
+            for (int i = 0; i < H; i++)
+                for (int j = 0; j < W; j++) {
+                    double xv = x[(((long)n * Cin + c) * H + i) * W + j];
+                    for (int o = 0; o < Cout; o++)
+                        for (int u = 0; u < 3; u++)
+                            for (int v = 0; v < 3; v++) {
+                                int p = 2 * i + u - 1, q = 2 * j + v - 1;
+                                if (p < 0 || p >= Ho || q < 0 || q >= Wo)
+                                    continue;
+                                y[(((long)n * Cout + o) * Ho + p) * Wo + q] +=
+                                    Wt[((c * Cout + o) * 3 + u) * 3 + v] * xv;
+                            }
+                }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Network description: packed weights, in order conv_1..conv_S then       */
+/* convT_S..convT_1, each layer as W followed by b.                         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int S, cin, cout, out_relu;
+    int width[9]; /* width[0] = cin, width[1..S] = encoder widths */
+    const double *encW[8], *encB[8];
+    const double *decW[9], *decB[9]; /* decoder convT_s, s = 1..S */
+    long n_floats;
+} orc_net;
+
+long orc_weight_count(int S, const int *widths, int cin, int cout)
+{
+    long n = 0;
+    int prev = cin;
+    for (int s = 0; s < S; s++) {
+        n += 9L * prev * widths[s] + widths[s];
+        prev = widths[s];
+    }
+    for (int s = S - 1; s >= 0; s--) {
+        int co = (s == 0) ? cout : widths[s - 1];
+        n += 9L * widths[s] * co + co;
+    }
+    return n;
+}
+
+/* Bind the packed (double) weight vector to the layer pointers. */
+static int bind_net(orc_net *net, int S, const int *widths, int cin, int cout,
+                    int out_relu, const double *w, long n_floats)
+{
+    if (S < 1 || S > 8)
+        return -1;
+    net->S = S;
+    net->cin = cin;
+    net->cout = cout;
+    net->out_relu = out_relu;
+    net->width[0] = cin;
+    for (int s = 0; s < S; s++)
+        net->width[s + 1] = widths[s];
+    if (orc_weight_count(S, widths, cin, cout) != n_floats)
+        return -2;
+    long off = 0;
+    for (int s = 1; s <= S; s++) {
+        net->encW[s - 1] = w + off;
+        off += 9L * net->width[s - 1] * net->width[s];
+        net->encB[s - 1] = w + off;
+        off += net->width[s];
+    }
+    for (int s = S; s >= 1; s--) {
+        int co = (s == 1) ? cout : net->width[s - 1];
+        net->decW[s] = w + off;
+        off += 9L * net->width[s] * co;
+        net->decB[s] = w + off;
+        off += co;
+    }
+    net->n_floats = off;
+    return 0;
+}
+
+static double *widen(const float *a, long n)
+{
+    double *d = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (long i = 0; i < n; i++)
+        d[i] = (double)a[i];
+    return d;
+}
+
+static void relu_inplace(double *a, long n)
+{
+    for (long i = 0; i < n; i++)
+        if (!(a[i] > 0.0))
+            a[i] = 0.0;
+}
+
+/* Input encode: channels 0..2 carry radiance; log1p(s*L) when the encode flag
+ * is set (a reading: the paper does not state a transform for its network,
+ * log1p keeps zero radiance at zero). */
+static void encode_input(double *x, int N, int C, int H, int W, double s)
+{
+    for (int n = 0; n < N; n++)
+        for (int c = 0; c < 3 && c < C; c++)
+            for (long p = 0; p < (long)H * W; p++) {
+                double *v = &x[((long)n * C + c) * H * W + p];
+                *v = log1p(s * (*v));
+            }
+}
+
+/* Forward state kept for the backward pass. */
+typedef struct {
+    int N, H, W;
+    double *e[9];  /* e[0] = encoded input, e[s] = ReLU(z[s]) */
+    double *z[9];  /* encoder pre-activations */
+    double *t[9];  /* decoder: t[S] = e[S]; t[s-1] = ReLU(zd[s]) + e[s-1] */
+    double *zd[9]; /* decoder pre-activations, zd[s] = convT_s(t[s]) */
+    double *out;   /* network output (log radiance), after optional ReLU */
+    double *zout;  /* output pre-activation */
+} orc_state;
+
+static long act_size(const orc_net *net, int N, int H, int W, int s)
+{
+    /* stage s has width[s] channels at (H >> s) x (W >> s) */
+    return (long)N * net->width[s] * (H >> s) * (W >> s);
+}
+
+static void free_state(orc_state *st, int S)
+{
+    for (int s = 0; s <= S; s++) {
+        free(st->e[s]);
+        free(st->z[s]);
+        free(st->zd[s]);
+        if (s < S)
+            free(st->t[s]);
+    }
+    free(st->out);
+    free(st->zout);
+}
+
+/* Encoder: e_0 = x, e_s = ReLU(conv_s(e_{s-1})).  Decoder: t = e_S; for
+ * s = S..2, t = ReLU(convT_s(t)) + e_{s-1} (skip connection added after the
+ * activation -- a reading, the paper only names skip connections); output
+ * = convT_1(t), optionally followed by ReLU (the paper's final ReLU). */
+static void run_forward(const orc_net *net, const double *x_enc, int N, int H,
+                        int W, orc_state *st)
+{
+    int S = net->S;
+    memset(st, 0, sizeof(*st));
+    st->N = N;
+    st->H = H;
+    st->W = W;
+    long n0 = (long)N * net->cin * H * W;
+    st->e[0] = (double *)malloc(sizeof(double) * n0);
+    memcpy(st->e[0], x_enc, sizeof(double) * n0);
+    for (int s = 1; s <= S; s++) {
+        long ns = act_size(net, N, H, W, s);
+        st->z[s] = (double *)malloc(sizeof(double) * ns);
+        orc_conv3x3s2(st->e[s - 1], N, net->width[s - 1], H >> (s - 1),
+                      W >> (s - 1), net->encW[s - 1], net->encB[s - 1],
+                      net->width[s], st->z[s]);
+        st->e[s] = (double *)malloc(sizeof(double) * ns);
+        memcpy(st->e[s], st->z[s], sizeof(double) * ns);
+        relu_inplace(st->e[s], ns);
+    }
+    st->t[S] = st->e[S];
+    for (int s = S; s >= 2; s--) {
+        long ns = act_size(net, N, H, W, s - 1);
+        st->zd[s] = (double *)malloc(sizeof(double) * ns);
+        orc_convT3x3s2(st->t[s], N, net->width[s], H >> s, W >> s,
+                       net->decW[s], net->decB[s], net->width[s - 1],
+                       st->zd[s]);
+        st->t[s - 1] = (double *)malloc(sizeof(double) * ns);
+        for (long i = 0; i < ns; i++)
+            st->t[s - 1][i] = (st->zd[s][i] > 0.0 ? st->zd[s][i] : 0.0) +
+                              st->e[s - 1][i];
+    }
+    long no = (long)N * net->cout * H * W;
+    st->zout = (double *)malloc(sizeof(double) * no);
+    orc_convT3x3s2(st->t[1], N, net->width[1], H >> 1, W >> 1, net->decW[1],
+                   net->decB[1], net->cout, st->zout);
+    st->out = (double *)malloc(sizeof(double) * no);
+    memcpy(st->out, st->zout, sizeof(double) * no);
+    if (net->out_relu)
+        relu_inplace(st->out, no);
+}
+
+/* Full denoise: in [N][cin][H][W] (float32) -> out [N][cout][H][W] (double).
+ * flags: ORC_F_ENCODE_INPUT applies log1p(s*L) to channels 0..2 first;
+ * ORC_F_DECODE_OUTPUT returns expm1(y)/s instead of the log-space y.
+ * Returns 0, or a negative code for a bad description. */
+int orc_forward(int S, const int *widths, int cin, int cout, int out_relu,
+                double s, unsigned flags, const float *weights, long n_floats,
+                const float *in, int N, int H, int W, double *out)
+{
+    if (H % (1 << S) || W % (1 << S))
+        return -3;
+    double *w = widen(weights, n_floats);
+    orc_net net;
+    int rc = bind_net(&net, S, widths, cin, cout, out_relu, w, n_floats);
+    if (rc) {
+        free(w);
+        return rc;
+    }
+    long nin = (long)N * cin * H * W;
+    double *x = widen(in, nin);
+    if (flags & ORC_F_ENCODE_INPUT)
+        encode_input(x, N, cin, H, W, s);
+    orc_state st;
+    run_forward(&net, x, N, H, W, &st);
+    long no = (long)N * cout * H * W;
+    for (long i = 0; i < no; i++)
+        out[i] = (flags & ORC_F_DECODE_OUTPUT) ? expm1(st.out[i]) / s
+                                               : st.out[i];
+    free_state(&st, S);
+    free(x);
+    free(w);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Irradiance of a hemispherical lat-long map (Eq. 2 with a diffuse BRDF).  */
+/* Map layout (a reading of the map encoding in Sec. 3.3): row i covers     */
+/* theta in [i*pi/(2H), (i+1)*pi/(2H)] with theta = 0 at the normal;        */
+/* column j covers phi in [2*pi*j/W, 2*pi*(j+1)/W).  Each texel's weight is */
+/* the exact integral of cos(theta) dOmega over its band:                   */
+/*   1/2 (sin^2 theta_{i+1} - sin^2 theta_i) * (2 pi / W).                  */
+/* payload = E / pi, i.e. the outgoing radiance of a white Lambertian       */
+/* surface lit by the map.                                                  */
+/* ------------------------------------------------------------------------ */
+void orc_payload(const double *L, int N, int C, int H, int W, double *payload)
+{
+    for (int n = 0; n < N; n++)
+        for (int c = 0; c < C; c++) {
+            double E = 0.0;
+            for (int i = 0; i < H; i++) {
+                double t0 = i * ORC_PI / (2.0 * H);
+                double t1 = (i + 1) * ORC_PI / (2.0 * H);
+                double band = 0.5 * (sin(t1) * sin(t1) - sin(t0) * sin(t0)) *
+                              (2.0 * ORC_PI / W);
+                for (int j = 0; j < W; j++)
+                    E += L[(((long)n * C + c) * H + i) * W + j] * band;
+            }
+            payload[(long)n * C + c] = E / ORC_PI;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Interpolation of cached radiance (Sec. 3.2).                             */
+/* ------------------------------------------------------------------------ */
+
+/* Local frame of a cache (map encoding, Sec. 3.3): the normal is the map's
+ * Z axis; the up vector is the scene's (+Z) and is turned to +Y only when
+ * the normal itself points along Z (reading: |n.z| > 1 - 1e-6).
+ * t = normalize(up x n), b = n x t.  Returns 0 for a zero-length normal. */
+static int cache_frame(const float *nrm, double t[3], double b[3], double n[3])
+{
+    double nx = nrm[0], ny = nrm[1], nz = nrm[2];
+    double len = sqrt(nx * nx + ny * ny + nz * nz);
+    if (!(len > 0.0))
+        return 0;
+    n[0] = nx / len;
+    n[1] = ny / len;
+    n[2] = nz / len;
+    double up[3] = {0.0, 0.0, 1.0};
+    if (fabs(n[2]) > 1.0 - 1e-6) {
+        up[0] = 0.0;
+        up[1] = 1.0;
+        up[2] = 0.0;
+    }
+    double cx = up[1] * n[2] - up[2] * n[1];
+    double cy = up[2] * n[0] - up[0] * n[2];
+    double cz = up[0] * n[1] - up[1] * n[0];
+    double cl = sqrt(cx * cx + cy * cy + cz * cz);
+    t[0] = cx / cl;
+    t[1] = cy / cl;
+    t[2] = cz / cl;
+    b[0] = n[1] * t[2] - n[2] * t[1];
+    b[1] = n[2] * t[0] - n[0] * t[2];
+    b[2] = n[0] * t[1] - n[1] * t[0];
+    return 1;
+}
+
+/* Bilinear lookup of channel c of map R (H x W lat-long), continuous texel
+ * coordinates (ti, tj) with texel centres at integer + 0.5 of the angle
+ * grid: wrap in phi (columns), clamp in theta (rows). */
+static double bilinear(const float *R, int H, int W, double ti, double tj)
+{
+    double fi = floor(ti), fj = floor(tj);
+    double ai = ti - fi, aj = tj - fj;
+    int i0 = (int)fi, j0 = (int)fj;
+    int i1 = i0 + 1, j1 = j0 + 1;
+    if (i0 < 0)
+        i0 = 0;
+    if (i0 > H - 1)
+        i0 = H - 1;
+    if (i1 < 0)
+        i1 = 0;
+    if (i1 > H - 1)
+        i1 = H - 1;
+    j0 = ((j0 % W) + W) % W;
+    j1 = ((j1 % W) + W) % W;
+    double v00 = R[(long)i0 * W + j0], v01 = R[(long)i0 * W + j1];
+    double v10 = R[(long)i1 * W + j0], v11 = R[(long)i1 * W + j1];
+    return (1 - ai) * ((1 - aj) * v00 + aj * v01) +
+           ai * ((1 - aj) * v10 + aj * v11);
+}
+
+/* For pixels p in [p_begin, p_end) of a width x height G-buffer:
+ *  1. distance d^2 to every cache: IMAGE metric in integer pixels on the image
+ *     plane (Sec. 3.2), WORLD metric between first-hit positions;
+ *  2. keep the k smallest by (d^2, cache index);
+ *  3. w_p = r/(d + delta_rel*r) (INVERSE, a reading: printed "dist/r" grows
+ *     with distance) or max(0, 1 - d/r) (LINEAR);
+ *     w_n = max(0, n_j . n_p) with unit normals (reading: the prose says the
+ *     normal weight is largest when the normals agree and zero when their dot
+ *     product is negative, which the printed 1 - max(0, .) contradicts);
+ *     w = w_p * w_n + w_p + eps (Eq. 4);
+ *  4. normalise, W_j = w_j / sum w;
+ *  5. IRRADIANCE: out = sum W_j payload_j.  LOOKUP: out = sum W_j R_j(l_j),
+ *     with l_j the pixel direction in cache j's frame, zero below the cache's
+ *     horizon -- the expectation over map choice of the paper's sampling of
+ *     maps with probabilities W_j.
+ * out is [p_end-p_begin][3].  nbr_idx ([.][k], nullable) receives the
+ * selected indices in (d^2, index) order; nbr_d2 ([.][k+1], nullable) the
+ * k+1 smallest d^2 (the last is +inf if n <= k) for tie analysis. */
+int orc_interp(int n_caches, int mapH, int mapW, const float *maps,
+               const float *payload, const float *cpos, const float *cnrm,
+               const int *cpix, int width, int height, const float *gpos,
+               const float *gnrm, const float *gdir, int k, int metric,
+               int wp_form, int mode, double r, double eps, double delta_rel,
+               long p_begin, long p_end, double *out, int *nbr_idx,
+               double *nbr_d2)
+{
+    if (k < 1 || k > 64 || n_caches < 1)
+        return -1;
+    if (mode == ORC_INTERP_LOOKUP && (!maps || !gdir))
+        return -1;
+    (void)height;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (long p = p_begin; p < p_end; p++) {
+        int px = (int)(p % width), py = (int)(p / width);
+        double bd[65];
+        int bi[65];
+        int nb = 0;
+        for (int j = 0; j < n_caches; j++) {
+            double d2;
+            if (metric == ORC_METRIC_IMAGE) {
+                double dx = (double)(px - cpix[2 * j]);
+                double dy = (double)(py - cpix[2 * j + 1]);
+                d2 = dx * dx + dy * dy;
+            } else {
+                double dx = (double)gpos[3 * p] - cpos[3 * j];
+                double dy = (double)gpos[3 * p + 1] - cpos[3 * j + 1];
+                double dz = (double)gpos[3 * p + 2] - cpos[3 * j + 2];
+                d2 = dx * dx + dy * dy + dz * dz;
+            }
+            /* insertion into the sorted list of the k+1 best, key (d2, j);
+             * j grows, so an equal d2 already in the list ranks first */
+            if (nb == k + 1 && !(d2 < bd[k]))
+                continue;
+            int pos = (nb < k + 1) ? nb++ : k;
+            while (pos > 0 && d2 < bd[pos - 1]) {
+                bd[pos] = bd[pos - 1];
+                bi[pos] = bi[pos - 1];
+                pos--;
+            }
+            bd[pos] = d2;
+            bi[pos] = j;
+        }
+        int kk = nb < k ? nb : k;
+        double w[64], wsum = 0.0;
+        double pn[3] = {gnrm[3 * p], gnrm[3 * p + 1], gnrm[3 * p + 2]};
+        double pl = sqrt(pn[0] * pn[0] + pn[1] * pn[1] + pn[2] * pn[2]);
+        for (int q = 0; q < kk; q++) {
+            int j = bi[q];
+            double d = sqrt(bd[q]);
+            double wp;
+            if (wp_form == ORC_WP_INVERSE)
+                wp = r / (d + delta_rel * r);
+            else
+                wp = 1.0 - d / r > 0.0 ? 1.0 - d / r : 0.0;
+            double cn[3] = {cnrm[3 * j], cnrm[3 * j + 1], cnrm[3 * j + 2]};
+            double cl = sqrt(cn[0] * cn[0] + cn[1] * cn[1] + cn[2] * cn[2]);
+            double wn = 0.0;
+            if (pl > 0.0 && cl > 0.0) {
+                double dot = (cn[0] * pn[0] + cn[1] * pn[1] + cn[2] * pn[2]) /
+                             (cl * pl);
+                wn = dot > 0.0 ? dot : 0.0;
+            }
+            w[q] = wp * wn + wp + eps;
+            wsum += w[q];
+        }
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int q = 0; q < kk; q++) {
+            int j = bi[q];
+            double Wq = w[q] / wsum;
+            if (mode == ORC_INTERP_IRRADIANCE) {
+                for (int c = 0; c < 3; c++)
+                    acc[c] += Wq * payload[3 * j + c];
+            } else {
+                double t[3], b[3], n[3];
+                if (!cache_frame(&cnrm[3 * j], t, b, n))
+                    continue;
+                double om[3] = {gdir[3 * p], gdir[3 * p + 1], gdir[3 * p + 2]};
+                double ol = sqrt(om[0] * om[0] + om[1] * om[1] + om[2] * om[2]);
+                if (!(ol > 0.0))
+                    continue;
+                for (int a = 0; a < 3; a++)
+                    om[a] /= ol;
+                double lx = om[0] * t[0] + om[1] * t[1] + om[2] * t[2];
+                double ly = om[0] * b[0] + om[1] * b[1] + om[2] * b[2];
+                double lz = om[0] * n[0] + om[1] * n[1] + om[2] * n[2];
+                if (!(lz > 0.0))
+                    continue;
+                if (lz > 1.0)
+                    lz = 1.0;
+                double theta = acos(lz);
+                double phi = atan2(ly, lx);
+                if (phi < 0.0)
+                    phi += 2.0 * ORC_PI;
+                double ti = theta / (0.5 * ORC_PI) * mapH - 0.5;
+                double tj = phi / (2.0 * ORC_PI) * mapW - 0.5;
+                for (int c = 0; c < 3; c++) {
+                    const float *R = maps + (((long)j * 3 + c) * mapH) * mapW;
+                    acc[c] += Wq * bilinear(R, mapH, mapW, ti, tj);
+                }
+            }
+        }
+        long o = p - p_begin;
+        for (int c = 0; c < 3; c++)
+            out[3 * o + c] = acc[c];
+        if (nbr_idx)
+            for (int q = 0; q < k; q++)
+                nbr_idx[o * k + q] = q < kk ? bi[q] : -1;
+        if (nbr_d2)
+            for (int q = 0; q <= k; q++)
+                nbr_d2[o * (k + 1) + q] = q < nb ? bd[q] : INFINITY;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Loss and gradient (training, Sec. 4; L1 of Sec. 3.3 and Eq. 7).          */
+/* ------------------------------------------------------------------------ */
+
+/* Adjoint of orc_conv3x3s2: accumulates dx (nullable), dW, db from g. */
+static void conv_adjoint(const double *x, int N, int Cin, int H, int W,
+                         const double *Wt, int Cout, const double *g,
+                         double *dx, double *dW, double *db)
+{
+    int Ho = H / 2, Wo = W / 2;
+#pragma omp parallel for schedule(static)
+    for (int o = 0; o < Cout; o++) {
+        double sb = 0.0;
+        for (int n = 0; n < N; n++)
+            for (int i = 0; i < Ho; i++)
+                for (int j = 0; j < Wo; j++) {
+                    double gv = g[(((long)n * Cout + o) * Ho + i) * Wo + j];
+                    sb += gv;
+                    for (int c = 0; c < Cin; c++)
+                        for (int u = 0; u < 3; u++)
+                            for (int v = 0; v < 3; v++) {
+                                int yy = 2 * i + u - 1, xx = 2 * j + v - 1;
+                                if (yy < 0 || yy >= H || xx < 0 || xx >= W)
+                                    continue;
+                                dW[((o * Cin + c) * 3 + u) * 3 + v] +=
+                                    gv * x[(((long)n * Cin + c) * H + yy) * W + xx];
+                            }
+                }
+        db[o] += sb;
+    }
+    if (!dx)
+        return;
+#pragma omp parallel for schedule(static)
+    for (int n = 0; n < N; n++)
+        for (int o = 0; o < Cout; o++)
+            for (int i = 0; i < Ho; i++)
+                for (int j = 0; j < Wo; j++) {
+                    double gv = g[(((long)n * Cout + o) * Ho + i) * Wo + j];
+                    for (int c = 0; c < Cin; c++)
+                        for (int u = 0; u < 3; u++)
+                            for (int v = 0; v < 3; v++) {
+                                int yy = 2 * i + u - 1, xx = 2 * j + v - 1;
+                                if (yy < 0 || yy >= H || xx < 0 || xx >= W)
+                                    continue;
+                                dx[(((long)n * Cin + c) * H + yy) * W + xx] +=
+                                    Wt[((o * Cin + c) * 3 + u) * 3 + v] * gv;
+                            }
+                }
+}
+
+/* Adjoint of orc_convT3x3s2 (input H x W, output 2H x 2W). */
+static void convT_adjoint(const double *x, int N, int Cin, int H, int W,
+                          const double *Wt, int Cout, const double *g,
+                          double *dx, double *dW, double *db)
+{
+    int Ho = 2 * H, Wo = 2 * W;
+#pragma omp parallel for schedule(static)
+    for (int o = 0; o < Cout; o++) {
+        double sb = 0.0;
+        for (int n = 0; n < N; n++)
+            for (int p = 0; p < Ho * Wo; p++)
+                sb += g[((long)n * Cout + o) * Ho * Wo + p];
+        db[o] += sb;
+        for (int c = 0; c < Cin; c++)
+            for (int n = 0; n < N; n++)
+                for (int i = 0; i < H; i++)
+                    for (int j = 0; j < W; j++) {
+                        double xv = x[(((long)n * Cin + c) * H + i) * W + j];
+                        for (int u = 0; u < 3; u++)
+                            for (int v = 0; v < 3; v++) {
+                                int p = 2 * i + u - 1, q = 2 * j + v - 1;
+                                if (p < 0 || p >= Ho || q < 0 || q >= Wo)
+                                    continue;
+                                dW[((c * Cout + o) * 3 + u) * 3 + v] +=
+                                    xv * g[(((long)n * Cout + o) * Ho + p) * Wo + q];
+                            }
+                    }
+    }
+    if (!dx)
+        return;
+#pragma omp parallel for schedule(static)
+    for (int n = 0; n < N; n++)
+        for (int c = 0; c < Cin; c++)
+            for (int i = 0; i < H; i++)
+                for (int j = 0; j < W; j++) {
+                    double acc = 0.0;
+                    for (int o = 0; o < Cout; o++)
+                        for (int u = 0; u < 3; u++)
+                            for (int v = 0; v < 3; v++) {
+                                int p = 2 * i + u - 1, q = 2 * j + v - 1;
+                                if (p < 0 || p >= Ho || q < 0 || q >= Wo)
+                                    continue;
+                                acc += Wt[((c * Cout + o) * 3 + u) * 3 + v] *
+                                       g[(((long)n * Cout + o) * Ho + p) * Wo + q];
+                            }
+                    dx[(((long)n * Cin + c) * H + i) * W + j] += acc;
+                }
+}
+
+/* Loss and exact gradient.  mode 0: target is the ground truth y (log
+ * radiance, [N][cout][H][W]); loss = mean |out - y| and dL/dout =
+ * sign(out - y)/numel with sign(0) = 0.  mode 1: target is dL/dout itself and
+ * the loss is not formed (reported as 0).
+ * Outputs: dweights (packed like the weights, overwritten), dinput (nullable,
+ * [N][cin][H][W], gradient with respect to the caller's input -- through the
+ * log encode when that flag is set), returns the loss. */
+double orc_l1_backward(int S, const int *widths, int cin, int cout,
+                       int out_relu, double s, unsigned flags,
+                       const float *weights, long n_floats, const float *in,
+                       const float *target, int N, int H, int W, int mode,
+                       double *dweights, double *dinput, int *rc_out)
+{
+    *rc_out = 0;
+    if (H % (1 << S) || W % (1 << S)) {
+        *rc_out = -3;
+        return 0.0;
+    }
+    double *w = widen(weights, n_floats);
+    orc_net net;
+    int rc = bind_net(&net, S, widths, cin, cout, out_relu, w, n_floats);
+    if (rc) {
+        free(w);
+        *rc_out = rc;
+        return 0.0;
+    }
+    long nin = (long)N * cin * H * W;
+    double *x = widen(in, nin);
+    double *x_raw = widen(in, nin);
+    if (flags & ORC_F_ENCODE_INPUT)
+        encode_input(x, N, cin, H, W, s);
+    orc_state st;
+    run_forward(&net, x, N, H, W, &st);
+
+    long no = (long)N * cout * H * W;
+    double *g = (double *)calloc(no, sizeof(double));
+    double loss = 0.0;
+    if (mode == 0) {
+        for (long i = 0; i < no; i++) {
+            double dlt = st.out[i] - (double)target[i];
+            loss += fabs(dlt);
+            g[i] = (dlt > 0.0 ? 1.0 : (dlt < 0.0 ? -1.0 : 0.0)) / (double)no;
+        }
+        loss /= (double)no;
+    } else {
+        for (long i = 0; i < no; i++)
+            g[i] = (double)target[i];
+    }
+    if (out_relu)
+        for (long i = 0; i < no; i++)
+            if (!(st.zout[i] > 0.0))
+                g[i] = 0.0;
+
+    /* gradient buffers, one per packed layer, bound to dweights */
+    memset(dweights, 0, sizeof(double) * n_floats);
+    orc_net dnet;
+    bind_net(&dnet, S, widths, cin, cout, out_relu, dweights, n_floats);
+    double *ge[9];
+    for (int q = 0; q <= S; q++)
+        ge[q] = (double *)calloc(act_size(&net, N, H, W, q), sizeof(double));
+
+    /* output head: out = convT_1(t_1) */
+    long n1 = act_size(&net, N, H, W, 1);
+    double *gt = (double *)calloc(n1, sizeof(double));
+    convT_adjoint(st.t[1], N, net.width[1], H >> 1, W >> 1, net.decW[1],
+                  cout, g, gt, (double *)dnet.decW[1], (double *)dnet.decB[1]);
+    free(g);
+    /* decoder, reversed: t_{q-1} = ReLU(zd_q) + e_{q-1}, zd_q = convT_q(t_q) */
+    for (int q = 2; q <= S; q++) {
+        long nq1 = act_size(&net, N, H, W, q - 1);
+        long nq = act_size(&net, N, H, W, q);
+        for (long i = 0; i < nq1; i++)
+            ge[q - 1][i] += gt[i]; /* skip branch */
+        double *gz = (double *)malloc(sizeof(double) * nq1);
+        for (long i = 0; i < nq1; i++)
+            gz[i] = st.zd[q][i] > 0.0 ? gt[i] : 0.0;
+        double *gtn = (double *)calloc(nq, sizeof(double));
+        convT_adjoint(st.t[q], N, net.width[q], H >> q, W >> q, net.decW[q],
+                      net.width[q - 1], gz, gtn, (double *)dnet.decW[q],
+                      (double *)dnet.decB[q]);
+        free(gz);
+        free(gt);
+        gt = gtn;
+    }
+    /* t_S = e_S */
+    {
+        long nS = act_size(&net, N, H, W, S);
+        for (long i = 0; i < nS; i++)
+            ge[S][i] += gt[i];
+        free(gt);
+    }
+    /* encoder, reversed: e_q = ReLU(z_q), z_q = conv_q(e_{q-1}) */
+    for (int q = S; q >= 1; q--) {
+        long nq = act_size(&net, N, H, W, q);
+        for (long i = 0; i < nq; i++)
+            if (!(st.z[q][i] > 0.0))
+                ge[q][i] = 0.0;
+        conv_adjoint(st.e[q - 1], N, net.width[q - 1], H >> (q - 1),
+                     W >> (q - 1), net.encW[q - 1], net.width[q], ge[q],
+                     ge[q - 1], (double *)dnet.encW[q - 1],
+                     (double *)dnet.encB[q - 1]);
+    }
+    if (dinput) {
+        for (long i = 0; i < nin; i++)
+            dinput[i] = ge[0][i];
+        if (flags & ORC_F_ENCODE_INPUT)
+            for (int n = 0; n < N; n++)
+                for (int c = 0; c < 3 && c < cin; c++)
+                    for (long p = 0; p < (long)H * W; p++) {
+                        long i = ((long)n * cin + c) * H * W + p;
+                        dinput[i] *= s / (1.0 + s * x_raw[i]);
+                    }
+    }
+    for (int q = 0; q <= S; q++)
+        free(ge[q]);
+    free_state(&st, S);
+    free(x);
+    free(x_raw);
+    free(w);
+    return loss;
+}
