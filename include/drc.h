@@ -1,0 +1,198 @@
+/*
+ * drc.h -- C ABI of the Deep Radiance Caching hot path on one GB300 (sm_103a).
+ *
+ * Method: Jiang & Kainz, "Deep Radiance Caching: Convolutional Autoencoders
+ * Deeper in Ray Tracing" (arXiv 1910.02480).  Two operations:
+ *   - denoise:      a convolutional autoencoder maps noisy low-sample
+ *                   hemispherical radiance maps (radiance RGB, distance,
+ *                   normal) to denoised radiance maps (Sec. 3.3);
+ *   - interpolate:  every first-hit pixel blends the k nearest cached maps
+ *                   with the weight w = w_p * w_n + w_p + eps, normalised
+ *                   (Sec. 3.2, Eqs. 4-6);
+ *   plus the gradient of an L1 loss through the autoencoder for training
+ *   (Sec. 3.3 loss, Sec. 4 training).
+ *
+ * Conventions for every call:
+ *   - Tensor pointers are caller-owned DEVICE memory on the context's device,
+ *     contiguous, 16-byte aligned, not overlapping unless stated.
+ *   - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream) and is asynchronous.  Argument errors are detected on the host
+ *     and returned before anything is enqueued.
+ *   - Errors raised on the device (a bounded wait that ran out) are latched in
+ *     a per-context status word and returned by drc_get_status().
+ *   - A context is used by one host thread at a time.  No C++ exception
+ *     crosses this interface.
+ */
+#ifndef DRC_H_
+#define DRC_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DRC_OK = 0,
+  DRC_ERR_INVALID_ARG = 1, /* bad pointer, shape, flag or configuration */
+  DRC_ERR_UNSUPPORTED = 2, /* valid request this build does not implement */
+  DRC_ERR_OOM = 3,         /* device allocation failed */
+  DRC_ERR_CUDA = 4,        /* a CUDA runtime call failed */
+  DRC_ERR_TIMEOUT = 5,     /* a device-side wait ran out (latched) */
+  DRC_ERR_INTERNAL = 6
+} drc_status;
+
+typedef enum {
+  DRC_PREC_FP32 = 0, /* fp32 operands split into two tf32 parts (3 products) */
+  DRC_PREC_BF16 = 1,
+  DRC_PREC_FP8_E4M3 = 2
+} drc_precision;
+
+/* Network description.  The autoencoder of Sec. 3.3 in the form used here:
+ * encoder stage s (s = 1..S): e_s = ReLU(conv3x3, stride 2, pad 1 (e_{s-1}) + b);
+ * decoder stage s (s = S..2): t_{s-1} = ReLU(convT3x3, stride 2, pad 1,
+ * output pad 1 (t_s) + b) + e_{s-1}  (t_S = e_S, skip added after the ReLU);
+ * head: out = convT3x3 s2 (t_1) + b, followed by ReLU when out_relu. */
+typedef struct {
+  int in_channels;  /* must be 7: [0..2] radiance (log), [3] distance, [4..6] normal */
+  int out_channels; /* must be 3 */
+  int num_stages;   /* S, 1..6 */
+  int widths[8];    /* encoder widths c_1..c_S; multiples of 16, <= 1024 */
+  int out_relu;     /* 0: linear head (default); 1: ReLU head (the paper's) */
+  drc_precision precision;
+  float exposure;    /* s in the log encode log1p(s L) / decode expm1(y)/s; > 0 */
+  int max_maps;      /* workspace sizing hint: largest N per call (grown on demand) */
+  int max_hw;        /* workspace sizing hint: largest H*W per map */
+  int wait_timeout_ms; /* bound on every device-side wait; 0 = 2000 ms */
+} drc_config;
+
+typedef struct drc_ctx drc_ctx;
+
+/* Packed weights: layers conv_1..conv_S then convT_S..convT_1, each as W
+ * followed by b, float32.  conv W is [Cout][Cin][3][3], convT W is
+ * [Cin][Cout][3][3] (the PyTorch Conv2d / ConvTranspose2d layouts).
+ * n_floats must equal sum over layers of 9*Cin*Cout + Cout. */
+size_t drc_weight_count(const drc_config *cfg);
+
+/* Create a context on the current CUDA device.  `weights_host` (host memory,
+ * n_floats floats, read during the call) may be NULL, in which case weights
+ * must be set with drc_set_weights before the first denoise.  On success
+ * *out owns all device memory it allocates; release it with drc_destroy. */
+drc_status drc_create(const drc_config *cfg, const float *weights_host,
+                      size_t n_floats, drc_ctx **out);
+
+/* Replace the weights: `weights` holds drc_weight_count() floats in host
+ * memory (weights_on_device = 0; copied before return) or device memory
+ * (weights_on_device = 1; read on `stream`).  Re-packs the tensor-core
+ * operand tiles on `stream`. */
+drc_status drc_set_weights(drc_ctx *ctx, const float *weights,
+                           int weights_on_device, void *stream);
+
+drc_status drc_destroy(drc_ctx *ctx);
+
+/* drc_denoise flags */
+#define DRC_F_ENCODE_INPUT 0x1u  /* apply log1p(s L) to input channels 0..2 */
+#define DRC_F_DECODE_OUTPUT 0x2u /* write expm1(y)/s instead of log-space y */
+#define DRC_F_DEBUG_STALL 0x100u /* test only: the first device wait never
+                                    completes; the call's kernels give up after
+                                    the context's wait timeout and latch
+                                    DRC_ERR_TIMEOUT (output undefined) */
+
+/* Denoise N maps (Sec. 3.3).
+ *   in:      device [N][7][H][W] float32 (NCHW), log radiance unless
+ *            DRC_F_ENCODE_INPUT;
+ *   out:     device [N][3][H][W] float32, log radiance unless
+ *            DRC_F_DECODE_OUTPUT;
+ *   payload: nullable; device [N][3] float32, overwritten with E/pi of the
+ *            decoded map (linear radiance expm1(y)/s): the irradiance a
+ *            white diffuse surface receives from the map, divided by pi
+ *            (Eq. 2 with a Lambertian BRDF).  Lat-long layout: row i spans
+ *            polar angle [i, i+1] * pi/(2H) from the normal, column j
+ *            azimuth [j, j+1] * 2 pi / W.
+ * H and W must be multiples of 2^S and at least 2^S; N >= 0 (0 is a no-op). */
+drc_status drc_denoise(drc_ctx *ctx, const float *in, float *out,
+                       float *payload, int N, int H, int W, unsigned flags,
+                       void *stream);
+
+/* Caches for interpolation (Sec. 3.2). */
+typedef struct {
+  int n;              /* number of caches, >= 1 */
+  int H, W;           /* map size (LOOKUP only) */
+  const float *maps;  /* LOOKUP: device [n][3][H][W] linear radiance, else NULL */
+  const float *payload; /* IRRADIANCE: device [n][3], else may be NULL */
+  const float *pos;   /* device [n][3] first-hit position (WORLD metric) */
+  const float *nrm;   /* device [n][3] surface normal (any length; 0 = none) */
+  const int *pix;     /* device [n][2] (x, y) integer pixel (IMAGE metric) */
+} drc_caches;
+
+typedef struct {
+  int width, height;  /* pixel p = y * width + x */
+  const float *pos;   /* device [P][3] first-hit position (WORLD metric) */
+  const float *nrm;   /* device [P][3] surface normal */
+  const float *dir;   /* LOOKUP: device [P][3] world direction (normalised by
+                         the callee), else NULL */
+} drc_gbuffer;
+
+#define DRC_METRIC_IMAGE 0  /* distance in pixels on the image plane (the paper's) */
+#define DRC_METRIC_WORLD 1  /* distance between first-hit positions */
+#define DRC_WP_INVERSE 0    /* w_p = r / (d + delta_rel * r) */
+#define DRC_WP_LINEAR 1     /* w_p = max(0, 1 - d / r) */
+#define DRC_INTERP_IRRADIANCE 0 /* out = sum_j W_j payload_j */
+#define DRC_INTERP_LOOKUP 1     /* out = sum_j W_j R_j(dir in cache j's frame) */
+
+typedef struct {
+  int k;          /* neighbours, 1..32 */
+  int metric;     /* DRC_METRIC_* */
+  int wp_form;    /* DRC_WP_* */
+  int mode;       /* DRC_INTERP_* */
+  float r;        /* grid spacing (pixels or world units), > 0 */
+  float eps;      /* the small term of Eq. 4, >= 0 (1e-6 typical) */
+  float delta_rel;/* INVERSE softening, delta = delta_rel * r, > 0 */
+  int *nbr_out;   /* nullable; device [P][k] int32, the chosen cache indices
+                     in (d^2, index) order -- a diagnostic output */
+} drc_interp_params;
+
+/* Interpolate cached values at every pixel (Sec. 3.2).  For each pixel: the
+ * k caches nearest by (d^2, index) order; w_p as selected; w_n =
+ * max(0, n_j . n_p) for unit normals (0 for a zero-length normal);
+ * w = w_p w_n + w_p + eps; W_j = w_j / sum w; out = sum W_j value_j.
+ * LOOKUP: value_j = bilinear lookup of map j at the pixel direction in cache
+ * j's frame (normal = map Z; up = +Z, or +Y when the normal is along Z;
+ * t = normalize(up x n), b = n x t), 0 when the direction is not above the
+ * cache's horizon.
+ * out_rgb: device [P][3] float32.  The context keeps a grid over the caches
+ * in its own device memory (grown on demand). */
+drc_status drc_interpolate(drc_ctx *ctx, const drc_caches *caches,
+                           const drc_gbuffer *gbuf,
+                           const drc_interp_params *params, float *out_rgb,
+                           void *stream);
+
+/* drc_backward flags */
+#define DRC_BWD_L1_TARGET 0x1u /* target = ground truth [N][3][H][W] (log
+                                  radiance); loss = mean |out - target| */
+#define DRC_BWD_GRAD_OUT 0x2u  /* target = dL/dout [N][3][H][W] */
+
+/* Gradient of the loss through the network (Sec. 4 training).
+ *   in:       device [N][7][H][W] (as drc_denoise; flags may add
+ *             DRC_F_ENCODE_INPUT);
+ *   dweights: device, drc_weight_count() floats, packed like the weights,
+ *             overwritten;
+ *   dinput:   nullable, device [N][7][H][W];
+ *   loss:     nullable, device float scalar (L1_TARGET only).  */
+drc_status drc_backward(drc_ctx *ctx, const float *in, const float *target,
+                        int N, int H, int W, unsigned flags, float *dweights,
+                        float *dinput, float *loss, void *stream);
+
+/* Synchronise `stream` and return (then clear) the latched device status:
+ * DRC_OK or DRC_ERR_TIMEOUT. */
+drc_status drc_get_status(drc_ctx *ctx, void *stream);
+
+/* Human-readable description of the last error on this context ("" if
+ * none).  Valid until the next call on the context. */
+const char *drc_last_error(drc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DRC_H_ */

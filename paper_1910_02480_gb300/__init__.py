@@ -1,0 +1,246 @@
+"""Deep Radiance Caching hot path on one GB300 (sm_103a).
+
+Python binding of the C ABI in ``include/drc.h`` (``libdrc.so``, built from
+``csrc/`` by ``build.py``).  This module only marshals arguments: device
+memory and streams come from PyTorch, every step of the computation runs in
+the library's CUDA kernels.  There is no CPU fallback: if the library is
+missing or no sm_103a device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LIB_PATH = _build.LIB
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_INTERNAL = range(7)
+STATUS_NAMES = {0: "DRC_OK", 1: "DRC_ERR_INVALID_ARG", 2: "DRC_ERR_UNSUPPORTED", 3: "DRC_ERR_OOM",
+                4: "DRC_ERR_CUDA", 5: "DRC_ERR_TIMEOUT", 6: "DRC_ERR_INTERNAL"}
+PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
+
+F_ENCODE_INPUT = 0x1
+F_DECODE_OUTPUT = 0x2
+F_DEBUG_STALL = 0x100
+METRIC_IMAGE, METRIC_WORLD = 0, 1
+WP_INVERSE, WP_LINEAR = 0, 1
+INTERP_IRRADIANCE, INTERP_LOOKUP = 0, 1
+BWD_L1_TARGET, BWD_GRAD_OUT = 0x1, 0x2
+
+
+class DrcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("in_channels", ctypes.c_int), ("out_channels", ctypes.c_int),
+                ("num_stages", ctypes.c_int), ("widths", ctypes.c_int * 8),
+                ("out_relu", ctypes.c_int), ("precision", ctypes.c_int),
+                ("exposure", ctypes.c_float), ("max_maps", ctypes.c_int),
+                ("max_hw", ctypes.c_int), ("wait_timeout_ms", ctypes.c_int)]
+
+
+class Caches(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("maps", ctypes.c_void_p), ("payload", ctypes.c_void_p),
+                ("pos", ctypes.c_void_p), ("nrm", ctypes.c_void_p), ("pix", ctypes.c_void_p)]
+
+
+class GBuffer(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("pos", ctypes.c_void_p),
+                ("nrm", ctypes.c_void_p), ("dir", ctypes.c_void_p)]
+
+
+class InterpParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("metric", ctypes.c_int), ("wp_form", ctypes.c_int),
+                ("mode", ctypes.c_int), ("r", ctypes.c_float), ("eps", ctypes.c_float),
+                ("delta_rel", ctypes.c_float), ("nbr_out", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load libdrc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libdrc.so is not built: run paper_1910_02480_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, U = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint
+    lib.drc_weight_count.argtypes = [ctypes.POINTER(Config)]
+    lib.drc_weight_count.restype = ctypes.c_size_t
+    lib.drc_create.argtypes = [ctypes.POINTER(Config), P, ctypes.c_size_t, ctypes.POINTER(P)]
+    lib.drc_create.restype = I
+    lib.drc_set_weights.argtypes = [P, P, I, P]
+    lib.drc_set_weights.restype = I
+    lib.drc_destroy.argtypes = [P]
+    lib.drc_destroy.restype = I
+    lib.drc_denoise.argtypes = [P, P, P, P, I, I, I, U, P]
+    lib.drc_denoise.restype = I
+    lib.drc_interpolate.argtypes = [P, ctypes.POINTER(Caches), ctypes.POINTER(GBuffer),
+                                    ctypes.POINTER(InterpParams), P, P]
+    lib.drc_interpolate.restype = I
+    lib.drc_backward.argtypes = [P, P, P, I, I, I, U, P, P, P, P]
+    lib.drc_backward.restype = I
+    lib.drc_get_status.argtypes = [P, P]
+    lib.drc_get_status.restype = I
+    lib.drc_last_error.argtypes = [P]
+    lib.drc_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def make_config(widths, precision="fp32", exposure=1.0, out_relu=False, max_maps=0, max_hw=0,
+                wait_timeout_ms=0, in_channels=7, out_channels=3):
+    c = Config()
+    c.in_channels = in_channels
+    c.out_channels = out_channels
+    c.num_stages = len(widths)
+    for i, w in enumerate(widths):
+        c.widths[i] = int(w)
+    c.out_relu = int(bool(out_relu))
+    c.precision = PREC[precision] if isinstance(precision, str) else int(precision)
+    c.exposure = float(exposure)
+    c.max_maps = int(max_maps)
+    c.max_hw = int(max_hw)
+    c.wait_timeout_ms = int(wait_timeout_ms)
+    return c
+
+
+def weight_count(widths) -> int:
+    cfg = make_config(widths)
+    return int(load_library().drc_weight_count(ctypes.byref(cfg)))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """One drc_ctx: a network (widths, precision, exposure) with its weights."""
+
+    def __init__(self, widths, weights=None, precision="fp32", exposure=1.0, out_relu=False,
+                 max_maps=0, max_hw=0, wait_timeout_ms=0):
+        self._lib = load_library()
+        self.widths = list(widths)
+        self.precision = precision
+        self.exposure = float(exposure)
+        self.cfg = make_config(widths, precision, exposure, out_relu, max_maps, max_hw, wait_timeout_ms)
+        self.n_weights = int(self._lib.drc_weight_count(ctypes.byref(self.cfg)))
+        self._ctx = ctypes.c_void_p()
+        wh = None
+        if weights is not None and not hasattr(weights, "is_cuda"):
+            wh = np.ascontiguousarray(weights, dtype=np.float32)
+            if wh.size != self.n_weights:
+                raise ValueError("expected %d weights, got %d" % (self.n_weights, wh.size))
+        rc = self._lib.drc_create(ctypes.byref(self.cfg),
+                                  None if wh is None else wh.ctypes.data_as(ctypes.c_void_p),
+                                  self.n_weights if wh is not None else 0, ctypes.byref(self._ctx))
+        if rc != OK:
+            raise DrcError(rc, "drc_create failed")
+        if weights is not None and hasattr(weights, "is_cuda"):
+            self.set_weights(weights)
+
+    def _check(self, rc, what):
+        if rc != OK:
+            msg = self._lib.drc_last_error(self._ctx).decode()
+            raise DrcError(rc, "%s: %s" % (what, msg))
+
+    def close(self):
+        if self._ctx:
+            self._lib.drc_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_weights(self, weights, stream=None):
+        if hasattr(weights, "is_cuda") and weights.is_cuda:
+            assert weights.dtype.itemsize == 4 and weights.numel() == self.n_weights
+            w = weights.contiguous()
+            self._check(self._lib.drc_set_weights(self._ctx, _ptr(w), 1, _stream(stream)), "drc_set_weights")
+        else:
+            w = np.ascontiguousarray(weights, dtype=np.float32)
+            if w.size != self.n_weights:
+                raise ValueError("expected %d weights, got %d" % (self.n_weights, w.size))
+            self._check(self._lib.drc_set_weights(self._ctx, w.ctypes.data_as(ctypes.c_void_p), 0, None),
+                        "drc_set_weights")
+
+    def denoise(self, x, out=None, payload=None, flags=0, stream=None, want_payload=False):
+        """x: cuda float32 [N,7,H,W] -> out [N,3,H,W] (and payload [N,3])."""
+        import torch
+        N, C, H, W = x.shape
+        if out is None:
+            out = torch.empty((N, 3, H, W), dtype=torch.float32, device=x.device)
+        if payload is None and want_payload:
+            payload = torch.empty((N, 3), dtype=torch.float32, device=x.device)
+        rc = self._lib.drc_denoise(self._ctx, _ptr(x), _ptr(out), _ptr(payload), N, H, W, flags,
+                                   _stream(stream))
+        self._check(rc, "drc_denoise")
+        return (out, payload) if (payload is not None) else out
+
+    def interpolate(self, caches, gbuf, k, metric, wp_form, mode, r, eps=1e-6, delta_rel=1e-3,
+                    out=None, nbr_out=None, stream=None):
+        """caches / gbuf: dicts of cuda tensors (see drc.h)."""
+        import torch
+        c = Caches()
+        c.n = int(caches["nrm"].shape[0])
+        maps = caches.get("maps")
+        c.H = int(maps.shape[2]) if maps is not None else 0
+        c.W = int(maps.shape[3]) if maps is not None else 0
+        c.maps = _ptr(maps)
+        c.payload = _ptr(caches.get("payload"))
+        c.pos = _ptr(caches.get("pos"))
+        c.nrm = _ptr(caches.get("nrm"))
+        c.pix = _ptr(caches.get("pix"))
+        g = GBuffer()
+        g.width, g.height = int(gbuf["width"]), int(gbuf["height"])
+        g.pos = _ptr(gbuf.get("pos"))
+        g.nrm = _ptr(gbuf.get("nrm"))
+        g.dir = _ptr(gbuf.get("dir"))
+        p = InterpParams()
+        p.k, p.metric, p.wp_form, p.mode = int(k), int(metric), int(wp_form), int(mode)
+        p.r, p.eps, p.delta_rel = float(r), float(eps), float(delta_rel)
+        p.nbr_out = _ptr(nbr_out)
+        P = g.width * g.height
+        if out is None:
+            dev = caches["nrm"].device
+            out = torch.empty((P, 3), dtype=torch.float32, device=dev)
+        rc = self._lib.drc_interpolate(self._ctx, ctypes.byref(c), ctypes.byref(g), ctypes.byref(p),
+                                       _ptr(out), _stream(stream))
+        self._check(rc, "drc_interpolate")
+        return out
+
+    def backward(self, x, target, flags=BWD_L1_TARGET, dweights=None, dinput=None, loss=None,
+                 stream=None):
+        import torch
+        N, C, H, W = x.shape
+        if dweights is None:
+            dweights = torch.empty(self.n_weights, dtype=torch.float32, device=x.device)
+        rc = self._lib.drc_backward(self._ctx, _ptr(x), _ptr(target), N, H, W, flags, _ptr(dweights),
+                                    _ptr(dinput), _ptr(loss), _stream(stream))
+        self._check(rc, "drc_backward")
+        return dweights
+
+    def status(self, stream=None):
+        """Synchronise and return the latched device status code."""
+        rc = self._lib.drc_get_status(self._ctx, _stream(stream))
+        return rc

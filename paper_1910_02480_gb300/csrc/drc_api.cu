@@ -1,0 +1,629 @@
+// drc_api.cu -- the C ABI of include/drc.h: context, argument checks,
+// weight packing, workspace, and the per-layer launch sequence of the
+// autoencoder (Sec. 3.3) and of the interpolation (Sec. 3.2).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "conv_tc.cuh"
+#include "drc.h"
+#include "drc_status.cuh"
+#include "interp.cuh"
+
+using namespace drc;
+
+static_assert(ERR_TIMEOUT == DRC_ERR_TIMEOUT, "device status code mismatch");
+
+namespace {
+
+struct Layer {
+  int kind;
+  int Cin, Cout;       // raw channels of the layer (LK_HEAD: Cout = 3)
+  size_t w_off, b_off; // offsets (floats) into the packed raw weights
+  int BN, n_tiles, num_phases;
+  PhaseDesc ph[4];
+  int phase_order[4];
+  size_t pack_off, pack_bytes;  // in the packed operand buffer(s)
+};
+
+}  // namespace
+
+struct drc_ctx {
+  drc_config cfg;
+  int device = 0;
+  int num_sms = 0;
+  int prec = PREC_TF32X3;
+  size_t n_floats = 0;
+  std::vector<Layer> layers;  // conv_1..conv_S, convT_S..convT_2, head
+  float *d_wraw = nullptr;
+  uint8_t *d_pack = nullptr, *d_pack_lo = nullptr;
+  float *d_bscale = nullptr;
+  size_t pack_total = 0;
+  void *d_act = nullptr;
+  size_t act_bytes = 0;
+  void *d_iscratch = nullptr;
+  size_t iscratch_bytes = 0;
+  int *d_status = nullptr;
+  bool weights_set = false;
+  unsigned long long timeout_ns = 0;
+  std::string err;
+};
+
+namespace {
+
+drc_status fail(drc_ctx *c, drc_status s, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+drc_status fail(drc_ctx *c, drc_status s, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return s;
+}
+
+drc_status cuda_fail(drc_ctx *c, cudaError_t e, const char *what) {
+  cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation) return fail(c, DRC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(c, DRC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int bke_of(int prec) { return KROW_BYTES / (prec == PREC_TF32X3 ? 4 : (prec == PREC_BF16 ? 2 : 1)); }
+int elem_act(int prec) { return prec == PREC_TF32X3 ? 4 : 2; }
+
+int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+int pick_bn(int Cout) {
+  if (Cout <= 256) return Cout;
+  for (int bn = 256; bn >= 16; bn -= 16)
+    if (Cout % bn == 0) return bn;
+  return 16;
+}
+
+// Decoder phase (oy, ox): output pixel (2a+oy, 2b+ox) gathers input
+// (a+di, b+dj) through kernel tap (u, v) with 2(a+di) + u - 1 = 2a + oy.
+void convT_phase(PhaseDesc &pd, int oy, int ox, int Cin, int bke) {
+  struct RT {
+    int u, d;
+  };
+  RT rows[2], cols[2];
+  int nr = 0, nc = 0;
+  if (oy == 0) {
+    rows[nr++] = {1, 0};
+  } else {
+    rows[nr++] = {0, 1};
+    rows[nr++] = {2, 0};
+  }
+  if (ox == 0) {
+    cols[nc++] = {1, 0};
+  } else {
+    cols[nc++] = {0, 1};
+    cols[nc++] = {2, 0};
+  }
+  memset(&pd, 0, sizeof pd);
+  pd.oy = oy;
+  pd.ox = ox;
+  pd.ntaps = nr * nc;
+  for (int r = 0; r < nr; ++r)
+    for (int c = 0; c < nc; ++c) {
+      const int t = r * nc + c;
+      pd.u[t] = (signed char)rows[r].u;
+      pd.v[t] = (signed char)cols[c].u;
+      pd.dy[t] = (signed char)rows[r].d;
+      pd.dx[t] = (signed char)cols[c].d;
+    }
+  pd.num_kb = ceil_div((long long)pd.ntaps * Cin, bke);
+}
+
+// Lay out every layer's GEMM(s) and the packed operand buffer.
+void plan_layers(drc_ctx *c) {
+  const drc_config &g = c->cfg;
+  const int S = g.num_stages;
+  const int bke = bke_of(c->prec);
+  std::vector<int> wd(S + 1);
+  wd[0] = g.in_channels;
+  for (int s = 1; s <= S; ++s) wd[s] = g.widths[s - 1];
+  c->layers.clear();
+  size_t off = 0, pack = 0;
+  auto finish = [&](Layer &L) {
+    L.pack_off = pack;
+    size_t bytes = 0;
+    for (int p = 0; p < L.num_phases; ++p) {
+      L.ph[p].b_off = (long long)(pack + bytes);
+      bytes += (size_t)L.n_tiles * L.ph[p].num_kb * L.BN * KROW_BYTES;
+    }
+    L.pack_bytes = bytes;
+    pack += bytes;
+    // heaviest phase first
+    for (int p = 0; p < 4; ++p) L.phase_order[p] = p < L.num_phases ? p : 0;
+    for (int a = 0; a < L.num_phases; ++a)
+      for (int b = a + 1; b < L.num_phases; ++b)
+        if (L.ph[L.phase_order[b]].num_kb > L.ph[L.phase_order[a]].num_kb) {
+          int t = L.phase_order[a];
+          L.phase_order[a] = L.phase_order[b];
+          L.phase_order[b] = t;
+        }
+    c->layers.push_back(L);
+  };
+  for (int s = 1; s <= S; ++s) {
+    Layer L;
+    memset(&L, 0, sizeof L);
+    L.kind = s == 1 ? LK_CONV_NCHW7 : LK_CONV;
+    L.Cin = wd[s - 1];
+    L.Cout = wd[s];
+    L.w_off = off;
+    off += 9ull * L.Cin * L.Cout;
+    L.b_off = off;
+    off += L.Cout;
+    L.BN = pick_bn(L.Cout);
+    L.n_tiles = L.Cout / L.BN;
+    L.num_phases = 1;
+    PhaseDesc &pd = L.ph[0];
+    pd.ntaps = 9;
+    for (int t = 0; t < 9; ++t) {
+      pd.u[t] = pd.dy[t] = (signed char)(t / 3);
+      pd.v[t] = pd.dx[t] = (signed char)(t % 3);
+    }
+    pd.num_kb = ceil_div(s == 1 ? 63 : 9ll * L.Cin, bke);
+    finish(L);
+  }
+  for (int s = S; s >= 1; --s) {
+    Layer L;
+    memset(&L, 0, sizeof L);
+    L.Cin = wd[s];
+    L.Cout = s == 1 ? g.out_channels : wd[s - 1];
+    L.w_off = off;
+    off += 9ull * L.Cin * L.Cout;
+    L.b_off = off;
+    off += L.Cout;
+    if (s == 1) {
+      L.kind = LK_HEAD;
+      L.BN = 16;
+      L.n_tiles = 1;
+      L.num_phases = 1;
+      PhaseDesc &pd = L.ph[0];
+      pd.ntaps = 4;
+      for (int t = 0; t < 4; ++t) {
+        pd.dy[t] = (signed char)(t >> 1);
+        pd.dx[t] = (signed char)(t & 1);
+      }
+      pd.num_kb = ceil_div(4ll * L.Cin, bke);
+    } else {
+      L.kind = LK_CONVT;
+      L.BN = pick_bn(L.Cout);
+      L.n_tiles = L.Cout / L.BN;
+      L.num_phases = 4;
+      for (int p = 0; p < 4; ++p) convT_phase(L.ph[p], p >> 1, p & 1, L.Cin, bke);
+    }
+    finish(L);
+  }
+  c->pack_total = pack;
+}
+
+drc_status check_config(const drc_config *g, drc_ctx *c) {
+  if (!g) return fail(c, DRC_ERR_INVALID_ARG, "config is NULL");
+  if (g->in_channels != 7) return fail(c, DRC_ERR_INVALID_ARG, "in_channels must be 7 (got %d)", g->in_channels);
+  if (g->out_channels != 3) return fail(c, DRC_ERR_INVALID_ARG, "out_channels must be 3 (got %d)", g->out_channels);
+  if (g->num_stages < 1 || g->num_stages > 6)
+    return fail(c, DRC_ERR_INVALID_ARG, "num_stages must be 1..6 (got %d)", g->num_stages);
+  for (int s = 0; s < g->num_stages; ++s)
+    if (g->widths[s] < 16 || g->widths[s] > 1024 || g->widths[s] % 16)
+      return fail(c, DRC_ERR_INVALID_ARG, "widths[%d] = %d: must be a multiple of 16 in 16..1024", s, g->widths[s]);
+  if (g->precision < DRC_PREC_FP32 || g->precision > DRC_PREC_FP8_E4M3)
+    return fail(c, DRC_ERR_INVALID_ARG, "unknown precision %d", (int)g->precision);
+  if (g->precision == DRC_PREC_FP8_E4M3) return fail(c, DRC_ERR_UNSUPPORTED, "fp8 precision is not built yet");
+  if (!(g->exposure > 0.f) || !std::isfinite(g->exposure))
+    return fail(c, DRC_ERR_INVALID_ARG, "exposure must be finite and > 0");
+  if (g->wait_timeout_ms < 0) return fail(c, DRC_ERR_INVALID_ARG, "wait_timeout_ms must be >= 0");
+  return DRC_OK;
+}
+
+size_t weight_count(const drc_config *g) {
+  size_t n = 0;
+  int prev = g->in_channels;
+  for (int s = 0; s < g->num_stages; ++s) {
+    n += 9ull * prev * g->widths[s] + g->widths[s];
+    prev = g->widths[s];
+  }
+  for (int s = g->num_stages - 1; s >= 0; --s) {
+    const int co = s == 0 ? g->out_channels : g->widths[s - 1];
+    n += 9ull * g->widths[s] * co + co;
+  }
+  return n;
+}
+
+bool is_device_ptr(const void *p, int device) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (at.type == cudaMemoryTypeDevice) return at.device == device;
+  return at.type == cudaMemoryTypeManaged;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+drc_status check_dev(drc_ctx *c, const void *p, const char *name, bool nullable) {
+  if (!p) return nullable ? DRC_OK : fail(c, DRC_ERR_INVALID_ARG, "%s is NULL", name);
+  if (!aligned16(p)) return fail(c, DRC_ERR_INVALID_ARG, "%s is not 16-byte aligned", name);
+  if (!is_device_ptr(p, c->device))
+    return fail(c, DRC_ERR_INVALID_ARG, "%s is not device memory on device %d", name, c->device);
+  return DRC_OK;
+}
+
+drc_status pack_all(drc_ctx *c, cudaStream_t st) {
+  for (const Layer &L : c->layers) {
+    PackArgs p;
+    memset(&p, 0, sizeof p);
+    p.kind = L.kind;
+    p.wraw = c->d_wraw + L.w_off;
+    p.Cin = L.Cin;
+    p.Cout = L.Cout;
+    p.BN = L.BN;
+    p.n_tiles = L.n_tiles;
+    p.num_phases = L.num_phases;
+    for (int i = 0; i < 4; ++i) p.ph[i] = L.ph[i];
+    p.B = c->d_pack;
+    p.B_lo = c->d_pack_lo;
+    p.bscale = c->d_bscale;
+    p.total_chunks = (long long)(L.pack_bytes / 16);
+    cudaError_t e = launch_pack(p, c->prec, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "weight packing");
+  }
+  return DRC_OK;
+}
+
+size_t act_bytes_for(const drc_ctx *c, long long N, int H, int W) {
+  size_t b = 0;
+  for (int s = 1; s <= c->cfg.num_stages; ++s)
+    b += (((size_t)N * (H >> s) * (W >> s) * c->cfg.widths[s - 1] * elem_act(c->prec)) + 255) & ~(size_t)255;
+  return b;
+}
+
+drc_status ensure_act(drc_ctx *c, long long N, int H, int W) {
+  const size_t need = act_bytes_for(c, N, H, W);
+  if (need <= c->act_bytes) return DRC_OK;
+  if (c->d_act) cudaFree(c->d_act);
+  c->d_act = nullptr;
+  c->act_bytes = 0;
+  cudaError_t e = cudaMalloc(&c->d_act, need);
+  if (e != cudaSuccess) return cuda_fail(c, e, "activation workspace");
+  c->act_bytes = need;
+  return DRC_OK;
+}
+
+void fill_common(const drc_ctx *c, const Layer &L, ConvArgs &a) {
+  memset(&a, 0, sizeof a);
+  a.kind = L.kind;
+  a.B = c->d_pack;
+  a.B_lo = c->d_pack_lo;
+  a.bias = c->d_wraw + L.b_off;
+  a.BN = L.BN;
+  a.n_tiles = L.n_tiles;
+  a.num_phases = L.num_phases;
+  for (int i = 0; i < 4; ++i) {
+    a.ph[i] = L.ph[i];
+    a.phase_order[i] = L.phase_order[i];
+  }
+  a.exposure = c->cfg.exposure;
+  a.inv_exposure = 1.0f / c->cfg.exposure;
+  a.act_scale_in = 1.f;
+  a.act_scale_out = 1.f;
+  a.status = c->d_status;
+  a.timeout_ns = c->timeout_ns;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t drc_weight_count(const drc_config *cfg) { return cfg ? weight_count(cfg) : 0; }
+
+drc_status drc_create(const drc_config *cfg, const float *weights_host, size_t n_floats, drc_ctx **out) {
+  if (!out) return DRC_ERR_INVALID_ARG;
+  *out = nullptr;
+  drc_status s = check_config(cfg, nullptr);
+  if (s != DRC_OK) return s;
+  drc_ctx *c = new (std::nothrow) drc_ctx();
+  if (!c) return DRC_ERR_OOM;
+  c->cfg = *cfg;
+  c->prec = cfg->precision == DRC_PREC_FP32 ? PREC_TF32X3 : (cfg->precision == DRC_PREC_BF16 ? PREC_BF16 : PREC_FP8);
+  c->n_floats = weight_count(cfg);
+  c->timeout_ns = (unsigned long long)(cfg->wait_timeout_ms > 0 ? cfg->wait_timeout_ms : 2000) * 1000000ull;
+  if (weights_host && n_floats != c->n_floats) {
+    delete c;
+    return DRC_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  int major = 0, minor = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, c->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, c->device);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return DRC_ERR_CUDA;
+  }
+  if (major != 10 || minor != 3) {
+    delete c;
+    return DRC_ERR_UNSUPPORTED;  // built for sm_103a only
+  }
+  plan_layers(c);
+  e = cudaMalloc(&c->d_wraw, c->n_floats * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_pack, c->pack_total);
+  if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&c->d_pack_lo, c->pack_total);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    drc_destroy(c);
+    return e == cudaErrorMemoryAllocation ? DRC_ERR_OOM : DRC_ERR_CUDA;
+  }
+  if (cfg->max_maps > 0 && cfg->max_hw > 0) {
+    int side = (int)std::sqrt((double)cfg->max_hw);
+    if (ensure_act(c, cfg->max_maps, side, side) != DRC_OK) {
+      drc_destroy(c);
+      return DRC_ERR_OOM;
+    }
+  }
+  if (weights_host) {
+    s = drc_set_weights(c, weights_host, 0, nullptr);
+    if (s == DRC_OK && cudaDeviceSynchronize() != cudaSuccess) s = DRC_ERR_CUDA;
+    if (s != DRC_OK) {
+      drc_destroy(c);
+      return s;
+    }
+  }
+  *out = c;
+  return DRC_OK;
+}
+
+drc_status drc_set_weights(drc_ctx *c, const float *weights, int weights_on_device, void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  if (!weights) return fail(c, DRC_ERR_INVALID_ARG, "weights is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (weights_on_device) {
+    if (!is_device_ptr(weights, c->device))
+      return fail(c, DRC_ERR_INVALID_ARG, "weights_on_device set but weights is not device memory");
+    e = cudaMemcpyAsync(c->d_wraw, weights, c->n_floats * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  } else {
+    e = cudaMemcpy(c->d_wraw, weights, c->n_floats * sizeof(float), cudaMemcpyHostToDevice);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "weight upload");
+  drc_status s = pack_all(c, st);
+  if (s == DRC_OK) c->weights_set = true;
+  return s;
+}
+
+drc_status drc_destroy(drc_ctx *c) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  cudaFree(c->d_wraw);
+  cudaFree(c->d_pack);
+  cudaFree(c->d_pack_lo);
+  cudaFree(c->d_bscale);
+  cudaFree(c->d_act);
+  cudaFree(c->d_iscratch);
+  cudaFree(c->d_status);
+  cudaGetLastError();
+  delete c;
+  return DRC_OK;
+}
+
+drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, int N, int H, int W,
+                       unsigned flags, void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  const int S = c->cfg.num_stages;
+  const unsigned known = DRC_F_ENCODE_INPUT | DRC_F_DECODE_OUTPUT | DRC_F_DEBUG_STALL;
+  if (flags & ~known) return fail(c, DRC_ERR_INVALID_ARG, "unknown flags 0x%x", flags & ~known);
+  if (N < 0) return fail(c, DRC_ERR_INVALID_ARG, "N must be >= 0");
+  if (H < (1 << S) || W < (1 << S) || H % (1 << S) || W % (1 << S))
+    return fail(c, DRC_ERR_INVALID_ARG, "H, W (%d, %d) must be positive multiples of 2^S = %d", H, W, 1 << S);
+  if (payload && H > 256) return fail(c, DRC_ERR_INVALID_ARG, "payload needs H <= 256");
+  if ((long long)N * H * W * 7 >= (1ll << 31))
+    return fail(c, DRC_ERR_INVALID_ARG, "N*7*H*W must stay below 2^31 elements per call");
+  if (!c->weights_set) return fail(c, DRC_ERR_INVALID_ARG, "weights were never set");
+  if (N == 0) return DRC_OK;
+  drc_status s;
+  if ((s = check_dev(c, in, "in", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, out, "out", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, payload, "payload", true)) != DRC_OK) return s;
+  if ((s = ensure_act(c, N, H, W)) != DRC_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+
+  // activation buffers e_1..e_S (decoder outputs overwrite them in place)
+  std::vector<uint8_t *> act(S + 1, nullptr);
+  {
+    size_t off = 0;
+    for (int s2 = 1; s2 <= S; ++s2) {
+      act[s2] = static_cast<uint8_t *>(c->d_act) + off;
+      off += (((size_t)N * (H >> s2) * (W >> s2) * c->cfg.widths[s2 - 1] * elem_act(c->prec)) + 255) &
+             ~(size_t)255;
+    }
+  }
+  if (payload) {
+    e = cudaMemsetAsync(payload, 0, (size_t)N * 3 * sizeof(float), st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "payload clear");
+  }
+  const int debug_stall = (flags & DRC_F_DEBUG_STALL) ? 1 : 0;
+  for (size_t li = 0; li < c->layers.size(); ++li) {
+    const Layer &L = c->layers[li];
+    ConvArgs a;
+    fill_common(c, L, a);
+    a.debug_stall = debug_stall && li == 0;
+    a.N = N;
+    if (L.kind == LK_CONV_NCHW7 || L.kind == LK_CONV) {
+      const int s2 = (int)li + 1;  // encoder stage
+      a.x = s2 == 1 ? static_cast<const void *>(in) : act[s2 - 1];
+      a.y = act[s2];
+      a.Hin = H >> (s2 - 1);
+      a.Win = W >> (s2 - 1);
+      a.Cin = L.Cin;
+      a.Hrow = a.Hout = H >> s2;
+      a.Wrow = a.Wout = W >> s2;
+      a.Cout = L.Cout;
+      a.relu = 1;
+      a.encode = (s2 == 1 && (flags & DRC_F_ENCODE_INPUT)) ? 1 : 0;
+    } else if (L.kind == LK_CONVT) {
+      const int s2 = S - ((int)li - S);  // decoder stage S..2
+      a.x = act[s2];
+      a.y = act[s2 - 1];
+      a.skip = act[s2 - 1];
+      a.Hin = a.Hrow = H >> s2;
+      a.Win = a.Wrow = W >> s2;
+      a.Cin = L.Cin;
+      a.Hout = H >> (s2 - 1);
+      a.Wout = W >> (s2 - 1);
+      a.Cout = L.Cout;
+      a.relu = 1;
+    } else {  // head
+      a.x = act[1];
+      a.y = out;
+      a.payload = payload;
+      a.Hin = a.Hrow = H >> 1;
+      a.Win = a.Wrow = W >> 1;
+      a.Cin = L.Cin;
+      a.Hout = H;
+      a.Wout = W;
+      a.Cout = 3;
+      a.relu = c->cfg.out_relu ? 1 : 0;
+      a.decode = (flags & DRC_F_DECODE_OUTPUT) ? 1 : 0;
+      if (payload) {
+        const double pi = 3.14159265358979323846;
+        for (int i = 0; i < H; ++i) {
+          const double t0 = i * pi / (2.0 * H), t1 = (i + 1) * pi / (2.0 * H);
+          a.band[i] = (float)((std::sin(t1) * std::sin(t1) - std::sin(t0) * std::sin(t0)) / W);
+        }
+      }
+    }
+    a.M = (int)((long long)N * a.Hrow * a.Wrow);
+    a.m_tiles = ceil_div(a.M, BM);
+    e = launch_conv(a, c->prec, c->num_sms, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "layer launch");
+  }
+  return DRC_OK;
+}
+
+drc_status drc_interpolate(drc_ctx *c, const drc_caches *caches, const drc_gbuffer *gbuf,
+                           const drc_interp_params *prm, float *out_rgb, void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!caches || !gbuf || !prm) return fail(c, DRC_ERR_INVALID_ARG, "NULL argument struct");
+  if (caches->n < 1) return fail(c, DRC_ERR_INVALID_ARG, "caches->n must be >= 1");
+  if (prm->k < 1 || prm->k > 32) return fail(c, DRC_ERR_INVALID_ARG, "k must be 1..32");
+  if (prm->metric != DRC_METRIC_IMAGE && prm->metric != DRC_METRIC_WORLD)
+    return fail(c, DRC_ERR_INVALID_ARG, "unknown metric");
+  if (prm->wp_form != DRC_WP_INVERSE && prm->wp_form != DRC_WP_LINEAR)
+    return fail(c, DRC_ERR_INVALID_ARG, "unknown wp_form");
+  if (prm->mode != DRC_INTERP_IRRADIANCE && prm->mode != DRC_INTERP_LOOKUP)
+    return fail(c, DRC_ERR_INVALID_ARG, "unknown mode");
+  if (!(prm->r > 0.f) || !(prm->eps >= 0.f) || !(prm->delta_rel > 0.f))
+    return fail(c, DRC_ERR_INVALID_ARG, "need r > 0, eps >= 0, delta_rel > 0");
+  if (gbuf->width < 0 || gbuf->height < 0) return fail(c, DRC_ERR_INVALID_ARG, "negative G-buffer size");
+  const long long P = (long long)gbuf->width * gbuf->height;
+  if (P >= (1ll << 31) / 3) return fail(c, DRC_ERR_INVALID_ARG, "G-buffer too large");
+  drc_status s;
+  if (prm->metric == DRC_METRIC_WORLD) {
+    if ((s = check_dev(c, caches->pos, "caches->pos", false)) != DRC_OK) return s;
+  } else {
+    if ((s = check_dev(c, caches->pix, "caches->pix", false)) != DRC_OK) return s;
+  }
+  if ((s = check_dev(c, caches->nrm, "caches->nrm", false)) != DRC_OK) return s;
+  if (prm->mode == DRC_INTERP_IRRADIANCE) {
+    if ((s = check_dev(c, caches->payload, "caches->payload", false)) != DRC_OK) return s;
+  } else {
+    if (caches->H < 1 || caches->W < 1) return fail(c, DRC_ERR_INVALID_ARG, "LOOKUP needs caches->H, W >= 1");
+    if ((s = check_dev(c, caches->maps, "caches->maps", false)) != DRC_OK) return s;
+  }
+  if (P > 0) {
+    if ((s = check_dev(c, out_rgb, "out_rgb", false)) != DRC_OK) return s;
+    if ((s = check_dev(c, gbuf->nrm, "gbuf->nrm", false)) != DRC_OK) return s;
+    if (prm->metric == DRC_METRIC_WORLD && (s = check_dev(c, gbuf->pos, "gbuf->pos", false)) != DRC_OK) return s;
+    if (prm->mode == DRC_INTERP_LOOKUP && (s = check_dev(c, gbuf->dir, "gbuf->dir", false)) != DRC_OK) return s;
+    if ((s = check_dev(c, prm->nbr_out, "nbr_out", true)) != DRC_OK) return s;
+  }
+  const size_t need = interp_scratch_bytes(caches->n, prm->k);
+  if (need > c->iscratch_bytes) {
+    if (c->d_iscratch) cudaFree(c->d_iscratch);
+    c->d_iscratch = nullptr;
+    c->iscratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->d_iscratch, need);
+    if (e != cudaSuccess) return cuda_fail(c, e, "interpolation scratch");
+    c->iscratch_bytes = need;
+  }
+  InterpArgs a;
+  memset(&a, 0, sizeof a);
+  a.n = caches->n;
+  a.mapH = caches->H;
+  a.mapW = caches->W;
+  a.maps = caches->maps;
+  a.payload = caches->payload;
+  a.cpos = caches->pos;
+  a.cnrm = caches->nrm;
+  a.cpix = caches->pix;
+  a.width = gbuf->width;
+  a.height = gbuf->height;
+  a.gpos = gbuf->pos;
+  a.gnrm = gbuf->nrm;
+  a.gdir = gbuf->dir;
+  a.k = prm->k;
+  a.metric = prm->metric;
+  a.wp_form = prm->wp_form;
+  a.mode = prm->mode;
+  a.r = prm->r;
+  a.eps = prm->eps;
+  a.delta_rel = prm->delta_rel;
+  a.out = out_rgb;
+  a.nbr_out = prm->nbr_out;
+  InterpScratch sc = interp_carve(c->d_iscratch, caches->n, prm->k);
+  cudaError_t e = launch_interp(a, sc, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "interpolation launch");
+  return DRC_OK;
+}
+
+drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N, int H, int W, unsigned flags,
+                        float *dweights, float *dinput, float *loss, void *stream) {
+  (void)in;
+  (void)target;
+  (void)N;
+  (void)H;
+  (void)W;
+  (void)flags;
+  (void)dweights;
+  (void)dinput;
+  (void)loss;
+  (void)stream;
+  if (!c) return DRC_ERR_INVALID_ARG;
+  return fail(c, DRC_ERR_UNSUPPORTED, "backward is not built yet");
+}
+
+drc_status drc_get_status(drc_ctx *c, void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  int v = 0;
+  e = cudaMemcpy(&v, c->d_status, sizeof v, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status read");
+  if (v != 0) {
+    cudaMemset(c->d_status, 0, sizeof(int));
+    return fail(c, (drc_status)v, "device-side error %d latched (a bounded wait ran out)", v);
+  }
+  return DRC_OK;
+}
+
+const char *drc_last_error(drc_ctx *c) { return c ? c->err.c_str() : "NULL context"; }
+
+}  // extern "C"

@@ -1,0 +1,139 @@
+"""Parity of drc_denoise (tensor-core implicit-GEMM autoencoder, Sec. 3.3)
+with the FP64 oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1910_02480_gb300 import synth
+from parity import FP32_TOL, median_rel, rel_err
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def drc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1910_02480_gb300 import build
+    build.build()
+    import paper_1910_02480_gb300 as m
+    return m
+
+
+def _maps(N, H, W, seed=3, linear=False):
+    g = synth.gbuffer(max(N, 1), 1, seed=seed + 10)
+    maps, _ = synth.hemisphere_maps(g["pos"][:N], g["nrm"][:N], H=H, W=W, seed=seed)
+    if linear:
+        maps = maps.copy()
+        maps[:, :3] = np.expm1(np.clip(maps[:, :3], 0.0, None))
+    return np.ascontiguousarray(maps, dtype=np.float32)
+
+
+CASES = [
+    # widths, N, H, W, bias, flags, out_relu
+    ([16], 2, 8, 8, False, 0, False),
+    ([16], 3, 8, 12, True, 0, True),
+    ([16, 32], 3, 16, 16, True, 1, False),
+    ([32, 64, 128], 64, 32, 32, False, 0, False),
+    ([32, 64, 128], 5, 32, 32, True, 3, True),
+    ([16, 32, 48, 64], 3, 32, 48, True, 0, False),
+    ([64, 128, 256], 9, 32, 32, True, 0, False),
+    ([64, 128, 256, 512], 2, 64, 64, True, 0, False),
+]
+
+
+@pytest.mark.parametrize("widths,N,H,W,bias,flags,out_relu", CASES)
+def test_fp32_matches_oracle(drc, widths, N, H, W, bias, flags, out_relu):
+    w = synth.he_weights(widths, seed=0, bias=bias)
+    x = _maps(N, H, W, linear=bool(flags & 1))
+    s = 0.75 if flags else 1.0
+    ctx = drc.Context(widths, w, precision="fp32", exposure=s, out_relu=out_relu)
+    xd = torch.from_numpy(x).cuda()
+    out, pay = ctx.denoise(xd, flags=flags, want_payload=True)
+    torch.cuda.synchronize()
+    assert ctx.status() == drc.OK
+    ref = oracle.forward(w, x, widths, out_relu=out_relu, exposure=s, flags=flags)
+    g = out.cpu().numpy()
+    err = rel_err(g, ref)
+    print("fp32 widths=%s N=%d %dx%d: max rel %.3e, median %.3e" % (widths, N, H, W, err, median_rel(g, ref)))
+    assert err <= FP32_TOL
+    ref_log = ref if not (flags & 2) else np.log1p(s * ref)
+    ref_pay = oracle.payload(np.expm1(ref_log) / s)
+    perr = rel_err(pay.cpu().numpy(), ref_pay)
+    assert perr <= FP32_TOL, perr
+
+
+def test_fp32_full_size_sampled(drc):
+    """4096 maps of 7x32x32, widths 64/128/256: the whole batch on the GPU in
+    one call, eight maps spread over it recomputed by the oracle."""
+    widths, N = [64, 128, 256], 4096
+    w = synth.he_weights(widths, seed=0)
+    g = synth.gbuffer(64, 64, seed=2)
+    c = synth.cache_grid(g, 64, 64)
+    x, _ = synth.hemisphere_maps(c["pos"], c["nrm"])
+    ctx = drc.Context(widths, w, precision="fp32")
+    xd = torch.from_numpy(x).cuda()
+    out, pay = ctx.denoise(xd, want_payload=True)
+    torch.cuda.synchronize()
+    assert ctx.status() == drc.OK
+    idx = np.array([0, 1, 777, 1500, 2048, 3001, 4094, 4095])
+    ref = oracle.forward(w, x[idx], widths)
+    err = rel_err(out.cpu().numpy()[idx], ref)
+    print("fp32 full size sampled: max rel %.3e" % err)
+    assert err <= FP32_TOL
+    assert rel_err(pay.cpu().numpy()[idx], oracle.payload(np.expm1(ref))) <= FP32_TOL
+    assert np.all(np.isfinite(out.cpu().numpy()))
+
+
+@pytest.mark.parametrize("widths,N,H,W", [([32, 64, 128], 64, 32, 32), ([16, 32], 3, 16, 16)])
+def test_bf16_error_reported(drc, widths, N, H, W):
+    w = synth.he_weights(widths, seed=0)
+    x = _maps(N, H, W)
+    ctx = drc.Context(widths, w, precision="bf16")
+    out = ctx.denoise(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    assert ctx.status() == drc.OK
+    ref = oracle.forward(w, x, widths)
+    err = rel_err(out.cpu().numpy(), ref)
+    print("bf16 widths=%s: max rel %.3e median %.3e" % (widths, err, median_rel(out.cpu().numpy(), ref)))
+    assert err < 0.1
+
+
+def test_zero_maps_is_a_no_op(drc):
+    ctx = drc.Context([16], synth.he_weights([16]), precision="fp32")
+    x = torch.empty((0, 7, 8, 8), device="cuda")
+    out = ctx.denoise(x)
+    assert out.shape == (0, 3, 8, 8)
+    assert ctx.status() == drc.OK
+
+
+def test_argument_errors_are_reported(drc):
+    ctx = drc.Context([16, 32], synth.he_weights([16, 32]), precision="fp32")
+    x = torch.zeros((2, 7, 16, 16), device="cuda")
+    with pytest.raises(drc.DrcError) as e:
+        ctx.denoise(torch.zeros((2, 7, 18, 16), device="cuda"))  # H not a multiple of 4
+    assert e.value.code == drc.ERR_INVALID_ARG
+    with pytest.raises(drc.DrcError) as e:
+        ctx.denoise(x, out=torch.zeros((2, 3, 16, 16)))  # host output
+    assert e.value.code == drc.ERR_INVALID_ARG
+    with pytest.raises(drc.DrcError) as e:
+        ctx.denoise(x, flags=0x80)
+    assert e.value.code == drc.ERR_INVALID_ARG
+    with pytest.raises(drc.DrcError):
+        drc.Context([16, 32], np.zeros(10, np.float32))
+
+
+def test_stalled_wait_times_out_and_context_recovers(drc):
+    """A wait that nothing completes (test flag) gives up after the context's
+    timeout and latches DRC_ERR_TIMEOUT; the next call runs normally."""
+    widths = [16, 32]
+    w = synth.he_weights(widths, seed=0)
+    ctx = drc.Context(widths, w, precision="fp32", wait_timeout_ms=50)
+    x = _maps(3, 16, 16)
+    xd = torch.from_numpy(x).cuda()
+    ctx.denoise(xd, flags=drc.F_DEBUG_STALL)
+    assert ctx.status() == drc.ERR_TIMEOUT
+    out = ctx.denoise(xd)
+    assert ctx.status() == drc.OK
+    assert rel_err(out.cpu().numpy(), oracle.forward(w, x, widths)) <= FP32_TOL
