@@ -191,6 +191,19 @@ __device__ __forceinline__ void store_nchw7(uint8_t *a0, uint8_t *a1, uint32_t o
   }
 }
 
+// Accumulator columns [c, c+16) of a tile: the main accumulator, plus the
+// correction accumulator BN columns further on for the split-tf32 path.
+template <int PREC>
+__device__ __forceinline__ void tmem_ld_acc(uint32_t taddr, int BN, float (&v)[16]) {
+  tmem_ld16(taddr, v);
+  if constexpr (PREC == PREC_TF32X3) {
+    float c[16];
+    tmem_ld16(taddr + (uint32_t)BN, c);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) v[e] += c[e];
+  }
+}
+
 // ------------------------------------------------------------- the kernel
 template <int PREC>
 __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_constant__ ConvArgs a) {
@@ -218,7 +231,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const uint32_t ncols = BN * 2 <= 32 ? 32u : (BN * 2 <= 64 ? 64u : (BN * 2 <= 128 ? 128u : (BN * 2 <= 256 ? 256u : 512u)));
+  // Accumulator layout per tile buffer: BN columns, or for the split-tf32
+  // path [hi*hi | hi*lo + lo*hi] (2 BN columns).  Keeping the two small
+  // correction products out of the main accumulator matters: the tensor core
+  // rounds the accumulator on every MMA, so three MMAs into one accumulator
+  // triple its rounding error.  Two buffers when they fit in 512 columns.
+  const int acc_cols = T::SPLIT * BN;
+  const int nbufs = 2 * acc_cols <= 512 ? 2 : 1;
+  const int need = nbufs * acc_cols;
+  const uint32_t ncols = need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : (need <= 256 ? 256u : 512u)));
 
   if (warp == MMA_WARP) {
     tmem_alloc(smem_u32(tmem_slot), ncols);
@@ -255,13 +276,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x, ++it) {
         const TileCoord tc = tile_coord(a, t);
         const int nkb = a.ph[tc.phase].num_kb;
-        const int buf = it & 1;
-        if (!mbar_wait(smem_u32(&tempty_bar[buf]), ((it >> 1) & 1) ^ 1, tmo, a.status, ERR_TIMEOUT)) {
+        const int buf = nbufs == 2 ? (it & 1) : 0;
+        const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
+        if (!mbar_wait(smem_u32(&tempty_bar[buf]), par ^ 1, tmo, a.status, ERR_TIMEOUT)) {
           ok = false;
           break;
         }
         tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * BN);
+        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * acc_cols);
+        const uint32_t c_tmem = d_tmem + (uint32_t)BN;  // correction accumulator (split-tf32)
         for (int kb = 0; kb < nkb; ++kb) {
           if (!mbar_wait(smem_u32(&full_bar[stage]), phase, tmo, a.status, ERR_TIMEOUT)) {
             ok = false;
@@ -279,8 +302,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
             const uint64_t bd = make_sdesc_sw128(sb0 + k * 32);
             tc_mma<T::KIND>(d_tmem, ad, bd, idesc, acc);
             if constexpr (PREC == PREC_TF32X3) {
-              tc_mma<T::KIND>(d_tmem, ad, make_sdesc_sw128(sb1 + k * 32), idesc, 1u);
-              tc_mma<T::KIND>(d_tmem, make_sdesc_sw128(sa1 + k * 32), bd, idesc, 1u);
+              tc_mma<T::KIND>(c_tmem, ad, make_sdesc_sw128(sb1 + k * 32), idesc, acc);
+              tc_mma<T::KIND>(c_tmem, make_sdesc_sw128(sa1 + k * 32), bd, idesc, 1u);
             }
           }
           tc_commit(smem_u32(&empty_bar[stage]));
@@ -443,18 +466,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++it) {
       const TileCoord tc = tile_coord(a, t);
       const PhaseDesc &pd = a.ph[tc.phase];
-      const int buf = it & 1;
-      if (!mbar_wait(smem_u32(&tfull_bar[buf]), (it >> 1) & 1, tmo, a.status, ERR_TIMEOUT)) break;
+      const int buf = nbufs == 2 ? (it & 1) : 0;
+      const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
+      if (!mbar_wait(smem_u32(&tfull_bar[buf]), par, tmo, a.status, ERR_TIMEOUT)) break;
       tc_fence_after();
       const int m = tc.m_tile * BM + row;
       const bool vrow = m < a.M;
       const int n = vrow ? m / rows_per_map : 0;
       const int rem = vrow ? m - n * rows_per_map : 0;
       const int i = rem / a.Wrow, j = rem - (rem / a.Wrow) * a.Wrow;
-      const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * BN);
+      const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
       if (a.kind == LK_HEAD) {
         float v[16];
-        tmem_ld16(taddr, v);
+        tmem_ld_acc<PREC>(taddr, BN, v);
         float pay[3] = {0.f, 0.f, 0.f};
         float *out = reinterpret_cast<float *>(a.y);
 #pragma unroll
@@ -506,7 +530,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
         const act_t *skip = reinterpret_cast<const act_t *>(a.skip);
         for (int cc = 0; cc < BN / 16; ++cc) {
           float v[16];
-          tmem_ld16(taddr + cc * 16, v);
+          tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
           const int col0 = tc.n_tile * BN + cc * 16;
           if (!vrow) continue;
           const float *bsc = a.bscale ? a.bscale + col0 : nullptr;

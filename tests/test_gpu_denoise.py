@@ -95,9 +95,17 @@ def test_bf16_error_reported(drc, widths, N, H, W):
     torch.cuda.synchronize()
     assert ctx.status() == drc.OK
     ref = oracle.forward(w, x, widths)
-    err = rel_err(out.cpu().numpy(), ref)
-    print("bf16 widths=%s: max rel %.3e median %.3e" % (widths, err, median_rel(out.cpu().numpy(), ref)))
-    assert err < 0.1
+    g = out.cpu().numpy()
+    err = rel_err(g, ref)
+    rms = np.sqrt(np.mean(ref ** 2))
+    normwise = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    print("bf16 widths=%s: max rel %.3e median %.3e, max|err|/rms %.3e, normwise %.3e"
+          % (widths, err, median_rel(g, ref), np.max(np.abs(g - ref)) / rms, normwise))
+    # bf16 keeps 8 significant bits (unit roundoff 2^-9 ~ 2e-3) in every stored
+    # activation and operand; five layers of it give a normwise error of a few
+    # 1e-3 and a largest deviation of a few percent of the output rms
+    assert normwise < 1e-2
+    assert np.max(np.abs(g - ref)) / rms < 0.1
 
 
 def test_zero_maps_is_a_no_op(drc):
@@ -120,7 +128,7 @@ def test_argument_errors_are_reported(drc):
     with pytest.raises(drc.DrcError) as e:
         ctx.denoise(x, flags=0x80)
     assert e.value.code == drc.ERR_INVALID_ARG
-    with pytest.raises(drc.DrcError):
+    with pytest.raises(ValueError):
         drc.Context([16, 32], np.zeros(10, np.float32))
 
 
