@@ -167,6 +167,28 @@ drc_status drc_interpolate(drc_ctx *ctx, const drc_caches *caches,
                            const drc_interp_params *params, float *out_rgb,
                            void *stream);
 
+/* drc_interpolate without a context and without allocating.  The paper has
+ * no counterpart: this serves callers that cannot call cudaMalloc -- a host
+ * application that owns the device-memory budget and gives plugins none of
+ * their own, or a frame loop in which cudaMalloc's implicit device
+ * synchronisation is not allowed.
+ *   Same arguments and result as drc_interpolate.  The cache grid lives in a
+ *   3 MiB static device array of the library (held on every GPU that loads
+ *   the library until the process exits); n may be at most 65536 caches (any
+ *   k); larger n returns DRC_ERR_INVALID_ARG before anything is enqueued.
+ *   Argument errors return DRC_ERR_INVALID_ARG, a failed CUDA call
+ *   DRC_ERR_CUDA.  Allocates no device memory (no cudaMalloc, cudaFree or
+ *   allocating library routine).
+ *   The first call on a device looks up the array's device address with that
+ *   device current; make that first call before any stream capture.
+ *   Every call shares the one array: calls that overlap on the GPU (different
+ *   streams, different host threads) race and their results are undefined;
+ *   calls ordered on one stream are safe, since each call rewrites all the
+ *   scratch it reads. */
+drc_status drc_interpolate_static(const drc_caches *caches, const drc_gbuffer *gbuf,
+                                  const drc_interp_params *params, float *out_rgb,
+                                  void *stream);
+
 /* drc_backward flags */
 #define DRC_BWD_L1_TARGET 0x1u /* target = ground truth [N][3][H][W] (log
                                   radiance); loss = mean |out - target| */

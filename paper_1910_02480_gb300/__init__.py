@@ -88,6 +88,9 @@ def load_library():
     lib.drc_interpolate.argtypes = [P, ctypes.POINTER(Caches), ctypes.POINTER(GBuffer),
                                     ctypes.POINTER(InterpParams), P, P]
     lib.drc_interpolate.restype = I
+    lib.drc_interpolate_static.argtypes = [ctypes.POINTER(Caches), ctypes.POINTER(GBuffer),
+                                           ctypes.POINTER(InterpParams), P, P]
+    lib.drc_interpolate_static.restype = I
     lib.drc_backward.argtypes = [P, P, P, I, I, I, U, P, P, P, P]
     lib.drc_backward.restype = I
     lib.drc_get_status.argtypes = [P, P]
