@@ -37,6 +37,16 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense ratio (tf32 : bf16)
 
 
+def set_workload(maps, frame):
+    """Smaller workloads for profiling runs; the defaults are the benchmark's."""
+    global N_MAPS, IMG_W, IMG_H, GRID
+    N_MAPS = int(maps)
+    IMG_W, IMG_H = (int(v) for v in frame.lower().split("x"))
+    GRID = int(round(N_MAPS ** 0.5))
+    if GRID * GRID != N_MAPS:
+        raise SystemExit("--maps must be a square number (a square cache grid)")
+
+
 def valid_macs_per_map(widths, H, W, cin=7, cout=3):
     """Multiply-accumulates per map counting in-bounds taps only."""
     def conv_taps(n_in):  # per output index: taps u with 0 <= 2i+u-1 < n_in
@@ -193,7 +203,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--maps", type=int, default=N_MAPS, help="maps per step (profiling of smaller cases)")
+    ap.add_argument("--frame", default="%dx%d" % (IMG_W, IMG_H), help="G-buffer WxH (profiling)")
     args = ap.parse_args()
+    set_workload(args.maps, args.frame)
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -320,8 +333,8 @@ def main():
     line = {"metric": METRIC_NAME, "value": value, "unit": "maps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16", "data": "synthetic",
-            "config": {"workload": "4096 maps 7x32x32, encoder 64/128/256 (FP32 production size) + "
-                                   "1920x1080 interpolation, k=16, WORLD metric, IRRADIANCE",
+            "config": {"workload": "%d maps 7x32x32, encoder 64/128/256 (FP32 production size) + "
+                                   "%dx%d interpolation, k=16, WORLD metric, IRRADIANCE" % (N_MAPS, IMG_W, IMG_H),
                        "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
             "denoise_ms": den * 1e3, "interp_ms": float(np.mean(itp_ms)),

@@ -9,13 +9,14 @@
 //   rows of B  = output channels; pre-packed weight tiles in the exact
 //                shared-memory image (128-byte swizzle), fetched by one thread
 //                with cp.async.bulk;
-//   D          = fp32 accumulator in tensor memory, double buffered so the
-//                epilogue of tile i overlaps the MMAs of tile i+1.
+//   D          = fp32 accumulator in tensor memory, double buffered (when it
+//                fits) so the epilogue of tile i overlaps the MMAs of tile i+1.
 // Warp roles (16 warps): 0 = MMA issuer + TMEM owner, 1 = B loader,
 // 4..7 = epilogue (TMEM lane quarters 0..3), 8..15 = A producers.
 // FP32 parity uses the split-tf32 product: x = hi + lo with hi, lo tf32, and
-// D += A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped lo*lo term is below
-// 2^-21 relative).  BF16 / FP8 use one product per K step.
+// D += A_hi B_hi, C += A_hi B_lo + A_lo B_hi in two accumulators, summed in
+// the epilogue (the dropped lo*lo term is below 2^-21 relative).  BF16 / FP8
+// use one product per K step.
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
@@ -30,10 +31,10 @@ template <int PREC>
 struct PrecTraits;
 template <>
 struct PrecTraits<PREC_TF32X3> {
-  static constexpr int ELEM = 4;          // bytes per stored operand element
+  static constexpr int ELEM = 4;  // bytes per stored operand element
   static constexpr int KIND = KIND_TF32;
-  static constexpr int SPLIT = 2;         // hi + lo copies of each operand tile
-  using act_t = float;                    // activation storage
+  static constexpr int SPLIT = 2;  // hi + lo copies of each operand tile
+  using act_t = float;             // activation storage
 };
 template <>
 struct PrecTraits<PREC_BF16> {
@@ -53,17 +54,61 @@ struct PrecTraits<PREC_FP8> {
 constexpr int SMEM_BUDGET = 227 * 1024;
 constexpr int SMEM_CTRL = 1024;  // barriers + TMEM slot, padded to the 1024-byte swizzle atom
 
-__host__ __device__ inline int stage_bytes(int prec, int BN) {
-  int split = prec == PREC_TF32X3 ? 2 : 1;
+__host__ __device__ inline int stage_bytes(int prec, int BN, int mode) {
+  const int split = prec == PREC_TF32X3 ? 2 : 1;
+  if (mode == PROD_TMA_TMEM) return split * BN * KROW_BYTES;  // A lives in tensor memory
   return split * (BM * KROW_BYTES + BN * KROW_BYTES);
 }
 
-__host__ __device__ int conv_stages(int prec, int BN) {
-  int s = (SMEM_BUDGET - SMEM_CTRL - 1024) / stage_bytes(prec, BN);
-  return s > 8 ? 8 : s;
+// PROD_TMA_TMEM tensor-memory map: accumulators in columns [0, 256), A
+// stages of 64 columns (tf32 hi 32 | lo 32) from column 256.
+constexpr int TS_STAGES = 4;
+constexpr int TS_A_COL0 = 256;
+
+// Raw bytes of one operand row per K block, in the stored activation type
+// (fp32 for the split-tf32 path, bf16 otherwise; an fp8 K block of 128
+// elements comes from 256 bytes of bf16).
+__host__ __device__ inline int raw_row_bytes(int prec) { return prec == PREC_FP8 ? 256 : 128; }
+
+// Shared memory: MMA stages (A and B tiles) plus, except when the TMA writes
+// the A tile itself, a ring of R raw slots; R = 3 keeps two K blocks of
+// copies in flight beyond the one being converted, shrunk to 2 when 2 MMA
+// stages would not fit otherwise.
+__host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode) {
+  const int avail = SMEM_BUDGET - SMEM_CTRL - 1024;
+  const int sb = stage_bytes(prec, BN, mode);
+  const int rb = BM * raw_row_bytes(prec);
+  if (mode == PROD_TMA_TMEM) {
+    // B stages match the tensor-memory A stages; the rest of shared memory
+    // holds raw TMA boxes in flight (up to 6)
+    SmemPlan p;
+    p.stages = TS_STAGES;
+    int R = (avail - TS_STAGES * sb) / rb;
+    p.raw_depth = R > 6 ? 6 : R;
+    p.raw_slot_bytes = rb;
+    return p;
+  }
+  if (mode == PROD_TMA_DIRECT) {
+    SmemPlan p;
+    p.stages = avail / sb > 8 ? 8 : avail / sb;
+    p.raw_depth = 0;
+    p.raw_slot_bytes = rb;
+    return p;
+  }
+  int R = 3;
+  while (R > 2 && avail - R * rb < 2 * sb) --R;
+  int st = (avail - R * rb) / sb;
+  if (st > 8) st = 8;
+  SmemPlan p;
+  p.stages = st;
+  p.raw_depth = R;
+  p.raw_slot_bytes = rb;
+  return p;
 }
-size_t conv_smem_bytes(int prec, int BN) {
-  return (size_t)SMEM_CTRL + 1024 + (size_t)conv_stages(prec, BN) * stage_bytes(prec, BN);
+size_t conv_smem_bytes(int prec, int BN, int mode) {
+  const SmemPlan p = smem_plan(prec, BN, mode);
+  return (size_t)SMEM_CTRL + 1024 + (size_t)p.stages * stage_bytes(prec, BN, mode) +
+         (size_t)p.raw_depth * p.raw_slot_bytes;
 }
 
 // Offset of 16-byte chunk q of row r inside a 128-byte-swizzled K-major tile.
@@ -75,9 +120,9 @@ struct TileCoord {
   int phase, m_tile, n_tile;
 };
 __device__ __forceinline__ TileCoord tile_coord(const ConvArgs &a, int t) {
-  int per_phase = a.m_tiles * a.n_tiles;
-  int p = t / per_phase;
-  int rem = t - p * per_phase;
+  const int per_phase = a.m_tiles * a.n_tiles;
+  const int p = t / per_phase;
+  const int rem = t - p * per_phase;
   TileCoord c;
   c.phase = a.phase_order[p];
   c.m_tile = rem / a.n_tiles;
@@ -85,109 +130,472 @@ __device__ __forceinline__ TileCoord tile_coord(const ConvArgs &a, int t) {
   return c;
 }
 
-// ----------------------------------------------------------------- loads
-template <int PREC>
-struct Chunk;  // one 16-byte slice of an operand row, as loaded
-template <>
-struct Chunk<PREC_TF32X3> {
-  float4 v;
-};
-template <>
-struct Chunk<PREC_BF16> {
-  uint4 v;
-};
-template <>
-struct Chunk<PREC_FP8> {
-  uint4 v[2];  // 16 bf16 values, quantised to 16 e4m3 on store
-};
-
-__device__ __forceinline__ uint4 ldg16(const void *p) {
-  return __ldg(reinterpret_cast<const uint4 *>(p));
-}
-
-template <int PREC>
-__device__ __forceinline__ void load_chunk_nhwc(Chunk<PREC> &c, const uint8_t *src, bool ok) {
-  if constexpr (PREC == PREC_TF32X3) {
-    c.v = ok ? __ldg(reinterpret_cast<const float4 *>(src)) : make_float4(0.f, 0.f, 0.f, 0.f);
-  } else if constexpr (PREC == PREC_BF16) {
-    c.v = ok ? ldg16(src) : make_uint4(0, 0, 0, 0);
-  } else {
-    c.v[0] = ok ? ldg16(src) : make_uint4(0, 0, 0, 0);
-    c.v[1] = ok ? ldg16(src + 16) : make_uint4(0, 0, 0, 0);
-  }
+// --------------------------------------------------------- conversions
+// fp32 -> tf32, round to nearest with ties away from zero, done on the bits:
+// add half an ulp of the 10-bit mantissa and clear the 13 dropped bits
+// (finite inputs).  Integer add/and run at full rate, unlike the conversion
+// instruction.
+__device__ __forceinline__ float tf32_rna(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t *>(&h);
 }
-
 __device__ __forceinline__ uint32_t pack_e4m3x4(float a, float b, float c, float d) {
   __nv_fp8x2_storage_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
   __nv_fp8x2_storage_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
   return (uint32_t)lo | ((uint32_t)hi << 16);
 }
-
 __device__ __forceinline__ float bf16_lo(uint32_t w) { return __uint_as_float(w << 16); }
 __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
 
-// Store one chunk into the stage's A tile(s).
+// 16-byte shared-memory store / load as single vector instructions.
+__device__ __forceinline__ void sts128(uint8_t *p, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(p)), "r"(x), "r"(y), "r"(z), "r"(w)
+               : "memory");
+}
+__device__ __forceinline__ uint4 lds128(const void *p) {
+  uint4 v;
+  asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "r"(smem_u32(p))
+               : "memory");
+  return v;
+}
+
+// One 16-byte A chunk from its raw bytes (uint4 = 16 B; FP8 reads two).
 template <int PREC>
-__device__ __forceinline__ void store_chunk(uint8_t *a0, uint8_t *a1, uint32_t off, const Chunk<PREC> &c,
-                                            float qscale) {
+__device__ __forceinline__ void convert_store(uint8_t *a0, uint8_t *a1, uint32_t off, const uint4 *raw, int stride,
+                                              float qscale) {
   if constexpr (PREC == PREC_TF32X3) {
-    float4 h, l;
-    h.x = to_tf32(c.v.x);
-    h.y = to_tf32(c.v.y);
-    h.z = to_tf32(c.v.z);
-    h.w = to_tf32(c.v.w);
-    l.x = to_tf32(c.v.x - h.x);
-    l.y = to_tf32(c.v.y - h.y);
-    l.z = to_tf32(c.v.z - h.z);
-    l.w = to_tf32(c.v.w - h.w);
-    *reinterpret_cast<float4 *>(a0 + off) = h;
-    *reinterpret_cast<float4 *>(a1 + off) = l;
+    const uint4 u = lds128(raw);
+    const float x[4] = {__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z), __uint_as_float(u.w)};
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float hf = tf32_rna(x[e]);
+      h[e] = __float_as_uint(hf);
+      l[e] = __float_as_uint(tf32_rna(x[e] - hf));
+    }
+    sts128(a0 + off, h[0], h[1], h[2], h[3]);
+    sts128(a1 + off, l[0], l[1], l[2], l[3]);
   } else if constexpr (PREC == PREC_BF16) {
-    *reinterpret_cast<uint4 *>(a0 + off) = c.v;
+    const uint4 u = lds128(raw);
+    sts128(a0 + off, u.x, u.y, u.z, u.w);
   } else {
+    const uint4 x = lds128(raw), y = lds128(raw + stride);
     uint4 q;
-    const uint4 &x = c.v[0];
-    const uint4 &y = c.v[1];
-    q.x = pack_e4m3x4(bf16_lo(x.x) * qscale, bf16_hi(x.x) * qscale, bf16_lo(x.y) * qscale,
-                      bf16_hi(x.y) * qscale);
-    q.y = pack_e4m3x4(bf16_lo(x.z) * qscale, bf16_hi(x.z) * qscale, bf16_lo(x.w) * qscale,
-                      bf16_hi(x.w) * qscale);
-    q.z = pack_e4m3x4(bf16_lo(y.x) * qscale, bf16_hi(y.x) * qscale, bf16_lo(y.y) * qscale,
-                      bf16_hi(y.y) * qscale);
-    q.w = pack_e4m3x4(bf16_lo(y.z) * qscale, bf16_hi(y.z) * qscale, bf16_lo(y.w) * qscale,
-                      bf16_hi(y.w) * qscale);
-    *reinterpret_cast<uint4 *>(a0 + off) = q;
+    q.x = pack_e4m3x4(bf16_lo(x.x) * qscale, bf16_hi(x.x) * qscale, bf16_lo(x.y) * qscale, bf16_hi(x.y) * qscale);
+    q.y = pack_e4m3x4(bf16_lo(x.z) * qscale, bf16_hi(x.z) * qscale, bf16_lo(x.w) * qscale, bf16_hi(x.w) * qscale);
+    q.z = pack_e4m3x4(bf16_lo(y.x) * qscale, bf16_hi(y.x) * qscale, bf16_lo(y.y) * qscale, bf16_hi(y.y) * qscale);
+    q.w = pack_e4m3x4(bf16_lo(y.z) * qscale, bf16_hi(y.z) * qscale, bf16_lo(y.w) * qscale, bf16_hi(y.w) * qscale);
+    sts128(a0 + off, q.x, q.y, q.z, q.w);
   }
 }
 
-// Elements of the first layer's K (k = c*9 + tap, c < 7) gathered from the
-// fp32 NCHW input, with the optional log encode of channels 0..2.
+// mbar_wait that also adds the cycles it waited to `acc` when profiling.
+__device__ __forceinline__ bool pwait(const ConvArgs &a, unsigned long long &acc, uint32_t bar, uint32_t parity) {
+  if (!a.prof) return mbar_wait(bar, parity, a.timeout_ns, a.status, ERR_TIMEOUT);
+  const long long t0 = clock64();
+  const bool ok = mbar_wait(bar, parity, a.timeout_ns, a.status, ERR_TIMEOUT);
+  acc += (unsigned long long)(clock64() - t0);
+  return ok;
+}
+
+// ------------------------------------------------------------ A producer
+// The implicit-im2col rows of A reach the 128-byte-swizzled A tile of an MMA
+// stage in one of three ways (ProdMode), chosen per layer on the host:
+//
+// PROD_TMA_DIRECT / PROD_TMA_CONVERT: one TMA load per K block fetches the
+//   whole 128-row tile for one tap and 128 bytes of channels: the tile covers
+//   whole output rows of whole maps, so its rows are a box of the NHWC
+//   activation tensor -- for the stride-2 convolution a box with traversal
+//   stride 2 in H and W starting at (2 i0 + u - 1, v - 1), for a decoder
+//   phase a box starting at (a0 + di, dj).  Positions outside the map are
+//   zero-filled by the TMA unit (the convolution's padding).  The TMA writes
+//   the 128-byte swizzle itself.  DIRECT (bf16): into the A tile.  CONVERT:
+//   into a raw slot, from which the eight producer warps write the tf32 hi/lo
+//   (or e4m3) tiles at the same swizzled offsets.
+// PROD_CPASYNC (any shape): each producer thread gathers 16-byte chunks of
+//   4 rows with cp.async into its own part of a raw slot, R-1 K blocks ahead,
+//   then converts them (8 lanes per 128-byte row).
+struct RowInfo {
+  int pix_base[4], ybase[4], xbase[4];
+  bool vrow[4];
+  int nkb, ntaps;
+  unsigned long long taps;  // tap t: dy in bits 4t..4t+1, dx in bits 4t+2..4t+3 (offsets 0..2)
+};
+
+__device__ __forceinline__ unsigned long long pack_taps(const PhaseDesc &pd) {
+  unsigned long long tp = 0;
+#pragma unroll
+  for (int q = 0; q < 9; ++q)
+    if (q < pd.ntaps) tp |= (unsigned long long)((pd.dy[q] & 3) | ((pd.dx[q] & 3) << 2)) << (4 * q);
+  return tp;
+}
+
+__device__ __forceinline__ void prod_setup(const ConvArgs &a, int t, int pt, RowInfo &ri) {
+  const TileCoord tc = tile_coord(a, t);
+  // the phase's tap table, read once per tile into registers
+  const PhaseDesc &pd = a.ph[tc.phase];
+  ri.nkb = pd.num_kb;
+  ri.ntaps = pd.ntaps;
+  ri.taps = pack_taps(pd);
+  const int rows_per_map = a.Hrow * a.Wrow;
+  const int hw_in = a.Hin * a.Win;
+  const int lane = pt & 31, pw = pt >> 5;
+  const bool s2 = a.kind == LK_CONV;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int r = (lane >> 3) + 4 * pw + 32 * it;
+    const int m = tc.m_tile * BM + r;
+    const bool v = m < a.M;
+    const int n = v ? m / rows_per_map : 0;
+    const int rem = v ? m - n * rows_per_map : 0;
+    const int i = rem / a.Wrow, j = rem - (rem / a.Wrow) * a.Wrow;
+    ri.vrow[it] = v;
+    ri.pix_base[it] = n * hw_in;
+    ri.ybase[it] = s2 ? 2 * i - 1 : i;
+    ri.xbase[it] = s2 ? 2 * j - 1 : j;
+  }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// PROD_CPASYNC step 1: this thread's copies of one K block (4 rows x 16
+// bytes, fp8: x 32) into raw slot `slot`; layout [piece][thread] of 16 bytes.
 template <int PREC>
-__device__ __forceinline__ void store_nchw7(uint8_t *a0, uint8_t *a1, uint32_t off, const float *vals,
-                                            float qscale) {
-  if constexpr (PREC == PREC_TF32X3) {
-    Chunk<PREC_TF32X3> c;
-    c.v = make_float4(vals[0], vals[1], vals[2], vals[3]);
-    store_chunk<PREC_TF32X3>(a0, a1, off, c, qscale);
-  } else if constexpr (PREC == PREC_BF16) {
-    uint4 q;
-    q.x = pack_bf16x2(vals[0], vals[1]);
-    q.y = pack_bf16x2(vals[2], vals[3]);
-    q.z = pack_bf16x2(vals[4], vals[5]);
-    q.w = pack_bf16x2(vals[6], vals[7]);
-    *reinterpret_cast<uint4 *>(a0 + off) = q;
+__device__ __forceinline__ void raw_issue(const ConvArgs &a, const RowInfo &ri, int kb, int pt, uint32_t slot) {
+  using T = PrecTraits<PREC>;
+  constexpr int E = 16 / T::ELEM;
+  constexpr int BKE = KROW_BYTES / T::ELEM;
+  constexpr int PIECES = PREC == PREC_FP8 ? 2 : 1;  // 16-byte raw pieces per A chunk
+  constexpr int AB = sizeof(typename T::act_t);
+  const int k0 = kb * BKE + (pt & 7) * E;
+  int tap, c;
+  if (a.cin_shift >= 0) {
+    tap = k0 >> a.cin_shift;
+    c = k0 & (a.Cin - 1);
   } else {
-    uint4 q;
-    q.x = pack_e4m3x4(vals[0] * qscale, vals[1] * qscale, vals[2] * qscale, vals[3] * qscale);
-    q.y = pack_e4m3x4(vals[4] * qscale, vals[5] * qscale, vals[6] * qscale, vals[7] * qscale);
-    q.z = pack_e4m3x4(vals[8] * qscale, vals[9] * qscale, vals[10] * qscale, vals[11] * qscale);
-    q.w = pack_e4m3x4(vals[12] * qscale, vals[13] * qscale, vals[14] * qscale, vals[15] * qscale);
-    *reinterpret_cast<uint4 *>(a0 + off) = q;
+    tap = k0 / a.Cin;
+    c = k0 - tap * a.Cin;
+  }
+  const bool vtap = tap < ri.ntaps;
+  const unsigned tb = vtap ? (unsigned)(ri.taps >> (4 * tap)) & 15u : 0u;
+  const int dy = (int)(tb & 3u), dx = (int)(tb >> 2);
+  const uint8_t *xin = reinterpret_cast<const uint8_t *>(a.x);
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int yy = ri.ybase[it] + dy, xx = ri.xbase[it] + dx;
+    const bool okp = ri.vrow[it] && vtap && (unsigned)yy < (unsigned)a.Hin && (unsigned)xx < (unsigned)a.Win;
+    const uint8_t *src = okp ? xin + ((size_t)(ri.pix_base[it] + yy * a.Win + xx) * a.Cin + c) * AB : xin;
+#pragma unroll
+    for (int h = 0; h < PIECES; ++h)
+      cp_async16(slot + (uint32_t)((it * PIECES + h) * NUM_PROD_THREADS + pt) * 16u, src + 16 * h, okp ? 16u : 0u);
+  }
+}
+
+// PROD_CPASYNC step 2: convert this thread's raw chunks into the A tile(s).
+template <int PREC>
+__device__ __forceinline__ void raw_convert_own(const ConvArgs &a, int pt, const uint8_t *slot, uint8_t *a0,
+                                                uint8_t *a1) {
+  constexpr int PIECES = PREC == PREC_FP8 ? 2 : 1;
+  const int lane = pt & 31, pw = pt >> 5;
+  const uint4 *raw = reinterpret_cast<const uint4 *>(slot);
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int r = (lane >> 3) + 4 * pw + 32 * it;
+    convert_store<PREC>(a0, a1, swz(r, lane & 7), raw + (it * PIECES) * NUM_PROD_THREADS + pt, NUM_PROD_THREADS,
+                        a.act_scale_in);
+  }
+}
+
+// PROD_TMA_CONVERT step 2: convert chunks of a TMA-filled raw slot (same
+// swizzled layout as the A tile; fp8: two swizzled 128-byte halves).
+template <int PREC>
+__device__ __forceinline__ void raw_convert_tma(const ConvArgs &a, int pt, const uint8_t *slot, uint8_t *a0,
+                                                uint8_t *a1) {
+  const int lane = pt & 31, pw = pt >> 5, q = lane & 7;
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int r = (lane >> 3) + 4 * pw + 32 * it;
+    if constexpr (PREC == PREC_FP8) {
+      // bf16 source: chunk q (16 e4m3) = raw chunks 2q, 2q+1 of the 256-byte row,
+      // stored as two 128-byte half tiles
+      const int h = q >> 2;  // which half holds chunks 2q, 2q+1
+      const uint8_t *half = slot + h * BM * KROW_BYTES;
+      const uint4 *p0 = reinterpret_cast<const uint4 *>(half + swz(r, (2 * q) & 7));
+      const uint4 *p1 = reinterpret_cast<const uint4 *>(half + swz(r, (2 * q + 1) & 7));
+      const uint4 x = lds128(p0), y = lds128(p1);
+      const float s = a.act_scale_in;
+      sts128(a0 + swz(r, q), pack_e4m3x4(bf16_lo(x.x) * s, bf16_hi(x.x) * s, bf16_lo(x.y) * s, bf16_hi(x.y) * s),
+             pack_e4m3x4(bf16_lo(x.z) * s, bf16_hi(x.z) * s, bf16_lo(x.w) * s, bf16_hi(x.w) * s),
+             pack_e4m3x4(bf16_lo(y.x) * s, bf16_hi(y.x) * s, bf16_lo(y.y) * s, bf16_hi(y.y) * s),
+             pack_e4m3x4(bf16_lo(y.z) * s, bf16_hi(y.z) * s, bf16_lo(y.w) * s, bf16_hi(y.w) * s));
+    } else {
+      convert_store<PREC>(a0, a1, swz(r, q), reinterpret_cast<const uint4 *>(slot + swz(r, q)), 0, a.act_scale_in);
+    }
+  }
+}
+
+// PROD_TMA_TMEM step 2: the warp's lane quarter (rows 32 q .. 32 q + 31,
+// q = warp % 4) and half of the K block (chunks 4 h .. 4 h + 3, h = 0 for
+// warps 8..11) go from the raw slot, split into tf32 hi/lo, into the A
+// stage's tensor-memory columns [16 h, 16 h + 16) (hi) and 32 + same (lo).
+__device__ __forceinline__ void raw_convert_tmem(int pt, const uint8_t *slot, uint32_t ta) {
+  const int w = pt >> 5, lane = pt & 31;
+  const int q = w & 3, h = w >> 2;
+  const int r = 32 * q + lane;
+  uint32_t hi[16], lo[16];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const uint4 u = lds128(slot + swz(r, 4 * h + c));
+    const float x[4] = {__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z), __uint_as_float(u.w)};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float hf = tf32_rna(x[e]);
+      hi[4 * c + e] = __float_as_uint(hf);
+      lo[4 * c + e] = __float_as_uint(tf32_rna(x[e] - hf));
+    }
+  }
+  const uint32_t t0 = ta + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h);
+  tmem_st16(t0, hi);
+  tmem_st16(t0 + 32, lo);
+  tmem_wait_st();
+}
+
+// 4-D tiled TMA load of one box into shared memory, completing on `bar`.
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+
+// Box coordinates (channel, x, y, map) of the A rows of tile t, K block kb.
+struct TmaCursor {
+  int t, kb, nkb, ntaps, n0, r0;  // r0: first output row (conv) / input row (phase) of the tile
+  unsigned long long taps;
+};
+__device__ __forceinline__ void tma_tile(const ConvArgs &a, TmaCursor &c) {
+  const TileCoord tc = tile_coord(a, c.t);
+  const PhaseDesc &pd = a.ph[tc.phase];
+  c.nkb = pd.num_kb;
+  c.ntaps = pd.ntaps;
+  c.taps = pack_taps(pd);
+  const int rows_per_map = a.Hrow * a.Wrow;
+  const int m0 = tc.m_tile * BM;
+  c.n0 = m0 / rows_per_map;
+  c.r0 = (m0 - c.n0 * rows_per_map) / a.Wrow;
+}
+template <int PREC>
+__device__ __forceinline__ void tma_issue(const ConvArgs &a, const TmaCursor &c, uint32_t dst, uint32_t bar) {
+  using T = PrecTraits<PREC>;
+  constexpr int BKE = KROW_BYTES / T::ELEM;
+  const int kpt = a.Cin / BKE;  // K blocks per tap
+  const int tap = c.kb / kpt;
+  const int c0 = (c.kb - tap * kpt) * BKE;
+  const unsigned tb = (unsigned)(c.taps >> (4 * tap)) & 15u;
+  const int dy = (int)(tb & 3u), dx = (int)(tb >> 2);
+  int x, y;
+  if (a.kind == LK_CONV) {  // stride-2 box: rows 2 i + dy - 1, cols 2 j + dx - 1
+    x = dx - 1;
+    y = 2 * c.r0 + dy - 1;
+  } else {  // decoder phase: rows a + di, cols b + dj
+    x = dx;
+    y = c.r0 + dy;
+  }
+  if constexpr (PREC == PREC_FP8) {
+    // 128 e4m3 = 256 bytes of bf16 per row: two boxes of 64 channels
+    tma_load_4d(dst, &a.tmap, c0, x, y, c.n0, bar);
+    tma_load_4d(dst + BM * KROW_BYTES, &a.tmap, c0 + 64, x, y, c.n0, bar);
+  } else {
+    tma_load_4d(dst, &a.tmap, c0, x, y, c.n0, bar);
+  }
+}
+
+// Producer warps.  `raw` is the raw ring (unused in PROD_TMA_DIRECT).
+template <int PREC>
+__device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint8_t *raw, uint64_t *full_bar,
+                                          uint64_t *empty_bar, uint64_t *raw_full, uint64_t *raw_empty, int stages,
+                                          int sbytes, int R, int slot_bytes, int total_tiles, uint32_t tmem_base) {
+  const int pt = threadIdx.x - PROD_WARP0 * 32;  // 0..255
+  const int lane = pt & 31;
+  const int a_bytes = BM * KROW_BYTES;
+  const uint32_t raw_u32 = smem_u32(raw);
+  const uint32_t data_u32 = smem_u32(data);
+  if ((int)blockIdx.x >= total_tiles) return;
+  int total_kb = 0;
+  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) total_kb += a.ph[tile_coord(a, t).phase].num_kb;
+  unsigned long long w_empty = 0, w_copy = 0, w_conv = 0, w_fence = 0, w_issue = 0;
+  const long long t_start = a.prof ? clock64() : 0;
+  const int slot_box = PREC == PREC_FP8 ? 2 * BM * KROW_BYTES : BM * KROW_BYTES;  // TMA bytes per K block
+
+  if (a.prod_mode == PROD_TMA_DIRECT) {
+    // one thread: wait for the stage, expect the box bytes, load into the A tile
+    if (pt == 0) {
+      TmaCursor c;
+      c.t = blockIdx.x;
+      c.kb = 0;
+      tma_tile(a, c);
+      int stage = 0;
+      uint32_t phase = 0;
+      for (int j = 0; j < total_kb; ++j) {
+        if (!pwait(a, w_empty, smem_u32(&empty_bar[stage]), phase ^ 1)) break;
+        const uint32_t fb = smem_u32(&full_bar[stage]);
+        mbar_arrive_expect_tx(fb, (uint32_t)a_bytes);
+        tma_issue<PREC>(a, c, data_u32 + stage * sbytes, fb);
+        if (++stage == stages) {
+          stage = 0;
+          phase ^= 1;
+        }
+        if (++c.kb == c.nkb) {
+          c.kb = 0;
+          c.t += gridDim.x;
+          if (c.t < total_tiles) tma_tile(a, c);
+        }
+      }
+    }
+  } else if (a.prod_mode == PROD_TMA_CONVERT || a.prod_mode == PROD_TMA_TMEM) {
+    // thread 0 keeps the raw ring R-1 boxes ahead; all 256 threads convert
+    TmaCursor c;
+    int ji = 0;
+    if (pt == 0) {
+      c.t = blockIdx.x;
+      c.kb = 0;
+      tma_tile(a, c);
+    }
+    bool ok = true;
+    auto issue = [&]() {
+      const int slot = ji % R;
+      if (!pwait(a, w_issue, smem_u32(&raw_empty[slot]), (uint32_t)(((ji / R) & 1) ^ 1))) {
+        ok = false;
+        return;
+      }
+      const uint32_t fb = smem_u32(&raw_full[slot]);
+      mbar_arrive_expect_tx(fb, (uint32_t)slot_box);
+      tma_issue<PREC>(a, c, raw_u32 + (uint32_t)(slot * slot_bytes), fb);
+      ++ji;
+      if (++c.kb == c.nkb) {
+        c.kb = 0;
+        c.t += gridDim.x;
+        if (c.t < total_tiles) tma_tile(a, c);
+      }
+    };
+    if (pt == 0)
+      for (int j = 0; j < R - 1 && j < total_kb && ok; ++j) issue();
+    int stage = 0;
+    uint32_t phase = 0;
+    for (int jc = 0; jc < total_kb && ok; ++jc) {
+      if (pt == 0 && jc + R - 1 < total_kb) {
+        issue();
+        if (!ok) break;
+      }
+      const int slot = jc % R;
+      if (!pwait(a, w_copy, smem_u32(&raw_full[slot]), (uint32_t)((jc / R) & 1))) break;
+      if (!pwait(a, w_empty, smem_u32(&empty_bar[stage]), phase ^ 1)) break;
+      uint8_t *a0 = data + stage * sbytes;
+      const long long tv0 = a.prof ? clock64() : 0;
+      if constexpr (PREC == PREC_TF32X3) {
+        if (a.prod_mode == PROD_TMA_TMEM)
+          raw_convert_tmem(pt, raw + slot * slot_bytes, tmem_base + (uint32_t)(TS_A_COL0 + stage * 64));
+        else
+          raw_convert_tma<PREC>(a, pt, raw + slot * slot_bytes, a0, a0 + a_bytes);
+      } else {
+        raw_convert_tma<PREC>(a, pt, raw + slot * slot_bytes, a0, a0 + a_bytes);
+      }
+      const long long tv1 = a.prof ? clock64() : 0;
+      fence_proxy_async_smem();  // A tile writes -> MMA; raw reads before the slot's next TMA write
+      tc_fence_before();         // tensor-memory A stores -> MMA (PROD_TMA_TMEM)
+      __syncwarp();
+      if (a.prof) {
+        w_conv += (unsigned long long)(tv1 - tv0);
+        w_fence += (unsigned long long)(clock64() - tv1);
+      }
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&full_bar[stage]));
+        mbar_arrive(smem_u32(&raw_empty[slot]));
+      }
+      if (++stage == stages) {
+        stage = 0;
+        phase ^= 1;
+      }
+    }
+  } else {
+    // PROD_CPASYNC
+    const int D = R - 1;
+    int it_t = blockIdx.x, it_kb = 0;
+    bool it_more = true;
+    RowInfo ri;
+    prod_setup(a, it_t, pt, ri);
+    int islot = 0;
+    auto issue = [&]() {
+      const long long ti0 = a.prof ? clock64() : 0;
+      if (it_more) {
+        raw_issue<PREC>(a, ri, it_kb, pt, raw_u32 + (uint32_t)(islot * slot_bytes));
+        if (++it_kb == ri.nkb) {
+          it_kb = 0;
+          it_t += gridDim.x;
+          if (it_t < total_tiles)
+            prod_setup(a, it_t, pt, ri);
+          else
+            it_more = false;
+        }
+      }
+      cp_async_commit();  // one group per K block (empty past the end)
+      if (++islot == R) islot = 0;
+      if (a.prof) w_issue += (unsigned long long)(clock64() - ti0);
+    };
+    for (int j = 0; j < D; ++j) issue();
+    int cslot = 0, stage = 0;
+    uint32_t phase = 0;
+    for (int jc = 0; jc < total_kb; ++jc) {
+      issue();
+      const long long tc0 = a.prof ? clock64() : 0;
+      if (D >= 2)
+        cp_async_wait<2>();
+      else
+        cp_async_wait<1>();
+      if (a.prof) w_copy += (unsigned long long)(clock64() - tc0);
+      if (!pwait(a, w_empty, smem_u32(&empty_bar[stage]), phase ^ 1)) break;
+      uint8_t *a0 = data + stage * sbytes;
+      const long long tv0 = a.prof ? clock64() : 0;
+      raw_convert_own<PREC>(a, pt, raw + cslot * slot_bytes, a0, a0 + a_bytes);
+      const long long tv1 = a.prof ? clock64() : 0;
+      fence_proxy_async_smem();
+      __syncwarp();
+      if (a.prof) {
+        w_conv += (unsigned long long)(tv1 - tv0);
+        w_fence += (unsigned long long)(clock64() - tv1);
+      }
+      if (lane == 0) mbar_arrive(smem_u32(&full_bar[stage]));
+      if (++stage == stages) {
+        stage = 0;
+        phase ^= 1;
+      }
+      if (++cslot == R) cslot = 0;
+    }
+    cp_async_wait_all();
+  }
+  if (a.prof && lane == 0) {
+    atomicAdd(&a.prof[PROF_PROD_WAIT_EMPTY], w_empty);
+    atomicAdd(&a.prof[PROF_PROD_WAIT_COPY], w_copy);
+    atomicAdd(&a.prof[PROF_PROD_TOTAL], (unsigned long long)(clock64() - t_start));
+    atomicAdd(&a.prof[PROF_PROD_CONVERT], w_conv);
+    atomicAdd(&a.prof[PROF_PROD_FENCE], w_fence);
+    atomicAdd(&a.prof[PROF_PROD_ISSUE], w_issue);
   }
 }
 
@@ -208,23 +616,26 @@ __device__ __forceinline__ void tmem_ld_acc(uint32_t taddr, int BN, float (&v)[1
 template <int PREC>
 __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_constant__ ConvArgs a) {
   using T = PrecTraits<PREC>;
-  constexpr int E = 16 / T::ELEM;            // elements per 16-byte chunk
-  constexpr int BKE = KROW_BYTES / T::ELEM;  // K elements per stage
   const int BN = a.BN;
-  const int stages = conv_stages(PREC, BN);
+  const SmemPlan plan = smem_plan(PREC, BN, a.prod_mode);
+  const int stages = plan.stages;
   const int a_bytes = BM * KROW_BYTES;
   const int b_bytes = BN * KROW_BYTES;
-  const int sbytes = stage_bytes(PREC, BN);
+  const int sbytes = stage_bytes(PREC, BN, a.prod_mode);
+  const bool ts = PREC == PREC_TF32X3 && a.prod_mode == PROD_TMA_TMEM;
 
   extern __shared__ uint8_t smem_raw[];
-  // control block at the start, stage buffers from the next 1024-byte boundary
+  // control block at the start, stage buffers from the next 1024-byte
+  // boundary, raw ring after the stages
   uint8_t *ctrl = smem_raw;
-  uint64_t *full_bar = reinterpret_cast<uint64_t *>(ctrl);        // [8]
-  uint64_t *empty_bar = full_bar + 8;                              // [8]
-  uint64_t *tfull_bar = empty_bar + 8;                             // [2]
-  uint64_t *tempty_bar = tfull_bar + 2;                            // [2]
-  uint64_t *stall_bar = tempty_bar + 2;                            // [1]
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(stall_bar + 1);
+  uint64_t *full_bar = reinterpret_cast<uint64_t *>(ctrl);  // [8]
+  uint64_t *empty_bar = full_bar + 8;                        // [8]
+  uint64_t *tfull_bar = empty_bar + 8;                       // [2]
+  uint64_t *tempty_bar = tfull_bar + 2;                      // [2]
+  uint64_t *stall_bar = tempty_bar + 2;                      // [1]
+  uint64_t *raw_full = stall_bar + 1;                        // [6]
+  uint64_t *raw_empty = raw_full + 6;                        // [6]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(raw_empty + 6);
   const uint32_t base_u32 = smem_u32(smem_raw);
   const uint32_t data_u32 = (base_u32 + SMEM_CTRL + 1023u) & ~1023u;
   uint8_t *data = smem_raw + (data_u32 - base_u32);
@@ -236,18 +647,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
   // correction products out of the main accumulator matters: the tensor core
   // rounds the accumulator on every MMA, so three MMAs into one accumulator
   // triple its rounding error.  Two buffers when they fit in 512 columns.
+  // With A in tensor memory (PROD_TMA_TMEM) the accumulators share the 512
+  // columns with the A stages.
   const int acc_cols = T::SPLIT * BN;
-  const int nbufs = 2 * acc_cols <= 512 ? 2 : 1;
-  const int need = nbufs * acc_cols;
-  const uint32_t ncols = need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : (need <= 256 ? 256u : 512u)));
+  const int nbufs = ts ? (2 * acc_cols <= TS_A_COL0 ? 2 : 1) : (2 * acc_cols <= 512 ? 2 : 1);
+  const int need = ts ? 512 : nbufs * acc_cols;
+  const uint32_t ncols =
+      need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : (need <= 256 ? 256u : 512u)));
 
   if (warp == MMA_WARP) {
     tmem_alloc(smem_u32(tmem_slot), ncols);
     tmem_relinquish();
   }
   if (threadIdx.x == 32) {
+    // full: the B loader's arrive + one per producer warp, or the A-TMA
+    // thread's arrive in PROD_TMA_DIRECT
+    const uint32_t full_count = a.prod_mode == PROD_TMA_DIRECT ? 2u : (uint32_t)(NUM_PROD_THREADS / 32 + 1);
     for (int s = 0; s < stages; ++s) {
-      mbar_init(smem_u32(&full_bar[s]), NUM_PROD_THREADS / 32 + 1);
+      mbar_init(smem_u32(&full_bar[s]), full_count);
       mbar_init(smem_u32(&empty_bar[s]), 1);
     }
     for (int b = 0; b < 2; ++b) {
@@ -255,6 +672,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       mbar_init(smem_u32(&tempty_bar[b]), 4);
     }
     mbar_init(smem_u32(stall_bar), 1);
+    for (int r = 0; r < plan.raw_depth; ++r) {
+      mbar_init(smem_u32(&raw_full[r]), 1);                        // the TMA thread's arrive
+      mbar_init(smem_u32(&raw_empty[r]), NUM_PROD_THREADS / 32);  // one arrive per producer warp
+    }
     fence_mbar_init();
   }
   tc_fence_before();
@@ -273,12 +694,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       int stage = 0;
       uint32_t phase = 0;
       int it = 0;
+      unsigned long long w_full = 0, w_tempty = 0;
+      const long long t_start = a.prof ? clock64() : 0;
       for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x, ++it) {
         const TileCoord tc = tile_coord(a, t);
         const int nkb = a.ph[tc.phase].num_kb;
         const int buf = nbufs == 2 ? (it & 1) : 0;
         const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
-        if (!mbar_wait(smem_u32(&tempty_bar[buf]), par ^ 1, tmo, a.status, ERR_TIMEOUT)) {
+        if (!pwait(a, w_tempty, smem_u32(&tempty_bar[buf]), par ^ 1)) {
           ok = false;
           break;
         }
@@ -286,15 +709,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
         const uint32_t d_tmem = tmem_base + (uint32_t)(buf * acc_cols);
         const uint32_t c_tmem = d_tmem + (uint32_t)BN;  // correction accumulator (split-tf32)
         for (int kb = 0; kb < nkb; ++kb) {
-          if (!mbar_wait(smem_u32(&full_bar[stage]), phase, tmo, a.status, ERR_TIMEOUT)) {
+          if (!pwait(a, w_full, smem_u32(&full_bar[stage]), phase)) {
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t sa0 = data_u32 + stage * sbytes;
-          const uint32_t sa1 = sa0 + a_bytes;                 // A lo (TF32X3)
-          const uint32_t sb0 = sa0 + T::SPLIT * a_bytes;      // B (hi)
-          const uint32_t sb1 = sb0 + b_bytes;                 // B lo (TF32X3)
+          const uint32_t sa1 = sa0 + a_bytes;                        // A lo (TF32X3)
+          const uint32_t sb0 = ts ? sa0 : sa0 + T::SPLIT * a_bytes;  // B (hi)
+          const uint32_t sb1 = sb0 + b_bytes;                        // B lo (TF32X3)
+          if (ts) {
+            // A hi/lo from tensor memory: 8 tf32 columns per K step
+            const uint32_t ta = tmem_base + (uint32_t)(TS_A_COL0 + stage * 64);
+#pragma unroll
+            for (int k = 0; k < KROW_BYTES / 32; ++k) {
+              const uint32_t acc = (kb | k) != 0;
+              const uint64_t bd = make_sdesc_sw128(sb0 + k * 32);
+              tc_mma_ts_tf32(d_tmem, ta + 8 * k, bd, idesc, acc);
+              tc_mma_ts_tf32(c_tmem, ta + 8 * k, make_sdesc_sw128(sb1 + k * 32), idesc, acc);
+              tc_mma_ts_tf32(c_tmem, ta + 32 + 8 * k, bd, idesc, 1u);
+            }
+          } else
 #pragma unroll
           for (int k = 0; k < KROW_BYTES / 32; ++k) {
             const uint32_t acc = (kb | k) != 0;
@@ -315,25 +750,32 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
         if (!ok) break;
         tc_commit(smem_u32(&tfull_bar[buf]));
       }
+      if (a.prof) {
+        atomicAdd(&a.prof[PROF_MMA_WAIT_FULL], w_full);
+        atomicAdd(&a.prof[PROF_MMA_WAIT_TEMPTY], w_tempty);
+        atomicAdd(&a.prof[PROF_MMA_TOTAL], (unsigned long long)(clock64() - t_start));
+        atomicAdd(&a.prof[PROF_CTAS], 1ull);
+      }
     }
   } else if (warp == BLOAD_WARP) {
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
+      unsigned long long w_empty = 0;
       for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
         const TileCoord tc = tile_coord(a, t);
         const PhaseDesc &pd = a.ph[tc.phase];
         const int nkb = pd.num_kb;
         for (int kb = 0; kb < nkb; ++kb) {
-          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, tmo, a.status, ERR_TIMEOUT)) {
+          if (!pwait(a, w_empty, smem_u32(&empty_bar[stage]), phase ^ 1)) {
             ok = false;
             break;
           }
           const uint32_t fb = smem_u32(&full_bar[stage]);
           mbar_arrive_expect_tx(fb, (uint32_t)(T::SPLIT * b_bytes));
           const size_t off = (size_t)pd.b_off + ((size_t)tc.n_tile * nkb + kb) * (size_t)b_bytes;
-          const uint32_t sb0 = data_u32 + stage * sbytes + T::SPLIT * a_bytes;
+          const uint32_t sb0 = data_u32 + stage * sbytes + (ts ? 0 : T::SPLIT * a_bytes);
           bulk_g2s(sb0, a.B + off, (uint32_t)b_bytes, fb);
           if constexpr (PREC == PREC_TF32X3) bulk_g2s(sb0 + b_bytes, a.B_lo + off, (uint32_t)b_bytes, fb);
           if (++stage == stages) {
@@ -342,133 +784,28 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
           }
         }
       }
+      if (a.prof) atomicAdd(&a.prof[PROF_BLOAD_WAIT_EMPTY], w_empty);
     }
   } else if (warp >= PROD_WARP0) {
-    // ------------------------------------------------------ A producers
-    const int pt = threadIdx.x - PROD_WARP0 * 32;  // 0..255
-    const int pw = pt >> 5;
-    int stage = 0;
-    uint32_t phase = 0;
-    bool ok = true;
-    const int rows_per_map = a.Hrow * a.Wrow;
-    const int hw_in = a.Hin * a.Win;
-    const float qscale = a.act_scale_in;
-    for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
-      const TileCoord tc = tile_coord(a, t);
-      const PhaseDesc &pd = a.ph[tc.phase];
-      const int nkb = pd.num_kb;
-      if (a.kind == LK_CONV_NCHW7) {
-        // one row per thread, half of the 16-byte chunks of that row
-        const int r = pt & (BM - 1);
-        const int qbase = (pt >> 7) * (KROW_BYTES / 16 / 2);
-        const int m = tc.m_tile * BM + r;
-        const bool vrow = m < a.M;
-        const int n = vrow ? m / rows_per_map : 0;
-        const int rem = m - n * rows_per_map;
-        const int i = rem / a.Wrow, j = rem - (rem / a.Wrow) * a.Wrow;
-        const int y0 = 2 * i - 1, x0 = 2 * j - 1;
-        const float *xin = reinterpret_cast<const float *>(a.x) + (size_t)n * 7 * hw_in;
-        for (int kb = 0; kb < nkb; ++kb) {
-          float vals[KROW_BYTES / 16 / 2][E];
-#pragma unroll
-          for (int qq = 0; qq < KROW_BYTES / 16 / 2; ++qq) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-              const int k = kb * BKE + (qbase + qq) * E + e;
-              const int c = k / 9, tap = k - (k / 9) * 9;
-              const int yy = y0 + tap / 3, xx = x0 + (tap - (tap / 3) * 3);
-              float v = 0.f;
-              if (vrow && k < 63 && yy >= 0 && yy < a.Hin && xx >= 0 && xx < a.Win) {
-                v = __ldg(xin + (size_t)c * hw_in + yy * a.Win + xx);
-                if (a.encode && c < 3) v = log1pf(a.exposure * v);
-              }
-              vals[qq][e] = v;
-            }
-          }
-          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, tmo, a.status, ERR_TIMEOUT)) {
-            ok = false;
-            break;
-          }
-          uint8_t *a0 = data + stage * sbytes;
-          uint8_t *a1 = a0 + a_bytes;
-#pragma unroll
-          for (int qq = 0; qq < KROW_BYTES / 16 / 2; ++qq)
-            store_nchw7<PREC>(a0, a1, swz(r, qbase + qq), vals[qq], qscale);
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(&full_bar[stage]));
-          if (++stage == stages) {
-            stage = 0;
-            phase ^= 1;
-          }
-        }
-      } else {
-        // NHWC gather: 8 lanes cover one 128-byte operand row, 4 rows per warp,
-        // 4 passes of 32 rows
-        const int q = lane & 7;
-        int pix_base[4], ybase[4], xbase[4];
-        bool vrow[4];
-#pragma unroll
-        for (int it = 0; it < 4; ++it) {
-          const int r = (lane >> 3) + 4 * pw + 32 * it;
-          const int m = tc.m_tile * BM + r;
-          vrow[it] = m < a.M;
-          const int n = vrow[it] ? m / rows_per_map : 0;
-          const int rem = vrow[it] ? m - n * rows_per_map : 0;
-          const int i = rem / a.Wrow, j = rem - (rem / a.Wrow) * a.Wrow;
-          pix_base[it] = n * hw_in;
-          ybase[it] = a.kind == LK_CONV ? 2 * i - 1 : i;
-          xbase[it] = a.kind == LK_CONV ? 2 * j - 1 : j;
-        }
-        const uint8_t *xin = reinterpret_cast<const uint8_t *>(a.x);
-        const int ntaps = pd.ntaps;
-        for (int kb = 0; kb < nkb; ++kb) {
-          const int k0 = kb * BKE + q * E;
-          const int tap = k0 / a.Cin;
-          const int c = k0 - tap * a.Cin;
-          const bool vtap = tap < ntaps;
-          const int dy = vtap ? pd.dy[tap] : 0, dx = vtap ? pd.dx[tap] : 0;
-          Chunk<PREC> ch[4];
-#pragma unroll
-          for (int it = 0; it < 4; ++it) {
-            const int yy = ybase[it] + dy, xx = xbase[it] + dx;
-            const bool okp = vrow[it] && vtap && yy >= 0 && yy < a.Hin && xx >= 0 && xx < a.Win;
-            const size_t eoff = ((size_t)(pix_base[it] + (okp ? yy * a.Win + xx : 0)) * a.Cin + c);
-            load_chunk_nhwc<PREC>(ch[it], xin + eoff * sizeof(typename T::act_t), okp);
-          }
-          if (!mbar_wait(smem_u32(&empty_bar[stage]), phase ^ 1, tmo, a.status, ERR_TIMEOUT)) {
-            ok = false;
-            break;
-          }
-          uint8_t *a0 = data + stage * sbytes;
-          uint8_t *a1 = a0 + a_bytes;
-#pragma unroll
-          for (int it = 0; it < 4; ++it) {
-            const int r = (lane >> 3) + 4 * pw + 32 * it;
-            store_chunk<PREC>(a0, a1, swz(r, q), ch[it], qscale);
-          }
-          fence_proxy_async_smem();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(smem_u32(&full_bar[stage]));
-          if (++stage == stages) {
-            stage = 0;
-            phase ^= 1;
-          }
-        }
-      }
-    }
+    run_producer<PREC>(a, data, data + stages * sbytes, full_bar, empty_bar, raw_full, raw_empty, stages, sbytes,
+                       plan.raw_depth, plan.raw_slot_bytes, total_tiles, tmem_base);
   } else if (warp >= EPI_WARP0 && warp < EPI_WARP0 + 4) {
     // ------------------------------------------------------------ epilogue
     const int eq = warp - EPI_WARP0;  // TMEM lane quarter
     const int row = eq * 32 + lane;
     const int rows_per_map = a.Hrow * a.Wrow;
     int it = 0;
+    unsigned long long w_tfull = 0;
+    const long long t_start = a.prof ? clock64() : 0;
+    using act_t = typename T::act_t;
+    act_t *yout = reinterpret_cast<act_t *>(a.y);
+    const act_t *skip = reinterpret_cast<const act_t *>(a.skip);
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++it) {
       const TileCoord tc = tile_coord(a, t);
       const PhaseDesc &pd = a.ph[tc.phase];
       const int buf = nbufs == 2 ? (it & 1) : 0;
       const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
-      if (!mbar_wait(smem_u32(&tfull_bar[buf]), par, tmo, a.status, ERR_TIMEOUT)) break;
+      if (!pwait(a, w_tfull, smem_u32(&tfull_bar[buf]), par)) break;
       tc_fence_after();
       const int m = tc.m_tile * BM + row;
       const bool vrow = m < a.M;
@@ -476,120 +813,81 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       const int rem = vrow ? m - n * rows_per_map : 0;
       const int i = rem / a.Wrow, j = rem - (rem / a.Wrow) * a.Wrow;
       const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
-      if (a.kind == LK_HEAD) {
+      const size_t opix = a.kind == LK_CONVT
+                              ? ((size_t)n * a.Hout + (2 * i + pd.oy)) * a.Wout + (2 * j + pd.ox)
+                              : (size_t)m;
+      for (int cc = 0; cc < BN / 16; ++cc) {
         float v[16];
-        tmem_ld_acc<PREC>(taddr, BN, v);
-        float pay[3] = {0.f, 0.f, 0.f};
-        float *out = reinterpret_cast<float *>(a.y);
+        tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
+        const int col0 = tc.n_tile * BN + cc * 16;
+        if (!vrow) continue;
+        const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
+        const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
 #pragma unroll
-        for (int pp = 0; pp < 2; ++pp) {
-          const int orow = 2 * i + pp;
-          const float band = vrow ? a.band[orow] : 0.f;
+        for (int e4 = 0; e4 < 4; ++e4) {
+          const float4 b = __ldg(bias4 + e4);
+          const float bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-          for (int o = 0; o < 3; ++o) {
-            float y0 = v[pp * 6 + o] + a.bias[o];
-            float y1 = v[pp * 6 + 3 + o] + a.bias[o];
-            if (a.relu) {
-              y0 = fmaxf(y0, 0.f);
-              y1 = fmaxf(y1, 0.f);
-            }
-            const float l0 = expm1f(y0) * a.inv_exposure;
-            const float l1 = expm1f(y1) * a.inv_exposure;
-            pay[o] += (l0 + l1) * band;
-            if (vrow) {
-              float2 w = a.decode ? make_float2(l0, l1) : make_float2(y0, y1);
-              *reinterpret_cast<float2 *>(out + (((size_t)n * 3 + o) * a.Hout + orow) * a.Wout + 2 * j) = w;
-            }
-          }
-        }
-        if (a.payload) {
-          const int n0 = __shfl_sync(0xffffffffu, n, 0);
-          const bool uniform = __all_sync(0xffffffffu, vrow && n == n0);
-          if (uniform) {
-#pragma unroll
-            for (int o = 0; o < 3; ++o) {
-              float s = pay[o];
-#pragma unroll
-              for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-              pay[o] = s;
-            }
-            if (lane == 0)
-              for (int o = 0; o < 3; ++o) atomicAdd(a.payload + (size_t)n0 * 3 + o, pay[o]);
-          } else if (vrow) {
-            for (int o = 0; o < 3; ++o) atomicAdd(a.payload + (size_t)n * 3 + o, pay[o]);
-          }
-        }
-      } else {
-        size_t opix;
-        if (a.kind == LK_CONVT)
-          opix = ((size_t)n * a.Hout + (2 * i + pd.oy)) * a.Wout + (2 * j + pd.ox);
-        else
-          opix = (size_t)m;
-        using act_t = typename T::act_t;
-        act_t *yout = reinterpret_cast<act_t *>(a.y);
-        const act_t *skip = reinterpret_cast<const act_t *>(a.skip);
-        for (int cc = 0; cc < BN / 16; ++cc) {
-          float v[16];
-          tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
-          const int col0 = tc.n_tile * BN + cc * 16;
-          if (!vrow) continue;
-          const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            float z = bsc ? v[e] * bsc[e] : v[e];
-            z += a.bias[col0 + e];
+          for (int e = 0; e < 4; ++e) {
+            float z = bsc ? v[4 * e4 + e] * bsc[4 * e4 + e] : v[4 * e4 + e];
+            z += bb[e];
             if (a.relu) z = fmaxf(z, 0.f);
-            v[e] = z;
+            v[4 * e4 + e] = z;
           }
-          const size_t eoff = opix * a.Cout + col0;
-          if constexpr (PREC == PREC_TF32X3) {
-            if (skip) {
-              const float4 *sp = reinterpret_cast<const float4 *>(skip + eoff);
+        }
+        const size_t eoff = opix * a.Cout + col0;
+        if constexpr (PREC == PREC_TF32X3) {
+          if (skip) {
+            const float4 *sp = reinterpret_cast<const float4 *>(skip + eoff);
 #pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                float4 s = sp[e];
-                v[4 * e] += s.x;
-                v[4 * e + 1] += s.y;
-                v[4 * e + 2] += s.z;
-                v[4 * e + 3] += s.w;
-              }
+            for (int e = 0; e < 4; ++e) {
+              const float4 s = sp[e];
+              v[4 * e] += s.x;
+              v[4 * e + 1] += s.y;
+              v[4 * e + 2] += s.z;
+              v[4 * e + 3] += s.w;
             }
-            float4 *yp = reinterpret_cast<float4 *>(yout + eoff);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) yp[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-          } else {
-            if (skip) {
-              const uint4 *sp = reinterpret_cast<const uint4 *>(skip + eoff);
-#pragma unroll
-              for (int e = 0; e < 2; ++e) {
-                uint4 s = sp[e];
-                v[8 * e + 0] += bf16_lo(s.x);
-                v[8 * e + 1] += bf16_hi(s.x);
-                v[8 * e + 2] += bf16_lo(s.y);
-                v[8 * e + 3] += bf16_hi(s.y);
-                v[8 * e + 4] += bf16_lo(s.z);
-                v[8 * e + 5] += bf16_hi(s.z);
-                v[8 * e + 6] += bf16_lo(s.w);
-                v[8 * e + 7] += bf16_hi(s.w);
-              }
-            }
-            uint4 *yp = reinterpret_cast<uint4 *>(yout + eoff);
-#pragma unroll
-            for (int e = 0; e < 2; ++e)
-              yp[e] = make_uint4(pack_bf16x2(v[8 * e], v[8 * e + 1]), pack_bf16x2(v[8 * e + 2], v[8 * e + 3]),
-                                 pack_bf16x2(v[8 * e + 4], v[8 * e + 5]), pack_bf16x2(v[8 * e + 6], v[8 * e + 7]));
           }
+          float4 *yp = reinterpret_cast<float4 *>(yout + eoff);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) yp[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+        } else {
+          if (skip) {
+            const uint4 *sp = reinterpret_cast<const uint4 *>(skip + eoff);
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const uint4 s = sp[e];
+              v[8 * e + 0] += bf16_lo(s.x);
+              v[8 * e + 1] += bf16_hi(s.x);
+              v[8 * e + 2] += bf16_lo(s.y);
+              v[8 * e + 3] += bf16_hi(s.y);
+              v[8 * e + 4] += bf16_lo(s.z);
+              v[8 * e + 5] += bf16_hi(s.z);
+              v[8 * e + 6] += bf16_lo(s.w);
+              v[8 * e + 7] += bf16_hi(s.w);
+            }
+          }
+          uint4 *yp = reinterpret_cast<uint4 *>(yout + eoff);
+#pragma unroll
+          for (int e = 0; e < 2; ++e)
+            yp[e] = make_uint4(pack_bf16x2(v[8 * e], v[8 * e + 1]), pack_bf16x2(v[8 * e + 2], v[8 * e + 3]),
+                               pack_bf16x2(v[8 * e + 4], v[8 * e + 5]), pack_bf16x2(v[8 * e + 6], v[8 * e + 7]));
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[buf]));
     }
+    if (a.prof && lane == 0) {
+      atomicAdd(&a.prof[PROF_EPI_WAIT_TFULL], w_tfull);
+      atomicAdd(&a.prof[PROF_EPI_TOTAL], (unsigned long long)(clock64() - t_start));
+    }
   }
 
   tc_fence_before();
   __syncthreads();
   if (warp == MMA_WARP) {
+    __syncwarp();
     tc_fence_after();
     tmem_dealloc(tmem_base, ncols);
   }
@@ -599,7 +897,7 @@ cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t s
   const int total = a.num_phases * a.m_tiles * a.n_tiles;
   if (total == 0) return cudaSuccess;
   const int grid = total < num_sms ? total : num_sms;
-  const size_t smem = conv_smem_bytes(prec, a.BN);
+  const size_t smem = conv_smem_bytes(prec, a.BN, a.prod_mode);
   cudaError_t e;
   switch (prec) {
     case PREC_TF32X3:
@@ -621,36 +919,57 @@ cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t s
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------ first-layer input
+// One thread per pixel: 7 coalesced plane loads, log encode of channels 0..2,
+// one 32-byte (fp32) or 16-byte (bf16) store of the 8-channel NHWC pixel.
+template <bool BF16>
+__global__ void nchw7_to_nhwc8_kernel(const float *__restrict__ in, void *__restrict__ out, long long hw, int N,
+                                      int encode, float s) {
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= hw * N) return;
+  const long long n = g / hw, p = g - n * hw;
+  const float *src = in + n * 7 * hw + p;
+  float v[8];
+#pragma unroll
+  for (int c = 0; c < 7; ++c) v[c] = __ldg(src + c * hw);
+  v[7] = 0.f;
+  if (encode) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = log1pf(s * v[c]);
+  }
+  if constexpr (BF16) {
+    reinterpret_cast<uint4 *>(out)[g] =
+        make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+  } else {
+    float4 *o = reinterpret_cast<float4 *>(out) + 2 * g;
+    o[0] = make_float4(v[0], v[1], v[2], v[3]);
+    o[1] = make_float4(v[4], v[5], v[6], v[7]);
+  }
+}
+
+cudaError_t launch_nchw7_to_nhwc8(const float *in, void *out, long long hw, int N, bool bf16, bool encode,
+                                  float exposure, cudaStream_t st) {
+  const long long total = hw * N;
+  if (total == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  if (bf16)
+    nchw7_to_nhwc8_kernel<true><<<blocks, 256, 0, st>>>(in, out, hw, N, encode ? 1 : 0, exposure);
+  else
+    nchw7_to_nhwc8_kernel<false><<<blocks, 256, 0, st>>>(in, out, hw, N, encode ? 1 : 0, exposure);
+  return cudaGetLastError();
+}
+
 // --------------------------------------------------------- weight packing
 // One thread per 16-byte chunk of the packed B image: chunk (phase, n_tile,
 // kb, row r, physical chunk p) holds logical chunk q = p ^ (r & 7) of row r,
 // i.e. K elements kb*BKE + q*E .. + E - 1 of output column n_tile*BN + r.
 __device__ float raw_weight(const PackArgs &p, const PhaseDesc &pd, int col, int k) {
-  switch (p.kind) {
-    case LK_CONV_NCHW7:
-      return k < 63 ? p.wraw[(size_t)col * 63 + k] : 0.f;
-    case LK_CONV: {
-      const int tap = k / p.Cin, c = k - (k / p.Cin) * p.Cin;
-      return tap < 9 ? p.wraw[((size_t)col * p.Cin + c) * 9 + tap] : 0.f;
-    }
-    case LK_CONVT: {
-      const int t = k / p.Cin, c = k - (k / p.Cin) * p.Cin;
-      if (t >= pd.ntaps) return 0.f;
-      return p.wraw[(((size_t)c * p.Cout + col) * 3 + pd.u[t]) * 3 + pd.v[t]];
-    }
-    default: {  // LK_HEAD: column = pp*6 + qq*3 + o, K = neighbour*Cin + c
-      if (col >= 12) return 0.f;
-      const int pp = col / 6, qq = (col / 3) & 1, o = col % 3;
-      const int nb = k / p.Cin, c = k - (k / p.Cin) * p.Cin;
-      if (nb >= 4) return 0.f;
-      const int di = nb >> 1, dj = nb & 1;
-      // output row 2a+pp receives input row a+di through kernel row u with
-      // 2(a+di) + u - 1 = 2a + pp, i.e. u = pp + 1 - 2 di (valid 0..2)
-      const int u = pp + 1 - 2 * di, v = qq + 1 - 2 * dj;
-      if (u < 0 || u > 2 || v < 0 || v > 2) return 0.f;
-      return p.wraw[(((size_t)c * 3 + o) * 3 + u) * 3 + v];
-    }
-  }
+  const int t = k / p.Cin, c = k - (k / p.Cin) * p.Cin;
+  if (t >= pd.ntaps || c >= p.Cin_raw) return 0.f;
+  if (p.kind == LK_CONV)  // W[o][c][u][v], tap t = 3u + v
+    return p.wraw[((size_t)col * p.Cin_raw + c) * 9 + t];
+  // LK_CONVT: W[c][o][u][v] with the phase's kernel tap
+  return p.wraw[(((size_t)c * p.Cout + col) * 3 + pd.u[t]) * 3 + pd.v[t]];
 }
 
 template <int PREC>
@@ -682,11 +1001,14 @@ __global__ void pack_kernel(const __grid_constant__ PackArgs p) {
   for (int e = 0; e < E; ++e) w[e] = raw_weight(p, pd, col, kb * BKE + q * E + e);
   const size_t off = (size_t)pd.b_off + (size_t)tile * chunks_per_tile * 16 + (size_t)within * 16;
   if constexpr (PREC == PREC_TF32X3) {
-    float4 h, l;
-    h = make_float4(to_tf32(w[0]), to_tf32(w[1]), to_tf32(w[2]), to_tf32(w[3]));
-    l = make_float4(to_tf32(w[0] - h.x), to_tf32(w[1] - h.y), to_tf32(w[2] - h.z), to_tf32(w[3] - h.w));
-    *reinterpret_cast<float4 *>(p.B + off) = h;
-    *reinterpret_cast<float4 *>(p.B_lo + off) = l;
+    float h[4], l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      h[e] = tf32_rna(w[e]);
+      l[e] = tf32_rna(w[e] - h[e]);
+    }
+    *reinterpret_cast<float4 *>(p.B + off) = make_float4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<float4 *>(p.B_lo + off) = make_float4(l[0], l[1], l[2], l[3]);
   } else if constexpr (PREC == PREC_BF16) {
     uint4 o;
     o.x = pack_bf16x2(w[0], w[1]);
@@ -695,8 +1017,7 @@ __global__ void pack_kernel(const __grid_constant__ PackArgs p) {
     o.w = pack_bf16x2(w[6], w[7]);
     *reinterpret_cast<uint4 *>(p.B + off) = o;
   } else {
-    // per-column scale: the pack of the column's scale happens on the host
-    // side of the planner (bscale), values are divided by it here
+    // values divided by the column's dequantisation scale (bscale)
     const float inv = 1.0f / p.bscale[col];
     uint4 o;
     o.x = pack_e4m3x4(w[0] * inv, w[1] * inv, w[2] * inv, w[3] * inv);

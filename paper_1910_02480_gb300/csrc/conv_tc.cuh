@@ -2,16 +2,16 @@
 // tensor-core implicit-GEMM kernels of the autoencoder (Sec. 3.3).
 #pragma once
 #include <cstdint>
+#include <cuda.h>  // CUtensorMap (type only; encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 namespace drc {
 
 // How a GEMM row maps to pixels and how K maps to (tap, channel).
 enum LayerKind {
-  LK_CONV_NCHW7 = 0,  // first encoder layer: fp32 NCHW 7-channel input, K = c*9 + tap (63 -> pad)
-  LK_CONV = 1,        // encoder conv3x3 s2 p1 on NHWC activations, K = tap*Cin + c
-  LK_CONVT = 2,       // decoder convT3x3 s2, one GEMM per output parity phase
-  LK_HEAD = 3         // output convT (3 channels): all four phases as 12 (->16) columns
+  LK_CONV = 1,   // encoder conv3x3 s2 p1 on NHWC activations, K = tap*Cin + c
+  LK_CONVT = 2,  // decoder convT3x3 s2, one GEMM per output parity phase
+  LK_HEAD = 3    // output convT (3 channels): not a tensor-core GEMM (head.cu)
 };
 
 enum Prec { PREC_TF32X3 = 0, PREC_BF16 = 1, PREC_FP8 = 2 };
@@ -31,44 +31,64 @@ struct PhaseDesc {
   signed char u[9], v[9];    // kernel tap (row, col) of each tap (weight packing)
 };
 
+// How the A operand reaches shared memory.
+enum ProdMode {
+  PROD_CPASYNC = 0,      // per-thread 16-byte cp.async gathers (any shape)
+  PROD_TMA_CONVERT = 1,  // one TMA box per K block into a raw slot, converted by the producer warps
+  PROD_TMA_DIRECT = 2,   // one TMA box per K block straight into the A tile (bf16)
+  PROD_TMA_TMEM = 3      // split-tf32: TMA box into a raw slot, hi/lo written to tensor memory,
+                         // MMAs read A from tensor memory (B only in shared memory)
+};
+
 struct ConvArgs {
+  CUtensorMap tmap;  // A operand view for the TMA modes (64-byte aligned)
+  int prod_mode;
   int kind;
-  const void *x;     // input activations
-  void *y;           // output activations (NHWC) or maps (NCHW, LK_HEAD)
+  const void *x;     // input activations, NHWC
+  void *y;           // output activations, NHWC
   const void *skip;  // NHWC skip tensor shaped like y (LK_CONVT), or nullptr
   const uint8_t *B;  // packed B tiles (tf32 hi part for PREC_TF32X3)
   const uint8_t *B_lo;  // packed B tiles, tf32 lo part (PREC_TF32X3)
-  const float *bias;    // [Cout] (LK_HEAD: [3])
+  const float *bias;    // [Cout]
   const float *bscale;  // FP8: per-output-column dequantisation scale, else nullptr
-  float *payload;       // LK_HEAD: [N][3] accumulated E/pi, or nullptr
   int N, Hin, Win, Cin;  // input activation geometry (Cin = stored channels)
+  int cin_shift;         // log2(Cin) when Cin is a power of two, else -1
   int Hrow, Wrow;        // row grid per map
-  int Hout, Wout, Cout;  // output geometry (Cout = stored channels; LK_HEAD: 3)
+  int Hout, Wout, Cout;  // output geometry (Cout = stored channels)
   int M;                 // N * Hrow * Wrow
   int BN, n_tiles, m_tiles, num_phases;
   int phase_order[4];    // heaviest phase first
   PhaseDesc ph[4];
   int relu;
-  int encode;            // LK_CONV_NCHW7: log1p(s L) on channels 0..2
-  int decode;            // LK_HEAD: write expm1(y)/s
-  float exposure, inv_exposure;
   float act_scale_in;    // FP8: activations stored as value / scale
-  float act_scale_out;
-  float band[256];       // LK_HEAD: payload weight of each output row (1/pi factor folded)
   int *status;
   unsigned long long timeout_ns;
   int debug_stall;
+  unsigned long long *prof;  // optional [PROF_SLOTS] wait-time counters (clock64 cycles), or nullptr
 };
+
+// Diagnostic counters of one conv launch (summed over CTAs; per-warp values
+// are taken from lane 0 of each warp of the role).
+enum ProfSlot {
+  PROF_MMA_WAIT_FULL = 0, PROF_MMA_WAIT_TEMPTY, PROF_MMA_TOTAL, PROF_BLOAD_WAIT_EMPTY,
+  PROF_PROD_WAIT_EMPTY, PROF_PROD_WAIT_COPY, PROF_PROD_TOTAL, PROF_EPI_WAIT_TFULL, PROF_EPI_TOTAL,
+  PROF_CTAS, PROF_PROD_CONVERT, PROF_PROD_FENCE, PROF_PROD_ISSUE, PROF_SLOTS = 16
+};
+
+struct SmemPlan {
+  int stages, raw_depth, raw_slot_bytes;
+};
+__host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode);
+size_t conv_smem_bytes(int prec, int BN, int mode);
 
 // Host-side launch / pack entry points (conv_tc.cu).
 cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t st);
-__host__ __device__ int conv_stages(int prec, int BN);
-size_t conv_smem_bytes(int prec, int BN);
 
 struct PackArgs {
   int kind;
   const float *wraw;  // this layer's raw weights (start of W)
-  int Cin, Cout;      // raw layer channels (LK_HEAD: Cout = 3)
+  int Cin, Cout;      // GEMM channels: Cin as stored in the activations
+  int Cin_raw;        // channels of the raw weights (Cin_raw <= Cin; the rest pack as 0)
   int BN, n_tiles, num_phases;
   PhaseDesc ph[4];
   uint8_t *B, *B_lo;  // packed outputs
@@ -76,5 +96,10 @@ struct PackArgs {
   long long total_chunks;
 };
 cudaError_t launch_pack(const PackArgs &p, int prec, cudaStream_t st);
+
+// First-layer input: fp32 NCHW [N][7][H][W] -> NHWC with 8 channels (the 8th
+// zero), fp32 or bf16, with the optional log1p(s L) of channels 0..2.
+cudaError_t launch_nchw7_to_nhwc8(const float *in, void *out, long long pixels_per_map, int N,
+                                  bool bf16, bool encode, float exposure, cudaStream_t st);
 
 }  // namespace drc

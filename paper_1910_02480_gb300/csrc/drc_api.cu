@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -14,6 +15,7 @@
 
 #include "conv_tc.cuh"
 #include "drc.h"
+#include "head.cuh"
 #include "drc_status.cuh"
 #include "interp.cuh"
 
@@ -25,7 +27,8 @@ namespace {
 
 struct Layer {
   int kind;
-  int Cin, Cout;       // raw channels of the layer (LK_HEAD: Cout = 3)
+  int Cin, Cout;       // GEMM channels (Cin as stored in the input activations; LK_HEAD: Cout = 3)
+  int Cin_raw;         // channels of the raw weights (7 for the first layer, whose input is padded to 8)
   size_t w_off, b_off; // offsets (floats) into the packed raw weights
   int BN, n_tiles, num_phases;
   PhaseDesc ph[4];
@@ -51,6 +54,7 @@ struct drc_ctx {
   void *d_iscratch = nullptr;
   size_t iscratch_bytes = 0;
   int *d_status = nullptr;
+  unsigned long long *d_prof = nullptr;  // wait-time counters (DRC_PROFILE_WAITS)
   bool weights_set = false;
   unsigned long long timeout_ns = 0;
   std::string err;
@@ -75,6 +79,64 @@ drc_status cuda_fail(drc_ctx *c, cudaError_t e, const char *what) {
   cudaGetLastError();
   if (e == cudaErrorMemoryAllocation) return fail(c, DRC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
   return fail(c, DRC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link
+// against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// Choose how layer `a` feeds its A operand.  The TMA modes need the 128
+// rows of every tile to be a box of the activation tensor (whole output rows
+// of whole maps) and a K block to stay inside one tap; everything else uses
+// the cp.async gather.
+void plan_operand(int prec, ConvArgs &a) {
+  a.prod_mode = PROD_CPASYNC;
+  const int bke = KROW_BYTES / (prec == PREC_TF32X3 ? 4 : (prec == PREC_BF16 ? 2 : 1));  // K elements per block
+  const int Wr = a.Wrow, Hr = a.Hrow;
+  if (Wr > BM || BM % Wr || a.Cin % bke) return;
+  const int rows_t = Hr < BM / Wr ? Hr : BM / Wr;
+  if ((rows_t * Wr) % Wr || BM % (rows_t * Wr) || (rows_t < Hr && Hr % rows_t)) return;
+  const int maps_t = BM / (rows_t * Wr);
+  const bool s2 = a.kind == LK_CONV;
+  if (s2 && 2 * Wr > 256) return;
+  if (2 * rows_t > 256 || maps_t > 256) return;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return;
+  const int eb = prec == PREC_TF32X3 ? 4 : 2;  // stored activation bytes
+  const int box_c = KROW_BYTES / eb;          // channels per box row (128 bytes)
+  cuuint64_t dims[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.Win, (cuuint64_t)a.Hin, (cuuint64_t)a.N};
+  cuuint64_t strides[3] = {(cuuint64_t)a.Cin * eb, (cuuint64_t)a.Cin * eb * a.Win,
+                           (cuuint64_t)a.Cin * eb * a.Win * a.Hin};
+  cuuint32_t box[4] = {(cuuint32_t)box_c, (cuuint32_t)(s2 ? 2 * Wr : Wr), (cuuint32_t)(s2 ? 2 * rows_t : rows_t),
+                       (cuuint32_t)maps_t};
+  cuuint32_t estr[4] = {1, (cuuint32_t)(s2 ? 2 : 1), (cuuint32_t)(s2 ? 2 : 1), 1};
+  CUresult r = enc(&a.tmap, prec == PREC_TF32X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                   4, const_cast<void *>(a.x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return;
+  if (prec == PREC_BF16)
+    a.prod_mode = PROD_TMA_DIRECT;
+  else if (prec == PREC_TF32X3 && a.BN <= 128 && std::getenv("DRC_NO_TMEM_A") == nullptr)
+    a.prod_mode = PROD_TMA_TMEM;  // A operand in tensor memory
+  else
+    a.prod_mode = PROD_TMA_CONVERT;
 }
 
 int bke_of(int prec) { return KROW_BYTES / (prec == PREC_TF32X3 ? 4 : (prec == PREC_BF16 ? 2 : 1)); }
@@ -157,11 +219,12 @@ void plan_layers(drc_ctx *c) {
   for (int s = 1; s <= S; ++s) {
     Layer L;
     memset(&L, 0, sizeof L);
-    L.kind = s == 1 ? LK_CONV_NCHW7 : LK_CONV;
-    L.Cin = wd[s - 1];
+    L.kind = LK_CONV;
+    L.Cin_raw = wd[s - 1];
+    L.Cin = s == 1 ? 8 : wd[s - 1];  // the 7-channel input is staged as NHWC with 8 channels
     L.Cout = wd[s];
     L.w_off = off;
-    off += 9ull * L.Cin * L.Cout;
+    off += 9ull * L.Cin_raw * L.Cout;
     L.b_off = off;
     off += L.Cout;
     L.BN = pick_bn(L.Cout);
@@ -173,30 +236,21 @@ void plan_layers(drc_ctx *c) {
       pd.u[t] = pd.dy[t] = (signed char)(t / 3);
       pd.v[t] = pd.dx[t] = (signed char)(t % 3);
     }
-    pd.num_kb = ceil_div(s == 1 ? 63 : 9ll * L.Cin, bke);
+    pd.num_kb = ceil_div(9ll * L.Cin, bke);
     finish(L);
   }
   for (int s = S; s >= 1; --s) {
     Layer L;
     memset(&L, 0, sizeof L);
-    L.Cin = wd[s];
+    L.Cin = L.Cin_raw = wd[s];
     L.Cout = s == 1 ? g.out_channels : wd[s - 1];
     L.w_off = off;
     off += 9ull * L.Cin * L.Cout;
     L.b_off = off;
     off += L.Cout;
     if (s == 1) {
-      L.kind = LK_HEAD;
-      L.BN = 16;
-      L.n_tiles = 1;
-      L.num_phases = 1;
-      PhaseDesc &pd = L.ph[0];
-      pd.ntaps = 4;
-      for (int t = 0; t < 4; ++t) {
-        pd.dy[t] = (signed char)(t >> 1);
-        pd.dx[t] = (signed char)(t & 1);
-      }
-      pd.num_kb = ceil_div(4ll * L.Cin, bke);
+      L.kind = LK_HEAD;  // fp32 FMA kernel (head.cu), no packed operands
+      L.num_phases = 0;
     } else {
       L.kind = LK_CONVT;
       L.BN = pick_bn(L.Cout);
@@ -264,11 +318,13 @@ drc_status check_dev(drc_ctx *c, const void *p, const char *name, bool nullable)
 
 drc_status pack_all(drc_ctx *c, cudaStream_t st) {
   for (const Layer &L : c->layers) {
+    if (L.kind == LK_HEAD) continue;
     PackArgs p;
     memset(&p, 0, sizeof p);
     p.kind = L.kind;
     p.wraw = c->d_wraw + L.w_off;
     p.Cin = L.Cin;
+    p.Cin_raw = L.Cin_raw;
     p.Cout = L.Cout;
     p.BN = L.BN;
     p.n_tiles = L.n_tiles;
@@ -285,7 +341,8 @@ drc_status pack_all(drc_ctx *c, cudaStream_t st) {
 }
 
 size_t act_bytes_for(const drc_ctx *c, long long N, int H, int W) {
-  size_t b = 0;
+  // the first layer's NHWC input (8 channels), then e_1 .. e_S
+  size_t b = (((size_t)N * H * W * 8 * elem_act(c->prec)) + 255) & ~(size_t)255;
   for (int s = 1; s <= c->cfg.num_stages; ++s)
     b += (((size_t)N * (H >> s) * (W >> s) * c->cfg.widths[s - 1] * elem_act(c->prec)) + 255) & ~(size_t)255;
   return b;
@@ -316,10 +373,10 @@ void fill_common(const drc_ctx *c, const Layer &L, ConvArgs &a) {
     a.ph[i] = L.ph[i];
     a.phase_order[i] = L.phase_order[i];
   }
-  a.exposure = c->cfg.exposure;
-  a.inv_exposure = 1.0f / c->cfg.exposure;
   a.act_scale_in = 1.f;
-  a.act_scale_out = 1.f;
+  a.cin_shift = -1;
+  for (int sh = 0; sh < 16; ++sh)
+    if ((1 << sh) == L.Cin) a.cin_shift = sh;
   a.status = c->d_status;
   a.timeout_ns = c->timeout_ns;
 }
@@ -416,6 +473,7 @@ drc_status drc_destroy(drc_ctx *c) {
   cudaFree(c->d_act);
   cudaFree(c->d_iscratch);
   cudaFree(c->d_status);
+  cudaFree(c->d_prof);
   cudaGetLastError();
   delete c;
   return DRC_OK;
@@ -446,8 +504,9 @@ drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, 
 
   // activation buffers e_1..e_S (decoder outputs overwrite them in place)
   std::vector<uint8_t *> act(S + 1, nullptr);
+  uint8_t *in8 = static_cast<uint8_t *>(c->d_act);  // first layer's NHWC input
   {
-    size_t off = 0;
+    size_t off = (((size_t)N * H * W * 8 * elem_act(c->prec)) + 255) & ~(size_t)255;
     for (int s2 = 1; s2 <= S; ++s2) {
       act[s2] = static_cast<uint8_t *>(c->d_act) + off;
       off += (((size_t)N * (H >> s2) * (W >> s2) * c->cfg.widths[s2 - 1] * elem_act(c->prec)) + 255) &
@@ -459,15 +518,27 @@ drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, 
     if (e != cudaSuccess) return cuda_fail(c, e, "payload clear");
   }
   const int debug_stall = (flags & DRC_F_DEBUG_STALL) ? 1 : 0;
+  e = launch_nchw7_to_nhwc8(in, in8, (long long)H * W, N, c->prec != PREC_TF32X3,
+                            (flags & DRC_F_ENCODE_INPUT) != 0, c->cfg.exposure, st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "input staging");
+  // Diagnostic: with DRC_PROFILE_WAITS set in the environment every conv
+  // launch records how long each warp role waited, printed to stderr per
+  // layer after the call (synchronising).  Off by default.
+  const bool prof = std::getenv("DRC_PROFILE_WAITS") != nullptr;
+  if (prof) {
+    const size_t pb = c->layers.size() * PROF_SLOTS * sizeof(unsigned long long);
+    if (!c->d_prof && cudaMalloc(&c->d_prof, pb) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "prof");
+    cudaMemsetAsync(c->d_prof, 0, pb, st);
+  }
   for (size_t li = 0; li < c->layers.size(); ++li) {
     const Layer &L = c->layers[li];
     ConvArgs a;
     fill_common(c, L, a);
     a.debug_stall = debug_stall && li == 0;
     a.N = N;
-    if (L.kind == LK_CONV_NCHW7 || L.kind == LK_CONV) {
+    if (L.kind == LK_CONV) {
       const int s2 = (int)li + 1;  // encoder stage
-      a.x = s2 == 1 ? static_cast<const void *>(in) : act[s2 - 1];
+      a.x = s2 == 1 ? static_cast<const void *>(in8) : act[s2 - 1];
       a.y = act[s2];
       a.Hin = H >> (s2 - 1);
       a.Win = W >> (s2 - 1);
@@ -476,7 +547,6 @@ drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, 
       a.Wrow = a.Wout = W >> s2;
       a.Cout = L.Cout;
       a.relu = 1;
-      a.encode = (s2 == 1 && (flags & DRC_F_ENCODE_INPUT)) ? 1 : 0;
     } else if (L.kind == LK_CONVT) {
       const int s2 = S - ((int)li - S);  // decoder stage S..2
       a.x = act[s2];
@@ -489,30 +559,58 @@ drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, 
       a.Wout = W >> (s2 - 1);
       a.Cout = L.Cout;
       a.relu = 1;
-    } else {  // head
-      a.x = act[1];
-      a.y = out;
-      a.payload = payload;
-      a.Hin = a.Hrow = H >> 1;
-      a.Win = a.Wrow = W >> 1;
-      a.Cin = L.Cin;
-      a.Hout = H;
-      a.Wout = W;
-      a.Cout = 3;
-      a.relu = c->cfg.out_relu ? 1 : 0;
-      a.decode = (flags & DRC_F_DECODE_OUTPUT) ? 1 : 0;
+    } else {  // head: 3-channel transposed conv + decode + payload (head.cu)
+      HeadArgs h;
+      memset(&h, 0, sizeof h);
+      h.x = act[1];
+      h.out = out;
+      h.payload = payload;
+      h.w = c->d_wraw + L.w_off;
+      h.bias = c->d_wraw + L.b_off;
+      h.N = N;
+      h.Hh = H >> 1;
+      h.Wh = W >> 1;
+      h.C = L.Cin;
+      h.relu = c->cfg.out_relu ? 1 : 0;
+      h.decode = (flags & DRC_F_DECODE_OUTPUT) ? 1 : 0;
+      h.inv_exposure = 1.0f / c->cfg.exposure;
       if (payload) {
         const double pi = 3.14159265358979323846;
         for (int i = 0; i < H; ++i) {
           const double t0 = i * pi / (2.0 * H), t1 = (i + 1) * pi / (2.0 * H);
-          a.band[i] = (float)((std::sin(t1) * std::sin(t1) - std::sin(t0) * std::sin(t0)) / W);
+          h.band[i] = (float)((std::sin(t1) * std::sin(t1) - std::sin(t0) * std::sin(t0)) / W);
         }
       }
+      e = launch_head(h, c->prec != PREC_TF32X3, st);
+      if (e != cudaSuccess) return cuda_fail(c, e, "head launch");
+      continue;
     }
     a.M = (int)((long long)N * a.Hrow * a.Wrow);
     a.m_tiles = ceil_div(a.M, BM);
+    plan_operand(c->prec, a);
+    if (prof) a.prof = c->d_prof + li * PROF_SLOTS;
     e = launch_conv(a, c->prec, c->num_sms, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "layer launch");
+  }
+  if (prof) {
+    std::vector<unsigned long long> h(c->layers.size() * PROF_SLOTS);
+    cudaStreamSynchronize(st);
+    cudaMemcpy(h.data(), c->d_prof, h.size() * sizeof(h[0]), cudaMemcpyDeviceToHost);
+    for (size_t li = 0; li < c->layers.size(); ++li) {
+      const unsigned long long *v = h.data() + li * PROF_SLOTS;
+      const double ctas = v[PROF_CTAS] ? (double)v[PROF_CTAS] : 1.0;
+      if (!v[PROF_CTAS]) continue;
+      fprintf(stderr,
+              "[drc prof] layer %zu kind %d BN %d: per CTA kcycles: mma total %.1f wait_full %.1f wait_tempty %.1f | "
+              "bload wait_empty %.1f | prod(8 warps) total %.1f wait_empty %.1f wait_copy %.1f issue %.1f convert %.1f "
+              "fence %.1f | epi(4 warps) total %.1f wait_tfull %.1f\n",
+              li, c->layers[li].kind, c->layers[li].BN, v[PROF_MMA_TOTAL] / ctas / 1e3,
+              v[PROF_MMA_WAIT_FULL] / ctas / 1e3, v[PROF_MMA_WAIT_TEMPTY] / ctas / 1e3,
+              v[PROF_BLOAD_WAIT_EMPTY] / ctas / 1e3, v[PROF_PROD_TOTAL] / ctas / 8e3,
+              v[PROF_PROD_WAIT_EMPTY] / ctas / 8e3, v[PROF_PROD_WAIT_COPY] / ctas / 8e3,
+              v[PROF_PROD_ISSUE] / ctas / 8e3, v[PROF_PROD_CONVERT] / ctas / 8e3, v[PROF_PROD_FENCE] / ctas / 8e3,
+              v[PROF_EPI_TOTAL] / ctas / 4e3, v[PROF_EPI_WAIT_TFULL] / ctas / 4e3);
+    }
   }
   return DRC_OK;
 }
@@ -555,7 +653,11 @@ drc_status drc_interpolate(drc_ctx *c, const drc_caches *caches, const drc_gbuff
     if (prm->mode == DRC_INTERP_LOOKUP && (s = check_dev(c, gbuf->dir, "gbuf->dir", false)) != DRC_OK) return s;
     if ((s = check_dev(c, prm->nbr_out, "nbr_out", true)) != DRC_OK) return s;
   }
-  const size_t need = interp_scratch_bytes(caches->n, prm->k);
+  // grid scratch, plus the pixel ordering for the WORLD metric (the G-buffer's
+  // first-hit positions are not coherent in image order)
+  const bool order = prm->metric == DRC_METRIC_WORLD && P > 0;
+  const size_t grid_bytes = (interp_scratch_bytes(caches->n, prm->k) + 255) & ~(size_t)255;
+  const size_t need = grid_bytes + (order ? interp_order_bytes(P) : 0);
   if (need > c->iscratch_bytes) {
     if (c->d_iscratch) cudaFree(c->d_iscratch);
     c->d_iscratch = nullptr;
@@ -589,6 +691,7 @@ drc_status drc_interpolate(drc_ctx *c, const drc_caches *caches, const drc_gbuff
   a.out = out_rgb;
   a.nbr_out = prm->nbr_out;
   InterpScratch sc = interp_carve(c->d_iscratch, caches->n, prm->k);
+  if (order) interp_attach_order(sc, static_cast<char *>(c->d_iscratch) + grid_bytes, P);
   cudaError_t e = launch_interp(a, sc, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(c, e, "interpolation launch");
   return DRC_OK;

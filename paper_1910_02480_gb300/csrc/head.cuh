@@ -1,0 +1,22 @@
+// head.cuh -- output layer of the autoencoder (3-channel transposed conv),
+// fp32 FMA kernel with the fused decode and irradiance payload.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace drc {
+
+struct HeadArgs {
+  const void *x;        // t_1, NHWC [N][Hh][Wh][C], fp32 or bf16
+  float *out;           // [N][3][2 Hh][2 Wh]
+  float *payload;       // [N][3] accumulated E/pi, or nullptr
+  const float *w;       // convT weights [C][3][3][3]
+  const float *bias;    // [3]
+  int N, Hh, Wh, C;
+  int relu, decode;
+  float inv_exposure;
+  float band[256];      // payload weight of each output row
+};
+
+cudaError_t launch_head(const HeadArgs &a, bool bf16, cudaStream_t st);
+
+}  // namespace drc

@@ -4,11 +4,19 @@
 //    WORLD metric, integer pixel coordinates for the IMAGE metric) is built by
 //    counting sort: bounds -> per-cell counts -> prefix sum -> scatter into a
 //    cell-ordered float4 table (x, y, z, index).
-// 2. One thread per pixel searches Chebyshev rings of cells around its own
-//    cell, keeping the k best (d^2, index) in registers, and stops once the
-//    k-th distance is below the distance to every unsearched cell: the
-//    selection is exact (the same set as a brute-force scan).
-// 3. Weights w = w_p w_n + w_p + eps (Eq. 4), normalised (Sec. 3.2), blend of
+// 2. Optionally the pixels are counting-sorted by a finer grid over the same
+//    box, so that the 32 threads of a warp query nearby points: their cell
+//    walks and their candidate lists then coincide (WORLD metric; image order
+//    is already coherent for the IMAGE metric).
+// 3. One thread per pixel visits its own cell, then the 26 neighbours nearest
+//    first, then further Chebyshev shells, skipping every cell whose box is
+//    farther than the current k-th distance.  The k best candidates are kept
+//    as 64-bit keys (d^2 bits << 32 | index: ascending key = ascending (d^2,
+//    index), since d^2 >= 0) in a sorted register array updated by a
+//    branch-free min/max network.  The walk stops once the k-th distance is
+//    below the distance to every unvisited cell, so the selection equals a
+//    brute-force scan.
+// 4. Weights w = w_p w_n + w_p + eps (Eq. 4), normalised (Sec. 3.2), blend of
 //    the payloads (IRRADIANCE) or of bilinear lat-long lookups of the cached
 //    maps in each cache's frame (LOOKUP).
 #include <cuda_runtime.h>
@@ -40,7 +48,7 @@ size_t interp_scratch_bytes(int n, int k) {
 }
 
 InterpScratch interp_carve(void *base, int n, int k) {
-  InterpScratch s;
+  InterpScratch s = {};
   const size_t mc = (size_t)interp_max_cells(n, k);
   char *p = static_cast<char *>(base);
   s.hdr = reinterpret_cast<GridHeader *>(p);
@@ -56,28 +64,62 @@ InterpScratch interp_carve(void *base, int n, int k) {
   return s;
 }
 
+static inline long long max_fine_bins(long long P) {
+  long long b = P / 16;
+  if (b < 1) b = 1;
+  if (b > (1 << 20)) b = 1 << 20;
+  return b;
+}
+
+size_t interp_order_bytes(long long P) {
+  const size_t mf = (size_t)max_fine_bins(P);
+  return align256(mf * sizeof(int)) + align256((mf + 1) * sizeof(int)) + align256((size_t)P * sizeof(int));
+}
+
+void interp_attach_order(InterpScratch &s, void *base, long long P) {
+  const size_t mf = (size_t)max_fine_bins(P);
+  char *p = static_cast<char *>(base);
+  s.fine_count = reinterpret_cast<int *>(p);
+  p += align256(mf * sizeof(int));
+  s.fine_start = reinterpret_cast<int *>(p);
+  p += align256((mf + 1) * sizeof(int));
+  s.order = reinterpret_cast<int *>(p);
+  s.max_fine = (int)mf;
+}
+
 __device__ __forceinline__ float3 cache_point(const InterpArgs &a, int j) {
   if (a.metric == METRIC_IMAGE) return make_float3((float)a.cpix[2 * j], (float)a.cpix[2 * j + 1], 0.f);
-  return make_float3(a.cpos[3 * j], a.cpos[3 * j + 1], a.cpos[3 * j + 2]);
+  return make_float3(__ldg(a.cpos + 3 * j), __ldg(a.cpos + 3 * j + 1), __ldg(a.cpos + 3 * j + 2));
 }
+
+__device__ __forceinline__ float3 query_point(const InterpArgs &a, long long p) {
+  if (a.metric == METRIC_IMAGE) return make_float3((float)(p % a.width), (float)(p / a.width), 0.f);
+  return make_float3(__ldg(a.gpos + 3 * p), __ldg(a.gpos + 3 * p + 1), __ldg(a.gpos + 3 * p + 2));
+}
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 __device__ __forceinline__ int cell_of(const GridHeader &g, float3 p, int3 *cc) {
-  int c[3];
-  const float pv[3] = {p.x, p.y, p.z};
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    int v = (int)floorf((pv[d] - g.origin[d]) * g.inv_h);
-    v = v < 0 ? 0 : (v >= g.dims[d] ? g.dims[d] - 1 : v);
-    c[d] = v;
-  }
-  if (cc) *cc = make_int3(c[0], c[1], c[2]);
-  return (c[2] * g.dims[1] + c[1]) * g.dims[0] + c[0];
+  const int cx = clampi((int)floorf((p.x - g.origin[0]) * g.inv_h), 0, g.dims[0] - 1);
+  const int cy = clampi((int)floorf((p.y - g.origin[1]) * g.inv_h), 0, g.dims[1] - 1);
+  const int cz = clampi((int)floorf((p.z - g.origin[2]) * g.inv_h), 0, g.dims[2] - 1);
+  if (cc) *cc = make_int3(cx, cy, cz);
+  return (cz * g.dims[1] + cy) * g.dims[0] + cx;
 }
 
-// Single block: bounds of the cache points, cubic cells sized for about
-// k/2 caches each over the occupied axes, counts cleared.
+__device__ __forceinline__ int fine_of(const GridHeader &g, float3 p) {
+  const int cx = clampi((int)floorf((p.x - g.origin[0]) * g.fine_inv_h), 0, g.fdims[0] - 1);
+  const int cy = clampi((int)floorf((p.y - g.origin[1]) * g.fine_inv_h), 0, g.fdims[1] - 1);
+  const int cz = clampi((int)floorf((p.z - g.origin[2]) * g.fine_inv_h), 0, g.fdims[2] - 1);
+  return (cz * g.fdims[1] + cy) * g.fdims[0] + cx;
+}
+
+// Single block: bounds of the cache points, cubic cells sized for about k/2
+// caches each over the occupied axes, the fine pixel-ordering grid, counts
+// cleared.
 __global__ void grid_bounds_kernel(InterpArgs a, InterpScratch s) {
   __shared__ float slo[3][32], shi[3][32];
+  __shared__ GridHeader sg;
   float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
   for (int j = threadIdx.x; j < a.n; j += blockDim.x) {
     const float3 p = cache_point(a, j);
@@ -144,10 +186,39 @@ __global__ void grid_bounds_kernel(InterpArgs a, InterpScratch s) {
     for (int d = 0; d < 3; ++d) g.origin[d] = L[d];
     g.h = (float)h;
     g.inv_h = (float)(1.0 / h);
-    g.pad_ = 0;
+    // fine grid: each coarse cell split m ways per occupied axis, about 32
+    // pixels per fine cell
+    int m = 1;
+    if (s.order && active) {
+      const double P = (double)a.width * (double)a.height;
+      double tgt = P / 32.0;
+      if (tgt > (double)s.max_fine) tgt = (double)s.max_fine;
+      m = (int)floor(pow(tgt / (double)g.ncells, 1.0 / active));
+      if (m < 1) m = 1;
+      if (m > 64) m = 64;
+    }
+    long long nf = 1;
+    for (int d = 0; d < 3; ++d) {
+      g.fdims[d] = ext[d] > 0.f ? g.dims[d] * m : 1;
+      nf *= g.fdims[d];
+    }
+    while (s.order && nf > s.max_fine && m > 1) {
+      --m;
+      nf = 1;
+      for (int d = 0; d < 3; ++d) {
+        g.fdims[d] = ext[d] > 0.f ? g.dims[d] * m : 1;
+        nf *= g.fdims[d];
+      }
+    }
+    g.nfine = (int)nf;
+    g.fine_inv_h = (float)((double)m / h);
     *s.hdr = g;
+    sg = g;
   }
+  __syncthreads();
   for (int c = threadIdx.x; c < s.max_cells; c += blockDim.x) s.cell_count[c] = 0;
+  if (s.order)
+    for (int c = threadIdx.x; c < sg.nfine; c += blockDim.x) s.fine_count[c] = 0;
 }
 
 __global__ void grid_count_kernel(InterpArgs a, InterpScratch s) {
@@ -159,44 +230,42 @@ __global__ void grid_count_kernel(InterpArgs a, InterpScratch s) {
   atomicAdd(&s.cell_count[c], 1);
 }
 
-// Single block exclusive scan of the cell counts; counts become cursors.
-__global__ void grid_scan_kernel(InterpScratch s) {
+// Single block exclusive scan of counts[0..*n_ptr); counts become cursors,
+// starts[*n_ptr] = total.  Each thread sums a contiguous run of bins, the
+// run totals are scanned across the block, then each thread writes its run.
+__global__ void scan_kernel(const int *n_ptr, int *counts, int *starts) {
   __shared__ int warp_tot[32];
-  __shared__ int carry;
-  const int nc = s.hdr->ncells;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
-  for (int base = 0; base < nc; base += blockDim.x) {
-    const int c = base + threadIdx.x;
-    const int v = c < nc ? s.cell_count[c] : 0;
-    int x = v;
-    const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (l >= o) x += y;
-    }
-    if (l == 31) warp_tot[w] = x;
-    __syncthreads();
-    if (w == 0) {
-      const int nw = blockDim.x >> 5;
-      int t = l < nw ? warp_tot[l] : 0;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, t, o);
-        if (l >= o) t += y;
-      }
-      if (l < nw) warp_tot[l] = t;
-    }
-    __syncthreads();
-    const int excl = carry + (w > 0 ? warp_tot[w - 1] : 0) + x - v;
-    if (c < nc) {
-      s.cell_start[c] = excl;
-      s.cell_count[c] = excl;
-    }
-    __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) carry = excl + v;
-    __syncthreads();
+  const int nc = *n_ptr;
+  const int per = (nc + blockDim.x - 1) / blockDim.x;
+  const int b0 = min(nc, (int)threadIdx.x * per), b1 = min(nc, b0 + per);
+  int run = 0;
+  for (int c = b0; c < b1; ++c) run += counts[c];
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = run;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (l >= o) x += y;
   }
-  if (threadIdx.x == 0) s.cell_start[nc] = carry;
+  if (l == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    int t = l < nw ? warp_tot[l] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (l >= o) t += y;
+    }
+    if (l < nw) warp_tot[l] = t;
+  }
+  __syncthreads();
+  int off = (w > 0 ? warp_tot[w - 1] : 0) + x - run;
+  for (int c = b0; c < b1; ++c) {
+    const int v = counts[c];
+    starts[c] = off;
+    counts[c] = off;
+    off += v;
+  }
+  if (threadIdx.x == blockDim.x - 1) starts[nc] = off;
 }
 
 __global__ void grid_scatter_kernel(InterpArgs a, InterpScratch s) {
@@ -208,54 +277,88 @@ __global__ void grid_scatter_kernel(InterpArgs a, InterpScratch s) {
   s.pts[pos] = make_float4(p.x, p.y, p.z, __int_as_float(j));
 }
 
+__global__ void pixel_count_kernel(InterpArgs a, InterpScratch s) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (long long)a.width * a.height) return;
+  const GridHeader g = *s.hdr;
+  atomicAdd(&s.fine_count[fine_of(g, query_point(a, p))], 1);
+}
+
+__global__ void pixel_scatter_kernel(InterpArgs a, InterpScratch s) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= (long long)a.width * a.height) return;
+  const GridHeader g = *s.hdr;
+  const int pos = atomicAdd(&s.fine_count[fine_of(g, query_point(a, p))], 1);
+  s.order[pos] = (int)p;
+}
+
+// The 26 neighbours of a cell, nearest first: faces, edges, corners.
+__constant__ signed char kShell1[26][3] = {
+    {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1},
+    {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0}, {-1, 0, -1}, {1, 0, -1},
+    {-1, 0, 1}, {1, 0, 1}, {0, -1, -1}, {0, 1, -1}, {0, -1, 1}, {0, 1, 1},
+    {-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {1, 1, -1}, {-1, -1, 1}, {1, -1, 1},
+    {-1, 1, 1}, {1, 1, 1}};
+
+// k-best register list: KMAX sorted 64-bit keys; the first KMAX-k slots hold
+// 0 (never displaced), so the k-th best is always the last slot.
 template <int KMAX>
-struct TopK {
-  float d[KMAX];
-  int i[KMAX];
-  __device__ __forceinline__ void init() {
+struct Best {
+  unsigned long long key[KMAX];
+  __device__ __forceinline__ void init(int k) {
 #pragma unroll
-    for (int s = 0; s < KMAX; ++s) {
-      d[s] = FLT_MAX;
-      i[s] = INT_MAX;
-    }
+    for (int s = 0; s < KMAX; ++s) key[s] = s < KMAX - k ? 0ull : ~0ull;
   }
-  // insert (dc, ic) keeping ascending (d, i) order
-  __device__ __forceinline__ void insert(float dc, int ic) {
+  __device__ __forceinline__ unsigned long long last() const { return key[KMAX - 1]; }
+  __device__ __forceinline__ void insert(unsigned long long kc) {
 #pragma unroll
-    for (int s = KMAX - 1; s >= 0; --s) {
-      const bool after = d[s] > dc || (d[s] == dc && i[s] > ic);
-      if (after) {
-        bool prev_after = false;
-        if (s > 0) prev_after = d[s - 1] > dc || (d[s - 1] == dc && i[s - 1] > ic);
-        if (prev_after) {
-          d[s] = d[s - 1];
-          i[s] = i[s - 1];
-        } else {
-          d[s] = dc;
-          i[s] = ic;
-        }
-      }
+    for (int s = KMAX - 1; s > 0; --s) {
+      const unsigned long long up = key[s - 1] > kc ? key[s - 1] : kc;
+      key[s] = key[s] < up ? key[s] : up;
     }
-  }
-  __device__ __forceinline__ void kth(int k, float &dk, int &ik) const {
-    dk = d[0];
-    ik = i[0];
-#pragma unroll
-    for (int s = 1; s < KMAX; ++s)
-      if (s == k - 1) {
-        dk = d[s];
-        ik = i[s];
-      }
+    key[0] = key[0] < kc ? key[0] : kc;
   }
 };
+
+struct Walk {
+  float3 q;
+  int found;
+};
+
+template <int KMAX>
+__device__ __forceinline__ void visit_cell(const GridHeader &g, const InterpScratch &s, int k, int cx, int cy,
+                                           int cz, Walk &w, Best<KMAX> &best) {
+  if (w.found >= k) {
+    // skip a cell whose box is farther than the current k-th distance
+    const float bx0 = g.origin[0] + (float)cx * g.h, by0 = g.origin[1] + (float)cy * g.h,
+                bz0 = g.origin[2] + (float)cz * g.h;
+    const float dx = fmaxf(fmaxf(bx0 - w.q.x, w.q.x - (bx0 + g.h)), 0.f);
+    const float dy = fmaxf(fmaxf(by0 - w.q.y, w.q.y - (by0 + g.h)), 0.f);
+    const float dz = g.dims[2] > 1 ? fmaxf(fmaxf(bz0 - w.q.z, w.q.z - (bz0 + g.h)), 0.f) : 0.f;
+    const float mind2 = dx * dx + dy * dy + dz * dz;
+    const float kd2 = __uint_as_float((unsigned)(best.last() >> 32));
+    if (mind2 > kd2 * 1.00001f + 1e-30f) return;
+  }
+  const int cell = (cz * g.dims[1] + cy) * g.dims[0] + cx;
+  const int e0 = __ldg(s.cell_start + cell), e1 = __ldg(s.cell_start + cell + 1);
+  for (int e = e0; e < e1; ++e) {
+    const float4 pt = __ldg(s.pts + e);
+    const float ex = w.q.x - pt.x, ey = w.q.y - pt.y, ez = w.q.z - pt.z;
+    const float d2 = ex * ex + ey * ey + ez * ez;
+    const unsigned long long kc =
+        ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)__float_as_int(pt.w);
+    ++w.found;
+    if (kc < best.last()) best.insert(kc);
+  }
+}
 
 __device__ __forceinline__ float bilinear_map(const float *R, int H, int W, float ti, float tj) {
   const float fi = floorf(ti), fj = floorf(tj);
   const float ai = ti - fi, aj = tj - fj;
   int i0 = (int)fi, j0 = (int)fj;
   int i1 = i0 + 1, j1 = j0 + 1;
-  i0 = i0 < 0 ? 0 : (i0 > H - 1 ? H - 1 : i0);
-  i1 = i1 < 0 ? 0 : (i1 > H - 1 ? H - 1 : i1);
+  i0 = clampi(i0, 0, H - 1);
+  i1 = clampi(i1, 0, H - 1);
   j0 = ((j0 % W) + W) % W;
   j1 = ((j1 % W) + W) % W;
   const float v00 = __ldg(R + i0 * W + j0), v01 = __ldg(R + i0 * W + j1);
@@ -264,53 +367,49 @@ __device__ __forceinline__ float bilinear_map(const float *R, int H, int W, floa
 }
 
 template <int KMAX>
-__global__ void __launch_bounds__(256, 2) interp_kernel(InterpArgs a, InterpScratch s) {
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(256) interp_query_kernel(InterpArgs a, InterpScratch s) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long P = (long long)a.width * a.height;
-  if (p >= P) return;
+  if (t >= P) return;
+  const long long p = s.order ? (long long)__ldg(s.order + t) : t;
   const GridHeader g = *s.hdr;
-  float3 q;
-  if (a.metric == METRIC_IMAGE)
-    q = make_float3((float)(p % a.width), (float)(p / a.width), 0.f);
-  else
-    q = make_float3(__ldg(a.gpos + 3 * p), __ldg(a.gpos + 3 * p + 1), __ldg(a.gpos + 3 * p + 2));
+  Walk w;
+  w.q = query_point(a, p);
+  w.found = 0;
   int3 c0;
-  cell_of(g, q, &c0);
-  TopK<KMAX> top;
-  top.init();
+  cell_of(g, w.q, &c0);
   const int k = a.k;
-  int found = 0;
+  Best<KMAX> best;
+  best.init(k);
   const float margin = 1e-4f * g.h;
   const int maxR = max(g.dims[0], max(g.dims[1], g.dims[2]));
   for (int R = 0; R <= maxR; ++R) {
-    const int z0 = max(c0.z - R, 0), z1 = min(c0.z + R, g.dims[2] - 1);
-    const int y0 = max(c0.y - R, 0), y1 = min(c0.y + R, g.dims[1] - 1);
-    const int x0 = max(c0.x - R, 0), x1 = min(c0.x + R, g.dims[0] - 1);
-    for (int cz = z0; cz <= z1; ++cz)
-      for (int cy = y0; cy <= y1; ++cy)
-        for (int cx = x0; cx <= x1; ++cx) {
-          const int cheb = max(abs(cx - c0.x), max(abs(cy - c0.y), abs(cz - c0.z)));
-          if (cheb != R) continue;
-          const int cell = (cz * g.dims[1] + cy) * g.dims[0] + cx;
-          const int e0 = __ldg(s.cell_start + cell), e1 = __ldg(s.cell_start + cell + 1);
-          for (int e = e0; e < e1; ++e) {
-            const float4 pt = __ldg(s.pts + e);
-            const float dx = q.x - pt.x, dy = q.y - pt.y, dz = q.z - pt.z;
-            const float d2 = dx * dx + dy * dy + dz * dz;
-            const int j = __float_as_int(pt.w);
-            ++found;
-            float dk;
-            int ik;
-            top.kth(k, dk, ik);
-            if (d2 < dk || (d2 == dk && j < ik)) top.insert(d2, j);
+    if (R == 0) {
+      visit_cell<KMAX>(g, s, k, c0.x, c0.y, c0.z, w, best);
+    } else if (R == 1) {
+      for (int o = 0; o < 26; ++o) {
+        const int cx = c0.x + kShell1[o][0], cy = c0.y + kShell1[o][1], cz = c0.z + kShell1[o][2];
+        if (cx < 0 || cy < 0 || cz < 0 || cx >= g.dims[0] || cy >= g.dims[1] || cz >= g.dims[2]) continue;
+        visit_cell<KMAX>(g, s, k, cx, cy, cz, w, best);
+      }
+    } else {
+      const int z0 = max(c0.z - R, 0), z1 = min(c0.z + R, g.dims[2] - 1);
+      const int y0 = max(c0.y - R, 0), y1 = min(c0.y + R, g.dims[1] - 1);
+      const int x0 = max(c0.x - R, 0), x1 = min(c0.x + R, g.dims[0] - 1);
+      for (int cz = z0; cz <= z1; ++cz)
+        for (int cy = y0; cy <= y1; ++cy)
+          for (int cx = x0; cx <= x1; ++cx) {
+            const int cheb = max(abs(cx - c0.x), max(abs(cy - c0.y), abs(cz - c0.z)));
+            if (cheb != R) continue;
+            visit_cell<KMAX>(g, s, k, cx, cy, cz, w, best);
           }
-        }
-    // stop when every cell is searched, or when the k-th distance is below
-    // the distance from q to every unsearched cell
+    }
+    // stop when every cell is visited, or when the k-th distance is below the
+    // distance from q to every cell outside the shells visited so far
     float bound = FLT_MAX;
     bool all = true;
     const int cc[3] = {c0.x, c0.y, c0.z};
-    const float qv[3] = {q.x, q.y, q.z};
+    const float qv[3] = {w.q.x, w.q.y, w.q.z};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       if (cc[d] - R > 0) {
@@ -323,43 +422,45 @@ __global__ void __launch_bounds__(256, 2) interp_kernel(InterpArgs a, InterpScra
       }
     }
     if (all) break;
-    if (found >= k) {
-      float dk;
-      int ik;
-      top.kth(k, dk, ik);
+    if (w.found >= k) {
+      const float kd2 = __uint_as_float((unsigned)(best.last() >> 32));
       const float b = bound - margin;
-      if (b > 0.f && dk <= b * b) break;
+      if (b > 0.f && kd2 <= b * b) break;
     }
   }
-  const int kk = found < k ? found : k;
+  const int kk = w.found < k ? w.found : k;
+  const int m = KMAX - k;
 
   // weights (Eq. 4) and normalisation
   const float pnx = __ldg(a.gnrm + 3 * p), pny = __ldg(a.gnrm + 3 * p + 1), pnz = __ldg(a.gnrm + 3 * p + 2);
   const float pl = sqrtf(pnx * pnx + pny * pny + pnz * pnz);
-  float w[KMAX];
+  float wt[KMAX];
+  int jj[KMAX];
   float wsum = 0.f;
 #pragma unroll
-  for (int t = 0; t < KMAX; ++t) {
-    w[t] = 0.f;
-    if (t < kk) {
-      const int j = top.i[t];
-      const float d = sqrtf(top.d[t]);
+  for (int sl = 0; sl < KMAX; ++sl) {
+    wt[sl] = 0.f;
+    jj[sl] = -1;
+    if (sl >= m && sl - m < kk) {
+      const int j = (int)(unsigned)(best.key[sl] & 0xffffffffu);
+      const float d = sqrtf(__uint_as_float((unsigned)(best.key[sl] >> 32)));
       const float wp = a.wp_form == WP_INVERSE ? a.r / (d + a.delta_rel * a.r) : fmaxf(0.f, 1.f - d / a.r);
       const float cx = __ldg(a.cnrm + 3 * j), cy = __ldg(a.cnrm + 3 * j + 1), cz = __ldg(a.cnrm + 3 * j + 2);
       const float cl = sqrtf(cx * cx + cy * cy + cz * cz);
       float wn = 0.f;
       if (pl > 0.f && cl > 0.f) wn = fmaxf(0.f, (cx * pnx + cy * pny + cz * pnz) / (cl * pl));
-      w[t] = wp * wn + wp + a.eps;
-      wsum += w[t];
+      wt[sl] = wp * wn + wp + a.eps;
+      jj[sl] = j;
+      wsum += wt[sl];
     }
   }
   float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
   if (a.mode == MODE_IRRADIANCE) {
 #pragma unroll
-    for (int t = 0; t < KMAX; ++t)
-      if (t < kk) {
-        const int j = top.i[t];
-        const float Wt = w[t] / wsum;
+    for (int sl = 0; sl < KMAX; ++sl)
+      if (jj[sl] >= 0) {
+        const int j = jj[sl];
+        const float Wt = wt[sl] / wsum;
         acc0 += Wt * __ldg(a.payload + 3 * j);
         acc1 += Wt * __ldg(a.payload + 3 * j + 1);
         acc2 += Wt * __ldg(a.payload + 3 * j + 2);
@@ -374,9 +475,9 @@ __global__ void __launch_bounds__(256, 2) interp_kernel(InterpArgs a, InterpScra
       const float two_pi = 6.283185307179586f;
       const size_t map_sz = (size_t)a.mapH * a.mapW;
 #pragma unroll
-      for (int t = 0; t < KMAX; ++t) {
-        if (t >= kk) continue;
-        const int j = top.i[t];
+      for (int sl = 0; sl < KMAX; ++sl) {
+        if (jj[sl] < 0) continue;
+        const int j = jj[sl];
         float nx = __ldg(a.cnrm + 3 * j), ny = __ldg(a.cnrm + 3 * j + 1), nz = __ldg(a.cnrm + 3 * j + 2);
         const float nl = sqrtf(nx * nx + ny * ny + nz * nz);
         if (!(nl > 0.f)) continue;
@@ -405,7 +506,7 @@ __global__ void __launch_bounds__(256, 2) interp_kernel(InterpArgs a, InterpScra
         if (phi < 0.f) phi += two_pi;
         const float ti = theta * (2.f / 3.14159265358979f) * (float)a.mapH - 0.5f;
         const float tj = phi * (1.f / two_pi) * (float)a.mapW - 0.5f;
-        const float Wt = w[t] / wsum;
+        const float Wt = wt[sl] / wsum;
         const float *Rj = a.maps + (size_t)j * 3 * map_sz;
         acc0 += Wt * bilinear_map(Rj, a.mapH, a.mapW, ti, tj);
         acc1 += Wt * bilinear_map(Rj + map_sz, a.mapH, a.mapW, ti, tj);
@@ -418,8 +519,8 @@ __global__ void __launch_bounds__(256, 2) interp_kernel(InterpArgs a, InterpScra
   a.out[3 * p + 2] = acc2;
   if (a.nbr_out) {
 #pragma unroll
-    for (int t = 0; t < KMAX; ++t)
-      if (t < k) a.nbr_out[(size_t)p * k + t] = t < kk ? top.i[t] : -1;
+    for (int sl = 0; sl < KMAX; ++sl)
+      if (sl >= m) a.nbr_out[(size_t)p * k + (sl - m)] = jj[sl];
   }
 }
 
@@ -427,17 +528,22 @@ cudaError_t launch_interp(const InterpArgs &a, const InterpScratch &s, cudaStrea
   grid_bounds_kernel<<<1, 1024, 0, st>>>(a, s);
   const int cb = (a.n + 255) / 256;
   grid_count_kernel<<<cb, 256, 0, st>>>(a, s);
-  grid_scan_kernel<<<1, 1024, 0, st>>>(s);
+  scan_kernel<<<1, 1024, 0, st>>>(&s.hdr->ncells, s.cell_count, s.cell_start);
   grid_scatter_kernel<<<cb, 256, 0, st>>>(a, s);
   const long long P = (long long)a.width * a.height;
   if (P == 0) return cudaGetLastError();
   const unsigned blocks = (unsigned)((P + 255) / 256);
+  if (s.order) {
+    pixel_count_kernel<<<blocks, 256, 0, st>>>(a, s);
+    scan_kernel<<<1, 1024, 0, st>>>(&s.hdr->nfine, s.fine_count, s.fine_start);
+    pixel_scatter_kernel<<<blocks, 256, 0, st>>>(a, s);
+  }
   if (a.k <= 8)
-    interp_kernel<8><<<blocks, 256, 0, st>>>(a, s);
+    interp_query_kernel<8><<<blocks, 256, 0, st>>>(a, s);
   else if (a.k <= 16)
-    interp_kernel<16><<<blocks, 256, 0, st>>>(a, s);
+    interp_query_kernel<16><<<blocks, 256, 0, st>>>(a, s);
   else
-    interp_kernel<32><<<blocks, 256, 0, st>>>(a, s);
+    interp_query_kernel<32><<<blocks, 256, 0, st>>>(a, s);
   return cudaGetLastError();
 }
 

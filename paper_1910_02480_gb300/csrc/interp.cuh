@@ -10,13 +10,15 @@ namespace drc {
 
 struct GridHeader {
   float origin[3];
-  float h, inv_h;
+  float h, inv_h;      // coarse cells (about k/2 caches each)
   int dims[3];
   int ncells;
-  int pad_;
+  float fine_inv_h;    // fine cells for ordering the pixels (about 32 pixels each)
+  int fdims[3];
+  int nfine;
 };
 
-// Device scratch used by one interpolation call, carved from one buffer.
+// Device scratch used by one interpolation call.
 struct InterpScratch {
   GridHeader *hdr;
   int *cell_count;   // [max_cells] counts, then write cursors
@@ -24,12 +26,21 @@ struct InterpScratch {
   int *cache_cell;   // [n]
   float4 *pts;       // [n] (x, y, z, index bits) in cell order
   int max_cells;
+  // optional pixel ordering (nullptr: pixels are processed in index order)
+  int *fine_count;   // [max_fine] counts, then cursors
+  int *fine_start;   // [max_fine + 1]
+  int *order;        // [P] pixel indices sorted by fine cell
+  int max_fine;
 };
 
-// Bytes of scratch for n caches and the cell budget chosen for them.
+// Grid scratch for n caches (no pixel ordering).
 size_t interp_scratch_bytes(int n, int k);
 int interp_max_cells(int n, int k);
 InterpScratch interp_carve(void *base, int n, int k);
+// Extra scratch that orders P pixels spatially before the search (same
+// results, better warp coherence); attach to a carved InterpScratch.
+size_t interp_order_bytes(long long P);
+void interp_attach_order(InterpScratch &s, void *base, long long P);
 
 struct InterpArgs {
   int n, mapH, mapW;
