@@ -366,20 +366,17 @@ __device__ __forceinline__ float bilinear_map(const float *R, int H, int W, floa
   return (1.f - ai) * ((1.f - aj) * v00 + aj * v01) + ai * ((1.f - aj) * v10 + aj * v11);
 }
 
+// Exact k nearest of q by walking Chebyshev shells of the coarse grid (own
+// cell, the 26 neighbours nearest first, then further shells), skipping
+// cells farther than the current k-th distance, until the k-th distance is
+// below the distance to every unvisited cell.  Returns the candidates seen.
 template <int KMAX>
-__global__ void __launch_bounds__(256) interp_query_kernel(InterpArgs a, InterpScratch s) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long P = (long long)a.width * a.height;
-  if (t >= P) return;
-  const long long p = s.order ? (long long)__ldg(s.order + t) : t;
-  const GridHeader g = *s.hdr;
+__device__ int knn_walk(const GridHeader &g, const InterpScratch &s, int k, float3 q, Best<KMAX> &best) {
   Walk w;
-  w.q = query_point(a, p);
+  w.q = q;
   w.found = 0;
   int3 c0;
   cell_of(g, w.q, &c0);
-  const int k = a.k;
-  Best<KMAX> best;
   best.init(k);
   const float margin = 1e-4f * g.h;
   const int maxR = max(g.dims[0], max(g.dims[1], g.dims[2]));
@@ -404,8 +401,6 @@ __global__ void __launch_bounds__(256) interp_query_kernel(InterpArgs a, InterpS
             visit_cell<KMAX>(g, s, k, cx, cy, cz, w, best);
           }
     }
-    // stop when every cell is visited, or when the k-th distance is below the
-    // distance from q to every cell outside the shells visited so far
     float bound = FLT_MAX;
     bool all = true;
     const int cc[3] = {c0.x, c0.y, c0.z};
@@ -428,10 +423,15 @@ __global__ void __launch_bounds__(256) interp_query_kernel(InterpArgs a, InterpS
       if (b > 0.f && kd2 <= b * b) break;
     }
   }
-  const int kk = w.found < k ? w.found : k;
-  const int m = KMAX - k;
+  return w.found;
+}
 
-  // weights (Eq. 4) and normalisation
+// Weights (Eq. 4), normalisation and blend for pixel p from its k best.
+template <int KMAX, int MODE>
+__device__ __forceinline__ void blend_store(const InterpArgs &a, long long p, const Best<KMAX> &best, int found) {
+  const int k = a.k;
+  const int kk = found < k ? found : k;
+  const int m = KMAX - k;
   const float pnx = __ldg(a.gnrm + 3 * p), pny = __ldg(a.gnrm + 3 * p + 1), pnz = __ldg(a.gnrm + 3 * p + 2);
   const float pl = sqrtf(pnx * pnx + pny * pny + pnz * pnz);
   float wt[KMAX];
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(256) interp_query_kernel(InterpArgs a, InterpS
     }
   }
   float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-  if (a.mode == MODE_IRRADIANCE) {
+  if constexpr (MODE == MODE_IRRADIANCE) {
 #pragma unroll
     for (int sl = 0; sl < KMAX; ++sl)
       if (jj[sl] >= 0) {
@@ -524,6 +524,22 @@ __global__ void __launch_bounds__(256) interp_query_kernel(InterpArgs a, InterpS
   }
 }
 
+// One thread per pixel (in the spatial order when the pixel ordering is
+// on): exact k nearest by the grid walk, then weights and blend.  MODE is
+// the blend (IRRADIANCE / LOOKUP), fixed at compile time so that each kernel
+// only carries its own registers and code.
+template <int KMAX, int MODE>
+__global__ void __launch_bounds__(256) interp_query_kernel(InterpArgs a, InterpScratch s) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long P = (long long)a.width * a.height;
+  if (t >= P) return;
+  const long long p = s.order ? (long long)__ldg(s.order + t) : t;
+  const GridHeader g = *s.hdr;
+  Best<KMAX> best;
+  const int found = knn_walk<KMAX>(g, s, a.k, query_point(a, p), best);
+  blend_store<KMAX, MODE>(a, p, best, found);
+}
+
 cudaError_t launch_interp(const InterpArgs &a, const InterpScratch &s, cudaStream_t st) {
   grid_bounds_kernel<<<1, 1024, 0, st>>>(a, s);
   const int cb = (a.n + 255) / 256;
@@ -538,12 +554,21 @@ cudaError_t launch_interp(const InterpArgs &a, const InterpScratch &s, cudaStrea
     scan_kernel<<<1, 1024, 0, st>>>(&s.hdr->nfine, s.fine_count, s.fine_start);
     pixel_scatter_kernel<<<blocks, 256, 0, st>>>(a, s);
   }
-  if (a.k <= 8)
-    interp_query_kernel<8><<<blocks, 256, 0, st>>>(a, s);
-  else if (a.k <= 16)
-    interp_query_kernel<16><<<blocks, 256, 0, st>>>(a, s);
-  else
-    interp_query_kernel<32><<<blocks, 256, 0, st>>>(a, s);
+  if (a.mode == MODE_IRRADIANCE) {
+    if (a.k <= 8)
+      interp_query_kernel<8, MODE_IRRADIANCE><<<blocks, 256, 0, st>>>(a, s);
+    else if (a.k <= 16)
+      interp_query_kernel<16, MODE_IRRADIANCE><<<blocks, 256, 0, st>>>(a, s);
+    else
+      interp_query_kernel<32, MODE_IRRADIANCE><<<blocks, 256, 0, st>>>(a, s);
+  } else {
+    if (a.k <= 8)
+      interp_query_kernel<8, 1><<<blocks, 256, 0, st>>>(a, s);
+    else if (a.k <= 16)
+      interp_query_kernel<16, 1><<<blocks, 256, 0, st>>>(a, s);
+    else
+      interp_query_kernel<32, 1><<<blocks, 256, 0, st>>>(a, s);
+  }
   return cudaGetLastError();
 }
 
