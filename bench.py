@@ -34,6 +34,11 @@ IMG_W, IMG_H, GRID = 1920, 1080, 64
 K_NN = 16
 METRIC_NAME = "cache-point maps denoised/sec on 1 GB300"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes (read + write) of the conv kernel's launches in one denoise call of
+# the 4096-map workload: ncu counters of the 2304-map case scaled by 4096/2304
+# (profiles/conv_tc_kernel_2304maps.md); None where not taken, and reset to
+# None whenever the kernel changes after the counters were taken.
+TRAFFIC = {"fp32": 1879e6, "bf16": None}
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense ratio (tf32 : bf16)
 
 
@@ -47,8 +52,9 @@ def set_workload(maps, frame):
         raise SystemExit("--maps must be a square number (a square cache grid)")
 
 
-def valid_macs_per_map(widths, H, W, cin=7, cout=3):
-    """Multiply-accumulates per map counting in-bounds taps only."""
+def valid_macs_per_layer(widths, H, W, cin=7, cout=3):
+    """{layer name: multiply-accumulates per map}, counting in-bounds taps only.
+    Names are the library's kernel labels (conv e1.., convT dS..d2, head)."""
     def conv_taps(n_in):  # per output index: taps u with 0 <= 2i+u-1 < n_in
         n_out = n_in // 2
         return sum(sum(1 for u in range(3) if 0 <= 2 * i + u - 1 < n_in) for i in range(n_out))
@@ -56,22 +62,26 @@ def valid_macs_per_map(widths, H, W, cin=7, cout=3):
     def convT_taps(n_in):  # per input index: taps landing inside 0..2n_in-1
         return sum(sum(1 for u in range(3) if 0 <= 2 * i + u - 1 < 2 * n_in) for i in range(n_in))
 
-    macs = 0
+    out = {}
     prev, h, w = cin, H, W
-    for c in widths:
-        macs += prev * c * conv_taps(h) * conv_taps(w)
+    for s, c in enumerate(widths, 1):
+        out["conv e%d" % s] = prev * c * conv_taps(h) * conv_taps(w)
         prev, h, w = c, h // 2, w // 2
     S = len(widths)
     for s in range(S, 0, -1):
         ci = widths[s - 1]
         co = cout if s == 1 else widths[s - 2]
         hs, ws = H >> s, W >> s
-        macs += ci * co * convT_taps(hs) * convT_taps(ws)
-    return macs
+        out["head" if s == 1 else "convT d%d" % s] = ci * co * convT_taps(hs) * convT_taps(ws)
+    return out
+
+
+def valid_macs_per_map(widths, H, W, cin=7, cout=3):
+    return sum(valid_macs_per_layer(widths, H, W, cin, cout).values())
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -84,7 +94,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                                          "--format=csv,noheader", "-lms", "200"],
+                                          "--format=csv,noheader", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -198,7 +208,7 @@ def run_reference(args, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
@@ -259,6 +269,9 @@ def main():
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ctx.read_timing()  # drop anything recorded before the timed region
+    ctx.set_timing(True)  # per-kernel CUDA events on the launching stream
+    launches0 = ctx.launch_count()
     for i in range(args.steps):
         flush.fill_(float(i))  # evict the previous step's data from L2 (outside the timed events)
         e0, e1, e2 = ev[i]
@@ -271,6 +284,9 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    ctx.set_timing(False)
+    ktimes = ctx.read_timing()
     step_ms = [a.elapsed_time(c_) for a, _, c_ in ev]
     den_ms = [a.elapsed_time(b) for a, b, _ in ev]
     itp_ms = [b.elapsed_time(c_) for _, b, c_ in ev]
@@ -312,24 +328,35 @@ def main():
     h2d = x.nbytes + g["pos"].nbytes + g["nrm"].nbytes
     d2h = IMG_W * IMG_H * 3 * 4
 
-    macs = valid_macs_per_map(WIDTHS, MAP_H, MAP_W)
-    flops = 2.0 * macs * N_MAPS
+    layer_macs = valid_macs_per_layer(WIDTHS, MAP_H, MAP_W)
     den = float(np.mean(den_ms)) * 1e-3
+    # the tensor-core conv kernel: its launches' device time (library events on
+    # the launching stream, over the timed region) against their valid FLOPs
+    conv_names = [n for n in layer_macs if n.startswith("conv")]
+    conv_flops = 2.0 * sum(layer_macs[n] for n in conv_names) * N_MAPS
+    conv_ms = sum(ktimes[n][1] for n in conv_names if n in ktimes) / args.steps
     peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else None
     if args.precision == "fp32":
         bf16 = peaks["bf16_tflops"] if peaks else 1900.0
         peak = bf16 * TF32_PER_BF16 / 3.0
-        peak_note = ("measured bf16 burst %.1f TF/s x nominal tf32/bf16 %.3f / 3 products" % (bf16, TF32_PER_BF16)
-                     if peaks else "fallback 1.9 PF/s bf16 x tf32/bf16 / 3")
+        peak_note = ("of measured: bf16 burst %.1f TF/s x nominal tf32/bf16 %.3f / 3 products" % (bf16, TF32_PER_BF16)
+                     if peaks else "of fallback: 1.9 PF/s bf16 x tf32/bf16 / 3")
     else:
         peak = peaks["bf16_tflops"] if peaks else 1900.0
-        peak_note = "measured bf16 burst" if peaks else "fallback bf16"
-    achieved = flops / den / 1e12
+        peak_note = "of measured: bf16 burst" if peaks else "of fallback: bf16"
+    achieved = conv_flops / (conv_ms * 1e-3) / 1e12 if conv_ms > 0 else None
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "conv_tc_kernel (the 6 layer launches of one denoise call)",
+                "frac": achieved / peak if achieved else None,
+                "traffic": TRAFFIC.get(args.precision) if N_MAPS == 4096 else None,
+                "kernel": "conv_tc_kernel (%d launches per denoise: %s)" % (len(conv_names), ", ".join(conv_names)),
                 "peak_source": peak_note,
-                "algorithmic_flops_per_call": flops}
+                "algorithmic_flops_per_call": conv_flops,
+                "kernel_ms_per_call": conv_ms}
+    kernels = {n: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
+               for n, v in ktimes.items()}
+    q = ktimes.get("interp query")
+    if q:
+        kernels["interp query"]["io_gb_per_s"] = IMG_W * IMG_H * 36 / (q[1] / q[0] * 1e-3) / 1e9
     line = {"metric": METRIC_NAME, "value": value, "unit": "maps/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "bf16", "data": "synthetic",
@@ -342,7 +369,8 @@ def main():
             "roofline": roofline,
             "e2e": {"value": world * N_MAPS / (e2e_step * 1e-3), "unit": "maps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": args.steps * (2 * len(WIDTHS) + 5),
+            "gpu_launches": launches,
+            "kernels": kernels,
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         b = cpu_baseline(w, x, g, c)

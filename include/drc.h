@@ -213,6 +213,30 @@ drc_status drc_get_status(drc_ctx *ctx, void *stream);
  * none).  Valid until the next call on the context. */
 const char *drc_last_error(drc_ctx *ctx);
 
+/* ---- Launch accounting (diagnostics; no counterpart in the paper) ---- */
+
+/* Kernel launches this context has issued since it was created (weight
+ * packing, denoise, interpolation), counted on the host at each launch. */
+drc_status drc_launch_count(drc_ctx *ctx, unsigned long long *count);
+
+/* While enabled, every kernel launch of the context is bracketed by two CUDA
+ * events recorded on its stream (a few microseconds of stream work each);
+ * off by default. */
+drc_status drc_set_timing(drc_ctx *ctx, int enable);
+
+typedef struct {
+  char name[32];      /* "conv e1", "convT d2", "head", "interp query", ... */
+  long long launches; /* timed launches of this kernel since the last read */
+  double total_ms;    /* their summed device time */
+} drc_kernel_time;
+
+/* Wait for the timed launches recorded since the last read, then write their
+ * per-kernel totals (in first-launch order) to out[0..*n_out) and clear them.
+ * capacity too small: the first `capacity` kernels are written and
+ * DRC_ERR_INVALID_ARG is returned. */
+drc_status drc_read_timing(drc_ctx *ctx, drc_kernel_time *out, int capacity,
+                           int *n_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -56,6 +56,10 @@ class GBuffer(ctypes.Structure):
                 ("nrm", ctypes.c_void_p), ("dir", ctypes.c_void_p)]
 
 
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
+
+
 class InterpParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("metric", ctypes.c_int), ("wp_form", ctypes.c_int),
                 ("mode", ctypes.c_int), ("r", ctypes.c_float), ("eps", ctypes.c_float),
@@ -97,6 +101,12 @@ def load_library():
     lib.drc_get_status.restype = I
     lib.drc_last_error.argtypes = [P]
     lib.drc_last_error.restype = ctypes.c_char_p
+    lib.drc_launch_count.argtypes = [P, ctypes.POINTER(ctypes.c_ulonglong)]
+    lib.drc_launch_count.restype = I
+    lib.drc_set_timing.argtypes = [P, I]
+    lib.drc_set_timing.restype = I
+    lib.drc_read_timing.argtypes = [P, ctypes.POINTER(KernelTime), I, ctypes.POINTER(I)]
+    lib.drc_read_timing.restype = I
     _lib = lib
     return lib
 
@@ -247,3 +257,21 @@ class Context:
         """Synchronise and return the latched device status code."""
         rc = self._lib.drc_get_status(self._ctx, _stream(stream))
         return rc
+
+    def launch_count(self):
+        """Kernel launches this context has issued since it was created."""
+        v = ctypes.c_ulonglong(0)
+        self._check(self._lib.drc_launch_count(self._ctx, ctypes.byref(v)), "drc_launch_count")
+        return int(v.value)
+
+    def set_timing(self, enable):
+        """Bracket every following kernel launch with CUDA events (diagnostics)."""
+        self._check(self._lib.drc_set_timing(self._ctx, 1 if enable else 0), "drc_set_timing")
+
+    def read_timing(self):
+        """{kernel name: (launches, total device ms)} of the timed launches since the last read."""
+        cap = 64
+        buf = (KernelTime * cap)()
+        n = ctypes.c_int(0)
+        self._check(self._lib.drc_read_timing(self._ctx, buf, cap, ctypes.byref(n)), "drc_read_timing")
+        return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(n.value)}

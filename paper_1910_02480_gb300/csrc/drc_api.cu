@@ -18,6 +18,7 @@
 #include "head.cuh"
 #include "drc_status.cuh"
 #include "interp.cuh"
+#include "trace.cuh"
 
 using namespace drc;
 
@@ -34,6 +35,7 @@ struct Layer {
   PhaseDesc ph[4];
   int phase_order[4];
   size_t pack_off, pack_bytes;  // in the packed operand buffer(s)
+  char name[16];                // kernel label for the launch tracer
 };
 
 }  // namespace
@@ -57,6 +59,7 @@ struct drc_ctx {
   unsigned long long *d_prof = nullptr;  // wait-time counters (DRC_PROFILE_WAITS)
   bool weights_set = false;
   unsigned long long timeout_ns = 0;
+  Tracer tracer;
   std::string err;
 };
 
@@ -220,6 +223,7 @@ void plan_layers(drc_ctx *c) {
     Layer L;
     memset(&L, 0, sizeof L);
     L.kind = LK_CONV;
+    snprintf(L.name, sizeof L.name, "conv e%d", s);
     L.Cin_raw = wd[s - 1];
     L.Cin = s == 1 ? 8 : wd[s - 1];  // the 7-channel input is staged as NHWC with 8 channels
     L.Cout = wd[s];
@@ -251,8 +255,10 @@ void plan_layers(drc_ctx *c) {
     if (s == 1) {
       L.kind = LK_HEAD;  // fp32 FMA kernel (head.cu), no packed operands
       L.num_phases = 0;
+      snprintf(L.name, sizeof L.name, "head");
     } else {
       L.kind = LK_CONVT;
+      snprintf(L.name, sizeof L.name, "convT d%d", s);
       L.BN = pick_bn(L.Cout);
       L.n_tiles = L.Cout / L.BN;
       L.num_phases = 4;
@@ -334,7 +340,8 @@ drc_status pack_all(drc_ctx *c, cudaStream_t st) {
     p.B_lo = c->d_pack_lo;
     p.bscale = c->d_bscale;
     p.total_chunks = (long long)(L.pack_bytes / 16);
-    cudaError_t e = launch_pack(p, c->prec, st);
+    cudaError_t e;
+    DRC_TRACED(&c->tracer, "weight pack", st, e = launch_pack(p, c->prec, st));
     if (e != cudaSuccess) return cuda_fail(c, e, "weight packing");
   }
   return DRC_OK;
@@ -518,8 +525,9 @@ drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, 
     if (e != cudaSuccess) return cuda_fail(c, e, "payload clear");
   }
   const int debug_stall = (flags & DRC_F_DEBUG_STALL) ? 1 : 0;
-  e = launch_nchw7_to_nhwc8(in, in8, (long long)H * W, N, c->prec != PREC_TF32X3,
-                            (flags & DRC_F_ENCODE_INPUT) != 0, c->cfg.exposure, st);
+  DRC_TRACED(&c->tracer, "stage input", st,
+             e = launch_nchw7_to_nhwc8(in, in8, (long long)H * W, N, c->prec != PREC_TF32X3,
+                                       (flags & DRC_F_ENCODE_INPUT) != 0, c->cfg.exposure, st));
   if (e != cudaSuccess) return cuda_fail(c, e, "input staging");
   // Diagnostic: with DRC_PROFILE_WAITS set in the environment every conv
   // launch records how long each warp role waited, printed to stderr per
@@ -581,7 +589,7 @@ drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, 
           h.band[i] = (float)((std::sin(t1) * std::sin(t1) - std::sin(t0) * std::sin(t0)) / W);
         }
       }
-      e = launch_head(h, c->prec != PREC_TF32X3, st);
+      DRC_TRACED(&c->tracer, L.name, st, e = launch_head(h, c->prec != PREC_TF32X3, st));
       if (e != cudaSuccess) return cuda_fail(c, e, "head launch");
       continue;
     }
@@ -589,7 +597,7 @@ drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, 
     a.m_tiles = ceil_div(a.M, BM);
     plan_operand(c->prec, a);
     if (prof) a.prof = c->d_prof + li * PROF_SLOTS;
-    e = launch_conv(a, c->prec, c->num_sms, st);
+    DRC_TRACED(&c->tracer, L.name, st, e = launch_conv(a, c->prec, c->num_sms, st));
     if (e != cudaSuccess) return cuda_fail(c, e, "layer launch");
   }
   if (prof) {
@@ -692,7 +700,7 @@ drc_status drc_interpolate(drc_ctx *c, const drc_caches *caches, const drc_gbuff
   a.nbr_out = prm->nbr_out;
   InterpScratch sc = interp_carve(c->d_iscratch, caches->n, prm->k);
   if (order) interp_attach_order(sc, static_cast<char *>(c->d_iscratch) + grid_bytes, P);
-  cudaError_t e = launch_interp(a, sc, static_cast<cudaStream_t>(stream));
+  cudaError_t e = launch_interp(a, sc, static_cast<cudaStream_t>(stream), &c->tracer);
   if (e != cudaSuccess) return cuda_fail(c, e, "interpolation launch");
   return DRC_OK;
 }
@@ -728,5 +736,35 @@ drc_status drc_get_status(drc_ctx *c, void *stream) {
 }
 
 const char *drc_last_error(drc_ctx *c) { return c ? c->err.c_str() : "NULL context"; }
+
+drc_status drc_launch_count(drc_ctx *c, unsigned long long *count) {
+  if (!c || !count) return DRC_ERR_INVALID_ARG;
+  *count = c->tracer.launches();
+  return DRC_OK;
+}
+
+drc_status drc_set_timing(drc_ctx *c, int enable) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->tracer.set_timing(enable != 0);
+  return DRC_OK;
+}
+
+drc_status drc_read_timing(drc_ctx *c, drc_kernel_time *out, int capacity, int *n_out) {
+  if (!c || !n_out || capacity < 0 || (capacity > 0 && !out)) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  std::vector<Tracer::Total> t = c->tracer.drain();
+  int n = 0;
+  for (const auto &x : t) {
+    if (n >= capacity) break;
+    memset(&out[n], 0, sizeof out[n]);
+    snprintf(out[n].name, sizeof out[n].name, "%s", x.name.c_str());
+    out[n].launches = x.launches;
+    out[n].total_ms = x.ms;
+    ++n;
+  }
+  *n_out = n;
+  if ((int)t.size() > capacity) return fail(c, DRC_ERR_INVALID_ARG, "capacity %d < %zu kernels", capacity, t.size());
+  return DRC_OK;
+}
 
 }  // extern "C"

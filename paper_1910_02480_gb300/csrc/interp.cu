@@ -540,20 +540,21 @@ __global__ void __launch_bounds__(256) interp_query_kernel(InterpArgs a, InterpS
   blend_store<KMAX, MODE>(a, p, best, found);
 }
 
-cudaError_t launch_interp(const InterpArgs &a, const InterpScratch &s, cudaStream_t st) {
-  grid_bounds_kernel<<<1, 1024, 0, st>>>(a, s);
+cudaError_t launch_interp(const InterpArgs &a, const InterpScratch &s, cudaStream_t st, Tracer *tr) {
+  DRC_TRACED(tr, "interp grid_bounds", st, (grid_bounds_kernel<<<1, 1024, 0, st>>>(a, s)));
   const int cb = (a.n + 255) / 256;
-  grid_count_kernel<<<cb, 256, 0, st>>>(a, s);
-  scan_kernel<<<1, 1024, 0, st>>>(&s.hdr->ncells, s.cell_count, s.cell_start);
-  grid_scatter_kernel<<<cb, 256, 0, st>>>(a, s);
+  DRC_TRACED(tr, "interp grid_count", st, (grid_count_kernel<<<cb, 256, 0, st>>>(a, s)));
+  DRC_TRACED(tr, "interp grid_scan", st, (scan_kernel<<<1, 1024, 0, st>>>(&s.hdr->ncells, s.cell_count, s.cell_start)));
+  DRC_TRACED(tr, "interp grid_scatter", st, (grid_scatter_kernel<<<cb, 256, 0, st>>>(a, s)));
   const long long P = (long long)a.width * a.height;
   if (P == 0) return cudaGetLastError();
   const unsigned blocks = (unsigned)((P + 255) / 256);
   if (s.order) {
-    pixel_count_kernel<<<blocks, 256, 0, st>>>(a, s);
-    scan_kernel<<<1, 1024, 0, st>>>(&s.hdr->nfine, s.fine_count, s.fine_start);
-    pixel_scatter_kernel<<<blocks, 256, 0, st>>>(a, s);
+    DRC_TRACED(tr, "interp pixel_count", st, (pixel_count_kernel<<<blocks, 256, 0, st>>>(a, s)));
+    DRC_TRACED(tr, "interp pixel_scan", st, (scan_kernel<<<1, 1024, 0, st>>>(&s.hdr->nfine, s.fine_count, s.fine_start)));
+    DRC_TRACED(tr, "interp pixel_scatter", st, (pixel_scatter_kernel<<<blocks, 256, 0, st>>>(a, s)));
   }
+  if (tr) tr->begin("interp query", st);
   if (a.mode == MODE_IRRADIANCE) {
     if (a.k <= 8)
       interp_query_kernel<8, MODE_IRRADIANCE><<<blocks, 256, 0, st>>>(a, s);
@@ -569,6 +570,7 @@ cudaError_t launch_interp(const InterpArgs &a, const InterpScratch &s, cudaStrea
     else
       interp_query_kernel<32, 1><<<blocks, 256, 0, st>>>(a, s);
   }
+  if (tr) tr->end(st);
   return cudaGetLastError();
 }
 

@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "trace.cuh"
+
 namespace drc {
 
 struct GridHeader {
@@ -54,6 +56,7 @@ struct InterpArgs {
   int *nbr_out;
 };
 
-cudaError_t launch_interp(const InterpArgs &a, const InterpScratch &s, cudaStream_t st);
+// tr: nullable launch tracer (counts and optionally times each kernel).
+cudaError_t launch_interp(const InterpArgs &a, const InterpScratch &s, cudaStream_t st, Tracer *tr = nullptr);
 
 }  // namespace drc

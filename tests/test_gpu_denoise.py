@@ -145,3 +145,28 @@ def test_stalled_wait_times_out_and_context_recovers(drc):
     out = ctx.denoise(xd)
     assert ctx.status() == drc.OK
     assert rel_err(out.cpu().numpy(), oracle.forward(w, x, widths)) <= FP32_TOL
+
+
+def test_launch_count_and_timing(drc):
+    """One denoise call launches the input staging kernel, S encoder convs,
+    S-1 decoder convTs and the head; with timing on each gets a device time,
+    and timing changes no result."""
+    widths = [16, 32, 48]
+    w = synth.he_weights(widths, seed=0, bias=True)
+    ctx = drc.Context(widths, w, precision="fp32")
+    x = torch.from_numpy(_maps(4, 32, 32)).cuda()
+    ref = ctx.denoise(x).clone()
+    n0 = ctx.launch_count()
+    ctx.set_timing(True)
+    out = ctx.denoise(x)
+    out = ctx.denoise(x, out=out)
+    ctx.set_timing(False)
+    assert ctx.launch_count() - n0 == 2 * (1 + 2 * len(widths))
+    t = ctx.read_timing()
+    names = ["stage input", "conv e1", "conv e2", "conv e3", "convT d3", "convT d2", "head"]
+    assert list(t) == names
+    for n in names:
+        assert t[n][0] == 2 and t[n][1] > 0.0
+    assert ctx.read_timing() == {}
+    assert ctx.status() == drc.OK
+    assert torch.equal(out, ref)
