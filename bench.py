@@ -38,7 +38,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the 4096-map workload: ncu counters of the 2304-map case scaled by 4096/2304
 # (profiles/conv_tc_kernel_2304maps.md); None where not taken, and reset to
 # None whenever the kernel changes after the counters were taken.
-TRAFFIC = {"fp32": 1879e6, "bf16": None}
+TRAFFIC = {"fp32": None, "bf16": None}
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense ratio (tf32 : bf16)
 
 
@@ -134,6 +134,122 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def _events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def measure_precision(drc, torch, dev, prec, fp32_denoise_ms, autotune=True, steps=20):
+    """Denoise-only throughput of another precision at the benchmark's size,
+    its speedup over the FP32 path, and its error against the FP64 oracle on
+    a sample of high-dynamic-range maps (lobes log-uniform in 1e-3..1e3)."""
+    import oracle
+    from paper_1910_02480_gb300 import synth
+    w = synth.he_weights(WIDTHS, seed=0)
+    g = synth.gbuffer(N_MAPS, 1, seed=12)
+    x, _ = synth.hemisphere_maps(g["pos"], g["nrm"], H=MAP_H, W=MAP_W, seed=3)
+    ctx = drc.Context(WIDTHS, w, precision=prec)
+    if autotune:
+        ctx.autotune(N_MAPS, MAP_H, MAP_W)
+    xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev)
+    out = torch.empty((N_MAPS, 3, MAP_H, MAP_W), device=dev)
+    pay = torch.empty((N_MAPS, 3), device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        ctx.denoise(xd, out=out, payload=pay)
+    ms = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        a, b = _events(torch)
+        a.record()
+        ctx.denoise(xd, out=out, payload=pay)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    if ctx.status() != drc.OK:
+        raise RuntimeError("device status after %s timing" % prec)
+    den = float(np.mean(ms))
+    # error sample: 16 maps of the HDR field, log1p-encoded radiance in
+    lobe = synth.lobes(seed=1, log_uniform=True)
+    xs, _ = synth.hemisphere_maps(g["pos"][:16], g["nrm"][:16], H=MAP_H, W=MAP_W, lobe=lobe, seed=5)
+    xs = np.ascontiguousarray(xs, dtype=np.float32)
+    o, pa = ctx.denoise(torch.from_numpy(xs).to(dev), want_payload=True)
+    torch.cuda.synchronize()
+    ref = oracle.forward(w, xs, WIDTHS)
+    refp = oracle.payload(np.expm1(ref))
+    err = {}
+    for name, gv, rv in (("out", o.cpu().numpy(), ref), ("payload", pa.cpu().numpy(), refp)):
+        rms = float(np.sqrt(np.mean(rv * rv)))
+        den_ = np.maximum(np.abs(rv), 0.1 * rms)
+        err[name] = {"max_rel": float(np.max(np.abs(gv - rv) / den_)),
+                     "normwise": float(np.linalg.norm(gv - rv) / np.linalg.norm(rv))}
+    ctx.close()
+    return {"denoise_ms": den, "denoise_maps_per_s": N_MAPS / (den * 1e-3),
+            "speedup_vs_fp32_denoise": fp32_denoise_ms / den, "error_vs_oracle": err,
+            "error_sample": "16 maps 7x32x32, lobes log-uniform 1e-3..1e3, FP64 oracle"}
+
+
+def measure_uneven(drc, torch, dev, prec="bf16", reps=3):
+    """Eight progressive passes with cache counts drawn in [200, 6000] and maps
+    16x16 or 32x32 with probability 1/2 (widths 32/64/128): one plan launch
+    per pass (autotuned tiles) against two drc_denoise calls per pass."""
+    from paper_1910_02480_gb300 import synth
+    widths = [32, 64, 128]
+    w = synth.he_weights(widths, seed=0)
+    counts, sizes = synth.pass_counts(seed=4)
+    per = [(int(np.sum(sz == 32)), int(np.sum(sz == 16))) for sz in sizes]
+    mx = int(max(counts))
+    g = synth.gbuffer(mx, 1, seed=13)
+    xs = {}
+    for h in (32, 16):
+        x, _ = synth.hemisphere_maps(g["pos"], g["nrm"], H=h, W=h, seed=6)
+        xs[h] = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev)
+    outs = {h: torch.empty((mx, 3, h, h), device=dev) for h in (32, 16)}
+    pays = {h: torch.empty((mx, 3), device=dev) for h in (32, 16)}
+    ctx = drc.Context(widths, w, precision=prec)
+    t0 = time.time()
+    plan = drc.Plan(ctx, [(32, 32, mx), (16, 16, mx)], autotune=True)
+    tune_s = time.time() - t0
+    dcounts = [torch.tensor(pc, dtype=torch.int32, device=dev) for pc in per]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def run_plan():
+        for dc in dcounts:
+            plan.launch(dc, [xs[32], xs[16]], [outs[32], outs[16]], [pays[32], pays[16]])
+
+    def run_calls():
+        for n32, n16 in per:
+            ctx.denoise(xs[32][:n32], out=outs[32][:n32], payload=pays[32][:n32])
+            ctx.denoise(xs[16][:n16], out=outs[16][:n16], payload=pays[16][:n16])
+
+    res = {}
+    for name, fn in (("plan", run_plan), ("denoise_calls", run_calls)):
+        fn()
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            a, b = _events(torch)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        res[name] = float(np.min(ms))
+    if ctx.status() != drc.OK:
+        raise RuntimeError("device status after uneven batching")
+    total = int(np.sum(counts))
+    tiles = {"32x32": [plan.describe(0, li)[0] for li in range(2 * len(widths) - 1)],
+             "16x16": [plan.describe(1, li)[0] for li in range(2 * len(widths) - 1)]}
+    plan.close()
+    ctx.close()
+    return {"passes": len(counts), "maps": total, "counts": [int(c) for c in counts],
+            "precision": prec, "widths": widths,
+            "plan_ms": res["plan"], "plan_maps_per_s": total / (res["plan"] * 1e-3),
+            "denoise_calls_ms": res["denoise_calls"],
+            "denoise_calls_maps_per_s": total / (res["denoise_calls"] * 1e-3),
+            "autotuned_tile_n": tiles, "autotune_s": tune_s}
+
+
 def make_inputs(seed_offset=0):
     from paper_1910_02480_gb300 import synth
     g = synth.gbuffer(IMG_W, IMG_H, seed=2 + seed_offset)
@@ -213,6 +329,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the precision and uneven-batching lines")
+    ap.add_argument("--no-autotune", action="store_true", help="default tile widths instead of drc_autotune")
     ap.add_argument("--maps", type=int, default=N_MAPS, help="maps per step (profiling of smaller cases)")
     ap.add_argument("--frame", default="%dx%d" % (IMG_W, IMG_H), help="G-buffer WxH (profiling)")
     args = ap.parse_args()
@@ -238,6 +356,9 @@ def main():
     w, x, g, c = make_inputs(seed_offset=rank)
     dev = torch.device("cuda", local)
     ctx = drc.Context(WIDTHS, w, precision=args.precision, max_maps=N_MAPS, max_hw=MAP_H * MAP_W)
+    if not args.no_autotune:
+        ctx.autotune(N_MAPS, MAP_H, MAP_W)  # setup: per-layer tile choice for this batch shape
+    tiles = [ctx.describe_layer(li) for li in range(2 * len(WIDTHS))]
     xd = torch.from_numpy(x).to(dev)
     gd = {"width": IMG_W, "height": IMG_H, "pos": torch.from_numpy(g["pos"]).to(dev),
           "nrm": torch.from_numpy(g["nrm"]).to(dev)}
@@ -363,6 +484,8 @@ def main():
             "config": {"workload": "%d maps 7x32x32, encoder 64/128/256 (FP32 production size) + "
                                    "%dx%d interpolation, k=16, WORLD metric, IRRADIANCE" % (N_MAPS, IMG_W, IMG_H),
                        "precision": args.precision, "l2": "flushed between timed steps (256 MB write)",
+                       "conv_tiles": {n: {"tile_n": t[0], "a_path": t[1]} for n, t in zip(
+                           [k for k in valid_macs_per_layer(WIDTHS, MAP_H, MAP_W)], tiles)},
                        "parallelism": "replica per GPU" if world > 1 else "1 GPU"},
             "denoise_ms": den * 1e3, "interp_ms": float(np.mean(itp_ms)),
             "interp_pixels_per_s": IMG_W * IMG_H / (float(np.mean(itp_ms)) * 1e-3),
@@ -372,6 +495,10 @@ def main():
             "gpu_launches": launches,
             "kernels": kernels,
             "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_extras and N_MAPS == 4096:
+        line["precision_variants"] = {p: measure_precision(drc, torch, dev, p, den * 1e3, not args.no_autotune)
+                                      for p in ("bf16",) if p != args.precision}
+        line["uneven_batching"] = measure_uneven(drc, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         b = cpu_baseline(w, x, g, c)
         b.pop("step_s", None)

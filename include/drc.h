@@ -213,6 +213,71 @@ drc_status drc_get_status(drc_ctx *ctx, void *stream);
  * none).  Valid until the next call on the context. */
 const char *drc_last_error(drc_ctx *ctx);
 
+/* Tune the context's conv layers for batches of N maps of H x W: each
+ * layer's tile width (GEMM N per tile: its output channels, or half of them)
+ * and, for FP32, its A-operand path are timed on the context's own workspace
+ * and the fastest kept for every later drc_denoise (results stay within the
+ * precision's tolerance).
+ * Synchronises the device; grows the workspace to N maps.  No counterpart in
+ * the paper. */
+drc_status drc_autotune(drc_ctx *ctx, int N, int H, int W);
+
+/* The tile width (0 for the head) and A-operand path (-1 default, 1 TMA +
+ * producer conversion) drc_denoise uses for one layer (0 .. 2S-1). */
+drc_status drc_describe_layer(drc_ctx *ctx, int layer, int *bn, int *a_path);
+
+/* ---- Plans: progressive passes with uneven batches ------------------------
+ * Sec. 3.2 ("Progressive refinement and interpolation"): every indirect pass
+ * shrinks the cache grid by a constant factor, so each pass denoises a
+ * different number of cache maps.  A plan is built once for a set of map
+ * sizes (classes), each with a maximum count; every pass is then one small
+ * kernel (this pass's counts and buffers into the plan's device slots) and
+ * one CUDA-graph launch holding the whole network for every class, its
+ * tensor-core kernels persistent (one CTA per SM) and sized by the count
+ * they read from device memory.  No allocation, synchronisation or host
+ * read of the counts per pass.                                              */
+
+typedef struct {
+  int H, W;     /* map size of this class (multiples of 2^num_stages, H <= 256) */
+  int max_maps; /* largest count a pass may give this class (>= 1) */
+} drc_size_class;
+
+typedef struct drc_plan drc_plan;
+
+#define DRC_PLAN_AUTOTUNE 0x1u /* time each conv layer's tile-width (and, for
+                                  FP32, A-operand path) candidates on the
+                                  class's full-size buffers at creation and
+                                  keep the fastest; otherwise the defaults of
+                                  drc_denoise */
+
+/* Build a plan on ctx (weights must be set).  Allocates its own activation
+ * buffers (max_maps of each class), packed operands and graph; synchronises
+ * the device while building.  1 <= n_classes <= 8.  The plan uses the
+ * context's weights and status word: destroy it before the context. */
+drc_status drc_plan_create(drc_ctx *ctx, const drc_size_class *classes,
+                           int n_classes, unsigned flags, drc_plan **plan);
+
+/* Run one pass on `stream`.
+ *   counts:  device int[n_classes], maps of each class in this pass; a count
+ *            outside 0..max_maps is clamped and latches DRC_ERR_INVALID_ARG
+ *            (returned by drc_get_status);
+ *   in[k]:   device [counts[k]][7][H_k][W_k] fp32 (host array of pointers);
+ *   out[k]:  device [counts[k]][3][H_k][W_k] fp32;
+ *   payload: nullable host array; payload[k] nullable device [counts[k]][3];
+ *   flags:   DRC_F_ENCODE_INPUT / DRC_F_DECODE_OUTPUT, as drc_denoise.
+ * Results equal drc_denoise of each class's maps.  Weights set on the
+ * context after the plan was built are repacked before the pass. */
+drc_status drc_plan_launch(drc_plan *plan, const int *counts,
+                           const float *const *in, float *const *out,
+                           float *const *payload, unsigned flags, void *stream);
+
+/* The chosen tile width (GEMM N per tile; 0 for the head) and A-operand
+ * path (-1 default, 1 TMA + producer conversion) of one layer of one class. */
+drc_status drc_plan_describe(drc_plan *plan, int size_class, int layer,
+                             int *bn, int *a_path);
+
+drc_status drc_plan_destroy(drc_plan *plan);
+
 /* ---- Launch accounting (diagnostics; no counterpart in the paper) ---- */
 
 /* Kernel launches this context has issued since it was created (weight

@@ -56,6 +56,10 @@ class GBuffer(ctypes.Structure):
                 ("nrm", ctypes.c_void_p), ("dir", ctypes.c_void_p)]
 
 
+class SizeClass(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("max_maps", ctypes.c_int)]
+
+
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("total_ms", ctypes.c_double)]
 
@@ -107,6 +111,19 @@ def load_library():
     lib.drc_set_timing.restype = I
     lib.drc_read_timing.argtypes = [P, ctypes.POINTER(KernelTime), I, ctypes.POINTER(I)]
     lib.drc_read_timing.restype = I
+    PP = ctypes.POINTER(P)
+    lib.drc_plan_create.argtypes = [P, ctypes.POINTER(SizeClass), I, U, PP]
+    lib.drc_plan_create.restype = I
+    lib.drc_plan_launch.argtypes = [P, P, PP, PP, PP, U, P]
+    lib.drc_plan_launch.restype = I
+    lib.drc_plan_describe.argtypes = [P, I, I, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.drc_plan_describe.restype = I
+    lib.drc_autotune.argtypes = [P, I, I, I]
+    lib.drc_autotune.restype = I
+    lib.drc_describe_layer.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.drc_describe_layer.restype = I
+    lib.drc_plan_destroy.argtypes = [P]
+    lib.drc_plan_destroy.restype = I
     _lib = lib
     return lib
 
@@ -258,6 +275,17 @@ class Context:
         rc = self._lib.drc_get_status(self._ctx, _stream(stream))
         return rc
 
+    def autotune(self, N, H, W):
+        """Time each conv layer's tile candidates for N maps of H x W and keep
+        the fastest for later denoise calls (synchronises)."""
+        self._check(self._lib.drc_autotune(self._ctx, int(N), int(H), int(W)), "drc_autotune")
+
+    def describe_layer(self, layer):
+        bn, path = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(self._lib.drc_describe_layer(self._ctx, layer, ctypes.byref(bn), ctypes.byref(path)),
+                    "drc_describe_layer")
+        return bn.value, path.value
+
     def launch_count(self):
         """Kernel launches this context has issued since it was created."""
         v = ctypes.c_ulonglong(0)
@@ -275,3 +303,50 @@ class Context:
         n = ctypes.c_int(0)
         self._check(self._lib.drc_read_timing(self._ctx, buf, cap, ctypes.byref(n)), "drc_read_timing")
         return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms)) for i in range(n.value)}
+
+
+PLAN_AUTOTUNE = 0x1
+
+
+class Plan:
+    """A drc_plan: progressive passes over several map sizes, one CUDA-graph
+    launch per pass, counts read from device memory."""
+
+    def __init__(self, ctx, classes, autotune=False):
+        self._ctx = ctx
+        self._lib = ctx._lib
+        self.classes = [tuple(int(v) for v in c) for c in classes]
+        arr = (SizeClass * len(classes))(*[SizeClass(h, w, m) for h, w, m in self.classes])
+        self._plan = ctypes.c_void_p()
+        rc = self._lib.drc_plan_create(ctx._ctx, arr, len(classes), PLAN_AUTOTUNE if autotune else 0,
+                                       ctypes.byref(self._plan))
+        ctx._check(rc, "drc_plan_create")
+
+    def launch(self, counts, ins, outs, payloads=None, flags=0, stream=None):
+        """counts: device int32 tensor [n_classes]; ins / outs / payloads: one
+        device tensor (or None for a payload) per class."""
+        n = len(self.classes)
+        P = ctypes.c_void_p
+        pin = (P * n)(*[t.data_ptr() for t in ins])
+        pout = (P * n)(*[t.data_ptr() for t in outs])
+        ppay = None if payloads is None else (P * n)(*[0 if t is None else t.data_ptr() for t in payloads])
+        rc = self._lib.drc_plan_launch(self._plan, _ptr(counts), pin, pout, ppay, flags, _stream(stream))
+        self._ctx._check(rc, "drc_plan_launch")
+
+    def describe(self, k, layer):
+        bn, path = ctypes.c_int(0), ctypes.c_int(0)
+        rc = self._lib.drc_plan_describe(self._plan, k, layer, ctypes.byref(bn), ctypes.byref(path))
+        if rc != OK:
+            raise DrcError(rc, "drc_plan_describe")
+        return bn.value, path.value
+
+    def close(self):
+        if self._plan:
+            self._lib.drc_plan_destroy(self._plan)
+            self._plan = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -119,14 +119,32 @@ __device__ __forceinline__ uint32_t swz(int r, int q) {
 struct TileCoord {
   int phase, m_tile, n_tile;
 };
+
+// Rows of the GEMM: a.M, or a.count maps (clamped to 0..a.N) when the count
+// lives in device memory.
+__device__ __forceinline__ int gemm_rows(const ConvArgs &a) {
+  if (!a.count) return a.M;
+  int n = *reinterpret_cast<const volatile int *>(a.count);
+  n = n < 0 ? 0 : (n > a.N ? a.N : n);
+  return n * a.Hrow * a.Wrow;
+}
+// Tile t of the persistent schedule (CTA b takes t = b, b + G, b + 2G, ...).
+// Several phases (decoder): the phases of one (m, n) tile are consecutive in
+// t, so they run side by side on neighbouring CTAs and read the same input
+// rows while they are in L2.  When G is a multiple of the phase count, a
+// CTA's phase also advances by one every round (t / G), so each CTA cycles
+// through the light and heavy phases instead of always drawing the same one;
+// the rotation stays a bijection because a tile's P consecutive t never
+// straddle a multiple of G.
 __device__ __forceinline__ TileCoord tile_coord(const ConvArgs &a, int t) {
-  const int per_phase = a.m_tiles * a.n_tiles;
-  const int p = t / per_phase;
-  const int rem = t - p * per_phase;
   TileCoord c;
-  c.phase = a.phase_order[p];
-  c.m_tile = rem / a.n_tiles;
-  c.n_tile = rem - c.m_tile * a.n_tiles;
+  const int P = a.num_phases;
+  const int unit = t / P;
+  int l = t - unit * P;
+  if (P > 1 && gridDim.x % P == 0) l = (l + (int)(t / gridDim.x)) % P;
+  c.phase = a.phase_order[l];
+  c.m_tile = unit / a.n_tiles;
+  c.n_tile = unit - c.m_tile * a.n_tiles;
   return c;
 }
 
@@ -236,7 +254,7 @@ __device__ __forceinline__ unsigned long long pack_taps(const PhaseDesc &pd) {
   return tp;
 }
 
-__device__ __forceinline__ void prod_setup(const ConvArgs &a, int t, int pt, RowInfo &ri) {
+__device__ __forceinline__ void prod_setup(const ConvArgs &a, int M, int t, int pt, RowInfo &ri) {
   const TileCoord tc = tile_coord(a, t);
   // the phase's tap table, read once per tile into registers
   const PhaseDesc &pd = a.ph[tc.phase];
@@ -251,7 +269,7 @@ __device__ __forceinline__ void prod_setup(const ConvArgs &a, int t, int pt, Row
   for (int it = 0; it < 4; ++it) {
     const int r = (lane >> 3) + 4 * pw + 32 * it;
     const int m = tc.m_tile * BM + r;
-    const bool v = m < a.M;
+    const bool v = m < M;
     const int n = v ? m / rows_per_map : 0;
     const int rem = v ? m - n * rows_per_map : 0;
     const int i = rem / a.Wrow, j = rem - (rem / a.Wrow) * a.Wrow;
@@ -430,7 +448,8 @@ __device__ __forceinline__ void tma_issue(const ConvArgs &a, const TmaCursor &c,
 template <int PREC>
 __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint8_t *raw, uint64_t *full_bar,
                                           uint64_t *empty_bar, uint64_t *raw_full, uint64_t *raw_empty, int stages,
-                                          int sbytes, int R, int slot_bytes, int total_tiles, uint32_t tmem_base) {
+                                          int sbytes, int R, int slot_bytes, int M, int total_tiles,
+                                          uint32_t tmem_base) {
   const int pt = threadIdx.x - PROD_WARP0 * 32;  // 0..255
   const int lane = pt & 31;
   const int a_bytes = BM * KROW_BYTES;
@@ -539,7 +558,7 @@ __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint
     int it_t = blockIdx.x, it_kb = 0;
     bool it_more = true;
     RowInfo ri;
-    prod_setup(a, it_t, pt, ri);
+    prod_setup(a, M, it_t, pt, ri);
     int islot = 0;
     auto issue = [&]() {
       const long long ti0 = a.prof ? clock64() : 0;
@@ -549,7 +568,7 @@ __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint
           it_kb = 0;
           it_t += gridDim.x;
           if (it_t < total_tiles)
-            prod_setup(a, it_t, pt, ri);
+            prod_setup(a, M, it_t, pt, ri);
           else
             it_more = false;
         }
@@ -609,6 +628,78 @@ __device__ __forceinline__ void tmem_ld_acc(uint32_t taddr, int BN, float (&v)[1
     tmem_ld16(taddr + (uint32_t)BN, c);
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] += c[e];
+  }
+}
+
+// 16 consecutive skip channels as raw 16-byte words (fp32: 4 words, bf16: 2).
+template <int PREC>
+__device__ __forceinline__ void load_skip(const typename PrecTraits<PREC>::act_t *p, uint4 (&s)[4]) {
+  const uint4 *q = reinterpret_cast<const uint4 *>(p);
+  if constexpr (PREC == PREC_TF32X3) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) s[e] = q[e];
+  } else {
+#pragma unroll
+    for (int e = 0; e < 2; ++e) s[e] = q[e];
+  }
+}
+
+// Epilogue of one 16-column chunk of one accumulator row: TMEM load (every
+// lane: the load is warp-collective), then for a valid row bias, ReLU, the
+// skip add and the NHWC store.
+template <int PREC>
+__device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int cc, int BN, int col0, bool vrow,
+                                          bool has_skip, const uint4 (&sk)[4],
+                                          typename PrecTraits<PREC>::act_t *yp) {
+  float v[16];
+  tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
+  if (!vrow) return;
+  const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
+  const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
+#pragma unroll
+  for (int e4 = 0; e4 < 4; ++e4) {
+    const float4 b = __ldg(bias4 + e4);
+    const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      float z = bsc ? v[4 * e4 + e] * bsc[4 * e4 + e] : v[4 * e4 + e];
+      z += bb[e];
+      if (a.relu) z = fmaxf(z, 0.f);
+      v[4 * e4 + e] = z;
+    }
+  }
+  if constexpr (PREC == PREC_TF32X3) {
+    if (has_skip) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        v[4 * e] += __uint_as_float(sk[e].x);
+        v[4 * e + 1] += __uint_as_float(sk[e].y);
+        v[4 * e + 2] += __uint_as_float(sk[e].z);
+        v[4 * e + 3] += __uint_as_float(sk[e].w);
+      }
+    }
+    float4 *q = reinterpret_cast<float4 *>(yp);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) q[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+  } else {
+    if (has_skip) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        v[8 * e + 0] += bf16_lo(sk[e].x);
+        v[8 * e + 1] += bf16_hi(sk[e].x);
+        v[8 * e + 2] += bf16_lo(sk[e].y);
+        v[8 * e + 3] += bf16_hi(sk[e].y);
+        v[8 * e + 4] += bf16_lo(sk[e].z);
+        v[8 * e + 5] += bf16_hi(sk[e].z);
+        v[8 * e + 6] += bf16_lo(sk[e].w);
+        v[8 * e + 7] += bf16_hi(sk[e].w);
+      }
+    }
+    uint4 *q = reinterpret_cast<uint4 *>(yp);
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+      q[e] = make_uint4(pack_bf16x2(v[8 * e], v[8 * e + 1]), pack_bf16x2(v[8 * e + 2], v[8 * e + 3]),
+                        pack_bf16x2(v[8 * e + 4], v[8 * e + 5]), pack_bf16x2(v[8 * e + 6], v[8 * e + 7]));
   }
 }
 
@@ -683,7 +774,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
 
-  const int total_tiles = a.num_phases * a.m_tiles * a.n_tiles;
+  // GEMM rows of this launch: fixed, or read from device memory (a graph
+  // captured once serves every count up to a.N)
+  const int M = gemm_rows(a);
+  const int total_tiles = a.num_phases * ((M + BM - 1) / BM) * a.n_tiles;
   const unsigned long long tmo = a.timeout_ns;
 
   if (warp == MMA_WARP) {
@@ -788,7 +882,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     }
   } else if (warp >= PROD_WARP0) {
     run_producer<PREC>(a, data, data + stages * sbytes, full_bar, empty_bar, raw_full, raw_empty, stages, sbytes,
-                       plan.raw_depth, plan.raw_slot_bytes, total_tiles, tmem_base);
+                       plan.raw_depth, plan.raw_slot_bytes, M, total_tiles, tmem_base);
   } else if (warp >= EPI_WARP0 && warp < EPI_WARP0 + 4) {
     // ------------------------------------------------------------ epilogue
     const int eq = warp - EPI_WARP0;  // TMEM lane quarter
@@ -800,78 +894,42 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     using act_t = typename T::act_t;
     act_t *yout = reinterpret_cast<act_t *>(a.y);
     const act_t *skip = reinterpret_cast<const act_t *>(a.skip);
+    const int nch = BN / 16;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++it) {
       const TileCoord tc = tile_coord(a, t);
       const PhaseDesc &pd = a.ph[tc.phase];
       const int buf = nbufs == 2 ? (it & 1) : 0;
       const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
-      if (!pwait(a, w_tfull, smem_u32(&tfull_bar[buf]), par)) break;
-      tc_fence_after();
       const int m = tc.m_tile * BM + row;
-      const bool vrow = m < a.M;
+      const bool vrow = m < M;
       const int n = vrow ? m / rows_per_map : 0;
       const int rem = vrow ? m - n * rows_per_map : 0;
       const int i = rem / a.Wrow, j = rem - (rem / a.Wrow) * a.Wrow;
-      const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
       const size_t opix = a.kind == LK_CONVT
                               ? ((size_t)n * a.Hout + (2 * i + pd.oy)) * a.Wout + (2 * j + pd.ox)
                               : (size_t)m;
-      for (int cc = 0; cc < BN / 16; ++cc) {
-        float v[16];
-        tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
-        const int col0 = tc.n_tile * BN + cc * 16;
-        if (!vrow) continue;
-        const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
-        const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
-#pragma unroll
-        for (int e4 = 0; e4 < 4; ++e4) {
-          const float4 b = __ldg(bias4 + e4);
-          const float bb[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            float z = bsc ? v[4 * e4 + e] * bsc[4 * e4 + e] : v[4 * e4 + e];
-            z += bb[e];
-            if (a.relu) z = fmaxf(z, 0.f);
-            v[4 * e4 + e] = z;
-          }
-        }
-        const size_t eoff = opix * a.Cout + col0;
-        if constexpr (PREC == PREC_TF32X3) {
-          if (skip) {
-            const float4 *sp = reinterpret_cast<const float4 *>(skip + eoff);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const float4 s = sp[e];
-              v[4 * e] += s.x;
-              v[4 * e + 1] += s.y;
-              v[4 * e + 2] += s.z;
-              v[4 * e + 3] += s.w;
-            }
-          }
-          float4 *yp = reinterpret_cast<float4 *>(yout + eoff);
-#pragma unroll
-          for (int e = 0; e < 4; ++e) yp[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-        } else {
-          if (skip) {
-            const uint4 *sp = reinterpret_cast<const uint4 *>(skip + eoff);
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              const uint4 s = sp[e];
-              v[8 * e + 0] += bf16_lo(s.x);
-              v[8 * e + 1] += bf16_hi(s.x);
-              v[8 * e + 2] += bf16_lo(s.y);
-              v[8 * e + 3] += bf16_hi(s.y);
-              v[8 * e + 4] += bf16_lo(s.z);
-              v[8 * e + 5] += bf16_hi(s.z);
-              v[8 * e + 6] += bf16_lo(s.w);
-              v[8 * e + 7] += bf16_hi(s.w);
-            }
-          }
-          uint4 *yp = reinterpret_cast<uint4 *>(yout + eoff);
-#pragma unroll
-          for (int e = 0; e < 2; ++e)
-            yp[e] = make_uint4(pack_bf16x2(v[8 * e], v[8 * e + 1]), pack_bf16x2(v[8 * e + 2], v[8 * e + 3]),
-                               pack_bf16x2(v[8 * e + 4], v[8 * e + 5]), pack_bf16x2(v[8 * e + 6], v[8 * e + 7]));
+      const size_t ebase = opix * a.Cout + (size_t)tc.n_tile * BN;
+      // The skip values of the first two 16-column chunks are loaded before
+      // the accumulator is ready (their latency hides behind the tile's
+      // MMAs); later chunks are fetched two ahead while earlier ones are
+      // stored.  Each output element is read (skip) and written by this
+      // thread only, so reading ahead of the in-place store is safe.
+      const bool has_skip = skip != nullptr && vrow;
+      uint4 sk0[4], sk1[4];
+      if (has_skip) {
+        load_skip<PREC>(skip + ebase, sk0);
+        if (nch > 1) load_skip<PREC>(skip + ebase + 16, sk1);
+      }
+      if (!pwait(a, w_tfull, smem_u32(&tfull_bar[buf]), par)) break;
+      tc_fence_after();
+      const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
+      for (int cc = 0; cc < nch; cc += 2) {
+        epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk0, yout + ebase + cc * 16);
+        if (has_skip && cc + 2 < nch) load_skip<PREC>(skip + ebase + (cc + 2) * 16, sk0);
+        if (cc + 1 < nch) {
+          epi_chunk<PREC>(a, taddr, cc + 1, BN, tc.n_tile * BN + (cc + 1) * 16, vrow, has_skip, sk1,
+                          yout + ebase + (cc + 1) * 16);
+          if (has_skip && cc + 3 < nch) load_skip<PREC>(skip + ebase + (cc + 3) * 16, sk1);
         }
       }
       tc_fence_before();
@@ -922,10 +980,19 @@ cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t s
 // ------------------------------------------------------ first-layer input
 // One thread per pixel: 7 coalesced plane loads, log encode of channels 0..2,
 // one 32-byte (fp32) or 16-byte (bf16) store of the 8-channel NHWC pixel.
+// With a pass slot the input pointer, the map count and the encode flag come
+// from device memory, and the kernel also clears the pass's payload.
 template <bool BF16>
 __global__ void nchw7_to_nhwc8_kernel(const float *__restrict__ in, void *__restrict__ out, long long hw, int N,
-                                      int encode, float s) {
+                                      int encode, float s, const PassSlot *slot) {
   const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (slot) {
+    const int cnt = slot->count;
+    N = cnt < 0 ? 0 : (cnt < N ? cnt : N);
+    in = slot->in;
+    encode = (slot->flags & SLOT_ENCODE) ? 1 : 0;
+    if (slot->payload && g < 3ll * N) slot->payload[g] = 0.f;
+  }
   if (g >= hw * N) return;
   const long long n = g / hw, p = g - n * hw;
   const float *src = in + n * 7 * hw + p;
@@ -948,14 +1015,15 @@ __global__ void nchw7_to_nhwc8_kernel(const float *__restrict__ in, void *__rest
 }
 
 cudaError_t launch_nchw7_to_nhwc8(const float *in, void *out, long long hw, int N, bool bf16, bool encode,
-                                  float exposure, cudaStream_t st) {
-  const long long total = hw * N;
+                                  float exposure, cudaStream_t st, const PassSlot *slot) {
+  long long total = hw * N;
+  if (slot && total < 3ll * N) total = 3ll * N;  // payload clear
   if (total == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((total + 255) / 256);
   if (bf16)
-    nchw7_to_nhwc8_kernel<true><<<blocks, 256, 0, st>>>(in, out, hw, N, encode ? 1 : 0, exposure);
+    nchw7_to_nhwc8_kernel<true><<<blocks, 256, 0, st>>>(in, out, hw, N, encode ? 1 : 0, exposure, slot);
   else
-    nchw7_to_nhwc8_kernel<false><<<blocks, 256, 0, st>>>(in, out, hw, N, encode ? 1 : 0, exposure);
+    nchw7_to_nhwc8_kernel<false><<<blocks, 256, 0, st>>>(in, out, hw, N, encode ? 1 : 0, exposure, slot);
   return cudaGetLastError();
 }
 

@@ -5,6 +5,8 @@
 #include <cuda.h>  // CUtensorMap (type only; encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
+#include "pass.cuh"
+
 namespace drc {
 
 // How a GEMM row maps to pixels and how K maps to (tap, channel).
@@ -56,6 +58,8 @@ struct ConvArgs {
   int Hrow, Wrow;        // row grid per map
   int Hout, Wout, Cout;  // output geometry (Cout = stored channels)
   int M;                 // N * Hrow * Wrow
+  const int *count;      // nullable: maps of this launch in device memory (0..N); M, m_tiles then
+                         // describe the N-map maximum the launch was sized for
   int BN, n_tiles, m_tiles, num_phases;
   int phase_order[4];    // heaviest phase first
   PhaseDesc ph[4];
@@ -99,7 +103,10 @@ cudaError_t launch_pack(const PackArgs &p, int prec, cudaStream_t st);
 
 // First-layer input: fp32 NCHW [N][7][H][W] -> NHWC with 8 channels (the 8th
 // zero), fp32 or bf16, with the optional log1p(s L) of channels 0..2.
+// slot (nullable): take the input, the count (<= N) and the encode flag from
+// device memory, and clear the slot's payload.
 cudaError_t launch_nchw7_to_nhwc8(const float *in, void *out, long long pixels_per_map, int N,
-                                  bool bf16, bool encode, float exposure, cudaStream_t st);
+                                  bool bf16, bool encode, float exposure, cudaStream_t st,
+                                  const PassSlot *slot = nullptr);
 
 }  // namespace drc

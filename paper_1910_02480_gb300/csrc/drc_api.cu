@@ -47,6 +47,7 @@ struct drc_ctx {
   int prec = PREC_TF32X3;
   size_t n_floats = 0;
   std::vector<Layer> layers;  // conv_1..conv_S, convT_S..convT_2, head
+  std::vector<int> modes;     // per layer: A-operand path chosen by drc_autotune (-1 = default)
   float *d_wraw = nullptr;
   uint8_t *d_pack = nullptr, *d_pack_lo = nullptr;
   float *d_bscale = nullptr;
@@ -58,6 +59,7 @@ struct drc_ctx {
   int *d_status = nullptr;
   unsigned long long *d_prof = nullptr;  // wait-time counters (DRC_PROFILE_WAITS)
   bool weights_set = false;
+  unsigned long long weights_version = 0;  // bumped by every drc_set_weights (plans repack on change)
   unsigned long long timeout_ns = 0;
   Tracer tracer;
   std::string err;
@@ -109,7 +111,8 @@ EncodeTiledFn encode_tiled() {
 // rows of every tile to be a box of the activation tensor (whole output rows
 // of whole maps) and a K block to stay inside one tap; everything else uses
 // the cp.async gather.
-void plan_operand(int prec, ConvArgs &a) {
+// force_mode >= 0 asks for that mode where the layer allows it (autotuner).
+void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
   a.prod_mode = PROD_CPASYNC;
   const int bke = KROW_BYTES / (prec == PREC_TF32X3 ? 4 : (prec == PREC_BF16 ? 2 : 1));  // K elements per block
   const int Wr = a.Wrow, Hr = a.Hrow;
@@ -134,6 +137,11 @@ void plan_operand(int prec, ConvArgs &a) {
                    4, const_cast<void *>(a.x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return;
+  if (force_mode == PROD_CPASYNC) return;
+  if (prec == PREC_TF32X3 && force_mode == PROD_TMA_CONVERT) {
+    a.prod_mode = PROD_TMA_CONVERT;
+    return;
+  }
   if (prec == PREC_BF16)
     a.prod_mode = PROD_TMA_DIRECT;
   else if (prec == PREC_TF32X3 && a.BN <= 128 && std::getenv("DRC_NO_TMEM_A") == nullptr)
@@ -189,6 +197,28 @@ void convT_phase(PhaseDesc &pd, int oy, int ox, int Cin, int bke) {
   pd.num_kb = ceil_div((long long)pd.ntaps * Cin, bke);
 }
 
+// Offsets of every layer's packed B tiles ([phase][n_tile][k_block][BN rows
+// x 128 B]) in one buffer; returns its size.
+size_t layout_packs(std::vector<Layer> &Ls) {
+  size_t pack = 0;
+  for (Layer &L : Ls) {
+    L.pack_off = pack;
+    size_t bytes = 0;
+    for (int p = 0; p < L.num_phases; ++p) {
+      L.ph[p].b_off = (long long)(pack + bytes);
+      bytes += (size_t)L.n_tiles * L.ph[p].num_kb * L.BN * KROW_BYTES;
+    }
+    L.pack_bytes = bytes;
+    pack += (bytes + 255) & ~(size_t)255;
+  }
+  return pack;
+}
+
+void set_bn(Layer &L, int BN) {
+  L.BN = BN;
+  L.n_tiles = L.Cout / BN;
+}
+
 // Lay out every layer's GEMM(s) and the packed operand buffer.
 void plan_layers(drc_ctx *c) {
   const drc_config &g = c->cfg;
@@ -198,16 +228,8 @@ void plan_layers(drc_ctx *c) {
   wd[0] = g.in_channels;
   for (int s = 1; s <= S; ++s) wd[s] = g.widths[s - 1];
   c->layers.clear();
-  size_t off = 0, pack = 0;
+  size_t off = 0;
   auto finish = [&](Layer &L) {
-    L.pack_off = pack;
-    size_t bytes = 0;
-    for (int p = 0; p < L.num_phases; ++p) {
-      L.ph[p].b_off = (long long)(pack + bytes);
-      bytes += (size_t)L.n_tiles * L.ph[p].num_kb * L.BN * KROW_BYTES;
-    }
-    L.pack_bytes = bytes;
-    pack += bytes;
     // heaviest phase first
     for (int p = 0; p < 4; ++p) L.phase_order[p] = p < L.num_phases ? p : 0;
     for (int a = 0; a < L.num_phases; ++a)
@@ -231,8 +253,7 @@ void plan_layers(drc_ctx *c) {
     off += 9ull * L.Cin_raw * L.Cout;
     L.b_off = off;
     off += L.Cout;
-    L.BN = pick_bn(L.Cout);
-    L.n_tiles = L.Cout / L.BN;
+    set_bn(L, pick_bn(L.Cout));
     L.num_phases = 1;
     PhaseDesc &pd = L.ph[0];
     pd.ntaps = 9;
@@ -259,14 +280,13 @@ void plan_layers(drc_ctx *c) {
     } else {
       L.kind = LK_CONVT;
       snprintf(L.name, sizeof L.name, "convT d%d", s);
-      L.BN = pick_bn(L.Cout);
-      L.n_tiles = L.Cout / L.BN;
+      set_bn(L, pick_bn(L.Cout));
       L.num_phases = 4;
       for (int p = 0; p < 4; ++p) convT_phase(L.ph[p], p >> 1, p & 1, L.Cin, bke);
     }
     finish(L);
   }
-  c->pack_total = pack;
+  c->pack_total = layout_packs(c->layers);
 }
 
 drc_status check_config(const drc_config *g, drc_ctx *c) {
@@ -322,8 +342,8 @@ drc_status check_dev(drc_ctx *c, const void *p, const char *name, bool nullable)
   return DRC_OK;
 }
 
-drc_status pack_all(drc_ctx *c, cudaStream_t st) {
-  for (const Layer &L : c->layers) {
+drc_status pack_layers(drc_ctx *c, const std::vector<Layer> &Ls, uint8_t *B, uint8_t *B_lo, cudaStream_t st) {
+  for (const Layer &L : Ls) {
     if (L.kind == LK_HEAD) continue;
     PackArgs p;
     memset(&p, 0, sizeof p);
@@ -336,8 +356,8 @@ drc_status pack_all(drc_ctx *c, cudaStream_t st) {
     p.n_tiles = L.n_tiles;
     p.num_phases = L.num_phases;
     for (int i = 0; i < 4; ++i) p.ph[i] = L.ph[i];
-    p.B = c->d_pack;
-    p.B_lo = c->d_pack_lo;
+    p.B = B;
+    p.B_lo = B_lo;
     p.bscale = c->d_bscale;
     p.total_chunks = (long long)(L.pack_bytes / 16);
     cudaError_t e;
@@ -346,6 +366,8 @@ drc_status pack_all(drc_ctx *c, cudaStream_t st) {
   }
   return DRC_OK;
 }
+
+drc_status pack_all(drc_ctx *c, cudaStream_t st) { return pack_layers(c, c->layers, c->d_pack, c->d_pack_lo, st); }
 
 size_t act_bytes_for(const drc_ctx *c, long long N, int H, int W) {
   // the first layer's NHWC input (8 channels), then e_1 .. e_S
@@ -367,11 +389,11 @@ drc_status ensure_act(drc_ctx *c, long long N, int H, int W) {
   return DRC_OK;
 }
 
-void fill_common(const drc_ctx *c, const Layer &L, ConvArgs &a) {
+void fill_common(const drc_ctx *c, const Layer &L, const uint8_t *B, const uint8_t *B_lo, ConvArgs &a) {
   memset(&a, 0, sizeof a);
   a.kind = L.kind;
-  a.B = c->d_pack;
-  a.B_lo = c->d_pack_lo;
+  a.B = B;
+  a.B_lo = B_lo;
   a.bias = c->d_wraw + L.b_off;
   a.BN = L.BN;
   a.n_tiles = L.n_tiles;
@@ -386,6 +408,274 @@ void fill_common(const drc_ctx *c, const Layer &L, ConvArgs &a) {
     if ((1 << sh) == L.Cin) a.cin_shift = sh;
   a.status = c->d_status;
   a.timeout_ns = c->timeout_ns;
+}
+
+// Activation buffers and geometry of one launch sequence of the network over
+// N maps of H x W (for a plan, N is the class's maximum and the real count is
+// read from device memory).
+struct Chain {
+  int N = 0, H = 0, W = 0;
+  uint8_t *in8 = nullptr;       // first layer's NHWC8 input
+  std::vector<uint8_t *> act;   // act[s] = e_s, s = 1..S (decoder outputs overwrite in place)
+  const int *count = nullptr;   // nullable: device map count (<= N)
+  const PassSlot *slot = nullptr;
+};
+
+void carve_chain(const drc_ctx *c, void *base, int N, int H, int W, Chain &ch) {
+  const int S = c->cfg.num_stages;
+  ch.N = N;
+  ch.H = H;
+  ch.W = W;
+  ch.in8 = static_cast<uint8_t *>(base);
+  ch.act.assign(S + 1, nullptr);
+  size_t off = (((size_t)N * H * W * 8 * elem_act(c->prec)) + 255) & ~(size_t)255;
+  for (int s2 = 1; s2 <= S; ++s2) {
+    ch.act[s2] = static_cast<uint8_t *>(base) + off;
+    off += (((size_t)N * (H >> s2) * (W >> s2) * c->cfg.widths[s2 - 1] * elem_act(c->prec)) + 255) & ~(size_t)255;
+  }
+}
+
+// ConvArgs of tensor-core layer li (encoder conv or decoder convT) of a chain.
+void conv_args_for(const drc_ctx *c, const Layer &L, size_t li, const Chain &ch, const uint8_t *B,
+                   const uint8_t *B_lo, int force_mode, ConvArgs &a) {
+  const int S = c->cfg.num_stages;
+  const int H = ch.H, W = ch.W;
+  fill_common(c, L, B, B_lo, a);
+  a.N = ch.N;
+  if (L.kind == LK_CONV) {
+    const int s2 = (int)li + 1;  // encoder stage
+    a.x = s2 == 1 ? static_cast<const void *>(ch.in8) : ch.act[s2 - 1];
+    a.y = ch.act[s2];
+    a.Hin = H >> (s2 - 1);
+    a.Win = W >> (s2 - 1);
+    a.Cin = L.Cin;
+    a.Hrow = a.Hout = H >> s2;
+    a.Wrow = a.Wout = W >> s2;
+    a.Cout = L.Cout;
+  } else {
+    const int s2 = S - ((int)li - S);  // decoder stage S..2
+    a.x = ch.act[s2];
+    a.y = ch.act[s2 - 1];
+    a.skip = ch.act[s2 - 1];
+    a.Hin = a.Hrow = H >> s2;
+    a.Win = a.Wrow = W >> s2;
+    a.Cin = L.Cin;
+    a.Hout = H >> (s2 - 1);
+    a.Wout = W >> (s2 - 1);
+    a.Cout = L.Cout;
+  }
+  a.relu = 1;
+  a.M = (int)((long long)ch.N * a.Hrow * a.Wrow);
+  a.m_tiles = ceil_div(a.M, BM);
+  a.count = ch.count;
+  plan_operand(c->prec, a, force_mode);
+}
+
+// Enqueue the whole network over one chain: input staging, S encoder convs,
+// S-1 decoder convTs, the head.  tr: launch tracer (nullptr while capturing a
+// graph); prof: wait-time counters per layer, or nullptr.
+drc_status run_chain(drc_ctx *c, const std::vector<Layer> &layers, const uint8_t *B, const uint8_t *B_lo,
+                     const std::vector<int> *modes, const Chain &ch, const float *in, float *out, float *payload,
+                     unsigned flags, cudaStream_t st, Tracer *tr, unsigned long long *prof) {
+  cudaError_t e;
+  DRC_TRACED(tr, "stage input", st,
+             e = launch_nchw7_to_nhwc8(in, ch.in8, (long long)ch.H * ch.W, ch.N, c->prec != PREC_TF32X3,
+                                       (flags & DRC_F_ENCODE_INPUT) != 0, c->cfg.exposure, st, ch.slot));
+  if (e != cudaSuccess) return cuda_fail(c, e, "input staging");
+  const int debug_stall = (flags & DRC_F_DEBUG_STALL) ? 1 : 0;
+  for (size_t li = 0; li < layers.size(); ++li) {
+    const Layer &L = layers[li];
+    if (L.kind == LK_HEAD) {  // 3-channel transposed conv + decode + payload (head.cu)
+      HeadArgs h;
+      memset(&h, 0, sizeof h);
+      h.x = ch.act[1];
+      h.out = out;
+      h.payload = payload;
+      h.w = c->d_wraw + L.w_off;
+      h.bias = c->d_wraw + L.b_off;
+      h.N = ch.N;
+      h.Hh = ch.H >> 1;
+      h.Wh = ch.W >> 1;
+      h.C = L.Cin;
+      h.relu = c->cfg.out_relu ? 1 : 0;
+      h.decode = (flags & DRC_F_DECODE_OUTPUT) ? 1 : 0;
+      h.inv_exposure = 1.0f / c->cfg.exposure;
+      h.slot = ch.slot;
+      if (payload || ch.slot) {
+        const double pi = 3.14159265358979323846;
+        for (int i = 0; i < ch.H; ++i) {
+          const double t0 = i * pi / (2.0 * ch.H), t1 = (i + 1) * pi / (2.0 * ch.H);
+          h.band[i] = (float)((std::sin(t1) * std::sin(t1) - std::sin(t0) * std::sin(t0)) / ch.W);
+        }
+      }
+      DRC_TRACED(tr, L.name, st, e = launch_head(h, c->prec != PREC_TF32X3, st));
+      if (e != cudaSuccess) return cuda_fail(c, e, "head launch");
+      continue;
+    }
+    ConvArgs a;
+    conv_args_for(c, L, li, ch, B, B_lo, modes ? (*modes)[li] : -1, a);
+    a.debug_stall = debug_stall && li == 0;
+    if (prof) a.prof = prof + li * PROF_SLOTS;
+    DRC_TRACED(tr, L.name, st, e = launch_conv(a, c->prec, c->num_sms, st));
+    if (e != cudaSuccess) return cuda_fail(c, e, "layer launch");
+  }
+  return DRC_OK;
+}
+
+// ------------------------------------------------------------------ plans
+
+constexpr int kMaxClasses = 8;
+
+struct SlotUpdate {
+  int n;
+  unsigned flags;
+  int max_maps[kMaxClasses];
+  const float *in[kMaxClasses];
+  float *out[kMaxClasses];
+  float *payload[kMaxClasses];
+};
+
+// Write this pass's counts (from the caller's device array) and buffers into
+// the plan's slots; a count outside 0..max_maps is clamped and latched as
+// DRC_ERR_INVALID_ARG in the context status.
+__global__ void set_slots_kernel(SlotUpdate u, const int *counts, PassSlot *slots, int *status) {
+  const int k = threadIdx.x;
+  if (k >= u.n) return;
+  int cnt = counts[k];
+  if (cnt < 0 || cnt > u.max_maps[k]) {
+    atomicCAS(status, 0, (int)DRC_ERR_INVALID_ARG);
+    cnt = cnt < 0 ? 0 : u.max_maps[k];
+  }
+  slots[k].count = cnt;
+  slots[k].flags = u.flags;
+  slots[k].in = u.in[k];
+  slots[k].out = u.out[k];
+  slots[k].payload = u.payload[k];
+}
+
+// Tile-width candidates of a layer: the default, and half of it while the
+// half stays a multiple of 16.
+std::vector<int> bn_candidates(const Layer &L) {
+  std::vector<int> v{L.BN};
+  if (L.BN % 32 == 0 && L.BN / 2 >= 32) v.push_back(L.BN / 2);
+  return v;
+}
+
+}  // namespace
+
+struct drc_plan {
+  drc_ctx *ctx = nullptr;
+  unsigned flags = 0;
+  std::vector<drc_size_class> cls;
+  std::vector<std::vector<Layer>> layers;  // per class: the context's layers with the chosen tile widths
+  std::vector<std::vector<int>> modes;     // per class and layer: A-operand path (-1 = default)
+  std::vector<uint8_t *> pack, pack_lo;    // per class
+  std::vector<Chain> chains;
+  void *d_act = nullptr;
+  PassSlot *d_slots = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long weights_version = 0;
+  int kernels_per_launch = 0;
+};
+
+namespace {
+
+void plan_free(drc_plan *p) {
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  for (uint8_t *b : p->pack) cudaFree(b);
+  for (uint8_t *b : p->pack_lo) cudaFree(b);
+  cudaFree(p->d_act);
+  cudaFree(p->d_slots);
+  cudaGetLastError();
+  delete p;
+}
+
+drc_status plan_pack(drc_plan *p, cudaStream_t st) {
+  drc_ctx *c = p->ctx;
+  for (size_t k = 0; k < p->cls.size(); ++k) {
+    drc_status s = pack_layers(c, p->layers[k], p->pack[k], p->pack_lo[k], st);
+    if (s != DRC_OK) return s;
+  }
+  p->weights_version = c->weights_version;
+  return DRC_OK;
+}
+
+// Time one conv layer of a chain (min of 3 launches after one warm-up).
+drc_status time_layer(drc_ctx *c, const Layer &L, size_t li, const Chain &ch, const uint8_t *B, const uint8_t *B_lo,
+                      int mode, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float *best_ms) {
+  ConvArgs a;
+  conv_args_for(c, L, li, ch, B, B_lo, mode, a);
+  a.count = nullptr;
+  float best = 1e30f;
+  for (int r = 0; r < 4; ++r) {
+    cudaEventRecord(e0, st);
+    cudaError_t e = launch_conv(a, c->prec, c->num_sms, st);
+    cudaEventRecord(e1, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "autotune launch");
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return cuda_fail(c, e, "autotune sync");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0 && ms < best) best = ms;
+  }
+  *best_ms = best;
+  return DRC_OK;
+}
+
+// Pick each conv layer's tile width (and, split-tf32, the A-operand path) by
+// timing the candidates on a chain's full-size buffers.
+drc_status autotune_layers(drc_ctx *c, std::vector<Layer> &Ls, std::vector<int> &modes, const Chain &ch,
+                           cudaStream_t st) {
+  size_t scratch = 0;
+  for (const Layer &L : Ls) {
+    if (L.kind == LK_HEAD) continue;
+    std::vector<Layer> one{L};
+    for (int bn : bn_candidates(L)) {
+      set_bn(one[0], bn);
+      const size_t b = layout_packs(one);
+      if (b > scratch) scratch = b;
+    }
+  }
+  uint8_t *B = nullptr, *B_lo = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&B, scratch);
+  if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&B_lo, scratch);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  drc_status s = e == cudaSuccess ? DRC_OK : cuda_fail(c, e, "autotune scratch");
+  for (size_t li = 0; s == DRC_OK && li < Ls.size(); ++li) {
+    if (Ls[li].kind == LK_HEAD) continue;
+    float best = 1e30f;
+    int best_bn = Ls[li].BN, best_mode = -1;
+    for (int bn : bn_candidates(Ls[li])) {
+      std::vector<Layer> one{Ls[li]};
+      set_bn(one[0], bn);
+      layout_packs(one);
+      if ((s = pack_layers(c, one, B, B_lo, st)) != DRC_OK) break;
+      std::vector<int> mode_list{-1};
+      if (c->prec == PREC_TF32X3 && bn <= 128) mode_list.push_back(PROD_TMA_CONVERT);
+      for (int mode : mode_list) {
+        float ms = 0.f;
+        if ((s = time_layer(c, one[0], li, ch, B, B_lo, mode, st, e0, e1, &ms)) != DRC_OK) break;
+        if (ms < best) {
+          best = ms;
+          best_bn = bn;
+          best_mode = mode;
+        }
+      }
+      if (s != DRC_OK) break;
+    }
+    set_bn(Ls[li], best_bn);
+    modes[li] = best_mode;
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(B);
+  cudaFree(B_lo);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGetLastError();
+  return s;
 }
 
 }  // namespace
@@ -424,6 +714,7 @@ drc_status drc_create(const drc_config *cfg, const float *weights_host, size_t n
     return DRC_ERR_UNSUPPORTED;  // built for sm_103a only
   }
   plan_layers(c);
+  c->modes.assign(c->layers.size(), -1);
   e = cudaMalloc(&c->d_wraw, c->n_floats * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_pack, c->pack_total);
   if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&c->d_pack_lo, c->pack_total);
@@ -467,7 +758,10 @@ drc_status drc_set_weights(drc_ctx *c, const float *weights, int weights_on_devi
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "weight upload");
   drc_status s = pack_all(c, st);
-  if (s == DRC_OK) c->weights_set = true;
+  if (s == DRC_OK) {
+    c->weights_set = true;
+    ++c->weights_version;
+  }
   return s;
 }
 
@@ -508,27 +802,12 @@ drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, 
   if ((s = ensure_act(c, N, H, W)) != DRC_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   cudaError_t e;
-
-  // activation buffers e_1..e_S (decoder outputs overwrite them in place)
-  std::vector<uint8_t *> act(S + 1, nullptr);
-  uint8_t *in8 = static_cast<uint8_t *>(c->d_act);  // first layer's NHWC input
-  {
-    size_t off = (((size_t)N * H * W * 8 * elem_act(c->prec)) + 255) & ~(size_t)255;
-    for (int s2 = 1; s2 <= S; ++s2) {
-      act[s2] = static_cast<uint8_t *>(c->d_act) + off;
-      off += (((size_t)N * (H >> s2) * (W >> s2) * c->cfg.widths[s2 - 1] * elem_act(c->prec)) + 255) &
-             ~(size_t)255;
-    }
-  }
+  Chain ch;
+  carve_chain(c, c->d_act, N, H, W, ch);
   if (payload) {
     e = cudaMemsetAsync(payload, 0, (size_t)N * 3 * sizeof(float), st);
     if (e != cudaSuccess) return cuda_fail(c, e, "payload clear");
   }
-  const int debug_stall = (flags & DRC_F_DEBUG_STALL) ? 1 : 0;
-  DRC_TRACED(&c->tracer, "stage input", st,
-             e = launch_nchw7_to_nhwc8(in, in8, (long long)H * W, N, c->prec != PREC_TF32X3,
-                                       (flags & DRC_F_ENCODE_INPUT) != 0, c->cfg.exposure, st));
-  if (e != cudaSuccess) return cuda_fail(c, e, "input staging");
   // Diagnostic: with DRC_PROFILE_WAITS set in the environment every conv
   // launch records how long each warp role waited, printed to stderr per
   // layer after the call (synchronising).  Off by default.
@@ -538,68 +817,9 @@ drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, 
     if (!c->d_prof && cudaMalloc(&c->d_prof, pb) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "prof");
     cudaMemsetAsync(c->d_prof, 0, pb, st);
   }
-  for (size_t li = 0; li < c->layers.size(); ++li) {
-    const Layer &L = c->layers[li];
-    ConvArgs a;
-    fill_common(c, L, a);
-    a.debug_stall = debug_stall && li == 0;
-    a.N = N;
-    if (L.kind == LK_CONV) {
-      const int s2 = (int)li + 1;  // encoder stage
-      a.x = s2 == 1 ? static_cast<const void *>(in8) : act[s2 - 1];
-      a.y = act[s2];
-      a.Hin = H >> (s2 - 1);
-      a.Win = W >> (s2 - 1);
-      a.Cin = L.Cin;
-      a.Hrow = a.Hout = H >> s2;
-      a.Wrow = a.Wout = W >> s2;
-      a.Cout = L.Cout;
-      a.relu = 1;
-    } else if (L.kind == LK_CONVT) {
-      const int s2 = S - ((int)li - S);  // decoder stage S..2
-      a.x = act[s2];
-      a.y = act[s2 - 1];
-      a.skip = act[s2 - 1];
-      a.Hin = a.Hrow = H >> s2;
-      a.Win = a.Wrow = W >> s2;
-      a.Cin = L.Cin;
-      a.Hout = H >> (s2 - 1);
-      a.Wout = W >> (s2 - 1);
-      a.Cout = L.Cout;
-      a.relu = 1;
-    } else {  // head: 3-channel transposed conv + decode + payload (head.cu)
-      HeadArgs h;
-      memset(&h, 0, sizeof h);
-      h.x = act[1];
-      h.out = out;
-      h.payload = payload;
-      h.w = c->d_wraw + L.w_off;
-      h.bias = c->d_wraw + L.b_off;
-      h.N = N;
-      h.Hh = H >> 1;
-      h.Wh = W >> 1;
-      h.C = L.Cin;
-      h.relu = c->cfg.out_relu ? 1 : 0;
-      h.decode = (flags & DRC_F_DECODE_OUTPUT) ? 1 : 0;
-      h.inv_exposure = 1.0f / c->cfg.exposure;
-      if (payload) {
-        const double pi = 3.14159265358979323846;
-        for (int i = 0; i < H; ++i) {
-          const double t0 = i * pi / (2.0 * H), t1 = (i + 1) * pi / (2.0 * H);
-          h.band[i] = (float)((std::sin(t1) * std::sin(t1) - std::sin(t0) * std::sin(t0)) / W);
-        }
-      }
-      DRC_TRACED(&c->tracer, L.name, st, e = launch_head(h, c->prec != PREC_TF32X3, st));
-      if (e != cudaSuccess) return cuda_fail(c, e, "head launch");
-      continue;
-    }
-    a.M = (int)((long long)N * a.Hrow * a.Wrow);
-    a.m_tiles = ceil_div(a.M, BM);
-    plan_operand(c->prec, a);
-    if (prof) a.prof = c->d_prof + li * PROF_SLOTS;
-    DRC_TRACED(&c->tracer, L.name, st, e = launch_conv(a, c->prec, c->num_sms, st));
-    if (e != cudaSuccess) return cuda_fail(c, e, "layer launch");
-  }
+  s = run_chain(c, c->layers, c->d_pack, c->d_pack_lo, &c->modes, ch, in, out, payload, flags, st, &c->tracer,
+                prof ? c->d_prof : nullptr);
+  if (s != DRC_OK) return s;
   if (prof) {
     std::vector<unsigned long long> h(c->layers.size() * PROF_SLOTS);
     cudaStreamSynchronize(st);
@@ -730,12 +950,204 @@ drc_status drc_get_status(drc_ctx *c, void *stream) {
   if (e != cudaSuccess) return cuda_fail(c, e, "status read");
   if (v != 0) {
     cudaMemset(c->d_status, 0, sizeof(int));
-    return fail(c, (drc_status)v, "device-side error %d latched (a bounded wait ran out)", v);
+    return fail(c, (drc_status)v, "device-side error %d latched (%s)", v,
+                v == DRC_ERR_TIMEOUT ? "a bounded wait ran out" : "a plan pass count was out of range");
   }
   return DRC_OK;
 }
 
 const char *drc_last_error(drc_ctx *c) { return c ? c->err.c_str() : "NULL context"; }
+
+drc_status drc_autotune(drc_ctx *c, int N, int H, int W) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  const int S = c->cfg.num_stages;
+  if (N < 1 || H < (1 << S) || W < (1 << S) || H % (1 << S) || W % (1 << S) ||
+      (long long)N * H * W * 7 >= (1ll << 31))
+    return fail(c, DRC_ERR_INVALID_ARG, "autotune shape N=%d H=%d W=%d is not a valid denoise batch", N, H, W);
+  if (!c->weights_set) return fail(c, DRC_ERR_INVALID_ARG, "weights were never set");
+  drc_status s = ensure_act(c, N, H, W);
+  if (s != DRC_OK) return s;
+  cudaStream_t st = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(c, e, "autotune stream");
+  Chain ch;
+  carve_chain(c, c->d_act, N, H, W, ch);
+  std::vector<Layer> Ls = c->layers;
+  std::vector<int> modes = c->modes;
+  s = autotune_layers(c, Ls, modes, ch, st);
+  if (s == DRC_OK) {
+    const size_t need = layout_packs(Ls);
+    if (need > c->pack_total) {  // a narrower tile can pad the packed image differently
+      uint8_t *B = nullptr, *B_lo = nullptr;
+      e = cudaMalloc(&B, need);
+      if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&B_lo, need);
+      if (e != cudaSuccess) {
+        cudaFree(B);
+        s = cuda_fail(c, e, "autotune operands");
+      } else {
+        cudaStreamSynchronize(st);
+        cudaFree(c->d_pack);
+        cudaFree(c->d_pack_lo);
+        c->d_pack = B;
+        c->d_pack_lo = B_lo;
+        c->pack_total = need;
+      }
+    }
+  }
+  if (s == DRC_OK) {
+    c->layers = Ls;
+    c->modes = modes;
+    s = pack_all(c, st);
+  }
+  if (s == DRC_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) s = cuda_fail(c, e, "autotune");
+  cudaStreamDestroy(st);
+  return s;
+}
+
+drc_status drc_describe_layer(drc_ctx *c, int layer, int *bn, int *a_path) {
+  if (!c || layer < 0 || layer >= (int)c->layers.size()) return DRC_ERR_INVALID_ARG;
+  const Layer &L = c->layers[layer];
+  if (bn) *bn = L.kind == LK_HEAD ? 0 : L.BN;
+  if (a_path) *a_path = c->modes[layer];
+  return DRC_OK;
+}
+
+drc_status drc_plan_create(drc_ctx *c, const drc_size_class *classes, int n_classes, unsigned flags,
+                           drc_plan **out) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!out) return fail(c, DRC_ERR_INVALID_ARG, "plan output pointer is NULL");
+  *out = nullptr;
+  if (!classes || n_classes < 1 || n_classes > kMaxClasses)
+    return fail(c, DRC_ERR_INVALID_ARG, "need 1..%d size classes", kMaxClasses);
+  if (flags & ~DRC_PLAN_AUTOTUNE) return fail(c, DRC_ERR_INVALID_ARG, "unknown plan flags 0x%x", flags);
+  if (!c->weights_set) return fail(c, DRC_ERR_INVALID_ARG, "weights were never set");
+  const int S = c->cfg.num_stages;
+  for (int k = 0; k < n_classes; ++k) {
+    const drc_size_class &q = classes[k];
+    if (q.H < (1 << S) || q.W < (1 << S) || q.H % (1 << S) || q.W % (1 << S) || q.H > 256)
+      return fail(c, DRC_ERR_INVALID_ARG, "class %d: H, W must be multiples of 2^S = %d, H <= 256", k, 1 << S);
+    if (q.max_maps < 1 || (long long)q.max_maps * q.H * q.W * 7 >= (1ll << 31))
+      return fail(c, DRC_ERR_INVALID_ARG, "class %d: max_maps must be >= 1 and max_maps*7*H*W < 2^31", k);
+  }
+  drc_plan *p = new (std::nothrow) drc_plan();
+  if (!p) return fail(c, DRC_ERR_OOM, "plan");
+  p->ctx = c;
+  p->flags = flags;
+  p->cls.assign(classes, classes + n_classes);
+  size_t act_total = 0;
+  std::vector<size_t> act_off(n_classes);
+  for (int k = 0; k < n_classes; ++k) {
+    act_off[k] = act_total;
+    act_total += (act_bytes_for(c, classes[k].max_maps, classes[k].H, classes[k].W) + 255) & ~(size_t)255;
+  }
+  cudaError_t e = cudaMalloc(&p->d_act, act_total);
+  if (e == cudaSuccess) e = cudaMemset(p->d_act, 0, act_total);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_slots, n_classes * sizeof(PassSlot));
+  if (e == cudaSuccess) e = cudaMemset(p->d_slots, 0, n_classes * sizeof(PassSlot));
+  if (e != cudaSuccess) {
+    drc_status s = cuda_fail(c, e, "plan buffers");
+    plan_free(p);
+    return s;
+  }
+  p->chains.resize(n_classes);
+  p->layers.assign(n_classes, c->layers);
+  p->modes.assign(n_classes, c->modes);
+  p->pack.assign(n_classes, nullptr);
+  p->pack_lo.assign(n_classes, nullptr);
+  cudaStream_t cs = nullptr;
+  drc_status s = DRC_OK;
+  if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess) s = cuda_fail(c, e, "plan stream");
+  for (int k = 0; s == DRC_OK && k < n_classes; ++k) {
+    carve_chain(c, static_cast<char *>(p->d_act) + act_off[k], classes[k].max_maps, classes[k].H, classes[k].W,
+                p->chains[k]);
+    if (flags & DRC_PLAN_AUTOTUNE) s = autotune_layers(c, p->layers[k], p->modes[k], p->chains[k], cs);
+    if (s != DRC_OK) break;
+    const size_t bytes = layout_packs(p->layers[k]);
+    e = cudaMalloc(&p->pack[k], bytes);
+    if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&p->pack_lo[k], bytes);
+    if (e != cudaSuccess) s = cuda_fail(c, e, "plan operands");
+  }
+  if (s == DRC_OK) s = plan_pack(p, cs);
+  if (s == DRC_OK && (e = cudaStreamSynchronize(cs)) != cudaSuccess) s = cuda_fail(c, e, "plan packing");
+  // capture the launch sequence of every class into one graph; the kernels
+  // read each pass's count and buffers from the plan's slots
+  if (s == DRC_OK && (e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+    s = cuda_fail(c, e, "begin capture");
+  if (s == DRC_OK) {
+    drc_status cap = DRC_OK;
+    for (int k = 0; cap == DRC_OK && k < n_classes; ++k) {
+      p->chains[k].count = &p->d_slots[k].count;
+      p->chains[k].slot = &p->d_slots[k];
+      cap = run_chain(c, p->layers[k], p->pack[k], p->pack_lo[k], &p->modes[k], p->chains[k], nullptr, nullptr,
+                      nullptr, 0, cs, nullptr, nullptr);
+      p->kernels_per_launch += 1 + (int)p->layers[k].size();
+    }
+    e = cudaStreamEndCapture(cs, &p->graph);
+    if (cap != DRC_OK) s = cap;
+    else if (e != cudaSuccess) s = cuda_fail(c, e, "end capture");
+  }
+  if (s == DRC_OK && (e = cudaGraphInstantiate(&p->exec, p->graph, 0)) != cudaSuccess)
+    s = cuda_fail(c, e, "graph instantiate");
+  if (cs) cudaStreamDestroy(cs);
+  if (s != DRC_OK) {
+    plan_free(p);
+    return s;
+  }
+  *out = p;
+  return DRC_OK;
+}
+
+drc_status drc_plan_launch(drc_plan *p, const int *counts, const float *const *in, float *const *out,
+                           float *const *payload, unsigned flags, void *stream) {
+  if (!p) return DRC_ERR_INVALID_ARG;
+  drc_ctx *c = p->ctx;
+  c->err.clear();
+  const unsigned known = DRC_F_ENCODE_INPUT | DRC_F_DECODE_OUTPUT;
+  if (flags & ~known) return fail(c, DRC_ERR_INVALID_ARG, "unknown flags 0x%x", flags & ~known);
+  if (!in || !out) return fail(c, DRC_ERR_INVALID_ARG, "in and out arrays are required");
+  drc_status s;
+  if ((s = check_dev(c, counts, "counts", false)) != DRC_OK) return s;
+  SlotUpdate u;
+  memset(&u, 0, sizeof u);
+  u.n = (int)p->cls.size();
+  u.flags = flags;
+  for (int k = 0; k < u.n; ++k) {
+    if ((s = check_dev(c, in[k], "in[k]", false)) != DRC_OK) return s;
+    if ((s = check_dev(c, out[k], "out[k]", false)) != DRC_OK) return s;
+    if (payload && (s = check_dev(c, payload[k], "payload[k]", true)) != DRC_OK) return s;
+    u.max_maps[k] = p->cls[k].max_maps;
+    u.in[k] = in[k];
+    u.out[k] = out[k];
+    u.payload[k] = payload ? payload[k] : nullptr;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (p->weights_version != c->weights_version && (s = plan_pack(p, st)) != DRC_OK) return s;
+  cudaError_t e;
+  DRC_TRACED(&c->tracer, "plan slots", st,
+             (set_slots_kernel<<<1, 32, 0, st>>>(u, counts, p->d_slots, c->d_status), e = cudaGetLastError()));
+  if (e != cudaSuccess) return cuda_fail(c, e, "plan slots");
+  DRC_TRACED(&c->tracer, "plan graph", st, e = cudaGraphLaunch(p->exec, st));
+  if (e != cudaSuccess) return cuda_fail(c, e, "graph launch");
+  c->tracer.add_launches(p->kernels_per_launch - 1);  // the graph's kernels (one counted above)
+  return DRC_OK;
+}
+
+drc_status drc_plan_describe(drc_plan *p, int k, int layer, int *bn, int *a_path) {
+  if (!p || k < 0 || k >= (int)p->cls.size() || layer < 0 || layer >= (int)p->layers[k].size())
+    return DRC_ERR_INVALID_ARG;
+  const Layer &L = p->layers[k][layer];
+  if (bn) *bn = L.kind == LK_HEAD ? 0 : L.BN;
+  if (a_path) *a_path = p->modes[k][layer];
+  return DRC_OK;
+}
+
+drc_status drc_plan_destroy(drc_plan *p) {
+  if (!p) return DRC_ERR_INVALID_ARG;
+  plan_free(p);
+  return DRC_OK;
+}
 
 drc_status drc_launch_count(drc_ctx *c, unsigned long long *count) {
   if (!c || !count) return DRC_ERR_INVALID_ARG;

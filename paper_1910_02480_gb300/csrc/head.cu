@@ -45,6 +45,14 @@ __global__ void __launch_bounds__(256, 4) head_kernel(const __grid_constant__ He
   const int tiles_x = (a.Wh + HT - 1) / HT, tiles_y = (a.Hh + HT - 1) / HT;
   const int tile = blockIdx.x % (tiles_x * tiles_y);
   const int n = blockIdx.x / (tiles_x * tiles_y);
+  float *out = a.out, *payload = a.payload;
+  int decode = a.decode;
+  if (a.slot) {  // block-uniform: the whole block leaves before any barrier
+    if (n >= a.slot->count) return;
+    out = a.slot->out;
+    payload = a.slot->payload;
+    decode = (a.slot->flags & SLOT_DECODE) ? 1 : 0;
+  }
   const int a0 = (tile / tiles_x) * HT, b0 = (tile % tiles_x) * HT;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int pp = (warp >> 1) >> 1, qq = (warp >> 1) & 1;  // output parity of this warp
@@ -137,10 +145,10 @@ __global__ void __launch_bounds__(256, 4) head_kernel(const __grid_constant__ He
   for (int o = 0; o < 3; ++o) {
     if (a.relu) y[o] = fmaxf(y[o], 0.f);
     const float L = expm1f(y[o]) * a.inv_exposure;
-    pay[o] = (valid && a.payload) ? L * a.band[p] : 0.f;
-    if (valid) a.out[(((size_t)n * 3 + o) * H + p) * W + q] = a.decode ? L : y[o];
+    pay[o] = (valid && payload) ? L * a.band[p] : 0.f;
+    if (valid) out[(((size_t)n * 3 + o) * H + p) * W + q] = decode ? L : y[o];
   }
-  if (a.payload) {
+  if (payload) {
 #pragma unroll
     for (int o = 0; o < 3; ++o) {
       float v = pay[o];
@@ -151,7 +159,7 @@ __global__ void __launch_bounds__(256, 4) head_kernel(const __grid_constant__ He
     if (threadIdx.x < 3) {
       float v = 0.f;
       for (int w = 0; w < 8; ++w) v += red[threadIdx.x][w];
-      atomicAdd(a.payload + (size_t)n * 3 + threadIdx.x, v);
+      atomicAdd(payload + (size_t)n * 3 + threadIdx.x, v);
     }
   }
 }

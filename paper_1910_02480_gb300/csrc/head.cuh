@@ -3,6 +3,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "pass.cuh"
+
 namespace drc {
 
 struct HeadArgs {
@@ -14,6 +16,7 @@ struct HeadArgs {
   int N, Hh, Wh, C;
   int relu, decode;
   float inv_exposure;
+  const PassSlot *slot; // nullable: out, payload, count (<= N) and decode flag from device memory
   float band[256];      // payload weight of each output row
 };
 

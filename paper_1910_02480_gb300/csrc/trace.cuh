@@ -45,6 +45,8 @@ class Tracer {
   }
 
   unsigned long long launches() const { return launches_; }
+  // Kernels launched inside a graph (counted, not timed one by one).
+  void add_launches(unsigned long long n) { launches_ += n; }
   void set_timing(bool on) { timing_ = on; }
 
   struct Total {

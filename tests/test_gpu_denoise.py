@@ -170,3 +170,28 @@ def test_launch_count_and_timing(drc):
     assert ctx.read_timing() == {}
     assert ctx.status() == drc.OK
     assert torch.equal(out, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_autotuned_context_keeps_parity(drc, precision):
+    """drc_autotune may change every layer's tile width and A path; the
+    results stay those of the oracle (FP32 bar) / of the untuned context."""
+    widths = [32, 64, 128]
+    w = synth.he_weights(widths, seed=3, bias=True)
+    x = torch.from_numpy(_maps(40, 32, 32)).cuda()
+    base = drc.Context(widths, w, precision=precision)
+    ref = base.denoise(x).cpu().numpy()
+    ctx = drc.Context(widths, w, precision=precision)
+    ctx.autotune(40, 32, 32)
+    tiles = [ctx.describe_layer(li) for li in range(2 * len(widths))]
+    print(precision, "autotuned (tile N, A path):", tiles)
+    assert tiles[-1][0] == 0
+    for li, (bn, _) in enumerate(tiles[:-1]):
+        cout = widths[li] if li < len(widths) else widths[2 * len(widths) - 2 - li]
+        assert bn in (cout, cout // 2)
+    g = ctx.denoise(x).cpu().numpy()
+    assert ctx.status() == drc.OK
+    if precision == "fp32":
+        assert rel_err(g, oracle.forward(w, x.cpu().numpy(), widths)) <= FP32_TOL
+    print("max |tuned - untuned| / rms:", np.max(np.abs(g - ref)) / np.sqrt(np.mean(ref * ref)))
+    assert rel_err(g, ref) <= (1e-6 if precision == "fp32" else 1e-2)
