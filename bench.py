@@ -148,6 +148,13 @@ def measure_precision(drc, torch, dev, prec, fp32_denoise_ms, autotune=True, ste
     g = synth.gbuffer(N_MAPS, 1, seed=12)
     x, _ = synth.hemisphere_maps(g["pos"], g["nrm"], H=MAP_H, W=MAP_W, seed=3)
     ctx = drc.Context(WIDTHS, w, precision=prec)
+    lobe = synth.lobes(seed=1, log_uniform=True)
+    cal_note = None
+    if prec == "fp8":  # per-channel scales from a separate batch of the same field
+        gc = synth.gbuffer(256, 1, seed=14)
+        xc, _ = synth.hemisphere_maps(gc["pos"], gc["nrm"], H=MAP_H, W=MAP_W, lobe=lobe, seed=7)
+        ctx.calibrate(torch.from_numpy(np.ascontiguousarray(xc, dtype=np.float32)).to(dev))
+        cal_note = "256 maps of the HDR field (not the error sample), drc_calibrate"
     if autotune:
         ctx.autotune(N_MAPS, MAP_H, MAP_W)
     xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev)
@@ -169,7 +176,6 @@ def measure_precision(drc, torch, dev, prec, fp32_denoise_ms, autotune=True, ste
         raise RuntimeError("device status after %s timing" % prec)
     den = float(np.mean(ms))
     # error sample: 16 maps of the HDR field, log1p-encoded radiance in
-    lobe = synth.lobes(seed=1, log_uniform=True)
     xs, _ = synth.hemisphere_maps(g["pos"][:16], g["nrm"][:16], H=MAP_H, W=MAP_W, lobe=lobe, seed=5)
     xs = np.ascontiguousarray(xs, dtype=np.float32)
     o, pa = ctx.denoise(torch.from_numpy(xs).to(dev), want_payload=True)
@@ -185,7 +191,8 @@ def measure_precision(drc, torch, dev, prec, fp32_denoise_ms, autotune=True, ste
     ctx.close()
     return {"denoise_ms": den, "denoise_maps_per_s": N_MAPS / (den * 1e-3),
             "speedup_vs_fp32_denoise": fp32_denoise_ms / den, "error_vs_oracle": err,
-            "error_sample": "16 maps 7x32x32, lobes log-uniform 1e-3..1e3, FP64 oracle"}
+            "error_sample": "16 maps 7x32x32, lobes log-uniform 1e-3..1e3, FP64 oracle",
+            "calibration": cal_note}
 
 
 def measure_uneven(drc, torch, dev, prec="bf16", reps=3):
@@ -497,7 +504,7 @@ def main():
             "clocks": clk}
     if rank == 0 and world == 1 and not args.no_extras and N_MAPS == 4096:
         line["precision_variants"] = {p: measure_precision(drc, torch, dev, p, den * 1e3, not args.no_autotune)
-                                      for p in ("bf16",) if p != args.precision}
+                                      for p in ("bf16", "fp8") if p != args.precision}
         line["uneven_batching"] = measure_uneven(drc, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         b = cpu_baseline(w, x, g, c)

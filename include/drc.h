@@ -222,6 +222,17 @@ const char *drc_last_error(drc_ctx *ctx);
  * the paper. */
 drc_status drc_autotune(drc_ctx *ctx, int N, int H, int W);
 
+/* FP8 e4m3 contexts: measure the network's activations on a representative
+ * batch (in, N, H, W, flags as drc_denoise) and set every layer's
+ * per-input-channel scales to the channel's maximum / 448 with one binade of
+ * headroom; the scales are folded into the layer's weights before they are
+ * quantised with per-output-channel scales.  Two passes (the second with the
+ * scales of the first).  Until calibrated, every scale is 1.  Synchronises;
+ * other precisions return DRC_ERR_UNSUPPORTED.  No counterpart in the paper
+ * (it runs in FP32 on a CPU). */
+drc_status drc_calibrate(drc_ctx *ctx, const float *in, int N, int H, int W,
+                         unsigned flags, void *stream);
+
 /* The tile width (0 for the head) and A-operand path (-1 default, 1 TMA +
  * producer conversion) drc_denoise uses for one layer (0 .. 2S-1). */
 drc_status drc_describe_layer(drc_ctx *ctx, int layer, int *bn, int *a_path);

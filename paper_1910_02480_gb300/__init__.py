@@ -118,6 +118,8 @@ def load_library():
     lib.drc_plan_launch.restype = I
     lib.drc_plan_describe.argtypes = [P, I, I, ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.drc_plan_describe.restype = I
+    lib.drc_calibrate.argtypes = [P, P, I, I, I, U, P]
+    lib.drc_calibrate.restype = I
     lib.drc_autotune.argtypes = [P, I, I, I]
     lib.drc_autotune.restype = I
     lib.drc_describe_layer.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]
@@ -274,6 +276,12 @@ class Context:
         """Synchronise and return the latched device status code."""
         rc = self._lib.drc_get_status(self._ctx, _stream(stream))
         return rc
+
+    def calibrate(self, x, flags=0, stream=None):
+        """FP8: set per-channel activation scales from a representative batch
+        x (device [N,7,H,W] float32); synchronises."""
+        N, C, H, W = x.shape
+        self._check(self._lib.drc_calibrate(self._ctx, _ptr(x), N, H, W, flags, _stream(stream)), "drc_calibrate")
 
     def autotune(self, N, H, W):
         """Time each conv layer's tile candidates for N maps of H x W and keep

@@ -48,7 +48,7 @@ struct PrecTraits<PREC_FP8> {
   static constexpr int ELEM = 1;
   static constexpr int KIND = KIND_F8;
   static constexpr int SPLIT = 1;
-  using act_t = __nv_bfloat16;  // fp8 path keeps bf16 activations, quantised on load
+  using act_t = uint8_t;  // e4m3 activations, quantised per channel by the producing layer
 };
 
 constexpr int SMEM_BUDGET = 227 * 1024;
@@ -66,9 +66,8 @@ constexpr int TS_STAGES = 4;
 constexpr int TS_A_COL0 = 256;
 
 // Raw bytes of one operand row per K block, in the stored activation type
-// (fp32 for the split-tf32 path, bf16 otherwise; an fp8 K block of 128
-// elements comes from 256 bytes of bf16).
-__host__ __device__ inline int raw_row_bytes(int prec) { return prec == PREC_FP8 ? 256 : 128; }
+// (fp32 for the split-tf32 path, bf16 / e4m3 otherwise): one swizzle row.
+__host__ __device__ inline int raw_row_bytes(int) { return 128; }
 
 // Shared memory: MMA stages (A and B tiles) plus, except when the TMA writes
 // the A tile itself, a ring of R raw slots; R = 3 keeps two K blocks of
@@ -185,8 +184,7 @@ __device__ __forceinline__ uint4 lds128(const void *p) {
 
 // One 16-byte A chunk from its raw bytes (uint4 = 16 B; FP8 reads two).
 template <int PREC>
-__device__ __forceinline__ void convert_store(uint8_t *a0, uint8_t *a1, uint32_t off, const uint4 *raw, int stride,
-                                              float qscale) {
+__device__ __forceinline__ void convert_store(uint8_t *a0, uint8_t *a1, uint32_t off, const uint4 *raw) {
   if constexpr (PREC == PREC_TF32X3) {
     const uint4 u = lds128(raw);
     const float x[4] = {__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z), __uint_as_float(u.w)};
@@ -199,17 +197,9 @@ __device__ __forceinline__ void convert_store(uint8_t *a0, uint8_t *a1, uint32_t
     }
     sts128(a0 + off, h[0], h[1], h[2], h[3]);
     sts128(a1 + off, l[0], l[1], l[2], l[3]);
-  } else if constexpr (PREC == PREC_BF16) {
+  } else {  // bf16 / e4m3: stored in the operand type already
     const uint4 u = lds128(raw);
     sts128(a0 + off, u.x, u.y, u.z, u.w);
-  } else {
-    const uint4 x = lds128(raw), y = lds128(raw + stride);
-    uint4 q;
-    q.x = pack_e4m3x4(bf16_lo(x.x) * qscale, bf16_hi(x.x) * qscale, bf16_lo(x.y) * qscale, bf16_hi(x.y) * qscale);
-    q.y = pack_e4m3x4(bf16_lo(x.z) * qscale, bf16_hi(x.z) * qscale, bf16_lo(x.w) * qscale, bf16_hi(x.w) * qscale);
-    q.z = pack_e4m3x4(bf16_lo(y.x) * qscale, bf16_hi(y.x) * qscale, bf16_lo(y.y) * qscale, bf16_hi(y.y) * qscale);
-    q.w = pack_e4m3x4(bf16_lo(y.z) * qscale, bf16_hi(y.z) * qscale, bf16_lo(y.w) * qscale, bf16_hi(y.w) * qscale);
-    sts128(a0 + off, q.x, q.y, q.z, q.w);
   }
 }
 
@@ -291,13 +281,12 @@ __device__ __forceinline__ void cp_async_wait() {
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // PROD_CPASYNC step 1: this thread's copies of one K block (4 rows x 16
-// bytes, fp8: x 32) into raw slot `slot`; layout [piece][thread] of 16 bytes.
+// bytes) into raw slot `slot`; layout [row][thread] of 16 bytes.
 template <int PREC>
 __device__ __forceinline__ void raw_issue(const ConvArgs &a, const RowInfo &ri, int kb, int pt, uint32_t slot) {
   using T = PrecTraits<PREC>;
   constexpr int E = 16 / T::ELEM;
   constexpr int BKE = KROW_BYTES / T::ELEM;
-  constexpr int PIECES = PREC == PREC_FP8 ? 2 : 1;  // 16-byte raw pieces per A chunk
   constexpr int AB = sizeof(typename T::act_t);
   const int k0 = kb * BKE + (pt & 7) * E;
   int tap, c;
@@ -317,9 +306,7 @@ __device__ __forceinline__ void raw_issue(const ConvArgs &a, const RowInfo &ri, 
     const int yy = ri.ybase[it] + dy, xx = ri.xbase[it] + dx;
     const bool okp = ri.vrow[it] && vtap && (unsigned)yy < (unsigned)a.Hin && (unsigned)xx < (unsigned)a.Win;
     const uint8_t *src = okp ? xin + ((size_t)(ri.pix_base[it] + yy * a.Win + xx) * a.Cin + c) * AB : xin;
-#pragma unroll
-    for (int h = 0; h < PIECES; ++h)
-      cp_async16(slot + (uint32_t)((it * PIECES + h) * NUM_PROD_THREADS + pt) * 16u, src + 16 * h, okp ? 16u : 0u);
+    cp_async16(slot + (uint32_t)(it * NUM_PROD_THREADS + pt) * 16u, src, okp ? 16u : 0u);
   }
 }
 
@@ -327,19 +314,17 @@ __device__ __forceinline__ void raw_issue(const ConvArgs &a, const RowInfo &ri, 
 template <int PREC>
 __device__ __forceinline__ void raw_convert_own(const ConvArgs &a, int pt, const uint8_t *slot, uint8_t *a0,
                                                 uint8_t *a1) {
-  constexpr int PIECES = PREC == PREC_FP8 ? 2 : 1;
   const int lane = pt & 31, pw = pt >> 5;
   const uint4 *raw = reinterpret_cast<const uint4 *>(slot);
 #pragma unroll
   for (int it = 0; it < 4; ++it) {
     const int r = (lane >> 3) + 4 * pw + 32 * it;
-    convert_store<PREC>(a0, a1, swz(r, lane & 7), raw + (it * PIECES) * NUM_PROD_THREADS + pt, NUM_PROD_THREADS,
-                        a.act_scale_in);
+    convert_store<PREC>(a0, a1, swz(r, lane & 7), raw + it * NUM_PROD_THREADS + pt);
   }
 }
 
 // PROD_TMA_CONVERT step 2: convert chunks of a TMA-filled raw slot (same
-// swizzled layout as the A tile; fp8: two swizzled 128-byte halves).
+// swizzled layout as the A tile).
 template <int PREC>
 __device__ __forceinline__ void raw_convert_tma(const ConvArgs &a, int pt, const uint8_t *slot, uint8_t *a0,
                                                 uint8_t *a1) {
@@ -347,22 +332,7 @@ __device__ __forceinline__ void raw_convert_tma(const ConvArgs &a, int pt, const
 #pragma unroll
   for (int it = 0; it < 4; ++it) {
     const int r = (lane >> 3) + 4 * pw + 32 * it;
-    if constexpr (PREC == PREC_FP8) {
-      // bf16 source: chunk q (16 e4m3) = raw chunks 2q, 2q+1 of the 256-byte row,
-      // stored as two 128-byte half tiles
-      const int h = q >> 2;  // which half holds chunks 2q, 2q+1
-      const uint8_t *half = slot + h * BM * KROW_BYTES;
-      const uint4 *p0 = reinterpret_cast<const uint4 *>(half + swz(r, (2 * q) & 7));
-      const uint4 *p1 = reinterpret_cast<const uint4 *>(half + swz(r, (2 * q + 1) & 7));
-      const uint4 x = lds128(p0), y = lds128(p1);
-      const float s = a.act_scale_in;
-      sts128(a0 + swz(r, q), pack_e4m3x4(bf16_lo(x.x) * s, bf16_hi(x.x) * s, bf16_lo(x.y) * s, bf16_hi(x.y) * s),
-             pack_e4m3x4(bf16_lo(x.z) * s, bf16_hi(x.z) * s, bf16_lo(x.w) * s, bf16_hi(x.w) * s),
-             pack_e4m3x4(bf16_lo(y.x) * s, bf16_hi(y.x) * s, bf16_lo(y.y) * s, bf16_hi(y.y) * s),
-             pack_e4m3x4(bf16_lo(y.z) * s, bf16_hi(y.z) * s, bf16_lo(y.w) * s, bf16_hi(y.w) * s));
-    } else {
-      convert_store<PREC>(a0, a1, swz(r, q), reinterpret_cast<const uint4 *>(slot + swz(r, q)), 0, a.act_scale_in);
-    }
+    convert_store<PREC>(a0, a1, swz(r, q), reinterpret_cast<const uint4 *>(slot + swz(r, q)));
   }
 }
 
@@ -435,13 +405,7 @@ __device__ __forceinline__ void tma_issue(const ConvArgs &a, const TmaCursor &c,
     x = dx;
     y = c.r0 + dy;
   }
-  if constexpr (PREC == PREC_FP8) {
-    // 128 e4m3 = 256 bytes of bf16 per row: two boxes of 64 channels
-    tma_load_4d(dst, &a.tmap, c0, x, y, c.n0, bar);
-    tma_load_4d(dst + BM * KROW_BYTES, &a.tmap, c0 + 64, x, y, c.n0, bar);
-  } else {
-    tma_load_4d(dst, &a.tmap, c0, x, y, c.n0, bar);
-  }
+  tma_load_4d(dst, &a.tmap, c0, x, y, c.n0, bar);
 }
 
 // Producer warps.  `raw` is the raw ring (unused in PROD_TMA_DIRECT).
@@ -460,7 +424,7 @@ __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint
   for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) total_kb += a.ph[tile_coord(a, t).phase].num_kb;
   unsigned long long w_empty = 0, w_copy = 0, w_conv = 0, w_fence = 0, w_issue = 0;
   const long long t_start = a.prof ? clock64() : 0;
-  const int slot_box = PREC == PREC_FP8 ? 2 * BM * KROW_BYTES : BM * KROW_BYTES;  // TMA bytes per K block
+  const int slot_box = BM * KROW_BYTES;  // TMA bytes per K block
 
   if (a.prod_mode == PROD_TMA_DIRECT) {
     // one thread: wait for the stage, expect the box bytes, load into the A tile
@@ -631,29 +595,37 @@ __device__ __forceinline__ void tmem_ld_acc(uint32_t taddr, int BN, float (&v)[1
   }
 }
 
-// 16 consecutive skip channels as raw 16-byte words (fp32: 4 words, bf16: 2).
+// 16 consecutive skip channels as raw 16-byte words (fp32: 4 words, bf16: 2,
+// e4m3: 1).
 template <int PREC>
 __device__ __forceinline__ void load_skip(const typename PrecTraits<PREC>::act_t *p, uint4 (&s)[4]) {
   const uint4 *q = reinterpret_cast<const uint4 *>(p);
-  if constexpr (PREC == PREC_TF32X3) {
+  constexpr int NW = PREC == PREC_TF32X3 ? 4 : (PREC == PREC_BF16 ? 2 : 1);
 #pragma unroll
-    for (int e = 0; e < 4; ++e) s[e] = q[e];
-  } else {
-#pragma unroll
-    for (int e = 0; e < 2; ++e) s[e] = q[e];
-  }
+  for (int e = 0; e < NW; ++e) s[e] = q[e];
+}
+
+// Four e4m3 bytes of a word -> floats.
+__device__ __forceinline__ void e4m3x4_to_f32(uint32_t w, float *f) {
+  const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xFFFFu), __NV_E4M3);
+  const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+  f[0] = a.x;
+  f[1] = a.y;
+  f[2] = b.x;
+  f[3] = b.y;
 }
 
 // Epilogue of one 16-column chunk of one accumulator row: TMEM load (every
-// lane: the load is warp-collective), then for a valid row bias, ReLU, the
-// skip add and the NHWC store.
+// lane: the load is warp-collective), dequantisation (FP8), bias, ReLU, the
+// skip add, the calibration max (warp-collective), then for a valid row the
+// NHWC store -- e4m3 with the consumer's scales when out_qinv is set.
 template <int PREC>
 __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int cc, int BN, int col0, bool vrow,
-                                          bool has_skip, const uint4 (&sk)[4],
-                                          typename PrecTraits<PREC>::act_t *yp) {
+                                          bool has_skip, const uint4 (&sk)[4], uint8_t *yb) {
   float v[16];
   tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
-  if (!vrow) return;
   const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
   const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
 #pragma unroll
@@ -662,14 +634,14 @@ __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int
     const float bb[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      float z = bsc ? v[4 * e4 + e] * bsc[4 * e4 + e] : v[4 * e4 + e];
+      float z = bsc ? v[4 * e4 + e] * __ldg(bsc + 4 * e4 + e) : v[4 * e4 + e];
       z += bb[e];
       if (a.relu) z = fmaxf(z, 0.f);
       v[4 * e4 + e] = z;
     }
   }
-  if constexpr (PREC == PREC_TF32X3) {
-    if (has_skip) {
+  if (has_skip) {
+    if constexpr (PREC == PREC_TF32X3) {
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         v[4 * e] += __uint_as_float(sk[e].x);
@@ -677,12 +649,7 @@ __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int
         v[4 * e + 2] += __uint_as_float(sk[e].z);
         v[4 * e + 3] += __uint_as_float(sk[e].w);
       }
-    }
-    float4 *q = reinterpret_cast<float4 *>(yp);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) q[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-  } else {
-    if (has_skip) {
+    } else if constexpr (PREC == PREC_BF16) {
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
         v[8 * e + 0] += bf16_lo(sk[e].x);
@@ -694,8 +661,39 @@ __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int
         v[8 * e + 6] += bf16_lo(sk[e].w);
         v[8 * e + 7] += bf16_hi(sk[e].w);
       }
+    } else {
+      float f[16];
+      e4m3x4_to_f32(sk[0].x, f);
+      e4m3x4_to_f32(sk[0].y, f + 4);
+      e4m3x4_to_f32(sk[0].z, f + 8);
+      e4m3x4_to_f32(sk[0].w, f + 12);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) v[e] = fmaf(f[e], __ldg(a.skip_scale + col0 + e), v[e]);
     }
-    uint4 *q = reinterpret_cast<uint4 *>(yp);
+  }
+  if (a.amax) {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const unsigned m = __reduce_max_sync(0xffffffffu, vrow ? __float_as_uint(fabsf(v[e])) : 0u);
+      if ((threadIdx.x & 31) == 0 && m) atomicMax(a.amax + col0 + e, m);
+    }
+  }
+  if (!vrow) return;
+  if (a.out_qinv) {
+    const float *qi = a.out_qinv + col0;
+    uint4 o;
+    o.x = pack_e4m3x4(v[0] * __ldg(qi), v[1] * __ldg(qi + 1), v[2] * __ldg(qi + 2), v[3] * __ldg(qi + 3));
+    o.y = pack_e4m3x4(v[4] * __ldg(qi + 4), v[5] * __ldg(qi + 5), v[6] * __ldg(qi + 6), v[7] * __ldg(qi + 7));
+    o.z = pack_e4m3x4(v[8] * __ldg(qi + 8), v[9] * __ldg(qi + 9), v[10] * __ldg(qi + 10), v[11] * __ldg(qi + 11));
+    o.w = pack_e4m3x4(v[12] * __ldg(qi + 12), v[13] * __ldg(qi + 13), v[14] * __ldg(qi + 14),
+                      v[15] * __ldg(qi + 15));
+    *reinterpret_cast<uint4 *>(yb) = o;
+  } else if constexpr (PREC == PREC_TF32X3) {
+    float4 *q = reinterpret_cast<float4 *>(yb);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) q[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+  } else {
+    uint4 *q = reinterpret_cast<uint4 *>(yb);
 #pragma unroll
     for (int e = 0; e < 2; ++e)
       q[e] = make_uint4(pack_bf16x2(v[8 * e], v[8 * e + 1]), pack_bf16x2(v[8 * e + 2], v[8 * e + 3]),
@@ -703,7 +701,6 @@ __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int
   }
 }
 
-// ------------------------------------------------------------- the kernel
 template <int PREC>
 __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_constant__ ConvArgs a) {
   using T = PrecTraits<PREC>;
@@ -892,7 +889,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     unsigned long long w_tfull = 0;
     const long long t_start = a.prof ? clock64() : 0;
     using act_t = typename T::act_t;
-    act_t *yout = reinterpret_cast<act_t *>(a.y);
+    uint8_t *yout = reinterpret_cast<uint8_t *>(a.y);
+    const int out_elem = a.out_qinv ? 1 : (int)sizeof(act_t);  // e4m3, or the activation type
     const act_t *skip = reinterpret_cast<const act_t *>(a.skip);
     const int nch = BN / 16;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++it) {
@@ -923,12 +921,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       if (!pwait(a, w_tfull, smem_u32(&tfull_bar[buf]), par)) break;
       tc_fence_after();
       const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
+      uint8_t *yb = yout + ebase * out_elem;
       for (int cc = 0; cc < nch; cc += 2) {
-        epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk0, yout + ebase + cc * 16);
+        epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk0, yb + cc * 16 * out_elem);
         if (has_skip && cc + 2 < nch) load_skip<PREC>(skip + ebase + (cc + 2) * 16, sk0);
         if (cc + 1 < nch) {
           epi_chunk<PREC>(a, taddr, cc + 1, BN, tc.n_tile * BN + (cc + 1) * 16, vrow, has_skip, sk1,
-                          yout + ebase + (cc + 1) * 16);
+                          yb + (cc + 1) * 16 * out_elem);
           if (has_skip && cc + 3 < nch) load_skip<PREC>(skip + ebase + (cc + 3) * 16, sk1);
         }
       }
@@ -1085,8 +1084,12 @@ __global__ void pack_kernel(const __grid_constant__ PackArgs p) {
     o.w = pack_bf16x2(w[6], w[7]);
     *reinterpret_cast<uint4 *>(p.B + off) = o;
   } else {
-    // values divided by the column's dequantisation scale (bscale)
+    // W x (input channel scale) / (column scale): the layer's input is stored
+    // as x / in_scale[c], so the product dequantises with bscale[col] alone
     const float inv = 1.0f / p.bscale[col];
+    const int k0 = kb * BKE + q * E;
+#pragma unroll
+    for (int e = 0; e < E; ++e) w[e] *= p.in_scale ? __ldg(p.in_scale + (k0 + e) % p.Cin) : 1.f;
     uint4 o;
     o.x = pack_e4m3x4(w[0] * inv, w[1] * inv, w[2] * inv, w[3] * inv);
     o.y = pack_e4m3x4(w[4] * inv, w[5] * inv, w[6] * inv, w[7] * inv);
@@ -1096,8 +1099,37 @@ __global__ void pack_kernel(const __grid_constant__ PackArgs p) {
   }
 }
 
+// FP8: bscale[col] = max over the layer's taps and channels of
+// |W[col][k] x in_scale[c]| / 448 (the e4m3 maximum), or 1 for a zero column.
+// One block per output column.
+__global__ void fp8_colscale_kernel(const __grid_constant__ PackArgs p) {
+  const int col = blockIdx.x;
+  float m = 0.f;
+  for (int ph = 0; ph < p.num_phases; ++ph) {
+    const PhaseDesc &pd = p.ph[ph];
+    for (int k = threadIdx.x; k < pd.ntaps * p.Cin; k += blockDim.x) {
+      const float sc = p.in_scale ? __ldg(p.in_scale + k % p.Cin) : 1.f;
+      m = fmaxf(m, fabsf(raw_weight(p, pd, col, k) * sc));
+    }
+  }
+  __shared__ float red[32];
+  for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+    m = fmaxf(m, red[0]);
+    p.bscale[col] = m > 0.f ? m / 448.f : 1.f;
+  }
+}
+
 cudaError_t launch_pack(const PackArgs &p, int prec, cudaStream_t st) {
   if (p.total_chunks == 0) return cudaSuccess;
+  if (prec == PREC_FP8) {
+    fp8_colscale_kernel<<<p.Cout, 256, 0, st>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const int threads = 256;
   const unsigned blocks = (unsigned)((p.total_chunks + threads - 1) / threads);
   switch (prec) {

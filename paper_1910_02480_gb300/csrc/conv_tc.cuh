@@ -64,7 +64,10 @@ struct ConvArgs {
   int phase_order[4];    // heaviest phase first
   PhaseDesc ph[4];
   int relu;
-  float act_scale_in;    // FP8: activations stored as value / scale
+  const float *out_qinv;   // nullable: store the output as e4m3, column c times out_qinv[c] (the inverse
+                           // of the consuming layer's input scale); else in the kernel's activation type
+  const float *skip_scale; // FP8 kernel: the e4m3 skip tensor's per-channel scales
+  unsigned *amax;          // nullable: per output column max |output| before quantisation (calibration)
   int *status;
   unsigned long long timeout_ns;
   int debug_stall;
@@ -96,7 +99,8 @@ struct PackArgs {
   int BN, n_tiles, num_phases;
   PhaseDesc ph[4];
   uint8_t *B, *B_lo;  // packed outputs
-  float *bscale;      // FP8: per-column scale out
+  float *bscale;      // FP8: per-column scale out (this layer's columns)
+  const float *in_scale;  // FP8: per-input-channel activation scale folded into W (nullable = 1)
   long long total_chunks;
 };
 cudaError_t launch_pack(const PackArgs &p, int prec, cudaStream_t st);

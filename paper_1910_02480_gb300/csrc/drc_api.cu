@@ -35,6 +35,9 @@ struct Layer {
   PhaseDesc ph[4];
   int phase_order[4];
   size_t pack_off, pack_bytes;  // in the packed operand buffer(s)
+  int prec;                     // kernel precision of this layer (FP8 contexts run the first layer in BF16)
+  size_t sc_off;                // FP8: offset of this layer's input-channel scales (Cin floats) in the scale arrays
+  size_t bs_off;                // FP8: offset of this layer's output-column scales (Cout floats)
   char name[16];                // kernel label for the launch tracer
 };
 
@@ -50,7 +53,13 @@ struct drc_ctx {
   std::vector<int> modes;     // per layer: A-operand path chosen by drc_autotune (-1 = default)
   float *d_wraw = nullptr;
   uint8_t *d_pack = nullptr, *d_pack_lo = nullptr;
-  float *d_bscale = nullptr;
+  float *d_bscale = nullptr;   // FP8: per-layer output-column dequantisation scales
+  float *d_inscale = nullptr;  // FP8: per-layer input-channel scales (activation = value / scale)
+  float *d_qinv = nullptr;     // FP8: their inverses (quantisation by the producing layer)
+  unsigned *d_amax = nullptr;  // FP8 calibration: per-layer output-column max |value| (float bits)
+  bool calibrating = false;
+  size_t n_scales = 0, n_bscales = 0;
+  std::vector<float> h_inscale;
   size_t pack_total = 0;
   void *d_act = nullptr;
   size_t act_bytes = 0;
@@ -125,15 +134,17 @@ void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
   if (2 * rows_t > 256 || maps_t > 256) return;
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return;
-  const int eb = prec == PREC_TF32X3 ? 4 : 2;  // stored activation bytes
-  const int box_c = KROW_BYTES / eb;          // channels per box row (128 bytes)
+  const int eb = prec == PREC_TF32X3 ? 4 : (prec == PREC_BF16 ? 2 : 1);  // stored activation bytes
+  const int box_c = KROW_BYTES / eb;                                     // channels per box row (128 bytes)
   cuuint64_t dims[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.Win, (cuuint64_t)a.Hin, (cuuint64_t)a.N};
   cuuint64_t strides[3] = {(cuuint64_t)a.Cin * eb, (cuuint64_t)a.Cin * eb * a.Win,
                            (cuuint64_t)a.Cin * eb * a.Win * a.Hin};
   cuuint32_t box[4] = {(cuuint32_t)box_c, (cuuint32_t)(s2 ? 2 * Wr : Wr), (cuuint32_t)(s2 ? 2 * rows_t : rows_t),
                        (cuuint32_t)maps_t};
   cuuint32_t estr[4] = {1, (cuuint32_t)(s2 ? 2 : 1), (cuuint32_t)(s2 ? 2 : 1), 1};
-  CUresult r = enc(&a.tmap, prec == PREC_TF32X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+  const CUtensorMapDataType dt = prec == PREC_TF32X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                : (prec == PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
+  CUresult r = enc(&a.tmap, dt,
                    4, const_cast<void *>(a.x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return;
@@ -142,7 +153,7 @@ void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
     a.prod_mode = PROD_TMA_CONVERT;
     return;
   }
-  if (prec == PREC_BF16)
+  if (prec == PREC_BF16 || prec == PREC_FP8)
     a.prod_mode = PROD_TMA_DIRECT;
   else if (prec == PREC_TF32X3 && a.BN <= 128 && std::getenv("DRC_NO_TMEM_A") == nullptr)
     a.prod_mode = PROD_TMA_TMEM;  // A operand in tensor memory
@@ -152,6 +163,9 @@ void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
 
 int bke_of(int prec) { return KROW_BYTES / (prec == PREC_TF32X3 ? 4 : (prec == PREC_BF16 ? 2 : 1)); }
 int elem_act(int prec) { return prec == PREC_TF32X3 ? 4 : 2; }
+// Bytes per element of stored activation s (0 = the first layer's NHWC8
+// input, s >= 1 = e_s): FP8 contexts keep the input in bf16 and store e4m3.
+int elem_store(int prec, int s) { return prec == PREC_FP8 ? (s == 0 ? 2 : 1) : elem_act(prec); }
 
 int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
@@ -223,12 +237,11 @@ void set_bn(Layer &L, int BN) {
 void plan_layers(drc_ctx *c) {
   const drc_config &g = c->cfg;
   const int S = g.num_stages;
-  const int bke = bke_of(c->prec);
   std::vector<int> wd(S + 1);
   wd[0] = g.in_channels;
   for (int s = 1; s <= S; ++s) wd[s] = g.widths[s - 1];
   c->layers.clear();
-  size_t off = 0;
+  size_t off = 0, sc = 0, bs = 0;
   auto finish = [&](Layer &L) {
     // heaviest phase first
     for (int p = 0; p < 4; ++p) L.phase_order[p] = p < L.num_phases ? p : 0;
@@ -245,6 +258,7 @@ void plan_layers(drc_ctx *c) {
     Layer L;
     memset(&L, 0, sizeof L);
     L.kind = LK_CONV;
+    L.prec = (c->prec == PREC_FP8 && s == 1) ? PREC_BF16 : c->prec;
     snprintf(L.name, sizeof L.name, "conv e%d", s);
     L.Cin_raw = wd[s - 1];
     L.Cin = s == 1 ? 8 : wd[s - 1];  // the 7-channel input is staged as NHWC with 8 channels
@@ -261,7 +275,11 @@ void plan_layers(drc_ctx *c) {
       pd.u[t] = pd.dy[t] = (signed char)(t / 3);
       pd.v[t] = pd.dx[t] = (signed char)(t % 3);
     }
-    pd.num_kb = ceil_div(9ll * L.Cin, bke);
+    pd.num_kb = ceil_div(9ll * L.Cin, bke_of(L.prec));
+    L.sc_off = sc;
+    sc += L.Cin;
+    L.bs_off = bs;
+    bs += L.Cout;
     finish(L);
   }
   for (int s = S; s >= 1; --s) {
@@ -269,6 +287,11 @@ void plan_layers(drc_ctx *c) {
     memset(&L, 0, sizeof L);
     L.Cin = L.Cin_raw = wd[s];
     L.Cout = s == 1 ? g.out_channels : wd[s - 1];
+    L.prec = c->prec;
+    L.sc_off = sc;
+    sc += L.Cin;
+    L.bs_off = bs;
+    bs += L.Cout;
     L.w_off = off;
     off += 9ull * L.Cin * L.Cout;
     L.b_off = off;
@@ -282,11 +305,13 @@ void plan_layers(drc_ctx *c) {
       snprintf(L.name, sizeof L.name, "convT d%d", s);
       set_bn(L, pick_bn(L.Cout));
       L.num_phases = 4;
-      for (int p = 0; p < 4; ++p) convT_phase(L.ph[p], p >> 1, p & 1, L.Cin, bke);
+      for (int p = 0; p < 4; ++p) convT_phase(L.ph[p], p >> 1, p & 1, L.Cin, bke_of(L.prec));
     }
     finish(L);
   }
   c->pack_total = layout_packs(c->layers);
+  c->n_scales = sc;
+  c->n_bscales = bs;
 }
 
 drc_status check_config(const drc_config *g, drc_ctx *c) {
@@ -300,7 +325,6 @@ drc_status check_config(const drc_config *g, drc_ctx *c) {
       return fail(c, DRC_ERR_INVALID_ARG, "widths[%d] = %d: must be a multiple of 16 in 16..1024", s, g->widths[s]);
   if (g->precision < DRC_PREC_FP32 || g->precision > DRC_PREC_FP8_E4M3)
     return fail(c, DRC_ERR_INVALID_ARG, "unknown precision %d", (int)g->precision);
-  if (g->precision == DRC_PREC_FP8_E4M3) return fail(c, DRC_ERR_UNSUPPORTED, "fp8 precision is not built yet");
   if (!(g->exposure > 0.f) || !std::isfinite(g->exposure))
     return fail(c, DRC_ERR_INVALID_ARG, "exposure must be finite and > 0");
   if (g->wait_timeout_ms < 0) return fail(c, DRC_ERR_INVALID_ARG, "wait_timeout_ms must be >= 0");
@@ -358,10 +382,14 @@ drc_status pack_layers(drc_ctx *c, const std::vector<Layer> &Ls, uint8_t *B, uin
     for (int i = 0; i < 4; ++i) p.ph[i] = L.ph[i];
     p.B = B;
     p.B_lo = B_lo;
-    p.bscale = c->d_bscale;
+    if (L.prec == PREC_FP8) {
+      p.bscale = c->d_bscale + L.bs_off;
+      p.in_scale = c->d_inscale + L.sc_off;
+    }
     p.total_chunks = (long long)(L.pack_bytes / 16);
     cudaError_t e;
-    DRC_TRACED(&c->tracer, "weight pack", st, e = launch_pack(p, c->prec, st));
+    DRC_TRACED(&c->tracer, "weight pack", st, e = launch_pack(p, L.prec, st));
+    if (L.prec == PREC_FP8) c->tracer.add_launches(1);  // the column-scale kernel before it
     if (e != cudaSuccess) return cuda_fail(c, e, "weight packing");
   }
   return DRC_OK;
@@ -371,9 +399,10 @@ drc_status pack_all(drc_ctx *c, cudaStream_t st) { return pack_layers(c, c->laye
 
 size_t act_bytes_for(const drc_ctx *c, long long N, int H, int W) {
   // the first layer's NHWC input (8 channels), then e_1 .. e_S
-  size_t b = (((size_t)N * H * W * 8 * elem_act(c->prec)) + 255) & ~(size_t)255;
+  size_t b = (((size_t)N * H * W * 8 * elem_store(c->prec, 0)) + 255) & ~(size_t)255;
   for (int s = 1; s <= c->cfg.num_stages; ++s)
-    b += (((size_t)N * (H >> s) * (W >> s) * c->cfg.widths[s - 1] * elem_act(c->prec)) + 255) & ~(size_t)255;
+    b += (((size_t)N * (H >> s) * (W >> s) * c->cfg.widths[s - 1] * elem_store(c->prec, s)) + 255) &
+         ~(size_t)255;
   return b;
 }
 
@@ -402,7 +431,6 @@ void fill_common(const drc_ctx *c, const Layer &L, const uint8_t *B, const uint8
     a.ph[i] = L.ph[i];
     a.phase_order[i] = L.phase_order[i];
   }
-  a.act_scale_in = 1.f;
   a.cin_shift = -1;
   for (int sh = 0; sh < 16; ++sh)
     if ((1 << sh) == L.Cin) a.cin_shift = sh;
@@ -428,16 +456,22 @@ void carve_chain(const drc_ctx *c, void *base, int N, int H, int W, Chain &ch) {
   ch.W = W;
   ch.in8 = static_cast<uint8_t *>(base);
   ch.act.assign(S + 1, nullptr);
-  size_t off = (((size_t)N * H * W * 8 * elem_act(c->prec)) + 255) & ~(size_t)255;
+  size_t off = (((size_t)N * H * W * 8 * elem_store(c->prec, 0)) + 255) & ~(size_t)255;
   for (int s2 = 1; s2 <= S; ++s2) {
     ch.act[s2] = static_cast<uint8_t *>(base) + off;
-    off += (((size_t)N * (H >> s2) * (W >> s2) * c->cfg.widths[s2 - 1] * elem_act(c->prec)) + 255) & ~(size_t)255;
+    off += (((size_t)N * (H >> s2) * (W >> s2) * c->cfg.widths[s2 - 1] * elem_store(c->prec, s2)) + 255) &
+           ~(size_t)255;
   }
 }
 
 // ConvArgs of tensor-core layer li (encoder conv or decoder convT) of a chain.
-void conv_args_for(const drc_ctx *c, const Layer &L, size_t li, const Chain &ch, const uint8_t *B,
-                   const uint8_t *B_lo, int force_mode, ConvArgs &a) {
+// Ls: the chain's layer table (L = Ls[li] or a retiled copy of it).
+// FP8 contexts: the output is quantised with the input scales of the layer
+// that consumes it (layer li + 1 in the table's order e_1..e_S, d_S..d_2,
+// head) and a decoder's skip e_{s-1} is dequantised with the input scales of
+// e_s, the layer that consumed it.
+void conv_args_for(const drc_ctx *c, const std::vector<Layer> &Ls, const Layer &L, size_t li, const Chain &ch,
+                   const uint8_t *B, const uint8_t *B_lo, int force_mode, ConvArgs &a) {
   const int S = c->cfg.num_stages;
   const int H = ch.H, W = ch.W;
   fill_common(c, L, B, B_lo, a);
@@ -468,7 +502,16 @@ void conv_args_for(const drc_ctx *c, const Layer &L, size_t li, const Chain &ch,
   a.M = (int)((long long)ch.N * a.Hrow * a.Wrow);
   a.m_tiles = ceil_div(a.M, BM);
   a.count = ch.count;
-  plan_operand(c->prec, a, force_mode);
+  if (c->prec == PREC_FP8) {
+    if (L.prec == PREC_FP8) a.bscale = c->d_bscale + L.bs_off;
+    a.out_qinv = c->d_qinv + Ls[li + 1].sc_off;
+    if (L.kind == LK_CONVT) {
+      const int s2 = S - ((int)li - S);
+      a.skip_scale = c->d_inscale + Ls[s2 - 1].sc_off;
+    }
+    if (c->calibrating) a.amax = c->d_amax + L.bs_off;
+  }
+  plan_operand(L.prec, a, force_mode);
 }
 
 // Enqueue the whole network over one chain: input staging, S encoder convs,
@@ -501,6 +544,7 @@ drc_status run_chain(drc_ctx *c, const std::vector<Layer> &layers, const uint8_t
       h.decode = (flags & DRC_F_DECODE_OUTPUT) ? 1 : 0;
       h.inv_exposure = 1.0f / c->cfg.exposure;
       h.slot = ch.slot;
+      if (c->prec == PREC_FP8) h.in_scale = c->d_inscale + L.sc_off;
       if (payload || ch.slot) {
         const double pi = 3.14159265358979323846;
         for (int i = 0; i < ch.H; ++i) {
@@ -508,15 +552,15 @@ drc_status run_chain(drc_ctx *c, const std::vector<Layer> &layers, const uint8_t
           h.band[i] = (float)((std::sin(t1) * std::sin(t1) - std::sin(t0) * std::sin(t0)) / ch.W);
         }
       }
-      DRC_TRACED(tr, L.name, st, e = launch_head(h, c->prec != PREC_TF32X3, st));
+      DRC_TRACED(tr, L.name, st, e = launch_head(h, c->prec, st));
       if (e != cudaSuccess) return cuda_fail(c, e, "head launch");
       continue;
     }
     ConvArgs a;
-    conv_args_for(c, L, li, ch, B, B_lo, modes ? (*modes)[li] : -1, a);
+    conv_args_for(c, layers, L, li, ch, B, B_lo, modes ? (*modes)[li] : -1, a);
     a.debug_stall = debug_stall && li == 0;
     if (prof) a.prof = prof + li * PROF_SLOTS;
-    DRC_TRACED(tr, L.name, st, e = launch_conv(a, c->prec, c->num_sms, st));
+    DRC_TRACED(tr, L.name, st, e = launch_conv(a, L.prec, c->num_sms, st));
     if (e != cudaSuccess) return cuda_fail(c, e, "layer launch");
   }
   return DRC_OK;
@@ -603,15 +647,16 @@ drc_status plan_pack(drc_plan *p, cudaStream_t st) {
 }
 
 // Time one conv layer of a chain (min of 3 launches after one warm-up).
-drc_status time_layer(drc_ctx *c, const Layer &L, size_t li, const Chain &ch, const uint8_t *B, const uint8_t *B_lo,
-                      int mode, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1, float *best_ms) {
+drc_status time_layer(drc_ctx *c, const std::vector<Layer> &Ls, const Layer &L, size_t li, const Chain &ch,
+                      const uint8_t *B, const uint8_t *B_lo, int mode, cudaStream_t st, cudaEvent_t e0,
+                      cudaEvent_t e1, float *best_ms) {
   ConvArgs a;
-  conv_args_for(c, L, li, ch, B, B_lo, mode, a);
+  conv_args_for(c, Ls, L, li, ch, B, B_lo, mode, a);
   a.count = nullptr;
   float best = 1e30f;
   for (int r = 0; r < 4; ++r) {
     cudaEventRecord(e0, st);
-    cudaError_t e = launch_conv(a, c->prec, c->num_sms, st);
+    cudaError_t e = launch_conv(a, L.prec, c->num_sms, st);
     cudaEventRecord(e1, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "autotune launch");
     if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return cuda_fail(c, e, "autotune sync");
@@ -657,7 +702,7 @@ drc_status autotune_layers(drc_ctx *c, std::vector<Layer> &Ls, std::vector<int> 
       if (c->prec == PREC_TF32X3 && bn <= 128) mode_list.push_back(PROD_TMA_CONVERT);
       for (int mode : mode_list) {
         float ms = 0.f;
-        if ((s = time_layer(c, one[0], li, ch, B, B_lo, mode, st, e0, e1, &ms)) != DRC_OK) break;
+        if ((s = time_layer(c, Ls, one[0], li, ch, B, B_lo, mode, st, e0, e1, &ms)) != DRC_OK) break;
         if (ms < best) {
           best = ms;
           best_bn = bn;
@@ -720,6 +765,19 @@ drc_status drc_create(const drc_config *cfg, const float *weights_host, size_t n
   if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&c->d_pack_lo, c->pack_total);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e == cudaSuccess && c->prec == PREC_FP8) {
+    // activation scales start at 1 (values up to the e4m3 maximum, 448)
+    // until drc_calibrate measures the network's activations
+    c->h_inscale.assign(c->n_scales, 1.0f);
+    e = cudaMalloc(&c->d_inscale, c->n_scales * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_qinv, c->n_scales * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_bscale, c->n_bscales * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_amax, c->n_bscales * sizeof(unsigned));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->d_inscale, c->h_inscale.data(), c->n_scales * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(c->d_qinv, c->h_inscale.data(), c->n_scales * sizeof(float), cudaMemcpyHostToDevice);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     drc_destroy(c);
@@ -771,6 +829,9 @@ drc_status drc_destroy(drc_ctx *c) {
   cudaFree(c->d_pack);
   cudaFree(c->d_pack_lo);
   cudaFree(c->d_bscale);
+  cudaFree(c->d_inscale);
+  cudaFree(c->d_qinv);
+  cudaFree(c->d_amax);
   cudaFree(c->d_act);
   cudaFree(c->d_iscratch);
   cudaFree(c->d_status);
@@ -1002,6 +1063,73 @@ drc_status drc_autotune(drc_ctx *c, int N, int H, int W) {
   }
   if (s == DRC_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) s = cuda_fail(c, e, "autotune");
   cudaStreamDestroy(st);
+  return s;
+}
+
+drc_status drc_calibrate(drc_ctx *c, const float *in, int N, int H, int W, unsigned flags, void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (c->prec != PREC_FP8) return fail(c, DRC_ERR_UNSUPPORTED, "calibration applies to FP8 contexts only");
+  const int S = c->cfg.num_stages;
+  if (flags & ~(DRC_F_ENCODE_INPUT | DRC_F_DECODE_OUTPUT))
+    return fail(c, DRC_ERR_INVALID_ARG, "unknown flags 0x%x", flags);
+  if (N < 1 || H < (1 << S) || W < (1 << S) || H % (1 << S) || W % (1 << S) ||
+      (long long)N * H * W * 7 >= (1ll << 31))
+    return fail(c, DRC_ERR_INVALID_ARG, "calibration batch N=%d H=%d W=%d is not a valid denoise batch", N, H, W);
+  if (!c->weights_set) return fail(c, DRC_ERR_INVALID_ARG, "weights were never set");
+  drc_status s;
+  if ((s = check_dev(c, in, "in", false)) != DRC_OK) return s;
+  if ((s = ensure_act(c, N, H, W)) != DRC_OK) return s;
+  float *out = nullptr;
+  cudaError_t e = cudaMalloc(&out, (size_t)N * 3 * H * W * sizeof(float));
+  if (e != cudaSuccess) return cuda_fail(c, e, "calibration output");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Chain ch;
+  carve_chain(c, c->d_act, N, H, W, ch);
+  std::vector<unsigned> amax(c->n_bscales);
+  // Two passes: the first runs with the current scales, the second with the
+  // scales the first measured, so every layer sees well-quantised inputs.
+  for (int pass = 0; pass < 2 && s == DRC_OK; ++pass) {
+    if ((e = cudaMemsetAsync(c->d_amax, 0, c->n_bscales * sizeof(unsigned), st)) != cudaSuccess) {
+      s = cuda_fail(c, e, "calibration clear");
+      break;
+    }
+    c->calibrating = true;
+    s = run_chain(c, c->layers, c->d_pack, c->d_pack_lo, &c->modes, ch, in, out, nullptr, flags, st, &c->tracer,
+                  nullptr);
+    c->calibrating = false;
+    if (s != DRC_OK) break;
+    if ((e = cudaMemcpyAsync(amax.data(), c->d_amax, amax.size() * sizeof(unsigned), cudaMemcpyDeviceToHost, st)) !=
+            cudaSuccess ||
+        (e = cudaStreamSynchronize(st)) != cudaSuccess) {
+      s = cuda_fail(c, e, "calibration read");
+      break;
+    }
+    // layer li + 1 consumes layer li's output: its input scale for channel
+    // ch is that channel's measured maximum over 448 (the e4m3 maximum), with
+    // one binade of headroom for batches brighter than this one
+    std::vector<float> qinv(c->n_scales);
+    for (size_t li = 0; li + 1 < c->layers.size(); ++li) {
+      const Layer &P = c->layers[li], &Q = c->layers[li + 1];
+      for (int ch2 = 0; ch2 < Q.Cin; ++ch2) {
+        float m;
+        memcpy(&m, &amax[P.bs_off + ch2], sizeof m);
+        c->h_inscale[Q.sc_off + ch2] = m > 0.f && std::isfinite(m) ? 2.0f * m / 448.0f : 1.0f;
+      }
+    }
+    for (size_t i = 0; i < c->n_scales; ++i) qinv[i] = 1.0f / c->h_inscale[i];
+    e = cudaMemcpy(c->d_inscale, c->h_inscale.data(), c->n_scales * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_qinv, qinv.data(), c->n_scales * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      s = cuda_fail(c, e, "calibration upload");
+      break;
+    }
+    s = pack_all(c, st);  // fold the new input scales into the e4m3 weights
+    ++c->weights_version;
+  }
+  cudaStreamSynchronize(st);
+  cudaFree(out);
+  cudaGetLastError();
   return s;
 }
 

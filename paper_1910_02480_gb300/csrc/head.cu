@@ -12,6 +12,9 @@
 // staged 64 at a time: the 9x9 input window transposed to [c][pixel] and the
 // weights as [tap][c] float4 (o = 0..2).
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include <cstdint>
 #include <cuda_runtime.h>
 
 #include "head.cuh"
@@ -25,16 +28,28 @@ constexpr int HC = 64;       // channels staged per pass
 // Four consecutive channels (16-byte fp32 / 8-byte bf16 aligned: C and the
 // channel offset are multiples of 4).
 template <typename ActT>
-__device__ __forceinline__ float4 load_act4(const ActT *p);
+__device__ __forceinline__ float4 load_act4(const ActT *p, const float *scale);
 template <>
-__device__ __forceinline__ float4 load_act4<float>(const float *p) {
+__device__ __forceinline__ float4 load_act4<float>(const float *p, const float *) {
   return __ldg(reinterpret_cast<const float4 *>(p));
 }
 template <>
-__device__ __forceinline__ float4 load_act4<__nv_bfloat16>(const __nv_bfloat16 *p) {
+__device__ __forceinline__ float4 load_act4<__nv_bfloat16>(const __nv_bfloat16 *p, const float *) {
   const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
   return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
                      __uint_as_float(u.y & 0xffff0000u));
+}
+// e4m3 (4-byte aligned: C and the channel offset are multiples of 4), times
+// the channels' scales.
+template <>
+__device__ __forceinline__ float4 load_act4<uint8_t>(const uint8_t *p, const float *scale) {
+  const uint32_t w = __ldg(reinterpret_cast<const unsigned int *>(p));
+  const __half2_raw lo = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w & 0xFFFFu), __NV_E4M3);
+  const __half2_raw hi = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w >> 16), __NV_E4M3);
+  const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&lo));
+  const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&hi));
+  const float4 s = __ldg(reinterpret_cast<const float4 *>(scale));
+  return make_float4(a.x * s.x, a.y * s.y, b.x * s.z, b.y * s.w);
 }
 
 template <typename ActT>
@@ -100,7 +115,7 @@ __global__ void __launch_bounds__(256, 4) head_kernel(const __grid_constant__ He
       const int y = a0 + pix / HWIN, xx = b0 + pix % HWIN;
       v[it] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (e < NG && 4 * g < cn && y < a.Hh && xx < a.Wh)
-        v[it] = load_act4<ActT>(x + ((size_t)y * a.Wh + xx) * a.C + c0 + 4 * g);
+        v[it] = load_act4<ActT>(x + ((size_t)y * a.Wh + xx) * a.C + c0 + 4 * g, a.in_scale + c0 + 4 * g);
     }
 #pragma unroll
     for (int it = 0; it < PER; ++it) {
@@ -164,11 +179,13 @@ __global__ void __launch_bounds__(256, 4) head_kernel(const __grid_constant__ He
   }
 }
 
-cudaError_t launch_head(const HeadArgs &a, bool bf16, cudaStream_t st) {
+cudaError_t launch_head(const HeadArgs &a, int prec, cudaStream_t st) {
   const long long tiles = (long long)((a.Hh + HT - 1) / HT) * ((a.Wh + HT - 1) / HT) * a.N;
   if (tiles == 0) return cudaSuccess;
-  if (bf16)
+  if (prec == 1)
     head_kernel<__nv_bfloat16><<<(unsigned)tiles, 256, 0, st>>>(a);
+  else if (prec == 2)
+    head_kernel<uint8_t><<<(unsigned)tiles, 256, 0, st>>>(a);
   else
     head_kernel<float><<<(unsigned)tiles, 256, 0, st>>>(a);
   return cudaGetLastError();
