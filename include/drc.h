@@ -189,18 +189,38 @@ drc_status drc_interpolate_static(const drc_caches *caches, const drc_gbuffer *g
                                   const drc_interp_params *params, float *out_rgb,
                                   void *stream);
 
-/* drc_backward flags */
-#define DRC_BWD_L1_TARGET 0x1u /* target = ground truth [N][3][H][W] (log
-                                  radiance); loss = mean |out - target| */
-#define DRC_BWD_GRAD_OUT 0x2u  /* target = dL/dout [N][3][H][W] */
+/* drc_backward flags (combine one of the first two with DRC_F_ENCODE_INPUT
+ * and DRC_BWD_RECOMPUTE_ENCODER as needed) */
+#define DRC_BWD_L1_TARGET 0x10u /* target = ground truth [N][3][H][W] (log
+                                   radiance); loss = mean |out - target| */
+#define DRC_BWD_GRAD_OUT 0x20u  /* target = dL/dout [N][3][H][W] */
+#define DRC_BWD_RECOMPUTE_ENCODER 0x40u /* activation checkpointing: the
+                                   decoder overwrites the encoder activations
+                                   in place during the forward and the
+                                   encoder is run again before its backward
+                                   (one more encoder pass, less memory) */
 
-/* Gradient of the loss through the network (Sec. 4 training).
- *   in:       device [N][7][H][W] (as drc_denoise; flags may add
- *             DRC_F_ENCODE_INPUT);
+/* Gradient of the loss through the network (Sec. 3.3: the autoencoder is
+ * trained with the L1 loss of Eq. 7 on log radiance).  One call runs the
+ * forward pass on `in`, forms dL/dout, and runs the reverse pass: the output
+ * head, then per decoder stage the weight gradient, bias gradient and data
+ * gradient (a stride-2 convolution with the same weights), then per encoder
+ * stage the same (a transposed convolution), with the ReLU masks and the
+ * skip-connection fan-out.  Data gradients run on the tensor cores in the
+ * context's precision (FP32: split-tf32; BF16: bf16 operands), weight and
+ * bias gradients accumulate in fp32.
+ *   in:       device [N][7][H][W] (as drc_denoise; DRC_F_ENCODE_INPUT may be
+ *             given: the gradient then flows through log1p(s L));
+ *   target:   device [N][3][H][W] (see the flags); the output is the network
+ *             output in log radiance (never decoded);
  *   dweights: device, drc_weight_count() floats, packed like the weights,
  *             overwritten;
  *   dinput:   nullable, device [N][7][H][W];
- *   loss:     nullable, device float scalar (L1_TARGET only).  */
+ *   loss:     nullable, device float scalar, overwritten (L1_TARGET; 0 for
+ *             GRAD_OUT).
+ * FP8 contexts return DRC_ERR_UNSUPPORTED.  The context keeps the training
+ * workspace (activations, ReLU outputs, gradients) in its own device memory,
+ * grown on demand. */
 drc_status drc_backward(drc_ctx *ctx, const float *in, const float *target,
                         int N, int H, int W, unsigned flags, float *dweights,
                         float *dinput, float *loss, void *stream);

@@ -28,7 +28,7 @@ F_DEBUG_STALL = 0x100
 METRIC_IMAGE, METRIC_WORLD = 0, 1
 WP_INVERSE, WP_LINEAR = 0, 1
 INTERP_IRRADIANCE, INTERP_LOOKUP = 0, 1
-BWD_L1_TARGET, BWD_GRAD_OUT = 0x1, 0x2
+BWD_L1_TARGET, BWD_GRAD_OUT, BWD_RECOMPUTE_ENCODER = 0x10, 0x20, 0x40
 
 
 class DrcError(RuntimeError):
@@ -261,16 +261,19 @@ class Context:
         self._check(rc, "drc_interpolate")
         return out
 
-    def backward(self, x, target, flags=BWD_L1_TARGET, dweights=None, dinput=None, loss=None,
-                 stream=None):
+    def backward(self, x, target, flags=BWD_L1_TARGET, want_dinput=False, want_loss=True, stream=None):
+        """drc_backward: (loss or None, dweights [n_weights], dinput or None).
+        flags: BWD_L1_TARGET (target = ground truth) or BWD_GRAD_OUT (target =
+        dL/dout), optionally | F_ENCODE_INPUT | BWD_RECOMPUTE_ENCODER."""
         import torch
         N, C, H, W = x.shape
-        if dweights is None:
-            dweights = torch.empty(self.n_weights, dtype=torch.float32, device=x.device)
+        dweights = torch.empty(self.n_weights, dtype=torch.float32, device=x.device)
+        dinput = torch.empty_like(x) if want_dinput else None
+        loss = torch.empty((), dtype=torch.float32, device=x.device) if want_loss else None
         rc = self._lib.drc_backward(self._ctx, _ptr(x), _ptr(target), N, H, W, flags, _ptr(dweights),
                                     _ptr(dinput), _ptr(loss), _stream(stream))
         self._check(rc, "drc_backward")
-        return dweights
+        return loss, dweights, dinput
 
     def status(self, stream=None):
         """Synchronise and return the latched device status code."""
@@ -358,3 +361,35 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def _autograd_function():
+    import torch
+
+    class DenoiseFunction(torch.autograd.Function):
+        """out = network(x; weights) through drc_denoise; the backward is
+        drc_backward with the incoming gradient (BWD_GRAD_OUT).  The weights
+        tensor must be the values the context holds (set_weights)."""
+
+        @staticmethod
+        def forward(ctx_, x, weights, drc_ctx, flags):
+            ctx_.drc = drc_ctx
+            ctx_.flags = flags
+            ctx_.save_for_backward(x)
+            return drc_ctx.denoise(x.contiguous(), flags=flags & F_ENCODE_INPUT)
+
+        @staticmethod
+        def backward(ctx_, grad_out):
+            (x,) = ctx_.saved_tensors
+            _, dw, dx = ctx_.drc.backward(x.contiguous(), grad_out.contiguous(),
+                                          flags=BWD_GRAD_OUT | (ctx_.flags & F_ENCODE_INPUT),
+                                          want_dinput=ctx_.needs_input_grad[0], want_loss=False)
+            return dx, dw, None, None
+
+    return DenoiseFunction
+
+
+def denoise_autograd(drc_ctx, x, weights, flags=0):
+    """Differentiable denoise: gradients flow to x and to `weights` (a float32
+    CUDA tensor holding the context's packed weights)."""
+    return _autograd_function().apply(x, weights, drc_ctx, flags)

@@ -621,9 +621,53 @@ __device__ __forceinline__ void e4m3x4_to_f32(uint32_t w, float *f) {
 // lane: the load is warp-collective), dequantisation (FP8), bias, ReLU, the
 // skip add, the calibration max (warp-collective), then for a valid row the
 // NHWC store -- e4m3 with the consumer's scales when out_qinv is set.
+// Store 16 values in the kernel's activation type (not e4m3).
+template <int PREC>
+__device__ __forceinline__ void store16(uint8_t *yb, const float (&v)[16]) {
+  if constexpr (PREC == PREC_TF32X3) {
+    float4 *q = reinterpret_cast<float4 *>(yb);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) q[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+  } else {
+    uint4 *q = reinterpret_cast<uint4 *>(yb);
+#pragma unroll
+    for (int e = 0; e < 2; ++e)
+      q[e] = make_uint4(pack_bf16x2(v[8 * e], v[8 * e + 1]), pack_bf16x2(v[8 * e + 2], v[8 * e + 3]),
+                        pack_bf16x2(v[8 * e + 4], v[8 * e + 5]), pack_bf16x2(v[8 * e + 6], v[8 * e + 7]));
+  }
+}
+
+// Zero v[e] where the mask tensor's value is not positive (16 channels at mb).
+template <int PREC>
+__device__ __forceinline__ void apply_mask(const uint8_t *mb, float (&v)[16]) {
+  if constexpr (PREC == PREC_TF32X3) {
+    const float4 *m = reinterpret_cast<const float4 *>(mb);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float4 q = m[e];
+      if (!(q.x > 0.f)) v[4 * e] = 0.f;
+      if (!(q.y > 0.f)) v[4 * e + 1] = 0.f;
+      if (!(q.z > 0.f)) v[4 * e + 2] = 0.f;
+      if (!(q.w > 0.f)) v[4 * e + 3] = 0.f;
+    }
+  } else {
+    const uint4 *m = reinterpret_cast<const uint4 *>(mb);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const uint4 q = m[e];
+      const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        if (!(bf16_lo(w[h]) > 0.f)) v[8 * e + 2 * h] = 0.f;
+        if (!(bf16_hi(w[h]) > 0.f)) v[8 * e + 2 * h + 1] = 0.f;
+      }
+    }
+  }
+}
+
 template <int PREC>
 __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int cc, int BN, int col0, bool vrow,
-                                          bool has_skip, const uint4 (&sk)[4], uint8_t *yb) {
+                                          bool has_skip, const uint4 (&sk)[4], uint8_t *yb, size_t eoff) {
   float v[16];
   tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
   const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
@@ -639,6 +683,10 @@ __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int
       if (a.relu) z = fmaxf(z, 0.f);
       v[4 * e4 + e] = z;
     }
+  }
+  if constexpr (PREC != PREC_FP8) {
+    if (a.y2 && a.y2_pre_skip && vrow)
+      store16<PREC>(reinterpret_cast<uint8_t *>(a.y2) + eoff * sizeof(typename PrecTraits<PREC>::act_t), v);
   }
   if (has_skip) {
     if constexpr (PREC == PREC_TF32X3) {
@@ -679,6 +727,11 @@ __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int
     }
   }
   if (!vrow) return;
+  if constexpr (PREC != PREC_FP8) {
+    constexpr int AB = sizeof(typename PrecTraits<PREC>::act_t);
+    if (a.y2 && !a.y2_pre_skip) store16<PREC>(reinterpret_cast<uint8_t *>(a.y2) + eoff * AB, v);
+    if (a.mask) apply_mask<PREC>(reinterpret_cast<const uint8_t *>(a.mask) + eoff * AB, v);
+  }
   if (a.out_qinv) {
     const float *qi = a.out_qinv + col0;
     uint4 o;
@@ -688,16 +741,8 @@ __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int
     o.w = pack_e4m3x4(v[12] * __ldg(qi + 12), v[13] * __ldg(qi + 13), v[14] * __ldg(qi + 14),
                       v[15] * __ldg(qi + 15));
     *reinterpret_cast<uint4 *>(yb) = o;
-  } else if constexpr (PREC == PREC_TF32X3) {
-    float4 *q = reinterpret_cast<float4 *>(yb);
-#pragma unroll
-    for (int e = 0; e < 4; ++e) q[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
-  } else {
-    uint4 *q = reinterpret_cast<uint4 *>(yb);
-#pragma unroll
-    for (int e = 0; e < 2; ++e)
-      q[e] = make_uint4(pack_bf16x2(v[8 * e], v[8 * e + 1]), pack_bf16x2(v[8 * e + 2], v[8 * e + 3]),
-                        pack_bf16x2(v[8 * e + 4], v[8 * e + 5]), pack_bf16x2(v[8 * e + 6], v[8 * e + 7]));
+  } else if constexpr (PREC != PREC_FP8) {
+    store16<PREC>(yb, v);
   }
 }
 
@@ -923,11 +968,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
       uint8_t *yb = yout + ebase * out_elem;
       for (int cc = 0; cc < nch; cc += 2) {
-        epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk0, yb + cc * 16 * out_elem);
+        epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk0, yb + cc * 16 * out_elem,
+                        ebase + cc * 16);
         if (has_skip && cc + 2 < nch) load_skip<PREC>(skip + ebase + (cc + 2) * 16, sk0);
         if (cc + 1 < nch) {
           epi_chunk<PREC>(a, taddr, cc + 1, BN, tc.n_tile * BN + (cc + 1) * 16, vrow, has_skip, sk1,
-                          yb + (cc + 1) * 16 * out_elem);
+                          yb + (cc + 1) * 16 * out_elem, ebase + (cc + 1) * 16);
           if (has_skip && cc + 3 < nch) load_skip<PREC>(skip + ebase + (cc + 3) * 16, sk1);
         }
       }
@@ -1036,7 +1082,9 @@ __device__ float raw_weight(const PackArgs &p, const PhaseDesc &pd, int col, int
   if (p.kind == LK_CONV)  // W[o][c][u][v], tap t = 3u + v
     return p.wraw[((size_t)col * p.Cin_raw + c) * 9 + t];
   // LK_CONVT: W[c][o][u][v] with the phase's kernel tap
-  return p.wraw[(((size_t)c * p.Cout + col) * 3 + pd.u[t]) * 3 + pd.v[t]];
+  const int co = p.Cout_raw > 0 ? p.Cout_raw : p.Cout;
+  if (col >= co) return 0.f;
+  return p.wraw[(((size_t)c * co + col) * 3 + pd.u[t]) * 3 + pd.v[t]];
 }
 
 template <int PREC>

@@ -68,6 +68,13 @@ struct ConvArgs {
                            // of the consuming layer's input scale); else in the kernel's activation type
   const float *skip_scale; // FP8 kernel: the e4m3 skip tensor's per-channel scales
   unsigned *amax;          // nullable: per output column max |output| before quantisation (calibration)
+  // Training: y2 (nullable, NHWC like y) receives the value before the skip
+  // add (y2_pre_skip = 1: the decoder's ReLU output) or before the mask
+  // (y2_pre_skip = 0: an unmasked gradient); mask (nullable, NHWC like y)
+  // zeroes the output where mask <= 0 (the ReLU derivative).
+  void *y2;
+  int y2_pre_skip;
+  const void *mask;
   int *status;
   unsigned long long timeout_ns;
   int debug_stall;
@@ -96,6 +103,7 @@ struct PackArgs {
   const float *wraw;  // this layer's raw weights (start of W)
   int Cin, Cout;      // GEMM channels: Cin as stored in the activations
   int Cin_raw;        // channels of the raw weights (Cin_raw <= Cin; the rest pack as 0)
+  int Cout_raw;       // LK_CONVT: output channels of the raw weights (<= Cout; the rest pack as 0)
   int BN, n_tiles, num_phases;
   PhaseDesc ph[4];
   uint8_t *B, *B_lo;  // packed outputs

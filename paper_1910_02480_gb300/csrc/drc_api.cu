@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "backward.cuh"
 #include "conv_tc.cuh"
 #include "drc.h"
 #include "head.cuh"
@@ -30,6 +31,7 @@ struct Layer {
   int kind;
   int Cin, Cout;       // GEMM channels (Cin as stored in the input activations; LK_HEAD: Cout = 3)
   int Cin_raw;         // channels of the raw weights (7 for the first layer, whose input is padded to 8)
+  int Cout_raw;        // LK_CONVT read of conv weights (data gradient): their input channels; 0 = Cout
   size_t w_off, b_off; // offsets (floats) into the packed raw weights
   int BN, n_tiles, num_phases;
   PhaseDesc ph[4];
@@ -51,6 +53,13 @@ struct drc_ctx {
   size_t n_floats = 0;
   std::vector<Layer> layers;  // conv_1..conv_S, convT_S..convT_2, head
   std::vector<int> modes;     // per layer: A-operand path chosen by drc_autotune (-1 = default)
+  std::vector<Layer> dlayers; // data-gradient GEMMs of conv_1..conv_S, convT_S..convT_2 (training)
+  uint8_t *d_dpack = nullptr, *d_dpack_lo = nullptr;
+  size_t dpack_total = 0;
+  unsigned long long dpack_version = 0;  // weights_version the data-gradient operands were packed from
+  void *d_train = nullptr;
+  size_t train_bytes = 0;
+  float *d_zero = nullptr;              // zero bias of the data-gradient GEMMs
   float *d_wraw = nullptr;
   uint8_t *d_pack = nullptr, *d_pack_lo = nullptr;
   float *d_bscale = nullptr;   // FP8: per-layer output-column dequantisation scales
@@ -375,6 +384,7 @@ drc_status pack_layers(drc_ctx *c, const std::vector<Layer> &Ls, uint8_t *B, uin
     p.wraw = c->d_wraw + L.w_off;
     p.Cin = L.Cin;
     p.Cin_raw = L.Cin_raw;
+    p.Cout_raw = L.Cout_raw;
     p.Cout = L.Cout;
     p.BN = L.BN;
     p.n_tiles = L.n_tiles;
@@ -607,6 +617,210 @@ std::vector<int> bn_candidates(const Layer &L) {
 
 }  // namespace
 
+namespace {
+
+// ---------------------------------------------------------------- training
+
+// Data-gradient GEMMs: the gradient of a stride-2 conv w.r.t. its input is a
+// transposed conv of the output gradient with the same weights (roles of
+// input and output channels swapped), and that of a transposed conv is a
+// stride-2 conv -- so encoder conv e_s becomes an LK_CONVT layer (Cin = c_s,
+// Cout = c_{s-1}; the first layer's 7 input channels padded to 16) and
+// decoder convT d_s an LK_CONV layer (Cin = c_{s-1}, Cout = c_s), both
+// reading the forward layer's raw weights.
+void plan_dgrad_layers(drc_ctx *c) {
+  const int S = c->cfg.num_stages;
+  const int bke = bke_of(c->prec);
+  c->dlayers.clear();
+  for (size_t li = 0; li + 1 < c->layers.size(); ++li) {
+    const Layer &F = c->layers[li];
+    Layer L;
+    memset(&L, 0, sizeof L);
+    L.prec = c->prec;
+    L.w_off = F.w_off;
+    L.b_off = F.b_off;
+    if (F.kind == LK_CONV) {
+      L.kind = LK_CONVT;
+      L.Cin = L.Cin_raw = F.Cout;
+      L.Cout_raw = F.Cin_raw;
+      L.Cout = F.Cin_raw < 16 ? 16 : F.Cin_raw;
+      set_bn(L, pick_bn(L.Cout));
+      L.num_phases = 4;
+      for (int p = 0; p < 4; ++p) convT_phase(L.ph[p], p >> 1, p & 1, L.Cin, bke);
+      snprintf(L.name, sizeof L.name, "dgrad e%d", (int)li + 1);
+    } else {
+      L.kind = LK_CONV;
+      L.Cin = L.Cin_raw = F.Cout;
+      L.Cout = F.Cin;
+      set_bn(L, pick_bn(L.Cout));
+      L.num_phases = 1;
+      PhaseDesc &pd = L.ph[0];
+      pd.ntaps = 9;
+      for (int t = 0; t < 9; ++t) {
+        pd.u[t] = pd.dy[t] = (signed char)(t / 3);
+        pd.v[t] = pd.dx[t] = (signed char)(t % 3);
+      }
+      pd.num_kb = ceil_div(9ll * L.Cin, bke);
+      snprintf(L.name, sizeof L.name, "dgrad d%d", S - ((int)li - S));
+    }
+    for (int p = 0; p < 4; ++p) L.phase_order[p] = p < L.num_phases ? p : 0;
+    for (int a = 0; a < L.num_phases; ++a)
+      for (int b = a + 1; b < L.num_phases; ++b)
+        if (L.ph[L.phase_order[b]].num_kb > L.ph[L.phase_order[a]].num_kb) {
+          const int t = L.phase_order[a];
+          L.phase_order[a] = L.phase_order[b];
+          L.phase_order[b] = t;
+        }
+    c->dlayers.push_back(L);
+  }
+  c->dpack_total = layout_packs(c->dlayers);
+}
+
+drc_status ensure_dgrad_pack(drc_ctx *c, cudaStream_t st) {
+  if (c->dlayers.empty()) {
+    plan_dgrad_layers(c);
+    cudaError_t e = cudaMalloc(&c->d_dpack, c->dpack_total);
+    if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&c->d_dpack_lo, c->dpack_total);
+    if (e != cudaSuccess) {
+      c->dlayers.clear();
+      return cuda_fail(c, e, "data-gradient operands");
+    }
+    c->dpack_version = 0;
+  }
+  if (c->dpack_version == c->weights_version) return DRC_OK;
+  drc_status s = pack_layers(c, c->dlayers, c->d_dpack, c->d_dpack_lo, st);
+  if (s == DRC_OK) c->dpack_version = c->weights_version;
+  return s;
+}
+
+// Training workspace: activation level q is (H >> q) x (W >> q) x c_q.
+struct TrainBufs {
+  uint8_t *in8 = nullptr;                 // level 0, 8 channels
+  std::vector<uint8_t *> e, t, r;         // e[q] q=1..S; t[q] q=1..S-1; r[s] (output of d_s, level s-1) s=2..S
+  std::vector<uint8_t *> Gt, gzd, gze;    // grad w.r.t. t_q (unmasked) and masked by r_{q+1}; encoder grad z_q
+  float *out = nullptr, *g4 = nullptr;    // network output [N][3][H][W]; dL/dout NHWC4
+  uint8_t *dx16 = nullptr;                // input gradient NHWC16
+  double *dW64 = nullptr;                 // FP32 path: fp64 accumulation of the weight gradients
+};
+
+size_t train_layout(const drc_ctx *c, int N, int H, int W, bool recompute, void *base, TrainBufs *tb) {
+  const int S = c->cfg.num_stages;
+  const size_t eb = elem_act(c->prec);
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> uint8_t * {
+    uint8_t *p = base ? static_cast<uint8_t *>(base) + off : nullptr;
+    off += (bytes + 255) & ~(size_t)255;
+    return p;
+  };
+  auto level = [&](int q) { return (size_t)N * (H >> q) * (W >> q) * c->cfg.widths[q - 1] * eb; };
+  TrainBufs b;
+  b.e.assign(S + 1, nullptr);
+  b.t.assign(S + 1, nullptr);
+  b.r.assign(S + 1, nullptr);
+  b.Gt.assign(S + 1, nullptr);
+  b.gzd.assign(S + 1, nullptr);
+  b.gze.assign(S + 1, nullptr);
+  b.in8 = take((size_t)N * H * W * 8 * eb);
+  for (int q = 1; q <= S; ++q) b.e[q] = take(level(q));
+  for (int q = 1; q < S; ++q) b.t[q] = recompute ? b.e[q] : take(level(q));
+  for (int s2 = 2; s2 <= S; ++s2) b.r[s2] = take(level(s2 - 1));
+  for (int q = 1; q < S; ++q) {
+    b.Gt[q] = take(level(q));
+    b.gzd[q] = take(level(q));
+  }
+  for (int q = 1; q <= S; ++q) b.gze[q] = take(level(q));
+  b.out = reinterpret_cast<float *>(take((size_t)N * 3 * H * W * sizeof(float)));
+  b.g4 = reinterpret_cast<float *>(take((size_t)N * H * W * 4 * sizeof(float)));
+  b.dx16 = take((size_t)N * H * W * 16 * eb);
+  if (c->prec == PREC_TF32X3) b.dW64 = reinterpret_cast<double *>(take(c->n_floats * sizeof(double)));
+  if (tb) *tb = b;
+  return off;
+}
+
+// ConvArgs of layer L on explicit buffers (input Hin x Win, N maps).
+void train_conv_args(const drc_ctx *c, const Layer &L, const uint8_t *B, const uint8_t *B_lo, int N, int Hin,
+                     int Win, const void *x, void *y, const void *skip, int relu, const float *bias, ConvArgs &a) {
+  fill_common(c, L, B, B_lo, a);
+  a.N = N;
+  a.x = x;
+  a.y = y;
+  a.skip = skip;
+  a.Hin = Hin;
+  a.Win = Win;
+  a.Cin = L.Cin;
+  a.Cout = L.Cout;
+  if (L.kind == LK_CONV) {
+    a.Hrow = a.Hout = Hin / 2;
+    a.Wrow = a.Wout = Win / 2;
+  } else {
+    a.Hrow = Hin;
+    a.Wrow = Win;
+    a.Hout = 2 * Hin;
+    a.Wout = 2 * Win;
+  }
+  a.relu = relu;
+  a.bias = bias;
+  a.M = (int)((long long)N * a.Hrow * a.Wrow);
+  a.m_tiles = ceil_div(a.M, BM);
+}
+
+// Forward pass keeping what the reverse pass needs: e_q, t_q, the decoder
+// ReLU outputs r_s (before the skip add), the output.  encoder_only: run
+// e_1..e_S again (activation checkpointing).
+drc_status train_forward(drc_ctx *c, const TrainBufs &b, const float *in, int N, int H, int W, unsigned flags,
+                         bool encoder_only, cudaStream_t st) {
+  const int S = c->cfg.num_stages;
+  const bool bf = c->prec != PREC_TF32X3;
+  Tracer *tr = &c->tracer;
+  cudaError_t e;
+  if (!encoder_only) {
+    DRC_TRACED(tr, "stage input", st,
+               e = launch_nchw7_to_nhwc8(in, b.in8, (long long)H * W, N, bf, (flags & DRC_F_ENCODE_INPUT) != 0,
+                                         c->cfg.exposure, st));
+    if (e != cudaSuccess) return cuda_fail(c, e, "input staging");
+  }
+  for (int s2 = 1; s2 <= S; ++s2) {
+    const Layer &L = c->layers[s2 - 1];
+    ConvArgs a;
+    train_conv_args(c, L, c->d_pack, c->d_pack_lo, N, H >> (s2 - 1), W >> (s2 - 1),
+                    s2 == 1 ? (const void *)b.in8 : b.e[s2 - 1], b.e[s2], nullptr, 1, c->d_wraw + L.b_off, a);
+    plan_operand(L.prec, a, c->modes[s2 - 1]);
+    DRC_TRACED(tr, L.name, st, e = launch_conv(a, L.prec, c->num_sms, st));
+    if (e != cudaSuccess) return cuda_fail(c, e, "encoder launch");
+  }
+  if (encoder_only) return DRC_OK;
+  for (int s2 = S; s2 >= 2; --s2) {
+    const size_t li = (size_t)(2 * S - s2);
+    const Layer &L = c->layers[li];
+    ConvArgs a;
+    train_conv_args(c, L, c->d_pack, c->d_pack_lo, N, H >> s2, W >> s2, s2 == S ? b.e[S] : b.t[s2], b.t[s2 - 1],
+                    b.e[s2 - 1], 1, c->d_wraw + L.b_off, a);
+    a.y2 = b.r[s2];
+    a.y2_pre_skip = 1;
+    plan_operand(L.prec, a, c->modes[li]);
+    DRC_TRACED(tr, L.name, st, e = launch_conv(a, L.prec, c->num_sms, st));
+    if (e != cudaSuccess) return cuda_fail(c, e, "decoder launch");
+  }
+  const Layer &Lh = c->layers.back();
+  HeadArgs h;
+  memset(&h, 0, sizeof h);
+  h.x = S >= 2 ? b.t[1] : b.e[1];
+  h.out = b.out;
+  h.w = c->d_wraw + Lh.w_off;
+  h.bias = c->d_wraw + Lh.b_off;
+  h.N = N;
+  h.Hh = H >> 1;
+  h.Wh = W >> 1;
+  h.C = Lh.Cin;
+  h.relu = c->cfg.out_relu ? 1 : 0;
+  h.inv_exposure = 1.0f / c->cfg.exposure;
+  DRC_TRACED(tr, Lh.name, st, e = launch_head(h, c->prec, st));
+  if (e != cudaSuccess) return cuda_fail(c, e, "head launch");
+  return DRC_OK;
+}
+
+}  // namespace
+
 struct drc_plan {
   drc_ctx *ctx = nullptr;
   unsigned flags = 0;
@@ -765,6 +979,8 @@ drc_status drc_create(const drc_config *cfg, const float *weights_host, size_t n
   if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&c->d_pack_lo, c->pack_total);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_zero, 1024 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(c->d_zero, 0, 1024 * sizeof(float));
   if (e == cudaSuccess && c->prec == PREC_FP8) {
     // activation scales start at 1 (values up to the e4m3 maximum, 448)
     // until drc_calibrate measures the network's activations
@@ -830,6 +1046,10 @@ drc_status drc_destroy(drc_ctx *c) {
   cudaFree(c->d_pack_lo);
   cudaFree(c->d_bscale);
   cudaFree(c->d_inscale);
+  cudaFree(c->d_dpack);
+  cudaFree(c->d_dpack_lo);
+  cudaFree(c->d_train);
+  cudaFree(c->d_zero);
   cudaFree(c->d_qinv);
   cudaFree(c->d_amax);
   cudaFree(c->d_act);
@@ -988,18 +1208,139 @@ drc_status drc_interpolate(drc_ctx *c, const drc_caches *caches, const drc_gbuff
 
 drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N, int H, int W, unsigned flags,
                         float *dweights, float *dinput, float *loss, void *stream) {
-  (void)in;
-  (void)target;
-  (void)N;
-  (void)H;
-  (void)W;
-  (void)flags;
-  (void)dweights;
-  (void)dinput;
-  (void)loss;
-  (void)stream;
   if (!c) return DRC_ERR_INVALID_ARG;
-  return fail(c, DRC_ERR_UNSUPPORTED, "backward is not built yet");
+  c->err.clear();
+  if (c->prec == PREC_FP8) return fail(c, DRC_ERR_UNSUPPORTED, "backward runs in FP32 or BF16 contexts");
+  const int S = c->cfg.num_stages;
+  const unsigned known = DRC_F_ENCODE_INPUT | DRC_BWD_L1_TARGET | DRC_BWD_GRAD_OUT | DRC_BWD_RECOMPUTE_ENCODER;
+  if (flags & ~known) return fail(c, DRC_ERR_INVALID_ARG, "unknown flags 0x%x", flags & ~known);
+  const bool grad_out = (flags & DRC_BWD_GRAD_OUT) != 0;
+  if (grad_out == ((flags & DRC_BWD_L1_TARGET) != 0))
+    return fail(c, DRC_ERR_INVALID_ARG, "give exactly one of DRC_BWD_L1_TARGET and DRC_BWD_GRAD_OUT");
+  if (N < 1) return fail(c, DRC_ERR_INVALID_ARG, "N must be >= 1");
+  if (H < (1 << S) || W < (1 << S) || H % (1 << S) || W % (1 << S))
+    return fail(c, DRC_ERR_INVALID_ARG, "H, W (%d, %d) must be positive multiples of 2^S = %d", H, W, 1 << S);
+  if ((long long)N * H * W * 16 >= (1ll << 31))
+    return fail(c, DRC_ERR_INVALID_ARG, "N*16*H*W must stay below 2^31 elements per call");
+  if (!c->weights_set) return fail(c, DRC_ERR_INVALID_ARG, "weights were never set");
+  drc_status s;
+  if ((s = check_dev(c, in, "in", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, target, "target", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, dweights, "dweights", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, dinput, "dinput", true)) != DRC_OK) return s;
+  if ((s = check_dev(c, loss, "loss", true)) != DRC_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if ((s = ensure_dgrad_pack(c, st)) != DRC_OK) return s;
+  const bool recompute = (flags & DRC_BWD_RECOMPUTE_ENCODER) != 0;
+  const size_t need = train_layout(c, N, H, W, recompute, nullptr, nullptr);
+  cudaError_t e;
+  if (need > c->train_bytes) {
+    cudaFree(c->d_train);
+    c->d_train = nullptr;
+    c->train_bytes = 0;
+    if ((e = cudaMalloc(&c->d_train, need)) != cudaSuccess) return cuda_fail(c, e, "training workspace");
+    c->train_bytes = need;
+  }
+  TrainBufs b;
+  train_layout(c, N, H, W, recompute, c->d_train, &b);
+  const bool bf = c->prec != PREC_TF32X3;
+  Tracer *tr = &c->tracer;
+  if ((e = cudaMemsetAsync(dweights, 0, c->n_floats * sizeof(float), st)) != cudaSuccess)
+    return cuda_fail(c, e, "dweights clear");
+  if (b.dW64 && (e = cudaMemsetAsync(b.dW64, 0, c->n_floats * sizeof(double), st)) != cudaSuccess)
+    return cuda_fail(c, e, "dweights clear");
+  double *const w64 = b.dW64;
+  auto o64 = [&](size_t off) -> double * { return w64 ? w64 + off : nullptr; };
+  if (loss && (e = cudaMemsetAsync(loss, 0, sizeof(float), st)) != cudaSuccess) return cuda_fail(c, e, "loss clear");
+
+  if ((s = train_forward(c, b, in, N, H, W, flags, false, st)) != DRC_OK) return s;
+  DRC_TRACED(tr, "loss", st, e = launch_l1_grad(b.out, target, N, H, W, grad_out, c->cfg.out_relu != 0, b.g4, loss, st));
+  if (e != cudaSuccess) return cuda_fail(c, e, "loss");
+
+  // output head: t_1 -> out; the gradient w.r.t. t_1 is masked by the ReLU of
+  // d_2 (or of e_1 when there is no decoder stage)
+  const Layer &Lh = c->layers.back();
+  const int c1 = c->cfg.widths[0];
+  DRC_TRACED(tr, "head bwd", st,
+             e = launch_head_bwd(b.g4, c->d_wraw + Lh.w_off, S >= 2 ? (const void *)b.r[2] : b.e[1],
+                                 S >= 2 ? (void *)b.Gt[1] : nullptr, S >= 2 ? b.gzd[1] : b.gze[1], N, H >> 1, W >> 1,
+                                 c1, bf, st));
+  if (e != cudaSuccess) return cuda_fail(c, e, "head backward");
+  DRC_TRACED(tr, "wgrad head", st,
+             e = launch_wgrad(S >= 2 ? b.t[1] : b.e[1], bf, b.g4, false, N, H >> 1, W >> 1, c1, 4, 3,
+                              dweights + Lh.w_off, o64(Lh.w_off), c->num_sms, st));
+  if (e == cudaSuccess)
+    DRC_TRACED(tr, "bgrad head", st,
+               e = launch_colsum(b.g4, false, (long long)N * H * W, 4, 3, dweights + Lh.b_off, o64(Lh.b_off),
+                                 c->num_sms, st));
+  if (e != cudaSuccess) return cuda_fail(c, e, "head weight gradient");
+
+  // decoder, from the output inwards: t_{s-1} = r_s + e_{s-1},
+  // r_s = ReLU(convT_s(t_s) + b)
+  for (int s2 = 2; s2 <= S; ++s2) {
+    const size_t li = (size_t)(2 * S - s2);
+    const Layer &F = c->layers[li], &D = c->dlayers[li];
+    const void *tin = s2 == S ? b.e[S] : b.t[s2];
+    const long long npix = (long long)N * (H >> (s2 - 1)) * (W >> (s2 - 1));
+    DRC_TRACED(tr, "wgrad", st,
+               e = launch_wgrad(tin, bf, b.gzd[s2 - 1], bf, N, H >> s2, W >> s2, F.Cin, F.Cout, F.Cout,
+                                dweights + F.w_off, o64(F.w_off), c->num_sms, st));
+    if (e == cudaSuccess)
+      DRC_TRACED(tr, "bgrad", st,
+                 e = launch_colsum(b.gzd[s2 - 1], bf, npix, F.Cout, F.Cout, dweights + F.b_off, o64(F.b_off),
+                                   c->num_sms, st));
+    if (e != cudaSuccess) return cuda_fail(c, e, "decoder weight gradient");
+    ConvArgs a;
+    train_conv_args(c, D, c->d_dpack, c->d_dpack_lo, N, H >> (s2 - 1), W >> (s2 - 1), b.gzd[s2 - 1],
+                    s2 < S ? b.gzd[s2] : b.gze[S], nullptr, 0, c->d_zero, a);
+    if (s2 < S) {
+      a.y2 = b.Gt[s2];
+      a.y2_pre_skip = 0;
+      a.mask = b.r[s2 + 1];
+    } else {
+      a.mask = b.e[S];
+    }
+    plan_operand(D.prec, a, -1);
+    DRC_TRACED(tr, D.name, st, e = launch_conv(a, D.prec, c->num_sms, st));
+    if (e != cudaSuccess) return cuda_fail(c, e, "decoder data gradient");
+  }
+  if (recompute && (s = train_forward(c, b, in, N, H, W, flags, true, st)) != DRC_OK) return s;
+
+  // encoder, from the bottleneck outwards: e_s = ReLU(conv_s(e_{s-1}) + b);
+  // the gradient w.r.t. e_{s-1} adds the skip branch's Gt_{s-1}
+  for (int s2 = S; s2 >= 1; --s2) {
+    const size_t li = (size_t)(s2 - 1);
+    const Layer &F = c->layers[li], &D = c->dlayers[li];
+    const long long npix = (long long)N * (H >> s2) * (W >> s2);
+    const void *xin = s2 == 1 ? (const void *)b.in8 : b.e[s2 - 1];
+    DRC_TRACED(tr, "wgrad", st,
+               e = launch_wgrad(b.gze[s2], bf, xin, bf, N, H >> s2, W >> s2, F.Cout, F.Cin, F.Cin_raw,
+                                dweights + F.w_off, o64(F.w_off), c->num_sms, st));
+    if (e == cudaSuccess)
+      DRC_TRACED(tr, "bgrad", st,
+                 e = launch_colsum(b.gze[s2], bf, npix, F.Cout, F.Cout, dweights + F.b_off, o64(F.b_off),
+                                   c->num_sms, st));
+    if (e != cudaSuccess) return cuda_fail(c, e, "encoder weight gradient");
+    if (s2 == 1 && !dinput) break;
+    ConvArgs a;
+    train_conv_args(c, D, c->d_dpack, c->d_dpack_lo, N, H >> s2, W >> s2, b.gze[s2], s2 > 1 ? b.gze[s2 - 1] : b.dx16,
+                    s2 > 1 ? (const void *)b.Gt[s2 - 1] : nullptr, 0, c->d_zero, a);
+    if (s2 > 1) a.mask = b.e[s2 - 1];
+    plan_operand(D.prec, a, -1);
+    DRC_TRACED(tr, D.name, st, e = launch_conv(a, D.prec, c->num_sms, st));
+    if (e != cudaSuccess) return cuda_fail(c, e, "encoder data gradient");
+  }
+  if (w64) {
+    DRC_TRACED(tr, "dweights f32", st, e = launch_to_f32(w64, (long long)c->n_floats, dweights, st));
+    if (e != cudaSuccess) return cuda_fail(c, e, "dweights");
+  }
+  if (dinput) {
+    DRC_TRACED(tr, "input grad", st,
+               e = launch_dinput(b.dx16, bf, in, (long long)H * W, N, (flags & DRC_F_ENCODE_INPUT) != 0,
+                                 c->cfg.exposure, dinput, st));
+    if (e != cudaSuccess) return cuda_fail(c, e, "input gradient");
+  }
+  return DRC_OK;
 }
 
 drc_status drc_get_status(drc_ctx *c, void *stream) {
