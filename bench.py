@@ -257,6 +257,50 @@ def measure_uneven(drc, torch, dev, prec="bf16", reps=3):
             "autotuned_tile_n": tiles, "autotune_s": tune_s}
 
 
+def measure_training(drc, torch, dev, prec="bf16", batch=256, steps=10):
+    """One training step = drc_backward on a batch of noisy / clean pairs of
+    7 x 64 x 64 maps (clean = the analytic lobe field, noisy = Poisson(4)/4
+    per texel, L1 on log radiance), widths 64/128/256/512: forward, loss and
+    the whole reverse pass (weight, bias and input-side gradients)."""
+    from paper_1910_02480_gb300 import synth
+    widths = [64, 128, 256, 512]
+    H = W = 64
+    w = synth.he_weights(widths, seed=0)
+    g = synth.gbuffer(batch, 1, seed=15)
+    x, clean = synth.hemisphere_maps(g["pos"], g["nrm"], H=H, W=W, seed=5, noise="poisson", spp=4)
+    xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev)
+    td = torch.from_numpy(np.ascontiguousarray(clean, dtype=np.float32)).to(dev)
+    ctx = drc.Context(widths, w, precision=prec)
+    for _ in range(3):
+        ctx.backward(xd, td)
+    torch.cuda.synchronize()
+    ctx.read_timing()
+    ctx.set_timing(True)
+    a, b = _events(torch)
+    a.record()
+    for _ in range(steps):
+        loss, _, _ = ctx.backward(xd, td)
+    b.record()
+    torch.cuda.synchronize()
+    ctx.set_timing(False)
+    kt = ctx.read_timing()
+    if ctx.status() != drc.OK:
+        raise RuntimeError("device status after training steps")
+    ms = a.elapsed_time(b) / steps
+    macs = sum(valid_macs_per_layer(widths, H, W).values())
+    flops_step = 2.0 * macs * batch * 3  # forward + data gradients + weight gradients
+    by = {}
+    for n, (cnt, t) in kt.items():
+        key = n.split()[0] if n.split()[0] in ("conv", "convT", "dgrad", "wgrad", "bgrad") else n
+        by[key] = by.get(key, 0.0) + t / steps
+    ctx.close()
+    return {"workload": "%d noisy/clean pairs 7x%dx%d, widths %s, L1 on log radiance, %s" % (
+                batch, H, W, "/".join(map(str, widths)), prec),
+            "ms_per_step": ms, "maps_per_s": batch / (ms * 1e-3), "loss": float(loss.item()),
+            "approx_flops_per_step": flops_step, "achieved_tflops": flops_step / (ms * 1e-3) / 1e12,
+            "kernel_ms_per_step": {k: round(v, 4) for k, v in sorted(by.items(), key=lambda kv: -kv[1])}}
+
+
 def make_inputs(seed_offset=0):
     from paper_1910_02480_gb300 import synth
     g = synth.gbuffer(IMG_W, IMG_H, seed=2 + seed_offset)
@@ -506,6 +550,7 @@ def main():
         line["precision_variants"] = {p: measure_precision(drc, torch, dev, p, den * 1e3, not args.no_autotune)
                                       for p in ("bf16", "fp8") if p != args.precision}
         line["uneven_batching"] = measure_uneven(drc, torch, dev)
+        line["training"] = measure_training(drc, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         b = cpu_baseline(w, x, g, c)
         b.pop("step_s", None)
