@@ -69,6 +69,7 @@ struct drc_ctx {
   bool calibrating = false;
   size_t n_scales = 0, n_bscales = 0;
   std::vector<float> h_inscale;
+  std::vector<float> h_headw;  // the head's weights on the host (launch parameters of the head kernel)
   size_t pack_total = 0;
   void *d_act = nullptr;
   size_t act_bytes = 0;
@@ -448,6 +449,15 @@ void fill_common(const drc_ctx *c, const Layer &L, const uint8_t *B, const uint8
   a.timeout_ns = c->timeout_ns;
 }
 
+// The head kernel takes weights of up to 64 input channels in its launch
+// parameters (constant-bank operands).
+void head_inline_weights(const drc_ctx *c, HeadArgs &h) {
+  if (h.C <= 64 && h.C % 16 == 0 && c->h_headw.size() == (size_t)h.C * 27) {
+    memcpy(h.wk, c->h_headw.data(), c->h_headw.size() * sizeof(float));
+    h.inline_w = 1;
+  }
+}
+
 // Activation buffers and geometry of one launch sequence of the network over
 // N maps of H x W (for a plan, N is the class's maximum and the real count is
 // read from device memory).
@@ -555,6 +565,7 @@ drc_status run_chain(drc_ctx *c, const std::vector<Layer> &layers, const uint8_t
       h.inv_exposure = 1.0f / c->cfg.exposure;
       h.slot = ch.slot;
       if (c->prec == PREC_FP8) h.in_scale = c->d_inscale + L.sc_off;
+      head_inline_weights(c, h);
       if (payload || ch.slot) {
         const double pi = 3.14159265358979323846;
         for (int i = 0; i < ch.H; ++i) {
@@ -814,6 +825,7 @@ drc_status train_forward(drc_ctx *c, const TrainBufs &b, const float *in, int N,
   h.C = Lh.Cin;
   h.relu = c->cfg.out_relu ? 1 : 0;
   h.inv_exposure = 1.0f / c->cfg.exposure;
+  head_inline_weights(c, h);
   DRC_TRACED(tr, Lh.name, st, e = launch_head(h, c->prec, st));
   if (e != cudaSuccess) return cuda_fail(c, e, "head launch");
   return DRC_OK;
@@ -833,7 +845,8 @@ struct drc_plan {
   PassSlot *d_slots = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  unsigned long long weights_version = 0;
+  unsigned long long weights_version = 0;  // the context weights the packed operands hold
+  unsigned long long graph_version = 0;    // ... and the graph's head parameters
   int kernels_per_launch = 0;
 };
 
@@ -848,6 +861,33 @@ void plan_free(drc_plan *p) {
   cudaFree(p->d_slots);
   cudaGetLastError();
   delete p;
+}
+
+// Capture the launch sequence of every class into one graph (replacing any
+// earlier one); the kernels read each pass's count and buffers from the
+// plan's slots.  The head's weights travel in its launch parameters, so the
+// graph is captured again whenever the context's weights change.
+drc_status plan_capture(drc_plan *p, cudaStream_t cs) {
+  drc_ctx *c = p->ctx;
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  p->exec = nullptr;
+  p->graph = nullptr;
+  p->kernels_per_launch = 0;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+  drc_status cap = DRC_OK;
+  for (size_t k = 0; cap == DRC_OK && k < p->cls.size(); ++k) {
+    cap = run_chain(c, p->layers[k], p->pack[k], p->pack_lo[k], &p->modes[k], p->chains[k], nullptr, nullptr,
+                    nullptr, 0, cs, nullptr, nullptr);
+    p->kernels_per_launch += 1 + (int)p->layers[k].size();
+  }
+  e = cudaStreamEndCapture(cs, &p->graph);
+  if (cap != DRC_OK) return cap;
+  if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+  if ((e = cudaGraphInstantiate(&p->exec, p->graph, 0)) != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+  p->graph_version = c->weights_version;
+  return DRC_OK;
 }
 
 drc_status plan_pack(drc_plan *p, cudaStream_t st) {
@@ -1031,6 +1071,18 @@ drc_status drc_set_weights(drc_ctx *c, const float *weights, int weights_on_devi
     e = cudaMemcpy(c->d_wraw, weights, c->n_floats * sizeof(float), cudaMemcpyHostToDevice);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "weight upload");
+  {
+    const Layer &Lh = c->layers.back();
+    c->h_headw.assign((size_t)Lh.Cin * 27, 0.f);
+    if (weights_on_device) {  // one synchronisation: the head kernel's parameters need the values
+      if ((e = cudaStreamSynchronize(st)) == cudaSuccess)
+        e = cudaMemcpy(c->h_headw.data(), c->d_wraw + Lh.w_off, c->h_headw.size() * sizeof(float),
+                       cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) return cuda_fail(c, e, "head weights");
+    } else {
+      memcpy(c->h_headw.data(), weights + Lh.w_off, c->h_headw.size() * sizeof(float));
+    }
+  }
   drc_status s = pack_all(c, st);
   if (s == DRC_OK) {
     c->weights_set = true;
@@ -1540,25 +1592,11 @@ drc_status drc_plan_create(drc_ctx *c, const drc_size_class *classes, int n_clas
   }
   if (s == DRC_OK) s = plan_pack(p, cs);
   if (s == DRC_OK && (e = cudaStreamSynchronize(cs)) != cudaSuccess) s = cuda_fail(c, e, "plan packing");
-  // capture the launch sequence of every class into one graph; the kernels
-  // read each pass's count and buffers from the plan's slots
-  if (s == DRC_OK && (e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed)) != cudaSuccess)
-    s = cuda_fail(c, e, "begin capture");
-  if (s == DRC_OK) {
-    drc_status cap = DRC_OK;
-    for (int k = 0; cap == DRC_OK && k < n_classes; ++k) {
-      p->chains[k].count = &p->d_slots[k].count;
-      p->chains[k].slot = &p->d_slots[k];
-      cap = run_chain(c, p->layers[k], p->pack[k], p->pack_lo[k], &p->modes[k], p->chains[k], nullptr, nullptr,
-                      nullptr, 0, cs, nullptr, nullptr);
-      p->kernels_per_launch += 1 + (int)p->layers[k].size();
-    }
-    e = cudaStreamEndCapture(cs, &p->graph);
-    if (cap != DRC_OK) s = cap;
-    else if (e != cudaSuccess) s = cuda_fail(c, e, "end capture");
+  for (int k = 0; k < n_classes; ++k) {
+    p->chains[k].count = &p->d_slots[k].count;
+    p->chains[k].slot = &p->d_slots[k];
   }
-  if (s == DRC_OK && (e = cudaGraphInstantiate(&p->exec, p->graph, 0)) != cudaSuccess)
-    s = cuda_fail(c, e, "graph instantiate");
+  if (s == DRC_OK) s = plan_capture(p, cs);
   if (cs) cudaStreamDestroy(cs);
   if (s != DRC_OK) {
     plan_free(p);
@@ -1593,6 +1631,14 @@ drc_status drc_plan_launch(drc_plan *p, const int *counts, const float *const *i
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (p->weights_version != c->weights_version && (s = plan_pack(p, st)) != DRC_OK) return s;
+  if (p->graph_version != c->weights_version) {
+    cudaStream_t cs = nullptr;
+    cudaError_t ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (ce != cudaSuccess) return cuda_fail(c, ce, "plan stream");
+    s = plan_capture(p, cs);
+    cudaStreamDestroy(cs);
+    if (s != DRC_OK) return s;
+  }
   cudaError_t e;
   DRC_TRACED(&c->tracer, "plan slots", st,
              (set_slots_kernel<<<1, 32, 0, st>>>(u, counts, p->d_slots, c->d_status), e = cudaGetLastError()));

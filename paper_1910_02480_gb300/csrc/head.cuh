@@ -19,6 +19,8 @@ struct HeadArgs {
   const PassSlot *slot; // nullable: out, payload, count (<= N) and decode flag from device memory
   const float *in_scale;  // e4m3 input: per-channel scales
   float band[256];      // payload weight of each output row
+  int inline_w;         // wk holds the weights (C <= 64, C % 16 == 0)
+  float wk[64 * 27];    // the weights again, read by the kernel as constant-bank operands
 };
 
 // prec: the activation precision of the context (0 fp32, 1 bf16, 2 e4m3).
