@@ -336,29 +336,43 @@ __device__ __forceinline__ void raw_convert_tma(const ConvArgs &a, int pt, const
   }
 }
 
-// PROD_TMA_TMEM step 2: the warp's lane quarter (rows 32 q .. 32 q + 31,
-// q = warp % 4) and half of the K block (chunks 4 h .. 4 h + 3, h = 0 for
-// warps 8..11) go from the raw slot, split into tf32 hi/lo, into the A
-// stage's tensor-memory columns [16 h, 16 h + 16) (hi) and 32 + same (lo).
-__device__ __forceinline__ void raw_convert_tmem(int pt, const uint8_t *slot, uint32_t ta) {
-  const int w = pt >> 5, lane = pt & 31;
-  const int q = w & 3, h = w >> 2;
-  const int r = 32 * q + lane;
-  uint32_t hi[16], lo[16];
+// PROD_TMA_CONVERT step 2 for one group of four producer warps (128
+// threads, gt = thread index in the group): the whole K block, 8 chunks of
+// 128 rows.
+template <int PREC>
+__device__ __forceinline__ void raw_convert_tma_group(int gt, const uint8_t *slot, uint8_t *a0, uint8_t *a1) {
+  const int lane = gt & 31, gw = gt >> 5, q = lane & 7;
 #pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const uint4 u = lds128(slot + swz(r, 4 * h + c));
-    const float x[4] = {__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z), __uint_as_float(u.w)};
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float hf = tf32_rna(x[e]);
-      hi[4 * c + e] = __float_as_uint(hf);
-      lo[4 * c + e] = __float_as_uint(tf32_rna(x[e] - hf));
-    }
+  for (int it = 0; it < 8; ++it) {
+    const int r = (lane >> 3) + 4 * gw + 16 * it;
+    convert_store<PREC>(a0, a1, swz(r, q), reinterpret_cast<const uint4 *>(slot + swz(r, q)));
   }
-  const uint32_t t0 = ta + ((uint32_t)(32 * q) << 16) + (uint32_t)(16 * h);
-  tmem_st16(t0, hi);
-  tmem_st16(t0 + 32, lo);
+}
+
+// PROD_TMA_TMEM step 2: the warp's lane quarter (rows 32 q .. 32 q + 31,
+// q = warp % 4) of the whole K block goes from the raw slot, split into tf32
+// hi/lo, into the A stage's tensor-memory columns [0, 32) (hi) and
+// [32, 64) (lo).
+__device__ __forceinline__ void raw_convert_tmem(int q, int lane, const uint8_t *slot, uint32_t ta) {
+  const int r = 32 * q + lane;
+  const uint32_t t0 = ta + ((uint32_t)(32 * q) << 16);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    uint32_t hi[16], lo[16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const uint4 u = lds128(slot + swz(r, 4 * h + c));
+      const float x[4] = {__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z), __uint_as_float(u.w)};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float hf = tf32_rna(x[e]);
+        hi[4 * c + e] = __float_as_uint(hf);
+        lo[4 * c + e] = __float_as_uint(tf32_rna(x[e] - hf));
+      }
+    }
+    tmem_st16(t0 + 16 * h, hi);
+    tmem_st16(t0 + 32 + 16 * h, lo);
+  }
   tmem_wait_st();
 }
 
@@ -408,6 +422,35 @@ __device__ __forceinline__ void tma_issue(const ConvArgs &a, const TmaCursor &c,
   tma_load_4d(dst, &a.tmap, c0, x, y, c.n0, bar);
 }
 
+// PROD_TMA_CONVERT / PROD_TMA_TMEM step 1, one thread: every raw box of the
+// CTA's K blocks in order, each into ring slot j % R once the group that
+// converted its previous occupant has released it.
+template <int PREC>
+__device__ __noinline__ void tma_issue_loop(const ConvArgs &a, uint32_t raw_u32, uint64_t *raw_full,
+                                            uint64_t *raw_empty, int R, int slot_bytes, int total_tiles) {
+  if ((int)blockIdx.x >= total_tiles) return;
+  int total_kb = 0;
+  for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) total_kb += a.ph[tile_coord(a, t).phase].num_kb;
+  TmaCursor c;
+  c.t = blockIdx.x;
+  c.kb = 0;
+  tma_tile(a, c);
+  unsigned long long w_issue = 0;
+  for (int j = 0; j < total_kb; ++j) {
+    const int slot = j % R;
+    if (!pwait(a, w_issue, smem_u32(&raw_empty[slot]), (uint32_t)(((j / R) & 1) ^ 1))) break;
+    const uint32_t fb = smem_u32(&raw_full[slot]);
+    mbar_arrive_expect_tx(fb, (uint32_t)(BM * KROW_BYTES));
+    tma_issue<PREC>(a, c, raw_u32 + (uint32_t)(slot * slot_bytes), fb);
+    if (++c.kb == c.nkb) {
+      c.kb = 0;
+      c.t += gridDim.x;
+      if (c.t < total_tiles) tma_tile(a, c);
+    }
+  }
+  if (a.prof) atomicAdd(&a.prof[PROF_PROD_ISSUE], w_issue * 8);  // reported per producer warp like the others
+}
+
 // Producer warps.  `raw` is the raw ring (unused in PROD_TMA_DIRECT).
 template <int PREC>
 __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint8_t *raw, uint64_t *full_bar,
@@ -424,7 +467,6 @@ __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint
   for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) total_kb += a.ph[tile_coord(a, t).phase].num_kb;
   unsigned long long w_empty = 0, w_copy = 0, w_conv = 0, w_fence = 0, w_issue = 0;
   const long long t_start = a.prof ? clock64() : 0;
-  const int slot_box = BM * KROW_BYTES;  // TMA bytes per K block
 
   if (a.prod_mode == PROD_TMA_DIRECT) {
     // one thread: wait for the stage, expect the box bytes, load into the A tile
@@ -452,52 +494,25 @@ __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint
       }
     }
   } else if (a.prod_mode == PROD_TMA_CONVERT || a.prod_mode == PROD_TMA_TMEM) {
-    // thread 0 keeps the raw ring R-1 boxes ahead; all 256 threads convert
-    TmaCursor c;
-    int ji = 0;
-    if (pt == 0) {
-      c.t = blockIdx.x;
-      c.kb = 0;
-      tma_tile(a, c);
-    }
-    bool ok = true;
-    auto issue = [&]() {
-      const int slot = ji % R;
-      if (!pwait(a, w_issue, smem_u32(&raw_empty[slot]), (uint32_t)(((ji / R) & 1) ^ 1))) {
-        ok = false;
-        return;
-      }
-      const uint32_t fb = smem_u32(&raw_full[slot]);
-      mbar_arrive_expect_tx(fb, (uint32_t)slot_box);
-      tma_issue<PREC>(a, c, raw_u32 + (uint32_t)(slot * slot_bytes), fb);
-      ++ji;
-      if (++c.kb == c.nkb) {
-        c.kb = 0;
-        c.t += gridDim.x;
-        if (c.t < total_tiles) tma_tile(a, c);
-      }
-    };
-    if (pt == 0)
-      for (int j = 0; j < R - 1 && j < total_kb && ok; ++j) issue();
-    int stage = 0;
-    uint32_t phase = 0;
-    for (int jc = 0; jc < total_kb && ok; ++jc) {
-      if (pt == 0 && jc + R - 1 < total_kb) {
-        issue();
-        if (!ok) break;
-      }
-      const int slot = jc % R;
+    // The raw boxes come from the TMA-issue warp (tma_issue_loop); the
+    // producer warps form two groups of four -- one warp per tensor-memory
+    // lane quarter -- that take alternate K blocks, so two blocks are being
+    // converted at any time.  K block j uses raw slot j % R and MMA stage
+    // j % stages; the barrier parities follow from j.
+    const int g = (pt >> 5) >> 2, gw = (pt >> 5) & 3, gt = pt & 127;
+    for (int jc = g; jc < total_kb; jc += 2) {
+      const int slot = jc % R, stage = jc % stages;
       if (!pwait(a, w_copy, smem_u32(&raw_full[slot]), (uint32_t)((jc / R) & 1))) break;
-      if (!pwait(a, w_empty, smem_u32(&empty_bar[stage]), phase ^ 1)) break;
+      if (!pwait(a, w_empty, smem_u32(&empty_bar[stage]), (uint32_t)(((jc / stages) & 1) ^ 1))) break;
       uint8_t *a0 = data + stage * sbytes;
       const long long tv0 = a.prof ? clock64() : 0;
       if constexpr (PREC == PREC_TF32X3) {
         if (a.prod_mode == PROD_TMA_TMEM)
-          raw_convert_tmem(pt, raw + slot * slot_bytes, tmem_base + (uint32_t)(TS_A_COL0 + stage * 64));
+          raw_convert_tmem(gw, lane, raw + slot * slot_bytes, tmem_base + (uint32_t)(TS_A_COL0 + stage * 64));
         else
-          raw_convert_tma<PREC>(a, pt, raw + slot * slot_bytes, a0, a0 + a_bytes);
+          raw_convert_tma_group<PREC>(gt, raw + slot * slot_bytes, a0, a0 + a_bytes);
       } else {
-        raw_convert_tma<PREC>(a, pt, raw + slot * slot_bytes, a0, a0 + a_bytes);
+        raw_convert_tma_group<PREC>(gt, raw + slot * slot_bytes, a0, a0 + a_bytes);
       }
       const long long tv1 = a.prof ? clock64() : 0;
       fence_proxy_async_smem();  // A tile writes -> MMA; raw reads before the slot's next TMA write
@@ -510,10 +525,6 @@ __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint
       if (lane == 0) {
         mbar_arrive(smem_u32(&full_bar[stage]));
         mbar_arrive(smem_u32(&raw_empty[slot]));
-      }
-      if (++stage == stages) {
-        stage = 0;
-        phase ^= 1;
       }
     }
   } else {
@@ -795,7 +806,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
   if (threadIdx.x == 32) {
     // full: the B loader's arrive + one per producer warp, or the A-TMA
     // thread's arrive in PROD_TMA_DIRECT
-    const uint32_t full_count = a.prod_mode == PROD_TMA_DIRECT ? 2u : (uint32_t)(NUM_PROD_THREADS / 32 + 1);
+    // PROD_CPASYNC: all eight producer warps fill every stage; the TMA
+    // convert modes: one group of four
+    const uint32_t full_count = a.prod_mode == PROD_TMA_DIRECT
+                                    ? 2u
+                                    : (a.prod_mode == PROD_CPASYNC ? (uint32_t)(NUM_PROD_THREADS / 32 + 1) : 5u);
     for (int s = 0; s < stages; ++s) {
       mbar_init(smem_u32(&full_bar[s]), full_count);
       mbar_init(smem_u32(&empty_bar[s]), 1);
@@ -807,7 +822,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     mbar_init(smem_u32(stall_bar), 1);
     for (int r = 0; r < plan.raw_depth; ++r) {
       mbar_init(smem_u32(&raw_full[r]), 1);                        // the TMA thread's arrive
-      mbar_init(smem_u32(&raw_empty[r]), NUM_PROD_THREADS / 32);  // one arrive per producer warp
+      mbar_init(smem_u32(&raw_empty[r]), 4);                      // one arrive per warp of the converting group
     }
     fence_mbar_init();
   }
@@ -922,6 +937,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       }
       if (a.prof) atomicAdd(&a.prof[PROF_BLOAD_WAIT_EMPTY], w_empty);
     }
+  } else if (warp == TMA_ISSUE_WARP && (a.prod_mode == PROD_TMA_CONVERT || a.prod_mode == PROD_TMA_TMEM)) {
+    if (lane == 0)
+      tma_issue_loop<PREC>(a, smem_u32(data + stages * sbytes), raw_full, raw_empty, plan.raw_depth,
+                           plan.raw_slot_bytes, total_tiles);
   } else if (warp >= PROD_WARP0) {
     run_producer<PREC>(a, data, data + stages * sbytes, full_bar, empty_bar, raw_full, raw_empty, stages, sbytes,
                        plan.raw_depth, plan.raw_slot_bytes, M, total_tiles, tmem_base);

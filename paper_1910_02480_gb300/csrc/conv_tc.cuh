@@ -21,7 +21,7 @@ enum Prec { PREC_TF32X3 = 0, PREC_BF16 = 1, PREC_FP8 = 2 };
 constexpr int BM = 128;          // GEMM rows per tile (TMEM lanes)
 constexpr int KROW_BYTES = 128;  // bytes of K per operand row per stage (one swizzle row)
 constexpr int NUM_THREADS = 512; // 16 warps
-constexpr int MMA_WARP = 0, BLOAD_WARP = 1, EPI_WARP0 = 4, PROD_WARP0 = 8;
+constexpr int MMA_WARP = 0, BLOAD_WARP = 1, TMA_ISSUE_WARP = 2, EPI_WARP0 = 4, PROD_WARP0 = 8;
 constexpr int NUM_PROD_THREADS = 256;
 
 struct PhaseDesc {

@@ -40,7 +40,7 @@ struct Layer {
   int prec;                     // kernel precision of this layer (FP8 contexts run the first layer in BF16)
   size_t sc_off;                // FP8: offset of this layer's input-channel scales (Cin floats) in the scale arrays
   size_t bs_off;                // FP8: offset of this layer's output-column scales (Cout floats)
-  char name[16];                // kernel label for the launch tracer
+  char name[24];                // kernel label for the launch tracer
 };
 
 }  // namespace
