@@ -842,6 +842,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       bool ok = true;
       if (a.debug_stall) ok = mbar_wait(smem_u32(stall_bar), 0, tmo, a.status, ERR_TIMEOUT);
       const uint32_t idesc = make_idesc(T::KIND, BM, BN);
+      const uint64_t dA0 = make_sdesc_sw128(data_u32);
+      const uint32_t dstage = (uint32_t)sbytes >> 4, dAlo = (uint32_t)a_bytes >> 4;
+      const uint32_t dB = (uint32_t)(ts ? 0 : T::SPLIT * a_bytes) >> 4, dBlo = (uint32_t)b_bytes >> 4;
       int stage = 0;
       uint32_t phase = 0;
       int it = 0;
@@ -865,31 +868,41 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
             break;
           }
           tc_fence_after();
-          const uint32_t sa0 = data_u32 + stage * sbytes;
-          const uint32_t sa1 = sa0 + a_bytes;                        // A lo (TF32X3)
-          const uint32_t sb0 = ts ? sa0 : sa0 + T::SPLIT * a_bytes;  // B (hi)
-          const uint32_t sb1 = sb0 + b_bytes;                        // B lo (TF32X3)
+          // descriptors: the stage-0 A tile's plus fixed offsets in units of
+          // the start-address field (bytes >> 4); the K step inside the
+          // 128-byte swizzle row adds 32 bytes (2 units).  Keeping this to a
+          // few adds matters: one thread issues every MMA, so its dependent
+          // instruction latency bounds the MMA rate.
+          const uint64_t sd = dA0 + (uint64_t)((uint32_t)stage * dstage);
+          const uint64_t bd0 = sd + dB, bd1 = bd0 + dBlo;
           if (ts) {
             // A hi/lo from tensor memory: 8 tf32 columns per K step
             const uint32_t ta = tmem_base + (uint32_t)(TS_A_COL0 + stage * 64);
+            const uint32_t acc0 = kb != 0;
+            tc_mma_ts_tf32(d_tmem, ta, bd0, idesc, acc0);
+            tc_mma_ts_tf32(c_tmem, ta, bd1, idesc, acc0);
+            tc_mma_ts_tf32(c_tmem, ta + 32, bd0, idesc, 1u);
 #pragma unroll
-            for (int k = 0; k < KROW_BYTES / 32; ++k) {
-              const uint32_t acc = (kb | k) != 0;
-              const uint64_t bd = make_sdesc_sw128(sb0 + k * 32);
-              tc_mma_ts_tf32(d_tmem, ta + 8 * k, bd, idesc, acc);
-              tc_mma_ts_tf32(c_tmem, ta + 8 * k, make_sdesc_sw128(sb1 + k * 32), idesc, acc);
-              tc_mma_ts_tf32(c_tmem, ta + 32 + 8 * k, bd, idesc, 1u);
+            for (int k = 1; k < KROW_BYTES / 32; ++k) {
+              tc_mma_ts_tf32(d_tmem, ta + 8 * k, bd0 + 2 * k, idesc, 1u);
+              tc_mma_ts_tf32(c_tmem, ta + 8 * k, bd1 + 2 * k, idesc, 1u);
+              tc_mma_ts_tf32(c_tmem, ta + 32 + 8 * k, bd0 + 2 * k, idesc, 1u);
             }
-          } else
-#pragma unroll
-          for (int k = 0; k < KROW_BYTES / 32; ++k) {
-            const uint32_t acc = (kb | k) != 0;
-            const uint64_t ad = make_sdesc_sw128(sa0 + k * 32);
-            const uint64_t bd = make_sdesc_sw128(sb0 + k * 32);
-            tc_mma<T::KIND>(d_tmem, ad, bd, idesc, acc);
+          } else {
+            const uint64_t ad1 = sd + dAlo;
+            const uint32_t acc0 = kb != 0;
+            tc_mma<T::KIND>(d_tmem, sd, bd0, idesc, acc0);
             if constexpr (PREC == PREC_TF32X3) {
-              tc_mma<T::KIND>(c_tmem, ad, make_sdesc_sw128(sb1 + k * 32), idesc, acc);
-              tc_mma<T::KIND>(c_tmem, make_sdesc_sw128(sa1 + k * 32), bd, idesc, 1u);
+              tc_mma<T::KIND>(c_tmem, sd, bd1, idesc, acc0);
+              tc_mma<T::KIND>(c_tmem, ad1, bd0, idesc, 1u);
+            }
+#pragma unroll
+            for (int k = 1; k < KROW_BYTES / 32; ++k) {
+              tc_mma<T::KIND>(d_tmem, sd + 2 * k, bd0 + 2 * k, idesc, 1u);
+              if constexpr (PREC == PREC_TF32X3) {
+                tc_mma<T::KIND>(c_tmem, sd + 2 * k, bd1 + 2 * k, idesc, 1u);
+                tc_mma<T::KIND>(c_tmem, ad1 + 2 * k, bd0 + 2 * k, idesc, 1u);
+              }
             }
           }
           tc_commit(smem_u32(&empty_bar[stage]));
