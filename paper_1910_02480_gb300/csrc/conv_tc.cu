@@ -73,8 +73,25 @@ __host__ __device__ inline int raw_row_bytes(int) { return 128; }
 // the A tile itself, a ring of R raw slots; R = 3 keeps two K blocks of
 // copies in flight beyond the one being converted, shrunk to 2 when 2 MMA
 // stages would not fit otherwise.
+static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, int avail);
+
+// With the epilogue's staging buffer where the pipeline keeps at least two
+// stages (and two raw slots where it uses a raw ring); otherwise without.
 __host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode) {
   const int avail = SMEM_BUDGET - SMEM_CTRL - 1024;
+  // the FP32 path only: with 16-byte bf16 / e4m3 row chunks the per-row
+  // epilogue measured faster
+  SmemPlan p = smem_plan_avail(prec, BN, mode, avail - EPI_STG_BYTES);
+  if (prec == PREC_TF32X3 && p.stages >= 2 && (mode == PROD_TMA_DIRECT || p.raw_depth >= 2)) {
+    p.epi_stage = 1;
+    return p;
+  }
+  p = smem_plan_avail(prec, BN, mode, avail);
+  p.epi_stage = 0;
+  return p;
+}
+
+static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, int avail) {
   const int sb = stage_bytes(prec, BN, mode);
   const int rb = BM * raw_row_bytes(prec);
   if (mode == PROD_TMA_TMEM) {
@@ -107,7 +124,7 @@ __host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode) {
 size_t conv_smem_bytes(int prec, int BN, int mode) {
   const SmemPlan p = smem_plan(prec, BN, mode);
   return (size_t)SMEM_CTRL + 1024 + (size_t)p.stages * stage_bytes(prec, BN, mode) +
-         (size_t)p.raw_depth * p.raw_slot_bytes;
+         (size_t)p.raw_depth * p.raw_slot_bytes + (p.epi_stage ? (size_t)EPI_STG_BYTES : 0);
 }
 
 // Offset of 16-byte chunk q of row r inside a 128-byte-swizzled K-major tile.
@@ -757,6 +774,149 @@ __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int
   }
 }
 
+// ---- staged epilogue: four consecutive elements at element offset e ----
+// Load 4 values of an NHWC tensor of the kernel's activation type (FP8: e4m3
+// times the channels' scales sc).
+template <int PREC>
+__device__ __forceinline__ float4 ld4(const void *base, size_t e, const float *sc) {
+  if constexpr (PREC == PREC_TF32X3) {
+    return *reinterpret_cast<const float4 *>(reinterpret_cast<const float *>(base) + e);
+  } else if constexpr (PREC == PREC_BF16) {
+    const uint2 u = *reinterpret_cast<const uint2 *>(reinterpret_cast<const __nv_bfloat16 *>(base) + e);
+    return make_float4(bf16_lo(u.x), bf16_hi(u.x), bf16_lo(u.y), bf16_hi(u.y));
+  } else {
+    float f[4];
+    e4m3x4_to_f32(*reinterpret_cast<const uint32_t *>(reinterpret_cast<const uint8_t *>(base) + e), f);
+    return make_float4(f[0] * __ldg(sc), f[1] * __ldg(sc + 1), f[2] * __ldg(sc + 2), f[3] * __ldg(sc + 3));
+  }
+}
+// Store 4 values in the kernel's activation type, or as e4m3 times qi.
+template <int PREC>
+__device__ __forceinline__ void st4(void *base, size_t e, float4 v, const float *qi) {
+  if (qi) {
+    *reinterpret_cast<uint32_t *>(reinterpret_cast<uint8_t *>(base) + e) =
+        pack_e4m3x4(v.x * __ldg(qi), v.y * __ldg(qi + 1), v.z * __ldg(qi + 2), v.w * __ldg(qi + 3));
+  } else if constexpr (PREC == PREC_TF32X3) {
+    *reinterpret_cast<float4 *>(reinterpret_cast<float *>(base) + e) = v;
+  } else {
+    *reinterpret_cast<uint2 *>(reinterpret_cast<__nv_bfloat16 *>(base) + e) =
+        make_uint2(pack_bf16x2(v.x, v.y), pack_bf16x2(v.z, v.w));
+  }
+}
+
+// One accumulator tile through the staging buffer.  Per 16-column chunk each
+// lane takes its own row out of tensor memory (the load is warp-collective)
+// and applies the dequantisation, bias, ReLU and the calibration maximum;
+// the warp's 32 rows x 16 columns then go through shared memory so that four
+// lanes cover one row and the skip load, the stores and the training mask /
+// second output are 16-byte accesses to 64 contiguous bytes of each row
+// (instead of 32 rows per warp instruction).
+template <int PREC>
+__device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t taddr, int BN, int n0, size_t ebase,
+                                                bool vrow, float *stg, unsigned long long &w_tfull, uint32_t tfull,
+                                                uint32_t par) {
+  const int lane = threadIdx.x & 31;
+  size_t er[4];
+  bool vr[4];
+#pragma unroll
+  for (int it = 0; it < 4; ++it) {
+    const int src = it * 8 + (lane >> 2);
+    er[it] = ((size_t)__shfl_sync(0xffffffffu, (unsigned)(ebase >> 32), src) << 32) |
+             (size_t)__shfl_sync(0xffffffffu, (unsigned)ebase, src);
+    vr[it] = __shfl_sync(0xffffffffu, vrow ? 1 : 0, src) != 0;
+  }
+  const int q = lane & 3;
+  float4 *stg4 = reinterpret_cast<float4 *>(stg);
+  // skip values one chunk ahead: chunk 0's before the accumulator is ready,
+  // each next chunk's as soon as the previous chunk has used its registers
+  float4 sk[4];
+  auto load_skip4 = [&](int cc) {
+    const int col0 = n0 + cc * 16;
+#pragma unroll
+    for (int it = 0; it < 4; ++it)
+      if (vr[it]) sk[it] = ld4<PREC>(a.skip, er[it] + col0 + 4 * q, a.skip_scale ? a.skip_scale + col0 + 4 * q : nullptr);
+  };
+  if (a.skip) load_skip4(0);
+  if (!pwait(a, w_tfull, tfull, par)) return false;
+  tc_fence_after();
+  for (int cc = 0; cc < BN / 16; ++cc) {
+    const int col0 = n0 + cc * 16;
+    float v[16];
+    tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
+    const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
+    const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
+#pragma unroll
+    for (int e4 = 0; e4 < 4; ++e4) {
+      const float4 b = __ldg(bias4 + e4);
+      const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float z = bsc ? v[4 * e4 + e] * __ldg(bsc + 4 * e4 + e) : v[4 * e4 + e];
+        z += bb[e];
+        if (a.relu) z = fmaxf(z, 0.f);
+        v[4 * e4 + e] = z;
+      }
+    }
+#pragma unroll
+    for (int e4 = 0; e4 < 4; ++e4)
+      stg4[lane * 5 + e4] = make_float4(v[4 * e4], v[4 * e4 + 1], v[4 * e4 + 2], v[4 * e4 + 3]);
+    __syncwarp();
+    float4 mx = make_float4(0.f, 0.f, 0.f, 0.f);  // calibration: max |stored value| of this lane's columns
+#pragma unroll
+    for (int it = 0; it < 4; ++it) {
+      if (!vr[it]) continue;
+      const int r = it * 8 + (lane >> 2);
+      float4 x = stg4[r * 5 + q];
+      const size_t e = er[it] + col0 + 4 * q;  // er: the row's first element; col0 includes the N tile
+      if constexpr (PREC != PREC_FP8) {
+        if (a.y2 && a.y2_pre_skip) st4<PREC>(a.y2, e, x, nullptr);
+      }
+      if (a.skip) {
+        x.x += sk[it].x;
+        x.y += sk[it].y;
+        x.z += sk[it].z;
+        x.w += sk[it].w;
+      }
+      if constexpr (PREC != PREC_FP8) {
+        if (a.y2 && !a.y2_pre_skip) st4<PREC>(a.y2, e, x, nullptr);
+        if (a.mask) {
+          const float4 mk = ld4<PREC>(a.mask, e, nullptr);
+          if (!(mk.x > 0.f)) x.x = 0.f;
+          if (!(mk.y > 0.f)) x.y = 0.f;
+          if (!(mk.z > 0.f)) x.z = 0.f;
+          if (!(mk.w > 0.f)) x.w = 0.f;
+        }
+      }
+      if (a.amax) {
+        mx.x = fmaxf(mx.x, fabsf(x.x));
+        mx.y = fmaxf(mx.y, fabsf(x.y));
+        mx.z = fmaxf(mx.z, fabsf(x.z));
+        mx.w = fmaxf(mx.w, fabsf(x.w));
+      }
+      st4<PREC>(a.y, e, x, a.out_qinv ? a.out_qinv + col0 + 4 * q : nullptr);
+    }
+    if (a.skip && cc + 1 < BN / 16) load_skip4(cc + 1);
+    if (a.amax) {  // lanes with the same q hold the same columns
+#pragma unroll
+      for (int o = 4; o < 32; o <<= 1) {
+        mx.x = fmaxf(mx.x, __shfl_xor_sync(0xffffffffu, mx.x, o));
+        mx.y = fmaxf(mx.y, __shfl_xor_sync(0xffffffffu, mx.y, o));
+        mx.z = fmaxf(mx.z, __shfl_xor_sync(0xffffffffu, mx.z, o));
+        mx.w = fmaxf(mx.w, __shfl_xor_sync(0xffffffffu, mx.w, o));
+      }
+      if (lane < 4) {
+        unsigned *am = a.amax + col0 + 4 * q;
+        if (mx.x > 0.f) atomicMax(am, __float_as_uint(mx.x));
+        if (mx.y > 0.f) atomicMax(am + 1, __float_as_uint(mx.y));
+        if (mx.z > 0.f) atomicMax(am + 2, __float_as_uint(mx.z));
+        if (mx.w > 0.f) atomicMax(am + 3, __float_as_uint(mx.w));
+      }
+    }
+    __syncwarp();
+  }
+  return true;
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_constant__ ConvArgs a) {
   using T = PrecTraits<PREC>;
@@ -970,6 +1130,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     const int out_elem = a.out_qinv ? 1 : (int)sizeof(act_t);  // e4m3, or the activation type
     const act_t *skip = reinterpret_cast<const act_t *>(a.skip);
     const int nch = BN / 16;
+    float *epi_stg = reinterpret_cast<float *>(data + (size_t)stages * sbytes + (size_t)plan.raw_depth * plan.raw_slot_bytes);
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++it) {
       const TileCoord tc = tile_coord(a, t);
       const PhaseDesc &pd = a.ph[tc.phase];
@@ -984,29 +1145,52 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
                               ? ((size_t)n * a.Hout + (2 * i + pd.oy)) * a.Wout + (2 * j + pd.ox)
                               : (size_t)m;
       const size_t ebase = opix * a.Cout + (size_t)tc.n_tile * BN;
-      // The skip values of the first two 16-column chunks are loaded before
-      // the accumulator is ready (their latency hides behind the tile's
-      // MMAs); later chunks are fetched two ahead while earlier ones are
-      // stored.  Each output element is read (skip) and written by this
-      // thread only, so reading ahead of the in-place store is safe.
-      const bool has_skip = skip != nullptr && vrow;
-      uint4 sk0[4], sk1[4];
-      if (has_skip) {
-        load_skip<PREC>(skip + ebase, sk0);
-        if (nch > 1) load_skip<PREC>(skip + ebase + 16, sk1);
+      if (plan.epi_stage) {
+        const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
+        if (!epi_tile_staged<PREC>(a, taddr, BN, tc.n_tile * BN, opix * a.Cout, vrow, epi_stg + eq * 32 * 20, w_tfull,
+                                   smem_u32(&tfull_bar[buf]), par))
+          break;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[buf]));
+        continue;
       }
-      if (!pwait(a, w_tfull, smem_u32(&tfull_bar[buf]), par)) break;
-      tc_fence_after();
+      // Per-row path: each lane stores its own row.  BF16 / FP8 load the
+      // skip values of the first two 16-column chunks before the accumulator
+      // is ready (their latency hides behind the tile's MMAs) and later
+      // chunks two ahead; each element is read (skip) and written by this
+      // thread only, so reading ahead of the in-place store is safe.  The
+      // FP32 kernel only takes this path when the staging buffer does not
+      // fit and loads each chunk's skip just before use (fewer registers).
+      const bool has_skip = skip != nullptr && vrow;
       const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
       uint8_t *yb = yout + ebase * out_elem;
-      for (int cc = 0; cc < nch; cc += 2) {
-        epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk0, yb + cc * 16 * out_elem,
-                        ebase + cc * 16);
-        if (has_skip && cc + 2 < nch) load_skip<PREC>(skip + ebase + (cc + 2) * 16, sk0);
-        if (cc + 1 < nch) {
-          epi_chunk<PREC>(a, taddr, cc + 1, BN, tc.n_tile * BN + (cc + 1) * 16, vrow, has_skip, sk1,
-                          yb + (cc + 1) * 16 * out_elem, ebase + (cc + 1) * 16);
-          if (has_skip && cc + 3 < nch) load_skip<PREC>(skip + ebase + (cc + 3) * 16, sk1);
+      if constexpr (PREC == PREC_TF32X3) {
+        if (!pwait(a, w_tfull, smem_u32(&tfull_bar[buf]), par)) break;
+        tc_fence_after();
+        for (int cc = 0; cc < nch; ++cc) {
+          uint4 sk[4];
+          if (has_skip) load_skip<PREC>(skip + ebase + cc * 16, sk);
+          epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk, yb + cc * 16 * out_elem,
+                          ebase + cc * 16);
+        }
+      } else {
+        uint4 sk0[4], sk1[4];
+        if (has_skip) {
+          load_skip<PREC>(skip + ebase, sk0);
+          if (nch > 1) load_skip<PREC>(skip + ebase + 16, sk1);
+        }
+        if (!pwait(a, w_tfull, smem_u32(&tfull_bar[buf]), par)) break;
+        tc_fence_after();
+        for (int cc = 0; cc < nch; cc += 2) {
+          epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk0, yb + cc * 16 * out_elem,
+                          ebase + cc * 16);
+          if (has_skip && cc + 2 < nch) load_skip<PREC>(skip + ebase + (cc + 2) * 16, sk0);
+          if (cc + 1 < nch) {
+            epi_chunk<PREC>(a, taddr, cc + 1, BN, tc.n_tile * BN + (cc + 1) * 16, vrow, has_skip, sk1,
+                            yb + (cc + 1) * 16 * out_elem, ebase + (cc + 1) * 16);
+            if (has_skip && cc + 3 < nch) load_skip<PREC>(skip + ebase + (cc + 3) * 16, sk1);
+          }
         }
       }
       tc_fence_before();

@@ -91,7 +91,11 @@ enum ProfSlot {
 
 struct SmemPlan {
   int stages, raw_depth, raw_slot_bytes;
+  int epi_stage;  // the epilogue's staging buffer (EPI_STG_BYTES after the raw ring) fits
 };
+// Epilogue staging: 4 warps x 32 rows x (16 + 4 pad) floats.
+constexpr int EPI_STG_FLOATS = 4 * 32 * 20;
+constexpr int EPI_STG_BYTES = EPI_STG_FLOATS * 4;
 __host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode);
 size_t conv_smem_bytes(int prec, int BN, int mode);
 
