@@ -614,12 +614,16 @@ __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint
 // correction accumulator BN columns further on for the split-tf32 path.
 template <int PREC>
 __device__ __forceinline__ void tmem_ld_acc(uint32_t taddr, int BN, float (&v)[16]) {
-  tmem_ld16(taddr, v);
   if constexpr (PREC == PREC_TF32X3) {
-    float c[16];
-    tmem_ld16(taddr + (uint32_t)BN, c);
+    // main and correction accumulators: both loads in flight, one wait
+    uint32_t a[16], c[16];
+    tmem_ld16_nowait(taddr, a);
+    tmem_ld16_nowait(taddr + (uint32_t)BN, c);
+    tmem_wait_ld();
 #pragma unroll
-    for (int e = 0; e < 16; ++e) v[e] += c[e];
+    for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(a[e]) + __uint_as_float(c[e]);
+  } else {
+    tmem_ld16(taddr, v);
   }
 }
 

@@ -529,7 +529,7 @@ __device__ __forceinline__ void blend_store(const InterpArgs &a, long long p, co
 // the blend (IRRADIANCE / LOOKUP), fixed at compile time so that each kernel
 // only carries its own registers and code.
 template <int KMAX, int MODE>
-__global__ void __launch_bounds__(256) interp_query_kernel(InterpArgs a, InterpScratch s) {
+__global__ void __launch_bounds__(256, KMAX <= 16 ? 4 : 2) interp_query_kernel(InterpArgs a, InterpScratch s) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long P = (long long)a.width * a.height;
   if (t >= P) return;
