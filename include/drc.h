@@ -225,6 +225,27 @@ drc_status drc_backward(drc_ctx *ctx, const float *in, const float *target,
                         int N, int H, int W, unsigned flags, float *dweights,
                         float *dinput, float *loss, void *stream);
 
+/* Weight gradient of one 3x3, stride-2, pad-1 layer alone (the per-layer
+ * step of the training pass above, Sec. 3.3):
+ *   dW[m][q][u][v] += sum over n, i, j of R[n][i][j][m] * Q[n][2i+u-1][2j+v-1][q]
+ * with Q read as zero outside [0, 2Hb) x [0, 2Wb).  For a conv layer R is the
+ * output gradient and Q the input (dW is then [Cout][Cin][3][3]); for a
+ * transposed conv R is the input and Q the output gradient (dW [Cin][Cout]
+ * [3][3]), the packed weight layouts of drc_create.
+ *   R:  device, NHWC [N][Hb][Wb][Mr], channels contiguous;
+ *   Q:  device, NHWC [N][2Hb][2Wb][Qc]; only channels q < Qraw enter dW;
+ *   dtype: DRC_PREC_FP32 (float operands) or DRC_PREC_BF16 (bfloat16);
+ *   dW: device fp32 [Mr][Qraw][3][3], ACCUMULATED into (clear it first).
+ * BF16 operands with Mr a multiple of 128, Qc of 64, Wb dividing 64 and 64
+ * pixels covering whole rows of whole maps run on the tensor cores (fp32
+ * accumulation, the pixel sum split over CTAs and added with atomics, so the
+ * summation order varies from run to run); every other shape, and FP32,
+ * runs a CUDA-core kernel with fp32 sums.  N = 0 leaves dW unchanged.  The
+ * context supplies the device, the status word and the wait bound only. */
+drc_status drc_weight_grad(drc_ctx *ctx, const void *R, const void *Q,
+                           drc_precision dtype, int N, int Hb, int Wb, int Mr,
+                           int Qc, int Qraw, float *dW, void *stream);
+
 /* Synchronise `stream` and return (then clear) the latched device status:
  * DRC_OK or DRC_ERR_TIMEOUT. */
 drc_status drc_get_status(drc_ctx *ctx, void *stream);

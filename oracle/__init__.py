@@ -9,6 +9,7 @@ through ctypes on numpy arrays.
 
 Functions (each cites the passage its C routine follows, see drc_oracle.c):
   conv3x3s2, convT3x3s2   the encoder / decoder layers (Sec. 3.3)
+  conv_weight_grad        one layer's weight gradient (training, Sec. 3.3)
   forward                 the autoencoder with skip connections (Sec. 3.3)
   payload                 cosine-weighted hemisphere integral (Eq. 2, Sec. 3.3)
   interpolate             kNN + weights w = w_p w_n + w_p + eps (Sec. 3.2)
@@ -72,6 +73,7 @@ def _load():
         lib.orc_l1_backward.argtypes = [i, P, i, i, i, d, u, P, l, P, P, i, i,
                                         i, i, P, P, P]
         lib.orc_l1_backward.restype = d
+        lib.orc_conv_wgrad.argtypes = [P, i, i, i, i, P, i, i, P]
         _lib = lib
     return _lib
 
@@ -115,6 +117,23 @@ def convT3x3s2(x, w, b=None):
     bb = None if b is None else _f64(b)
     _load().orc_convT3x3s2(_ptr(x), N, Cin, H, W, _ptr(w), _ptr(bb), Cout, _ptr(y))
     return y
+
+
+def conv_weight_grad(x, g, transposed=False):
+    """Weight gradient of one layer from its input x [N,Cin,H,W] and output
+    gradient g: a conv (g [N,Cout,H/2,W/2]) -> dW [Cout,Cin,3,3], or a
+    transposed conv (g [N,Cout,2H,2W]) -> dW [Cin,Cout,3,3] (Sec. 3.3)."""
+    x, g = _f64(x), _f64(g)
+    N, Cin, H, W = x.shape
+    Cout = g.shape[1]
+    if transposed:
+        assert g.shape == (N, Cout, 2 * H, 2 * W)
+        dw = np.empty((Cin, Cout, 3, 3))
+    else:
+        assert g.shape == (N, Cout, H // 2, W // 2) and H % 2 == 0 and W % 2 == 0
+        dw = np.empty((Cout, Cin, 3, 3))
+    _load().orc_conv_wgrad(_ptr(x), N, Cin, H, W, _ptr(g), Cout, int(transposed), _ptr(dw))
+    return dw
 
 
 def forward(weights, x, widths, cin=7, cout=3, out_relu=False, exposure=1.0,

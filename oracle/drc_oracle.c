@@ -626,6 +626,23 @@ static void convT_adjoint(const double *x, int N, int Cin, int H, int W,
                 }
 }
 
+/* Weight gradient of one layer alone (training, Sec. 3.3), the dW part of
+ * the adjoints above: transposed = 0, a conv with input x [N][Cin][H][W] and
+ * output gradient g [N][Cout][H/2][W/2], dW [Cout][Cin][3][3]; transposed =
+ * 1, a transposed conv with input x [N][Cin][H][W] and output gradient g
+ * [N][Cout][2H][2W], dW [Cin][Cout][3][3].  dW is overwritten. */
+void orc_conv_wgrad(const double *x, int N, int Cin, int H, int W,
+                    const double *g, int Cout, int transposed, double *dW)
+{
+    double *db = calloc((size_t)Cout, sizeof(double));
+    memset(dW, 0, sizeof(double) * 9 * (size_t)Cin * Cout);
+    if (transposed)
+        convT_adjoint(x, N, Cin, H, W, NULL, Cout, g, NULL, dW, db);
+    else
+        conv_adjoint(x, N, Cin, H, W, NULL, Cout, g, NULL, dW, db);
+    free(db);
+}
+
 /* Loss and exact gradient.  mode 0: target is the ground truth y (log
  * radiance, [N][cout][H][W]); loss = mean |out - y| and dL/dout =
  * sign(out - y)/numel with sign(0) = 0.  mode 1: target is dL/dout itself and

@@ -101,6 +101,8 @@ def load_library():
     lib.drc_interpolate_static.restype = I
     lib.drc_backward.argtypes = [P, P, P, I, I, I, U, P, P, P, P]
     lib.drc_backward.restype = I
+    lib.drc_weight_grad.argtypes = [P, P, P, I, I, I, I, I, I, I, P, P]
+    lib.drc_weight_grad.restype = I
     lib.drc_get_status.argtypes = [P, P]
     lib.drc_get_status.restype = I
     lib.drc_last_error.argtypes = [P]
@@ -274,6 +276,28 @@ class Context:
                                     _ptr(dinput), _ptr(loss), _stream(stream))
         self._check(rc, "drc_backward")
         return loss, dweights, dinput
+
+    def weight_grad(self, R, Q, qraw=None, dW=None, stream=None):
+        """drc_weight_grad: one layer's weight gradient
+        dW[m][q][u][v] += sum R[n,i,j,m] Q[n,2i+u-1,2j+v-1,q] from NHWC CUDA
+        tensors R [N,Hb,Wb,Mr] and Q [N,2Hb,2Wb,Qc] (both float32 or both
+        bfloat16).  Returns dW [Mr, qraw, 3, 3] float32 (a new zeroed tensor
+        unless dW is given, which is accumulated into)."""
+        import torch
+        N, Hb, Wb, Mr = R.shape
+        Qc = Q.shape[3]
+        if tuple(Q.shape) != (N, 2 * Hb, 2 * Wb, Qc):
+            raise ValueError("Q must be [N, 2Hb, 2Wb, Qc]")
+        if R.dtype != Q.dtype or R.dtype not in (torch.float32, torch.bfloat16):
+            raise ValueError("R and Q must both be float32 or both bfloat16")
+        qraw = Qc if qraw is None else int(qraw)
+        if dW is None:
+            dW = torch.zeros((Mr, qraw, 3, 3), dtype=torch.float32, device=R.device)
+        dtype = PREC["bf16"] if R.dtype == torch.bfloat16 else PREC["fp32"]
+        rc = self._lib.drc_weight_grad(self._ctx, _ptr(R), _ptr(Q), dtype, N, Hb, Wb, Mr, Qc, qraw, _ptr(dW),
+                                       _stream(stream))
+        self._check(rc, "drc_weight_grad")
+        return dW
 
     def status(self, stream=None):
         """Synchronise and return the latched device status code."""

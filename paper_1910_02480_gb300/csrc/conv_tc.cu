@@ -393,16 +393,6 @@ __device__ __forceinline__ void raw_convert_tmem(int q, int lane, const uint8_t 
   tmem_wait_st();
 }
 
-// 4-D tiled TMA load of one box into shared memory, completing on `bar`.
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                            uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-      "%5}], [%6];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-      : "memory");
-}
-
 // Box coordinates (channel, x, y, map) of the A rows of tile t, K block kb.
 struct TmaCursor {
   int t, kb, nkb, ntaps, n0, r0;  // r0: first output row (conv) / input row (phase) of the tile

@@ -20,6 +20,7 @@
 #include "drc_status.cuh"
 #include "interp.cuh"
 #include "trace.cuh"
+#include "wgrad_tc.cuh"
 
 using namespace drc;
 
@@ -748,6 +749,48 @@ size_t train_layout(const drc_ctx *c, int N, int H, int W, bool recompute, void 
   return off;
 }
 
+// Weight gradient dW[m][q][3][3] += sum R[n,i,j,m] Q[n,2i+u-1,2j+v-1,q]: on
+// the tensor cores where both operands are BF16 and the shape fits
+// (wgrad_tc.cu), else the SIMT kernel (fp32 or compensated fp64 sums).
+cudaError_t weight_grad(const drc_ctx *c, const void *R, bool r_bf16, const void *Q, bool q_bf16, int N, int Hb,
+                        int Wb, int Mr, int Qc, int Qraw, float *dW, double *dW64, cudaStream_t st) {
+  EncodeTiledFn enc = encode_tiled();
+  if (r_bf16 && q_bf16 && !dW64 && enc && N > 0 && wgrad_tc_supported(Hb, Wb, Mr, Qc)) {
+    WgradTcArgs a;
+    memset(&a, 0, sizeof a);
+    int rows, maps;
+    wgrad_tc_box(Hb, Wb, &rows, &maps);
+    const cuuint64_t K = (cuuint64_t)N * Hb * Wb;
+    cuuint64_t rd[2] = {(cuuint64_t)Mr, K}, rs[1] = {(cuuint64_t)Mr * 2};
+    cuuint32_t rb[2] = {64, 64}, re[2] = {1, 1};
+    cuuint64_t qd[4] = {(cuuint64_t)Qc, (cuuint64_t)(2 * Wb), (cuuint64_t)(2 * Hb), (cuuint64_t)N};
+    cuuint64_t qs[3] = {(cuuint64_t)Qc * 2, (cuuint64_t)Qc * 2 * 2 * Wb, (cuuint64_t)Qc * 2 * 2 * Wb * 2 * Hb};
+    cuuint32_t qb[4] = {64, (cuuint32_t)(2 * Wb), (cuuint32_t)(2 * rows), (cuuint32_t)maps}, qe[4] = {1, 2, 2, 1};
+    const bool ok =
+        enc(&a.mapR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(R), rd, rs, rb, re,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
+        enc(&a.mapQ, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(Q), qd, qs, qb, qe,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    if (ok) {
+      a.dW = dW;
+      a.status = c->d_status;
+      a.timeout_ns = c->timeout_ns;
+      a.N = N;
+      a.Hb = Hb;
+      a.Wb = Wb;
+      a.Mr = Mr;
+      a.Qraw = Qraw;
+      a.BNq = Qc % 128 == 0 ? 128 : 64;
+      a.m_tiles = Mr / 128;
+      a.n_tiles = Qc / a.BNq;
+      return launch_wgrad_tc(a, c->num_sms, st);
+    }
+  }
+  return launch_wgrad(R, r_bf16, Q, q_bf16, N, Hb, Wb, Mr, Qc, Qraw, dW, dW64, c->num_sms, st);
+}
+
 // ConvArgs of layer L on explicit buffers (input Hin x Win, N maps).
 void train_conv_args(const drc_ctx *c, const Layer &L, const uint8_t *B, const uint8_t *B_lo, int N, int Hin,
                      int Win, const void *x, void *y, const void *skip, int relu, const float *bias, ConvArgs &a) {
@@ -1319,8 +1362,8 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
                                  c1, bf, st));
   if (e != cudaSuccess) return cuda_fail(c, e, "head backward");
   DRC_TRACED(tr, "wgrad head", st,
-             e = launch_wgrad(S >= 2 ? b.t[1] : b.e[1], bf, b.g4, false, N, H >> 1, W >> 1, c1, 4, 3,
-                              dweights + Lh.w_off, o64(Lh.w_off), c->num_sms, st));
+             e = weight_grad(c, S >= 2 ? b.t[1] : b.e[1], bf, b.g4, false, N, H >> 1, W >> 1, c1, 4, 3,
+                              dweights + Lh.w_off, o64(Lh.w_off), st));
   if (e == cudaSuccess)
     DRC_TRACED(tr, "bgrad head", st,
                e = launch_colsum(b.g4, false, (long long)N * H * W, 4, 3, dweights + Lh.b_off, o64(Lh.b_off),
@@ -1335,8 +1378,8 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
     const void *tin = s2 == S ? b.e[S] : b.t[s2];
     const long long npix = (long long)N * (H >> (s2 - 1)) * (W >> (s2 - 1));
     DRC_TRACED(tr, "wgrad", st,
-               e = launch_wgrad(tin, bf, b.gzd[s2 - 1], bf, N, H >> s2, W >> s2, F.Cin, F.Cout, F.Cout,
-                                dweights + F.w_off, o64(F.w_off), c->num_sms, st));
+               e = weight_grad(c, tin, bf, b.gzd[s2 - 1], bf, N, H >> s2, W >> s2, F.Cin, F.Cout, F.Cout,
+                                dweights + F.w_off, o64(F.w_off), st));
     if (e == cudaSuccess)
       DRC_TRACED(tr, "bgrad", st,
                  e = launch_colsum(b.gzd[s2 - 1], bf, npix, F.Cout, F.Cout, dweights + F.b_off, o64(F.b_off),
@@ -1366,8 +1409,8 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
     const long long npix = (long long)N * (H >> s2) * (W >> s2);
     const void *xin = s2 == 1 ? (const void *)b.in8 : b.e[s2 - 1];
     DRC_TRACED(tr, "wgrad", st,
-               e = launch_wgrad(b.gze[s2], bf, xin, bf, N, H >> s2, W >> s2, F.Cout, F.Cin, F.Cin_raw,
-                                dweights + F.w_off, o64(F.w_off), c->num_sms, st));
+               e = weight_grad(c, b.gze[s2], bf, xin, bf, N, H >> s2, W >> s2, F.Cout, F.Cin, F.Cin_raw,
+                                dweights + F.w_off, o64(F.w_off), st));
     if (e == cudaSuccess)
       DRC_TRACED(tr, "bgrad", st,
                  e = launch_colsum(b.gze[s2], bf, npix, F.Cout, F.Cout, dweights + F.b_off, o64(F.b_off),
@@ -1393,6 +1436,26 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
     if (e != cudaSuccess) return cuda_fail(c, e, "input gradient");
   }
   return DRC_OK;
+}
+
+drc_status drc_weight_grad(drc_ctx *c, const void *R, const void *Q, drc_precision dtype, int N, int Hb, int Wb,
+                           int Mr, int Qc, int Qraw, float *dW, void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (dtype != DRC_PREC_FP32 && dtype != DRC_PREC_BF16)
+    return fail(c, DRC_ERR_INVALID_ARG, "operands are FP32 or BF16");
+  if (N < 0 || Hb < 1 || Wb < 1 || Mr < 1 || Qc < 1 || Qraw < 1 || Qraw > Qc)
+    return fail(c, DRC_ERR_INVALID_ARG, "bad shape N=%d Hb=%d Wb=%d Mr=%d Qc=%d Qraw=%d", N, Hb, Wb, Mr, Qc, Qraw);
+  if ((long long)N * 4 * Hb * Wb * (Qc > Mr ? Qc : Mr) >= (1ll << 31))
+    return fail(c, DRC_ERR_INVALID_ARG, "operands must stay below 2^31 elements");
+  drc_status s;
+  if ((s = check_dev(c, dW, "dW", false)) != DRC_OK) return s;
+  if (N == 0) return DRC_OK;
+  if ((s = check_dev(c, R, "R", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, Q, "Q", false)) != DRC_OK) return s;
+  const bool bf = dtype == DRC_PREC_BF16;
+  cudaError_t e = weight_grad(c, R, bf, Q, bf, N, Hb, Wb, Mr, Qc, Qraw, dW, nullptr, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? DRC_OK : cuda_fail(c, e, "weight gradient");
 }
 
 drc_status drc_get_status(drc_ctx *c, void *stream) {

@@ -1,6 +1,8 @@
 // ptx.cuh -- thin inline-PTX wrappers for sm_103a: mbarriers, bulk copies,
 // proxy fences and the tcgen05 tensor-core / tensor-memory instructions.
 #pragma once
+#include <cuda.h>  // CUtensorMap (type only)
+
 #include <cstdint>
 
 namespace drc {
@@ -45,7 +47,7 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
 // `timeout_ns` (globaltimer) has passed since the first failed probe, latches
 // `code` into *status and returns false; every caller then leaves its loop,
 // so a kernel never spins forever.
-__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity,
+static __device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity,
                                             unsigned long long timeout_ns, int *status, int code) {
   const uint64_t t0 = global_timer_ns();
   for (uint32_t it = 1;; ++it) {
@@ -71,6 +73,25 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
           dst),
       "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// 2-D / 4-D tiled TMA loads of one box into shared memory, completing on
+// `bar` (coordinates innermost first; the innermost one x element size a
+// multiple of 16 bytes).
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
       : "memory");
 }
 

@@ -105,3 +105,51 @@ def test_grad_out_mode_is_linear_and_matches_l1():
     _, al, xl = oracle.l1_backward(w, x, y, WIDTHS)
     _, ag, xg = oracle.l1_backward(w, x, g, WIDTHS, grad_out=True)
     np.testing.assert_allclose(ag, al, rtol=1e-6, atol=1e-12)
+
+
+@pytest.mark.parametrize("transposed", [False, True])
+def test_layer_weight_gradient_is_the_adjoint_of_the_layer(transposed):
+    """A layer without bias is linear in its weights, so the weight gradient
+    of <g, layer(x; D)> is exactly the tensor G with <G, D> = <g, layer(x; D)>
+    for every D: checked for random D against the (separately pinned)
+    conv3x3s2 / convT3x3s2, and on a basis direction per tap (one weight)."""
+    rng = np.random.default_rng(11 + transposed)
+    N, Cin, Cout, H, W = 3, 5, 4, 6, 10
+    x = rng.normal(size=(N, Cin, H, W))
+    if transposed:
+        g = rng.normal(size=(N, Cout, 2 * H, 2 * W))
+        layer, shape = oracle.convT3x3s2, (Cin, Cout, 3, 3)
+    else:
+        g = rng.normal(size=(N, Cout, H // 2, W // 2))
+        layer, shape = oracle.conv3x3s2, (Cout, Cin, 3, 3)
+    G = oracle.conv_weight_grad(x, g, transposed=transposed)
+    assert G.shape == shape
+    for _ in range(3):
+        D = rng.normal(size=shape)
+        lhs = float(np.sum(G * D))
+        rhs = float(np.sum(g * layer(x, D)))
+        assert abs(lhs - rhs) <= 1e-12 * (np.sum(np.abs(G * D)) + 1.0)
+    for t in range(9):  # each tap (u, v) separately: catches a swapped or shifted tap
+        D = np.zeros(shape)
+        D[1, 2, t // 3, t % 3] = 1.0
+        assert abs(G[1, 2, t // 3, t % 3] - np.sum(g * layer(x, D))) <= 1e-12 * np.sum(np.abs(g)) * np.abs(x).max()
+
+
+def test_layer_weight_gradient_brute_force():
+    """Direct sum from the definition on a tiny conv: dW[o][c][u][v] = sum over
+    n, i, j of g[n,o,i,j] x[n,c,2i+u-1,2j+v-1], zero outside the input."""
+    rng = np.random.default_rng(5)
+    x = rng.normal(size=(2, 2, 4, 6))
+    g = rng.normal(size=(2, 3, 2, 3))
+    ref = np.zeros((3, 2, 3, 3))
+    for n in range(2):
+        for o in range(3):
+            for c in range(2):
+                for u in range(3):
+                    for v in range(3):
+                        for i in range(2):
+                            for j in range(3):
+                                y, xx = 2 * i + u - 1, 2 * j + v - 1
+                                if 0 <= y < 4 and 0 <= xx < 6:
+                                    ref[o, c, u, v] += g[n, o, i, j] * x[n, c, y, xx]
+    np.testing.assert_allclose(oracle.conv_weight_grad(x, g), ref, rtol=1e-13, atol=1e-13)
