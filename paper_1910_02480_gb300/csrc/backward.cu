@@ -38,10 +38,11 @@ __device__ __forceinline__ __nv_bfloat16 stf<__nv_bfloat16>(float v) {
 
 // L1 loss mean |out - target| and dL/dout = sign(out - target) / numel
 // (sign(0) = 0), or dL/dout given (GRAD_OUT); zero where the output ReLU was
-// inactive.  g is written NHWC with 4 channels (the 4th zero).
+// inactive.  g is written NHWC with 4 channels (the 4th zero), and when g8 is
+// given also as bf16 NHWC with 8 channels (5 zero).
 __global__ void l1_grad_kernel(const float *__restrict__ out, const float *__restrict__ target, int N, int H, int W,
                                int grad_out, int out_relu, float inv_numel, float *__restrict__ g4,
-                               float *__restrict__ loss) {
+                               __nv_bfloat16 *__restrict__ g8, float *__restrict__ loss) {
   const long long hw = (long long)H * W;
   const long long total = (long long)N * hw;
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -65,6 +66,11 @@ __global__ void l1_grad_kernel(const float *__restrict__ out, const float *__res
       gv[o] = gi;
     }
     reinterpret_cast<float4 *>(g4)[pix] = make_float4(gv[0], gv[1], gv[2], 0.f);
+    if (g8) {
+      const __nv_bfloat162 a = __floats2bfloat162_rn(gv[0], gv[1]), b = __floats2bfloat162_rn(gv[2], 0.f);
+      reinterpret_cast<uint4 *>(g8)[pix] = make_uint4(*reinterpret_cast<const uint32_t *>(&a),
+                                                      *reinterpret_cast<const uint32_t *>(&b), 0u, 0u);
+    }
   }
   if (!grad_out && loss) {
     __shared__ float red[32];
@@ -80,54 +86,113 @@ __global__ void l1_grad_kernel(const float *__restrict__ out, const float *__res
 }
 
 // Head backward, data part: dt1[n,i,j,c] = sum_{o,u,v} W[c][o][u][v] *
-// g[n, 2i+u-1, 2j+v-1, o] (g zero outside the map).  A block takes 16 t_1
-// pixels; the 27 g values of each are staged in shared memory and the head
-// weights, transposed to [27][C], too; a warp covers 32 channels of a pixel
-// (coalesced stores).  Writes gt (unmasked, nullable) and gz = gt x [mask > 0]
-// (mask nullable).
-constexpr int HB_PIX = 16;
+// g[n, 2i+u-1, 2j+v-1, o] (g zero outside the map).  The head weights,
+// transposed to [27][C], sit in shared memory once per block; a thread takes
+// 8 channels of HB_P neighbouring t_1 pixels of a row (C/8 threads per pixel
+// group, 16-byte bf16 accesses), so each 16-byte weight read from shared
+// memory serves HB_P pixels, and reads the pixels' g vectors itself.
+// Writes gt (unmasked, nullable) and gz = gt x [mask > 0] (mask nullable).
+template <typename ActT>
+__device__ __forceinline__ void load8(const ActT *p, float (&v)[8]);
+template <>
+__device__ __forceinline__ void load8<float>(const float *p, float (&v)[8]) {
+  const float4 a = __ldg(reinterpret_cast<const float4 *>(p)), b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+  v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+}
+template <>
+__device__ __forceinline__ void load8<__nv_bfloat16>(const __nv_bfloat16 *p, float (&v)[8]) {
+  const uint4 r = __ldg(reinterpret_cast<const uint4 *>(p));
+  const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    v[2 * e] = __uint_as_float(w[e] << 16);
+    v[2 * e + 1] = __uint_as_float(w[e] & 0xFFFF0000u);
+  }
+}
+template <typename ActT>
+__device__ __forceinline__ void store8(ActT *p, const float (&v)[8]);
+template <>
+__device__ __forceinline__ void store8<float>(float *p, const float (&v)[8]) {
+  reinterpret_cast<float4 *>(p)[0] = make_float4(v[0], v[1], v[2], v[3]);
+  reinterpret_cast<float4 *>(p)[1] = make_float4(v[4], v[5], v[6], v[7]);
+}
+template <>
+__device__ __forceinline__ void store8<__nv_bfloat16>(__nv_bfloat16 *p, const float (&v)[8]) {
+  uint32_t w[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+    w[e] = *reinterpret_cast<const uint32_t *>(&h);
+  }
+  *reinterpret_cast<uint4 *>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+constexpr int HB_P = 4;  // t_1 pixels per thread (along a row)
 template <typename ActT>
 __global__ void __launch_bounds__(256) head_bwd_kernel(const float *__restrict__ g4, const float *__restrict__ Wh,
                                                        const ActT *__restrict__ mask, ActT *__restrict__ gt,
                                                        ActT *__restrict__ gz, int N, int Hh, int Wh_, int C) {
-  extern __shared__ float hb_smem[];
-  float *wt = hb_smem;            // [27][C]
-  float *gs = hb_smem + 27 * C;   // [HB_PIX][27]
+  extern __shared__ float4 wt4[];  // [27][C / 4], row r = 9 o + 3 u + v
+  float *wt = reinterpret_cast<float *>(wt4);
   for (int e = threadIdx.x; e < 27 * C; e += blockDim.x) {
-    const int c = e / 27, r = e - c * 27;  // W[c][o][u][v], r = 9 o + 3 u + v
+    const int c = e / 27, r = e - c * 27;  // W[c][o][u][v]
     wt[r * C + c] = __ldg(Wh + e);
   }
-  const long long total = (long long)N * Hh * Wh_;
-  const long long p0 = (long long)blockIdx.x * HB_PIX;
-  const int H = 2 * Hh, W = 2 * Wh_;
-  for (int e = threadIdx.x; e < HB_PIX * 27; e += blockDim.x) {
-    const int lp = e / 27, r = e - lp * 27;
-    const long long pix = p0 + lp;
-    float v = 0.f;
-    if (pix < total) {
-      const int o = r / 9, u = (r / 3) % 3, vv = r % 3;
-      const long long n = pix / ((long long)Hh * Wh_);
-      const int rem = (int)(pix - n * Hh * Wh_);
-      const int i = rem / Wh_, j = rem - (rem / Wh_) * Wh_;
-      const int y = 2 * i + u - 1, x = 2 * j + vv - 1;
-      if ((unsigned)y < (unsigned)H && (unsigned)x < (unsigned)W) v = g4[((n * H + y) * W + x) * 4 + o];
-    }
-    gs[e] = v;
-  }
   __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int lp = warp; lp < HB_PIX; lp += blockDim.x >> 5) {
-    const long long pix = p0 + lp;
-    if (pix >= total) break;
-    const float *gp = gs + lp * 27;
-    for (int c = lane; c < C; c += 32) {
-      float acc = 0.f;
+  const int tpg = C / 8, gpb = (int)blockDim.x / tpg;  // threads per pixel group, groups per block step
+  const int lg = threadIdx.x / tpg, c0 = 8 * (threadIdx.x - lg * tpg);
+  if (lg >= gpb) return;
+  const int gpr = (Wh_ + HB_P - 1) / HB_P;  // pixel groups per t_1 row
+  const long long groups = (long long)N * Hh * gpr;
+  const int H = 2 * Hh, W = 2 * Wh_, C4 = C / 4;
+  for (long long gi = (long long)blockIdx.x * gpb + lg; gi < groups; gi += (long long)gridDim.x * gpb) {
+    const long long row = gi / gpr;  // n * Hh + i
+    const int j0 = HB_P * (int)(gi - row * gpr);
+    const long long n = row / Hh;
+    const int i = (int)(row - n * Hh);
+    float acc[HB_P][8];
 #pragma unroll
-      for (int r = 0; r < 27; ++r) acc = fmaf(wt[r * C + c], gp[r], acc);
-      const size_t off = (size_t)pix * C + c;
-      if (gt) gt[off] = stf<ActT>(acc);
-      if (mask && !(ldf<ActT>(mask + off) > 0.f)) acc = 0.f;
-      gz[off] = stf<ActT>(acc);
+    for (int p = 0; p < HB_P; ++p)
+#pragma unroll
+      for (int e = 0; e < 8; ++e) acc[p][e] = 0.f;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      const int y = 2 * i + u - 1;
+      if ((unsigned)y >= (unsigned)H) continue;
+      const float4 *grow = reinterpret_cast<const float4 *>(g4) + (n * H + y) * W;
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        float w[3][8];  // the tap's weights of output channels o = 0..2, channels c0 .. c0 + 7
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+          const float4 lo = wt4[(9 * o + 3 * u + v) * C4 + c0 / 4], hi = wt4[(9 * o + 3 * u + v) * C4 + c0 / 4 + 1];
+          w[o][0] = lo.x, w[o][1] = lo.y, w[o][2] = lo.z, w[o][3] = lo.w;
+          w[o][4] = hi.x, w[o][5] = hi.y, w[o][6] = hi.z, w[o][7] = hi.w;
+        }
+#pragma unroll
+        for (int p = 0; p < HB_P; ++p) {
+          const int x = 2 * (j0 + p) + v - 1;
+          if ((unsigned)x >= (unsigned)W) continue;
+          const float4 g = __ldg(grow + x);
+#pragma unroll
+          for (int e = 0; e < 8; ++e)
+            acc[p][e] = fmaf(g.z, w[2][e], fmaf(g.y, w[1][e], fmaf(g.x, w[0][e], acc[p][e])));
+        }
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < HB_P; ++p) {
+      if (j0 + p >= Wh_) break;
+      const size_t off = ((size_t)row * Wh_ + j0 + p) * C + c0;
+      if (gt) store8<ActT>(gt + off, acc[p]);
+      if (mask) {
+        float m[8];
+        load8<ActT>(mask + off, m);
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (!(m[e] > 0.f)) acc[p][e] = 0.f;
+      }
+      store8<ActT>(gz + off, acc[p]);
     }
   }
 }
@@ -236,26 +301,78 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const ActR *__restrict__ R, 
   }
 }
 
-// db[c] += sum over pixels of T[pix][c], c < Craw.  256 threads: up to 256
-// channels side by side (coalesced), 256 / that many pixel lanes.
+// db[c] += sum over pixels of T[pix][c], c < Craw.  A thread sums one
+// 16-byte group of V channels over every L-th pixel of the block's range
+// (G = C / V groups side by side, L = 256 / G pixel lanes, four loads in
+// flight); the L partial rows are then added through shared memory and the
+// block total goes to db with one atomic per channel.  AccT = double (the
+// FP32 path): Kahan-compensated partial sums, totals in fp64.
 template <typename Act, typename AccT>
 __global__ void __launch_bounds__(256) colsum_kernel(const Act *__restrict__ T, long long npix, int C, int Craw,
                                                      long long pix_per_block, AccT *__restrict__ db) {
+  constexpr int V = 16 / sizeof(Act);
+  constexpr bool KAHAN = sizeof(AccT) == 8;
+  extern __shared__ float cs_part[];  // [L][C] sums, then [L][C] compensations
+  const int G = C / V, L = 256 / G;
+  const int sub = threadIdx.x / G, g = threadIdx.x - sub * G;
   const long long p0 = (long long)blockIdx.x * pix_per_block;
   const long long p1 = p0 + pix_per_block < npix ? p0 + pix_per_block : npix;
-  const int cs = C < 256 ? C : 256;
-  const int lanes = 256 / cs;
-  const int cl = threadIdx.x % cs, sub = threadIdx.x / cs;
-  if (sub >= lanes) return;
-  for (int c = cl; c < C; c += cs) {
-    float s = 0.f, comp = 0.f;  // Kahan-compensated (the compensation is dropped for fp32 totals)
-    for (long long p = p0 + sub; p < p1; p += lanes) {
-      const float y = ldf<Act>(T + (size_t)p * C + c) - comp;
-      const float t = s + y;
-      comp = (t - s) - y;
-      s = t;
+  float s[V], cp[V];
+#pragma unroll
+  for (int e = 0; e < V; ++e) s[e] = cp[e] = 0.f;
+  auto add = [&](const float (&x)[V]) {
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      if constexpr (KAHAN) {
+        const float y = x[e] - cp[e];
+        const float t = s[e] + y;
+        cp[e] = (t - s[e]) - y;
+        s[e] = t;
+      } else {
+        s[e] += x[e];
+      }
     }
-    if (c < Craw) atomicAdd(db + c, (AccT)s - (AccT)comp);
+  };
+  auto load = [&](long long p, float (&x)[V]) {
+    if constexpr (V == 8) {
+      load8<Act>(T + (size_t)p * C + g * V, x);
+    } else {
+      const float4 a = __ldg(reinterpret_cast<const float4 *>(T + (size_t)p * C + g * V));
+      x[0] = a.x, x[1] = a.y, x[2] = a.z, x[3] = a.w;
+    }
+  };
+  if (sub < L) {
+    long long p = p0 + sub;
+    for (; p + 3ll * L < p1; p += 4ll * L) {
+      float x0[V], x1[V], x2[V], x3[V];
+      load(p, x0);
+      load(p + L, x1);
+      load(p + 2ll * L, x2);
+      load(p + 3ll * L, x3);
+      add(x0);
+      add(x1);
+      add(x2);
+      add(x3);
+    }
+    for (; p < p1; p += L) {
+      float x0[V];
+      load(p, x0);
+      add(x0);
+    }
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+      cs_part[sub * C + g * V + e] = s[e];
+      if constexpr (KAHAN) cs_part[(L + sub) * C + g * V + e] = cp[e];
+    }
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < Craw; c += blockDim.x) {
+    AccT t = 0;
+    for (int l = 0; l < L; ++l) {
+      t += (AccT)cs_part[l * C + c];
+      if constexpr (KAHAN) t -= (AccT)cs_part[(L + l) * C + c];
+    }
+    atomicAdd(db + c, t);
   }
 }
 
@@ -285,33 +402,38 @@ __global__ void dinput_kernel(const Act *__restrict__ g16, const float *__restri
 }  // namespace
 
 cudaError_t launch_l1_grad(const float *out, const float *target, int N, int H, int W, bool grad_out, bool out_relu,
-                           float *g4, float *loss, cudaStream_t st) {
+                           float *g4, void *g8, float *loss, cudaStream_t st) {
   const long long total = (long long)N * H * W;
   if (total == 0) return cudaSuccess;
   const float inv = 1.0f / (float)(3.0 * (double)total);
   l1_grad_kernel<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(out, target, N, H, W, grad_out ? 1 : 0,
-                                                                  out_relu ? 1 : 0, inv, g4, loss);
+                                                                  out_relu ? 1 : 0, inv, g4,
+                                                                  static_cast<__nv_bfloat16 *>(g8), loss);
   return cudaGetLastError();
 }
 
 cudaError_t launch_head_bwd(const float *g4, const float *Whead, const void *mask, void *gt, void *gz, int N, int Hh,
-                            int Wh, int C, bool bf16, cudaStream_t st) {
+                            int Wh, int C, bool bf16, int num_sms, cudaStream_t st) {
   const long long total = (long long)N * Hh * Wh;
   if (total == 0) return cudaSuccess;
-  const size_t smem = (size_t)(27 * C + HB_PIX * 27) * sizeof(float);
-  const unsigned blocks = (unsigned)((total + HB_PIX - 1) / HB_PIX);
+  if (C % 8 || C > 2048) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)27 * C * sizeof(float);
+  const long long gpb = 256 / (C / 8), groups = (long long)N * Hh * ((Wh + HB_P - 1) / HB_P);
+  long long blocks = (groups + gpb - 1) / gpb;
+  if (blocks > 8ll * num_sms) blocks = 8ll * num_sms;
   cudaError_t e;
   if (bf16) {
     e = cudaFuncSetAttribute(head_bwd_kernel<__nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    head_bwd_kernel<__nv_bfloat16><<<blocks, 256, smem, st>>>(
+    head_bwd_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, smem, st>>>(
         g4, Whead, static_cast<const __nv_bfloat16 *>(mask), static_cast<__nv_bfloat16 *>(gt),
         static_cast<__nv_bfloat16 *>(gz), N, Hh, Wh, C);
   } else {
     e = cudaFuncSetAttribute(head_bwd_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    head_bwd_kernel<float><<<blocks, 256, smem, st>>>(g4, Whead, static_cast<const float *>(mask),
-                                                      static_cast<float *>(gt), static_cast<float *>(gz), N, Hh, Wh, C);
+    head_bwd_kernel<float><<<(unsigned)blocks, 256, smem, st>>>(g4, Whead, static_cast<const float *>(mask),
+                                                                static_cast<float *>(gt), static_cast<float *>(gz),
+                                                                N, Hh, Wh, C);
   }
   return cudaGetLastError();
 }
@@ -356,20 +478,25 @@ cudaError_t launch_wgrad(const void *R, bool r_bf16, const void *Q, bool q_bf16,
 cudaError_t launch_colsum(const void *T, bool bf16, long long npix, int C, int Craw, float *db, double *db64,
                           int num_sms, cudaStream_t st) {
   if (npix == 0) return cudaSuccess;
+  const int V = bf16 ? 8 : 4;
+  if (C % V || C / V > 256) return cudaErrorInvalidValue;
+  const int L = 256 / (C / V);
   long long ppb = (npix + 2ll * num_sms - 1) / (2ll * num_sms);
-  if (ppb < 64) ppb = 64;
+  if (ppb < 4ll * L) ppb = 4ll * L;
   const unsigned blocks = (unsigned)((npix + ppb - 1) / ppb);
+  const size_t smem = (size_t)(db64 ? 2 : 1) * L * C * sizeof(float);
   using bf = __nv_bfloat16;
   if (db64) {
     if (bf16)
-      colsum_kernel<bf, double><<<blocks, 256, 0, st>>>(static_cast<const bf *>(T), npix, C, Craw, ppb, db64);
+      colsum_kernel<bf, double><<<blocks, 256, smem, st>>>(static_cast<const bf *>(T), npix, C, Craw, ppb, db64);
     else
-      colsum_kernel<float, double><<<blocks, 256, 0, st>>>(static_cast<const float *>(T), npix, C, Craw, ppb, db64);
+      colsum_kernel<float, double><<<blocks, 256, smem, st>>>(static_cast<const float *>(T), npix, C, Craw, ppb,
+                                                              db64);
   } else {
     if (bf16)
-      colsum_kernel<bf, float><<<blocks, 256, 0, st>>>(static_cast<const bf *>(T), npix, C, Craw, ppb, db);
+      colsum_kernel<bf, float><<<blocks, 256, smem, st>>>(static_cast<const bf *>(T), npix, C, Craw, ppb, db);
     else
-      colsum_kernel<float, float><<<blocks, 256, 0, st>>>(static_cast<const float *>(T), npix, C, Craw, ppb, db);
+      colsum_kernel<float, float><<<blocks, 256, smem, st>>>(static_cast<const float *>(T), npix, C, Craw, ppb, db);
   }
   return cudaGetLastError();
 }

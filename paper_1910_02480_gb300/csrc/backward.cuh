@@ -6,21 +6,23 @@
 namespace drc {
 
 // L1 loss (added to *loss, nullable) and dL/dout as NHWC4 fp32 [N][H][W][4]
-// from out/target [N][3][H][W]; grad_out: target already is dL/dout.
+// (and, g8 nullable, as bf16 NHWC8) from out/target [N][3][H][W]; grad_out:
+// target already is dL/dout.
 cudaError_t launch_l1_grad(const float *out, const float *target, int N, int H, int W, bool grad_out, bool out_relu,
-                           float *g4, float *loss, cudaStream_t st);
+                           float *g4, void *g8, float *loss, cudaStream_t st);
 
 // Head backward (data): gradient w.r.t. t_1 [N][Hh][Wh][C] from g4 and the
 // head weights [C][3][3][3]; gt (nullable) unmasked, gz masked by mask > 0.
 cudaError_t launch_head_bwd(const float *g4, const float *Whead, const void *mask, void *gt, void *gz, int N, int Hh,
-                            int Wh, int C, bool bf16, cudaStream_t st);
+                            int Wh, int C, bool bf16, int num_sms, cudaStream_t st);
 
 // dW[m][q][3][3] += sum R[n,i,j,m] Q[n,2i+u-1,2j+v-1,q] (see backward.cu),
 // into dW64 (fp64, compensated; nullable) or else dW (fp32).
 cudaError_t launch_wgrad(const void *R, bool r_bf16, const void *Q, bool q_bf16, int N, int Hb, int Wb, int Mr,
                          int Qc, int Qraw, float *dW, double *dW64, int num_sms, cudaStream_t st);
 
-// db[c] += column sums of T [npix][C], c < Craw, into db64 (nullable) or db.
+// db[c] += column sums of T [npix][C], c < Craw, into db64 (nullable) or db;
+// C a multiple of 16 bytes' worth of elements (8 bf16 / 4 fp32).
 cudaError_t launch_colsum(const void *T, bool bf16, long long npix, int C, int Craw, float *db, double *db64,
                           int num_sms, cudaStream_t st);
 

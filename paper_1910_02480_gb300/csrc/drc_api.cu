@@ -711,6 +711,7 @@ struct TrainBufs {
   std::vector<uint8_t *> e, t, r;         // e[q] q=1..S; t[q] q=1..S-1; r[s] (output of d_s, level s-1) s=2..S
   std::vector<uint8_t *> Gt, gzd, gze;    // grad w.r.t. t_q (unmasked) and masked by r_{q+1}; encoder grad z_q
   float *out = nullptr, *g4 = nullptr;    // network output [N][3][H][W]; dL/dout NHWC4
+  void *g8 = nullptr;                     // BF16 contexts: dL/dout as bf16 NHWC8 (the head's weight gradient)
   uint8_t *dx16 = nullptr;                // input gradient NHWC16
   double *dW64 = nullptr;                 // FP32 path: fp64 accumulation of the weight gradients
 };
@@ -743,6 +744,7 @@ size_t train_layout(const drc_ctx *c, int N, int H, int W, bool recompute, void 
   for (int q = 1; q <= S; ++q) b.gze[q] = take(level(q));
   b.out = reinterpret_cast<float *>(take((size_t)N * 3 * H * W * sizeof(float)));
   b.g4 = reinterpret_cast<float *>(take((size_t)N * H * W * 4 * sizeof(float)));
+  if (c->prec != PREC_TF32X3) b.g8 = take((size_t)N * H * W * 8 * 2);
   b.dx16 = take((size_t)N * H * W * 16 * eb);
   if (c->prec == PREC_TF32X3) b.dW64 = reinterpret_cast<double *>(take(c->n_floats * sizeof(double)));
   if (tb) *tb = b;
@@ -755,7 +757,9 @@ size_t train_layout(const drc_ctx *c, int N, int H, int W, bool recompute, void 
 cudaError_t weight_grad(const drc_ctx *c, const void *R, bool r_bf16, const void *Q, bool q_bf16, int N, int Hb,
                         int Wb, int Mr, int Qc, int Qraw, float *dW, double *dW64, cudaStream_t st) {
   EncodeTiledFn enc = encode_tiled();
-  if (r_bf16 && q_bf16 && !dW64 && enc && N > 0 && wgrad_tc_supported(Hb, Wb, Mr, Qc)) {
+  const int form = r_bf16 && q_bf16 && !dW64 && enc && N > 0 ? wgrad_tc_form(Hb, Wb, Mr, Qc) : WGRAD_TC_NONE;
+  if (form != WGRAD_TC_NONE) {
+    const bool narrow = form == WGRAD_TC_NARROW;
     WgradTcArgs a;
     memset(&a, 0, sizeof a);
     int rows, maps;
@@ -765,14 +769,15 @@ cudaError_t weight_grad(const drc_ctx *c, const void *R, bool r_bf16, const void
     cuuint32_t rb[2] = {64, 64}, re[2] = {1, 1};
     cuuint64_t qd[4] = {(cuuint64_t)Qc, (cuuint64_t)(2 * Wb), (cuuint64_t)(2 * Hb), (cuuint64_t)N};
     cuuint64_t qs[3] = {(cuuint64_t)Qc * 2, (cuuint64_t)Qc * 2 * 2 * Wb, (cuuint64_t)Qc * 2 * 2 * Wb * 2 * Hb};
-    cuuint32_t qb[4] = {64, (cuuint32_t)(2 * Wb), (cuuint32_t)(2 * rows), (cuuint32_t)maps}, qe[4] = {1, 2, 2, 1};
+    cuuint32_t qb[4] = {narrow ? 8u : 64u, (cuuint32_t)(2 * Wb), (cuuint32_t)(2 * rows), (cuuint32_t)maps};
+    cuuint32_t qe[4] = {1, 2, 2, 1};
     const bool ok =
         enc(&a.mapR, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(R), rd, rs, rb, re,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
         enc(&a.mapQ, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void *>(Q), qd, qs, qb, qe,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+            CU_TENSOR_MAP_INTERLEAVE_NONE, narrow ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
     if (ok) {
       a.dW = dW;
       a.status = c->d_status;
@@ -782,10 +787,16 @@ cudaError_t weight_grad(const drc_ctx *c, const void *R, bool r_bf16, const void
       a.Wb = Wb;
       a.Mr = Mr;
       a.Qraw = Qraw;
-      a.BNq = Qc % 128 == 0 ? 128 : 64;
-      a.m_tiles = Mr / 128;
-      a.n_tiles = Qc / a.BNq;
-      return launch_wgrad_tc(a, c->num_sms, st);
+      if (narrow) {  // N of the GEMM = R channels, up to 256 per tile
+        a.BN = Mr <= 256 ? Mr : (Mr % 256 == 0 ? 256 : (Mr % 128 == 0 ? 128 : 64));
+        a.m_tiles = 1;
+        a.n_tiles = Mr / a.BN;
+      } else {
+        a.BN = Qc % 128 == 0 ? 128 : 64;
+        a.m_tiles = Mr / 128;
+        a.n_tiles = Qc / a.BN;
+      }
+      return launch_wgrad_tc(a, form, c->num_sms, st);
     }
   }
   return launch_wgrad(R, r_bf16, Q, q_bf16, N, Hb, Wb, Mr, Qc, Qraw, dW, dW64, c->num_sms, st);
@@ -1349,7 +1360,7 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
   if (loss && (e = cudaMemsetAsync(loss, 0, sizeof(float), st)) != cudaSuccess) return cuda_fail(c, e, "loss clear");
 
   if ((s = train_forward(c, b, in, N, H, W, flags, false, st)) != DRC_OK) return s;
-  DRC_TRACED(tr, "loss", st, e = launch_l1_grad(b.out, target, N, H, W, grad_out, c->cfg.out_relu != 0, b.g4, loss, st));
+  DRC_TRACED(tr, "loss", st, e = launch_l1_grad(b.out, target, N, H, W, grad_out, c->cfg.out_relu != 0, b.g4, b.g8, loss, st));
   if (e != cudaSuccess) return cuda_fail(c, e, "loss");
 
   // output head: t_1 -> out; the gradient w.r.t. t_1 is masked by the ReLU of
@@ -1359,10 +1370,11 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
   DRC_TRACED(tr, "head bwd", st,
              e = launch_head_bwd(b.g4, c->d_wraw + Lh.w_off, S >= 2 ? (const void *)b.r[2] : b.e[1],
                                  S >= 2 ? (void *)b.Gt[1] : nullptr, S >= 2 ? b.gzd[1] : b.gze[1], N, H >> 1, W >> 1,
-                                 c1, bf, st));
+                                 c1, bf, c->num_sms, st));
   if (e != cudaSuccess) return cuda_fail(c, e, "head backward");
   DRC_TRACED(tr, "wgrad head", st,
-             e = weight_grad(c, S >= 2 ? b.t[1] : b.e[1], bf, b.g4, false, N, H >> 1, W >> 1, c1, 4, 3,
+             e = weight_grad(c, S >= 2 ? b.t[1] : b.e[1], bf, bf ? b.g8 : (const void *)b.g4, bf, N, H >> 1, W >> 1,
+                             c1, bf ? 8 : 4, 3,
                               dweights + Lh.w_off, o64(Lh.w_off), st));
   if (e == cudaSuccess)
     DRC_TRACED(tr, "bgrad head", st,
@@ -1377,11 +1389,12 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
     const Layer &F = c->layers[li], &D = c->dlayers[li];
     const void *tin = s2 == S ? b.e[S] : b.t[s2];
     const long long npix = (long long)N * (H >> (s2 - 1)) * (W >> (s2 - 1));
-    DRC_TRACED(tr, "wgrad", st,
+    const std::string wname = std::string("wgrad ") + F.name, bname = std::string("bgrad ") + F.name;
+    DRC_TRACED(tr, wname.c_str(), st,
                e = weight_grad(c, tin, bf, b.gzd[s2 - 1], bf, N, H >> s2, W >> s2, F.Cin, F.Cout, F.Cout,
                                 dweights + F.w_off, o64(F.w_off), st));
     if (e == cudaSuccess)
-      DRC_TRACED(tr, "bgrad", st,
+      DRC_TRACED(tr, bname.c_str(), st,
                  e = launch_colsum(b.gzd[s2 - 1], bf, npix, F.Cout, F.Cout, dweights + F.b_off, o64(F.b_off),
                                    c->num_sms, st));
     if (e != cudaSuccess) return cuda_fail(c, e, "decoder weight gradient");
@@ -1408,11 +1421,12 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
     const Layer &F = c->layers[li], &D = c->dlayers[li];
     const long long npix = (long long)N * (H >> s2) * (W >> s2);
     const void *xin = s2 == 1 ? (const void *)b.in8 : b.e[s2 - 1];
-    DRC_TRACED(tr, "wgrad", st,
+    const std::string wname = std::string("wgrad ") + F.name, bname = std::string("bgrad ") + F.name;
+    DRC_TRACED(tr, wname.c_str(), st,
                e = weight_grad(c, b.gze[s2], bf, xin, bf, N, H >> s2, W >> s2, F.Cout, F.Cin, F.Cin_raw,
                                 dweights + F.w_off, o64(F.w_off), st));
     if (e == cudaSuccess)
-      DRC_TRACED(tr, "bgrad", st,
+      DRC_TRACED(tr, bname.c_str(), st,
                  e = launch_colsum(b.gze[s2], bf, npix, F.Cout, F.Cout, dweights + F.b_off, o64(F.b_off),
                                    c->num_sms, st));
     if (e != cudaSuccess) return cuda_fail(c, e, "encoder weight gradient");

@@ -10,11 +10,12 @@ tol = 2^-22 (sqrt(K) + 16) for K pixels -- a random-walk estimate of fp32
 rounding over the chained partial sums (tensor-core accumulator, split K,
 atomics) with a factor 2 for accumulators that truncate.  At the small sizes
 this is below the weight of one pixel (~S/K), so a dropped or doubled pixel,
-tap or channel fails.  The shapes cover both kernels (tensor cores: Mr a
-multiple of 128, Qc of 64, 64-pixel blocks of whole rows of whole maps;
-CUDA cores otherwise, and FP32), ragged tails, several m and q tiles, and the
-layers of the training benchmark (256 maps of 64 x 64, widths
-64/128/256/512) at full size."""
+tap or channel fails.  The shapes cover every kernel (tensor cores, wide
+form: Mr a multiple of 128, Qc of 64; narrow form: Qc = 8, Mr a multiple of
+64; both need 64-pixel blocks of whole rows of whole maps; CUDA cores
+otherwise, and FP32), ragged tails, several m and q tiles, and the layers of
+the training benchmark (256 maps of 64 x 64, widths 64/128/256/512) at full
+size."""
 import numpy as np
 import pytest
 
@@ -90,11 +91,23 @@ def test_transposed_layer_orientation(ctx):
     _check(ctx, 6, 8, 8, 128, 64, 64, torch.bfloat16, seed=4, transposed=True)
 
 
+@pytest.mark.parametrize("N,Hb,Wb,Mr,Qc,Qraw", [
+    (3, 16, 16, 64, 8, 7),     # the first layer: 8 stored input channels, 7 in dW
+    (7, 8, 8, 64, 8, 3),       # the head: dL/dout in 8 channels, 3 in dW
+    (5, 4, 4, 128, 8, 8),      # four maps per block, ragged
+    (3, 8, 8, 320, 8, 8),      # five 64-channel column tiles
+    (2, 16, 16, 256, 8, 7),    # one 256-column tile
+])
+def test_tensor_core_narrow_shapes(ctx, N, Hb, Wb, Mr, Qc, Qraw):
+    _check(ctx, N, Hb, Wb, Mr, Qc, Qraw, torch.bfloat16, seed=N + 7)
+
+
 @pytest.mark.parametrize("N,Hb,Wb,Mr,Qc,Qraw,dt", [
     (4, 8, 8, 64, 32, 32, "bf16"),   # Mr not a multiple of 128
     (4, 3, 5, 128, 64, 64, "bf16"),  # rows of 5 pixels: no whole-row blocks
     (4, 8, 8, 128, 64, 64, "fp32"),  # FP32 operands
-    (3, 16, 16, 64, 8, 7, "bf16"),   # the first layer's 8 stored input channels
+    (3, 8, 8, 48, 8, 7, "bf16"),     # 8 Q channels, Mr not a multiple of 64
+    (3, 8, 8, 64, 16, 16, "bf16"),   # 16 Q channels
 ])
 def test_cuda_core_shapes(ctx, N, Hb, Wb, Mr, Qc, Qraw, dt):
     _check(ctx, N, Hb, Wb, Mr, Qc, Qraw, torch.bfloat16 if dt == "bf16" else torch.float32, seed=N + 1)
@@ -104,10 +117,16 @@ def test_cuda_core_shapes(ctx, N, Hb, Wb, Mr, Qc, Qraw, dt):
     (16, 128, 64, 64),    # encoder stage 2 (and decoder stage 2 transposed)
     (8, 256, 128, 128),   # stage 3
     (4, 512, 256, 256),   # stage 4: four m tiles, two q tiles
-    (32, 64, 8, 7),       # stage 1 (CUDA cores)
+    (32, 64, 8, 7),       # stage 1: narrow form
 ])
 def test_training_benchmark_layers_full_size(ctx, Hb, Mr, Qc, Qraw):
     _check(ctx, 256, Hb, Hb, Mr, Qc, Qraw, torch.bfloat16, seed=Hb)
+
+
+def test_training_benchmark_head_full_size(ctx):
+    """The head's weight gradient: R = t_1 (64 channels, 32 x 32), Q = dL/dout
+    in 8 bf16 channels at 64 x 64, 3 of them in dW."""
+    _check(ctx, 256, 32, 32, 64, 8, 3, torch.bfloat16, seed=31)
 
 
 def test_empty_batch_and_accumulation(ctx):
