@@ -40,6 +40,8 @@ CASES = [
     ([16, 32, 48, 64], 3, 32, 48, True, 0, False),
     ([64, 128, 256], 9, 32, 32, True, 0, False),
     ([64, 128, 256, 512], 2, 64, 64, True, 0, False),
+    ([96, 128], 3, 32, 48, True, 0, False),   # head over 96 channels: staged weights, halo column in the map
+    ([128], 2, 64, 64, True, 2, True),        # head over 128 channels on 2 x 2 tiles per map
 ]
 
 
