@@ -356,9 +356,25 @@ __device__ __forceinline__ void raw_convert_tma(const ConvArgs &a, int pt, const
 // PROD_TMA_CONVERT step 2 for one group of four producer warps (128
 // threads, gt = thread index in the group): the whole K block, 8 chunks of
 // 128 rows.
-template <int PREC>
+// With tap boxes the slot is tap-major: chunk (r, q) of the K block is at
+// (q / 2) BM 32 + 32 r + 16 (q % 2); a quarter warp then takes 8 rows of one
+// chunk, so the reads see at most 2-way bank conflicts and the swizzled
+// writes none.
+__device__ __forceinline__ const uint8_t *tap_chunk(const uint8_t *slot, int r, int q) {
+  return slot + (q >> 1) * (BM * 32) + r * 32 + (q & 1) * 16;
+}
+template <int PREC, bool TAPS>
 __device__ __forceinline__ void raw_convert_tma_group(int gt, const uint8_t *slot, uint8_t *a0, uint8_t *a1) {
   const int lane = gt & 31, gw = gt >> 5, q = lane & 7;
+  if constexpr (TAPS) {
+    const int rr = lane & 7, qq = lane >> 3;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const int r = 32 * gw + 8 * (it & 3) + rr, qt = 4 * (it >> 2) + qq;
+      convert_store<PREC>(a0, a1, swz(r, qt), reinterpret_cast<const uint4 *>(tap_chunk(slot, r, qt)));
+    }
+    return;
+  }
 #pragma unroll
   for (int it = 0; it < 8; ++it) {
     const int r = (lane >> 3) + 4 * gw + 16 * it;
@@ -370,6 +386,7 @@ __device__ __forceinline__ void raw_convert_tma_group(int gt, const uint8_t *slo
 // q = warp % 4) of the whole K block goes from the raw slot, split into tf32
 // hi/lo, into the A stage's tensor-memory columns [0, 32) (hi) and
 // [32, 64) (lo).
+template <bool TAPS>
 __device__ __forceinline__ void raw_convert_tmem(int q, int lane, const uint8_t *slot, uint32_t ta) {
   const int r = 32 * q + lane;
   const uint32_t t0 = ta + ((uint32_t)(32 * q) << 16);
@@ -378,7 +395,7 @@ __device__ __forceinline__ void raw_convert_tmem(int q, int lane, const uint8_t 
     uint32_t hi[16], lo[16];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const uint4 u = lds128(slot + swz(r, 4 * h + c));
+      const uint4 u = lds128(TAPS ? tap_chunk(slot, r, 4 * h + c) : slot + swz(r, 4 * h + c));
       const float x[4] = {__uint_as_float(u.x), __uint_as_float(u.y), __uint_as_float(u.z), __uint_as_float(u.w)};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
@@ -413,6 +430,18 @@ template <int PREC>
 __device__ __forceinline__ void tma_issue(const ConvArgs &a, const TmaCursor &c, uint32_t dst, uint32_t bar) {
   using T = PrecTraits<PREC>;
   constexpr int BKE = KROW_BYTES / T::ELEM;
+  if (a.tap_boxes) {
+    // four taps of 8 channels per K block (stride-2 conv), one box each; a
+    // slot past the last tap loads tap 0 again, against B rows packed as zero
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int tap = 4 * c.kb + t < c.ntaps ? 4 * c.kb + t : 0;
+      const unsigned tb = (unsigned)(c.taps >> (4 * tap)) & 15u;
+      const int dy = (int)(tb & 3u), dx = (int)(tb >> 2);
+      tma_load_4d(dst + (uint32_t)(t * BM * 32), &a.tmap, 0, dx - 1, 2 * c.r0 + dy - 1, c.n0, bar);
+    }
+    return;
+  }
   const int kpt = a.Cin / BKE;  // K blocks per tap
   const int tap = c.kb / kpt;
   const int c0 = (c.kb - tap * kpt) * BKE;
@@ -458,6 +487,53 @@ __device__ __noinline__ void tma_issue_loop(const ConvArgs &a, uint32_t raw_u32,
   if (a.prof) atomicAdd(&a.prof[PROF_PROD_ISSUE], w_issue * 8);  // reported per producer warp like the others
 }
 
+// PROD_TMA_CONVERT / PROD_TMA_TMEM producer loop (TAPS: the raw slots hold
+// tap boxes, see tma_issue).
+template <int PREC, bool TAPS>
+__device__ __forceinline__ void convert_loop(const ConvArgs &a, uint8_t *data, uint8_t *raw, uint64_t *full_bar,
+                                             uint64_t *empty_bar, uint64_t *raw_full, uint64_t *raw_empty,
+                                             int stages, int sbytes, int R, int slot_bytes, int total_kb,
+                                             uint32_t tmem_base, unsigned long long &w_empty,
+                                             unsigned long long &w_copy, unsigned long long &w_conv,
+                                             unsigned long long &w_fence) {
+  const int pt = threadIdx.x - PROD_WARP0 * 32;  // 0..255
+  const int lane = pt & 31;
+  const int a_bytes = BM * KROW_BYTES;
+  // The raw boxes come from the TMA-issue warp (tma_issue_loop); the
+  // producer warps form two groups of four -- one warp per tensor-memory
+  // lane quarter -- that take alternate K blocks, so two blocks are being
+  // converted at any time.  K block j uses raw slot j % R and MMA stage
+  // j % stages; the barrier parities follow from j.
+  const int g = (pt >> 5) >> 2, gw = (pt >> 5) & 3, gt = pt & 127;
+  for (int jc = g; jc < total_kb; jc += 2) {
+    const int slot = jc % R, stage = jc % stages;
+    if (!pwait(a, w_copy, smem_u32(&raw_full[slot]), (uint32_t)((jc / R) & 1))) break;
+    if (!pwait(a, w_empty, smem_u32(&empty_bar[stage]), (uint32_t)(((jc / stages) & 1) ^ 1))) break;
+    uint8_t *a0 = data + stage * sbytes;
+    const long long tv0 = a.prof ? clock64() : 0;
+    if constexpr (PREC == PREC_TF32X3) {
+      if (a.prod_mode == PROD_TMA_TMEM)
+        raw_convert_tmem<TAPS>(gw, lane, raw + slot * slot_bytes, tmem_base + (uint32_t)(TS_A_COL0 + stage * 64));
+      else
+        raw_convert_tma_group<PREC, TAPS>(gt, raw + slot * slot_bytes, a0, a0 + a_bytes);
+    } else {
+      raw_convert_tma_group<PREC, false>(gt, raw + slot * slot_bytes, a0, a0 + a_bytes);
+    }
+    const long long tv1 = a.prof ? clock64() : 0;
+    fence_proxy_async_smem();  // A tile writes -> MMA; raw reads before the slot's next TMA write
+    tc_fence_before();         // tensor-memory A stores -> MMA (PROD_TMA_TMEM)
+    __syncwarp();
+    if (a.prof) {
+      w_conv += (unsigned long long)(tv1 - tv0);
+      w_fence += (unsigned long long)(clock64() - tv1);
+    }
+    if (lane == 0) {
+      mbar_arrive(smem_u32(&full_bar[stage]));
+      mbar_arrive(smem_u32(&raw_empty[slot]));
+    }
+  }
+}
+
 // Producer warps.  `raw` is the raw ring (unused in PROD_TMA_DIRECT).
 template <int PREC>
 __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint8_t *raw, uint64_t *full_bar,
@@ -501,39 +577,12 @@ __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint
       }
     }
   } else if (a.prod_mode == PROD_TMA_CONVERT || a.prod_mode == PROD_TMA_TMEM) {
-    // The raw boxes come from the TMA-issue warp (tma_issue_loop); the
-    // producer warps form two groups of four -- one warp per tensor-memory
-    // lane quarter -- that take alternate K blocks, so two blocks are being
-    // converted at any time.  K block j uses raw slot j % R and MMA stage
-    // j % stages; the barrier parities follow from j.
-    const int g = (pt >> 5) >> 2, gw = (pt >> 5) & 3, gt = pt & 127;
-    for (int jc = g; jc < total_kb; jc += 2) {
-      const int slot = jc % R, stage = jc % stages;
-      if (!pwait(a, w_copy, smem_u32(&raw_full[slot]), (uint32_t)((jc / R) & 1))) break;
-      if (!pwait(a, w_empty, smem_u32(&empty_bar[stage]), (uint32_t)(((jc / stages) & 1) ^ 1))) break;
-      uint8_t *a0 = data + stage * sbytes;
-      const long long tv0 = a.prof ? clock64() : 0;
-      if constexpr (PREC == PREC_TF32X3) {
-        if (a.prod_mode == PROD_TMA_TMEM)
-          raw_convert_tmem(gw, lane, raw + slot * slot_bytes, tmem_base + (uint32_t)(TS_A_COL0 + stage * 64));
-        else
-          raw_convert_tma_group<PREC>(gt, raw + slot * slot_bytes, a0, a0 + a_bytes);
-      } else {
-        raw_convert_tma_group<PREC>(gt, raw + slot * slot_bytes, a0, a0 + a_bytes);
-      }
-      const long long tv1 = a.prof ? clock64() : 0;
-      fence_proxy_async_smem();  // A tile writes -> MMA; raw reads before the slot's next TMA write
-      tc_fence_before();         // tensor-memory A stores -> MMA (PROD_TMA_TMEM)
-      __syncwarp();
-      if (a.prof) {
-        w_conv += (unsigned long long)(tv1 - tv0);
-        w_fence += (unsigned long long)(clock64() - tv1);
-      }
-      if (lane == 0) {
-        mbar_arrive(smem_u32(&full_bar[stage]));
-        mbar_arrive(smem_u32(&raw_empty[slot]));
-      }
-    }
+    if (a.tap_boxes)
+      convert_loop<PREC, true>(a, data, raw, full_bar, empty_bar, raw_full, raw_empty, stages, sbytes, R, slot_bytes,
+                               total_kb, tmem_base, w_empty, w_copy, w_conv, w_fence);
+    else
+      convert_loop<PREC, false>(a, data, raw, full_bar, empty_bar, raw_full, raw_empty, stages, sbytes, R, slot_bytes,
+                                total_kb, tmem_base, w_empty, w_copy, w_conv, w_fence);
   } else {
     // PROD_CPASYNC
     const int D = R - 1;
@@ -808,7 +857,7 @@ __device__ __forceinline__ void st4(void *base, size_t e, float4 v, const float 
 template <int PREC>
 __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t taddr, int BN, int n0, size_t ebase,
                                                 bool vrow, float *stg, unsigned long long &w_tfull, uint32_t tfull,
-                                                uint32_t par) {
+                                                uint32_t par, unsigned long long &w_ld) {
   const int lane = threadIdx.x & 31;
   size_t er[4];
   bool vr[4];
@@ -836,7 +885,9 @@ __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t tadd
   for (int cc = 0; cc < BN / 16; ++cc) {
     const int col0 = n0 + cc * 16;
     float v[16];
+    const long long tl0 = a.prof ? clock64() : 0;
     tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
+    if (a.prof) w_ld += (unsigned long long)(clock64() - tl0);
     const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
     const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
 #pragma unroll
@@ -1117,7 +1168,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     const int row = eq * 32 + lane;
     const int rows_per_map = a.Hrow * a.Wrow;
     int it = 0;
-    unsigned long long w_tfull = 0;
+    unsigned long long w_tfull = 0, w_ld = 0;
     const long long t_start = a.prof ? clock64() : 0;
     using act_t = typename T::act_t;
     uint8_t *yout = reinterpret_cast<uint8_t *>(a.y);
@@ -1142,7 +1193,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       if (plan.epi_stage) {
         const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
         if (!epi_tile_staged<PREC>(a, taddr, BN, tc.n_tile * BN, opix * a.Cout, vrow, epi_stg + eq * 32 * 20, w_tfull,
-                                   smem_u32(&tfull_bar[buf]), par))
+                                   smem_u32(&tfull_bar[buf]), par, w_ld))
           break;
         tc_fence_before();
         __syncwarp();
@@ -1193,6 +1244,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     }
     if (a.prof && lane == 0) {
       atomicAdd(&a.prof[PROF_EPI_WAIT_TFULL], w_tfull);
+      atomicAdd(&a.prof[PROF_EPI_LD], w_ld);
       atomicAdd(&a.prof[PROF_EPI_TOTAL], (unsigned long long)(clock64() - t_start));
     }
   }

@@ -45,6 +45,8 @@ enum ProdMode {
 struct ConvArgs {
   CUtensorMap tmap;  // A operand view for the TMA modes (64-byte aligned)
   int prod_mode;
+  int tap_boxes;     // TMA modes, FP32 with 8 stored input channels (32 bytes per tap): one box per tap,
+                     // four per K block, placed tap-major in the raw slot (BM rows x 32 bytes each)
   int kind;
   const void *x;     // input activations, NHWC
   void *y;           // output activations, NHWC
@@ -86,7 +88,7 @@ struct ConvArgs {
 enum ProfSlot {
   PROF_MMA_WAIT_FULL = 0, PROF_MMA_WAIT_TEMPTY, PROF_MMA_TOTAL, PROF_BLOAD_WAIT_EMPTY,
   PROF_PROD_WAIT_EMPTY, PROF_PROD_WAIT_COPY, PROF_PROD_TOTAL, PROF_EPI_WAIT_TFULL, PROF_EPI_TOTAL,
-  PROF_CTAS, PROF_PROD_CONVERT, PROF_PROD_FENCE, PROF_PROD_ISSUE, PROF_SLOTS = 16
+  PROF_CTAS, PROF_PROD_CONVERT, PROF_PROD_FENCE, PROF_PROD_ISSUE, PROF_EPI_LD, PROF_SLOTS = 16
 };
 
 struct SmemPlan {

@@ -134,9 +134,13 @@ EncodeTiledFn encode_tiled() {
 // force_mode >= 0 asks for that mode where the layer allows it (autotuner).
 void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
   a.prod_mode = PROD_CPASYNC;
+  a.tap_boxes = 0;
   const int bke = KROW_BYTES / (prec == PREC_TF32X3 ? 4 : (prec == PREC_BF16 ? 2 : 1));  // K elements per block
   const int Wr = a.Wrow, Hr = a.Hrow;
-  if (Wr > BM || BM % Wr || a.Cin % bke) return;
+  // FP32 conv over 8 stored channels (the first layer): 32 bytes per tap, so
+  // a K block holds four taps, each its own TMA box
+  const bool taps = prec == PREC_TF32X3 && a.kind == LK_CONV && a.Cin * 4 * 4 == KROW_BYTES;
+  if (Wr > BM || BM % Wr || (!taps && a.Cin % bke)) return;
   const int rows_t = Hr < BM / Wr ? Hr : BM / Wr;
   if ((rows_t * Wr) % Wr || BM % (rows_t * Wr) || (rows_t < Hr && Hr % rows_t)) return;
   const int maps_t = BM / (rows_t * Wr);
@@ -146,7 +150,7 @@ void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return;
   const int eb = prec == PREC_TF32X3 ? 4 : (prec == PREC_BF16 ? 2 : 1);  // stored activation bytes
-  const int box_c = KROW_BYTES / eb;                                     // channels per box row (128 bytes)
+  const int box_c = taps ? a.Cin : KROW_BYTES / eb;                      // channels per box row (128 / 32 bytes)
   cuuint64_t dims[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.Win, (cuuint64_t)a.Hin, (cuuint64_t)a.N};
   cuuint64_t strides[3] = {(cuuint64_t)a.Cin * eb, (cuuint64_t)a.Cin * eb * a.Win,
                            (cuuint64_t)a.Cin * eb * a.Win * a.Hin};
@@ -157,9 +161,11 @@ void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
                                 : (prec == PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
   CUresult r = enc(&a.tmap, dt,
                    4, const_cast<void *>(a.x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   taps ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return;
   if (force_mode == PROD_CPASYNC) return;
+  a.tap_boxes = taps ? 1 : 0;
   if (prec == PREC_TF32X3 && force_mode == PROD_TMA_CONVERT) {
     a.prod_mode = PROD_TMA_CONVERT;
     return;
@@ -1008,6 +1014,7 @@ drc_status autotune_layers(drc_ctx *c, std::vector<Layer> &Ls, std::vector<int> 
       if ((s = pack_layers(c, one, B, B_lo, st)) != DRC_OK) break;
       std::vector<int> mode_list{-1};
       if (c->prec == PREC_TF32X3 && bn <= 128) mode_list.push_back(PROD_TMA_CONVERT);
+      if (c->prec == PREC_TF32X3 && Ls[li].kind == LK_CONV && Ls[li].Cin == 8) mode_list.push_back(PROD_CPASYNC);
       for (int mode : mode_list) {
         float ms = 0.f;
         if ((s = time_layer(c, Ls, one[0], li, ch, B, B_lo, mode, st, e0, e1, &ms)) != DRC_OK) break;
@@ -1218,13 +1225,13 @@ drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, 
       fprintf(stderr,
               "[drc prof] layer %zu kind %d BN %d: per CTA kcycles: mma total %.1f wait_full %.1f wait_tempty %.1f | "
               "bload wait_empty %.1f | prod(8 warps) total %.1f wait_empty %.1f wait_copy %.1f issue %.1f convert %.1f "
-              "fence %.1f | epi(4 warps) total %.1f wait_tfull %.1f\n",
+              "fence %.1f | epi(4 warps) total %.1f wait_tfull %.1f acc_ld %.1f\n",
               li, c->layers[li].kind, c->layers[li].BN, v[PROF_MMA_TOTAL] / ctas / 1e3,
               v[PROF_MMA_WAIT_FULL] / ctas / 1e3, v[PROF_MMA_WAIT_TEMPTY] / ctas / 1e3,
               v[PROF_BLOAD_WAIT_EMPTY] / ctas / 1e3, v[PROF_PROD_TOTAL] / ctas / 8e3,
               v[PROF_PROD_WAIT_EMPTY] / ctas / 8e3, v[PROF_PROD_WAIT_COPY] / ctas / 8e3,
               v[PROF_PROD_ISSUE] / ctas / 8e3, v[PROF_PROD_CONVERT] / ctas / 8e3, v[PROF_PROD_FENCE] / ctas / 8e3,
-              v[PROF_EPI_TOTAL] / ctas / 4e3, v[PROF_EPI_WAIT_TFULL] / ctas / 4e3);
+              v[PROF_EPI_TOTAL] / ctas / 4e3, v[PROF_EPI_WAIT_TFULL] / ctas / 4e3, v[PROF_EPI_LD] / ctas / 4e3);
     }
   }
   return DRC_OK;

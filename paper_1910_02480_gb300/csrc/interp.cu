@@ -231,41 +231,68 @@ __global__ void grid_count_kernel(InterpArgs a, InterpScratch s) {
 }
 
 // Single block exclusive scan of counts[0..*n_ptr); counts become cursors,
-// starts[*n_ptr] = total.  Each thread sums a contiguous run of bins, the
-// run totals are scanned across the block, then each thread writes its run.
-__global__ void scan_kernel(const int *n_ptr, int *counts, int *starts) {
+// starts[*n_ptr] = total.  The bins go in tiles of 4 x blockDim.x: each
+// thread takes four consecutive bins (one 16-byte load and store), the
+// thread totals are scanned across the block, and the running total carries
+// to the next tile, whose loads are issued before this tile's scan.
+__device__ __forceinline__ void scan_load4(const int *counts, int nc, int i0, int (&v)[4]) {
+  if (i0 + 3 < nc) {
+    const int4 q = *reinterpret_cast<const int4 *>(counts + i0);
+    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = i0 + e < nc ? counts[i0 + e] : 0;
+  }
+}
+__global__ void __launch_bounds__(1024) scan_kernel(const int *n_ptr, int *counts, int *starts) {
   __shared__ int warp_tot[32];
   const int nc = *n_ptr;
-  const int per = (nc + blockDim.x - 1) / blockDim.x;
-  const int b0 = min(nc, (int)threadIdx.x * per), b1 = min(nc, b0 + per);
-  int run = 0;
-  for (int c = b0; c < b1; ++c) run += counts[c];
-  const int l = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int x = run;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (l >= o) x += y;
-  }
-  if (l == 31) warp_tot[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    const int nw = blockDim.x >> 5;
-    int t = l < nw ? warp_tot[l] : 0;
+  const int T = 4 * (int)blockDim.x;
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int carry = 0;
+  int v[4];
+  scan_load4(counts, nc, 4 * threadIdx.x, v);
+  for (int base = 0; base < nc; base += T) {
+    const int i0 = base + 4 * threadIdx.x;
+    int nv[4] = {0, 0, 0, 0};
+    if (base + T < nc) scan_load4(counts, nc, i0 + T, nv);
+    const int tsum = v[0] + v[1] + v[2] + v[3];
+    int x = tsum;
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, t, o);
-      if (l >= o) t += y;
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (l >= o) x += y;
     }
-    if (l < nw) warp_tot[l] = t;
+    if (l == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      int t = l < nw ? warp_tot[l] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (l >= o) t += y;
+      }
+      if (l < nw) warp_tot[l] = t;
+    }
+    __syncthreads();
+    const int off = carry + (w > 0 ? warp_tot[w - 1] : 0) + x - tsum;
+    const int o4[4] = {off, off + v[0], off + v[0] + v[1], off + v[0] + v[1] + v[2]};
+    if (i0 + 3 < nc) {
+      *reinterpret_cast<int4 *>(counts + i0) = make_int4(o4[0], o4[1], o4[2], o4[3]);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) starts[i0 + e] = o4[e];  // starts + i0 may not be 16-byte aligned
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (i0 + e < nc) {
+          counts[i0 + e] = o4[e];
+          starts[i0 + e] = o4[e];
+        }
+    }
+    carry += warp_tot[nw - 1];
+    __syncthreads();  // warp_tot is rewritten by the next tile
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = nv[e];
   }
-  __syncthreads();
-  int off = (w > 0 ? warp_tot[w - 1] : 0) + x - run;
-  for (int c = b0; c < b1; ++c) {
-    const int v = counts[c];
-    starts[c] = off;
-    counts[c] = off;
-    off += v;
-  }
-  if (threadIdx.x == blockDim.x - 1) starts[nc] = off;
+  if (threadIdx.x == 0) starts[nc] = carry;
 }
 
 __global__ void grid_scatter_kernel(InterpArgs a, InterpScratch s) {
@@ -301,7 +328,11 @@ __constant__ signed char kShell1[26][3] = {
     {-1, 1, 1}, {1, 1, 1}};
 
 // k-best register list: KMAX sorted 64-bit keys; the first KMAX-k slots hold
-// 0 (never displaced), so the k-th best is always the last slot.
+// 0 (never displaced), so the k-th best is always the last slot.  Insertion
+// (kc below the last key): gt[s] = key[s] > kc is false up to the insertion
+// point and true after it, so each slot takes its lower neighbour (past the
+// point), kc (at it) or itself (before it) -- one 64-bit compare and two
+// 64-bit selects per slot, the compare of slot s - 1 serving slot s - 1 next.
 template <int KMAX>
 struct Best {
   unsigned long long key[KMAX];
@@ -311,12 +342,14 @@ struct Best {
   }
   __device__ __forceinline__ unsigned long long last() const { return key[KMAX - 1]; }
   __device__ __forceinline__ void insert(unsigned long long kc) {
+    bool g_hi = key[KMAX - 1] > kc;  // gt of the slot being written
 #pragma unroll
     for (int s = KMAX - 1; s > 0; --s) {
-      const unsigned long long up = key[s - 1] > kc ? key[s - 1] : kc;
-      key[s] = key[s] < up ? key[s] : up;
+      const bool g_lo = key[s - 1] > kc;  // key[s - 1] is still the old value
+      key[s] = g_lo ? key[s - 1] : (g_hi ? kc : key[s]);
+      g_hi = g_lo;
     }
-    key[0] = key[0] < kc ? key[0] : kc;
+    key[0] = g_hi ? kc : key[0];
   }
 };
 
