@@ -190,6 +190,9 @@ __device__ __forceinline__ void sts128(uint8_t *p, uint32_t x, uint32_t y, uint3
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(p)), "r"(x), "r"(y), "r"(z), "r"(w)
                : "memory");
 }
+__device__ __forceinline__ void sts128f(uint32_t addr, float x, float y, float z, float w) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
+}
 __device__ __forceinline__ uint4 lds128(const void *p) {
   uint4 v;
   asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
@@ -854,6 +857,53 @@ __device__ __forceinline__ void st4(void *base, size_t e, float4 v, const float 
 // lanes cover one row and the skip load, the stores and the training mask /
 // second output are 16-byte accesses to 64 contiguous bytes of each row
 // (instead of 32 rows per warp instruction).
+// FP32 encoder epilogue by TMA stores (y_tma: output rows contiguous, no
+// skip, no training outputs).  Each 16-column chunk of the warp's 32 rows
+// (bias, ReLU) goes into a 2 KB staging box -- row r at 64 r, its 16-byte
+// chunk c at the 64-byte swizzle position c ^ ((r / 2) % 4) -- and one TMA
+// store writes the box; the box is rewritten only once the previous store
+// has read it.  Rows past M are clipped by the tensor map.
+template <int PREC>
+__device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, int BN, int n0, int row0,
+                                             uint32_t stg, unsigned long long &w_tfull, uint32_t tfull, uint32_t par,
+                                             unsigned long long &w_ld) {
+  const int lane = threadIdx.x & 31;
+  if (!pwait(a, w_tfull, tfull, par)) return false;
+  tc_fence_after();
+  for (int cc = 0; cc < BN / 16; ++cc) {
+    const int col0 = n0 + cc * 16;
+    float v[16];
+    const long long tl0 = a.prof ? clock64() : 0;
+    tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
+    if (a.prof) w_ld += (unsigned long long)(clock64() - tl0);
+    const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
+#pragma unroll
+    for (int e4 = 0; e4 < 4; ++e4) {
+      const float4 b = __ldg(bias4 + e4);
+      const float bb[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        float z = v[4 * e4 + e] + bb[e];
+        if (a.relu) z = fmaxf(z, 0.f);
+        v[4 * e4 + e] = z;
+      }
+    }
+    if (lane == 0) bulk_wait_read0();
+    __syncwarp();
+#pragma unroll
+    for (int e4 = 0; e4 < 4; ++e4)
+      sts128f(stg + (uint32_t)(lane * 64 + ((e4 ^ ((lane >> 1) & 3)) << 4)), v[4 * e4], v[4 * e4 + 1],
+              v[4 * e4 + 2], v[4 * e4 + 3]);
+    fence_proxy_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+      tma_store_2d(&a.ymap, stg, col0, row0);
+      bulk_commit();
+    }
+  }
+  return true;
+}
+
 template <int PREC>
 __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t taddr, int BN, int n0, size_t ebase,
                                                 bool vrow, float *stg, unsigned long long &w_tfull, uint32_t tfull,
@@ -962,7 +1012,9 @@ __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t tadd
   return true;
 }
 
-template <int PREC>
+// YTMA: the FP32 encoder form whose epilogue stores tiles by TMA (a.y_tma),
+// compiled apart so that the other layers carry none of its code.
+template <int PREC, bool YTMA>
 __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_constant__ ConvArgs a) {
   using T = PrecTraits<PREC>;
   const int BN = a.BN;
@@ -1190,6 +1242,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
                               ? ((size_t)n * a.Hout + (2 * i + pd.oy)) * a.Wout + (2 * j + pd.ox)
                               : (size_t)m;
       const size_t ebase = opix * a.Cout + (size_t)tc.n_tile * BN;
+      if (YTMA && plan.epi_stage) {
+        const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
+        if (!epi_tile_tma<PREC>(a, taddr, BN, tc.n_tile * BN, tc.m_tile * BM + eq * 32,
+                                smem_u32(epi_stg) + (uint32_t)(eq * 2048), w_tfull, smem_u32(&tfull_bar[buf]), par,
+                                w_ld))
+          break;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[buf]));
+        continue;
+      }
       if (plan.epi_stage) {
         const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
         if (!epi_tile_staged<PREC>(a, taddr, BN, tc.n_tile * BN, opix * a.Cout, vrow, epi_stg + eq * 32 * 20, w_tfull,
@@ -1242,6 +1305,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[buf]));
     }
+    if (YTMA && plan.epi_stage && lane == 0) bulk_wait0();  // no store in flight at exit
     if (a.prof && lane == 0) {
       atomicAdd(&a.prof[PROF_EPI_WAIT_TFULL], w_tfull);
       atomicAdd(&a.prof[PROF_EPI_LD], w_ld);
@@ -1266,19 +1330,29 @@ cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t s
   cudaError_t e;
   switch (prec) {
     case PREC_TF32X3:
-      e = cudaFuncSetAttribute(conv_tc_kernel<PREC_TF32X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      conv_tc_kernel<PREC_TF32X3><<<grid, NUM_THREADS, smem, st>>>(a);
+      if (a.y_tma) {
+        e = cudaFuncSetAttribute(conv_tc_kernel<PREC_TF32X3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        conv_tc_kernel<PREC_TF32X3, true><<<grid, NUM_THREADS, smem, st>>>(a);
+      } else {
+        e = cudaFuncSetAttribute(conv_tc_kernel<PREC_TF32X3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        conv_tc_kernel<PREC_TF32X3, false><<<grid, NUM_THREADS, smem, st>>>(a);
+      }
       break;
     case PREC_BF16:
-      e = cudaFuncSetAttribute(conv_tc_kernel<PREC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(conv_tc_kernel<PREC_BF16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
       if (e != cudaSuccess) return e;
-      conv_tc_kernel<PREC_BF16><<<grid, NUM_THREADS, smem, st>>>(a);
+      conv_tc_kernel<PREC_BF16, false><<<grid, NUM_THREADS, smem, st>>>(a);
       break;
     default:
-      e = cudaFuncSetAttribute(conv_tc_kernel<PREC_FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(conv_tc_kernel<PREC_FP8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
       if (e != cudaSuccess) return e;
-      conv_tc_kernel<PREC_FP8><<<grid, NUM_THREADS, smem, st>>>(a);
+      conv_tc_kernel<PREC_FP8, false><<<grid, NUM_THREADS, smem, st>>>(a);
       break;
   }
   return cudaGetLastError();

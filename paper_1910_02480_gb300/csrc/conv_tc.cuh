@@ -44,6 +44,8 @@ enum ProdMode {
 
 struct ConvArgs {
   CUtensorMap tmap;  // A operand view for the TMA modes (64-byte aligned)
+  CUtensorMap ymap;  // y_tma: the output as a 2-D fp32 tensor [M][Cout], box {16, 32}, 64-byte swizzle
+  int y_tma;         // FP32 conv without skip / training outputs: tiles stored by TMA from shared memory
   int prod_mode;
   int tap_boxes;     // TMA modes, FP32 with 8 stored input channels (32 bytes per tap): one box per tap,
                      // four per K block, placed tap-major in the raw slot (BM rows x 32 bytes each)

@@ -132,7 +132,26 @@ EncodeTiledFn encode_tiled() {
 // of whole maps) and a K block to stay inside one tap; everything else uses
 // the cp.async gather.
 // force_mode >= 0 asks for that mode where the layer allows it (autotuner).
+// FP32 convs whose epilogue only stores (no skip, no training outputs, no
+// quantisation) write each tile's rows -- contiguous NHWC pixels -- by TMA:
+// the output as a 2-D tensor [M][Cout] with 16-column x 32-row boxes.
+void plan_store(int prec, ConvArgs &a) {
+  a.y_tma = 0;
+  if (prec != PREC_TF32X3 || a.kind != LK_CONV || a.skip || a.y2 || a.mask || a.amax || a.out_qinv || a.bscale ||
+      a.BN % 16 || a.Cout % 4)
+    return;
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return;
+  cuuint64_t dims[2] = {(cuuint64_t)a.Cout, (cuuint64_t)a.M};
+  cuuint64_t strides[1] = {(cuuint64_t)a.Cout * 4};
+  cuuint32_t box[2] = {16, 32}, estr[2] = {1, 1};
+  if (enc(&a.ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.y, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
+    a.y_tma = 1;
+}
+
 void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
+  plan_store(prec, a);
   a.prod_mode = PROD_CPASYNC;
   a.tap_boxes = 0;
   const int bke = KROW_BYTES / (prec == PREC_TF32X3 ? 4 : (prec == PREC_BF16 ? 2 : 1));  // K elements per block
