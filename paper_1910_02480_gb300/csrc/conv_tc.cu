@@ -863,11 +863,31 @@ __device__ __forceinline__ void st4(void *base, size_t e, float4 v, const float 
 // chunk c at the 64-byte swizzle position c ^ ((r / 2) % 4) -- and one TMA
 // store writes the box; the box is rewritten only once the previous store
 // has read it.  Rows past M are clipped by the tensor map.
+//
+// Decoder phases (LK_CONVT): the warp's 32 rows are y_mw maps x y_rw phase
+// rows x Wrow columns, i.e. a box of the output with element strides 2 in H
+// and W starting at (2 i0 + oy, ox); the skip add reads each lane's own row
+// (prefetched one chunk ahead, as in the other epilogues).
 template <int PREC>
 __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, int BN, int n0, int row0,
-                                             uint32_t stg, unsigned long long &w_tfull, uint32_t tfull, uint32_t par,
-                                             unsigned long long &w_ld) {
+                                             const PhaseDesc &pd, uint32_t stg, unsigned long long &w_tfull,
+                                             uint32_t tfull, uint32_t par, unsigned long long &w_ld) {
   const int lane = threadIdx.x & 31;
+  const bool convt = a.kind == LK_CONVT;
+  // box origin (convT) and this lane's skip row
+  const int rows_per_map = a.Hrow * a.Wrow;
+  const int bn0 = row0 / rows_per_map, bi0 = (row0 - bn0 * rows_per_map) / a.Wrow;
+  const int m = row0 + lane;
+  const bool vrow = m < a.M;
+  const int n = m / rows_per_map, rem = m - n * rows_per_map;
+  const int i = rem / a.Wrow, j = rem - (rem / a.Wrow) * a.Wrow;
+  const size_t sbase = (((size_t)n * a.Hout + (2 * i + pd.oy)) * a.Wout + (2 * j + pd.ox)) * a.Cout + n0;
+  const float *skp = a.skip && vrow ? reinterpret_cast<const float *>(a.skip) + sbase : nullptr;
+  float4 sk[4];
+  if (skp) {
+#pragma unroll
+    for (int e4 = 0; e4 < 4; ++e4) sk[e4] = __ldg(reinterpret_cast<const float4 *>(skp) + e4);
+  }
   if (!pwait(a, w_tfull, tfull, par)) return false;
   tc_fence_after();
   for (int cc = 0; cc < BN / 16; ++cc) {
@@ -888,6 +908,19 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
         v[4 * e4 + e] = z;
       }
     }
+    if (skp) {
+#pragma unroll
+      for (int e4 = 0; e4 < 4; ++e4) {
+        v[4 * e4] += sk[e4].x;
+        v[4 * e4 + 1] += sk[e4].y;
+        v[4 * e4 + 2] += sk[e4].z;
+        v[4 * e4 + 3] += sk[e4].w;
+      }
+      if (cc + 1 < BN / 16) {
+#pragma unroll
+        for (int e4 = 0; e4 < 4; ++e4) sk[e4] = __ldg(reinterpret_cast<const float4 *>(skp + (cc + 1) * 16) + e4);
+      }
+    }
     if (lane == 0) bulk_wait_read0();
     __syncwarp();
 #pragma unroll
@@ -897,7 +930,10 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
     fence_proxy_async_smem();
     __syncwarp();
     if (lane == 0) {
-      tma_store_2d(&a.ymap, stg, col0, row0);
+      if (convt)
+        tma_store_4d(&a.ymap, stg, col0, pd.ox, 2 * bi0 + pd.oy, bn0);
+      else
+        tma_store_2d(&a.ymap, stg, col0, row0);
       bulk_commit();
     }
   }
@@ -1244,7 +1280,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       const size_t ebase = opix * a.Cout + (size_t)tc.n_tile * BN;
       if (YTMA && plan.epi_stage) {
         const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
-        if (!epi_tile_tma<PREC>(a, taddr, BN, tc.n_tile * BN, tc.m_tile * BM + eq * 32,
+        if (!epi_tile_tma<PREC>(a, taddr, BN, tc.n_tile * BN, tc.m_tile * BM + eq * 32, pd,
                                 smem_u32(epi_stg) + (uint32_t)(eq * 2048), w_tfull, smem_u32(&tfull_bar[buf]), par,
                                 w_ld))
           break;

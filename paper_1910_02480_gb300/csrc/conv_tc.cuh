@@ -44,8 +44,11 @@ enum ProdMode {
 
 struct ConvArgs {
   CUtensorMap tmap;  // A operand view for the TMA modes (64-byte aligned)
-  CUtensorMap ymap;  // y_tma: the output as a 2-D fp32 tensor [M][Cout], box {16, 32}, 64-byte swizzle
-  int y_tma;         // FP32 conv without skip / training outputs: tiles stored by TMA from shared memory
+  CUtensorMap ymap;  // y_tma: the output for TMA stores, 64-byte swizzle, one box = 16 channels of one
+                     // epilogue warp's 32 rows -- LK_CONV: 2-D [M][Cout], box {16, 32}; LK_CONVT: 4-D
+                     // [N][Hout][Wout][Cout] with element strides {1, 2, 2, 1}, box {16, 2 Wrow, 2 rw, mw}
+  int y_tma;         // FP32 without training outputs: tiles stored by TMA from shared memory
+  int y_rw, y_mw;    // LK_CONVT: phase rows and maps per 32-row box (Wrow * y_rw * y_mw = 32)
   int prod_mode;
   int tap_boxes;     // TMA modes, FP32 with 8 stored input channels (32 bytes per tap): one box per tap,
                      // four per K block, placed tap-major in the raw slot (BM rows x 32 bytes each)

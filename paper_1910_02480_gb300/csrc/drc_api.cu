@@ -137,17 +137,36 @@ EncodeTiledFn encode_tiled() {
 // the output as a 2-D tensor [M][Cout] with 16-column x 32-row boxes.
 void plan_store(int prec, ConvArgs &a) {
   a.y_tma = 0;
-  if (prec != PREC_TF32X3 || a.kind != LK_CONV || a.skip || a.y2 || a.mask || a.amax || a.out_qinv || a.bscale ||
-      a.BN % 16 || a.Cout % 4)
-    return;
+  if (prec != PREC_TF32X3 || a.y2 || a.mask || a.amax || a.out_qinv || a.bscale || a.BN % 16 || a.Cout % 4) return;
+  if (a.kind == LK_CONV && a.skip) return;
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return;
-  cuuint64_t dims[2] = {(cuuint64_t)a.Cout, (cuuint64_t)a.M};
-  cuuint64_t strides[1] = {(cuuint64_t)a.Cout * 4};
-  cuuint32_t box[2] = {16, 32}, estr[2] = {1, 1};
-  if (enc(&a.ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.y, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS)
-    a.y_tma = 1;
+  CUresult r;
+  if (a.kind == LK_CONV) {
+    cuuint64_t dims[2] = {(cuuint64_t)a.Cout, (cuuint64_t)a.M};
+    cuuint64_t strides[1] = {(cuuint64_t)a.Cout * 4};
+    cuuint32_t box[2] = {16, 32}, estr[2] = {1, 1};
+    r = enc(&a.ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, a.y, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else if (a.kind == LK_CONVT) {
+    // a warp's 32 rows must be whole phase rows of whole maps
+    const int Wr = a.Wrow, Hr = a.Hrow;
+    if (Wr > 32 || 32 % Wr) return;
+    const int rw = Hr < 32 / Wr ? Hr : 32 / Wr;
+    if (rw < Hr ? Hr % rw != 0 : (32 / Wr) % Hr != 0) return;
+    const int mw = 32 / (Wr * rw);
+    a.y_rw = rw;
+    a.y_mw = mw;
+    cuuint64_t dims[4] = {(cuuint64_t)a.Cout, (cuuint64_t)a.Wout, (cuuint64_t)a.Hout, (cuuint64_t)a.N};
+    cuuint64_t strides[3] = {(cuuint64_t)a.Cout * 4, (cuuint64_t)a.Cout * 4 * a.Wout,
+                             (cuuint64_t)a.Cout * 4 * a.Wout * a.Hout};
+    cuuint32_t box[4] = {16, (cuuint32_t)(2 * Wr), (cuuint32_t)(2 * rw), (cuuint32_t)mw}, estr[4] = {1, 2, 2, 1};
+    r = enc(&a.ymap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, a.y, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    return;
+  }
+  if (r == CUDA_SUCCESS) a.y_tma = 1;
 }
 
 void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
