@@ -189,6 +189,33 @@ drc_status drc_interpolate_static(const drc_caches *caches, const drc_gbuffer *g
                                   const drc_interp_params *params, float *out_rgb,
                                   void *stream);
 
+/* One frame end to end from host memory: drc_denoise of N maps, then
+ * drc_interpolate (IRRADIANCE) of a G-buffer from their payloads, with the
+ * uploads and the download inside the call (Sec. 3.3 denoising feeding the
+ * Sec. 3.2 interpolation).  The maps, then the G-buffer, go to the device on
+ * the context's own copy stream; the denoise starts once the maps have
+ * landed, the interpolation once the G-buffer has; the image comes back on
+ * `stream`.  A call's uploads wait only for the previous call's reads of the
+ * same staging, so in a frame loop one frame's maps upload under the
+ * previous frame's interpolation and its G-buffer under its own denoise.
+ *   maps_host: host [N][7][H][W] float32 (page-locked for overlap);
+ *              flags: 0 or DRC_F_ENCODE_INPUT, as drc_denoise;
+ *   caches:    DEVICE positions / normals / pixels of the N caches as for
+ *              drc_interpolate (caches->n == N); payload and maps are not
+ *              read -- the call uses its own denoised payloads;
+ *   gbuf_host: the G-buffer with HOST pointers pos, nrm ([P][3] float32,
+ *              page-locked for overlap); dir is not read;
+ *   params:    as drc_interpolate, mode DRC_INTERP_IRRADIANCE;
+ *   rgb_host:  host [P][3] float32, written when `stream` reaches the end
+ *              of the call.
+ * The host buffers must stay valid and unchanged until then.  The denoised
+ * maps and payloads stay in the context's device staging (grown on demand). */
+drc_status drc_frame_host(drc_ctx *ctx, const float *maps_host, int N, int H,
+                          int W, unsigned flags, const drc_caches *caches,
+                          const drc_gbuffer *gbuf_host,
+                          const drc_interp_params *params, float *rgb_host,
+                          void *stream);
+
 /* drc_backward flags (combine one of the first two with DRC_F_ENCODE_INPUT
  * and DRC_BWD_RECOMPUTE_ENCODER as needed) */
 #define DRC_BWD_L1_TARGET 0x10u /* target = ground truth [N][3][H][W] (log

@@ -101,6 +101,9 @@ def load_library():
     lib.drc_interpolate_static.restype = I
     lib.drc_backward.argtypes = [P, P, P, I, I, I, U, P, P, P, P]
     lib.drc_backward.restype = I
+    lib.drc_frame_host.argtypes = [P, P, I, I, I, U, ctypes.POINTER(Caches), ctypes.POINTER(GBuffer),
+                                   ctypes.POINTER(InterpParams), P, P]
+    lib.drc_frame_host.restype = I
     lib.drc_weight_grad.argtypes = [P, P, P, I, I, I, I, I, I, I, P, P]
     lib.drc_weight_grad.restype = I
     lib.drc_get_status.argtypes = [P, P]
@@ -262,6 +265,39 @@ class Context:
                                        _ptr(out), _stream(stream))
         self._check(rc, "drc_interpolate")
         return out
+
+    def frame_host(self, maps_host, caches, gbuf_host, k, metric, wp_form, r, rgb_host=None, flags=0, eps=1e-6,
+                   delta_rel=1e-3, stream=None):
+        """drc_frame_host: denoise the host maps [N,7,H,W] (CPU float32,
+        pinned for overlap) and interpolate the G-buffer given as CPU tensors
+        gbuf_host["pos"], ["nrm"] ([P,3]) from their payloads; caches: dict of
+        CUDA tensors pos / nrm / pix of the N caches.  Returns rgb_host [P,3]
+        (a new pinned tensor unless given), valid once `stream` has reached
+        the end of the call."""
+        import torch
+        N, C, H, W = maps_host.shape
+        if maps_host.is_cuda or gbuf_host["nrm"].is_cuda:
+            raise ValueError("frame_host takes host (CPU) maps and G-buffer")
+        c = Caches()
+        c.n = int(caches["nrm"].shape[0])
+        c.pos = _ptr(caches.get("pos"))
+        c.nrm = _ptr(caches.get("nrm"))
+        c.pix = _ptr(caches.get("pix"))
+        g = GBuffer()
+        g.width, g.height = int(gbuf_host["width"]), int(gbuf_host["height"])
+        g.pos = ctypes.c_void_p(gbuf_host["pos"].data_ptr()) if gbuf_host.get("pos") is not None else None
+        g.nrm = ctypes.c_void_p(gbuf_host["nrm"].data_ptr())
+        p = InterpParams()
+        p.k, p.metric, p.wp_form, p.mode = int(k), int(metric), int(wp_form), INTERP_IRRADIANCE
+        p.r, p.eps, p.delta_rel = float(r), float(eps), float(delta_rel)
+        P = g.width * g.height
+        if rgb_host is None:
+            rgb_host = torch.empty((P, 3), dtype=torch.float32).pin_memory()
+        rc = self._lib.drc_frame_host(self._ctx, ctypes.c_void_p(maps_host.data_ptr()), N, H, W, flags,
+                                      ctypes.byref(c), ctypes.byref(g), ctypes.byref(p),
+                                      ctypes.c_void_p(rgb_host.data_ptr()), _stream(stream))
+        self._check(rc, "drc_frame_host")
+        return rgb_host
 
     def backward(self, x, target, flags=BWD_L1_TARGET, want_dinput=False, want_loss=True, stream=None):
         """drc_backward: (loss or None, dweights [n_weights], dinput or None).
