@@ -1048,6 +1048,91 @@ __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t tadd
   return true;
 }
 
+// MMA issue loop of one CTA (one thread): per tile wait for a free
+// accumulator, per K block wait for the stage and issue its MMAs, then hand
+// the accumulator to the epilogue.  TS: A from tensor memory (split-tf32).
+template <int PREC, bool TS>
+__device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, int sbytes, int a_bytes,
+                                          int b_bytes, int stages, int total_tiles, int nbufs, int acc_cols,
+                                          uint32_t tmem_base, uint64_t *full_bar, uint64_t *empty_bar,
+                                          uint64_t *tfull_bar, uint64_t *tempty_bar, unsigned long long &w_full,
+                                          unsigned long long &w_tempty) {
+  using T = PrecTraits<PREC>;
+  const int BN = a.BN;
+  bool ok = true;
+  const uint32_t idesc = make_idesc(T::KIND, BM, BN);
+  const uint64_t dA0 = make_sdesc_sw128(data_u32);
+  const uint32_t dstage = (uint32_t)sbytes >> 4, dAlo = (uint32_t)a_bytes >> 4;
+  const uint32_t dB = (uint32_t)(TS ? 0 : T::SPLIT * a_bytes) >> 4, dBlo = (uint32_t)b_bytes >> 4;
+  int stage = 0;
+  uint32_t phase = 0;
+  int it = 0;
+  for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x, ++it) {
+    const TileCoord tc = tile_coord(a, t);
+    const int nkb = a.ph[tc.phase].num_kb;
+    const int buf = nbufs == 2 ? (it & 1) : 0;
+    const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
+    if (!pwait(a, w_tempty, smem_u32(&tempty_bar[buf]), par ^ 1)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    const uint32_t d_tmem = tmem_base + (uint32_t)(buf * acc_cols);
+    const uint32_t c_tmem = d_tmem + (uint32_t)BN;  // correction accumulator (split-tf32)
+    for (int kb = 0; kb < nkb; ++kb) {
+      if (!pwait(a, w_full, smem_u32(&full_bar[stage]), phase)) {
+        ok = false;
+        break;
+      }
+      tc_fence_after();
+      // descriptors: the stage-0 A tile's plus fixed offsets in units of
+      // the start-address field (bytes >> 4); the K step inside the
+      // 128-byte swizzle row adds 32 bytes (2 units).  Keeping this to a
+      // few adds matters: one thread issues every MMA, so its dependent
+      // instruction latency bounds the MMA rate.
+      const uint64_t sd = dA0 + (uint64_t)((uint32_t)stage * dstage);
+      const uint64_t bd0 = sd + dB, bd1 = bd0 + dBlo;
+      if constexpr (TS) {
+        // A hi/lo from tensor memory: 8 tf32 columns per K step
+        const uint32_t ta = tmem_base + (uint32_t)(TS_A_COL0 + stage * 64);
+        const uint32_t acc0 = kb != 0;
+        tc_mma_ts_tf32(d_tmem, ta, bd0, idesc, acc0);
+        tc_mma_ts_tf32(c_tmem, ta, bd1, idesc, acc0);
+        tc_mma_ts_tf32(c_tmem, ta + 32, bd0, idesc, 1u);
+#pragma unroll
+        for (int k = 1; k < KROW_BYTES / 32; ++k) {
+          tc_mma_ts_tf32(d_tmem, ta + 8 * k, bd0 + 2 * k, idesc, 1u);
+          tc_mma_ts_tf32(c_tmem, ta + 8 * k, bd1 + 2 * k, idesc, 1u);
+          tc_mma_ts_tf32(c_tmem, ta + 32 + 8 * k, bd0 + 2 * k, idesc, 1u);
+        }
+      } else {
+        const uint64_t ad1 = sd + dAlo;
+        const uint32_t acc0 = kb != 0;
+        tc_mma<T::KIND>(d_tmem, sd, bd0, idesc, acc0);
+        if constexpr (PREC == PREC_TF32X3) {
+          tc_mma<T::KIND>(c_tmem, sd, bd1, idesc, acc0);
+          tc_mma<T::KIND>(c_tmem, ad1, bd0, idesc, 1u);
+        }
+#pragma unroll
+        for (int k = 1; k < KROW_BYTES / 32; ++k) {
+          tc_mma<T::KIND>(d_tmem, sd + 2 * k, bd0 + 2 * k, idesc, 1u);
+          if constexpr (PREC == PREC_TF32X3) {
+            tc_mma<T::KIND>(c_tmem, sd + 2 * k, bd1 + 2 * k, idesc, 1u);
+            tc_mma<T::KIND>(c_tmem, ad1 + 2 * k, bd0 + 2 * k, idesc, 1u);
+          }
+        }
+      }
+      tc_commit(smem_u32(&empty_bar[stage]));
+      if (++stage == stages) {
+        stage = 0;
+        phase ^= 1;
+      }
+    }
+    if (!ok) break;
+    tc_commit(smem_u32(&tfull_bar[buf]));
+  }
+}
+
 // YTMA: the FP32 encoder form whose epilogue stores tiles by TMA (a.y_tma),
 // compiled apart so that the other layers carry none of its code.
 template <int PREC, bool YTMA>
@@ -1134,78 +1219,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     if (lane == 0) {
       bool ok = true;
       if (a.debug_stall) ok = mbar_wait(smem_u32(stall_bar), 0, tmo, a.status, ERR_TIMEOUT);
-      const uint32_t idesc = make_idesc(T::KIND, BM, BN);
-      const uint64_t dA0 = make_sdesc_sw128(data_u32);
-      const uint32_t dstage = (uint32_t)sbytes >> 4, dAlo = (uint32_t)a_bytes >> 4;
-      const uint32_t dB = (uint32_t)(ts ? 0 : T::SPLIT * a_bytes) >> 4, dBlo = (uint32_t)b_bytes >> 4;
-      int stage = 0;
-      uint32_t phase = 0;
-      int it = 0;
       unsigned long long w_full = 0, w_tempty = 0;
       const long long t_start = a.prof ? clock64() : 0;
-      for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x, ++it) {
-        const TileCoord tc = tile_coord(a, t);
-        const int nkb = a.ph[tc.phase].num_kb;
-        const int buf = nbufs == 2 ? (it & 1) : 0;
-        const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
-        if (!pwait(a, w_tempty, smem_u32(&tempty_bar[buf]), par ^ 1)) {
-          ok = false;
-          break;
-        }
-        tc_fence_after();
-        const uint32_t d_tmem = tmem_base + (uint32_t)(buf * acc_cols);
-        const uint32_t c_tmem = d_tmem + (uint32_t)BN;  // correction accumulator (split-tf32)
-        for (int kb = 0; kb < nkb; ++kb) {
-          if (!pwait(a, w_full, smem_u32(&full_bar[stage]), phase)) {
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          // descriptors: the stage-0 A tile's plus fixed offsets in units of
-          // the start-address field (bytes >> 4); the K step inside the
-          // 128-byte swizzle row adds 32 bytes (2 units).  Keeping this to a
-          // few adds matters: one thread issues every MMA, so its dependent
-          // instruction latency bounds the MMA rate.
-          const uint64_t sd = dA0 + (uint64_t)((uint32_t)stage * dstage);
-          const uint64_t bd0 = sd + dB, bd1 = bd0 + dBlo;
-          if (ts) {
-            // A hi/lo from tensor memory: 8 tf32 columns per K step
-            const uint32_t ta = tmem_base + (uint32_t)(TS_A_COL0 + stage * 64);
-            const uint32_t acc0 = kb != 0;
-            tc_mma_ts_tf32(d_tmem, ta, bd0, idesc, acc0);
-            tc_mma_ts_tf32(c_tmem, ta, bd1, idesc, acc0);
-            tc_mma_ts_tf32(c_tmem, ta + 32, bd0, idesc, 1u);
-#pragma unroll
-            for (int k = 1; k < KROW_BYTES / 32; ++k) {
-              tc_mma_ts_tf32(d_tmem, ta + 8 * k, bd0 + 2 * k, idesc, 1u);
-              tc_mma_ts_tf32(c_tmem, ta + 8 * k, bd1 + 2 * k, idesc, 1u);
-              tc_mma_ts_tf32(c_tmem, ta + 32 + 8 * k, bd0 + 2 * k, idesc, 1u);
-            }
-          } else {
-            const uint64_t ad1 = sd + dAlo;
-            const uint32_t acc0 = kb != 0;
-            tc_mma<T::KIND>(d_tmem, sd, bd0, idesc, acc0);
-            if constexpr (PREC == PREC_TF32X3) {
-              tc_mma<T::KIND>(c_tmem, sd, bd1, idesc, acc0);
-              tc_mma<T::KIND>(c_tmem, ad1, bd0, idesc, 1u);
-            }
-#pragma unroll
-            for (int k = 1; k < KROW_BYTES / 32; ++k) {
-              tc_mma<T::KIND>(d_tmem, sd + 2 * k, bd0 + 2 * k, idesc, 1u);
-              if constexpr (PREC == PREC_TF32X3) {
-                tc_mma<T::KIND>(c_tmem, sd + 2 * k, bd1 + 2 * k, idesc, 1u);
-                tc_mma<T::KIND>(c_tmem, ad1 + 2 * k, bd0 + 2 * k, idesc, 1u);
-              }
-            }
-          }
-          tc_commit(smem_u32(&empty_bar[stage]));
-          if (++stage == stages) {
-            stage = 0;
-            phase ^= 1;
-          }
-        }
-        if (!ok) break;
-        tc_commit(smem_u32(&tfull_bar[buf]));
+      // one instantiation per A form: a branch between the forms inside the
+      // issue loop measured ~110 cycles per MMA against 45-64 without
+      if (ok) {
+        if (PREC == PREC_TF32X3 && ts)
+          mma_issue<PREC, PREC == PREC_TF32X3>(a, data_u32, sbytes, a_bytes, b_bytes, stages, total_tiles, nbufs,
+                                               acc_cols, tmem_base, full_bar, empty_bar, tfull_bar, tempty_bar,
+                                               w_full, w_tempty);
+        else
+          mma_issue<PREC, false>(a, data_u32, sbytes, a_bytes, b_bytes, stages, total_tiles, nbufs, acc_cols,
+                                 tmem_base, full_bar, empty_bar, tfull_bar, tempty_bar, w_full, w_tempty);
       }
       if (a.prof) {
         atomicAdd(&a.prof[PROF_MMA_WAIT_FULL], w_full);
