@@ -1051,7 +1051,7 @@ __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t tadd
 // MMA issue loop of one CTA (one thread): per tile wait for a free
 // accumulator, per K block wait for the stage and issue its MMAs, then hand
 // the accumulator to the epilogue.  TS: A from tensor memory (split-tf32).
-template <int PREC, bool TS>
+template <int PREC, bool TS, bool PROF>
 __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, int sbytes, int a_bytes,
                                           int b_bytes, int stages, int total_tiles, int nbufs, int acc_cols,
                                           uint32_t tmem_base, uint64_t *full_bar, uint64_t *empty_bar,
@@ -1059,6 +1059,19 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
                                           unsigned long long &w_tempty) {
   using T = PrecTraits<PREC>;
   const int BN = a.BN;
+  const unsigned long long tmo = a.timeout_ns;
+  int *const status = a.status;
+  // the wait-time accounting is compiled in only where it is on (PROF)
+  auto pwait = [&](const ConvArgs &, unsigned long long &acc, uint32_t bar, uint32_t parity) -> bool {
+    if constexpr (PROF) {
+      const long long t0 = clock64();
+      const bool r = mbar_wait(bar, parity, tmo, status, ERR_TIMEOUT);
+      acc += (unsigned long long)(clock64() - t0);
+      return r;
+    } else {
+      return mbar_wait(bar, parity, tmo, status, ERR_TIMEOUT);
+    }
+  };
   bool ok = true;
   const uint32_t idesc = make_idesc(T::KIND, BM, BN);
   const uint64_t dA0 = make_sdesc_sw128(data_u32);
@@ -1123,10 +1136,8 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
         }
       }
       tc_commit(smem_u32(&empty_bar[stage]));
-      if (++stage == stages) {
-        stage = 0;
-        phase ^= 1;
-      }
+      stage = stage + 1 == stages ? 0 : stage + 1;  // selects, not a branch
+      phase ^= stage == 0 ? 1u : 0u;
     }
     if (!ok) break;
     tc_commit(smem_u32(&tfull_bar[buf]));
@@ -1224,13 +1235,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       // one instantiation per A form: a branch between the forms inside the
       // issue loop measured ~110 cycles per MMA against 45-64 without
       if (ok) {
-        if (PREC == PREC_TF32X3 && ts)
-          mma_issue<PREC, PREC == PREC_TF32X3>(a, data_u32, sbytes, a_bytes, b_bytes, stages, total_tiles, nbufs,
-                                               acc_cols, tmem_base, full_bar, empty_bar, tfull_bar, tempty_bar,
-                                               w_full, w_tempty);
-        else
-          mma_issue<PREC, false>(a, data_u32, sbytes, a_bytes, b_bytes, stages, total_tiles, nbufs, acc_cols,
-                                 tmem_base, full_bar, empty_bar, tfull_bar, tempty_bar, w_full, w_tempty);
+#define DRC_MMA_ISSUE(TSV, PROFV)                                                                               \
+  mma_issue<PREC, TSV, PROFV>(a, data_u32, sbytes, a_bytes, b_bytes, stages, total_tiles, nbufs, acc_cols, tmem_base, \
+                              full_bar, empty_bar, tfull_bar, tempty_bar, w_full, w_tempty)
+        constexpr bool kTS = PREC == PREC_TF32X3;
+        if (a.prof) {
+          if (kTS && ts)
+            DRC_MMA_ISSUE(kTS, true);
+          else
+            DRC_MMA_ISSUE(false, true);
+        } else {
+          if (kTS && ts)
+            DRC_MMA_ISSUE(kTS, false);
+          else
+            DRC_MMA_ISSUE(false, false);
+        }
+#undef DRC_MMA_ISSUE
       }
       if (a.prof) {
         atomicAdd(&a.prof[PROF_MMA_WAIT_FULL], w_full);
