@@ -346,6 +346,22 @@ def cpu_baseline(w, x, g, c, budget_s=12.0):
             "step_s": step_s}
 
 
+def max_over_ranks(value, dist, device):
+    """The slowest rank's figure (step times are reduced with MAX); the
+    value itself on one rank."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, maps_per_rank, ms_per_step):
+    """Whole-job throughput: every rank's maps over the slowest rank's step."""
+    return world * maps_per_rank / (ms_per_step * 1e-3)
+
+
 def run_reference(args, rank):
     """--impl reference: the oracle as it stands, timed per step on a bounded
     sample of the same workload."""
@@ -464,12 +480,8 @@ def main():
     itp_ms = [b.elapsed_time(c_) for _, b, c_ in ev]
     if ctx.status() != drc.OK:
         raise RuntimeError("device status after timed region")
-    ms = float(np.mean(step_ms))
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * N_MAPS / (ms * 1e-3)
+    ms = max_over_ranks(float(np.mean(step_ms)), dist, dev)
+    value = job_value(world, N_MAPS, ms)
 
     # end to end through the public API with host buffers: drc_frame_host
     # copies the pinned maps and G-buffer in and the image out inside every
@@ -501,10 +513,7 @@ def main():
     e2e_step = (time.perf_counter() - t0) * 1e3 / n_e2e
     if ctx.status() != drc.OK:
         raise RuntimeError("device status after the end-to-end frames")
-    if dist:
-        t = torch.tensor([e2e_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
+    e2e_step = max_over_ranks(e2e_step, dist, dev)
     h2d = x.nbytes + g["pos"].nbytes + g["nrm"].nbytes
     d2h = IMG_W * IMG_H * 3 * 4
 
@@ -549,7 +558,7 @@ def main():
             "denoise_ms": den * 1e3, "interp_ms": float(np.mean(itp_ms)),
             "interp_pixels_per_s": IMG_W * IMG_H / (float(np.mean(itp_ms)) * 1e-3),
             "roofline": roofline,
-            "e2e": {"value": world * N_MAPS / (e2e_step * 1e-3), "unit": "maps/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job_value(world, N_MAPS, e2e_step), "unit": "maps/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "kernels": kernels,
