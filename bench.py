@@ -310,7 +310,7 @@ def make_inputs(seed_offset=0):
     return w, x, g, c
 
 
-def cpu_baseline(w, x, g, c, budget_s=12.0):
+def cpu_baseline(w, x, g, c, budget_s=12.0, one_thread=False):
     """The FP64 oracle on a bounded sample of the step, scaled to maps/s."""
     import oracle
     from paper_1910_02480_gb300 import synth
@@ -339,11 +339,44 @@ def cpu_baseline(w, x, g, c, budget_s=12.0):
                        p_range=(0, n_p))
     per_px = (time.perf_counter() - t0) / n_p
     step_s = per_map * N_MAPS + per_px * P
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": N_MAPS / step_s, "unit": "maps/s", "cores": cores, "kind": "oracle",
-            "sample": "%d of %d maps denoised + %d of %d pixels interpolated (FP64 C oracle, OpenMP), "
-                      "scaled to one full step" % (n_f2, N_MAPS, n_p, P),
-            "step_s": step_s}
+    cores = oracle.get_threads()
+    out = {"value": N_MAPS / step_s, "unit": "maps/s", "cores": cores, "kind": "oracle",
+           "sample": "%d of %d maps denoised + %d of %d pixels interpolated (FP64 C oracle, OpenMP), "
+                     "scaled to one full step" % (n_f2, N_MAPS, n_p, P),
+           "step_s": step_s, "cpu_model": cpu_model()}
+    if one_thread:
+        # the same on one thread, on a smaller sample (about a tenth of the budget)
+        oracle.set_threads(1)
+        try:
+            m1 = max(2, min(n_f2, int(0.05 * budget_s / max(per_map * cores, 1e-6))))
+            t0 = time.perf_counter()
+            oracle.forward(w, x[:m1], WIDTHS)
+            pm1 = (time.perf_counter() - t0) / m1
+            p1 = max(256, min(n_p, int(0.05 * budget_s / max(per_px * cores, 1e-9))))
+            t0 = time.perf_counter()
+            oracle.interpolate(cc, g, K_NN, oracle.METRIC_WORLD, oracle.WP_INVERSE, oracle.INTERP_IRRADIANCE, r,
+                               p_range=(0, p1))
+            pp1 = (time.perf_counter() - t0) / p1
+        finally:
+            oracle.set_threads(cores)
+        out["one_thread"] = {"value": N_MAPS / (pm1 * N_MAPS + pp1 * P), "unit": "maps/s",
+                             "sample": "%d maps + %d pixels on 1 thread, scaled to one full step" % (m1, p1)}
+    return out
+
+
+def cpu_model():
+    """The host CPU's model string from /proc/cpuinfo (or the platform)."""
+    import platform
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = f.read()
+        for key in ("model name", "Model name", "CPU part"):
+            for line in info.splitlines():
+                if line.startswith(key):
+                    return line.split(":", 1)[1].strip() + ("" if key != "CPU part" else " (CPU part)")
+    except OSError:
+        pass
+    return platform.processor() or platform.machine()
 
 
 def max_over_ranks(value, dist, device):
@@ -569,7 +602,7 @@ def main():
         line["uneven_batching"] = measure_uneven(drc, torch, dev)
         line["training"] = measure_training(drc, torch, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        b = cpu_baseline(w, x, g, c)
+        b = cpu_baseline(w, x, g, c, one_thread=True)
         b.pop("step_s", None)
         line["cpu_baseline"] = b
     if rank == 0:

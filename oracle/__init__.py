@@ -74,6 +74,8 @@ def _load():
                                         i, i, P, P, P]
         lib.orc_l1_backward.restype = d
         lib.orc_conv_wgrad.argtypes = [P, i, i, i, i, P, i, i, P]
+        lib.orc_set_threads.argtypes = [i]
+        lib.orc_get_threads.restype = i
         _lib = lib
     return _lib
 
@@ -88,6 +90,15 @@ def _f64(a):
 
 def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads of the oracle's loops (timing only)."""
+    _load().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(_load().orc_get_threads())
 
 
 def weight_count(widths, cin=7, cout=3) -> int:

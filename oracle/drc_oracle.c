@@ -33,6 +33,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_F_ENCODE_INPUT 1u
 #define ORC_F_DECODE_OUTPUT 2u
@@ -763,4 +766,25 @@ double orc_l1_backward(int S, const int *widths, int cin, int cout,
     free(x_raw);
     free(w);
     return loss;
+}
+
+/* Thread control for timing (not arithmetic): the OpenMP team size of the
+ * loops above, and the current setting. */
+void orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0)
+        omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_get_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
