@@ -434,14 +434,17 @@ __device__ __forceinline__ void tma_issue(const ConvArgs &a, const TmaCursor &c,
   using T = PrecTraits<PREC>;
   constexpr int BKE = KROW_BYTES / T::ELEM;
   if (a.tap_boxes) {
-    // four taps of 8 channels per K block (stride-2 conv), one box each; a
-    // slot past the last tap loads tap 0 again, against B rows packed as zero
+    // taps of 8 channels (FP32: 32 bytes, four per K block; BF16: 16 bytes,
+    // eight per K block) of the stride-2 conv, one box each, tap-major; a slot
+    // past the last tap loads tap 0 again, against B rows packed as zero
+    constexpr int TB = 8 * T::ELEM;           // bytes of one tap row
+    constexpr int TPB = KROW_BYTES / TB;      // taps per K block
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int tap = 4 * c.kb + t < c.ntaps ? 4 * c.kb + t : 0;
+    for (int t = 0; t < TPB; ++t) {
+      const int tap = TPB * c.kb + t < c.ntaps ? TPB * c.kb + t : 0;
       const unsigned tb = (unsigned)(c.taps >> (4 * tap)) & 15u;
       const int dy = (int)(tb & 3u), dx = (int)(tb >> 2);
-      tma_load_4d(dst + (uint32_t)(t * BM * 32), &a.tmap, 0, dx - 1, 2 * c.r0 + dy - 1, c.n0, bar);
+      tma_load_4d(dst + (uint32_t)(t * BM * TB), &a.tmap, 0, dx - 1, 2 * c.r0 + dy - 1, c.n0, bar);
     }
     return;
   }
@@ -1051,7 +1054,7 @@ __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t tadd
 // MMA issue loop of one CTA (one thread): per tile wait for a free
 // accumulator, per K block wait for the stage and issue its MMAs, then hand
 // the accumulator to the epilogue.  TS: A from tensor memory (split-tf32).
-template <int PREC, bool TS, bool PROF>
+template <int PREC, bool TS, bool PROF, bool TAPA>
 __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, int sbytes, int a_bytes,
                                           int b_bytes, int stages, int total_tiles, int nbufs, int acc_cols,
                                           uint32_t tmem_base, uint64_t *full_bar, uint64_t *empty_bar,
@@ -1074,9 +1077,14 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
   };
   bool ok = true;
   const uint32_t idesc = make_idesc(T::KIND, BM, BN);
-  const uint64_t dA0 = make_sdesc_sw128(data_u32);
+  // TAPA (BF16 tap boxes): A is K-major without swizzle, 2 KB per 8-element
+  // K group (one tap box), 128 bytes per 8-row group; a 16-element K step
+  // spans two groups (4096 bytes = 256 units)
+  const uint64_t dA0 = TAPA ? make_sdesc_kmajor_plain(data_u32, BM * 16, 128) : make_sdesc_sw128(data_u32);
+  constexpr uint32_t kA = TAPA ? 256u : 2u;
   const uint32_t dstage = (uint32_t)sbytes >> 4, dAlo = (uint32_t)a_bytes >> 4;
-  const uint32_t dB = (uint32_t)(TS ? 0 : T::SPLIT * a_bytes) >> 4, dBlo = (uint32_t)b_bytes >> 4;
+  const uint64_t dB0 = make_sdesc_sw128(data_u32 + (uint32_t)(TS ? 0 : T::SPLIT * a_bytes));
+  const uint32_t dBlo = (uint32_t)b_bytes >> 4;
   int stage = 0;
   uint32_t phase = 0;
   int it = 0;
@@ -1104,7 +1112,7 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
       // few adds matters: one thread issues every MMA, so its dependent
       // instruction latency bounds the MMA rate.
       const uint64_t sd = dA0 + (uint64_t)((uint32_t)stage * dstage);
-      const uint64_t bd0 = sd + dB, bd1 = bd0 + dBlo;
+      const uint64_t bd0 = dB0 + (uint64_t)((uint32_t)stage * dstage), bd1 = bd0 + dBlo;
       if constexpr (TS) {
         // A hi/lo from tensor memory: 8 tf32 columns per K step
         const uint32_t ta = tmem_base + (uint32_t)(TS_A_COL0 + stage * 64);
@@ -1128,10 +1136,10 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
         }
 #pragma unroll
         for (int k = 1; k < KROW_BYTES / 32; ++k) {
-          tc_mma<T::KIND>(d_tmem, sd + 2 * k, bd0 + 2 * k, idesc, 1u);
+          tc_mma<T::KIND>(d_tmem, sd + kA * k, bd0 + 2 * k, idesc, 1u);
           if constexpr (PREC == PREC_TF32X3) {
-            tc_mma<T::KIND>(c_tmem, sd + 2 * k, bd1 + 2 * k, idesc, 1u);
-            tc_mma<T::KIND>(c_tmem, ad1 + 2 * k, bd0 + 2 * k, idesc, 1u);
+            tc_mma<T::KIND>(c_tmem, sd + kA * k, bd1 + 2 * k, idesc, 1u);
+            tc_mma<T::KIND>(c_tmem, ad1 + kA * k, bd0 + 2 * k, idesc, 1u);
           }
         }
       }
@@ -1235,20 +1243,26 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       // one instantiation per A form: a branch between the forms inside the
       // issue loop measured ~110 cycles per MMA against 45-64 without
       if (ok) {
-#define DRC_MMA_ISSUE(TSV, PROFV)                                                                               \
-  mma_issue<PREC, TSV, PROFV>(a, data_u32, sbytes, a_bytes, b_bytes, stages, total_tiles, nbufs, acc_cols, tmem_base, \
-                              full_bar, empty_bar, tfull_bar, tempty_bar, w_full, w_tempty)
+#define DRC_MMA_ISSUE(TSV, PROFV, TAPV)                                                                          \
+  mma_issue<PREC, TSV, PROFV, TAPV>(a, data_u32, sbytes, a_bytes, b_bytes, stages, total_tiles, nbufs, acc_cols,     \
+                                    tmem_base, full_bar, empty_bar, tfull_bar, tempty_bar, w_full, w_tempty)
         constexpr bool kTS = PREC == PREC_TF32X3;
+        constexpr bool kTAP = PREC == PREC_BF16;  // BF16 tap boxes land in the A tile itself
+        const bool tapa = kTAP && a.tap_boxes && a.prod_mode == PROD_TMA_DIRECT;
         if (a.prof) {
           if (kTS && ts)
-            DRC_MMA_ISSUE(kTS, true);
+            DRC_MMA_ISSUE(kTS, true, false);
+          else if (tapa)
+            DRC_MMA_ISSUE(false, true, kTAP);
           else
-            DRC_MMA_ISSUE(false, true);
+            DRC_MMA_ISSUE(false, true, false);
         } else {
           if (kTS && ts)
-            DRC_MMA_ISSUE(kTS, false);
+            DRC_MMA_ISSUE(kTS, false, false);
+          else if (tapa)
+            DRC_MMA_ISSUE(false, false, kTAP);
           else
-            DRC_MMA_ISSUE(false, false);
+            DRC_MMA_ISSUE(false, false, false);
         }
 #undef DRC_MMA_ISSUE
       }

@@ -182,9 +182,10 @@ void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
   a.tap_boxes = 0;
   const int bke = KROW_BYTES / (prec == PREC_TF32X3 ? 4 : (prec == PREC_BF16 ? 2 : 1));  // K elements per block
   const int Wr = a.Wrow, Hr = a.Hrow;
-  // FP32 conv over 8 stored channels (the first layer): 32 bytes per tap, so
-  // a K block holds four taps, each its own TMA box
-  const bool taps = prec == PREC_TF32X3 && a.kind == LK_CONV && a.Cin * 4 * 4 == KROW_BYTES;
+  // conv over 8 stored channels (the first layer): 32 bytes per tap in FP32
+  // (four taps per K block) or 16 in BF16 (eight), each tap its own TMA box;
+  // BF16 boxes land in the A tile directly (no-swizzle K-major layout)
+  const bool taps = a.kind == LK_CONV && a.Cin == 8 && (prec == PREC_TF32X3 || prec == PREC_BF16);
   if (Wr > BM || BM % Wr || (!taps && a.Cin % bke)) return;
   const int rows_t = Hr < BM / Wr ? Hr : BM / Wr;
   if ((rows_t * Wr) % Wr || BM % (rows_t * Wr) || (rows_t < Hr && Hr % rows_t)) return;

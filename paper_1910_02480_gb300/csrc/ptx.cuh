@@ -223,6 +223,19 @@ __device__ __forceinline__ uint64_t make_sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
+// Shared-memory matrix descriptor for a K-major operand without swizzle:
+// core matrices of 8 rows x 16 bytes, LBO = distance between core matrices
+// along K, SBO = distance between 8-row groups along M/N.
+__device__ __forceinline__ uint64_t make_sdesc_kmajor_plain(uint32_t saddr, uint32_t kgroup_bytes,
+                                                            uint32_t rowgroup_bytes) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((kgroup_bytes >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((rowgroup_bytes >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
 // tcgen05.ld, 32 lanes x 32 bits, 16 consecutive columns per thread, without
 // the wait (tmem_wait_ld before the registers are read).
 __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t (&r)[16]) {
