@@ -77,12 +77,12 @@ static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, 
 
 // With the epilogue's staging buffer where the pipeline keeps at least two
 // stages (and two raw slots where it uses a raw ring); otherwise without.
-__host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode) {
+__host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode, int ytma) {
   const int avail = SMEM_BUDGET - SMEM_CTRL - 1024;
-  // the FP32 path only: with 16-byte bf16 / e4m3 row chunks the per-row
-  // epilogue measured faster
+  // the FP32 path, and BF16 stores by TMA: with 16-byte bf16 / e4m3 row
+  // chunks the staged per-lane epilogue measured slower than the per-row one
   SmemPlan p = smem_plan_avail(prec, BN, mode, avail - EPI_STG_BYTES);
-  if (prec == PREC_TF32X3 && p.stages >= 2 && (mode == PROD_TMA_DIRECT || p.raw_depth >= 2)) {
+  if ((prec == PREC_TF32X3 || ytma) && p.stages >= 2 && (mode == PROD_TMA_DIRECT || p.raw_depth >= 2)) {
     p.epi_stage = 1;
     return p;
   }
@@ -121,8 +121,8 @@ static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, 
   p.raw_slot_bytes = rb;
   return p;
 }
-size_t conv_smem_bytes(int prec, int BN, int mode) {
-  const SmemPlan p = smem_plan(prec, BN, mode);
+size_t conv_smem_bytes(int prec, int BN, int mode, int ytma) {
+  const SmemPlan p = smem_plan(prec, BN, mode, ytma);
   return (size_t)SMEM_CTRL + 1024 + (size_t)p.stages * stage_bytes(prec, BN, mode) +
          (size_t)p.raw_depth * p.raw_slot_bytes + (p.epi_stage ? (size_t)EPI_STG_BYTES : 0);
 }
@@ -189,6 +189,9 @@ __device__ __forceinline__ float bf16_hi(uint32_t w) { return __uint_as_float(w 
 __device__ __forceinline__ void sts128(uint8_t *p, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
   asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(p)), "r"(x), "r"(y), "r"(z), "r"(w)
                : "memory");
+}
+__device__ __forceinline__ void sts128u(uint32_t addr, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
 }
 __device__ __forceinline__ void sts128f(uint32_t addr, float x, float y, float z, float w) {
   asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
@@ -885,12 +888,24 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
   const int n = m / rows_per_map, rem = m - n * rows_per_map;
   const int i = rem / a.Wrow, j = rem - (rem / a.Wrow) * a.Wrow;
   const size_t sbase = (((size_t)n * a.Hout + (2 * i + pd.oy)) * a.Wout + (2 * j + pd.ox)) * a.Cout + n0;
-  const float *skp = a.skip && vrow ? reinterpret_cast<const float *>(a.skip) + sbase : nullptr;
+  using act_t = typename PrecTraits<PREC>::act_t;
+  const act_t *skp = a.skip && vrow ? reinterpret_cast<const act_t *>(a.skip) + sbase : nullptr;
   float4 sk[4];
-  if (skp) {
+  // 16 skip values of chunk cc (fp32: four 16-byte loads; bf16: two)
+  auto load_sk = [&](int cc) {
+    if constexpr (PREC == PREC_BF16) {
 #pragma unroll
-    for (int e4 = 0; e4 < 4; ++e4) sk[e4] = __ldg(reinterpret_cast<const float4 *>(skp) + e4);
-  }
+      for (int h = 0; h < 2; ++h) {
+        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(skp + cc * 16) + h);
+        sk[2 * h] = make_float4(bf16_lo(u.x), bf16_hi(u.x), bf16_lo(u.y), bf16_hi(u.y));
+        sk[2 * h + 1] = make_float4(bf16_lo(u.z), bf16_hi(u.z), bf16_lo(u.w), bf16_hi(u.w));
+      }
+    } else {
+#pragma unroll
+      for (int e4 = 0; e4 < 4; ++e4) sk[e4] = __ldg(reinterpret_cast<const float4 *>(skp + cc * 16) + e4);
+    }
+  };
+  if (skp) load_sk(0);
   if (!pwait(a, w_tfull, tfull, par)) return false;
   tc_fence_after();
   for (int cc = 0; cc < BN / 16; ++cc) {
@@ -919,17 +934,23 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
         v[4 * e4 + 2] += sk[e4].z;
         v[4 * e4 + 3] += sk[e4].w;
       }
-      if (cc + 1 < BN / 16) {
-#pragma unroll
-        for (int e4 = 0; e4 < 4; ++e4) sk[e4] = __ldg(reinterpret_cast<const float4 *>(skp + (cc + 1) * 16) + e4);
-      }
+      if (cc + 1 < BN / 16) load_sk(cc + 1);
     }
     if (lane == 0) bulk_wait_read0();
     __syncwarp();
+    if constexpr (PREC == PREC_BF16) {
+      // 32-byte rows, 32-byte swizzle: 16-byte chunk h at h ^ ((r / 4) % 2)
 #pragma unroll
-    for (int e4 = 0; e4 < 4; ++e4)
-      sts128f(stg + (uint32_t)(lane * 64 + ((e4 ^ ((lane >> 1) & 3)) << 4)), v[4 * e4], v[4 * e4 + 1],
-              v[4 * e4 + 2], v[4 * e4 + 3]);
+      for (int h = 0; h < 2; ++h)
+        sts128u(stg + (uint32_t)(lane * 32 + ((h ^ ((lane >> 2) & 1)) << 4)),
+               pack_bf16x2(v[8 * h], v[8 * h + 1]), pack_bf16x2(v[8 * h + 2], v[8 * h + 3]),
+               pack_bf16x2(v[8 * h + 4], v[8 * h + 5]), pack_bf16x2(v[8 * h + 6], v[8 * h + 7]));
+    } else {
+#pragma unroll
+      for (int e4 = 0; e4 < 4; ++e4)
+        sts128f(stg + (uint32_t)(lane * 64 + ((e4 ^ ((lane >> 1) & 3)) << 4)), v[4 * e4], v[4 * e4 + 1],
+                v[4 * e4 + 2], v[4 * e4 + 3]);
+    }
     fence_proxy_async_smem();
     __syncwarp();
     if (lane == 0) {
@@ -1158,7 +1179,7 @@ template <int PREC, bool YTMA>
 __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_constant__ ConvArgs a) {
   using T = PrecTraits<PREC>;
   const int BN = a.BN;
-  const SmemPlan plan = smem_plan(PREC, BN, a.prod_mode);
+  const SmemPlan plan = smem_plan(PREC, BN, a.prod_mode, YTMA ? 1 : 0);
   const int stages = plan.stages;
   const int a_bytes = BM * KROW_BYTES;
   const int b_bytes = BN * KROW_BYTES;
@@ -1421,7 +1442,7 @@ cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t s
   const int total = a.num_phases * a.m_tiles * a.n_tiles;
   if (total == 0) return cudaSuccess;
   const int grid = total < num_sms ? total : num_sms;
-  const size_t smem = conv_smem_bytes(prec, a.BN, a.prod_mode);
+  const size_t smem = conv_smem_bytes(prec, a.BN, a.prod_mode, a.y_tma);
   cudaError_t e;
   switch (prec) {
     case PREC_TF32X3:
@@ -1438,10 +1459,17 @@ cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t s
       }
       break;
     case PREC_BF16:
-      e = cudaFuncSetAttribute(conv_tc_kernel<PREC_BF16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-      if (e != cudaSuccess) return e;
-      conv_tc_kernel<PREC_BF16, false><<<grid, NUM_THREADS, smem, st>>>(a);
+      if (a.y_tma) {
+        e = cudaFuncSetAttribute(conv_tc_kernel<PREC_BF16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        conv_tc_kernel<PREC_BF16, true><<<grid, NUM_THREADS, smem, st>>>(a);
+      } else {
+        e = cudaFuncSetAttribute(conv_tc_kernel<PREC_BF16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        conv_tc_kernel<PREC_BF16, false><<<grid, NUM_THREADS, smem, st>>>(a);
+      }
       break;
     default:
       e = cudaFuncSetAttribute(conv_tc_kernel<PREC_FP8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -103,8 +103,8 @@ struct SmemPlan {
 // Epilogue staging: 4 warps x 32 rows x (16 + 4 pad) floats.
 constexpr int EPI_STG_FLOATS = 4 * 32 * 20;
 constexpr int EPI_STG_BYTES = EPI_STG_FLOATS * 4;
-__host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode);
-size_t conv_smem_bytes(int prec, int BN, int mode);
+__host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode, int ytma);
+size_t conv_smem_bytes(int prec, int BN, int mode, int ytma);
 
 // Host-side launch / pack entry points (conv_tc.cu).
 cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t st);
