@@ -38,7 +38,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # the 4096-map workload: ncu counters of the 2304-map case scaled by 4096/2304
 # (profiles/conv_tc_kernel_2304maps.md); None where not taken, and reset to
 # None whenever the kernel changes after the counters were taken.
-TRAFFIC = {"fp32": 1605e6, "bf16": None}
+TRAFFIC = {"fp32": 1600e6, "bf16": None}
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense ratio (tf32 : bf16)
 
 
@@ -365,8 +365,16 @@ def cpu_baseline(w, x, g, c, budget_s=12.0, one_thread=False):
 
 
 def cpu_model():
-    """The host CPU's model string from /proc/cpuinfo (or the platform)."""
+    """The host CPU's model string (lscpu, else /proc/cpuinfo, else the platform)."""
     import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             info = f.read()
