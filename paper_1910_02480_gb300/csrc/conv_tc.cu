@@ -346,22 +346,6 @@ __device__ __forceinline__ void raw_convert_own(const ConvArgs &a, int pt, const
   }
 }
 
-// PROD_TMA_CONVERT step 2: convert chunks of a TMA-filled raw slot (same
-// swizzled layout as the A tile).
-template <int PREC>
-__device__ __forceinline__ void raw_convert_tma(const ConvArgs &a, int pt, const uint8_t *slot, uint8_t *a0,
-                                                uint8_t *a1) {
-  const int lane = pt & 31, pw = pt >> 5, q = lane & 7;
-#pragma unroll
-  for (int it = 0; it < 4; ++it) {
-    const int r = (lane >> 3) + 4 * pw + 32 * it;
-    convert_store<PREC>(a0, a1, swz(r, q), reinterpret_cast<const uint4 *>(slot + swz(r, q)));
-  }
-}
-
-// PROD_TMA_CONVERT step 2 for one group of four producer warps (128
-// threads, gt = thread index in the group): the whole K block, 8 chunks of
-// 128 rows.
 // With tap boxes the slot is tap-major: chunk (r, q) of the K block is at
 // (q / 2) BM 32 + 32 r + 16 (q % 2); a quarter warp then takes 8 rows of one
 // chunk, so the reads see at most 2-way bank conflicts and the swizzled
@@ -369,6 +353,11 @@ __device__ __forceinline__ void raw_convert_tma(const ConvArgs &a, int pt, const
 __device__ __forceinline__ const uint8_t *tap_chunk(const uint8_t *slot, int r, int q) {
   return slot + (q >> 1) * (BM * 32) + r * 32 + (q & 1) * 16;
 }
+
+// PROD_TMA_CONVERT step 2 for one group of four producer warps (128
+// threads, gt = thread index in the group): the whole K block, 8 chunks of
+// 128 rows, from the raw slot (the A tile's swizzled layout, or tap-major
+// with TAPS) into the tf32 hi / lo (or e4m3) tiles.
 template <int PREC, bool TAPS>
 __device__ __forceinline__ void raw_convert_tma_group(int gt, const uint8_t *slot, uint8_t *a0, uint8_t *a1) {
   const int lane = gt & 31, gw = gt >> 5, q = lane & 7;

@@ -227,7 +227,7 @@ void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
   }
   if (prec == PREC_BF16 || prec == PREC_FP8)
     a.prod_mode = PROD_TMA_DIRECT;
-  else if (prec == PREC_TF32X3 && a.BN <= 128 && std::getenv("DRC_NO_TMEM_A") == nullptr)
+  else if (prec == PREC_TF32X3 && a.BN <= 128)
     a.prod_mode = PROD_TMA_TMEM;  // A operand in tensor memory
   else
     a.prod_mode = PROD_TMA_CONVERT;
