@@ -32,7 +32,10 @@ static constexpr int METRIC_IMAGE = 0;
 static constexpr int WP_INVERSE = 0;
 static constexpr int MODE_IRRADIANCE = 0;
 
-static inline int per_cell(int k) { return k / 2 > 1 ? k / 2 : 1; }
+// Caches per grid cell the grid is sized for: 3k/8 (at least 1).  At 4096
+// caches, k = 16, 1080p WORLD the query measured 0.854 ms with 6 per cell,
+// against 0.876 (5), 0.863 (7), 0.874 (8) and 0.892 (12).
+static inline int per_cell(int k) { return 3 * k / 8 > 1 ? 3 * k / 8 : 1; }
 
 int interp_max_cells(int n, int k) {
   const int pc = per_cell(k);
@@ -114,7 +117,7 @@ __device__ __forceinline__ int fine_of(const GridHeader &g, float3 p) {
   return (cz * g.fdims[1] + cy) * g.fdims[0] + cx;
 }
 
-// Single block: bounds of the cache points, cubic cells sized for about k/2
+// Single block: bounds of the cache points, cubic cells sized for about 3k/8
 // caches each over the occupied axes, the fine pixel-ordering grid, counts
 // cleared.
 __global__ void grid_bounds_kernel(InterpArgs a, InterpScratch s) {
@@ -164,7 +167,7 @@ __global__ void grid_bounds_kernel(InterpArgs a, InterpScratch s) {
         vol *= (double)ext[d];
       }
     }
-    const int pc = a.k / 2 > 1 ? a.k / 2 : 1;
+    const int pc = 3 * a.k / 8 > 1 ? 3 * a.k / 8 : 1;  // as per_cell()
     const double target = (double)((a.n + pc - 1) / pc);
     double h = active ? pow(vol / target, 1.0 / active) : 1.0;
     if (!(h > 0.0)) h = 1.0;

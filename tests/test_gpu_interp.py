@@ -153,3 +153,23 @@ def test_interp_argument_errors(drc, ctx):
         ctx.interpolate(_cuda(c), _cuda(g), 4, drc.METRIC_IMAGE, 0, 0, -1.0)
     with pytest.raises(drc.DrcError):
         ctx.interpolate(_cuda(c), _cuda(g), 4, drc.METRIC_IMAGE, 0, drc.INTERP_LOOKUP, 4.0)
+
+
+def test_empty_and_single_pixel_gbuffer(drc, ctx):
+    """P = 0 enqueues nothing and leaves the output alone; a 1 x 1 G-buffer
+    (one pixel, every cache a candidate) matches the oracle."""
+    g, c = _scene(16, 16, 4, 4)
+    r = synth.world_radius(16)
+    g0 = dict(g)
+    g0["width"], g0["height"] = 0, 0
+    g0["pos"], g0["nrm"] = g["pos"][:0], g["nrm"][:0]
+    out0 = torch.full((1, 3), 7.0, device="cuda")
+    ctx.interpolate(_cuda(c), _cuda(g0), 4, drc.METRIC_WORLD, drc.WP_INVERSE, drc.INTERP_IRRADIANCE, r, out=out0)
+    torch.cuda.synchronize()
+    assert ctx.status() == drc.OK and bool(torch.all(out0 == 7.0))
+    g1 = dict(g)
+    g1["width"], g1["height"] = 1, 1
+    g1["pos"], g1["nrm"] = np.ascontiguousarray(g["pos"][5:6]), np.ascontiguousarray(g["nrm"][5:6])
+    out, nbr, ref, idx, d2 = _run(drc, ctx, g1, c, 16, drc.METRIC_WORLD, drc.WP_INVERSE, drc.INTERP_IRRADIANCE, r)
+    np.testing.assert_array_equal(np.sort(nbr, axis=1), np.sort(idx, axis=1))  # k = n: every cache
+    assert rel_err(out, ref) <= FP32_TOL
