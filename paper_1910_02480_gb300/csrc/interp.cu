@@ -32,10 +32,11 @@ static constexpr int METRIC_IMAGE = 0;
 static constexpr int WP_INVERSE = 0;
 static constexpr int MODE_IRRADIANCE = 0;
 
-// Caches per grid cell the grid is sized for: 3k/8 (at least 1).  At 4096
-// caches, k = 16, 1080p WORLD the query measured 0.854 ms with 6 per cell,
-// against 0.876 (5), 0.863 (7), 0.874 (8) and 0.892 (12).
-static inline int per_cell(int k) { return 3 * k / 8 > 1 ? 3 * k / 8 : 1; }
+// Caches per grid cell the grid is sized for: k/2 (at least 1).  At 4096
+// caches, k = 16, 1080p WORLD the two-walk query measured 0.697 ms with 8
+// per cell, against 0.709 (7) and 0.697 (9); 6 per cell suited the single
+// 64-bit walk, whose insertions cost three times as much.
+static inline int per_cell(int k) { return k / 2 > 1 ? k / 2 : 1; }
 
 int interp_max_cells(int n, int k) {
   const int pc = per_cell(k);
@@ -117,13 +118,15 @@ __device__ __forceinline__ int fine_of(const GridHeader &g, float3 p) {
   return (cz * g.fdims[1] + cy) * g.fdims[0] + cx;
 }
 
-// Single block: bounds of the cache points, cubic cells sized for about 3k/8
+// Single block: bounds of the cache points, cubic cells sized for about k/2
 // caches each over the occupied axes, the fine pixel-ordering grid, counts
-// cleared.
+// cleared.  The sizing is float arithmetic in the log domain (the cell size
+// only moves work between cells: any size gives the same neighbours).
 __global__ void grid_bounds_kernel(InterpArgs a, InterpScratch s) {
   __shared__ float slo[3][32], shi[3][32];
   __shared__ GridHeader sg;
   float lo[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, hi[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+#pragma unroll 4
   for (int j = threadIdx.x; j < a.n; j += blockDim.x) {
     const float3 p = cache_point(a, j);
     lo[0] = fminf(lo[0], p.x);
@@ -159,46 +162,53 @@ __global__ void grid_bounds_kernel(InterpArgs a, InterpScratch s) {
     }
     float ext[3];
     int active = 0;
-    double vol = 1.0;
+    float log_vol = 0.f;
     for (int d = 0; d < 3; ++d) {
       ext[d] = Hh[d] - L[d];
       if (ext[d] > 0.f) {
         ++active;
-        vol *= (double)ext[d];
+        log_vol += logf(ext[d]);
       }
     }
-    const int pc = 3 * a.k / 8 > 1 ? 3 * a.k / 8 : 1;  // as per_cell()
-    const double target = (double)((a.n + pc - 1) / pc);
-    double h = active ? pow(vol / target, 1.0 / active) : 1.0;
-    if (!(h > 0.0)) h = 1.0;
+    const int pc = a.k / 2 > 1 ? a.k / 2 : 1;  // as per_cell()
+    const float target = (float)((a.n + pc - 1) / pc);
+    float h = active ? expf((log_vol - logf(target)) / (float)active) : 1.f;
+    if (!(h > 0.f) || !(h < FLT_MAX)) h = 1.f;
     GridHeader g;
+    // grow h until the cells fit the scratch (a bounded number of times: a
+    // non-finite extent ends in one cell, which is still an exact search)
+    int tries = 0;
     for (;;) {
       long long prod = 1;
       for (int d = 0; d < 3; ++d) {
-        int nd = ext[d] > 0.f ? (int)ceil((double)ext[d] / h) : 1;
-        if (nd < 1) nd = 1;
+        const float q = ext[d] > 0.f ? ceilf(ext[d] / h) : 1.f;
+        const int nd = q >= 1.f ? (q <= (float)s.max_cells ? (int)q : s.max_cells + 1) : 1;
         g.dims[d] = nd;
         prod *= nd;
+        if (prod > s.max_cells) prod = (long long)s.max_cells + 1;  // no overflow on the next axis
       }
       if (prod <= s.max_cells) {
         g.ncells = (int)prod;
         break;
       }
-      h *= 1.125;
+      if (++tries == 256) {
+        g.dims[0] = g.dims[1] = g.dims[2] = 1;
+        g.ncells = 1;
+        break;
+      }
+      h *= 1.125f;
     }
     for (int d = 0; d < 3; ++d) g.origin[d] = L[d];
-    g.h = (float)h;
-    g.inv_h = (float)(1.0 / h);
+    g.h = h;
+    g.inv_h = 1.f / h;
     // fine grid: each coarse cell split m ways per occupied axis, about 32
-    // pixels per fine cell
+    // pixels per fine cell (16 and 64 measured slower at 1080p)
     int m = 1;
     if (s.order && active) {
-      const double P = (double)a.width * (double)a.height;
-      double tgt = P / 32.0;
-      if (tgt > (double)s.max_fine) tgt = (double)s.max_fine;
-      m = (int)floor(pow(tgt / (double)g.ncells, 1.0 / active));
-      if (m < 1) m = 1;
-      if (m > 64) m = 64;
+      float tgt = (float)a.width * (float)a.height / 32.f;
+      if (tgt > (float)s.max_fine) tgt = (float)s.max_fine;
+      const float mf = floorf(expf(logf(tgt / (float)g.ncells) / (float)active));
+      m = mf >= 64.f ? 64 : (mf >= 1.f ? (int)mf : 1);
     }
     long long nf = 1;
     for (int d = 0; d < 3; ++d) {
@@ -213,8 +223,15 @@ __global__ void grid_bounds_kernel(InterpArgs a, InterpScratch s) {
         nf *= g.fdims[d];
       }
     }
+    if (s.order && nf > s.max_fine) {
+      // more coarse cells than the order scratch has bins (a few pixels,
+      // many caches): every pixel in one bin
+      g.fdims[0] = g.fdims[1] = g.fdims[2] = 1;
+      nf = 1;
+      m = 0;
+    }
     g.nfine = (int)nf;
-    g.fine_inv_h = (float)((double)m / h);
+    g.fine_inv_h = (float)m / h;
     *s.hdr = g;
     sg = g;
   }
@@ -234,32 +251,41 @@ __global__ void grid_count_kernel(InterpArgs a, InterpScratch s) {
 }
 
 // Single block exclusive scan of counts[0..*n_ptr); counts become cursors,
-// starts[*n_ptr] = total.  The bins go in tiles of 4 x blockDim.x: each
-// thread takes four consecutive bins (one 16-byte load and store), the
-// thread totals are scanned across the block, and the running total carries
-// to the next tile, whose loads are issued before this tile's scan.
-__device__ __forceinline__ void scan_load4(const int *counts, int nc, int i0, int (&v)[4]) {
-  if (i0 + 3 < nc) {
-    const int4 q = *reinterpret_cast<const int4 *>(counts + i0);
-    v[0] = q.x, v[1] = q.y, v[2] = q.z, v[3] = q.w;
+// starts[*n_ptr] = total.  The bins go in tiles of SCAN_V x blockDim.x: each
+// thread takes SCAN_V consecutive bins (16-byte loads and stores; counts and
+// starts are 16-byte aligned), the thread totals are scanned across the
+// block, and the running total carries to the next tile, whose loads are
+// issued before this tile's scan.
+static constexpr int SCAN_V = 16;
+__device__ __forceinline__ void scan_load(const int *counts, int nc, int i0, int (&v)[SCAN_V]) {
+  if (i0 + SCAN_V <= nc) {
+#pragma unroll
+    for (int q = 0; q < SCAN_V / 4; ++q) {
+      const int4 t = *reinterpret_cast<const int4 *>(counts + i0 + 4 * q);
+      v[4 * q] = t.x, v[4 * q + 1] = t.y, v[4 * q + 2] = t.z, v[4 * q + 3] = t.w;
+    }
   } else {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = i0 + e < nc ? counts[i0 + e] : 0;
+    for (int e = 0; e < SCAN_V; ++e) v[e] = i0 + e < nc ? counts[i0 + e] : 0;
   }
 }
 __global__ void __launch_bounds__(1024) scan_kernel(const int *n_ptr, int *counts, int *starts) {
   __shared__ int warp_tot[32];
   const int nc = *n_ptr;
-  const int T = 4 * (int)blockDim.x;
+  const int T = SCAN_V * (int)blockDim.x;
   const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int carry = 0;
-  int v[4];
-  scan_load4(counts, nc, 4 * threadIdx.x, v);
+  int v[SCAN_V];
+  scan_load(counts, nc, SCAN_V * threadIdx.x, v);
   for (int base = 0; base < nc; base += T) {
-    const int i0 = base + 4 * threadIdx.x;
-    int nv[4] = {0, 0, 0, 0};
-    if (base + T < nc) scan_load4(counts, nc, i0 + T, nv);
-    const int tsum = v[0] + v[1] + v[2] + v[3];
+    const int i0 = base + SCAN_V * threadIdx.x;
+    int nv[SCAN_V];
+#pragma unroll
+    for (int e = 0; e < SCAN_V; ++e) nv[e] = 0;
+    if (base + T < nc) scan_load(counts, nc, i0 + T, nv);
+    int tsum = 0;
+#pragma unroll
+    for (int e = 0; e < SCAN_V; ++e) tsum += v[e];
     int x = tsum;
     for (int o = 1; o < 32; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, o);
@@ -276,24 +302,32 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int *n_ptr, int *count
       if (l < nw) warp_tot[l] = t;
     }
     __syncthreads();
-    const int off = carry + (w > 0 ? warp_tot[w - 1] : 0) + x - tsum;
-    const int o4[4] = {off, off + v[0], off + v[0] + v[1], off + v[0] + v[1] + v[2]};
-    if (i0 + 3 < nc) {
-      *reinterpret_cast<int4 *>(counts + i0) = make_int4(o4[0], o4[1], o4[2], o4[3]);
+    int run = carry + (w > 0 ? warp_tot[w - 1] : 0) + x - tsum;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) starts[i0 + e] = o4[e];  // starts + i0 may not be 16-byte aligned
+    for (int e = 0; e < SCAN_V; ++e) {  // v becomes the exclusive offsets
+      const int c = v[e];
+      v[e] = run;
+      run += c;
+    }
+    if (i0 + SCAN_V <= nc) {
+#pragma unroll
+      for (int q = 0; q < SCAN_V / 4; ++q) {
+        const int4 o4 = make_int4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        *reinterpret_cast<int4 *>(counts + i0 + 4 * q) = o4;
+        *reinterpret_cast<int4 *>(starts + i0 + 4 * q) = o4;
+      }
     } else {
 #pragma unroll
-      for (int e = 0; e < 4; ++e)
+      for (int e = 0; e < SCAN_V; ++e)
         if (i0 + e < nc) {
-          counts[i0 + e] = o4[e];
-          starts[i0 + e] = o4[e];
+          counts[i0 + e] = v[e];
+          starts[i0 + e] = v[e];
         }
     }
     carry += warp_tot[nw - 1];
     __syncthreads();  // warp_tot is rewritten by the next tile
 #pragma unroll
-    for (int e = 0; e < 4; ++e) v[e] = nv[e];
+    for (int e = 0; e < SCAN_V; ++e) v[e] = nv[e];
   }
   if (threadIdx.x == 0) starts[nc] = carry;
 }
@@ -307,19 +341,34 @@ __global__ void grid_scatter_kernel(InterpArgs a, InterpScratch s) {
   s.pts[pos] = make_float4(p.x, p.y, p.z, __int_as_float(j));
 }
 
+// Pixel counting sort by fine cell.  Neighbouring pixels mostly share a
+// fine cell, so the lanes of a warp that do are grouped (match.any) and one
+// of them adds the group's count: one atomic per group instead of per pixel.
+// The scatter gives a group consecutive slots in lane order.
 __global__ void pixel_count_kernel(InterpArgs a, InterpScratch s) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= (long long)a.width * a.height) return;
+  const long long P = (long long)a.width * a.height;
+  const unsigned live = __ballot_sync(0xffffffffu, p < P);
+  if (p >= P) return;
   const GridHeader g = *s.hdr;
-  atomicAdd(&s.fine_count[fine_of(g, query_point(a, p))], 1);
+  const int f = fine_of(g, query_point(a, p));
+  const unsigned peers = __match_any_sync(live, f);
+  if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&s.fine_count[f], __popc(peers));
 }
 
 __global__ void pixel_scatter_kernel(InterpArgs a, InterpScratch s) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= (long long)a.width * a.height) return;
+  const long long P = (long long)a.width * a.height;
+  const unsigned live = __ballot_sync(0xffffffffu, p < P);
+  if (p >= P) return;
   const GridHeader g = *s.hdr;
-  const int pos = atomicAdd(&s.fine_count[fine_of(g, query_point(a, p))], 1);
-  s.order[pos] = (int)p;
+  const int f = fine_of(g, query_point(a, p));
+  const unsigned peers = __match_any_sync(live, f);
+  const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(&s.fine_count[f], __popc(peers));
+  base = __shfl_sync(live, base, leader);
+  s.order[base + __popc(peers & ((1u << lane) - 1u))] = (int)p;
 }
 
 // The 26 neighbours of a cell, nearest first: faces, edges, corners.
@@ -330,12 +379,21 @@ __constant__ signed char kShell1[26][3] = {
     {-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {1, 1, -1}, {-1, -1, 1}, {1, -1, 1},
     {-1, 1, 1}, {1, 1, 1}};
 
-// k-best register list: KMAX sorted 64-bit keys; the first KMAX-k slots hold
-// 0 (never displaced), so the k-th best is always the last slot.  Insertion
-// (kc below the last key): gt[s] = key[s] > kc is false up to the insertion
-// point and true after it, so each slot takes its lower neighbour (past the
-// point), kc (at it) or itself (before it) -- one 64-bit compare and two
-// 64-bit selects per slot, the compare of slot s - 1 serving slot s - 1 next.
+static constexpr int QUERY_THREADS = 256;
+
+// Selection policies of the walk.  Each takes every candidate the walk
+// visits (offer: its d^2, its slot e in the cell-ordered table and its cache
+// index bits), and tells the walk its current pruning distance (kd2) and
+// whether that distance is a bound yet (bounded).
+
+// Exact k best: KMAX sorted 64-bit keys (d^2 bits << 32 | index, ascending
+// = ascending (d^2, index)); the first KMAX-k slots hold 0 (never
+// displaced), so the k-th best is always the last slot.  Insertion (kc below
+// the last key): gt[s] = key[s] > kc is false up to the insertion point and
+// true after it, so each slot takes its lower neighbour (past the point), kc
+// (at it) or itself (before it) -- one 64-bit compare and two 64-bit selects
+// per slot, the compare of slot s - 1 serving slot s - 1 next.  This gives
+// the ordered neighbour list and settles ties at the k-th distance by index.
 template <int KMAX>
 struct Best {
   unsigned long long key[KMAX];
@@ -354,6 +412,57 @@ struct Best {
     }
     key[0] = g_hi ? kc : key[0];
   }
+  __device__ __forceinline__ bool bounded(int found, int k) const { return found >= k; }
+  __device__ __forceinline__ float kd2() const { return __uint_as_float((unsigned)(last() >> 32)); }
+  __device__ __forceinline__ void offer(float d2, int, float idx_bits) {
+    const unsigned long long kc = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)__float_as_int(idx_bits);
+    if (kc < last()) insert(kc);
+  }
+};
+
+// The k smallest d^2 alone, as 32-bit keys (the bits of a non-negative float
+// order as the float does), same padding.  With no index riding along, slot
+// s after inserting kc is min(key[s], max(key[s-1], kc)): two integer
+// min/max per slot instead of six 32-bit operations.  The last slot ends as
+// the exact k-th smallest d^2, ties counted.
+template <int KMAX>
+struct KthDist {
+  unsigned key[KMAX];
+  __device__ __forceinline__ void init(int k) {
+#pragma unroll
+    for (int s = 0; s < KMAX; ++s) key[s] = s < KMAX - k ? 0u : ~0u;
+  }
+  __device__ __forceinline__ unsigned last() const { return key[KMAX - 1]; }
+  __device__ __forceinline__ bool bounded(int found, int k) const { return found >= k; }
+  __device__ __forceinline__ float kd2() const { return __uint_as_float(last()); }
+  __device__ __forceinline__ void offer(float d2, int, float) {
+    const unsigned kc = __float_as_uint(d2);
+    if (kc < last()) {
+#pragma unroll
+      for (int s = KMAX - 1; s > 0; --s) key[s] = min(key[s], max(key[s - 1], kc));
+      key[0] = min(key[0], kc);
+    }
+  }
+};
+
+// Second walk, under the k-th distance tau: every candidate with d^2 <= tau
+// (bits compared, as in the first walk) is one of the k nearest or tied with
+// the k-th.  Their table slots go down the thread's shared-memory column
+// (stride QUERY_THREADS, at most cap of them); n counts them all, so n > k
+// flags a tie.  tau = ~0u (fewer than k candidates) takes every candidate:
+// as a float it is a NaN, which prunes no cell and stops no shell.
+struct Collect {
+  unsigned tau;
+  int n, cap;
+  int *col;
+  __device__ __forceinline__ bool bounded(int, int) const { return true; }
+  __device__ __forceinline__ float kd2() const { return __uint_as_float(tau); }
+  __device__ __forceinline__ void offer(float d2, int e, float) {
+    if (__float_as_uint(d2) <= tau) {
+      if (n < cap) col[n * QUERY_THREADS] = e;
+      ++n;
+    }
+  }
 };
 
 struct Walk {
@@ -361,10 +470,15 @@ struct Walk {
   int found;
 };
 
-template <int KMAX>
+__device__ __forceinline__ float cand_d2(float3 q, float4 pt) {
+  const float ex = q.x - pt.x, ey = q.y - pt.y, ez = q.z - pt.z;
+  return ex * ex + ey * ey + ez * ez;
+}
+
+template <class Sel>
 __device__ __forceinline__ void visit_cell(const GridHeader &g, const InterpScratch &s, int k, int cx, int cy,
-                                           int cz, Walk &w, Best<KMAX> &best) {
-  if (w.found >= k) {
+                                           int cz, Walk &w, Sel &sel) {
+  if (sel.bounded(w.found, k)) {
     // skip a cell whose box is farther than the current k-th distance
     const float bx0 = g.origin[0] + (float)cx * g.h, by0 = g.origin[1] + (float)cy * g.h,
                 bz0 = g.origin[2] + (float)cz * g.h;
@@ -372,19 +486,14 @@ __device__ __forceinline__ void visit_cell(const GridHeader &g, const InterpScra
     const float dy = fmaxf(fmaxf(by0 - w.q.y, w.q.y - (by0 + g.h)), 0.f);
     const float dz = g.dims[2] > 1 ? fmaxf(fmaxf(bz0 - w.q.z, w.q.z - (bz0 + g.h)), 0.f) : 0.f;
     const float mind2 = dx * dx + dy * dy + dz * dz;
-    const float kd2 = __uint_as_float((unsigned)(best.last() >> 32));
-    if (mind2 > kd2 * 1.00001f + 1e-30f) return;
+    if (mind2 > sel.kd2() * 1.00001f + 1e-30f) return;
   }
   const int cell = (cz * g.dims[1] + cy) * g.dims[0] + cx;
   const int e0 = __ldg(s.cell_start + cell), e1 = __ldg(s.cell_start + cell + 1);
   for (int e = e0; e < e1; ++e) {
     const float4 pt = __ldg(s.pts + e);
-    const float ex = w.q.x - pt.x, ey = w.q.y - pt.y, ez = w.q.z - pt.z;
-    const float d2 = ex * ex + ey * ey + ez * ez;
-    const unsigned long long kc =
-        ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)__float_as_int(pt.w);
     ++w.found;
-    if (kc < best.last()) best.insert(kc);
+    sel.offer(cand_d2(w.q, pt), e, pt.w);
   }
 }
 
@@ -402,28 +511,28 @@ __device__ __forceinline__ float bilinear_map(const float *R, int H, int W, floa
   return (1.f - ai) * ((1.f - aj) * v00 + aj * v01) + ai * ((1.f - aj) * v10 + aj * v11);
 }
 
-// Exact k nearest of q by walking Chebyshev shells of the coarse grid (own
-// cell, the 26 neighbours nearest first, then further shells), skipping
-// cells farther than the current k-th distance, until the k-th distance is
-// below the distance to every unvisited cell.  Returns the candidates seen.
-template <int KMAX>
-__device__ int knn_walk(const GridHeader &g, const InterpScratch &s, int k, float3 q, Best<KMAX> &best) {
+// Walk of Chebyshev shells of the coarse grid around q (own cell, the 26
+// neighbours nearest first, then further shells), skipping cells farther
+// than the policy's current distance, until that distance is below the
+// distance to every unvisited cell: the policy then has seen every
+// candidate a brute-force scan would keep.  Returns the candidates seen.
+template <class Sel>
+__device__ int knn_walk(const GridHeader &g, const InterpScratch &s, int k, float3 q, Sel &sel) {
   Walk w;
   w.q = q;
   w.found = 0;
   int3 c0;
   cell_of(g, w.q, &c0);
-  best.init(k);
   const float margin = 1e-4f * g.h;
   const int maxR = max(g.dims[0], max(g.dims[1], g.dims[2]));
   for (int R = 0; R <= maxR; ++R) {
     if (R == 0) {
-      visit_cell<KMAX>(g, s, k, c0.x, c0.y, c0.z, w, best);
+      visit_cell(g, s, k, c0.x, c0.y, c0.z, w, sel);
     } else if (R == 1) {
       for (int o = 0; o < 26; ++o) {
         const int cx = c0.x + kShell1[o][0], cy = c0.y + kShell1[o][1], cz = c0.z + kShell1[o][2];
         if (cx < 0 || cy < 0 || cz < 0 || cx >= g.dims[0] || cy >= g.dims[1] || cz >= g.dims[2]) continue;
-        visit_cell<KMAX>(g, s, k, cx, cy, cz, w, best);
+        visit_cell(g, s, k, cx, cy, cz, w, sel);
       }
     } else {
       const int z0 = max(c0.z - R, 0), z1 = min(c0.z + R, g.dims[2] - 1);
@@ -434,7 +543,7 @@ __device__ int knn_walk(const GridHeader &g, const InterpScratch &s, int k, floa
           for (int cx = x0; cx <= x1; ++cx) {
             const int cheb = max(abs(cx - c0.x), max(abs(cy - c0.y), abs(cz - c0.z)));
             if (cheb != R) continue;
-            visit_cell<KMAX>(g, s, k, cx, cy, cz, w, best);
+            visit_cell(g, s, k, cx, cy, cz, w, sel);
           }
     }
     float bound = FLT_MAX;
@@ -453,8 +562,8 @@ __device__ int knn_walk(const GridHeader &g, const InterpScratch &s, int k, floa
       }
     }
     if (all) break;
-    if (w.found >= k) {
-      const float kd2 = __uint_as_float((unsigned)(best.last() >> 32));
+    if (sel.bounded(w.found, k)) {
+      const float kd2 = sel.kd2();
       const float b = bound - margin;
       if (b > 0.f && kd2 <= b * b) break;
     }
@@ -462,14 +571,103 @@ __device__ int knn_walk(const GridHeader &g, const InterpScratch &s, int k, floa
   return w.found;
 }
 
-// Weights (Eq. 4), normalisation and blend for pixel p from its k best.
+// Per-pixel data of the blend: the unit-length test of the surface normal
+// and, for LOOKUP, the unit direction the maps are read in.
+struct PixelShade {
+  float nx, ny, nz, nl;
+  float ox, oy, oz;
+  bool dir_ok;
+};
+
+template <int MODE>
+__device__ __forceinline__ PixelShade pixel_shade(const InterpArgs &a, long long p) {
+  PixelShade px;
+  px.nx = __ldg(a.gnrm + 3 * p), px.ny = __ldg(a.gnrm + 3 * p + 1), px.nz = __ldg(a.gnrm + 3 * p + 2);
+  px.nl = sqrtf(px.nx * px.nx + px.ny * px.ny + px.nz * px.nz);
+  px.ox = px.oy = px.oz = 0.f;
+  px.dir_ok = false;
+  if constexpr (MODE != MODE_IRRADIANCE) {
+    const float ox = __ldg(a.gdir + 3 * p), oy = __ldg(a.gdir + 3 * p + 1), oz = __ldg(a.gdir + 3 * p + 2);
+    const float ol = sqrtf(ox * ox + oy * oy + oz * oz);
+    if (ol > 0.f) {
+      px.ox = ox / ol;
+      px.oy = oy / ol;
+      px.oz = oz / ol;
+      px.dir_ok = true;
+    }
+  }
+  return px;
+}
+
+// Eq. 4: w = w_p w_n + w_p + eps for cache j at squared distance d2, with
+// w_p = r / (d + delta) (INVERSE) or max(0, 1 - d / r) (LINEAR) and w_n the
+// clamped cosine between the normals (0 for a zero-length normal).
+__device__ __forceinline__ float nbr_weight(const InterpArgs &a, const PixelShade &px, int j, float d2) {
+  const float d = sqrtf(d2);
+  const float wp = a.wp_form == WP_INVERSE ? a.r / (d + a.delta_rel * a.r) : fmaxf(0.f, 1.f - d / a.r);
+  const float cx = __ldg(a.cnrm + 3 * j), cy = __ldg(a.cnrm + 3 * j + 1), cz = __ldg(a.cnrm + 3 * j + 2);
+  const float cl = sqrtf(cx * cx + cy * cy + cz * cz);
+  float wn = 0.f;
+  if (px.nl > 0.f && cl > 0.f) wn = fmaxf(0.f, (cx * px.nx + cy * px.ny + cz * px.nz) / (cl * px.nl));
+  return wp * wn + wp + a.eps;
+}
+
+// What cache j contributes to the blend: its irradiance payload, or (LOOKUP)
+// a bilinear lat-long read of its map in the pixel's direction expressed in
+// the cache's frame (up = +Z, or +Y when the normal is along Z; t = up x n,
+// b = n x t).  False where the cache adds nothing: a zero normal, or the
+// direction below the cache's horizon.
+template <int MODE>
+__device__ __forceinline__ bool nbr_value(const InterpArgs &a, const PixelShade &px, int j, float3 &v) {
+  if constexpr (MODE == MODE_IRRADIANCE) {
+    v = make_float3(__ldg(a.payload + 3 * j), __ldg(a.payload + 3 * j + 1), __ldg(a.payload + 3 * j + 2));
+    return true;
+  } else {
+    if (!px.dir_ok) return false;
+    const float two_pi = 6.283185307179586f;
+    const size_t map_sz = (size_t)a.mapH * a.mapW;
+    float nx = __ldg(a.cnrm + 3 * j), ny = __ldg(a.cnrm + 3 * j + 1), nz = __ldg(a.cnrm + 3 * j + 2);
+    const float nl = sqrtf(nx * nx + ny * ny + nz * nz);
+    if (!(nl > 0.f)) return false;
+    nx /= nl;
+    ny /= nl;
+    nz /= nl;
+    float ux = 0.f, uy = 0.f, uz = 1.f;
+    if (fabsf(nz) > 1.f - 1e-6f) {
+      uy = 1.f;
+      uz = 0.f;
+    }
+    float tx = uy * nz - uz * ny, ty = uz * nx - ux * nz, tz = ux * ny - uy * nx;
+    const float tl = sqrtf(tx * tx + ty * ty + tz * tz);
+    tx /= tl;
+    ty /= tl;
+    tz /= tl;
+    const float bx = ny * tz - nz * ty, by = nz * tx - nx * tz, bz = nx * ty - ny * tx;
+    const float lx = px.ox * tx + px.oy * ty + px.oz * tz;
+    const float ly = px.ox * bx + px.oy * by + px.oz * bz;
+    float lz = px.ox * nx + px.oy * ny + px.oz * nz;
+    if (!(lz > 0.f)) return false;
+    lz = fminf(lz, 1.f);
+    const float theta = acosf(lz);
+    float phi = atan2f(ly, lx);
+    if (phi < 0.f) phi += two_pi;
+    const float ti = theta * (2.f / 3.14159265358979f) * (float)a.mapH - 0.5f;
+    const float tj = phi * (1.f / two_pi) * (float)a.mapW - 0.5f;
+    const float *Rj = a.maps + (size_t)j * 3 * map_sz;
+    v = make_float3(bilinear_map(Rj, a.mapH, a.mapW, ti, tj), bilinear_map(Rj + map_sz, a.mapH, a.mapW, ti, tj),
+                    bilinear_map(Rj + 2 * map_sz, a.mapH, a.mapW, ti, tj));
+    return true;
+  }
+}
+
+// Normalisation (Sec. 3.2) and blend for pixel p from its k best in (d^2,
+// index) order; the optional neighbour list in that order.
 template <int KMAX, int MODE>
 __device__ __forceinline__ void blend_store(const InterpArgs &a, long long p, const Best<KMAX> &best, int found) {
   const int k = a.k;
   const int kk = found < k ? found : k;
   const int m = KMAX - k;
-  const float pnx = __ldg(a.gnrm + 3 * p), pny = __ldg(a.gnrm + 3 * p + 1), pnz = __ldg(a.gnrm + 3 * p + 2);
-  const float pl = sqrtf(pnx * pnx + pny * pny + pnz * pnz);
+  const PixelShade px = pixel_shade<MODE>(a, p);
   float wt[KMAX];
   int jj[KMAX];
   float wsum = 0.f;
@@ -479,75 +677,20 @@ __device__ __forceinline__ void blend_store(const InterpArgs &a, long long p, co
     jj[sl] = -1;
     if (sl >= m && sl - m < kk) {
       const int j = (int)(unsigned)(best.key[sl] & 0xffffffffu);
-      const float d = sqrtf(__uint_as_float((unsigned)(best.key[sl] >> 32)));
-      const float wp = a.wp_form == WP_INVERSE ? a.r / (d + a.delta_rel * a.r) : fmaxf(0.f, 1.f - d / a.r);
-      const float cx = __ldg(a.cnrm + 3 * j), cy = __ldg(a.cnrm + 3 * j + 1), cz = __ldg(a.cnrm + 3 * j + 2);
-      const float cl = sqrtf(cx * cx + cy * cy + cz * cz);
-      float wn = 0.f;
-      if (pl > 0.f && cl > 0.f) wn = fmaxf(0.f, (cx * pnx + cy * pny + cz * pnz) / (cl * pl));
-      wt[sl] = wp * wn + wp + a.eps;
+      wt[sl] = nbr_weight(a, px, j, __uint_as_float((unsigned)(best.key[sl] >> 32)));
       jj[sl] = j;
       wsum += wt[sl];
     }
   }
   float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
-  if constexpr (MODE == MODE_IRRADIANCE) {
 #pragma unroll
-    for (int sl = 0; sl < KMAX; ++sl)
-      if (jj[sl] >= 0) {
-        const int j = jj[sl];
-        const float Wt = wt[sl] / wsum;
-        acc0 += Wt * __ldg(a.payload + 3 * j);
-        acc1 += Wt * __ldg(a.payload + 3 * j + 1);
-        acc2 += Wt * __ldg(a.payload + 3 * j + 2);
-      }
-  } else {
-    float ox = __ldg(a.gdir + 3 * p), oy = __ldg(a.gdir + 3 * p + 1), oz = __ldg(a.gdir + 3 * p + 2);
-    const float ol = sqrtf(ox * ox + oy * oy + oz * oz);
-    if (ol > 0.f) {
-      ox /= ol;
-      oy /= ol;
-      oz /= ol;
-      const float two_pi = 6.283185307179586f;
-      const size_t map_sz = (size_t)a.mapH * a.mapW;
-#pragma unroll
-      for (int sl = 0; sl < KMAX; ++sl) {
-        if (jj[sl] < 0) continue;
-        const int j = jj[sl];
-        float nx = __ldg(a.cnrm + 3 * j), ny = __ldg(a.cnrm + 3 * j + 1), nz = __ldg(a.cnrm + 3 * j + 2);
-        const float nl = sqrtf(nx * nx + ny * ny + nz * nz);
-        if (!(nl > 0.f)) continue;
-        nx /= nl;
-        ny /= nl;
-        nz /= nl;
-        // frame: up = +Z, or +Y when the normal is along Z; t = up x n, b = n x t
-        float ux = 0.f, uy = 0.f, uz = 1.f;
-        if (fabsf(nz) > 1.f - 1e-6f) {
-          uy = 1.f;
-          uz = 0.f;
-        }
-        float tx = uy * nz - uz * ny, ty = uz * nx - ux * nz, tz = ux * ny - uy * nx;
-        const float tl = sqrtf(tx * tx + ty * ty + tz * tz);
-        tx /= tl;
-        ty /= tl;
-        tz /= tl;
-        const float bx = ny * tz - nz * ty, by = nz * tx - nx * tz, bz = nx * ty - ny * tx;
-        const float lx = ox * tx + oy * ty + oz * tz;
-        const float ly = ox * bx + oy * by + oz * bz;
-        float lz = ox * nx + oy * ny + oz * nz;
-        if (!(lz > 0.f)) continue;
-        lz = fminf(lz, 1.f);
-        const float theta = acosf(lz);
-        float phi = atan2f(ly, lx);
-        if (phi < 0.f) phi += two_pi;
-        const float ti = theta * (2.f / 3.14159265358979f) * (float)a.mapH - 0.5f;
-        const float tj = phi * (1.f / two_pi) * (float)a.mapW - 0.5f;
-        const float Wt = wt[sl] / wsum;
-        const float *Rj = a.maps + (size_t)j * 3 * map_sz;
-        acc0 += Wt * bilinear_map(Rj, a.mapH, a.mapW, ti, tj);
-        acc1 += Wt * bilinear_map(Rj + map_sz, a.mapH, a.mapW, ti, tj);
-        acc2 += Wt * bilinear_map(Rj + 2 * map_sz, a.mapH, a.mapW, ti, tj);
-      }
+  for (int sl = 0; sl < KMAX; ++sl) {
+    float3 v;
+    if (jj[sl] >= 0 && nbr_value<MODE>(a, px, jj[sl], v)) {
+      const float Wt = wt[sl] / wsum;
+      acc0 += Wt * v.x;
+      acc1 += Wt * v.y;
+      acc2 += Wt * v.z;
     }
   }
   a.out[3 * p] = acc0;
@@ -560,20 +703,79 @@ __device__ __forceinline__ void blend_store(const InterpArgs &a, long long p, co
   }
 }
 
+// The same blend from the collected table slots (cnt of them, in visit
+// order): sum of w v over the sum of w.
+template <int MODE>
+__device__ __forceinline__ void blend_list(const InterpArgs &a, const InterpScratch &s, long long p, float3 q,
+                                           const int *col, int cnt) {
+  const PixelShade px = pixel_shade<MODE>(a, p);
+  float wsum = 0.f, acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+  for (int i = 0; i < cnt; ++i) {
+    const float4 pt = __ldg(s.pts + col[i * QUERY_THREADS]);
+    const int j = __float_as_int(pt.w);
+    const float w = nbr_weight(a, px, j, cand_d2(q, pt));
+    wsum += w;
+    float3 v;
+    if (nbr_value<MODE>(a, px, j, v)) {
+      acc0 += w * v.x;
+      acc1 += w * v.y;
+      acc2 += w * v.z;
+    }
+  }
+  const bool any = cnt > 0;
+  a.out[3 * p] = any ? acc0 / wsum : 0.f;
+  a.out[3 * p + 1] = any ? acc1 / wsum : 0.f;
+  a.out[3 * p + 2] = any ? acc2 / wsum : 0.f;
+}
+
 // One thread per pixel (in the spatial order when the pixel ordering is
-// on): exact k nearest by the grid walk, then weights and blend.  MODE is
-// the blend (IRRADIANCE / LOOKUP), fixed at compile time so that each kernel
-// only carries its own registers and code.
-template <int KMAX, int MODE>
-__global__ void __launch_bounds__(256, KMAX <= 16 ? 4 : 2) interp_query_kernel(InterpArgs a, InterpScratch s) {
+// on).  MODE is the blend (IRRADIANCE / LOOKUP), fixed at compile time so
+// that each kernel only carries its own registers and code.
+//
+// FAST (WORLD metric, no neighbour list asked for): the first walk finds the
+// k-th smallest d^2 with 32-bit keys, the second collects every candidate
+// at or below it, and the blend reads them back.  Only a pixel with more
+// than k candidates at or below the k-th distance (a tie there, which the
+// (d^2, index) order settles) takes the exact 64-bit walk.  The other form
+// always takes that walk: integer IMAGE distances tie often, and the
+// neighbour list is given in (d^2, index) order.
+template <int KMAX, int MODE, bool FAST>
+// Blocks per SM: 5 for the IRRADIANCE two-walk form at k <= 16 (48
+// registers and some spill traffic, yet 0.697 ms against 0.705 with 4 at
+// 1080p, k = 16), else 4 (64 registers) or 2.
+__global__ void __launch_bounds__(QUERY_THREADS, KMAX <= 16 ? (FAST && MODE == MODE_IRRADIANCE ? 5 : 4) : 2)
+    interp_query_kernel(InterpArgs a, InterpScratch s) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long P = (long long)a.width * a.height;
   if (t >= P) return;
   const long long p = s.order ? (long long)__ldg(s.order + t) : t;
   const GridHeader g = *s.hdr;
+  const float3 q = query_point(a, p);
+  if constexpr (FAST) {
+    __shared__ int column[KMAX * QUERY_THREADS];
+    int *col = column + threadIdx.x;
+    KthDist<KMAX> kth;
+    kth.init(a.k);
+    knn_walk(g, s, a.k, q, kth);
+    Collect c{kth.last(), 0, KMAX, col};
+    knn_walk(g, s, a.k, q, c);
+    if (c.n <= a.k) {
+      blend_list<MODE>(a, s, p, q, col, c.n);
+      return;
+    }
+  }
   Best<KMAX> best;
-  const int found = knn_walk<KMAX>(g, s, a.k, query_point(a, p), best);
+  best.init(a.k);
+  const int found = knn_walk(g, s, a.k, q, best);
   blend_store<KMAX, MODE>(a, p, best, found);
+}
+
+template <int KMAX, int MODE>
+static void launch_query(const InterpArgs &a, const InterpScratch &s, unsigned blocks, cudaStream_t st) {
+  if (a.metric != METRIC_IMAGE && a.nbr_out == nullptr)
+    interp_query_kernel<KMAX, MODE, true><<<blocks, QUERY_THREADS, 0, st>>>(a, s);
+  else
+    interp_query_kernel<KMAX, MODE, false><<<blocks, QUERY_THREADS, 0, st>>>(a, s);
 }
 
 cudaError_t launch_interp(const InterpArgs &a, const InterpScratch &s, cudaStream_t st, Tracer *tr) {
@@ -590,21 +792,22 @@ cudaError_t launch_interp(const InterpArgs &a, const InterpScratch &s, cudaStrea
     DRC_TRACED(tr, "interp pixel_scan", st, (scan_kernel<<<1, 1024, 0, st>>>(&s.hdr->nfine, s.fine_count, s.fine_start)));
     DRC_TRACED(tr, "interp pixel_scatter", st, (pixel_scatter_kernel<<<blocks, 256, 0, st>>>(a, s)));
   }
+  const unsigned qblocks = (unsigned)((P + QUERY_THREADS - 1) / QUERY_THREADS);
   if (tr) tr->begin("interp query", st);
   if (a.mode == MODE_IRRADIANCE) {
     if (a.k <= 8)
-      interp_query_kernel<8, MODE_IRRADIANCE><<<blocks, 256, 0, st>>>(a, s);
+      launch_query<8, MODE_IRRADIANCE>(a, s, qblocks, st);
     else if (a.k <= 16)
-      interp_query_kernel<16, MODE_IRRADIANCE><<<blocks, 256, 0, st>>>(a, s);
+      launch_query<16, MODE_IRRADIANCE>(a, s, qblocks, st);
     else
-      interp_query_kernel<32, MODE_IRRADIANCE><<<blocks, 256, 0, st>>>(a, s);
+      launch_query<32, MODE_IRRADIANCE>(a, s, qblocks, st);
   } else {
     if (a.k <= 8)
-      interp_query_kernel<8, 1><<<blocks, 256, 0, st>>>(a, s);
+      launch_query<8, 1>(a, s, qblocks, st);
     else if (a.k <= 16)
-      interp_query_kernel<16, 1><<<blocks, 256, 0, st>>>(a, s);
+      launch_query<16, 1>(a, s, qblocks, st);
     else
-      interp_query_kernel<32, 1><<<blocks, 256, 0, st>>>(a, s);
+      launch_query<32, 1>(a, s, qblocks, st);
   }
   if (tr) tr->end(st);
   return cudaGetLastError();

@@ -12,7 +12,7 @@ namespace drc {
 
 struct GridHeader {
   float origin[3];
-  float h, inv_h;      // coarse cells (about 3k/8 caches each)
+  float h, inv_h;      // coarse cells (about k/2 caches each)
   int dims[3];
   int ncells;
   float fine_inv_h;    // fine cells for ordering the pixels (about 32 pixels each)

@@ -173,3 +173,95 @@ def test_empty_and_single_pixel_gbuffer(drc, ctx):
     out, nbr, ref, idx, d2 = _run(drc, ctx, g1, c, 16, drc.METRIC_WORLD, drc.WP_INVERSE, drc.INTERP_IRRADIANCE, r)
     np.testing.assert_array_equal(np.sort(nbr, axis=1), np.sort(idx, axis=1))  # k = n: every cache
     assert rel_err(out, ref) <= FP32_TOL
+
+
+def _window(g, x0, y0, w, h):
+    """A w x h sub-window of a G-buffer, as a G-buffer of its own."""
+    W, H = g["width"], g["height"]
+    pos = g["pos"].reshape(H, W, 3)[y0:y0 + h, x0:x0 + w]
+    nrm = g["nrm"].reshape(H, W, 3)[y0:y0 + h, x0:x0 + w]
+    return {"width": w, "height": h, "pos": np.ascontiguousarray(pos.reshape(-1, 3)),
+            "nrm": np.ascontiguousarray(nrm.reshape(-1, 3))}
+
+
+@pytest.mark.parametrize("gx,gy,win,k", [(64, 64, (3, 2), 16), (160, 150, (128, 96), 4)])
+def test_many_caches_few_pixels(drc, ctx, gx, gy, win, k):
+    """More cache-grid cells than pixel-order bins.  4096 caches over 3 x 2
+    pixels: every pixel goes to one order bin.  24000 caches with k = 4 (one
+    cache per grid cell): the prefix sum over the cache cells spans two tiles
+    of bins and a ragged tail."""
+    big, c = _scene(2 * gx, 2 * gy, gx, gy)
+    g = _window(big, 50, 60, *win)
+    r = synth.world_radius(gx * gy)
+    out, nbr, ref, idx, d2 = _run(drc, ctx, g, c, k, drc.METRIC_WORLD, drc.WP_INVERSE, drc.INTERP_IRRADIANCE, r)
+    ok = ~_ambiguous(d2, k)
+    assert ok.mean() > 0.99
+    np.testing.assert_array_equal(np.sort(nbr[ok], axis=1), np.sort(idx[ok], axis=1))
+    assert rel_err(out[ok], ref[ok]) <= FP32_TOL
+
+
+def _horizon_ok(c, g, idx):
+    """Pixels whose direction grazes none of their caches' horizons (a LOOKUP
+    term switches on or off there)."""
+    n = c["nrm"].astype(np.float64)
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    lz = np.einsum("pc,pkc->pk", g["dir"].astype(np.float64), n[idx])
+    return ~np.any(np.abs(lz) < 1e-5, axis=1)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("k", [1, 4, 8, 13, 16, 32])
+def test_world_without_neighbour_list(drc, ctx, k, mode):
+    """WORLD metric with no neighbour list asked for: the k-th distance from
+    32-bit keys, then every candidate at or below it, blended in visit order.
+    Same images as the oracle and as the exact (d^2, index) path."""
+    g, c = _scene(96, 64, 16, 12, with_maps=mode == 1)
+    r = synth.world_radius(16 * 12)
+    fast = ctx.interpolate(_cuda(c), _cuda(g), k, drc.METRIC_WORLD, drc.WP_INVERSE, mode, r)
+    torch.cuda.synchronize()
+    assert ctx.status() == drc.OK
+    fast = fast.cpu().numpy()
+    exact, nbr, ref, idx, d2 = _run(drc, ctx, g, c, k, drc.METRIC_WORLD, drc.WP_INVERSE, mode, r)
+    ok = ~_ambiguous(d2, k)
+    if mode == 1:
+        ok &= _horizon_ok(c, g, idx)
+    assert ok.mean() > 0.99
+    assert rel_err(fast[ok], ref[ok]) <= FP32_TOL
+    np.testing.assert_allclose(fast[ok], exact[ok], rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("k", [4, 5, 9, 16])
+def test_world_ties_at_kth_distance(drc, ctx, k, mode):
+    """Every cache twice (same point, its own payload and map, index + n):
+    each distance comes in a pair.  Odd k cuts a pair at the k-th distance,
+    where only the lower index belongs: more than k candidates reach the k-th
+    distance and the pixel takes the exact (d^2, index) walk.  Even k keeps
+    pairs whole.  Pixels are compared where the distinct distances around
+    the cut are not near-equal."""
+    g, c = _scene(96, 64, 16, 12, with_maps=mode == 1)
+    n = len(c["pos"])
+    rng = np.random.default_rng(9)
+    c2 = {"pos": np.concatenate([c["pos"], c["pos"]]), "nrm": np.concatenate([c["nrm"], c["nrm"]]),
+          "pix": np.concatenate([c["pix"], c["pix"]]),
+          "payload": np.concatenate([c["payload"], rng.uniform(0.0, 2.0, size=(n, 3)).astype(np.float32)])}
+    if mode == 1:
+        c2["maps"] = np.concatenate([c["maps"], rng.uniform(0.0, 3.0, size=c["maps"].shape).astype(np.float32)])
+    r = synth.world_radius(n)
+    out = ctx.interpolate(_cuda(c2), _cuda(g), k, drc.METRIC_WORLD, drc.WP_INVERSE, mode, r)
+    torch.cuda.synchronize()
+    assert ctx.status() == drc.OK
+    out = out.cpu().numpy()
+    ref, idx, _ = oracle.interpolate(c2, g, k, drc.METRIC_WORLD, drc.WP_INVERSE, mode, r, want_neighbors=True)
+    dd = np.sort(((g["pos"].astype(np.float64)[:, None, :] - c["pos"].astype(np.float64)[None, :, :]) ** 2).sum(-1),
+                 axis=1)
+    m = (k + 1) // 2  # distinct distances taken, the last possibly once
+    ok = ~_ambiguous(dd, m)  # which pair is the m-th
+    if k % 2 == 1 and m > 1:
+        ok &= ~_ambiguous(dd, m - 1)  # which pair is cut
+    if mode == 1:
+        ok &= _horizon_ok(c2, g, idx)
+    assert ok.mean() > 0.97
+    if k % 2 == 1:  # the lower index of the cut pair is the one kept
+        assert np.all(idx[ok, -1] < n)
+    assert rel_err(out[ok], ref[ok]) <= FP32_TOL
