@@ -33,8 +33,8 @@ static constexpr int WP_INVERSE = 0;
 static constexpr int MODE_IRRADIANCE = 0;
 
 // Caches per grid cell the grid is sized for: k/2 (at least 1).  At 4096
-// caches, k = 16, 1080p WORLD the two-walk query measured 0.697 ms with 8
-// per cell, against 0.709 (7) and 0.697 (9); 6 per cell suited the single
+// caches, k = 16, 1080p WORLD the two-walk query measured 0.609 ms with 8
+// per cell, against 0.614 (9) and 0.615 (10); 6 per cell suited the single
 // 64-bit walk, whose insertions cost three times as much.
 static inline int per_cell(int k) { return k / 2 > 1 ? k / 2 : 1; }
 
@@ -413,6 +413,7 @@ struct Best {
     key[0] = g_hi ? kc : key[0];
   }
   __device__ __forceinline__ bool bounded(int found, int k) const { return found >= k; }
+  __device__ __forceinline__ void enter(unsigned) {}
   __device__ __forceinline__ float kd2() const { return __uint_as_float((unsigned)(last() >> 32)); }
   __device__ __forceinline__ void offer(float d2, int, float idx_bits) {
     const unsigned long long kc = ((unsigned long long)__float_as_uint(d2) << 32) | (unsigned)__float_as_int(idx_bits);
@@ -424,23 +425,42 @@ struct Best {
 // order as the float does), same padding.  With no index riding along, slot
 // s after inserting kc is min(key[s], max(key[s-1], kc)): two integer
 // min/max per slot instead of six 32-bit operations.  The last slot ends as
-// the exact k-th smallest d^2, ties counted.
+// the exact k-th smallest d^2, tau.
+//
+// It also keeps, for the second walk, the cells a key went into (mask: bit
+// o < 26 for the o-th neighbour of the first shell, bit 26 for the own cell,
+// bit 27 for any farther cell) and whether more than k candidates may lie
+// within tau (tie).  Every candidate below tau went in when offered (tau
+// only falls), so without a tie the k nearest all lie in mask's cells.  A
+// tie shows as a key equal to the current k-th (refused), or as a key that
+// pushed out a k-th equal to the one below it (that candidate stays within
+// the new k-th distance but out of the list).
+static constexpr unsigned kOwnCell = 1u << 26, kFarCells = 1u << 27;
 template <int KMAX>
 struct KthDist {
   unsigned key[KMAX];
+  unsigned cur, mask;
+  bool tie;
   __device__ __forceinline__ void init(int k) {
 #pragma unroll
     for (int s = 0; s < KMAX; ++s) key[s] = s < KMAX - k ? 0u : ~0u;
+    cur = mask = 0u;
+    tie = false;
   }
   __device__ __forceinline__ unsigned last() const { return key[KMAX - 1]; }
   __device__ __forceinline__ bool bounded(int found, int k) const { return found >= k; }
+  __device__ __forceinline__ void enter(unsigned bit) { cur = bit; }
   __device__ __forceinline__ float kd2() const { return __uint_as_float(last()); }
   __device__ __forceinline__ void offer(float d2, int, float) {
-    const unsigned kc = __float_as_uint(d2);
-    if (kc < last()) {
+    const unsigned kc = __float_as_uint(d2), kl = last();
+    if (kc <= kl) {
+      tie |= kc == kl || (key[KMAX - 2] == kl && kl != ~0u);
+      if (kc < kl) {
 #pragma unroll
-      for (int s = KMAX - 1; s > 0; --s) key[s] = min(key[s], max(key[s - 1], kc));
-      key[0] = min(key[0], kc);
+        for (int s = KMAX - 1; s > 0; --s) key[s] = min(key[s], max(key[s - 1], kc));
+        key[0] = min(key[0], kc);
+        mask |= cur;
+      }
     }
   }
 };
@@ -456,6 +476,7 @@ struct Collect {
   int n, cap;
   int *col;
   __device__ __forceinline__ bool bounded(int, int) const { return true; }
+  __device__ __forceinline__ void enter(unsigned) {}
   __device__ __forceinline__ float kd2() const { return __uint_as_float(tau); }
   __device__ __forceinline__ void offer(float d2, int e, float) {
     if (__float_as_uint(d2) <= tau) {
@@ -476,6 +497,16 @@ __device__ __forceinline__ float cand_d2(float3 q, float4 pt) {
 }
 
 template <class Sel>
+__device__ __forceinline__ void visit_range(const InterpScratch &s, int cell, Walk &w, Sel &sel) {
+  const int e0 = __ldg(s.cell_start + cell), e1 = __ldg(s.cell_start + cell + 1);
+  for (int e = e0; e < e1; ++e) {
+    const float4 pt = __ldg(s.pts + e);
+    ++w.found;
+    sel.offer(cand_d2(w.q, pt), e, pt.w);
+  }
+}
+
+template <class Sel>
 __device__ __forceinline__ void visit_cell(const GridHeader &g, const InterpScratch &s, int k, int cx, int cy,
                                            int cz, Walk &w, Sel &sel) {
   if (sel.bounded(w.found, k)) {
@@ -488,13 +519,7 @@ __device__ __forceinline__ void visit_cell(const GridHeader &g, const InterpScra
     const float mind2 = dx * dx + dy * dy + dz * dz;
     if (mind2 > sel.kd2() * 1.00001f + 1e-30f) return;
   }
-  const int cell = (cz * g.dims[1] + cy) * g.dims[0] + cx;
-  const int e0 = __ldg(s.cell_start + cell), e1 = __ldg(s.cell_start + cell + 1);
-  for (int e = e0; e < e1; ++e) {
-    const float4 pt = __ldg(s.pts + e);
-    ++w.found;
-    sel.offer(cand_d2(w.q, pt), e, pt.w);
-  }
+  visit_range(s, (cz * g.dims[1] + cy) * g.dims[0] + cx, w, sel);
 }
 
 __device__ __forceinline__ float bilinear_map(const float *R, int H, int W, float ti, float tj) {
@@ -527,14 +552,17 @@ __device__ int knn_walk(const GridHeader &g, const InterpScratch &s, int k, floa
   const int maxR = max(g.dims[0], max(g.dims[1], g.dims[2]));
   for (int R = 0; R <= maxR; ++R) {
     if (R == 0) {
+      sel.enter(kOwnCell);
       visit_cell(g, s, k, c0.x, c0.y, c0.z, w, sel);
     } else if (R == 1) {
       for (int o = 0; o < 26; ++o) {
         const int cx = c0.x + kShell1[o][0], cy = c0.y + kShell1[o][1], cz = c0.z + kShell1[o][2];
         if (cx < 0 || cy < 0 || cz < 0 || cx >= g.dims[0] || cy >= g.dims[1] || cz >= g.dims[2]) continue;
+        sel.enter(1u << o);
         visit_cell(g, s, k, cx, cy, cz, w, sel);
       }
     } else {
+      sel.enter(kFarCells);
       const int z0 = max(c0.z - R, 0), z1 = min(c0.z + R, g.dims[2] - 1);
       const int y0 = max(c0.y - R, 0), y1 = min(c0.y + R, g.dims[1] - 1);
       const int x0 = max(c0.x - R, 0), x1 = min(c0.x + R, g.dims[0] - 1);
@@ -734,16 +762,18 @@ __device__ __forceinline__ void blend_list(const InterpArgs &a, const InterpScra
 //
 // FAST (WORLD metric, no neighbour list asked for): the first walk finds the
 // k-th smallest d^2 with 32-bit keys, the second collects every candidate
-// at or below it, and the blend reads them back.  Only a pixel with more
-// than k candidates at or below the k-th distance (a tie there, which the
-// (d^2, index) order settles) takes the exact 64-bit walk.  The other form
+// at or below it from the cells where keys went in (or from a whole second
+// walk, when one went in beyond the first shell), and the blend reads them
+// back.  A pixel with a possible tie at the k-th distance (which the (d^2,
+// index) order settles), or with a count other than min(k, candidates),
+// takes the exact 64-bit walk.  The other form
 // always takes that walk: integer IMAGE distances tie often, and the
 // neighbour list is given in (d^2, index) order.
 template <int KMAX, int MODE, bool FAST>
-// Blocks per SM: 5 for the IRRADIANCE two-walk form at k <= 16 (48
-// registers and some spill traffic, yet 0.697 ms against 0.705 with 4 at
-// 1080p, k = 16), else 4 (64 registers) or 2.
-__global__ void __launch_bounds__(QUERY_THREADS, KMAX <= 16 ? (FAST && MODE == MODE_IRRADIANCE ? 5 : 4) : 2)
+// Blocks per SM: 6 for the IRRADIANCE two-walk form at k <= 16 (40
+// registers and some spill traffic, yet at 1080p, k = 16: 0.609 ms, against
+// 0.626 with 5, 0.632 with 4 and 0.675 with 7), else 4 (64 registers) or 2.
+__global__ void __launch_bounds__(QUERY_THREADS, KMAX <= 16 ? (FAST && MODE == MODE_IRRADIANCE ? 6 : 4) : 2)
     interp_query_kernel(InterpArgs a, InterpScratch s) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long P = (long long)a.width * a.height;
@@ -756,10 +786,25 @@ __global__ void __launch_bounds__(QUERY_THREADS, KMAX <= 16 ? (FAST && MODE == M
     int *col = column + threadIdx.x;
     KthDist<KMAX> kth;
     kth.init(a.k);
-    knn_walk(g, s, a.k, q, kth);
+    const int found = knn_walk(g, s, a.k, q, kth);
     Collect c{kth.last(), 0, KMAX, col};
-    knn_walk(g, s, a.k, q, c);
-    if (c.n <= a.k) {
+    if (kth.mask & kFarCells) {
+      knn_walk(g, s, a.k, q, c);
+    } else {
+      // only the cells of the first shell a key went into
+      Walk w;
+      w.q = q;
+      w.found = 0;
+      int3 c0;
+      const int cell0 = cell_of(g, q, &c0);
+      for (unsigned m = kth.mask; m; m &= m - 1) {
+        const int o = __ffs(m) - 1;
+        const int cell = o == 26 ? cell0
+                                 : cell0 + kShell1[o][0] + g.dims[0] * (kShell1[o][1] + g.dims[1] * kShell1[o][2]);
+        visit_range(s, cell, w, c);
+      }
+    }
+    if (!kth.tie && c.n == min(found, a.k)) {
       blend_list<MODE>(a, s, p, q, col, c.n);
       return;
     }
