@@ -75,9 +75,12 @@ static inline long long max_fine_bins(long long P) {
   return b;
 }
 
+static constexpr long long kScanTile = 16 * 1024;  // bins per scan tile (SCAN_T)
+static inline size_t fine_tiles(long long mf) { return (size_t)((mf + kScanTile - 1) / kScanTile); }
+
 size_t interp_order_bytes(long long P) {
   const size_t mf = (size_t)max_fine_bins(P);
-  return align256(mf * sizeof(int)) + align256((mf + 1) * sizeof(int)) + align256((size_t)P * sizeof(int));
+  return align256(mf * sizeof(int)) + align256(fine_tiles(mf) * sizeof(int)) + align256((size_t)P * sizeof(int));
 }
 
 void interp_attach_order(InterpScratch &s, void *base, long long P) {
@@ -85,8 +88,8 @@ void interp_attach_order(InterpScratch &s, void *base, long long P) {
   char *p = static_cast<char *>(base);
   s.fine_count = reinterpret_cast<int *>(p);
   p += align256(mf * sizeof(int));
-  s.fine_start = reinterpret_cast<int *>(p);
-  p += align256((mf + 1) * sizeof(int));
+  s.fine_tile_sum = reinterpret_cast<int *>(p);
+  p += align256(fine_tiles(mf) * sizeof(int));
   s.order = reinterpret_cast<int *>(p);
   s.max_fine = (int)mf;
 }
@@ -250,13 +253,12 @@ __global__ void grid_count_kernel(InterpArgs a, InterpScratch s) {
   atomicAdd(&s.cell_count[c], 1);
 }
 
-// Single block exclusive scan of counts[0..*n_ptr); counts become cursors,
-// starts[*n_ptr] = total.  The bins go in tiles of SCAN_V x blockDim.x: each
-// thread takes SCAN_V consecutive bins (16-byte loads and stores; counts and
-// starts are 16-byte aligned), the thread totals are scanned across the
-// block, and the running total carries to the next tile, whose loads are
-// issued before this tile's scan.
+// Exclusive scans of bin counts; counts become write cursors.  Each thread
+// takes SCAN_V consecutive bins (16-byte loads and stores; the arrays are
+// 16-byte aligned), so a 1024-thread block covers a tile of SCAN_T bins.
 static constexpr int SCAN_V = 16;
+static constexpr int SCAN_THREADS = 1024;
+static constexpr int SCAN_T = SCAN_V * SCAN_THREADS;
 __device__ __forceinline__ void scan_load(const int *counts, int nc, int i0, int (&v)[SCAN_V]) {
   if (i0 + SCAN_V <= nc) {
 #pragma unroll
@@ -269,67 +271,118 @@ __device__ __forceinline__ void scan_load(const int *counts, int nc, int i0, int
     for (int e = 0; e < SCAN_V; ++e) v[e] = i0 + e < nc ? counts[i0 + e] : 0;
   }
 }
-__global__ void __launch_bounds__(1024) scan_kernel(const int *n_ptr, int *counts, int *starts) {
+
+// Block total of the thread values x (every thread gets it).
+__device__ __forceinline__ int block_sum(int x, int *warp_tot) {
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if (l == 0) warp_tot[w] = x;
+  __syncthreads();
+  int t = 0;
+  for (int i = 0; i < nw; ++i) t += warp_tot[i];
+  __syncthreads();
+  return t;
+}
+
+// One tile starting at base: the thread's bins v (loaded), the total before
+// the tile (carry); writes the exclusive offsets to counts and, when given,
+// starts.  Returns the tile's total.
+__device__ __forceinline__ int scan_tile(int *counts, int *starts, int nc, int base, int carry, int (&v)[SCAN_V],
+                                         int *warp_tot) {
+  const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int i0 = base + SCAN_V * threadIdx.x;
+  int tsum = 0;
+#pragma unroll
+  for (int e = 0; e < SCAN_V; ++e) tsum += v[e];
+  int x = tsum;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (l >= o) x += y;
+  }
+  if (l == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int t = l < nw ? warp_tot[l] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (l >= o) t += y;
+    }
+    if (l < nw) warp_tot[l] = t;
+  }
+  __syncthreads();
+  int run = carry + (w > 0 ? warp_tot[w - 1] : 0) + x - tsum;
+#pragma unroll
+  for (int e = 0; e < SCAN_V; ++e) {  // v becomes the exclusive offsets
+    const int c = v[e];
+    v[e] = run;
+    run += c;
+  }
+  if (i0 + SCAN_V <= nc) {
+#pragma unroll
+    for (int q = 0; q < SCAN_V / 4; ++q) {
+      const int4 o4 = make_int4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+      *reinterpret_cast<int4 *>(counts + i0 + 4 * q) = o4;
+      if (starts) *reinterpret_cast<int4 *>(starts + i0 + 4 * q) = o4;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < SCAN_V; ++e)
+      if (i0 + e < nc) {
+        counts[i0 + e] = v[e];
+        if (starts) starts[i0 + e] = v[e];
+      }
+  }
+  const int tot = warp_tot[nw - 1];
+  __syncthreads();  // warp_tot is rewritten by the next tile
+  return tot;
+}
+
+// Single block over counts[0..*n_ptr) (the cache grid): tile after tile,
+// the next tile's loads issued before this tile's scan; starts[*n_ptr] =
+// total.
+__global__ void __launch_bounds__(SCAN_THREADS) scan_kernel(const int *n_ptr, int *counts, int *starts) {
   __shared__ int warp_tot[32];
   const int nc = *n_ptr;
-  const int T = SCAN_V * (int)blockDim.x;
-  const int l = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   int carry = 0;
   int v[SCAN_V];
   scan_load(counts, nc, SCAN_V * threadIdx.x, v);
-  for (int base = 0; base < nc; base += T) {
-    const int i0 = base + SCAN_V * threadIdx.x;
+  for (int base = 0; base < nc; base += SCAN_T) {
     int nv[SCAN_V];
 #pragma unroll
     for (int e = 0; e < SCAN_V; ++e) nv[e] = 0;
-    if (base + T < nc) scan_load(counts, nc, i0 + T, nv);
-    int tsum = 0;
-#pragma unroll
-    for (int e = 0; e < SCAN_V; ++e) tsum += v[e];
-    int x = tsum;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (l >= o) x += y;
-    }
-    if (l == 31) warp_tot[w] = x;
-    __syncthreads();
-    if (w == 0) {
-      int t = l < nw ? warp_tot[l] : 0;
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, t, o);
-        if (l >= o) t += y;
-      }
-      if (l < nw) warp_tot[l] = t;
-    }
-    __syncthreads();
-    int run = carry + (w > 0 ? warp_tot[w - 1] : 0) + x - tsum;
-#pragma unroll
-    for (int e = 0; e < SCAN_V; ++e) {  // v becomes the exclusive offsets
-      const int c = v[e];
-      v[e] = run;
-      run += c;
-    }
-    if (i0 + SCAN_V <= nc) {
-#pragma unroll
-      for (int q = 0; q < SCAN_V / 4; ++q) {
-        const int4 o4 = make_int4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        *reinterpret_cast<int4 *>(counts + i0 + 4 * q) = o4;
-        *reinterpret_cast<int4 *>(starts + i0 + 4 * q) = o4;
-      }
-    } else {
-#pragma unroll
-      for (int e = 0; e < SCAN_V; ++e)
-        if (i0 + e < nc) {
-          counts[i0 + e] = v[e];
-          starts[i0 + e] = v[e];
-        }
-    }
-    carry += warp_tot[nw - 1];
-    __syncthreads();  // warp_tot is rewritten by the next tile
+    if (base + SCAN_T < nc) scan_load(counts, nc, base + SCAN_T + SCAN_V * threadIdx.x, nv);
+    carry += scan_tile(counts, starts, nc, base, carry, v, warp_tot);
 #pragma unroll
     for (int e = 0; e < SCAN_V; ++e) v[e] = nv[e];
   }
   if (threadIdx.x == 0) starts[nc] = carry;
+}
+
+// Many bins (the pixel order): block b of scan_sum_kernel totals tile b,
+// then block b of scan_tiles_kernel scans tile b from the totals before it.
+// The grids cover the largest bin count; blocks past *n_ptr do nothing.
+__global__ void __launch_bounds__(SCAN_THREADS) scan_sum_kernel(const int *n_ptr, const int *counts, int *tile_sum) {
+  __shared__ int warp_tot[32];
+  const int nc = *n_ptr, base = blockIdx.x * SCAN_T;
+  if (base >= nc) return;  // block-uniform
+  int v[SCAN_V];
+  scan_load(counts, nc, base + SCAN_V * threadIdx.x, v);
+  int t = 0;
+#pragma unroll
+  for (int e = 0; e < SCAN_V; ++e) t += v[e];
+  t = block_sum(t, warp_tot);
+  if (threadIdx.x == 0) tile_sum[blockIdx.x] = t;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_tiles_kernel(const int *n_ptr, int *counts, const int *tile_sum) {
+  __shared__ int warp_tot[32];
+  const int nc = *n_ptr, base = blockIdx.x * SCAN_T;
+  if (base >= nc) return;  // block-uniform
+  int v[SCAN_V];
+  scan_load(counts, nc, base + SCAN_V * threadIdx.x, v);
+  int carry = 0;
+  for (int b = 0; b < (int)blockIdx.x; ++b) carry += __ldg(tile_sum + b);
+  scan_tile(counts, nullptr, nc, base, carry, v, warp_tot);
 }
 
 __global__ void grid_scatter_kernel(InterpArgs a, InterpScratch s) {
@@ -827,14 +880,18 @@ cudaError_t launch_interp(const InterpArgs &a, const InterpScratch &s, cudaStrea
   DRC_TRACED(tr, "interp grid_bounds", st, (grid_bounds_kernel<<<1, 1024, 0, st>>>(a, s)));
   const int cb = (a.n + 255) / 256;
   DRC_TRACED(tr, "interp grid_count", st, (grid_count_kernel<<<cb, 256, 0, st>>>(a, s)));
-  DRC_TRACED(tr, "interp grid_scan", st, (scan_kernel<<<1, 1024, 0, st>>>(&s.hdr->ncells, s.cell_count, s.cell_start)));
+  DRC_TRACED(tr, "interp grid_scan", st, (scan_kernel<<<1, SCAN_THREADS, 0, st>>>(&s.hdr->ncells, s.cell_count, s.cell_start)));
   DRC_TRACED(tr, "interp grid_scatter", st, (grid_scatter_kernel<<<cb, 256, 0, st>>>(a, s)));
   const long long P = (long long)a.width * a.height;
   if (P == 0) return cudaGetLastError();
   const unsigned blocks = (unsigned)((P + 255) / 256);
   if (s.order) {
     DRC_TRACED(tr, "interp pixel_count", st, (pixel_count_kernel<<<blocks, 256, 0, st>>>(a, s)));
-    DRC_TRACED(tr, "interp pixel_scan", st, (scan_kernel<<<1, 1024, 0, st>>>(&s.hdr->nfine, s.fine_count, s.fine_start)));
+    const unsigned tiles = (unsigned)fine_tiles(s.max_fine);
+    DRC_TRACED(tr, "interp pixel_scan", st,
+               (scan_sum_kernel<<<tiles, SCAN_THREADS, 0, st>>>(&s.hdr->nfine, s.fine_count, s.fine_tile_sum)));
+    DRC_TRACED(tr, "interp pixel_scan", st,
+               (scan_tiles_kernel<<<tiles, SCAN_THREADS, 0, st>>>(&s.hdr->nfine, s.fine_count, s.fine_tile_sum)));
     DRC_TRACED(tr, "interp pixel_scatter", st, (pixel_scatter_kernel<<<blocks, 256, 0, st>>>(a, s)));
   }
   const unsigned qblocks = (unsigned)((P + QUERY_THREADS - 1) / QUERY_THREADS);

@@ -29,8 +29,8 @@ struct InterpScratch {
   float4 *pts;       // [n] (x, y, z, index bits) in cell order
   int max_cells;
   // optional pixel ordering (nullptr: pixels are processed in index order)
-  int *fine_count;   // [max_fine] counts, then cursors
-  int *fine_start;   // [max_fine + 1]
+  int *fine_count;     // [max_fine] counts, then cursors
+  int *fine_tile_sum;  // [max_fine / 16384, rounded up] per-tile totals of the counts
   int *order;        // [P] pixel indices sorted by fine cell
   int max_fine;
 };
