@@ -81,7 +81,7 @@ __host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode, int ytma) {
   const int avail = SMEM_BUDGET - SMEM_CTRL - 1024;
   // the FP32 path, and BF16 stores by TMA: with 16-byte bf16 / e4m3 row
   // chunks the staged per-lane epilogue measured slower than the per-row one
-  SmemPlan p = smem_plan_avail(prec, BN, mode, avail - EPI_STG_BYTES);
+  SmemPlan p = smem_plan_avail(prec, BN, mode, avail - (ytma ? EPI_TMA_BYTES : EPI_STG_BYTES));
   if ((prec == PREC_TF32X3 || ytma) && p.stages >= 2 && (mode == PROD_TMA_DIRECT || p.raw_depth >= 2)) {
     p.epi_stage = 1;
     return p;
@@ -124,7 +124,8 @@ static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, 
 size_t conv_smem_bytes(int prec, int BN, int mode, int ytma) {
   const SmemPlan p = smem_plan(prec, BN, mode, ytma);
   return (size_t)SMEM_CTRL + 1024 + (size_t)p.stages * stage_bytes(prec, BN, mode) +
-         (size_t)p.raw_depth * p.raw_slot_bytes + (p.epi_stage ? (size_t)EPI_STG_BYTES : 0);
+         (size_t)p.raw_depth * p.raw_slot_bytes +
+         (p.epi_stage ? (size_t)(ytma ? EPI_TMA_BYTES : EPI_STG_BYTES) : 0);
 }
 
 // Offset of 16-byte chunk q of row r inside a 128-byte-swizzled K-major tile.
@@ -856,8 +857,11 @@ __device__ __forceinline__ void st4(void *base, size_t e, float4 v, const float 
 // skip, no training outputs).  Each 16-column chunk of the warp's 32 rows
 // (bias, ReLU) goes into a 2 KB staging box -- row r at 64 r, its 16-byte
 // chunk c at the 64-byte swizzle position c ^ ((r / 2) % 4) -- and one TMA
-// store writes the box; the box is rewritten only once the previous store
-// has read it.  Rows past M are clipped by the tensor map.
+// store writes the box.  The warp's boxes form a ring (box counts chunks
+// across tiles): a box is rewritten once the store that read it
+// EPI_TMA_BOXES chunks ago is done, while the later ones are still in
+// flight.  With a single box every chunk waited for the store just issued
+// (e1 at 4096 maps: 0.167 ms).  Rows past M are clipped by the tensor map.
 //
 // Decoder phases (LK_CONVT): the warp's 32 rows are y_mw maps x y_rw phase
 // rows x Wrow columns, i.e. a box of the output with element strides 2 in H
@@ -865,7 +869,7 @@ __device__ __forceinline__ void st4(void *base, size_t e, float4 v, const float 
 // (prefetched one chunk ahead, as in the other epilogues).
 template <int PREC>
 __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, int BN, int n0, int row0,
-                                             const PhaseDesc &pd, uint32_t stg, unsigned long long &w_tfull,
+                                             const PhaseDesc &pd, uint32_t ring, int &box, unsigned long long &w_tfull,
                                              uint32_t tfull, uint32_t par, unsigned long long &w_ld) {
   const int lane = threadIdx.x & 31;
   const bool convt = a.kind == LK_CONVT;
@@ -925,7 +929,9 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
       }
       if (cc + 1 < BN / 16) load_sk(cc + 1);
     }
-    if (lane == 0) bulk_wait_read0();
+    const uint32_t stg = ring + (uint32_t)(box * EPI_TMA_BOX_BYTES);
+    box = box + 1 == EPI_TMA_BOXES ? 0 : box + 1;
+    if (lane == 0) bulk_wait_read<EPI_TMA_BOXES - 1>();
     __syncwarp();
     if constexpr (PREC == PREC_BF16) {
       // 32-byte rows, 32-byte swizzle: 16-byte chunk h at h ^ ((r / 4) % 2)
@@ -1333,6 +1339,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     const act_t *skip = reinterpret_cast<const act_t *>(a.skip);
     const int nch = BN / 16;
     float *epi_stg = reinterpret_cast<float *>(data + (size_t)stages * sbytes + (size_t)plan.raw_depth * plan.raw_slot_bytes);
+    int tma_box = 0;  // next box of this warp's TMA staging ring
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++it) {
       const TileCoord tc = tile_coord(a, t);
       const PhaseDesc &pd = a.ph[tc.phase];
@@ -1350,8 +1357,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       if (YTMA && plan.epi_stage) {
         const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
         if (!epi_tile_tma<PREC>(a, taddr, BN, tc.n_tile * BN, tc.m_tile * BM + eq * 32, pd,
-                                smem_u32(epi_stg) + (uint32_t)(eq * 2048), w_tfull, smem_u32(&tfull_bar[buf]), par,
-                                w_ld))
+                                smem_u32(epi_stg) + (uint32_t)(eq * EPI_TMA_BOXES * EPI_TMA_BOX_BYTES), tma_box,
+                                w_tfull, smem_u32(&tfull_bar[buf]), par, w_ld))
           break;
         tc_fence_before();
         __syncwarp();

@@ -103,6 +103,12 @@ struct SmemPlan {
 // Epilogue staging: 4 warps x 32 rows x (16 + 4 pad) floats.
 constexpr int EPI_STG_FLOATS = 4 * 32 * 20;
 constexpr int EPI_STG_BYTES = EPI_STG_FLOATS * 4;
+// Epilogue staging for TMA stores: per warp a ring of boxes of 32 rows x 16
+// columns (2 KB fp32), so a box is rewritten only once the store that read
+// it EPI_TMA_BOXES chunks earlier is done, not the store just issued.
+constexpr int EPI_TMA_BOXES = 4;
+constexpr int EPI_TMA_BOX_BYTES = 2048;
+constexpr int EPI_TMA_BYTES = 4 * EPI_TMA_BOXES * EPI_TMA_BOX_BYTES;
 __host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode, int ytma);
 size_t conv_smem_bytes(int prec, int BN, int mode, int ytma);
 
