@@ -14,6 +14,8 @@ Functions (each cites the passage its C routine follows, see drc_oracle.c):
   payload                 cosine-weighted hemisphere integral (Eq. 2, Sec. 3.3)
   interpolate             kNN + weights w = w_p w_n + w_p + eps (Sec. 3.2)
   l1_backward             L1 loss (Sec. 3.3, Eq. 7) and its exact gradient
+  augment                 rotation / flip of training maps (Sec. 4)
+  adam_step               the Adam step of the training (Sec. 4; Kingma & Ba)
 
 Pins (the tests under ``tests/test_oracle_*.py``) tie every function to
 values fixed by the paper or by mathematics; the one function without such a
@@ -74,6 +76,8 @@ def _load():
                                         i, i, P, P, P]
         lib.orc_l1_backward.restype = d
         lib.orc_conv_wgrad.argtypes = [P, i, i, i, i, P, i, i, P]
+        lib.orc_augment.argtypes = [P, i, i, i, i, P, P]
+        lib.orc_adam_step.argtypes = [P, P, P, P, l, i, d, d, d, d]
         lib.orc_set_threads.argtypes = [i]
         lib.orc_get_threads.restype = i
         _lib = lib
@@ -228,3 +232,33 @@ def l1_backward(weights, x, target, widths, cin=7, cout=3, out_relu=False,
     if rc.value:
         raise ValueError("oracle backward: bad network description (%d)" % rc.value)
     return loss, dw, dx
+
+
+def augment(x, codes):
+    """The eight symmetries of square maps, one per map: code = r + 4 f is a
+    column mirror (f = 1) followed by r counter-clockwise quarter turns.
+    x [N, C, H, W] (H == W), codes [N] in 0..7; returns float64."""
+    x = _f64(x)
+    N, C, H, W = x.shape
+    if H != W:
+        raise ValueError("augment: maps must be square")
+    cd = np.ascontiguousarray(codes, dtype=np.int32)
+    if cd.shape != (N,) or np.any((cd < 0) | (cd > 7)):
+        raise ValueError("augment: one code in 0..7 per map")
+    y = np.empty_like(x)
+    _load().orc_augment(_ptr(x), N, C, H, W, _ptr(cd), _ptr(y))
+    return y
+
+
+def adam_step(w, g, m, v, t, lr=6e-5, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam step (Kingma & Ba 2015, Alg. 1) on copies: returns the new
+    (w, m, v) in float64."""
+    w, g, m, v = _f64(w).copy(), _f64(g), _f64(m).copy(), _f64(v).copy()
+    if not (w.shape == g.shape == m.shape == v.shape):
+        raise ValueError("adam_step: shapes differ")
+    if t < 1:
+        raise ValueError("adam_step: t counts from 1")
+    _load().orc_adam_step(_ptr(w), _ptr(g), _ptr(m), _ptr(v), w.size, int(t), float(lr), float(beta1),
+                          float(beta2), float(eps))
+    return w, m, v
+

@@ -10,8 +10,9 @@
  * of what the method computes, in double precision, so that a reader can
  * check it against the paper by eye.
  *
- * Every tensor handed in is float32 (the exact bytes the GPU path consumes);
- * every computation is carried out in double.
+ * Tensors handed in are float32 (the exact bytes the GPU path consumes), or
+ * exact double copies of them for the augmentation and the optimiser; every
+ * computation is carried out in double.
  *
  * Functions and the passages they follow:
  *   orc_conv3x3s2     3x3 convolution, stride 2, pad 1 (the encoder stages of
@@ -28,6 +29,10 @@
  *                     blend of the cached values (Sec. 3.2, Eqs. 4-6).
  *   orc_l1_backward   L1 loss (Sec. 3.3, Sec. 5.1 Eq. 7) and its exact
  *                     gradient through the network (reverse mode).
+ *   orc_augment       training-data augmentation by rotation and flipping
+ *                     (Sec. 4, Implementation).
+ *   orc_adam_step     one step of the Adam optimiser the training uses
+ *                     (Sec. 4), as defined by Kingma & Ba (2015), Alg. 1.
  * Readings of passages the paper leaves open are listed beside each function.
  */
 #include <math.h>
@@ -766,6 +771,61 @@ double orc_l1_backward(int S, const int *widths, int cin, int cout,
     free(x_raw);
     free(w);
     return loss;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Training (Sec. 4, Implementation): augmentation and the optimiser step.  */
+/* ------------------------------------------------------------------------ */
+
+/* Reading: the paper augments the training pairs with "combinations of
+ * rotation and flipping" of the maps and says no more.  Taken here as the
+ * eight symmetries of the square H = W map, the same one for every channel
+ * of a map (and for the input and target of a pair): code = r + 4 f, first
+ * a mirror of the columns when f = 1 (column j -> W - 1 - j), then r
+ * quarter turns counter-clockwise, one turn being b[i][j] = a[j][W - 1 - i].
+ * Channel values are not changed.  Done literally, one operation after the
+ * other on a scratch image.  x, y: [N][C][H][W]; codes: [N] in 0..7. */
+void orc_augment(const double *x, int N, int C, int H, int W, const int *codes, double *y)
+{
+    const long plane = (long)H * W;
+    double *a = (double *)malloc(sizeof(double) * (size_t)plane);
+    double *b = (double *)malloc(sizeof(double) * (size_t)plane);
+    for (int n = 0; n < N; ++n) {
+        const int f = codes[n] / 4, r = codes[n] % 4;
+        for (int c = 0; c < C; ++c) {
+            const double *src = x + ((long)n * C + c) * plane;
+            for (int i = 0; i < H; ++i)
+                for (int j = 0; j < W; ++j)
+                    a[i * W + j] = f ? src[i * W + (W - 1 - j)] : src[i * W + j];
+            for (int q = 0; q < r; ++q) {
+                for (int i = 0; i < H; ++i)
+                    for (int j = 0; j < W; ++j)
+                        b[i * W + j] = a[j * W + (W - 1 - i)];
+                memcpy(a, b, sizeof(double) * (size_t)plane);
+            }
+            memcpy(y + ((long)n * C + c) * plane, a, sizeof(double) * (size_t)plane);
+        }
+    }
+    free(a);
+    free(b);
+}
+
+/* Adam (Kingma & Ba 2015, Algorithm 1), step t >= 1, on n parameters in
+ * place: m <- b1 m + (1 - b1) g; v <- b2 v + (1 - b2) g^2; the bias
+ * corrections m^ = m / (1 - b1^t), v^ = v / (1 - b2^t); w <- w - lr m^ /
+ * (sqrt(v^) + eps).  The paper uses PyTorch's optimiser, whose update is
+ * this one, with lr = 6e-5 (Sec. 4) and PyTorch's defaults b1 = 0.9,
+ * b2 = 0.999, eps = 1e-8. */
+void orc_adam_step(double *w, const double *g, double *m, double *v, long n, int t, double lr, double b1,
+                   double b2, double eps)
+{
+    const double c1 = 1.0 - pow(b1, (double)t), c2 = 1.0 - pow(b2, (double)t);
+    for (long i = 0; i < n; ++i) {
+        m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+        v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+        const double mh = m[i] / c1, vh = v[i] / c2;
+        w[i] = w[i] - lr * mh / (sqrt(vh) + eps);
+    }
 }
 
 /* Thread control for timing (not arithmetic): the OpenMP team size of the
