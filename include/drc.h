@@ -273,6 +273,36 @@ drc_status drc_weight_grad(drc_ctx *ctx, const void *R, const void *Q,
                            drc_precision dtype, int N, int Hb, int Wb, int Mr,
                            int Qc, int Qraw, float *dW, void *stream);
 
+/* Training-data augmentation (Sec. 4, Implementation: the training pairs are
+ * augmented with combinations of rotation and flipping).  Read as the eight
+ * symmetries of a square map: codes[n] = r + 4 f (only its low three bits
+ * are used) mirrors the columns of map n if f (column j -> W - 1 - j) and
+ * then turns it r quarter turns counter-clockwise (one turn: out[i][j] =
+ * in[j][W - 1 - i]), every channel alike; values are not changed.  Give the
+ * input maps and the targets of a pair the same code.
+ *   in, out: device fp32 [N][C][H][W] (NCHW, contiguous, 16-byte aligned),
+ *            H == W, not overlapping;
+ *   codes:   device int32 [N] (16-byte aligned).
+ * Asynchronous on `stream`.  INVALID_ARG for H != W, a bad shape, host or
+ * unaligned pointers, or overlapping buffers; N = 0 does nothing. */
+drc_status drc_augment(drc_ctx *ctx, const float *in, float *out, int N, int C,
+                       int H, int W, const int *codes, void *stream);
+
+/* One step t >= 1 of Adam (Kingma & Ba 2015, Algorithm 1), the optimiser of
+ * the paper's training (Sec. 4: PyTorch's Adam, learning rate 6e-5; PyTorch's
+ * defaults beta1 = 0.9, beta2 = 0.999, eps = 1e-8), on n parameters in place:
+ *   m = beta1 m + (1 - beta1) g,  v = beta2 v + (1 - beta2) g^2,
+ *   w -= lr m / (1 - beta1^t) / (sqrt(v / (1 - beta2^t)) + eps).
+ * w, grad, m, v: device fp32 [n], 16-byte aligned, caller-owned (m and v
+ * start at zero before step 1).  For the network, w is a device copy of the packed weights and
+ * grad drc_backward's dweights; drc_set_weights(ctx, w, 1, stream) then
+ * makes the new weights current.  Asynchronous on `stream`; INVALID_ARG for
+ * t < 1, lr <= 0, a beta outside [0, 1), eps < 0, host or unaligned
+ * pointers. */
+drc_status drc_adam_step(drc_ctx *ctx, float *w, const float *grad, float *m,
+                         float *v, size_t n, int t, float lr, float beta1,
+                         float beta2, float eps, void *stream);
+
 /* Synchronise `stream` and return (then clear) the latched device status:
  * DRC_OK or DRC_ERR_TIMEOUT. */
 drc_status drc_get_status(drc_ctx *ctx, void *stream);

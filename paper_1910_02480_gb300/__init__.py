@@ -106,6 +106,11 @@ def load_library():
     lib.drc_frame_host.restype = I
     lib.drc_weight_grad.argtypes = [P, P, P, I, I, I, I, I, I, I, P, P]
     lib.drc_weight_grad.restype = I
+    lib.drc_augment.argtypes = [P, P, P, I, I, I, I, P, P]
+    lib.drc_augment.restype = I
+    F = ctypes.c_float
+    lib.drc_adam_step.argtypes = [P, P, P, P, P, ctypes.c_size_t, I, F, F, F, F, P]
+    lib.drc_adam_step.restype = I
     lib.drc_get_status.argtypes = [P, P]
     lib.drc_get_status.restype = I
     lib.drc_last_error.argtypes = [P]
@@ -335,6 +340,29 @@ class Context:
         self._check(rc, "drc_weight_grad")
         return dW
 
+    def augment(self, x, codes, out=None, stream=None):
+        """drc_augment: the symmetry codes[n] (r + 4 f: column mirror, then r
+        counter-clockwise quarter turns) of each square map.  x: cuda float32
+        [N, C, S, S]; codes: cuda int32 [N]."""
+        import torch
+        N, C, H, W = x.shape
+        if out is None:
+            out = torch.empty_like(x)
+        rc = self._lib.drc_augment(self._ctx, _ptr(x), _ptr(out), N, C, H, W, _ptr(codes), _stream(stream))
+        self._check(rc, "drc_augment")
+        return out
+
+    def adam_step(self, w, grad, m, v, t, lr=6e-5, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        """drc_adam_step: one Adam step t >= 1 on cuda float32 tensors w, m, v
+        (updated in place) from grad, all of one size."""
+        n = w.numel()
+        if not (grad.numel() == m.numel() == v.numel() == n):
+            raise ValueError("w, grad, m and v must have one size")
+        rc = self._lib.drc_adam_step(self._ctx, _ptr(w), _ptr(grad), _ptr(m), _ptr(v), n, int(t), float(lr),
+                                     float(beta1), float(beta2), float(eps), _stream(stream))
+        self._check(rc, "drc_adam_step")
+        return w
+
     def status(self, stream=None):
         """Synchronise and return the latched device status code."""
         rc = self._lib.drc_get_status(self._ctx, _stream(stream))
@@ -453,3 +481,34 @@ def denoise_autograd(drc_ctx, x, weights, flags=0):
     """Differentiable denoise: gradients flow to x and to `weights` (a float32
     CUDA tensor holding the context's packed weights)."""
     return _autograd_function().apply(x, weights, drc_ctx, flags)
+
+
+class Trainer:
+    """The training step of Sec. 4 through the C ABI: augment each pair (one
+    code per pair, drc_augment on input and target), the L1 loss and its
+    gradient (drc_backward), one Adam step (drc_adam_step) on a device copy
+    of the weights, which drc_set_weights then makes current.  The defaults
+    are the paper's: lr 6e-5 and PyTorch's Adam constants."""
+
+    def __init__(self, ctx, weights, lr=6e-5, beta1=0.9, beta2=0.999, eps=1e-8, flags=BWD_L1_TARGET):
+        import torch
+        self.ctx = ctx
+        self.w = torch.as_tensor(np.ascontiguousarray(weights, dtype=np.float32)).cuda()
+        self.m = torch.zeros_like(self.w)
+        self.v = torch.zeros_like(self.w)
+        self.t = 0
+        self.lr, self.beta1, self.beta2, self.eps, self.flags = lr, beta1, beta2, eps, flags
+        ctx.set_weights(self.w)
+
+    def step(self, x, target, codes, stream=None):
+        """One step on the pairs (x [N,7,S,S], target [N,3,S,S], cuda float32)
+        with the symmetries codes (cuda int32 [N]); returns the loss tensor."""
+        xa = self.ctx.augment(x, codes, stream=stream)
+        ta = self.ctx.augment(target, codes, stream=stream)
+        loss, dw, _ = self.ctx.backward(xa, ta, flags=self.flags, stream=stream)
+        self.t += 1
+        self.ctx.adam_step(self.w, dw, self.m, self.v, self.t, self.lr, self.beta1, self.beta2, self.eps,
+                           stream=stream)
+        self.ctx.set_weights(self.w, stream=stream)
+        return loss
+

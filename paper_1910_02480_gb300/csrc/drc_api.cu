@@ -20,6 +20,7 @@
 #include "drc_status.cuh"
 #include "interp.cuh"
 #include "trace.cuh"
+#include "train.cuh"
 #include "wgrad_tc.cuh"
 
 using namespace drc;
@@ -1541,6 +1542,46 @@ drc_status drc_weight_grad(drc_ctx *c, const void *R, const void *Q, drc_precisi
   const bool bf = dtype == DRC_PREC_BF16;
   cudaError_t e = weight_grad(c, R, bf, Q, bf, N, Hb, Wb, Mr, Qc, Qraw, dW, nullptr, static_cast<cudaStream_t>(stream));
   return e == cudaSuccess ? DRC_OK : cuda_fail(c, e, "weight gradient");
+}
+
+drc_status drc_augment(drc_ctx *c, const float *in, float *out, int N, int C, int H, int W, const int *codes,
+                       void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (N < 0 || C < 1 || H < 1 || W < 1) return fail(c, DRC_ERR_INVALID_ARG, "bad shape N=%d C=%d H=%d W=%d", N, C, H, W);
+  if (H != W) return fail(c, DRC_ERR_INVALID_ARG, "the rotations need square maps (H=%d, W=%d)", H, W);
+  const long long count = (long long)N * C * H * W;
+  if (count >= (1ll << 31)) return fail(c, DRC_ERR_INVALID_ARG, "maps must stay below 2^31 elements");
+  if (N == 0) return DRC_OK;
+  drc_status s;
+  if ((s = check_dev(c, in, "in", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, out, "out", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, codes, "codes", false)) != DRC_OK) return s;
+  if (in < out + count && out < in + count) return fail(c, DRC_ERR_INVALID_ARG, "in and out overlap");
+  const cudaError_t e = launch_augment(in, out, N, C, H, codes, static_cast<cudaStream_t>(stream), &c->tracer);
+  return e == cudaSuccess ? DRC_OK : cuda_fail(c, e, "augment");
+}
+
+drc_status drc_adam_step(drc_ctx *c, float *w, const float *grad, float *m, float *v, size_t n, int t, float lr,
+                         float beta1, float beta2, float eps, void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (t < 1) return fail(c, DRC_ERR_INVALID_ARG, "t counts steps from 1");
+  if (!(lr > 0.f) || !(lr < INFINITY) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) ||
+      !(eps >= 0.f && eps < INFINITY))
+    return fail(c, DRC_ERR_INVALID_ARG, "need lr > 0, 0 <= beta1, beta2 < 1, eps >= 0");
+  if (n == 0) return DRC_OK;
+  drc_status s;
+  if ((s = check_dev(c, w, "w", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, grad, "grad", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, m, "m", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, v, "v", false)) != DRC_OK) return s;
+  // bias corrections in double on the host, applied as factors
+  const double c1 = 1.0 / (1.0 - std::pow((double)beta1, (double)t));
+  const double c2 = 1.0 / std::sqrt(1.0 - std::pow((double)beta2, (double)t));
+  const cudaError_t e = launch_adam(w, grad, m, v, n, lr, beta1, beta2, eps, (float)c1, (float)c2,
+                                    static_cast<cudaStream_t>(stream), &c->tracer);
+  return e == cudaSuccess ? DRC_OK : cuda_fail(c, e, "adam step");
 }
 
 drc_status drc_frame_host(drc_ctx *c, const float *maps_host, int N, int H, int W, unsigned flags,
