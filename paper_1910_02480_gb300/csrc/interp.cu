@@ -10,12 +10,15 @@
 //    is already coherent for the IMAGE metric).
 // 3. One thread per pixel visits its own cell, then the 26 neighbours nearest
 //    first, then further Chebyshev shells, skipping every cell whose box is
-//    farther than the current k-th distance.  The k best candidates are kept
-//    as 64-bit keys (d^2 bits << 32 | index: ascending key = ascending (d^2,
-//    index), since d^2 >= 0) in a sorted register array updated by a
-//    branch-free min/max network.  The walk stops once the k-th distance is
-//    below the distance to every unvisited cell, so the selection equals a
-//    brute-force scan.
+//    farther than the current k-th distance.  The walk stops once the k-th
+//    distance is below the distance to every unvisited cell, so the
+//    selection equals a brute-force scan.  WORLD metric without a neighbour
+//    list: a first walk keeps the k smallest d^2 as 32-bit keys (two integer
+//    min/max per slot per insertion) and notes the cells where keys went in;
+//    a second pass collects from those cells every candidate at or below the
+//    k-th distance.  Ties there, the IMAGE metric and the neighbour list take
+//    the exact walk, whose sorted register array holds 64-bit keys (d^2 bits
+//    << 32 | index: ascending key = ascending (d^2, index), since d^2 >= 0).
 // 4. Weights w = w_p w_n + w_p + eps (Eq. 4), normalised (Sec. 3.2), blend of
 //    the payloads (IRRADIANCE) or of bilinear lat-long lookups of the cached
 //    maps in each cache's frame (LOOKUP).
