@@ -16,6 +16,9 @@ Functions (each cites the passage its C routine follows, see drc_oracle.c):
   l1_backward             L1 loss (Sec. 3.3, Eq. 7) and its exact gradient
   augment                 rotation / flip of training maps (Sec. 4)
   adam_step               the Adam step of the training (Sec. 4; Kingma & Ba)
+  unet_forward            the paper's own network form: a U-Net (Sec. 3.3),
+                          with its parts conv3x3s1, convT3x3s1, maxpool2,
+                          upsample2 and unet_param_count
 
 Pins (the tests under ``tests/test_oracle_*.py``) tie every function to
 values fixed by the paper or by mathematics; the one function without such a
@@ -77,6 +80,14 @@ def _load():
         lib.orc_l1_backward.restype = d
         lib.orc_conv_wgrad.argtypes = [P, i, i, i, i, P, i, i, P]
         lib.orc_augment.argtypes = [P, i, i, i, i, P, P]
+        lib.orc_conv3x3s1.argtypes = [P, i, P, i, i, i, i, P, P, i, P]
+        lib.orc_convT3x3s1.argtypes = [P, i, P, i, i, i, i, P, P, i, P]
+        lib.orc_maxpool2.argtypes = [P, i, i, i, i, P]
+        lib.orc_upsample2.argtypes = [P, i, i, i, i, P]
+        lib.orc_unet_param_count.argtypes = [i, i, i, i]
+        lib.orc_unet_param_count.restype = l
+        lib.orc_unet_forward.argtypes = [i, i, i, i, P, l, P, i, i, i, P]
+        lib.orc_unet_forward.restype = i
         lib.orc_adam_step.argtypes = [P, P, P, P, l, i, d, d, d, d]
         lib.orc_set_threads.argtypes = [i]
         lib.orc_get_threads.restype = i
@@ -261,4 +272,63 @@ def adam_step(w, g, m, v, t, lr=6e-5, beta1=0.9, beta2=0.999, eps=1e-8):
     _load().orc_adam_step(_ptr(w), _ptr(g), _ptr(m), _ptr(v), w.size, int(t), float(lr), float(beta1),
                           float(beta2), float(eps))
     return w, m, v
+
+
+def conv3x3s1(x, w, b=None, x2=None):
+    """3x3 convolution, stride 1, padding 1, of x (concatenated with x2 along
+    channels when given): x [N, C1, H, W], w [Cout, C1 + C2, 3, 3]."""
+    x = _f64(x)
+    N, C1, H, W = x.shape
+    x2 = None if x2 is None else _f64(x2)
+    C2 = 0 if x2 is None else x2.shape[1]
+    w = _f64(w)
+    y = np.empty((N, w.shape[0], H, W))
+    _load().orc_conv3x3s1(_ptr(x), C1, _ptr(x2), C2, N, H, W, _ptr(w), _ptr(None if b is None else _f64(b)),
+                          w.shape[0], _ptr(y))
+    return y
+
+
+def convT3x3s1(x, w, b=None, x2=None):
+    """3x3 transposed convolution, stride 1, padding 1: w [C1 + C2, Cout, 3, 3]."""
+    x = _f64(x)
+    N, C1, H, W = x.shape
+    x2 = None if x2 is None else _f64(x2)
+    C2 = 0 if x2 is None else x2.shape[1]
+    w = _f64(w)
+    y = np.empty((N, w.shape[1], H, W))
+    _load().orc_convT3x3s1(_ptr(x), C1, _ptr(x2), C2, N, H, W, _ptr(w), _ptr(None if b is None else _f64(b)),
+                           w.shape[1], _ptr(y))
+    return y
+
+
+def maxpool2(x):
+    x = _f64(x)
+    N, C, H, W = x.shape
+    y = np.empty((N, C, H // 2, W // 2))
+    _load().orc_maxpool2(_ptr(x), N, C, H, W, _ptr(y))
+    return y
+
+
+def upsample2(x):
+    """Bilinear 2x upsampling at half-pixel centres."""
+    x = _f64(x)
+    N, C, H, W = x.shape
+    y = np.empty((N, C, 2 * H, 2 * W))
+    _load().orc_upsample2(_ptr(x), N, C, H, W, _ptr(y))
+    return y
+
+
+def unet_param_count(base=64, levels=3, cin=7, cout=3) -> int:
+    return int(_load().orc_unet_param_count(cin, cout, base, levels))
+
+
+def unet_forward(params, x, base=64, levels=3, cin=7, cout=3):
+    """The paper's U-Net (readings in drc_oracle.c) on x [N, cin, H, W]."""
+    p, x = _f32(params), _f32(x)
+    N, C, H, W = x.shape
+    out = np.empty((N, cout, H, W))
+    rc = _load().orc_unet_forward(cin, cout, base, levels, _ptr(p), p.size, _ptr(x), N, H, W, _ptr(out))
+    if rc:
+        raise ValueError("oracle unet: parameter count or shape does not fit")
+    return out
 

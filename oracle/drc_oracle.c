@@ -33,6 +33,13 @@
  *                     (Sec. 4, Implementation).
  *   orc_adam_step     one step of the Adam optimiser the training uses
  *                     (Sec. 4), as defined by Kingma & Ba (2015), Alg. 1.
+ *   orc_unet_forward  the paper's own network form (Sec. 3.3 "Neural
+ *                     network"): a U-Net of two 3x3 convolutions per stage
+ *                     with batch normalisation and LeakyReLU, 2x2 max
+ *                     pooling, 2x bilinear upsampling, concatenated skips
+ *                     and a 1x1 convolution with ReLU; with its parts
+ *                     orc_conv3x3s1, orc_convT3x3s1, orc_maxpool2 and
+ *                     orc_upsample2.
  * Readings of passages the paper leaves open are listed beside each function.
  */
 #include <math.h>
@@ -826,6 +833,259 @@ void orc_adam_step(double *w, const double *g, double *m, double *v, long n, int
         const double mh = m[i] / c1, vh = v[i] / c2;
         w[i] = w[i] - lr * mh / (sqrt(vh) + eps);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* The paper's network form (Sec. 3.3, "Neural network").  Each encoder    */
+/* stage takes two 3x3 convolutions and doubles the depth, each decoder    */
+/* stage two 3x3 deconvolutions halving it; intermediate stages use batch  */
+/* normalisation and LeakyReLU; the output stage has two deconvolutions    */
+/* with LeakyReLU and a final 1x1 convolution with ReLU; downsampling is   */
+/* 2x2 max pooling, upsampling 2x bilinear.  Base depth 64, three          */
+/* downsizing steps (4x4 at the bottom for 32x32 maps).                    */
+/*                                                                          */
+/* Readings (the paper's network diagram is missing):                       */
+/*  - the convolutions have stride 1 and zero padding 1, the deconvolutions */
+/*    are stride-1 transposed convolutions, padding 1;                      */
+/*  - levels l = 0..L have depths c_l = base 2^l; the deepest level (l = L) */
+/*    is the 4x4 bottleneck, reached by L poolings;                         */
+/*  - U-Net skips: a decoder stage upsamples the deeper features and        */
+/*    concatenates them (first) with the encoder output of its level        */
+/*    (second), then applies its two deconvolutions;                        */
+/*  - the output stage is decoder level 0: its deconvolutions take          */
+/*    LeakyReLU without batch normalisation;                                 */
+/*  - PyTorch's conventions, the paper's framework: LeakyReLU slope 0.01,   */
+/*    batch normalisation at inference y = g (x - mu) / sqrt(var + 1e-5) +  */
+/*    b, bilinear sampling at half-pixel centres (source (i + 1/2)/2 - 1/2, */
+/*    clamped at 0; the upper neighbour clamped at the last row / column).  */
+/* Packed parameters, layer by layer: encoder levels 0..L (two 3x3 convs    */
+/* each, W [Cout][Cin][3][3], b, g, beta, mu, var), decoder levels L-1..0   */
+/* (two 3x3 deconvs each, W [Cin][Cout][3][3], b, and g, beta, mu, var      */
+/* below level 0), then the head (W [Cout][c_0], b).                        */
+/* ------------------------------------------------------------------------ */
+
+static const double ORC_LRELU_SLOPE = 0.01, ORC_BN_EPS = 1e-5;
+
+/* y[n,o,i,j] = b[o] + sum_{c,u,v} W[o,c,u,v] z[n,c,i+u-1,j+v-1], z the
+ * channel concatenation of x1 (C1 channels) and x2 (C2, may be 0), zero
+ * outside the map.  Output H x W. */
+void orc_conv3x3s1(const double *x1, int C1, const double *x2, int C2, int N, int H, int W,
+                   const double *Wt, const double *b, int Cout, double *y)
+{
+    const int Cin = C1 + C2;
+#pragma omp parallel for schedule(static)
+    for (int n = 0; n < N; n++)
+        for (int o = 0; o < Cout; o++)
+            for (int i = 0; i < H; i++)
+                for (int j = 0; j < W; j++) {
+                    double acc = b ? b[o] : 0.0;
+                    for (int c = 0; c < Cin; c++) {
+                        const double *src = c < C1 ? x1 + ((long)n * C1 + c) * H * W
+                                                   : x2 + ((long)n * C2 + (c - C1)) * H * W;
+                        for (int u = 0; u < 3; u++)
+                            for (int v = 0; v < 3; v++) {
+                                int yy = i + u - 1, xx = j + v - 1;
+                                if (yy < 0 || yy >= H || xx < 0 || xx >= W)
+                                    continue;
+                                acc += Wt[((o * Cin + c) * 3 + u) * 3 + v] * src[yy * W + xx];
+                            }
+                    }
+                    y[(((long)n * Cout + o) * H + i) * W + j] = acc;
+                }
+}
+
+/* y[n,o,p,q] = b[o] + sum over (c,i,j,u,v) with i+u-1 = p, j+v-1 = q of
+ * W[c,o,u,v] z[n,c,i,j] (z as above): the scatter of every input pixel
+ * through every tap, dropping taps outside the map.  Output H x W. */
+void orc_convT3x3s1(const double *x1, int C1, const double *x2, int C2, int N, int H, int W,
+                    const double *Wt, const double *b, int Cout, double *y)
+{
+    const int Cin = C1 + C2;
+#pragma omp parallel for schedule(static)
+    for (int n = 0; n < N; n++) {
+        double *yn = y + (long)n * Cout * H * W;
+        for (int o = 0; o < Cout; o++)
+            for (long e = 0; e < (long)H * W; e++)
+                yn[(long)o * H * W + e] = b ? b[o] : 0.0;
+        for (int c = 0; c < Cin; c++) {
+            const double *src = c < C1 ? x1 + ((long)n * C1 + c) * H * W
+                                       : x2 + ((long)n * C2 + (c - C1)) * H * W;
+            for (int i = 0; i < H; i++)
+                for (int j = 0; j < W; j++)
+                    for (int o = 0; o < Cout; o++)
+                        for (int u = 0; u < 3; u++)
+                            for (int v = 0; v < 3; v++) {
+                                int p = i + u - 1, q = j + v - 1;
+                                if (p < 0 || p >= H || q < 0 || q >= W)
+                                    continue;
+                                yn[((long)o * H + p) * W + q] += Wt[((c * Cout + o) * 3 + u) * 3 + v] * src[i * W + j];
+                            }
+        }
+    }
+}
+
+/* y[n,c,i,j] = max of x[n,c,2i..2i+1,2j..2j+1].  Output (H/2) x (W/2). */
+void orc_maxpool2(const double *x, int N, int C, int H, int W, double *y)
+{
+    const int Ho = H / 2, Wo = W / 2;
+    for (long nc = 0; nc < (long)N * C; nc++)
+        for (int i = 0; i < Ho; i++)
+            for (int j = 0; j < Wo; j++) {
+                const double *s = x + nc * H * W;
+                double m = s[(2 * i) * W + 2 * j];
+                if (s[(2 * i) * W + 2 * j + 1] > m) m = s[(2 * i) * W + 2 * j + 1];
+                if (s[(2 * i + 1) * W + 2 * j] > m) m = s[(2 * i + 1) * W + 2 * j];
+                if (s[(2 * i + 1) * W + 2 * j + 1] > m) m = s[(2 * i + 1) * W + 2 * j + 1];
+                y[(nc * Ho + i) * Wo + j] = m;
+            }
+}
+
+/* Bilinear 2x upsampling at half-pixel centres: output row p samples input
+ * row s = (p + 1/2) / 2 - 1/2 (s >= 0), between floor(s) and the next row
+ * (clamped to the last), weights 1 - (s - floor s) and s - floor s; columns
+ * alike.  Output (2H) x (2W). */
+static void up_index(int p, int n, int *i0, int *i1, double *f)
+{
+    double s = (p + 0.5) / 2.0 - 0.5;
+    if (s < 0.0) s = 0.0;
+    *i0 = (int)floor(s);
+    *i1 = *i0 + 1 < n ? *i0 + 1 : n - 1;
+    *f = s - *i0;
+}
+void orc_upsample2(const double *x, int N, int C, int H, int W, double *y)
+{
+    const int Ho = 2 * H, Wo = 2 * W;
+    for (long nc = 0; nc < (long)N * C; nc++)
+        for (int p = 0; p < Ho; p++)
+            for (int q = 0; q < Wo; q++) {
+                int i0, i1, j0, j1;
+                double fi, fj;
+                up_index(p, H, &i0, &i1, &fi);
+                up_index(q, W, &j0, &j1, &fj);
+                const double *s = x + nc * H * W;
+                const double top = (1.0 - fj) * s[i0 * W + j0] + fj * s[i0 * W + j1];
+                const double bot = (1.0 - fj) * s[i1 * W + j0] + fj * s[i1 * W + j1];
+                y[(nc * Ho + p) * Wo + q] = (1.0 - fi) * top + fi * bot;
+            }
+}
+
+/* batch normalisation at inference (when g is given), then LeakyReLU. */
+static void bn_lrelu(double *x, int N, int C, long HW, const double *g, const double *beta, const double *mu,
+                     const double *var)
+{
+    for (int n = 0; n < N; n++)
+        for (int c = 0; c < C; c++) {
+            double *p = x + ((long)n * C + c) * HW;
+            for (long e = 0; e < HW; e++) {
+                double z = p[e];
+                if (g)
+                    z = g[c] * (z - mu[c]) / sqrt(var[c] + ORC_BN_EPS) + beta[c];
+                p[e] = z >= 0.0 ? z : ORC_LRELU_SLOPE * z;
+            }
+        }
+}
+
+static long unet_layer_floats(int cin, int cout, int bn) { return 9L * cin * cout + cout + (bn ? 4L * cout : 0); }
+
+long orc_unet_param_count(int cin, int cout, int base, int levels)
+{
+    long n = 0;
+    for (int l = 0; l <= levels; l++) {
+        const int c = base << l, ci = l == 0 ? cin : base << (l - 1);
+        n += unet_layer_floats(ci, c, 1) + unet_layer_floats(c, c, 1);
+    }
+    for (int l = levels - 1; l >= 0; l--) {
+        const int c = base << l;
+        n += unet_layer_floats(2 * c + c, c, l > 0) + unet_layer_floats(c, c, l > 0);
+    }
+    return n + (long)cout * base + cout;
+}
+
+/* The forward pass of the U-Net above on x [N][cin][H][W] (H and W multiples
+ * of 2^levels) into out [N][cout][H][W].  Returns 0, or -1 for a parameter
+ * count or shape that does not fit. */
+int orc_unet_forward(int cin, int cout, int base, int levels, const float *params, long n_params, const float *xf,
+                     int N, int H, int W, double *out)
+{
+    if (levels < 1 || levels > 6 || base < 1 || H % (1 << levels) || W % (1 << levels) ||
+        n_params != orc_unet_param_count(cin, cout, base, levels))
+        return -1;
+    double *P = widen(params, n_params);
+    const double *p = P;
+    double *enc[8];
+    double *x = widen(xf, (long)N * cin * H * W);
+    int h = H, w = W;
+    const double *in = x;
+    int ci = cin;
+    double *pooled = NULL;
+    for (int l = 0; l <= levels; l++) {
+        const int c = base << l;
+        const long hw = (long)h * w;
+        double *a = (double *)malloc(sizeof(double) * N * c * hw);
+        enc[l] = (double *)malloc(sizeof(double) * N * c * hw);
+        for (int k = 0; k < 2; k++) {
+            const int kin = k == 0 ? ci : c;
+            const double *Wt = p, *b = p + 9L * kin * c, *g = b + c, *be = g + c, *mu = be + c, *var = mu + c;
+            p = var + c;
+            double *dst = k == 0 ? a : enc[l];
+            orc_conv3x3s1(k == 0 ? in : a, kin, NULL, 0, N, h, w, Wt, b, c, dst);
+            bn_lrelu(dst, N, c, hw, g, be, mu, var);
+        }
+        free(a);
+        free(pooled);
+        pooled = NULL;
+        if (l < levels) {
+            pooled = (double *)malloc(sizeof(double) * N * c * (hw / 4));
+            orc_maxpool2(enc[l], N, c, h, w, pooled);
+            h /= 2;
+            w /= 2;
+            in = pooled;
+            ci = c;
+        }
+    }
+    double *d = enc[levels];
+    for (int l = levels - 1; l >= 0; l--) {
+        const int c = base << l, cd = base << (l + 1);
+        h *= 2;
+        w *= 2;
+        const long hw = (long)h * w;
+        double *u = (double *)malloc(sizeof(double) * N * cd * hw);
+        orc_upsample2(d, N, cd, h / 2, w / 2, u);
+        double *a = (double *)malloc(sizeof(double) * N * c * hw);
+        double *dn = (double *)malloc(sizeof(double) * N * c * hw);
+        const int bn = l > 0;
+        for (int k = 0; k < 2; k++) {
+            const int kin = k == 0 ? cd + c : c;
+            const double *Wt = p, *b = p + 9L * kin * c;
+            const double *g = bn ? b + c : NULL, *be = bn ? b + 2 * c : NULL, *mu = bn ? b + 3 * c : NULL,
+                         *var = bn ? b + 4 * c : NULL;
+            p = b + c + (bn ? 4 * c : 0);
+            if (k == 0)
+                orc_convT3x3s1(u, cd, enc[l], c, N, h, w, Wt, b, c, a);
+            else
+                orc_convT3x3s1(a, c, NULL, 0, N, h, w, Wt, b, c, dn);
+            bn_lrelu(k == 0 ? a : dn, N, c, hw, g, be, mu, var);
+        }
+        free(u);
+        free(a);
+        free(d);
+        d = dn;
+    }
+    /* head: 1x1 convolution c_0 -> cout, ReLU */
+    const double *Wh = p, *bh = p + (long)cout * base;
+    const long hw = (long)H * W;
+    for (int n = 0; n < N; n++)
+        for (int o = 0; o < cout; o++)
+            for (long e = 0; e < hw; e++) {
+                double acc = bh[o];
+                for (int c = 0; c < base; c++) acc += Wh[o * base + c] * d[((long)n * base + c) * hw + e];
+                out[((long)n * cout + o) * hw + e] = acc > 0.0 ? acc : 0.0;
+            }
+    free(d);
+    for (int l = 0; l < levels; l++) free(enc[l]);
+    free(x);
+    free(P);
+    return 0;
 }
 
 /* Thread control for timing (not arithmetic): the OpenMP team size of the

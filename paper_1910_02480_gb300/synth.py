@@ -12,7 +12,9 @@ noisy low-sample radiance, interior-room geometry (a unit box).
 
 Recipe (all draws from numpy's PCG64 ``default_rng(seed)``):
   * weights: He init, W ~ N(0, 2 / (9 * Cin)) for every conv and transposed
-    conv, b = 0 (or U(-0.1, 0.1) when ``bias=True``).
+    conv, b = 0 (or U(-0.1, 0.1) when ``bias=True``).  The paper-form U-Net
+    adds batch-normalisation statistics gamma, var ~ U(0.5, 1.5) and beta,
+    mean ~ U(-0.1, 0.1).
   * environment: m = 8 spherical-Gaussian lobes
     L(w) = sum_l a_l exp(lam_l (mu_l . w - 1)), mu_l uniform on the sphere,
     lam_l ~ U[2, 50], a_l RGB ~ U[0.1, 2] (or log-uniform on [1e-3, 1e3]).
@@ -70,6 +72,45 @@ def he_weights(widths, cin=CIN, cout=COUT, seed=0, bias=False) -> np.ndarray:
             parts.append(rng.uniform(-0.1, 0.1, size=blen))
         else:
             parts.append(np.zeros(blen))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def unet_layer_shapes(base=64, levels=3, cin=CIN, cout=COUT):
+    """The packed layout of the paper-form U-Net: (kind, W shape, number of
+    per-channel vectors after W: bias, then gamma, beta, mean, var when the
+    layer has batch normalisation).  Encoder levels 0..L (two convs each),
+    decoder levels L-1..0 (two transposed convs each; the first takes the
+    upsampled deeper features and the level's skip, concatenated; level 0
+    without batch normalisation), then the 1x1 head."""
+    out = []
+    for lvl in range(levels + 1):
+        c = base << lvl
+        ci = cin if lvl == 0 else base << (lvl - 1)
+        out.append(("conv", (c, ci, 3, 3), 5))
+        out.append(("conv", (c, c, 3, 3), 5))
+    for lvl in range(levels - 1, -1, -1):
+        c = base << lvl
+        nvec = 5 if lvl > 0 else 1
+        out.append(("convT", (3 * c, c, 3, 3), nvec))
+        out.append(("convT", (c, c, 3, 3), nvec))
+    out.append(("head", (cout, base), 1))
+    return out
+
+
+def unet_params(base=64, levels=3, cin=CIN, cout=COUT, seed=0) -> np.ndarray:
+    """Packed float32 U-Net parameters: He-initialised W, b ~ U(-0.1, 0.1),
+    and batch-normalisation statistics gamma ~ U(0.5, 1.5), beta ~
+    U(-0.1, 0.1), mean ~ U(-0.1, 0.1), var ~ U(0.5, 1.5)."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for kind, wshape, nvec in unet_layer_shapes(base, levels, cin, cout):
+        fan_in = wshape[1] if kind == "head" else 9 * (wshape[1] if kind == "conv" else wshape[0])
+        parts.append(rng.normal(0.0, np.sqrt(2.0 / fan_in), size=wshape).ravel())
+        co = wshape[0] if kind in ("conv", "head") else wshape[1]
+        parts.append(rng.uniform(-0.1, 0.1, size=co))
+        if nvec == 5:
+            parts += [rng.uniform(0.5, 1.5, size=co), rng.uniform(-0.1, 0.1, size=co),
+                      rng.uniform(-0.1, 0.1, size=co), rng.uniform(0.5, 1.5, size=co)]
     return np.concatenate(parts).astype(np.float32)
 
 
