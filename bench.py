@@ -354,6 +354,54 @@ def measure_training_paper(drc, torch, dev, batch=32, pool=512, steps=40):
             "kernel_ms_per_step": {k: round(v, 4) for k, v in sorted(by.items(), key=lambda kv: -kv[1])}}
 
 
+def unet_flops_per_map(base=64, levels=3, H=32, W=32, cin=7, cout=3):
+    """Valid multiply-adds x 2 of the paper-form U-Net on one H x W map: a
+    stride-1 3x3 layer with zero padding meets (3H - 2)(3W - 2) in-map taps
+    per channel pair; the 1x1 head H W."""
+    flops = 0.0
+    for lvl in range(levels + 1):
+        h, w, c = H >> lvl, W >> lvl, base << lvl
+        ci = cin if lvl == 0 else base << (lvl - 1)
+        flops += 2.0 * (3 * h - 2) * (3 * w - 2) * (ci * c + c * c)
+    for lvl in range(levels - 1, -1, -1):
+        h, w, c = H >> lvl, W >> lvl, base << lvl
+        flops += 2.0 * (3 * h - 2) * (3 * w - 2) * (3 * c * c + c * c)
+    return flops + 2.0 * H * W * base * cout
+
+
+def measure_unet(drc, torch, dev, N=256, steps=10):
+    """The paper's own network form (Sec. 3.3: a U-Net, base 64, three
+    downsizing steps, 7.8 M parameters), FP32 on the CUDA cores, on 256
+    synthetic 7 x 32 x 32 maps.  Bound by FP32 FMA issue: the peak is 152 SMs
+    x 128 lanes x 2 FLOP at the 2070 MHz maximum clock."""
+    from paper_1910_02480_gb300 import synth
+    g = synth.gbuffer(N, 1, seed=18)
+    x, _ = synth.hemisphere_maps(g["pos"], g["nrm"], H=32, W=32, seed=19)
+    xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev)
+    ctx = drc.Context([16], synth.he_weights([16]), precision="fp32")
+    net = drc.UNet(ctx, synth.unet_params(64, 3, seed=0), 64, 3)
+    for _ in range(3):
+        net.forward(xd)
+    torch.cuda.synchronize()
+    a, b = _events(torch)
+    a.record()
+    for _ in range(steps):
+        net.forward(xd)
+    b.record()
+    torch.cuda.synchronize()
+    if ctx.status() != drc.OK:
+        raise RuntimeError("device status after the U-Net")
+    ms = a.elapsed_time(b) / steps
+    fl = unet_flops_per_map() * N
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    ctx.close()
+    return {"workload": "%d maps 7x32x32, U-Net base 64, 3 levels, fp32 CUDA cores" % N, "ms": ms,
+            "maps_per_s": N / (ms * 1e-3), "flops_per_map": fl / N,
+            "roofline": {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": fl / (ms * 1e-3) / 1e12 / peak,
+                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal unit counts)"}}
+
+
 def make_inputs(seed_offset=0):
     from paper_1910_02480_gb300 import synth
     g = synth.gbuffer(IMG_W, IMG_H, seed=2 + seed_offset)
@@ -671,6 +719,7 @@ def main():
         extra("uneven_batching", lambda: measure_uneven(drc, torch, dev))
         extra("training", lambda: measure_training(drc, torch, dev))
         extra("training_paper_settings", lambda: measure_training_paper(drc, torch, dev))
+        extra("paper_form_unet", lambda: measure_unet(drc, torch, dev))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         b = cpu_baseline(w, x, g, c, one_thread=True)
         b.pop("step_s", None)

@@ -303,6 +303,39 @@ drc_status drc_adam_step(drc_ctx *ctx, float *w, const float *grad, float *m,
                          float *v, size_t n, int t, float lr, float beta1,
                          float beta2, float eps, void *stream);
 
+/* The paper's own network form (Sec. 3.3, "Neural network"), FP32 on the
+ * CUDA cores: a U-Net.  Levels l = 0..levels have depth base * 2^l.  Each
+ * encoder level applies two 3x3 convolutions (stride 1, padding 1), each
+ * followed by batch normalisation (inference statistics, eps 1e-5) and
+ * LeakyReLU (slope 0.01); 2x2 max pooling leads to the next level.  Each
+ * decoder level l = levels-1..0 upsamples the deeper features 2x
+ * (bilinear, half-pixel centres), concatenates them (first) with the encoder
+ * output of level l (second) and applies two 3x3 transposed convolutions
+ * (stride 1, padding 1), each followed by batch normalisation and LeakyReLU,
+ * except at level 0 (LeakyReLU only).  A 1x1 convolution to out_ch channels
+ * with ReLU ends it.  The paper's network: in_ch 7, out_ch 3, base 64,
+ * levels 3.
+ *   params: device fp32, drc_unet_param_count floats, layer by layer:
+ *           encoder levels 0..levels (two convs each: W [Cout][Cin][3][3],
+ *           b, gamma, beta, mean, var), decoder levels levels-1..0 (two
+ *           transposed convs each: W [Cin][Cout][3][3], b, and gamma, beta,
+ *           mean, var except at level 0), the head (W [out_ch][base], b)
+ *           -- the PyTorch layouts;
+ *   in:     device fp32 [N][in_ch][H][W], H and W multiples of 2^levels;
+ *   out:    device fp32 [N][out_ch][H][W];
+ *   workspace: device memory of drc_unet_workspace_bytes (folded weights
+ *           and every activation), caller-owned.
+ * All pointers 16-byte aligned.  Asynchronous on `stream`; INVALID_ARG for a
+ * bad shape, a short workspace, host or unaligned pointers.  The two size
+ * queries return 0 for shapes the forward pass refuses. */
+size_t drc_unet_param_count(int in_ch, int out_ch, int base, int levels);
+size_t drc_unet_workspace_bytes(int in_ch, int out_ch, int base, int levels,
+                                int N, int H, int W);
+drc_status drc_unet_forward(drc_ctx *ctx, int in_ch, int out_ch, int base,
+                            int levels, const float *params, const float *in,
+                            float *out, int N, int H, int W, void *workspace,
+                            size_t workspace_bytes, void *stream);
+
 /* Synchronise `stream` and return (then clear) the latched device status:
  * DRC_OK or DRC_ERR_TIMEOUT. */
 drc_status drc_get_status(drc_ctx *ctx, void *stream);

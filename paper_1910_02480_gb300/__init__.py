@@ -111,6 +111,13 @@ def load_library():
     F = ctypes.c_float
     lib.drc_adam_step.argtypes = [P, P, P, P, P, ctypes.c_size_t, I, F, F, F, F, P]
     lib.drc_adam_step.restype = I
+    SZ = ctypes.c_size_t
+    lib.drc_unet_param_count.argtypes = [I, I, I, I]
+    lib.drc_unet_param_count.restype = SZ
+    lib.drc_unet_workspace_bytes.argtypes = [I, I, I, I, I, I, I]
+    lib.drc_unet_workspace_bytes.restype = SZ
+    lib.drc_unet_forward.argtypes = [P, I, I, I, I, P, P, P, I, I, I, P, SZ, P]
+    lib.drc_unet_forward.restype = I
     lib.drc_get_status.argtypes = [P, P]
     lib.drc_get_status.restype = I
     lib.drc_last_error.argtypes = [P]
@@ -511,4 +518,46 @@ class Trainer:
                            stream=stream)
         self.ctx.set_weights(self.w, stream=stream)
         return loss
+
+
+def unet_param_count(base=64, levels=3, in_ch=7, out_ch=3):
+    """drc_unet_param_count: packed parameters of the paper-form U-Net (0 for
+    a shape the forward pass refuses)."""
+    return int(load_library().drc_unet_param_count(in_ch, out_ch, base, levels))
+
+
+class UNet:
+    """The paper's own network form (a U-Net, Sec. 3.3) through
+    drc_unet_forward, on a context's stream and error reporting.  params:
+    the packed layout of drc.h (e.g. synth.unet_params); the workspace is
+    kept per batch shape."""
+
+    def __init__(self, ctx, params, base=64, levels=3, in_ch=7, out_ch=3):
+        import torch
+        self.ctx, self.base, self.levels, self.in_ch, self.out_ch = ctx, base, levels, in_ch, out_ch
+        n = unet_param_count(base, levels, in_ch, out_ch)
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if n == 0 or p.size != n:
+            raise ValueError("expected %d U-Net parameters, got %d" % (n, p.size))
+        self.params = torch.from_numpy(p).cuda()
+        self._ws, self._ws_shape = None, None
+
+    def workspace_bytes(self, N, H, W):
+        return int(self.ctx._lib.drc_unet_workspace_bytes(self.in_ch, self.out_ch, self.base, self.levels, N, H, W))
+
+    def forward(self, x, out=None, stream=None):
+        """x: cuda float32 [N, in_ch, H, W] -> out [N, out_ch, H, W]."""
+        import torch
+        N, C, H, W = x.shape
+        if out is None:
+            out = torch.empty((N, self.out_ch, H, W), dtype=torch.float32, device=x.device)
+        if self._ws_shape != (N, H, W):
+            nb = max(self.workspace_bytes(N, H, W), 16)
+            self._ws = torch.empty(nb, dtype=torch.uint8, device=x.device)
+            self._ws_shape = (N, H, W)
+        rc = self.ctx._lib.drc_unet_forward(self.ctx._ctx, self.in_ch, self.out_ch, self.base, self.levels,
+                                            _ptr(self.params), _ptr(x), _ptr(out), N, H, W, _ptr(self._ws),
+                                            self._ws.numel(), _stream(stream))
+        self.ctx._check(rc, "drc_unet_forward")
+        return out
 

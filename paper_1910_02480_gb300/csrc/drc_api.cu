@@ -21,6 +21,7 @@
 #include "interp.cuh"
 #include "trace.cuh"
 #include "train.cuh"
+#include "unet.cuh"
 #include "wgrad_tc.cuh"
 
 using namespace drc;
@@ -1582,6 +1583,51 @@ drc_status drc_adam_step(drc_ctx *c, float *w, const float *grad, float *m, floa
   const cudaError_t e = launch_adam(w, grad, m, v, n, lr, beta1, beta2, eps, (float)c1, (float)c2,
                                     static_cast<cudaStream_t>(stream), &c->tracer);
   return e == cudaSuccess ? DRC_OK : cuda_fail(c, e, "adam step");
+}
+
+static bool unet_shape_ok(int in_ch, int out_ch, int base, int levels) {
+  return in_ch >= 1 && in_ch <= 64 && out_ch >= 1 && out_ch <= 64 && levels >= 1 && levels <= 6 && base >= 1 &&
+         ((long long)base << levels) <= 4096;
+}
+
+size_t drc_unet_param_count(int in_ch, int out_ch, int base, int levels) {
+  if (!unet_shape_ok(in_ch, out_ch, base, levels)) return 0;
+  return unet_param_count(UnetShape{in_ch, out_ch, base, levels});
+}
+
+size_t drc_unet_workspace_bytes(int in_ch, int out_ch, int base, int levels, int N, int H, int W) {
+  if (!unet_shape_ok(in_ch, out_ch, base, levels) || N < 0 || H < 1 || W < 1 || H % (1 << levels) ||
+      W % (1 << levels))
+    return 0;
+  return unet_workspace_bytes(UnetShape{in_ch, out_ch, base, levels}, N, H, W);
+}
+
+drc_status drc_unet_forward(drc_ctx *c, int in_ch, int out_ch, int base, int levels, const float *params,
+                            const float *in, float *out, int N, int H, int W, void *workspace, size_t workspace_bytes,
+                            void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!unet_shape_ok(in_ch, out_ch, base, levels))
+    return fail(c, DRC_ERR_INVALID_ARG, "bad network in_ch=%d out_ch=%d base=%d levels=%d", in_ch, out_ch, base, levels);
+  if (N < 0 || H < 1 || W < 1 || H % (1 << levels) || W % (1 << levels))
+    return fail(c, DRC_ERR_INVALID_ARG, "maps must be multiples of 2^levels (N=%d H=%d W=%d)", N, H, W);
+  const long long widest = 3LL * base > in_ch ? 3LL * base : in_ch;
+  if ((long long)N * H * W * widest >= (1ll << 31))
+    return fail(c, DRC_ERR_INVALID_ARG, "activations must stay below 2^31 elements");
+  const UnetShape u{in_ch, out_ch, base, levels};
+  const size_t need = unet_workspace_bytes(u, N, H, W);
+  if (workspace_bytes < need)
+    return fail(c, DRC_ERR_INVALID_ARG, "workspace of %zu bytes, %zu needed (drc_unet_workspace_bytes)",
+                workspace_bytes, need);
+  if (N == 0) return DRC_OK;
+  drc_status s;
+  if ((s = check_dev(c, params, "params", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, in, "in", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, out, "out", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, workspace, "workspace", false)) != DRC_OK) return s;
+  const cudaError_t e = unet_forward(u, params, in, out, N, H, W, workspace, static_cast<cudaStream_t>(stream),
+                                     &c->tracer);
+  return e == cudaSuccess ? DRC_OK : cuda_fail(c, e, "unet forward");
 }
 
 drc_status drc_frame_host(drc_ctx *c, const float *maps_host, int N, int H, int W, unsigned flags,
