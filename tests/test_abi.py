@@ -69,3 +69,29 @@ def test_null_context_is_rejected(lib):
     assert lib.drc_denoise(None, None, None, None, 1, 32, 32, 0, None) == drc.ERR_INVALID_ARG
     assert lib.drc_get_status(None, None) == drc.ERR_INVALID_ARG
     assert lib.drc_destroy(None) == drc.ERR_INVALID_ARG
+
+
+def test_unet_size_queries(lib):
+    """The paper-form U-Net's two host-side size queries: the parameter count
+    agrees with the oracle's and with the seeded generator's layout; the
+    workspace holds the folded weights plus every activation and grows with
+    the batch; shapes the forward pass refuses give 0."""
+    import numpy as np
+
+    import oracle
+    import paper_1910_02480_gb300 as drc
+    from paper_1910_02480_gb300 import synth
+    for base, levels in ((64, 3), (8, 2), (20, 1), (4, 4)):
+        n = drc.unet_param_count(base, levels)
+        assert n == oracle.unet_param_count(base, levels) == synth.unet_params(base, levels).size
+    ws = lambda N, H, W, base=64, levels=3: int(lib.drc_unet_workspace_bytes(7, 3, base, levels, N, H, W))
+    # per level l (c = 64 2^l channels): enc_a, enc; the pooled input (c / 2,
+    # l > 0); up (2c), dec_a, dec (l < 3)
+    floats_per_map = sum((64 << l) * ((32 >> l) ** 2) * (2 + (0.5 if l > 0 else 0) + (4 if l < 3 else 0))
+                         for l in range(4))
+    assert ws(256, 32, 32) - ws(0, 32, 32) >= 256 * floats_per_map * 4
+    assert ws(0, 32, 32) >= 4 * (drc.unet_param_count(64, 3) - 4 * 64 * 2 * 3)  # folded weights
+    assert ws(512, 32, 32) > ws(256, 32, 32) > ws(1, 32, 32)
+    assert ws(1, 24, 32) == 0 and ws(-1, 32, 32) == 0 and ws(1, 32, 32, levels=0) == 0
+    assert drc.unet_param_count(64, 7) == 0 and drc.unet_param_count(0, 3) == 0
+    assert np.isfinite(ws(1, 32, 32))
