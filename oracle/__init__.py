@@ -16,6 +16,9 @@ Functions (each cites the passage its C routine follows, see drc_oracle.c):
   l1_backward             L1 loss (Sec. 3.3, Eq. 7) and its exact gradient
   augment                 rotation / flip of training maps (Sec. 4)
   adam_step               the Adam step of the training (Sec. 4; Kingma & Ba)
+  mis_indirect            the indirect term of Eq. 3 by multiple importance
+                          sampling over the blended maps and the BRDF
+                          (Sec. 3.2), with indirect_expected, its expectation
   unet_forward            the paper's own network form: a U-Net (Sec. 3.3),
                           with its parts conv3x3s1, convT3x3s1, maxpool2,
                           upsample2 and unet_param_count
@@ -73,7 +76,11 @@ def _load():
         lib.orc_forward.restype = i
         lib.orc_payload.argtypes = [P, i, i, i, i, P]
         lib.orc_interp.argtypes = [i, i, i, P, P, P, P, P, i, i, P, P, P,
-                                   i, i, i, i, d, d, d, l, l, P, P, P]
+                                   i, i, i, i, d, d, d, l, l, P, P, P, P]
+        lib.orc_mis_indirect.argtypes = [i, i, i, P, P, l, i, P, P, P, P, i, P, P]
+        lib.orc_mis_indirect.restype = i
+        lib.orc_indirect_expected.argtypes = [i, i, i, P, P, l, i, P, P, P, P, i, P]
+        lib.orc_indirect_expected.restype = i
         lib.orc_interp.restype = i
         lib.orc_l1_backward.argtypes = [i, P, i, i, i, d, u, P, l, P, P, i, i,
                                         i, i, P, P, P]
@@ -189,7 +196,7 @@ def payload(L):
 
 
 def interpolate(caches, gbuf, k, metric, wp_form, mode, r, eps=1e-6,
-                delta_rel=1e-3, p_range=None, want_neighbors=False):
+                delta_rel=1e-3, p_range=None, want_neighbors=False, want_weights=False):
     """Blend cached values at every G-buffer pixel (Sec. 3.2).
 
     caches: dict with 'payload' [n,3], 'pos' [n,3], 'nrm' [n,3], 'pix' [n,2]
@@ -197,7 +204,8 @@ def interpolate(caches, gbuf, k, metric, wp_form, mode, r, eps=1e-6,
     gbuf:   dict with 'width', 'height', 'pos' [P,3], 'nrm' [P,3],
             'dir' [P,3] (LOOKUP only).
     Returns out [p1-p0, 3] (and neighbour indices [.,k], the k+1 smallest
-    squared distances [.,k+1] when want_neighbors).
+    squared distances [.,k+1] when want_neighbors; and the normalised weights
+    [.,k] last when want_weights).
     """
     n = caches["pos"].shape[0]
     maps = caches.get("maps")
@@ -215,16 +223,16 @@ def interpolate(caches, gbuf, k, metric, wp_form, mode, r, eps=1e-6,
     out = np.empty((p1 - p0, 3))
     idx = np.empty((p1 - p0, k), dtype=np.int32) if want_neighbors else None
     d2 = np.empty((p1 - p0, k + 1)) if want_neighbors else None
+    wts = np.empty((p1 - p0, k)) if want_weights else None
     rc = _load().orc_interp(n, mH, mW, _ptr(maps), _ptr(pay), _ptr(cpos),
                             _ptr(cnrm), _ptr(cpix), width, height, _ptr(gpos),
                             _ptr(gnrm), _ptr(gdir), k, metric, wp_form, mode,
                             float(r), float(eps), float(delta_rel), p0, p1,
-                            _ptr(out), _ptr(idx), _ptr(d2))
+                            _ptr(out), _ptr(idx), _ptr(d2), _ptr(wts))
     if rc:
         raise ValueError("oracle interpolate: bad arguments (%d)" % rc)
-    if want_neighbors:
-        return out, idx, d2
-    return out
+    res = (out,) + ((idx, d2) if want_neighbors else ()) + ((wts,) if want_weights else ())
+    return res if len(res) > 1 else out
 
 
 def l1_backward(weights, x, target, widths, cin=7, cout=3, out_relu=False,
@@ -330,5 +338,44 @@ def unet_forward(params, x, base=64, levels=3, cin=7, cout=3):
     rc = _load().orc_unet_forward(cin, cout, base, levels, _ptr(p), p.size, _ptr(x), N, H, W, _ptr(out))
     if rc:
         raise ValueError("oracle unet: parameter count or shape does not fit")
+    return out
+
+
+def _mis_args(caches, nbr_idx, nbr_w, gnrm, albedo):
+    maps = _f32(caches["maps"])
+    n, _, H, W = maps.shape
+    idx = np.ascontiguousarray(nbr_idx, dtype=np.int32)
+    P, k = idx.shape
+    w = _f64(nbr_w)
+    if w.shape != (P, k):
+        raise ValueError("nbr_w must match nbr_idx")
+    return maps, n, H, W, _f32(caches["nrm"]), idx, P, k, w, _f32(gnrm), _f32(albedo)
+
+
+def mis_indirect(caches, nbr_idx, nbr_w, gnrm, albedo, u):
+    """The indirect term at P pixels: caches 'maps' [n,3,H,W] (linear
+    radiance) and 'nrm'; the pixels' k caches and normalised weights
+    [P,k]; pixel normals and albedos [P,3]; uniforms u [P,S,4].  Readings
+    in drc_oracle.c.  Returns [P,3]."""
+    maps, n, H, W, cnrm, idx, P, k, w, gn, alb = _mis_args(caches, nbr_idx, nbr_w, gnrm, albedo)
+    u = _f64(u)
+    if u.shape[0] != P or u.shape[2] != 4:
+        raise ValueError("u must be [P, S, 4]")
+    out = np.empty((P, 3))
+    rc = _load().orc_mis_indirect(n, H, W, _ptr(maps), _ptr(cnrm), P, k, _ptr(idx), _ptr(w), _ptr(gn), _ptr(alb),
+                                  u.shape[1], _ptr(u), _ptr(out))
+    if rc:
+        raise ValueError("oracle mis_indirect: bad arguments")
+    return out
+
+
+def indirect_expected(caches, nbr_idx, nbr_w, gnrm, albedo, m=16):
+    """The expectation of mis_indirect by quadrature (m x m cells per texel)."""
+    maps, n, H, W, cnrm, idx, P, k, w, gn, alb = _mis_args(caches, nbr_idx, nbr_w, gnrm, albedo)
+    out = np.empty((P, 3))
+    rc = _load().orc_indirect_expected(n, H, W, _ptr(maps), _ptr(cnrm), P, k, _ptr(idx), _ptr(w), _ptr(gn),
+                                       _ptr(alb), int(m), _ptr(out))
+    if rc:
+        raise ValueError("oracle indirect_expected: bad arguments")
     return out
 

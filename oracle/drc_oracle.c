@@ -33,6 +33,10 @@
  *                     (Sec. 4, Implementation).
  *   orc_adam_step     one step of the Adam optimiser the training uses
  *                     (Sec. 4), as defined by Kingma & Ba (2015), Alg. 1.
+ *   orc_mis_indirect  the indirect term of Eq. 3 estimated with multiple
+ *                     importance sampling over the blended cached maps and
+ *                     the BRDF (Sec. 3.2); orc_indirect_expected, its
+ *                     expectation by quadrature.
  *   orc_unet_forward  the paper's own network form (Sec. 3.3 "Neural
  *                     network"): a U-Net of two 3x3 convolutions per stage
  *                     with batch normalisation and LeakyReLU, 2x2 max
@@ -432,7 +436,7 @@ int orc_interp(int n_caches, int mapH, int mapW, const float *maps,
                const float *gnrm, const float *gdir, int k, int metric,
                int wp_form, int mode, double r, double eps, double delta_rel,
                long p_begin, long p_end, double *out, int *nbr_idx,
-               double *nbr_d2)
+               double *nbr_d2, double *nbr_w)
 {
     if (k < 1 || k > 64 || n_caches < 1)
         return -1;
@@ -538,6 +542,215 @@ int orc_interp(int n_caches, int mapH, int mapW, const float *maps,
         if (nbr_d2)
             for (int q = 0; q <= k; q++)
                 nbr_d2[o * (k + 1) + q] = q < nb ? bd[q] : INFINITY;
+        if (nbr_w)
+            for (int q = 0; q < k; q++)
+                nbr_w[o * k + q] = q < kk ? w[q] / wsum : 0.0;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The indirect term by multiple importance sampling (Sec. 3.2 with Eq. 3), */
+/* a next step of this build.                                               */
+/* ------------------------------------------------------------------------ */
+/* The paper evaluates the indirect term of Eq. 3, the hemisphere integral of
+ * f_r cos(theta_i) R(omega_i), with a small fixed number of samples,
+ * alternating between sampling R as an environment map with perfect
+ * visibility and sampling the BRDF, combined by multiple importance sampling
+ * (Veach).  R at a pixel is the blend of its k nearest caches' maps with the
+ * normalised weights of Eq. 4 (orc_interp); drawn as map-selection
+ * probabilities the weights make the estimate's expectation the integral of
+ * that blend.
+ * Readings: a Lambertian BRDF f_r = albedo / pi.  Texel (a, b) of a map holds
+ * one radiance over its solid angle: polar angle in [a, a+1) pi / (2H) from
+ * the cache normal, azimuth in [b, b+1) 2 pi / W in the cache frame (the
+ * frame rule of the lookup above).  Environment sampling picks a texel with
+ * probability proportional to its luminance 0.2126 R + 0.7152 G + 0.0722 B
+ * times its solid angle, then a direction uniform in solid angle inside it.
+ * BRDF sampling is cosine-weighted about the pixel normal (a frame of the
+ * same rule).  Sample s takes the environment for even s and the BRDF for
+ * odd s; the balance heuristic weighs them by their sample counts, which
+ * reduces a sample's contribution to f_r cos R / (n_env pdf_env + n_brdf
+ * pdf_brdf).  The random numbers are an input: u [P][S][4] uniform in
+ * [0, 1), the map choice and three for the direction. */
+
+static double texel_lum(const float *maps, int j, int H, int W, int a, int b)
+{
+    const long plane = (long)H * W;
+    const float *R = maps + (long)j * 3 * plane + (long)a * W + b;
+    return 0.2126 * R[0] + 0.7152 * R[plane] + 0.0722 * R[2 * plane];
+}
+
+/* solid angle of a texel in row a */
+static double texel_omega(int a, int H, int W)
+{
+    return (cos(a * 0.5 * ORC_PI / H) - cos((a + 1) * 0.5 * ORC_PI / H)) * 2.0 * ORC_PI / W;
+}
+
+/* texel of world direction w in the frame (t, b, n); 0 below the hemisphere */
+static int texel_of(const double t[3], const double b[3], const double n[3], const double w[3], int H, int W,
+                    int *ta, int *tb)
+{
+    double lx = w[0] * t[0] + w[1] * t[1] + w[2] * t[2];
+    double ly = w[0] * b[0] + w[1] * b[1] + w[2] * b[2];
+    double lz = w[0] * n[0] + w[1] * n[1] + w[2] * n[2];
+    if (!(lz > 0.0))
+        return 0;
+    double theta = acos(lz > 1.0 ? 1.0 : lz);
+    double phi = atan2(ly, lx);
+    if (phi < 0.0)
+        phi += 2.0 * ORC_PI;
+    int a = (int)floor(theta / (0.5 * ORC_PI) * H), c = (int)floor(phi / (2.0 * ORC_PI) * W);
+    *ta = a < 0 ? 0 : (a > H - 1 ? H - 1 : a);
+    *tb = c < 0 ? 0 : (c > W - 1 ? W - 1 : c);
+    return 1;
+}
+
+/* per-map luminance x solid-angle CDF over the H W texels (row-major) */
+static double *env_cdfs(int n_caches, int H, int W, const float *maps)
+{
+    const long plane = (long)H * W;
+    double *cdf = (double *)malloc(sizeof(double) * (size_t)(n_caches * plane));
+    for (int j = 0; j < n_caches; j++) {
+        double acc = 0.0;
+        for (int a = 0; a < H; a++)
+            for (int b = 0; b < W; b++) {
+                acc += texel_lum(maps, j, H, W, a, b) * texel_omega(a, H, W);
+                cdf[(long)j * plane + (long)a * W + b] = acc;
+            }
+    }
+    return cdf;
+}
+
+int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const float *cnrm, long P, int k,
+                     const int *nbr_idx, const double *nbr_w, const float *gnrm, const float *albedo, int S,
+                     const double *u, double *out)
+{
+    if (n_caches < 1 || mapH < 1 || mapW < 1 || k < 1 || S < 1)
+        return -1;
+    const long plane = (long)mapH * mapW;
+    double *cdf = env_cdfs(n_caches, mapH, mapW, maps);
+    const double n_env = (double)((S + 1) / 2), n_brdf = (double)(S / 2);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long p = 0; p < P; p++) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        double tp[3], bp[3], np_[3];
+        if (cache_frame(&gnrm[3 * p], tp, bp, np_)) {
+            for (int s = 0; s < S; s++) {
+                const double *us = u + ((size_t)p * S + s) * 4;
+                /* the map, by the normalised weights */
+                int q = -1;
+                double c = 0.0;
+                for (int i = 0; i < k; i++) {
+                    if (nbr_idx[p * k + i] < 0)
+                        continue;
+                    q = i;
+                    c += nbr_w[p * k + i];
+                    if (us[0] < c)
+                        break;
+                }
+                if (q < 0)
+                    continue;
+                const int j = nbr_idx[p * k + q];
+                double t[3], b[3], n[3];
+                if (!cache_frame(&cnrm[3 * j], t, b, n))
+                    continue;
+                const double *cj = cdf + (long)j * plane;
+                const double total = cj[plane - 1];
+                double w[3];
+                if (s % 2 == 0) { /* environment: texel by the CDF, direction uniform inside */
+                    if (!(total > 0.0))
+                        continue;
+                    const double target = us[1] * total;
+                    long e = 0;
+                    while (e < plane - 1 && !(cj[e] > target))
+                        e++;
+                    const int a = (int)(e / mapW), bc = (int)(e % mapW);
+                    const double c0 = cos(a * 0.5 * ORC_PI / mapH), c1 = cos((a + 1) * 0.5 * ORC_PI / mapH);
+                    const double mu = c0 - us[2] * (c0 - c1), sn = sqrt(1.0 - mu * mu > 0.0 ? 1.0 - mu * mu : 0.0);
+                    const double phi = (bc + us[3]) * 2.0 * ORC_PI / mapW;
+                    const double l[3] = {sn * cos(phi), sn * sin(phi), mu};
+                    for (int d = 0; d < 3; d++)
+                        w[d] = l[0] * t[d] + l[1] * b[d] + l[2] * n[d];
+                } else { /* BRDF: cosine-weighted about the pixel normal */
+                    const double rr = sqrt(us[1]), phi = 2.0 * ORC_PI * us[2];
+                    const double l[3] = {rr * cos(phi), rr * sin(phi), sqrt(1.0 - us[1] > 0.0 ? 1.0 - us[1] : 0.0)};
+                    for (int d = 0; d < 3; d++)
+                        w[d] = l[0] * tp[d] + l[1] * bp[d] + l[2] * np_[d];
+                }
+                const double cosp = w[0] * np_[0] + w[1] * np_[1] + w[2] * np_[2];
+                if (!(cosp > 0.0))
+                    continue;
+                int ta, tb;
+                if (!texel_of(t, b, n, w, mapH, mapW, &ta, &tb))
+                    continue; /* below the cache's hemisphere: R = 0 */
+                const double pdf_env = total > 0.0 ? texel_lum(maps, j, mapH, mapW, ta, tb) / total : 0.0;
+                const double denom = n_env * pdf_env + n_brdf * cosp / ORC_PI;
+                if (!(denom > 0.0))
+                    continue;
+                for (int d = 0; d < 3; d++) {
+                    const double R = maps[((long)j * 3 + d) * plane + (long)ta * mapW + tb];
+                    acc[d] += albedo[3 * p + d] / ORC_PI * cosp * R / denom;
+                }
+            }
+        }
+        for (int d = 0; d < 3; d++)
+            out[3 * p + d] = acc[d];
+    }
+    free(cdf);
+    return 0;
+}
+
+/* The estimator's expectation by quadrature: sum over the selected maps of
+ * weight x sum over texels of the texel radiance x (albedo / pi) x the
+ * integral of max(0, cos to the pixel normal) over the texel, taken on
+ * m x m cells of equal solid angle (midpoints in cos theta and phi). */
+int orc_indirect_expected(int n_caches, int mapH, int mapW, const float *maps, const float *cnrm, long P, int k,
+                          const int *nbr_idx, const double *nbr_w, const float *gnrm, const float *albedo, int m,
+                          double *out)
+{
+    if (n_caches < 1 || mapH < 1 || mapW < 1 || k < 1 || m < 1)
+        return -1;
+    const long plane = (long)mapH * mapW;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long p = 0; p < P; p++) {
+        double acc[3] = {0.0, 0.0, 0.0};
+        double tp[3], bp[3], np_[3];
+        if (cache_frame(&gnrm[3 * p], tp, bp, np_)) {
+            for (int i = 0; i < k; i++) {
+                const int j = nbr_idx[p * k + i];
+                if (j < 0)
+                    continue;
+                double t[3], b[3], n[3];
+                if (!cache_frame(&cnrm[3 * j], t, b, n))
+                    continue;
+                for (int a = 0; a < mapH; a++) {
+                    const double c0 = cos(a * 0.5 * ORC_PI / mapH), c1 = cos((a + 1) * 0.5 * ORC_PI / mapH);
+                    const double cell = (c0 - c1) / m * (2.0 * ORC_PI / mapW) / m;
+                    for (int bc = 0; bc < mapW; bc++) {
+                        double integ = 0.0;
+                        for (int x = 0; x < m; x++) {
+                            const double mu = c0 - (x + 0.5) * (c0 - c1) / m;
+                            const double sn = sqrt(1.0 - mu * mu);
+                            for (int y = 0; y < m; y++) {
+                                const double phi = (bc + (y + 0.5) / m) * 2.0 * ORC_PI / mapW;
+                                const double l[3] = {sn * cos(phi), sn * sin(phi), mu};
+                                double cp = 0.0;
+                                for (int d = 0; d < 3; d++)
+                                    cp += (l[0] * t[d] + l[1] * b[d] + l[2] * n[d]) * np_[d];
+                                if (cp > 0.0)
+                                    integ += cp * cell;
+                            }
+                        }
+                        for (int d = 0; d < 3; d++)
+                            acc[d] += nbr_w[p * k + i] * albedo[3 * p + d] / ORC_PI *
+                                      maps[((long)j * 3 + d) * plane + (long)a * mapW + bc] * integ;
+                    }
+                }
+            }
+        }
+        for (int d = 0; d < 3; d++)
+            out[3 * p + d] = acc[d];
     }
     return 0;
 }
