@@ -19,6 +19,8 @@ Functions (each cites the passage its C routine follows, see drc_oracle.c):
   mis_indirect            the indirect term of Eq. 3 by multiple importance
                           sampling over the blended maps and the BRDF
                           (Sec. 3.2), with indirect_expected, its expectation
+  gen_maps                the 7-channel input maps traced from cache points
+                          in an analytic interior (Sec. 3.2-3.3)
   unet_forward            the paper's own network form: a U-Net (Sec. 3.3),
                           with its parts conv3x3s1, convT3x3s1, maxpool2,
                           upsample2 and unet_param_count
@@ -81,6 +83,8 @@ def _load():
         lib.orc_mis_indirect.restype = i
         lib.orc_indirect_expected.argtypes = [i, i, i, P, P, l, i, P, P, P, P, i, P]
         lib.orc_indirect_expected.restype = i
+        lib.orc_gen_maps.argtypes = [i, P, P, i, i, P, P, P, i, P, i, P, P]
+        lib.orc_gen_maps.restype = i
         lib.orc_interp.restype = i
         lib.orc_l1_backward.argtypes = [i, P, i, i, i, d, u, P, l, P, P, i, i,
                                         i, i, P, P, P]
@@ -377,5 +381,30 @@ def indirect_expected(caches, nbr_idx, nbr_w, gnrm, albedo, m=16):
                                        _ptr(alb), int(m), _ptr(out))
     if rc:
         raise ValueError("oracle indirect_expected: bad arguments")
+    return out
+
+
+def gen_maps(pos, nrm, H, W, wall_alb, wall_em=None, light=None, spheres=(), D=3, u=None):
+    """Maps [n, 7, H, W] traced from cache points pos [n,3] (inside the unit
+    box) with normals nrm [n,3]: radiance leaving the first hit without its
+    own emission (D cosine-sampled bounces), distance, hit normal.  wall_alb,
+    wall_em: [6,3] for -x, +x, -y, +y, -z, +z; light: (x0, x1, y0, y1, Le
+    rgb) on the ceiling; spheres: rows (cx, cy, cz, r, albedo rgb); u:
+    uniforms [n, H, W, D, 2] (default zeros)."""
+    pos, nrm = _f32(pos), _f32(nrm)
+    n = pos.shape[0]
+    wa = _f64(wall_alb).reshape(6, 3)
+    we = np.zeros((6, 3)) if wall_em is None else _f64(wall_em).reshape(6, 3)
+    lt = None if light is None else _f64(light).reshape(7)
+    sp = _f64(np.asarray(spheres, dtype=np.float64).reshape(-1, 7)) if len(spheres) else np.zeros((0, 7))
+    u = np.zeros((n, H, W, max(D, 1), 2)) if u is None else _f64(u)
+    if u.shape[:3] != (n, H, W) or u.shape[3] < D or u.shape[4] != 2:
+        raise ValueError("u must be [n, H, W, D, 2]")
+    u = np.ascontiguousarray(u[:, :, :, :max(D, 1)])
+    out = np.empty((n, 7, H, W))
+    rc = _load().orc_gen_maps(n, _ptr(pos), _ptr(nrm), H, W, _ptr(wa), _ptr(we), _ptr(lt), sp.shape[0], _ptr(sp),
+                              D, _ptr(u), _ptr(out))
+    if rc:
+        raise ValueError("oracle gen_maps: points must lie inside the unit box, normals nonzero")
     return out
 

@@ -37,6 +37,9 @@
  *                     importance sampling over the blended cached maps and
  *                     the BRDF (Sec. 3.2); orc_indirect_expected, its
  *                     expectation by quadrature.
+ *   orc_gen_maps      the input maps traced from cache points in an
+ *                     analytic interior: radiance without the direct light,
+ *                     distance, normal (Sec. 3.2-3.3).
  *   orc_unet_forward  the paper's own network form (Sec. 3.3 "Neural
  *                     network"): a U-Net of two 3x3 convolutions per stage
  *                     with batch normalisation and LeakyReLU, 2x2 max
@@ -753,6 +756,160 @@ int orc_indirect_expected(int n_caches, int mapH, int mapW, const float *maps, c
             out[3 * p + d] = acc[d];
     }
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Input-map generation, a next step of this build: the maps are traced    */
+/* from the first intersection point (Sec. 3.1-3.2), radiance with the     */
+/* direct light excluded, distance and normal (Sec. 3.3's seven channels). */
+/* ------------------------------------------------------------------------ */
+/* Readings (the paper's scenes are not available):
+ *  - the scene is an interior: the unit box [0,1]^3 of six diffuse walls
+ *    (albedo and emission per wall, in the order -x, +x, -y, +y, -z, +z),
+ *    an extra emitting rectangle on the ceiling z = 1 (x in [x0, x1], y in
+ *    [y0, y1], radiance Le), and diffuse spheres (centre, radius, albedo)
+ *    seen from outside;
+ *  - texel (a, b) of a cache's map takes one ray from the cache point along
+ *    its centre direction: polar angle (a + 1/2) pi / (2H) from the cache
+ *    normal, azimuth (b + 1/2) 2 pi / W in the cache frame (the lookup's
+ *    frame rule);
+ *  - channels 3 and 4-6 are the distance to the first hit and the hit's
+ *    normal facing the ray; channels 0-2 the radiance leaving the first hit
+ *    toward the cache point without the hit's own emission (the direct
+ *    light the paper leaves out of R), from a path of D bounces: each takes
+ *    a cosine-weighted direction about the current normal (in a frame of the
+ *    same rule), adds the throughput times the next hit's emission and
+ *    multiplies the throughput by that hit's albedo, the Lambertian estimate
+ *    of one bounce; the random numbers are an input u [n][H][W][D][2]. */
+
+typedef struct {
+    const double *wall_alb, *wall_em; /* [6][3] */
+    const double *light;              /* x0 x1 y0 y1 Le[3] */
+    int nsph;
+    const double *sph; /* [nsph][7]: centre, radius, albedo[3] */
+} orc_scene;
+
+/* nearest hit of the ray o + t d (d unit, t > 0): distance, normal facing
+ * the ray, albedo and emission there; 0 when nothing is hit */
+static int scene_hit(const orc_scene *sc, const double o[3], const double d[3], double *th, double nh[3],
+                     double alb[3], double em[3])
+{
+    double best = INFINITY;
+    int which = -1; /* 0..5 wall, 6 + s sphere s */
+    for (int i = 0; i < 3; i++) {
+        if (d[i] > 0.0) {
+            const double t = (1.0 - o[i]) / d[i];
+            if (t > 1e-12 && t < best) { best = t; which = 2 * i + 1; }
+        } else if (d[i] < 0.0) {
+            const double t = -o[i] / d[i];
+            if (t > 1e-12 && t < best) { best = t; which = 2 * i; }
+        }
+    }
+    for (int s = 0; s < sc->nsph; s++) {
+        const double *sp = sc->sph + 7 * s;
+        const double oc[3] = {o[0] - sp[0], o[1] - sp[1], o[2] - sp[2]};
+        const double B = oc[0] * d[0] + oc[1] * d[1] + oc[2] * d[2];
+        const double C = oc[0] * oc[0] + oc[1] * oc[1] + oc[2] * oc[2] - sp[3] * sp[3];
+        const double disc = B * B - C;
+        if (C <= 0.0 || disc < 0.0)
+            continue; /* seen from outside only */
+        const double t = -B - sqrt(disc);
+        if (t > 1e-12 && t < best) { best = t; which = 6 + s; }
+    }
+    if (which < 0)
+        return 0;
+    *th = best;
+    const double h[3] = {o[0] + best * d[0], o[1] + best * d[1], o[2] + best * d[2]};
+    if (which < 6) {
+        const int axis = which / 2, side = which % 2;
+        nh[0] = nh[1] = nh[2] = 0.0;
+        nh[axis] = side ? -1.0 : 1.0; /* inward */
+        for (int c = 0; c < 3; c++) {
+            alb[c] = sc->wall_alb[3 * which + c];
+            em[c] = sc->wall_em[3 * which + c];
+        }
+        if (which == 5 && sc->light && h[0] >= sc->light[0] && h[0] <= sc->light[1] && h[1] >= sc->light[2] &&
+            h[1] <= sc->light[3])
+            for (int c = 0; c < 3; c++)
+                em[c] += sc->light[4 + c];
+    } else {
+        const double *sp = sc->sph + 7 * (which - 6);
+        for (int c = 0; c < 3; c++) {
+            nh[c] = (h[c] - sp[c]) / sp[3];
+            alb[c] = sp[4 + c];
+            em[c] = 0.0;
+        }
+    }
+    return 1;
+}
+
+int orc_gen_maps(int n, const float *pos, const float *nrm, int H, int W, const double *wall_alb,
+                 const double *wall_em, const double *light, int nsph, const double *sph, int D, const double *u,
+                 double *maps)
+{
+    if (n < 0 || H < 1 || W < 1 || D < 0 || nsph < 0)
+        return -1;
+    for (int j = 0; j < n; j++)
+        for (int c = 0; c < 3; c++)
+            if (!(pos[3 * j + c] > 0.0f && pos[3 * j + c] < 1.0f))
+                return -1;
+    const orc_scene sc = {wall_alb, wall_em, light, nsph, sph};
+    const long plane = (long)H * W;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int j = 0; j < n; j++) {
+        double t[3], b[3], nn[3];
+        if (!cache_frame(&nrm[3 * j], t, b, nn)) {
+            bad = 1;
+            continue;
+        }
+        const double x[3] = {pos[3 * j], pos[3 * j + 1], pos[3 * j + 2]};
+        double *out = maps + (long)j * 7 * plane;
+        for (int a = 0; a < H; a++)
+            for (int bc = 0; bc < W; bc++) {
+                const long e = (long)a * W + bc;
+                const double th = (a + 0.5) * 0.5 * ORC_PI / H, ph = (bc + 0.5) * 2.0 * ORC_PI / W;
+                const double l[3] = {sin(th) * cos(ph), sin(th) * sin(ph), cos(th)};
+                double d[3];
+                for (int c = 0; c < 3; c++)
+                    d[c] = l[0] * t[c] + l[1] * b[c] + l[2] * nn[c];
+                double dist, nh[3], alb[3], em[3];
+                for (int c = 0; c < 7; c++)
+                    out[c * plane + e] = 0.0;
+                if (!scene_hit(&sc, x, d, &dist, nh, alb, em))
+                    continue;
+                out[3 * plane + e] = dist;
+                for (int c = 0; c < 3; c++)
+                    out[(4 + c) * plane + e] = nh[c];
+                /* the path from the first hit: its emission left out */
+                double thr[3] = {alb[0], alb[1], alb[2]}, L[3] = {0.0, 0.0, 0.0};
+                double o[3] = {x[0] + dist * d[0], x[1] + dist * d[1], x[2] + dist * d[2]};
+                double nc[3] = {nh[0], nh[1], nh[2]};
+                for (int k = 0; k < D; k++) {
+                    const double *uk = u + ((((long)j * H + a) * W + bc) * D + k) * 2;
+                    const float nf[3] = {(float)nc[0], (float)nc[1], (float)nc[2]};
+                    double tt[3], bb[3], n2[3];
+                    cache_frame(nf, tt, bb, n2);
+                    const double rr = sqrt(uk[0]), phi = 2.0 * ORC_PI * uk[1];
+                    const double lz = sqrt(1.0 - uk[0] > 0.0 ? 1.0 - uk[0] : 0.0);
+                    double dn[3];
+                    for (int c = 0; c < 3; c++)
+                        dn[c] = rr * cos(phi) * tt[c] + rr * sin(phi) * bb[c] + lz * nc[c];
+                    double t2, nh2[3], alb2[3], em2[3];
+                    if (!scene_hit(&sc, o, dn, &t2, nh2, alb2, em2))
+                        break;
+                    for (int c = 0; c < 3; c++) {
+                        L[c] += thr[c] * em2[c];
+                        thr[c] *= alb2[c];
+                        o[c] = o[c] + t2 * dn[c];
+                        nc[c] = nh2[c];
+                    }
+                }
+                for (int c = 0; c < 3; c++)
+                    out[c * plane + e] = L[c];
+            }
+    }
+    return bad ? -1 : 0;
 }
 
 /* ------------------------------------------------------------------------ */
