@@ -215,3 +215,57 @@ def test_lookup_row_linear_map_pins_polar_angle():
         out = oracle.interpolate(caches, gb, 1, oracle.METRIC_WORLD, oracle.WP_INVERSE,
                                  oracle.INTERP_LOOKUP, 1.0)
         np.testing.assert_allclose(out[0], ti, rtol=0, atol=1e-9)
+
+
+def _two_cache_row(width=8):
+    """A one-row image with two caches at pixels x = 2 and x = 6 (IMAGE
+    metric), all normals +Z, payloads a = (1, 2, 4) and b = (8, 16, 32)."""
+    gb = {"width": width, "height": 1, "pos": np.zeros((width, 3), np.float32),
+          "nrm": np.tile(np.float32([0, 0, 1]), (width, 1)), "dir": None}
+    caches = {"pos": np.zeros((2, 3), np.float32), "nrm": np.tile(np.float32([0, 0, 1]), (2, 1)),
+              "pix": np.int32([[2, 0], [6, 0]]),
+              "payload": np.float32([[1, 2, 4], [8, 16, 32]]), "maps": None}
+    return gb, caches
+
+
+def test_linear_weight_inside_radius_handworked():
+    """LINEAR w_p = max(0, 1 - d/r) for d < r, worked by hand at r = 4,
+    eps = 0: pixel 3 is 1 and 3 pixels from the caches, so w_p = 3/4 and 1/4
+    and, with aligned normals (w = 2 w_p), the blend is 3/4 a + 1/4 b.
+    Pixel 4 sits half way (1/2, 1/2); pixel 2 is on cache a with b at
+    d = r (w_p = 1 and 0); pixel 7 is 5 and 1 away (0 and 3/4).
+    1 - d^2/r^2 would give 15/16 and 7/16 at pixel 3, and 1/(d + delta)
+    would give 1/(1+delta) and 1/(3+delta): neither matches."""
+    gb, caches = _two_cache_row()
+    a, b = np.float64([1, 2, 4]), np.float64([8, 16, 32])
+    expect = {0: a, 1: a, 2: a, 3: 0.75 * a + 0.25 * b, 4: 0.5 * a + 0.5 * b,
+              5: 0.25 * a + 0.75 * b, 6: b, 7: b}
+    out = oracle.interpolate(caches, gb, 2, oracle.METRIC_IMAGE, oracle.WP_LINEAR,
+                             oracle.INTERP_IRRADIANCE, 4.0, eps=0.0)
+    for x, e in expect.items():
+        np.testing.assert_allclose(out[x], e, rtol=1e-15, atol=0)
+    # the normal term on a LINEAR weight: cache b facing away (w_n = 0) keeps
+    # w = w_p, cache a aligned keeps w = 2 w_p; at pixel 3: (1.5 a + 0.25 b) / 1.75
+    caches["nrm"] = np.float32([[0, 0, 1], [0, 0, -1]])
+    out = oracle.interpolate(caches, gb, 2, oracle.METRIC_IMAGE, oracle.WP_LINEAR,
+                             oracle.INTERP_IRRADIANCE, 4.0, eps=0.0)
+    np.testing.assert_allclose(out[3], (1.5 * a + 0.25 * b) / 1.75, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(out[5], (0.5 * a + 0.75 * b) / 1.25, rtol=1e-15, atol=0)
+
+
+def test_inverse_weight_radius_factor_with_eps_handworked():
+    """INVERSE w_p = r/(d + delta_rel r): at r = 4, delta_rel = 1/4 (delta = 1)
+    pixel 3 has d = 1 and 3, so w_p = 4/2 = 2 and 4/4 = 1; aligned normals and
+    eps = 1 give w = 2 w_p + eps = 5 and 3, so the blend is (5 a + 3 b)/8.
+    Without the factor r (w_p = 1/2, 1/4) it would be (2 a + 1.5 b)/3.5, and
+    with delta = delta_rel rather than delta_rel r it would differ again, so
+    eps > 0 makes the r factor visible."""
+    gb, caches = _two_cache_row()
+    a, b = np.float64([1, 2, 4]), np.float64([8, 16, 32])
+    out = oracle.interpolate(caches, gb, 2, oracle.METRIC_IMAGE, oracle.WP_INVERSE,
+                             oracle.INTERP_IRRADIANCE, 4.0, eps=1.0, delta_rel=0.25)
+    np.testing.assert_allclose(out[3], (5 * a + 3 * b) / 8, rtol=1e-15, atol=0)
+    # pixel 4: d = 2, 2 -> equal weights; pixel 2: d = 0, 4 -> w_p = 4, 4/5,
+    # w = 9 and 2.6
+    np.testing.assert_allclose(out[4], 0.5 * (a + b), rtol=1e-15, atol=0)
+    np.testing.assert_allclose(out[2], (9 * a + 2.6 * b) / 11.6, rtol=1e-14, atol=0)
