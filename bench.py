@@ -35,8 +35,8 @@ K_NN = 16
 METRIC_NAME = "cache-point maps denoised/sec on 1 GB300"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) of the conv kernel's launches in one denoise call of
-# the 4096-map workload: ncu counters of the 2304-map case scaled by 4096/2304
-# (profiles/conv_tc_kernel_2304maps.md); None where not taken, and reset to
+# the 4096-map workload: ncu dram__bytes_read.sum + dram__bytes_write.sum of a
+# 2304-map denoise, scaled by 4096/2304; None where not taken, and reset to
 # None whenever the kernel changes after the counters were taken.
 TRAFFIC = {"fp32": 1600e6, "bf16": None}
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense ratio (tf32 : bf16)
@@ -257,11 +257,14 @@ def measure_uneven(drc, torch, dev, prec="bf16", reps=3):
             "autotuned_tile_n": tiles, "autotune_s": tune_s}
 
 
-def measure_training(drc, torch, dev, prec="bf16", batch=256, steps=10):
+def measure_training(drc, torch, dev, prec="bf16", batch=256, steps=10, recompute=True):
     """One training step = drc_backward on a batch of noisy / clean pairs of
     7 x 64 x 64 maps (clean = the analytic lobe field, noisy = Poisson(4)/4
     per texel, L1 on log radiance), widths 64/128/256/512: forward, loss and
-    the whole reverse pass (weight, bias and input-side gradients)."""
+    the whole reverse pass (weight, bias and input-side gradients).  With
+    recompute the encoder's activations are checkpointed (the decoder
+    overwrites them and the encoder runs again before its backward), as the
+    training configuration specifies; without, every activation is kept."""
     from paper_1910_02480_gb300 import synth
     widths = [64, 128, 256, 512]
     H = W = 64
@@ -271,15 +274,16 @@ def measure_training(drc, torch, dev, prec="bf16", batch=256, steps=10):
     xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev)
     td = torch.from_numpy(np.ascontiguousarray(clean, dtype=np.float32)).to(dev)
     ctx = drc.Context(widths, w, precision=prec)
+    flags = drc.BWD_L1_TARGET | (drc.BWD_RECOMPUTE_ENCODER if recompute else 0)
     for _ in range(3):
-        ctx.backward(xd, td)
+        ctx.backward(xd, td, flags=flags)
     torch.cuda.synchronize()
     ctx.read_timing()
     ctx.set_timing(True)
     a, b = _events(torch)
     a.record()
     for _ in range(steps):
-        loss, _, _ = ctx.backward(xd, td)
+        loss, _, _ = ctx.backward(xd, td, flags=flags)
     b.record()
     torch.cuda.synchronize()
     ctx.set_timing(False)
@@ -288,14 +292,15 @@ def measure_training(drc, torch, dev, prec="bf16", batch=256, steps=10):
         raise RuntimeError("device status after training steps")
     ms = a.elapsed_time(b) / steps
     macs = sum(valid_macs_per_layer(widths, H, W).values())
-    flops_step = 2.0 * macs * batch * 3  # forward + data gradients + weight gradients
+    flops_step = 2.0 * macs * batch * 3  # forward + data gradients + weight gradients (recompute not counted)
     by = {}
     for n, (cnt, t) in kt.items():
         key = n.split()[0] if n.split()[0] in ("conv", "convT", "dgrad", "wgrad", "bgrad") else n
         by[key] = by.get(key, 0.0) + t / steps
     ctx.close()
-    return {"workload": "%d noisy/clean pairs 7x%dx%d, widths %s, L1 on log radiance, %s" % (
-                batch, H, W, "/".join(map(str, widths)), prec),
+    return {"workload": "%d noisy/clean pairs 7x%dx%d, widths %s, L1 on log radiance, %s, %s" % (
+                batch, H, W, "/".join(map(str, widths)), prec,
+                "encoder activations checkpointed (recomputed)" if recompute else "all activations kept"),
             "ms_per_step": ms, "maps_per_s": batch / (ms * 1e-3), "loss": float(loss.item()),
             "approx_flops_per_step": flops_step, "achieved_tflops": flops_step / (ms * 1e-3) / 1e12,
             "kernel_ms_per_step": {k: round(v, 4) for k, v in sorted(by.items(), key=lambda kv: -kv[1])}}
@@ -307,9 +312,9 @@ def measure_training_paper(drc, torch, dev, batch=32, pool=512, steps=40):
     64/128/256 (base width 64, three downsizing steps), FP32.  Each step
     augments its pairs by one of the eight square symmetries each (seeded
     codes, an input of the step), takes the L1 loss and its gradient, and
-    applies an Adam step whose weights the context then denoises with
-    (drc_set_weights reads the head's weights back: one host round trip per
-    step).  Steps cycle through a pool of 512 synthetic pairs."""
+    applies an Adam step whose weights the context then takes from device
+    memory (drc_set_weights, no host round trip).  Steps cycle through a
+    pool of 512 synthetic pairs."""
     from paper_1910_02480_gb300 import synth
     widths = [64, 128, 256]
     H = W = 32
@@ -717,7 +722,8 @@ def main():
               lambda: {p: measure_precision(drc, torch, dev, p, den * 1e3, not args.no_autotune)
                        for p in ("bf16", "fp8") if p != args.precision})
         extra("uneven_batching", lambda: measure_uneven(drc, torch, dev))
-        extra("training", lambda: measure_training(drc, torch, dev))
+        extra("training", lambda: measure_training(drc, torch, dev, recompute=True))
+        extra("training_keep_activations", lambda: measure_training(drc, torch, dev, recompute=False))
         extra("training_paper_settings", lambda: measure_training_paper(drc, torch, dev))
         extra("paper_form_unet", lambda: measure_unet(drc, torch, dev))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -84,7 +84,12 @@ drc_status drc_create(const drc_config *cfg, const float *weights_host,
 /* Replace the weights: `weights` holds drc_weight_count() floats in host
  * memory (weights_on_device = 0; copied before return) or device memory
  * (weights_on_device = 1; read on `stream`).  Re-packs the tensor-core
- * operand tiles on `stream`. */
+ * operand tiles on `stream`.  Setting weights from device memory does not
+ * synchronise: until the next drc_denoise, drc_frame_host or plan capture
+ * (which synchronises `stream` once to copy the output head's weights to the
+ * host, where its kernel takes them as launch parameters), the head reads
+ * its weights from device memory, as drc_backward does after such an
+ * update. */
 drc_status drc_set_weights(drc_ctx *ctx, const float *weights,
                            int weights_on_device, void *stream);
 
@@ -179,8 +184,13 @@ drc_status drc_interpolate(drc_ctx *ctx, const drc_caches *caches,
  *   Argument errors return DRC_ERR_INVALID_ARG, a failed CUDA call
  *   DRC_ERR_CUDA.  Allocates no device memory (no cudaMalloc, cudaFree or
  *   allocating library routine).
- *   The first call on a device looks up the array's device address with that
- *   device current; make that first call before any stream capture.
+ *   Every call looks up the array's device address in the current context
+ *   (cudaGetSymbolAddress, a host-side lookup).  The first call in a context
+ *   may load the library's module: make it before any stream capture.
+ *   For the WORLD metric this path does not reorder the pixels spatially
+ *   (that ordering needs a scratch array as large as the G-buffer): the
+ *   result is the same, but an incoherent G-buffer is searched more slowly
+ *   than by drc_interpolate.
  *   Every call shares the one array: calls that overlap on the GPU (different
  *   streams, different host threads) race and their results are undefined;
  *   calls ordered on one stream are safe, since each call rewrites all the

@@ -73,6 +73,7 @@ struct drc_ctx {
   size_t n_scales = 0, n_bscales = 0;
   std::vector<float> h_inscale;
   std::vector<float> h_headw;  // the head's weights on the host (launch parameters of the head kernel)
+  bool headw_stale = false;    // weights were set from device memory since h_headw was filled
   size_t pack_total = 0;
   void *d_act = nullptr;
   size_t act_bytes = 0;
@@ -514,13 +515,19 @@ void fill_common(const drc_ctx *c, const Layer &L, const uint8_t *B, const uint8
 }
 
 // The head kernel takes weights of up to 64 input channels in its launch
-// parameters (constant-bank operands).
+// parameters (constant-bank operands).  Without a current host copy (weights
+// set from device memory) it stages them from device memory instead.
 void head_inline_weights(const drc_ctx *c, HeadArgs &h) {
   if (h.C <= 64 && h.C % 16 == 0 && c->h_headw.size() == (size_t)h.C * 27) {
     memcpy(h.wk, c->h_headw.data(), c->h_headw.size() * sizeof(float));
     h.inline_w = 1;
   }
 }
+
+// Inference calls bring the host copy of the head's weights up to date after
+// weights were set from device memory: one synchronisation of `st` per
+// weight update, not per call.  Never called inside a stream capture.
+drc_status refresh_head_weights(drc_ctx *c, cudaStream_t st);
 
 // Activation buffers and geometry of one launch sequence of the network over
 // N maps of H x W (for a plan, N is the class's maximum and the real count is
@@ -688,6 +695,19 @@ std::vector<int> bn_candidates(const Layer &L) {
   std::vector<int> v{L.BN};
   if (L.BN % 32 == 0 && L.BN / 2 >= 32) v.push_back(L.BN / 2);
   return v;
+}
+
+drc_status refresh_head_weights(drc_ctx *c, cudaStream_t st) {
+  if (!c->headw_stale) return DRC_OK;
+  const Layer &Lh = c->layers.back();
+  std::vector<float> h((size_t)Lh.Cin * 27);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(h.data(), c->d_wraw + Lh.w_off, h.size() * sizeof(float), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "head weights");
+  c->h_headw.swap(h);
+  c->headw_stale = false;
+  return DRC_OK;
 }
 
 }  // namespace
@@ -1191,14 +1211,16 @@ drc_status drc_set_weights(drc_ctx *c, const float *weights, int weights_on_devi
   if (e != cudaSuccess) return cuda_fail(c, e, "weight upload");
   {
     const Layer &Lh = c->layers.back();
-    c->h_headw.assign((size_t)Lh.Cin * 27, 0.f);
-    if (weights_on_device) {  // one synchronisation: the head kernel's parameters need the values
-      if ((e = cudaStreamSynchronize(st)) == cudaSuccess)
-        e = cudaMemcpy(c->h_headw.data(), c->d_wraw + Lh.w_off, c->h_headw.size() * sizeof(float),
-                       cudaMemcpyDeviceToHost);
-      if (e != cudaSuccess) return cuda_fail(c, e, "head weights");
+    if (weights_on_device) {
+      // No read-back here (a training loop sets weights from the device every
+      // step): until an inference call refreshes the host copy, the head
+      // reads its weights from device memory.
+      c->h_headw.clear();
+      c->headw_stale = true;
     } else {
+      c->h_headw.assign((size_t)Lh.Cin * 27, 0.f);
       memcpy(c->h_headw.data(), weights + Lh.w_off, c->h_headw.size() * sizeof(float));
+      c->headw_stale = false;
     }
   }
   drc_status s = pack_all(c, st);
@@ -1277,6 +1299,7 @@ drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, 
     if (!c->d_prof && cudaMalloc(&c->d_prof, pb) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "prof");
     cudaMemsetAsync(c->d_prof, 0, pb, st);
   }
+  if ((s = refresh_head_weights(c, st)) != DRC_OK) return s;
   s = run_chain(c, c->layers, c->d_pack, c->d_pack_lo, &c->modes, ch, in, out, payload, flags, st, &c->tracer,
                 prof ? c->d_prof : nullptr);
   if (s != DRC_OK) return s;
@@ -1928,6 +1951,7 @@ drc_status drc_plan_create(drc_ctx *c, const drc_size_class *classes, int n_clas
     p->chains[k].count = &p->d_slots[k].count;
     p->chains[k].slot = &p->d_slots[k];
   }
+  if (s == DRC_OK) s = refresh_head_weights(c, cs);
   if (s == DRC_OK) s = plan_capture(p, cs);
   if (cs) cudaStreamDestroy(cs);
   if (s != DRC_OK) {
@@ -1964,6 +1988,7 @@ drc_status drc_plan_launch(drc_plan *p, const int *counts, const float *const *i
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (p->weights_version != c->weights_version && (s = plan_pack(p, st)) != DRC_OK) return s;
   if (p->graph_version != c->weights_version) {
+    if ((s = refresh_head_weights(c, st)) != DRC_OK) return s;
     cudaStream_t cs = nullptr;
     cudaError_t ce = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
     if (ce != cudaSuccess) return cuda_fail(c, ce, "plan stream");

@@ -12,7 +12,6 @@
 
 #include <cstdint>
 #include <cstring>
-#include <mutex>
 
 #include "drc.h"
 #include "interp.cuh"
@@ -23,14 +22,13 @@ namespace {
 
 constexpr size_t kStaticScratchBytes = 3u << 20;  // 3 MiB
 constexpr int kStaticMaxCaches = 65536;            // fits kStaticScratchBytes for every k
-constexpr int kMaxDevices = 64;
 
 // The grid scratch.  In host code this name is only a stand-in: its device
-// address comes from cudaGetSymbolAddress, once per device.
+// address comes from cudaGetSymbolAddress, looked up on every call with the
+// caller's device current.  The lookup is a host-side table read, and it is
+// not cached: after cudaDeviceReset, or under another context on the same
+// device, the module is loaded again and the array may move.
 static __device__ __align__(256) unsigned char g_interp_scratch[kStaticScratchBytes];
-
-std::mutex g_mu;
-void *g_scratch_addr[kMaxDevices] = {};
 
 bool device_ptr_ok(const void *p, int device) {
   if (!p || (reinterpret_cast<uintptr_t>(p) & 15u)) return false;
@@ -64,7 +62,6 @@ extern "C" drc_status drc_interpolate_static(const drc_caches *caches, const drc
     cudaGetLastError();
     return DRC_ERR_CUDA;
   }
-  if (dev < 0 || dev >= kMaxDevices) return DRC_ERR_UNSUPPORTED;
   const bool world = prm->metric == DRC_METRIC_WORLD;
   const bool lookup = prm->mode == DRC_INTERP_LOOKUP;
   if (!device_ptr_ok(world ? (const void *)caches->pos : (const void *)caches->pix, dev)) return DRC_ERR_INVALID_ARG;
@@ -81,20 +78,13 @@ extern "C" drc_status drc_interpolate_static(const drc_caches *caches, const drc
     if (prm->nbr_out && !device_ptr_ok(prm->nbr_out, dev)) return DRC_ERR_INVALID_ARG;
   }
 
-  // First call on this device: look up the array's device address with the
-  // device current.
+  // The array's address in the current context.  The first call in a
+  // context may load the library's module, so make it before any stream
+  // capture.
   void *scratch = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-      void *p = nullptr;
-      if (cudaGetSymbolAddress(&p, g_interp_scratch) != cudaSuccess || !p) {
-        cudaGetLastError();
-        return DRC_ERR_CUDA;
-      }
-      g_scratch_addr[dev] = p;
-    }
-    scratch = g_scratch_addr[dev];
+  if (cudaGetSymbolAddress(&scratch, g_interp_scratch) != cudaSuccess || !scratch) {
+    cudaGetLastError();
+    return DRC_ERR_CUDA;
   }
 
   InterpArgs a;

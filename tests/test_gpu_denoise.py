@@ -88,6 +88,34 @@ def test_fp32_full_size_sampled(drc):
     assert np.all(np.isfinite(out.cpu().numpy()))
 
 
+def test_fp32_full_size_autotuned_sampled(drc):
+    """The benchmark's configuration exactly: 4096 maps of 7x32x32, widths
+    64/128/256, with the tiles and A paths drc_autotune picks for that batch
+    shape (the setting the benchmark times), and the payload; maps spread over
+    the batch -- both ends, the middle, tile boundaries -- recomputed by the
+    oracle."""
+    widths, N = [64, 128, 256], 4096
+    w = synth.he_weights(widths, seed=0)
+    g = synth.gbuffer(1920, 1080, seed=2)
+    c = synth.cache_grid(g, 64, 64)
+    x, _ = synth.hemisphere_maps(c["pos"], c["nrm"], H=32, W=32, seed=3)
+    ctx = drc.Context(widths, w, precision="fp32", max_maps=N, max_hw=32 * 32)
+    ctx.autotune(N, 32, 32)
+    tiles = [ctx.describe_layer(li) for li in range(2 * len(widths))]
+    print("autotuned (tile_n, a_path) per layer:", tiles)
+    xd = torch.from_numpy(x).cuda()
+    out, pay = ctx.denoise(xd, want_payload=True)
+    torch.cuda.synchronize()
+    assert ctx.status() == drc.OK
+    idx = np.array([0, 1, 127, 128, 1023, 2047, 2048, 3071, 4094, 4095])
+    ref = oracle.forward(w, x[idx], widths)
+    err = rel_err(out.cpu().numpy()[idx], ref)
+    print("fp32 full size autotuned sampled: max rel %.3e" % err)
+    assert err <= FP32_TOL
+    assert rel_err(pay.cpu().numpy()[idx], oracle.payload(np.expm1(ref))) <= FP32_TOL
+    assert np.all(np.isfinite(out.cpu().numpy()))
+
+
 @pytest.mark.parametrize("widths,N,H,W", [([32, 64, 128], 64, 32, 32), ([16, 32], 3, 16, 16)])
 def test_bf16_error_reported(drc, widths, N, H, W):
     w = synth.he_weights(widths, seed=0)

@@ -143,6 +143,32 @@ def test_full_size_world_sampled(drc, ctx):
         assert rel_err(out[p0:p1][ok], ref[ok]) <= FP32_TOL
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_full_size_world_fast_sampled(drc, ctx, mode):
+    """Exactly what the benchmark times: 1920x1080 G-buffer, 64x64 caches,
+    k = 16, WORLD metric, no neighbour list (the fast query), IRRADIANCE or
+    LOOKUP (32x32 maps); four row bands recomputed by the oracle, ambiguous
+    and horizon-grazing pixels excluded."""
+    g, c = _scene(1920, 1080, 64, 64, with_maps=mode == 1, H=32, W=32)
+    k = 16
+    r = synth.world_radius(4096)
+    P = 1920 * 1080
+    out = ctx.interpolate(_cuda(c), _cuda(g), k, drc.METRIC_WORLD, drc.WP_INVERSE, mode, r)
+    torch.cuda.synchronize()
+    assert ctx.status() == drc.OK
+    out = out.cpu().numpy()
+    assert np.all(np.isfinite(out))
+    for p0 in (0, 1920 * 300 + 11, 1920 * 540 + 7, P - 3072):
+        p1 = p0 + 3072
+        ref, idx, d2 = oracle.interpolate(c, g, k, drc.METRIC_WORLD, drc.WP_INVERSE, mode, r,
+                                          p_range=(p0, p1), want_neighbors=True)
+        ok = ~_ambiguous(d2, k)
+        if mode == 1:
+            ok &= _horizon_ok(c, dict(g, dir=g["dir"][p0:p1]), idx)
+        assert ok.mean() > 0.99
+        assert rel_err(out[p0:p1][ok], ref[ok]) <= FP32_TOL
+
+
 def test_interp_argument_errors(drc, ctx):
     g, c = _scene(16, 16, 4, 4)
     with pytest.raises(drc.DrcError):
