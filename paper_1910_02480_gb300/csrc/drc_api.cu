@@ -1368,7 +1368,7 @@ drc_status drc_interpolate(drc_ctx *c, const drc_caches *caches, const drc_gbuff
   // first-hit positions are not coherent in image order)
   const bool order = prm->metric == DRC_METRIC_WORLD && P > 0;
   const size_t grid_bytes = (interp_scratch_bytes(caches->n, prm->k) + 255) & ~(size_t)255;
-  const size_t need = grid_bytes + (order ? interp_order_bytes(P) : 0);
+  const size_t need = grid_bytes + (order ? interp_order_bytes(P, caches->n) : 0);
   if (need > c->iscratch_bytes) {
     if (c->d_iscratch) cudaFree(c->d_iscratch);
     c->d_iscratch = nullptr;
@@ -1402,7 +1402,7 @@ drc_status drc_interpolate(drc_ctx *c, const drc_caches *caches, const drc_gbuff
   a.out = out_rgb;
   a.nbr_out = prm->nbr_out;
   InterpScratch sc = interp_carve(c->d_iscratch, caches->n, prm->k);
-  if (order) interp_attach_order(sc, static_cast<char *>(c->d_iscratch) + grid_bytes, P);
+  if (order) interp_attach_order(sc, static_cast<char *>(c->d_iscratch) + grid_bytes, P, caches->n);
   cudaError_t e = launch_interp(a, sc, static_cast<cudaStream_t>(stream), &c->tracer);
   if (e != cudaSuccess) return cuda_fail(c, e, "interpolation launch");
   return DRC_OK;

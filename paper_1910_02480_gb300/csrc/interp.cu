@@ -5,10 +5,14 @@
 //    counting sort: bounds -> per-cell counts -> prefix sum -> scatter into a
 //    cell-ordered float4 table (x, y, z, index).
 // 2. Optionally the pixels are counting-sorted by a finer grid over the same
-//    box, so that the 32 threads of a warp query nearby points: their cell
-//    walks and their candidate lists then coincide (WORLD metric; image order
-//    is already coherent for the IMAGE metric).
-// 3. One thread per pixel visits its own cell, then the 26 neighbours nearest
+//    box (serpentine bin order), so that the 32 threads of a warp query
+//    nearby points: their candidate sets then coincide (WORLD metric; image
+//    order is already coherent for the IMAGE metric).  The sorted copy holds
+//    each pixel's position and index.
+// 3. WORLD metric with the ordering and no neighbour list: the warp-
+//    cooperative query below -- a warp gathers the caches near its 32 points
+//    into shared memory once and every lane selects from that buffer.
+//    Otherwise one thread per pixel visits its own cell, then the 26 neighbours nearest
 //    first, then further Chebyshev shells, skipping every cell whose box is
 //    farther than the current k-th distance.  The walk stops once the k-th
 //    distance is below the distance to every unvisited cell, so the
@@ -26,6 +30,8 @@
 
 #include <cfloat>
 #include <climits>
+#include <cstdio>
+#include <cstdlib>
 
 #include "interp.cuh"
 
@@ -35,14 +41,25 @@ static constexpr int METRIC_IMAGE = 0;
 static constexpr int WP_INVERSE = 0;
 static constexpr int MODE_IRRADIANCE = 0;
 
-// Caches per grid cell the grid is sized for: k/2 (at least 1).  At 4096
-// caches, k = 16, 1080p WORLD the two-walk query measured 0.609 ms with 8
-// per cell, against 0.614 (9) and 0.615 (10); 6 per cell suited the single
-// 64-bit walk, whose insertions cost three times as much.
+// Caches per grid cell the grid is sized for.  The per-thread walks: k/2 (at
+// least 1).  At 4096 caches, k = 16, 1080p WORLD the per-thread two-walk
+// query measured 0.609 ms with 8 per cell, against 0.614 (9) and 0.615 (10);
+// 6 per cell suited the single 64-bit walk, whose insertions cost three times
+// as much.  The warp-cooperative query gathers whole cells around a warp's
+// points, so finer cells gather fewer caches beyond the radius it needs.
 static inline int per_cell(int k) { return k / 2 > 1 ? k / 2 : 1; }
+// At 1080p, 4096 caches, k = 16: 1 cache per cell 0.363 ms, 2 per cell 0.400.
+static constexpr int kCoopPerCell = 1;
+// First-gather radius and near distance of the cooperative query, in units of
+// the expected distance to the (k+1)-th nearest cache at the caches' mean
+// density.  Measured at 1080p, 4096 caches, k = 16 (near 0.8): rho 1.2
+// 0.410 ms, 1.4 0.364, 1.6 0.394; near 0.6 / 0.8 / 1.0 (rho 1.4): 0.383,
+// 0.364, 0.363.
+static constexpr float kCoopRho = 1.4f, kCoopNear = 0.9f;
 
+// Sized for the finer of the two grids, so one scratch serves either query.
 int interp_max_cells(int n, int k) {
-  const int pc = per_cell(k);
+  const int pc = per_cell(k) < kCoopPerCell ? per_cell(k) : kCoopPerCell;
   return 2 * ((n + pc - 1) / pc) + 8;
 }
 
@@ -81,19 +98,23 @@ static inline long long max_fine_bins(long long P) {
 static constexpr long long kScanTile = 16 * 1024;  // bins per scan tile (SCAN_T)
 static inline size_t fine_tiles(long long mf) { return (size_t)((mf + kScanTile - 1) / kScanTile); }
 
-size_t interp_order_bytes(long long P) {
+size_t interp_order_bytes(long long P, int n) {
   const size_t mf = (size_t)max_fine_bins(P);
-  return align256(mf * sizeof(int)) + align256(fine_tiles(mf) * sizeof(int)) + align256((size_t)P * sizeof(int));
+  return align256(mf * sizeof(int)) + align256(fine_tiles(mf) * sizeof(int)) + align256((size_t)P * sizeof(float4)) +
+         align256((size_t)n * 2 * sizeof(float4));
 }
 
-void interp_attach_order(InterpScratch &s, void *base, long long P) {
+void interp_attach_order(InterpScratch &s, void *base, long long P, int n) {
   const size_t mf = (size_t)max_fine_bins(P);
   char *p = static_cast<char *>(base);
   s.fine_count = reinterpret_cast<int *>(p);
   p += align256(mf * sizeof(int));
   s.fine_tile_sum = reinterpret_cast<int *>(p);
   p += align256(fine_tiles(mf) * sizeof(int));
-  s.order = reinterpret_cast<int *>(p);
+  s.order = reinterpret_cast<float4 *>(p);
+  p += align256((size_t)P * sizeof(float4));
+  s.aux = reinterpret_cast<float4 *>(p);
+  (void)n;
   s.max_fine = (int)mf;
 }
 
@@ -117,11 +138,17 @@ __device__ __forceinline__ int cell_of(const GridHeader &g, float3 p, int3 *cc) 
   return (cz * g.dims[1] + cy) * g.dims[0] + cx;
 }
 
+// Fine cell of a point, numbered along a serpentine path (x runs reverse on
+// every other row, rows on every other plane), so consecutive bins are
+// neighbouring cells and a warp of consecutive sorted pixels stays compact.
 __device__ __forceinline__ int fine_of(const GridHeader &g, float3 p) {
-  const int cx = clampi((int)floorf((p.x - g.origin[0]) * g.fine_inv_h), 0, g.fdims[0] - 1);
-  const int cy = clampi((int)floorf((p.y - g.origin[1]) * g.fine_inv_h), 0, g.fdims[1] - 1);
+  int cx = clampi((int)floorf((p.x - g.origin[0]) * g.fine_inv_h), 0, g.fdims[0] - 1);
+  int cy = clampi((int)floorf((p.y - g.origin[1]) * g.fine_inv_h), 0, g.fdims[1] - 1);
   const int cz = clampi((int)floorf((p.z - g.origin[2]) * g.fine_inv_h), 0, g.fdims[2] - 1);
-  return (cz * g.fdims[1] + cy) * g.fdims[0] + cx;
+  if (cz & 1) cy = g.fdims[1] - 1 - cy;
+  const int row = cz * g.fdims[1] + cy;
+  if (row & 1) cx = g.fdims[0] - 1 - cx;
+  return row * g.fdims[0] + cx;
 }
 
 // Single block: bounds of the cache points, cubic cells sized for about k/2
@@ -176,7 +203,7 @@ __global__ void grid_bounds_kernel(InterpArgs a, InterpScratch s) {
         log_vol += logf(ext[d]);
       }
     }
-    const int pc = a.k / 2 > 1 ? a.k / 2 : 1;  // as per_cell()
+    const int pc = a.cell_caches > 1 ? a.cell_caches : 1;
     const float target = (float)((a.n + pc - 1) / pc);
     float h = active ? expf((log_vol - logf(target)) / (float)active) : 1.f;
     if (!(h > 0.f) || !(h < FLT_MAX)) h = 1.f;
@@ -238,6 +265,17 @@ __global__ void grid_bounds_kernel(InterpArgs a, InterpScratch s) {
     }
     g.nfine = (int)nf;
     g.fine_inv_h = (float)m / h;
+    // expected distance to the (k+1)-th nearest cache at the mean density
+    // over the occupied axes (unit-ball volume 2, pi, 4 pi / 3)
+    float rk = 0.f;
+    if (active) {
+      const float per = (float)(a.k + 1) / (float)a.n;  // of the occupied volume
+      const float ball = active == 1 ? 2.f : (active == 2 ? 3.14159265f : 4.18879020f);
+      rk = expf((logf(per / ball) + log_vol) / (float)active);
+      if (!(rk < FLT_MAX)) rk = 0.f;
+    }
+    g.coop_r0 = a.coop_rho * rk;
+    g.coop_near = a.coop_near * rk;
     *s.hdr = g;
     sg = g;
   }
@@ -395,6 +433,25 @@ __global__ void grid_scatter_kernel(InterpArgs a, InterpScratch s) {
   const int pos = atomicAdd(&s.cell_count[c], 1);
   const float3 p = cache_point(a, j);
   s.pts[pos] = make_float4(p.x, p.y, p.z, __int_as_float(j));
+  if (s.aux) {
+    float nx = __ldg(a.cnrm + 3 * j), ny = __ldg(a.cnrm + 3 * j + 1), nz = __ldg(a.cnrm + 3 * j + 2);
+    const float nl = sqrtf(nx * nx + ny * ny + nz * nz);
+    if (nl > 0.f) {
+      nx /= nl;
+      ny /= nl;
+      nz /= nl;
+    } else {
+      nx = ny = nz = 0.f;
+    }
+    float e0 = 0.f, e1 = 0.f, e2 = 0.f;
+    if (a.payload) {
+      e0 = __ldg(a.payload + 3 * j);
+      e1 = __ldg(a.payload + 3 * j + 1);
+      e2 = __ldg(a.payload + 3 * j + 2);
+    }
+    s.aux[2 * pos] = make_float4(nx, ny, nz, e0);
+    s.aux[2 * pos + 1] = make_float4(e1, e2, 0.f, 0.f);
+  }
 }
 
 // Pixel counting sort by fine cell.  Neighbouring pixels mostly share a
@@ -418,13 +475,14 @@ __global__ void pixel_scatter_kernel(InterpArgs a, InterpScratch s) {
   const unsigned live = __ballot_sync(0xffffffffu, p < P);
   if (p >= P) return;
   const GridHeader g = *s.hdr;
-  const int f = fine_of(g, query_point(a, p));
+  const float3 q = query_point(a, p);
+  const int f = fine_of(g, q);
   const unsigned peers = __match_any_sync(live, f);
   const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
   int base = 0;
   if (lane == leader) base = atomicAdd(&s.fine_count[f], __popc(peers));
   base = __shfl_sync(live, base, leader);
-  s.order[base + __popc(peers & ((1u << lane) - 1u))] = (int)p;
+  s.order[base + __popc(peers & ((1u << lane) - 1u))] = make_float4(q.x, q.y, q.z, __int_as_float((int)p));
 }
 
 // The 26 neighbours of a cell, nearest first: faces, edges, corners.
@@ -834,7 +892,7 @@ __global__ void __launch_bounds__(QUERY_THREADS, KMAX <= 16 ? (FAST && MODE == M
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long P = (long long)a.width * a.height;
   if (t >= P) return;
-  const long long p = s.order ? (long long)__ldg(s.order + t) : t;
+  const long long p = s.order ? (long long)__float_as_int(__ldg(s.order + t).w) : t;
   const GridHeader g = *s.hdr;
   const float3 q = query_point(a, p);
   if constexpr (FAST) {
@@ -871,15 +929,334 @@ __global__ void __launch_bounds__(QUERY_THREADS, KMAX <= 16 ? (FAST && MODE == M
   blend_store<KMAX, MODE>(a, p, best, found);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-cooperative query: WORLD metric, pixels in spatial order, no neighbour
+// list.  The 32 pixels of a warp are neighbours in the fine order, so they
+// share most of their candidates.  The warp gathers once, into its own
+// shared-memory buffer, every cache of the grid cells whose box lies within
+// a radius rho of the box around its 32 points; each lane then scans the
+// buffer (broadcast reads) for its k + 1 smallest keys
+//   key = (bits of d^2 with the low 8 bits cleared) | buffer index,
+// two integer min/max per slot per insertion.  The buffer holds every cache
+// within rho of each of the warp's points, so a lane whose (k+1)-th distance
+// is below rho (less a rounding margin) has its exact k + 1 nearest.  Lanes
+// further out make the warp gather a second time, out to the largest radius
+// they need, which settles them: their (k+1)-th distance can only fall.  A
+// lane whose k-th and (k+1)-th keys agree above the index bits (a tie, or a
+// near-tie within 2^-15 relative, at the cut), or a warp whose buffer would
+// overflow, takes the exact per-thread (d^2, index) walk instead, so the
+// selection is the exact one.  Gathered caches within the near distance of
+// the box go to the front of the buffer and the rest to the back, so the
+// scan meets close candidates first and later ones rarely insert.
+static constexpr int COOP_CAP = 256;  // caches per warp buffer (8-bit index in the key)
+static constexpr int COOP_WARPS = QUERY_THREADS / 32;
+static constexpr unsigned kIdxBits = 0xffu;
+
+// v as a cell coordinate in [0, dims - 1]; huge, infinite or NaN v are safe.
+__device__ __forceinline__ int cell_coord(float v, int dims) {
+  return (int)fminf(fmaxf(floorf(v), 0.f), (float)(dims - 1));
+}
+
+struct RowSet {
+  int y0, y1, z0, z1;
+};
+
+// The rows (cy, cz) of cells that can lie within rho of the box [lo, hi].
+__device__ __forceinline__ RowSet row_set(const GridHeader &g, const float (&lo)[3], const float (&hi)[3],
+                                          float rho) {
+  RowSet r;
+  r.y0 = cell_coord((lo[1] - rho - g.origin[1]) * g.inv_h, g.dims[1]);
+  r.y1 = cell_coord((hi[1] + rho - g.origin[1]) * g.inv_h, g.dims[1]);
+  r.z0 = cell_coord((lo[2] - rho - g.origin[2]) * g.inv_h, g.dims[2]);
+  r.z1 = cell_coord((hi[2] + rho - g.origin[2]) * g.inv_h, g.dims[2]);
+  return r;
+}
+
+// Cells [x0, x1] of row (cy, cz) whose box lies within rho of the box
+// [lo, hi] (x0 > x1: none; rho < 0: none).  A pure function of its
+// arguments, monotone in rho, so the cells of a smaller radius are found
+// again, and only they, when a larger gather leaves them out.
+__device__ __forceinline__ void row_cells(const GridHeader &g, const float (&lo)[3], const float (&hi)[3],
+                                          float rho, const RowSet &rs, int cy, int cz, int &x0, int &x1) {
+  x0 = 1;
+  x1 = 0;
+  if (!(rho >= 0.f) || cy < rs.y0 || cy > rs.y1 || cz < rs.z0 || cz > rs.z1) return;
+  const float by = g.origin[1] + (float)cy * g.h, bz = g.origin[2] + (float)cz * g.h;
+  const float dy = fmaxf(fmaxf(by - hi[1], lo[1] - (by + g.h)), 0.f);
+  const float dz = fmaxf(fmaxf(bz - hi[2], lo[2] - (bz + g.h)), 0.f);
+  const float rem = rho * rho - (dy * dy + dz * dz);
+  if (rem < 0.f) return;
+  const float w = sqrtf(rem);
+  x0 = cell_coord((lo[0] - w - g.origin[0]) * g.inv_h, g.dims[0]);
+  x1 = cell_coord((hi[0] + w - g.origin[0]) * g.inv_h, g.dims[0]);
+}
+
+__device__ __forceinline__ float box_d2(const float (&lo)[3], const float (&hi)[3], float4 pt) {
+  const float dx = fmaxf(fmaxf(lo[0] - pt.x, pt.x - hi[0]), 0.f);
+  const float dy = fmaxf(fmaxf(lo[1] - pt.y, pt.y - hi[1]), 0.f);
+  const float dz = fmaxf(fmaxf(lo[2] - pt.z, pt.z - hi[2]), 0.f);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// Warp-wide: appends to the warp's buffer the caches within rho_out of the
+// box [lo, hi] (box distance, squared, against rho_out^2) that an earlier
+// call with rho_in did not take (rho_in < 0: none) -- those within the near
+// distance upwards from nf, the others downwards from COOP_CAP - 1 - nb.  An
+// earlier call took the caches within rho_in of the box from the cells
+// within rho_in of it; this call reads the cells within rho_out and leaves
+// out exactly those, so the two calls together hold each cache once.  One
+// lane per row of cells: a row's selected cells are consecutive, so one
+// contiguous range of the cell-ordered table, with the earlier call's cells
+// a contiguous sub-range.  A buffer entry is (x, y, z, table slot bits).
+// False (buffer unusable) when it would overflow.
+__device__ bool coop_gather(const GridHeader &g, const InterpScratch &s, const float (&lo)[3],
+                            const float (&hi)[3], float rho_in, float rho_out, float near2, float4 *buf, int &nf,
+                            int &nb) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  const RowSet ro = row_set(g, lo, hi, rho_out);
+  const RowSet ri = row_set(g, lo, hi, rho_in);
+  const float in2 = rho_in >= 0.f ? rho_in * rho_in : -1.f, out2 = rho_out * rho_out;
+  const int ny = ro.y1 - ro.y0 + 1, nrows = ny * (ro.z1 - ro.z0 + 1);
+  for (int r0 = 0; r0 < nrows; r0 += 32) {
+    const int r = r0 + lane;
+    int e = 0, e1 = 0, i0 = 0, i1 = 0;  // table range [e, e1), the earlier call's cells [i0, i1)
+    if (r < nrows) {
+      const int cy = ro.y0 + r % ny, cz = ro.z0 + r / ny;
+      int ox0, ox1, ix0, ix1;
+      row_cells(g, lo, hi, rho_out, ro, cy, cz, ox0, ox1);
+      row_cells(g, lo, hi, rho_in, ri, cy, cz, ix0, ix1);
+      if (ox0 <= ox1) {
+        const int base = (cz * g.dims[1] + cy) * g.dims[0];
+        e = __ldg(s.cell_start + base + ox0);
+        e1 = __ldg(s.cell_start + base + ox1 + 1);
+        if (ix0 <= ix1) {
+          i0 = __ldg(s.cell_start + base + ix0);
+          i1 = __ldg(s.cell_start + base + ix1 + 1);
+        }
+      }
+    }
+    for (;;) {
+      const bool has = e < e1;
+      if (!__any_sync(0xffffffffu, has)) break;
+      float4 pt = make_float4(0.f, 0.f, 0.f, 0.f);
+      bool take = false, nr = false;
+      if (has) {
+        pt = __ldg(s.pts + e);
+        const float bd2 = box_d2(lo, hi, pt);
+        take = bd2 <= out2 && !(e >= i0 && e < i1 && bd2 <= in2);
+        nr = bd2 <= near2;
+        pt.w = __int_as_float(e);
+        ++e;
+      }
+      const unsigned mf = __ballot_sync(0xffffffffu, take && nr), mb = __ballot_sync(0xffffffffu, take && !nr);
+      if (nf + nb + __popc(mf) + __popc(mb) > COOP_CAP) return false;
+      if (take) buf[nr ? nf + __popc(mf & lt) : COOP_CAP - 1 - nb - __popc(mb & lt)] = pt;
+      nf += __popc(mf);
+      nb += __popc(mb);
+    }
+  }
+  return true;
+}
+
+// The lane's k + 1 smallest keys over buffer entries [i0, i1), four
+// candidates' keys at a time (independent arithmetic), then their insertions.
+template <int KC>
+__device__ __forceinline__ void coop_insert(unsigned (&key)[KC], unsigned kc) {
+  if (kc < key[KC - 1]) {
+#pragma unroll
+    for (int sl = KC - 1; sl > 0; --sl) key[sl] = min(key[sl], max(key[sl - 1], kc));
+    key[0] = min(key[0], kc);
+  }
+}
+__device__ __forceinline__ unsigned coop_key(const float4 *buf, int i, float3 q) {
+  return (__float_as_uint(cand_d2(q, buf[i])) & ~kIdxBits) | (unsigned)i;
+}
+template <int KC>
+__device__ __forceinline__ void coop_scan(const float4 *buf, int i0, int i1, float3 q, unsigned (&key)[KC]) {
+  int i = i0;
+  for (; i + 4 <= i1; i += 4) {
+    const unsigned k0 = coop_key(buf, i, q), k1 = coop_key(buf, i + 1, q), k2 = coop_key(buf, i + 2, q),
+                   k3 = coop_key(buf, i + 3, q);
+    coop_insert<KC>(key, k0);
+    coop_insert<KC>(key, k1);
+    coop_insert<KC>(key, k2);
+    coop_insert<KC>(key, k3);
+  }
+  for (; i < i1; ++i) coop_insert<KC>(key, coop_key(buf, i, q));
+}
+
+// An upper bound on the (k+1)-th squared distance from its key (the cleared
+// low bits set), infinite while the list is not full.
+__device__ __forceinline__ float kth_bound2(unsigned klast) {
+  return klast == ~0u ? __int_as_float(0x7f800000) : __uint_as_float(klast | kIdxBits);
+}
+
+// Whether the lane's list is exact after gathering out to rho.
+__device__ __forceinline__ bool coop_covered(unsigned klast, float rho, float rho_all, float margin) {
+  if (rho >= rho_all) return true;
+  const float c = rho - margin;
+  return c > 0.f && kth_bound2(klast) <= c * c;
+}
+
+// Normalisation (Sec. 3.2) and blend from the k nearest keys, in ascending
+// key order: w = w_p w_n + w_p + eps (Eq. 4) with the cache's unit normal
+// and payload from the cell-ordered table (IRRADIANCE), or the map lookup of
+// the generic path (LOOKUP); one reciprocal of the weight sum per pixel.
+template <int KMAX, int MODE>
+__device__ __forceinline__ void coop_blend(const InterpArgs &a, const InterpScratch &s, long long p, float3 q,
+                                           const float4 *buf, const unsigned (&key)[KMAX + 1]) {
+  const int m = KMAX - a.k;  // slot of the nearest (the (k+1)-th is slot KMAX)
+  const PixelShade px = pixel_shade<MODE>(a, p);
+  const float inl = px.nl > 0.f ? 1.f / px.nl : 0.f;
+  const float pnx = px.nx * inl, pny = px.ny * inl, pnz = px.nz * inl;
+  const bool inverse = a.wp_form == WP_INVERSE;
+  const float delta = a.delta_rel * a.r, inv_r = 1.f / a.r;
+  float wsum = 0.f, acc0 = 0.f, acc1 = 0.f, acc2 = 0.f;
+#pragma unroll
+  for (int sl = 0; sl < KMAX; ++sl) {
+    if (sl >= m && key[sl] != ~0u) {
+      const float4 pt = buf[key[sl] & kIdxBits];
+      const int e = __float_as_int(pt.w);
+      const float4 x0 = __ldg(s.aux + 2 * e);
+      const float d = sqrtf(cand_d2(q, pt));
+      const float wp = inverse ? a.r * __frcp_rn(d + delta) : fmaxf(0.f, 1.f - d * inv_r);
+      const float wn = fmaxf(0.f, x0.x * pnx + x0.y * pny + x0.z * pnz);
+      const float w = wp * wn + wp + a.eps;
+      wsum += w;
+      if constexpr (MODE == MODE_IRRADIANCE) {
+        const float4 x1 = __ldg(s.aux + 2 * e + 1);
+        acc0 += w * x0.w;
+        acc1 += w * x1.x;
+        acc2 += w * x1.y;
+      } else {
+        float3 v;
+        if (nbr_value<MODE>(a, px, __float_as_int(__ldg(s.pts + e).w), v)) {
+          acc0 += w * v.x;
+          acc1 += w * v.y;
+          acc2 += w * v.z;
+        }
+      }
+    }
+  }
+  const float iw = __frcp_rn(wsum);
+  a.out[3 * p] = acc0 * iw;
+  a.out[3 * p + 1] = acc1 * iw;
+  a.out[3 * p + 2] = acc2 * iw;
+}
+
+template <int KMAX, int MODE>
+__global__ void __launch_bounds__(QUERY_THREADS, KMAX <= 16 ? 4 : 2) interp_coop_kernel(InterpArgs a, InterpScratch s) {
+  constexpr int KC = KMAX + 1;
+  __shared__ float4 sbuf[COOP_WARPS * COOP_CAP];
+  float4 *buf = sbuf + (threadIdx.x >> 5) * COOP_CAP;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long P = (long long)a.width * a.height;
+  const bool live = t < P;
+  if (!__any_sync(0xffffffffu, live)) return;  // warp-uniform
+  const GridHeader g = *s.hdr;
+  const int k = a.k;
+  const float4 o = live ? __ldg(s.order + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float3 q = make_float3(o.x, o.y, o.z);
+  const long long p = live ? (long long)__float_as_int(o.w) : 0;
+  float lo[3] = {live ? q.x : FLT_MAX, live ? q.y : FLT_MAX, live ? q.z : FLT_MAX};
+  float hi[3] = {live ? q.x : -FLT_MAX, live ? q.y : -FLT_MAX, live ? q.z : -FLT_MAX};
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+      lo[d] = fminf(lo[d], __shfl_xor_sync(0xffffffffu, lo[d], sh));
+      hi[d] = fmaxf(hi[d], __shfl_xor_sync(0xffffffffu, hi[d], sh));
+    }
+  const float margin = 1e-3f * g.h;
+  // gathering as far as the grid reaches from the box takes every cache
+  float far2 = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float e = fmaxf(fmaxf(g.origin[d] + (float)g.dims[d] * g.h - lo[d], hi[d] - g.origin[d]), 0.f);
+    far2 += e * e;
+  }
+  const float rho_all = sqrtf(far2) + 2.f * margin;
+  const float near2 = g.coop_near * g.coop_near;
+  unsigned key[KC];
+#pragma unroll
+  for (int sl = 0; sl < KC; ++sl) key[sl] = sl < KC - (k + 1) ? 0u : ~0u;
+  int nf = 0, nb = 0;
+  const float rho = fminf(g.coop_r0, rho_all);
+  const bool ok = coop_gather(g, s, lo, hi, -1.f, rho, near2, buf, nf, nb);
+  __syncwarp();
+  bool covered = false;
+  if (ok) {
+    if (live) {
+      coop_scan<KC>(buf, 0, nf, q, key);
+      coop_scan<KC>(buf, COOP_CAP - nb, COOP_CAP, q, key);
+    }
+    covered = coop_covered(key[KC - 1], rho, rho_all, margin);
+    const bool need = live && !covered;
+    if (__any_sync(0xffffffffu, need)) {
+      // the largest radius a lane still needs, then the caches out to it
+      float rn = 0.f;
+      if (need) rn = key[KC - 1] == ~0u ? rho_all : sqrtf(kth_bound2(key[KC - 1])) + 2.f * margin;
+#pragma unroll
+      for (int sh = 16; sh > 0; sh >>= 1) rn = fmaxf(rn, __shfl_xor_sync(0xffffffffu, rn, sh));
+      const float rho1 = fminf(rn, rho_all);
+      const int nf0 = nf, nb0 = nb;
+      const bool ok2 = coop_gather(g, s, lo, hi, rho, rho1, near2, buf, nf, nb);
+      __syncwarp();
+      if (ok2 && need) {
+        coop_scan<KC>(buf, nf0, nf, q, key);
+        coop_scan<KC>(buf, COOP_CAP - nb, COOP_CAP - nb0, q, key);
+        covered = coop_covered(key[KC - 1], rho1, rho_all, margin);
+      }
+    }
+  }
+  // a tie or near-tie at the cut: the exact walk orders it by (d^2, index)
+  const bool tie = key[KC - 1] != ~0u && ((key[KC - 2] ^ key[KC - 1]) & ~kIdxBits) == 0u;
+  if (!live) return;
+  if (ok && covered && !tie) {
+    coop_blend<KMAX, MODE>(a, s, p, q, buf, key);
+    return;
+  }
+  Best<KMAX> best;
+  best.init(k);
+  const int found = knn_walk(g, s, k, q, best);
+  blend_store<KMAX, MODE>(a, p, best, found);
+}
+
+// The cooperative query needs the pixel order (coherent warps); without it
+// (no order scratch) the WORLD metric takes the per-thread two-walk query.
+static inline bool use_coop(const InterpArgs &a, const InterpScratch &s) {
+  return a.metric != METRIC_IMAGE && a.nbr_out == nullptr && s.order != nullptr;
+}
+
 template <int KMAX, int MODE>
 static void launch_query(const InterpArgs &a, const InterpScratch &s, unsigned blocks, cudaStream_t st) {
-  if (a.metric != METRIC_IMAGE && a.nbr_out == nullptr)
+  if (use_coop(a, s))
+    interp_coop_kernel<KMAX, MODE><<<blocks, QUERY_THREADS, 0, st>>>(a, s);
+  else if (a.metric != METRIC_IMAGE && a.nbr_out == nullptr)
     interp_query_kernel<KMAX, MODE, true><<<blocks, QUERY_THREADS, 0, st>>>(a, s);
   else
     interp_query_kernel<KMAX, MODE, false><<<blocks, QUERY_THREADS, 0, st>>>(a, s);
 }
 
-cudaError_t launch_interp(const InterpArgs &a, const InterpScratch &s, cudaStream_t st, Tracer *tr) {
+cudaError_t launch_interp(const InterpArgs &a_in, const InterpScratch &s, cudaStream_t st, Tracer *tr) {
+  InterpArgs a = a_in;
+  a.cell_caches = use_coop(a, s) ? kCoopPerCell : per_cell(a.k);
+  a.coop_rho = kCoopRho;
+  a.coop_near = kCoopNear;
+  // Tuning knob for measurements: DRC_INTERP_COOP="caches_per_cell,rho,near"
+  // overrides the cooperative query's grid and radii (same results).
+  if (use_coop(a, s)) {
+    if (const char *e = std::getenv("DRC_INTERP_COOP")) {
+      int pc = 0;
+      float rho = 0.f, nr = 0.f;
+      if (sscanf(e, "%d,%f,%f", &pc, &rho, &nr) == 3 && pc >= 1 && rho > 0.f && nr >= 0.f) {
+        a.cell_caches = pc < kCoopPerCell ? pc : kCoopPerCell;  // the scratch is sized for kCoopPerCell
+        a.coop_rho = rho;
+        a.coop_near = nr;
+      }
+    }
+  }
   DRC_TRACED(tr, "interp grid_bounds", st, (grid_bounds_kernel<<<1, 1024, 0, st>>>(a, s)));
   const int cb = (a.n + 255) / 256;
   DRC_TRACED(tr, "interp grid_count", st, (grid_count_kernel<<<cb, 256, 0, st>>>(a, s)));

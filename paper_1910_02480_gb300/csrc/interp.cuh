@@ -12,12 +12,15 @@ namespace drc {
 
 struct GridHeader {
   float origin[3];
-  float h, inv_h;      // coarse cells (about k/2 caches each)
+  float h, inv_h;      // coarse cells (InterpArgs::cell_caches caches each)
   int dims[3];
   int ncells;
   float fine_inv_h;    // fine cells for ordering the pixels (about 32 pixels each)
   int fdims[3];
   int nfine;
+  // warp-cooperative query: the radius of the first gather around a warp's
+  // points and the distance within which a gathered cache is scanned first
+  float coop_r0, coop_near;
 };
 
 // Device scratch used by one interpolation call.
@@ -31,8 +34,12 @@ struct InterpScratch {
   // optional pixel ordering (nullptr: pixels are processed in index order)
   int *fine_count;     // [max_fine] counts, then cursors
   int *fine_tile_sum;  // [max_fine / 16384, rounded up] per-tile totals of the counts
-  int *order;        // [P] pixel indices sorted by fine cell
+  float4 *order;       // [P] (x, y, z, pixel index bits) sorted by fine cell
   int max_fine;
+  // with the ordering: per cache, in the cell order of pts, the unit normal
+  // (0 for a zero-length one) and the payload: aux[2 e] = (nx, ny, nz, E0),
+  // aux[2 e + 1] = (E1, E2, 0, 0); read by the warp-cooperative blend
+  float4 *aux;
 };
 
 // Grid scratch for n caches (no pixel ordering).
@@ -41,8 +48,8 @@ int interp_max_cells(int n, int k);
 InterpScratch interp_carve(void *base, int n, int k);
 // Extra scratch that orders P pixels spatially before the search (same
 // results, better warp coherence); attach to a carved InterpScratch.
-size_t interp_order_bytes(long long P);
-void interp_attach_order(InterpScratch &s, void *base, long long P);
+size_t interp_order_bytes(long long P, int n);
+void interp_attach_order(InterpScratch &s, void *base, long long P, int n);
 
 struct InterpArgs {
   int n, mapH, mapW;
@@ -54,6 +61,11 @@ struct InterpArgs {
   float r, eps, delta_rel;
   float *out;
   int *nbr_out;
+  // set by launch_interp: caches per grid cell the grid is sized for, and
+  // the cooperative query's first-gather radius and near distance, in units
+  // of the expected distance to the (k+1)-th nearest cache
+  int cell_caches;
+  float coop_rho, coop_near;
 };
 
 // tr: nullable launch tracer (counts and optionally times each kernel).

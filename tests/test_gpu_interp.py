@@ -256,6 +256,58 @@ def test_world_without_neighbour_list(drc, ctx, k, mode):
     np.testing.assert_allclose(fast[ok], exact[ok], rtol=1e-5, atol=1e-6)
 
 
+def _coop_case(name, seed=21):
+    """Cache layouts that drive the warp-cooperative query's edge paths."""
+    rng = np.random.default_rng(seed)
+    if name == "few_caches":  # fewer caches than k + 1: every warp gathers the whole grid
+        g = synth.gbuffer(40, 30, seed=seed)
+        pos = rng.uniform(0.2, 0.8, size=(5, 3)).astype(np.float32)
+    elif name == "one_point":  # every cache at one point: buffer overflow, exact walk, ties by index
+        g = synth.gbuffer(48, 40, seed=seed)
+        pos = np.tile(np.float32([[0.4, 0.55, 0.3]]), (600, 1))
+    elif name == "coplanar":  # caches on a plane, pixels all around it: a 2-D grid, 3-D queries
+        g = synth.gbuffer(64, 48, seed=seed)
+        pos = rng.uniform(0.0, 1.0, size=(300, 3)).astype(np.float32)
+        pos[:, 2] = 0.5
+    elif name == "clustered":  # half the caches in a small ball: densities far from the mean
+        g = synth.gbuffer(96, 64, seed=seed)
+        pos = rng.uniform(0.0, 1.0, size=(400, 3))
+        pos[:200] = 0.3 + 0.03 * rng.normal(size=(200, 3))
+        pos = pos.astype(np.float32)
+    else:  # "ragged": a pixel count that is not a multiple of a warp, uniform caches
+        g = synth.gbuffer(37, 29, seed=seed)
+        pos = rng.uniform(0.0, 1.0, size=(250, 3)).astype(np.float32)
+    n = len(pos)
+    nrm = rng.normal(size=(n, 3))
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    c = {"pos": pos, "nrm": nrm.astype(np.float32), "pix": np.zeros((n, 2), np.int32),
+         "payload": rng.uniform(0.0, 2.0, size=(n, 3)).astype(np.float32)}
+    return g, c
+
+
+@pytest.mark.parametrize("name", ["few_caches", "one_point", "coplanar", "clustered", "ragged"])
+@pytest.mark.parametrize("k", [4, 16, 32])
+def test_cooperative_query_edge_layouts(drc, ctx, name, k):
+    """The WORLD query without a neighbour list (warp-cooperative gathers,
+    second gathers, overflow and tie fallbacks) against the oracle on cache
+    layouts far from the uniform benchmark scene."""
+    g, c = _coop_case(name)
+    n = len(c["pos"])
+    r = synth.world_radius(n)
+    out = ctx.interpolate(_cuda(c), _cuda(g), k, drc.METRIC_WORLD, drc.WP_INVERSE, drc.INTERP_IRRADIANCE, r)
+    torch.cuda.synchronize()
+    assert ctx.status() == drc.OK
+    out = out.cpu().numpy()
+    ref, idx, d2 = oracle.interpolate(c, g, k, drc.METRIC_WORLD, drc.WP_INVERSE, drc.INTERP_IRRADIANCE, r,
+                                      want_neighbors=True)
+    if name in ("few_caches", "one_point"):
+        ok = np.ones(len(out), bool)  # every cache taken, or all tied: (d^2, index) decides on both sides
+    else:
+        ok = ~_ambiguous(d2, k)
+        assert ok.mean() > 0.98
+    assert rel_err(out[ok], ref[ok]) <= FP32_TOL
+
+
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("k", [4, 5, 9, 16])
 def test_world_ties_at_kth_distance(drc, ctx, k, mode):
