@@ -154,7 +154,11 @@ typedef struct {
   float eps;      /* the small term of Eq. 4, >= 0 (1e-6 typical) */
   float delta_rel;/* INVERSE softening, delta = delta_rel * r, > 0 */
   int *nbr_out;   /* nullable; device [P][k] int32, the chosen cache indices
-                     in (d^2, index) order -- a diagnostic output */
+                     in (d^2, index) order (-1 past the number of caches) */
+  float *nbr_w;   /* nullable (needs nbr_out); device [P][k] float32, the
+                     normalised weights W_j of those caches (0 past the number
+                     of caches): the map-choice probabilities drc_indirect
+                     samples with */
 } drc_interp_params;
 
 /* Interpolate cached values at every pixel (Sec. 3.2).  For each pixel: the
@@ -198,6 +202,43 @@ drc_status drc_interpolate(drc_ctx *ctx, const drc_caches *caches,
 drc_status drc_interpolate_static(const drc_caches *caches, const drc_gbuffer *gbuf,
                                   const drc_interp_params *params, float *out_rgb,
                                   void *stream);
+
+/* The indirect term of Eq. 3 at every pixel, by multiple importance
+ * sampling (Sec. 3.2): R, the blend of the pixel's k caches' maps by their
+ * normalised weights, is sampled as an environment map with perfect
+ * visibility for even samples s and the BRDF (Lambertian, f_r = albedo / pi,
+ * cosine-weighted about the pixel normal) for odd s; each sample first
+ * draws one of the k maps with probability W_j, and contributes
+ * f_r cos R / (n_env pdf_env + n_brdf pdf_brdf) (balance heuristic, sample
+ * counts n_env = ceil(S/2), n_brdf = floor(S/2)).  Environment sampling
+ * takes a texel with probability proportional to its luminance
+ * (0.2126 R + 0.7152 G + 0.0722 B) times its solid angle, then a direction
+ * uniform in solid angle inside it.  Texel (a, b) of a map covers polar
+ * angles [a, a+1) pi/2H from the cache normal and azimuths [b, b+1) 2 pi/W in
+ * the cache frame of drc_interpolate's LOOKUP mode.
+ *   out = emit + direct + the estimate (Eq. 3: L_e, the direct-light integral
+ *   of the renderer's own pass, and the indirect integral over R).
+ * caches: n, H (<= 256), W, maps (device [n][3][H][W] LINEAR radiance, e.g.
+ * drc_denoise with DRC_F_DECODE_OUTPUT) and nrm (device [n][3]).  gbuf:
+ * width, height, nrm (device [P][3]).  out_rgb: device [P][3].  Uniforms and
+ * neighbours are inputs, so a call is deterministic.  The context keeps the
+ * maps' CDFs and frames in its own device memory (grown on demand).
+ * INVALID_ARG for k outside 1..32, S outside 1..4096, H > 256, host or
+ * unaligned pointers; asynchronous on `stream`. */
+typedef struct {
+  int k;                /* neighbours per pixel, 1..32 */
+  const int *nbr;       /* device [P][k] cache indices, -1 for none */
+  const float *nbr_w;   /* device [P][k] normalised weights (sum 1 over the valid ones) */
+  int S;                /* samples per pixel */
+  const float *u;       /* device [P][S][4] uniforms in [0, 1): the map choice, then
+                           three for the direction; 16-byte aligned */
+  const float *albedo;  /* device [P][3] */
+  const float *emit;    /* nullable device [P][3]: L_e */
+  const float *direct;  /* nullable device [P][3]: the direct-light term */
+} drc_indirect_params;
+
+drc_status drc_indirect(drc_ctx *ctx, const drc_caches *caches, const drc_gbuffer *gbuf,
+                        const drc_indirect_params *params, float *out_rgb, void *stream);
 
 /* One frame end to end from host memory: drc_denoise of N maps, then
  * drc_interpolate (IRRADIANCE) of a G-buffer from their payloads, with the

@@ -79,7 +79,7 @@ def _load():
         lib.orc_payload.argtypes = [P, i, i, i, i, P]
         lib.orc_interp.argtypes = [i, i, i, P, P, P, P, P, i, i, P, P, P,
                                    i, i, i, i, d, d, d, l, l, P, P, P, P]
-        lib.orc_mis_indirect.argtypes = [i, i, i, P, P, l, i, P, P, P, P, i, P, P]
+        lib.orc_mis_indirect.argtypes = [i, i, i, P, P, l, i, P, P, P, P, i, P, P, P]
         lib.orc_mis_indirect.restype = i
         lib.orc_indirect_expected.argtypes = [i, i, i, P, P, l, i, P, P, P, P, i, P]
         lib.orc_indirect_expected.restype = i
@@ -356,21 +356,25 @@ def _mis_args(caches, nbr_idx, nbr_w, gnrm, albedo):
     return maps, n, H, W, _f32(caches["nrm"]), idx, P, k, w, _f32(gnrm), _f32(albedo)
 
 
-def mis_indirect(caches, nbr_idx, nbr_w, gnrm, albedo, u):
+def mis_indirect(caches, nbr_idx, nbr_w, gnrm, albedo, u, want_margin=False):
     """The indirect term at P pixels: caches 'maps' [n,3,H,W] (linear
     radiance) and 'nrm'; the pixels' k caches and normalised weights
     [P,k]; pixel normals and albedos [P,3]; uniforms u [P,S,4].  Readings
-    in drc_oracle.c.  Returns [P,3]."""
+    in drc_oracle.c.  Returns [P,3], and with want_margin also [P]: per
+    pixel the smallest distance of a sample's discrete decision (map,
+    texel, hemisphere, frame) from where it changes, so that a float
+    evaluation is compared only where it must take the same decisions."""
     maps, n, H, W, cnrm, idx, P, k, w, gn, alb = _mis_args(caches, nbr_idx, nbr_w, gnrm, albedo)
     u = _f64(u)
     if u.shape[0] != P or u.shape[2] != 4:
         raise ValueError("u must be [P, S, 4]")
     out = np.empty((P, 3))
+    margin = np.empty(P) if want_margin else None
     rc = _load().orc_mis_indirect(n, H, W, _ptr(maps), _ptr(cnrm), P, k, _ptr(idx), _ptr(w), _ptr(gn), _ptr(alb),
-                                  u.shape[1], _ptr(u), _ptr(out))
+                                  u.shape[1], _ptr(u), _ptr(out), _ptr(margin))
     if rc:
         raise ValueError("oracle mis_indirect: bad arguments")
-    return out
+    return (out, margin) if want_margin else out
 
 
 def indirect_expected(caches, nbr_idx, nbr_w, gnrm, albedo, m=16):

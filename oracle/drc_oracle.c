@@ -625,9 +625,36 @@ static double *env_cdfs(int n_caches, int H, int W, const float *maps)
     return cdf;
 }
 
+/* margin (nullable, [P]): for the comparison with a float evaluation, the
+ * smallest distance, over the pixel's samples, of a value that takes a
+ * discrete decision from the boundary where that decision changes: the map
+ * choice (u0 against the running weight sums), the environment texel
+ * (target against the CDF, relative to its total), the texel a direction
+ * falls in (polar and azimuthal texel coordinates against integers), the
+ * hemisphere tests (cosines against 0) and the up-vector switch of the
+ * frames (|n_z| against 1 - 1e-6).  The estimate does not depend on it. */
+static void margin_min(double *m, double v)
+{
+    v = fabs(v);
+    if (v < *m)
+        *m = v;
+}
+
+static double frac_dist(double x)
+{
+    return fabs(x - floor(x + 0.5));
+}
+
+static double frame_margin(const float *nrm)
+{
+    double nx = nrm[0], ny = nrm[1], nz = nrm[2];
+    double len = sqrt(nx * nx + ny * ny + nz * nz);
+    return len > 0.0 ? fabs(fabs(nz / len) - (1.0 - 1e-6)) : 1.0;
+}
+
 int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const float *cnrm, long P, int k,
                      const int *nbr_idx, const double *nbr_w, const float *gnrm, const float *albedo, int S,
-                     const double *u, double *out)
+                     const double *u, double *out, double *margin)
 {
     if (n_caches < 1 || mapH < 1 || mapW < 1 || k < 1 || S < 1)
         return -1;
@@ -638,6 +665,7 @@ int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const 
     for (long p = 0; p < P; p++) {
         double acc[3] = {0.0, 0.0, 0.0};
         double tp[3], bp[3], np_[3];
+        double mg = frame_margin(&gnrm[3 * p]);
         if (cache_frame(&gnrm[3 * p], tp, bp, np_)) {
             for (int s = 0; s < S; s++) {
                 const double *us = u + ((size_t)p * S + s) * 4;
@@ -649,6 +677,7 @@ int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const 
                         continue;
                     q = i;
                     c += nbr_w[p * k + i];
+                    margin_min(&mg, us[0] - c);
                     if (us[0] < c)
                         break;
                 }
@@ -656,6 +685,7 @@ int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const 
                     continue;
                 const int j = nbr_idx[p * k + q];
                 double t[3], b[3], n[3];
+                margin_min(&mg, frame_margin(&cnrm[3 * j]));
                 if (!cache_frame(&cnrm[3 * j], t, b, n))
                     continue;
                 const double *cj = cdf + (long)j * plane;
@@ -668,6 +698,9 @@ int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const 
                     long e = 0;
                     while (e < plane - 1 && !(cj[e] > target))
                         e++;
+                    margin_min(&mg, (cj[e] - target) / total);
+                    if (e > 0)
+                        margin_min(&mg, (target - cj[e - 1]) / total);
                     const int a = (int)(e / mapW), bc = (int)(e % mapW);
                     const double c0 = cos(a * 0.5 * ORC_PI / mapH), c1 = cos((a + 1) * 0.5 * ORC_PI / mapH);
                     const double mu = c0 - us[2] * (c0 - c1), sn = sqrt(1.0 - mu * mu > 0.0 ? 1.0 - mu * mu : 0.0);
@@ -682,8 +715,23 @@ int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const 
                         w[d] = l[0] * tp[d] + l[1] * bp[d] + l[2] * np_[d];
                 }
                 const double cosp = w[0] * np_[0] + w[1] * np_[1] + w[2] * np_[2];
+                margin_min(&mg, cosp);
                 if (!(cosp > 0.0))
                     continue;
+                {
+                    const double lx = w[0] * t[0] + w[1] * t[1] + w[2] * t[2];
+                    const double ly = w[0] * b[0] + w[1] * b[1] + w[2] * b[2];
+                    const double lz = w[0] * n[0] + w[1] * n[1] + w[2] * n[2];
+                    margin_min(&mg, lz);
+                    if (lz > 0.0) {
+                        const double th = acos(lz > 1.0 ? 1.0 : lz);
+                        double ph = atan2(ly, lx);
+                        if (ph < 0.0)
+                            ph += 2.0 * ORC_PI;
+                        margin_min(&mg, frac_dist(th / (0.5 * ORC_PI) * mapH));
+                        margin_min(&mg, frac_dist(ph / (2.0 * ORC_PI) * mapW));
+                    }
+                }
                 int ta, tb;
                 if (!texel_of(t, b, n, w, mapH, mapW, &ta, &tb))
                     continue; /* below the cache's hemisphere: R = 0 */
@@ -699,6 +747,8 @@ int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const 
         }
         for (int d = 0; d < 3; d++)
             out[3 * p + d] = acc[d];
+        if (margin)
+            margin[p] = mg;
     }
     free(cdf);
     return 0;

@@ -67,7 +67,13 @@ class KernelTime(ctypes.Structure):
 class InterpParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("metric", ctypes.c_int), ("wp_form", ctypes.c_int),
                 ("mode", ctypes.c_int), ("r", ctypes.c_float), ("eps", ctypes.c_float),
-                ("delta_rel", ctypes.c_float), ("nbr_out", ctypes.c_void_p)]
+                ("delta_rel", ctypes.c_float), ("nbr_out", ctypes.c_void_p), ("nbr_w", ctypes.c_void_p)]
+
+
+class IndirectParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("nbr", ctypes.c_void_p), ("nbr_w", ctypes.c_void_p), ("S", ctypes.c_int),
+                ("u", ctypes.c_void_p), ("albedo", ctypes.c_void_p), ("emit", ctypes.c_void_p),
+                ("direct", ctypes.c_void_p)]
 
 
 _lib = None
@@ -99,6 +105,9 @@ def load_library():
     lib.drc_interpolate_static.argtypes = [ctypes.POINTER(Caches), ctypes.POINTER(GBuffer),
                                            ctypes.POINTER(InterpParams), P, P]
     lib.drc_interpolate_static.restype = I
+    lib.drc_indirect.argtypes = [P, ctypes.POINTER(Caches), ctypes.POINTER(GBuffer), ctypes.POINTER(IndirectParams),
+                                 P, P]
+    lib.drc_indirect.restype = I
     lib.drc_backward.argtypes = [P, P, P, I, I, I, U, P, P, P, P]
     lib.drc_backward.restype = I
     lib.drc_frame_host.argtypes = [P, P, I, I, I, U, ctypes.POINTER(Caches), ctypes.POINTER(GBuffer),
@@ -247,8 +256,10 @@ class Context:
         return (out, payload) if (payload is not None) else out
 
     def interpolate(self, caches, gbuf, k, metric, wp_form, mode, r, eps=1e-6, delta_rel=1e-3,
-                    out=None, nbr_out=None, stream=None):
-        """caches / gbuf: dicts of cuda tensors (see drc.h)."""
+                    out=None, nbr_out=None, nbr_w=None, stream=None):
+        """caches / gbuf: dicts of cuda tensors (see drc.h).  nbr_out [P,k]
+        int32 and nbr_w [P,k] float32 (which needs nbr_out) receive the
+        chosen caches and their normalised weights."""
         import torch
         c = Caches()
         c.n = int(caches["nrm"].shape[0])
@@ -269,6 +280,7 @@ class Context:
         p.k, p.metric, p.wp_form, p.mode = int(k), int(metric), int(wp_form), int(mode)
         p.r, p.eps, p.delta_rel = float(r), float(eps), float(delta_rel)
         p.nbr_out = _ptr(nbr_out)
+        p.nbr_w = _ptr(nbr_w)
         P = g.width * g.height
         if out is None:
             dev = caches["nrm"].device
@@ -276,6 +288,33 @@ class Context:
         rc = self._lib.drc_interpolate(self._ctx, ctypes.byref(c), ctypes.byref(g), ctypes.byref(p),
                                        _ptr(out), _stream(stream))
         self._check(rc, "drc_interpolate")
+        return out
+
+    def indirect(self, maps, cache_nrm, gnrm, width, height, nbr, nbr_w, u, albedo, emit=None, direct=None,
+                 out=None, stream=None):
+        """drc_indirect: the indirect term of Eq. 3 by multiple importance
+        sampling, plus emit and direct when given.  maps [n,3,H,W] linear
+        radiance, cache_nrm [n,3], gnrm [P,3], nbr [P,k] int32, nbr_w [P,k],
+        u [P,S,4], albedo / emit / direct [P,3]; all cuda float32."""
+        import torch
+        c = Caches()
+        c.n = int(maps.shape[0])
+        c.H, c.W = int(maps.shape[2]), int(maps.shape[3])
+        c.maps = _ptr(maps)
+        c.nrm = _ptr(cache_nrm)
+        g = GBuffer()
+        g.width, g.height = int(width), int(height)
+        g.nrm = _ptr(gnrm)
+        p = IndirectParams()
+        p.k = int(nbr.shape[1])
+        p.nbr, p.nbr_w = _ptr(nbr), _ptr(nbr_w)
+        p.S = int(u.shape[1])
+        p.u, p.albedo, p.emit, p.direct = _ptr(u), _ptr(albedo), _ptr(emit), _ptr(direct)
+        if out is None:
+            out = torch.empty((g.width * g.height, 3), dtype=torch.float32, device=maps.device)
+        rc = self._lib.drc_indirect(self._ctx, ctypes.byref(c), ctypes.byref(g), ctypes.byref(p), _ptr(out),
+                                    _stream(stream))
+        self._check(rc, "drc_indirect")
         return out
 
     def frame_host(self, maps_host, caches, gbuf_host, k, metric, wp_form, r, rgb_host=None, flags=0, eps=1e-6,

@@ -18,6 +18,7 @@
 #include "drc.h"
 #include "head.cuh"
 #include "drc_status.cuh"
+#include "indirect.cuh"
 #include "interp.cuh"
 #include "trace.cuh"
 #include "train.cuh"
@@ -79,6 +80,8 @@ struct drc_ctx {
   size_t act_bytes = 0;
   void *d_iscratch = nullptr;
   size_t iscratch_bytes = 0;
+  void *d_indscratch = nullptr;  // drc_indirect: per-map CDFs and frames
+  size_t indscratch_bytes = 0;
   int *d_status = nullptr;
   unsigned long long *d_prof = nullptr;  // wait-time counters (DRC_PROFILE_WAITS)
   bool weights_set = false;
@@ -1246,6 +1249,7 @@ drc_status drc_destroy(drc_ctx *c) {
   cudaFree(c->d_amax);
   cudaFree(c->d_act);
   cudaFree(c->d_iscratch);
+  cudaFree(c->d_indscratch);
   cudaFree(c->d_status);
   cudaFree(c->d_prof);
   cudaFree(c->d_fmaps);
@@ -1363,6 +1367,8 @@ drc_status drc_interpolate(drc_ctx *c, const drc_caches *caches, const drc_gbuff
     if (prm->metric == DRC_METRIC_WORLD && (s = check_dev(c, gbuf->pos, "gbuf->pos", false)) != DRC_OK) return s;
     if (prm->mode == DRC_INTERP_LOOKUP && (s = check_dev(c, gbuf->dir, "gbuf->dir", false)) != DRC_OK) return s;
     if ((s = check_dev(c, prm->nbr_out, "nbr_out", true)) != DRC_OK) return s;
+    if ((s = check_dev(c, prm->nbr_w, "nbr_w", true)) != DRC_OK) return s;
+    if (prm->nbr_w && !prm->nbr_out) return fail(c, DRC_ERR_INVALID_ARG, "nbr_w needs nbr_out");
   }
   // grid scratch, plus the pixel ordering for the WORLD metric (the G-buffer's
   // first-hit positions are not coherent in image order)
@@ -1401,10 +1407,81 @@ drc_status drc_interpolate(drc_ctx *c, const drc_caches *caches, const drc_gbuff
   a.delta_rel = prm->delta_rel;
   a.out = out_rgb;
   a.nbr_out = prm->nbr_out;
+  a.nbr_w = prm->nbr_w;
   InterpScratch sc = interp_carve(c->d_iscratch, caches->n, prm->k);
   if (order) interp_attach_order(sc, static_cast<char *>(c->d_iscratch) + grid_bytes, P, caches->n);
   cudaError_t e = launch_interp(a, sc, static_cast<cudaStream_t>(stream), &c->tracer);
   if (e != cudaSuccess) return cuda_fail(c, e, "interpolation launch");
+  return DRC_OK;
+}
+
+drc_status drc_indirect(drc_ctx *c, const drc_caches *caches, const drc_gbuffer *gbuf,
+                        const drc_indirect_params *prm, float *out_rgb, void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!caches || !gbuf || !prm) return fail(c, DRC_ERR_INVALID_ARG, "NULL argument struct");
+  if (caches->n < 1) return fail(c, DRC_ERR_INVALID_ARG, "caches->n must be >= 1");
+  if (caches->H < 1 || caches->W < 1 || caches->H > kIndirectMaxRows)
+    return fail(c, DRC_ERR_INVALID_ARG, "map size must be 1..%d rows, >= 1 column", kIndirectMaxRows);
+  if ((long long)caches->n * caches->H * caches->W * 3 >= (1ll << 31))
+    return fail(c, DRC_ERR_INVALID_ARG, "maps too large");
+  if (prm->k < 1 || prm->k > 32) return fail(c, DRC_ERR_INVALID_ARG, "k must be 1..32");
+  if (prm->S < 1 || prm->S > 4096) return fail(c, DRC_ERR_INVALID_ARG, "S must be 1..4096");
+  if (gbuf->width < 0 || gbuf->height < 0) return fail(c, DRC_ERR_INVALID_ARG, "negative G-buffer size");
+  const long long P = (long long)gbuf->width * gbuf->height;
+  if (P * prm->S >= (1ll << 40)) return fail(c, DRC_ERR_INVALID_ARG, "too many samples");
+  drc_status s;
+  if ((s = check_dev(c, caches->maps, "caches->maps", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, caches->nrm, "caches->nrm", false)) != DRC_OK) return s;
+  if (P > 0) {
+    if ((s = check_dev(c, out_rgb, "out_rgb", false)) != DRC_OK) return s;
+    if ((s = check_dev(c, gbuf->nrm, "gbuf->nrm", false)) != DRC_OK) return s;
+    if ((s = check_dev(c, prm->nbr, "nbr", false)) != DRC_OK) return s;
+    if ((s = check_dev(c, prm->nbr_w, "nbr_w", false)) != DRC_OK) return s;
+    if ((s = check_dev(c, prm->u, "u", false)) != DRC_OK) return s;
+    if ((s = check_dev(c, prm->albedo, "albedo", false)) != DRC_OK) return s;
+    if ((s = check_dev(c, prm->emit, "emit", true)) != DRC_OK) return s;
+    if ((s = check_dev(c, prm->direct, "direct", true)) != DRC_OK) return s;
+  }
+  IndirectArgs a;
+  memset(&a, 0, sizeof a);
+  a.n = caches->n;
+  a.H = caches->H;
+  a.W = caches->W;
+  const size_t need = indirect_scratch_bytes(a.n, a.H, a.W);
+  if (need > c->indscratch_bytes) {
+    if (c->d_indscratch) cudaFree(c->d_indscratch);
+    c->d_indscratch = nullptr;
+    c->indscratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&c->d_indscratch, need);
+    if (e != cudaSuccess) return cuda_fail(c, e, "indirect scratch");
+    c->indscratch_bytes = need;
+  }
+  indirect_carve(a, c->d_indscratch);
+  a.maps = caches->maps;
+  a.cnrm = caches->nrm;
+  a.P = P;
+  a.k = prm->k;
+  a.S = prm->S;
+  a.nbr = prm->nbr;
+  a.nbr_w = prm->nbr_w;
+  a.gnrm = gbuf->nrm;
+  a.albedo = prm->albedo;
+  a.u = reinterpret_cast<const float4 *>(prm->u);
+  a.emit = prm->emit;
+  a.direct = prm->direct;
+  a.out = out_rgb;
+  // row geometry in double: cos of the band edges, and the texel solid angle
+  // written as 2 sin(mid) sin(half-width) (2 pi / W), free of the cancellation
+  // of a difference of cosines near the pole
+  const double pi = 3.14159265358979323846;
+  for (int r = 0; r <= a.H; ++r) a.rowcos[r] = (float)std::cos(r * 0.5 * pi / a.H);
+  for (int r = 0; r < a.H; ++r) {
+    const double t0 = r * 0.5 * pi / a.H, t1 = (r + 1) * 0.5 * pi / a.H;
+    a.omega[r] = (float)(2.0 * std::sin(0.5 * (t0 + t1)) * std::sin(0.5 * (t1 - t0)) * (2.0 * pi / a.W));
+  }
+  cudaError_t e = launch_indirect(a, static_cast<cudaStream_t>(stream), &c->tracer);
+  if (e != cudaSuccess) return cuda_fail(c, e, "indirect launch");
   return DRC_OK;
 }
 

@@ -76,6 +76,7 @@ extern "C" drc_status drc_interpolate_static(const drc_caches *caches, const drc
     if (world && !device_ptr_ok(gbuf->pos, dev)) return DRC_ERR_INVALID_ARG;
     if (lookup && !device_ptr_ok(gbuf->dir, dev)) return DRC_ERR_INVALID_ARG;
     if (prm->nbr_out && !device_ptr_ok(prm->nbr_out, dev)) return DRC_ERR_INVALID_ARG;
+    if (prm->nbr_w && (!prm->nbr_out || !device_ptr_ok(prm->nbr_w, dev))) return DRC_ERR_INVALID_ARG;
   }
 
   // The array's address in the current context.  The first call in a
@@ -111,6 +112,7 @@ extern "C" drc_status drc_interpolate_static(const drc_caches *caches, const drc
   a.delta_rel = prm->delta_rel;
   a.out = out_rgb;
   a.nbr_out = prm->nbr_out;
+  a.nbr_w = prm->nbr_w;
   // The grid kernels rewrite every part of the scratch they read (the cell
   // counts are cleared first), so nothing is left over from an earlier call.
   const InterpScratch sc = interp_carve(scratch, caches->n, prm->k);

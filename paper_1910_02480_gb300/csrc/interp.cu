@@ -843,6 +843,11 @@ __device__ __forceinline__ void blend_store(const InterpArgs &a, long long p, co
     for (int sl = 0; sl < KMAX; ++sl)
       if (sl >= m) a.nbr_out[(size_t)p * k + (sl - m)] = jj[sl];
   }
+  if (a.nbr_w) {
+#pragma unroll
+    for (int sl = 0; sl < KMAX; ++sl)
+      if (sl >= m) a.nbr_w[(size_t)p * k + (sl - m)] = jj[sl] >= 0 ? wt[sl] / wsum : 0.f;
+  }
 }
 
 // The same blend from the collected table slots (cnt of them, in visit

@@ -61,6 +61,7 @@ struct InterpArgs {
   float r, eps, delta_rel;
   float *out;
   int *nbr_out;
+  float *nbr_w;      // with nbr_out: the normalised weights
   // set by launch_interp: caches per grid cell the grid is sized for, and
   // the cooperative query's first-gather radius and near distance, in units
   // of the expected distance to the (k+1)-th nearest cache

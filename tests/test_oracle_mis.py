@@ -126,3 +126,20 @@ def test_texel_geometry_closed_forms():
                               np.ones((T, 3)), u)
     mean, se = est.mean(axis=0), est.std(axis=0, ddof=1) / math.sqrt(T)
     assert np.all(np.abs(mean - 2.0 * math.sin(math.pi / (2 * H)) ** 2) <= 5 * se + 1e-12)
+
+
+def test_decision_margin_is_zero_on_a_boundary_and_leaves_the_estimate_alone():
+    """The margin output reports how close a sample's discrete decisions come
+    to changing: u0 placed exactly on the running weight sum gives 0, and
+    asking for it does not change the estimate."""
+    caches, idx, w, pn, alb = _scene(seed=3, n=3, P=4)
+    u = np.random.default_rng(4).uniform(0.0, 1.0, size=(4, 6, 4))
+    a = oracle.mis_indirect(caches, idx, w, pn, alb, u)
+    b, m = oracle.mis_indirect(caches, idx, w, pn, alb, u, want_margin=True)
+    np.testing.assert_array_equal(a, b)
+    assert np.all(m >= 0.0) and np.all(m <= 1.0)
+    u2 = u.copy()
+    u2[1, 2, 0] = w[1, 0]  # on the first boundary of pixel 1's map choice
+    _, m2 = oracle.mis_indirect(caches, idx, w, pn, alb, u2, want_margin=True)
+    assert m2[1] == 0.0
+    np.testing.assert_array_equal(m2[[0, 2, 3]], m[[0, 2, 3]])
