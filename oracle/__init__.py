@@ -361,9 +361,10 @@ def mis_indirect(caches, nbr_idx, nbr_w, gnrm, albedo, u, want_margin=False):
     radiance) and 'nrm'; the pixels' k caches and normalised weights
     [P,k]; pixel normals and albedos [P,3]; uniforms u [P,S,4].  Readings
     in drc_oracle.c.  Returns [P,3], and with want_margin also [P]: per
-    pixel the smallest distance of a sample's discrete decision (map,
-    texel, hemisphere, frame) from where it changes, so that a float
-    evaluation is compared only where it must take the same decisions."""
+    pixel the smallest distance of a sample's continuous-valued decision
+    (texel of a direction, hemisphere, frame) from where it changes, in
+    units of the float32 error of that value (below 1: a float evaluation
+    may rightly decide otherwise)."""
     maps, n, H, W, cnrm, idx, P, k, w, gn, alb = _mis_args(caches, nbr_idx, nbr_w, gnrm, albedo)
     u = _f64(u)
     if u.shape[0] != P or u.shape[2] != 4:

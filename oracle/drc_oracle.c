@@ -625,19 +625,58 @@ static double *env_cdfs(int n_caches, int H, int W, const float *maps)
     return cdf;
 }
 
-/* margin (nullable, [P]): for the comparison with a float evaluation, the
- * smallest distance, over the pixel's samples, of a value that takes a
- * discrete decision from the boundary where that decision changes: the map
- * choice (u0 against the running weight sums), the environment texel
- * (target against the CDF, relative to its total), the texel a direction
- * falls in (polar and azimuthal texel coordinates against integers), the
- * hemisphere tests (cosines against 0) and the up-vector switch of the
- * frames (|n_z| against 1 - 1e-6).  The estimate does not depend on it. */
-static void margin_min(double *m, double v)
+/* Two discrete choices of a sample are taken from running sums: the map
+ * (u0 against the running sum of the weights) and the environment texel
+ * (u1 times the total against the CDF).  The paper fixes no precision for
+ * them; a float32 evaluation sums in float32, and near a boundary the two
+ * precisions may rightly choose differently.  So both choices are taken in
+ * float32 here, from the same float32 operations in the same order as the
+ * GPU path: the weights summed one by one, and each map's CDF summed texel
+ * by texel in row-major order from float32 luminance
+ * (0.2126 R + 0.7152 G) + 0.0722 B times the row's solid angle, that angle
+ * being 2 sin(mid) sin(half-width) (2 pi / W) in double rounded to float32.
+ * Everything else stays double.
+ *
+ * margin (nullable, [P]): for the comparison with a float evaluation, the
+ * smallest distance, over the pixel's samples, of a value that takes one of
+ * the other discrete decisions from the boundary where it changes, in units
+ * of the float32 error that value may carry: the texel a direction falls in
+ * (polar and azimuthal texel coordinates against integers, units 2e-4
+ * texel), the hemisphere tests (cosines against 0, units 2e-6) and the
+ * up-vector switch of the frames (|n_z| against 1 - 1e-6, units 2e-6).
+ * Below 1, a float32 evaluation may rightly decide the other way.  The
+ * estimate does not depend on it. */
+static void margin_min(double *m, double v, double unit)
 {
-    v = fabs(v);
+    v = fabs(v) / unit;
     if (v < *m)
         *m = v;
+}
+
+static float omega_f32(int a, int H, int W)
+{
+    const double t0 = a * 0.5 * ORC_PI / H, t1 = (a + 1) * 0.5 * ORC_PI / H;
+    return (float)(2.0 * sin(0.5 * (t0 + t1)) * sin(0.5 * (t1 - t0)) * (2.0 * ORC_PI / W));
+}
+
+/* per-map float32 CDF of the texel choice, summed as described above */
+static float *env_cdfs_f32(int n_caches, int H, int W, const float *maps)
+{
+    const long plane = (long)H * W;
+    float *cdf = (float *)malloc(sizeof(float) * (size_t)(n_caches * plane));
+    for (int j = 0; j < n_caches; j++) {
+        float acc = 0.0f;
+        for (int a = 0; a < H; a++) {
+            const float om = omega_f32(a, H, W);
+            for (int b = 0; b < W; b++) {
+                const float *R = maps + (long)j * 3 * plane + (long)a * W + b;
+                const float lum = (0.2126f * R[0] + 0.7152f * R[plane]) + 0.0722f * R[2 * plane];
+                acc = acc + lum * om;
+                cdf[(long)j * plane + (long)a * W + b] = acc;
+            }
+        }
+    }
+    return cdf;
 }
 
 static double frac_dist(double x)
@@ -649,7 +688,7 @@ static double frame_margin(const float *nrm)
 {
     double nx = nrm[0], ny = nrm[1], nz = nrm[2];
     double len = sqrt(nx * nx + ny * ny + nz * nz);
-    return len > 0.0 ? fabs(fabs(nz / len) - (1.0 - 1e-6)) : 1.0;
+    return len > 0.0 ? fabs(fabs(nz / len) - (1.0 - 1e-6)) / 2e-6 : 1e30;
 }
 
 int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const float *cnrm, long P, int k,
@@ -660,6 +699,7 @@ int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const 
         return -1;
     const long plane = (long)mapH * mapW;
     double *cdf = env_cdfs(n_caches, mapH, mapW, maps);
+    float *cdf_f = env_cdfs_f32(n_caches, mapH, mapW, maps);
     const double n_env = (double)((S + 1) / 2), n_brdf = (double)(S / 2);
 #pragma omp parallel for schedule(dynamic, 16)
     for (long p = 0; p < P; p++) {
@@ -669,23 +709,22 @@ int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const 
         if (cache_frame(&gnrm[3 * p], tp, bp, np_)) {
             for (int s = 0; s < S; s++) {
                 const double *us = u + ((size_t)p * S + s) * 4;
-                /* the map, by the normalised weights */
+                /* the map, by the normalised weights (running sum in float32) */
                 int q = -1;
-                double c = 0.0;
+                float c = 0.0f;
                 for (int i = 0; i < k; i++) {
                     if (nbr_idx[p * k + i] < 0)
                         continue;
                     q = i;
-                    c += nbr_w[p * k + i];
-                    margin_min(&mg, us[0] - c);
-                    if (us[0] < c)
+                    c = c + (float)nbr_w[p * k + i];
+                    if ((float)us[0] < c)
                         break;
                 }
                 if (q < 0)
                     continue;
                 const int j = nbr_idx[p * k + q];
                 double t[3], b[3], n[3];
-                margin_min(&mg, frame_margin(&cnrm[3 * j]));
+                margin_min(&mg, frame_margin(&cnrm[3 * j]), 1.0);
                 if (!cache_frame(&cnrm[3 * j], t, b, n))
                     continue;
                 const double *cj = cdf + (long)j * plane;
@@ -694,13 +733,12 @@ int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const 
                 if (s % 2 == 0) { /* environment: texel by the CDF, direction uniform inside */
                     if (!(total > 0.0))
                         continue;
-                    const double target = us[1] * total;
+                    /* the texel, by the float32 CDF */
+                    const float *cf = cdf_f + (long)j * plane;
+                    const float target = (float)us[1] * cf[plane - 1];
                     long e = 0;
-                    while (e < plane - 1 && !(cj[e] > target))
+                    while (e < plane - 1 && !(cf[e] > target))
                         e++;
-                    margin_min(&mg, (cj[e] - target) / total);
-                    if (e > 0)
-                        margin_min(&mg, (target - cj[e - 1]) / total);
                     const int a = (int)(e / mapW), bc = (int)(e % mapW);
                     const double c0 = cos(a * 0.5 * ORC_PI / mapH), c1 = cos((a + 1) * 0.5 * ORC_PI / mapH);
                     const double mu = c0 - us[2] * (c0 - c1), sn = sqrt(1.0 - mu * mu > 0.0 ? 1.0 - mu * mu : 0.0);
@@ -715,21 +753,21 @@ int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const 
                         w[d] = l[0] * tp[d] + l[1] * bp[d] + l[2] * np_[d];
                 }
                 const double cosp = w[0] * np_[0] + w[1] * np_[1] + w[2] * np_[2];
-                margin_min(&mg, cosp);
+                margin_min(&mg, cosp, 2e-6);
                 if (!(cosp > 0.0))
                     continue;
                 {
                     const double lx = w[0] * t[0] + w[1] * t[1] + w[2] * t[2];
                     const double ly = w[0] * b[0] + w[1] * b[1] + w[2] * b[2];
                     const double lz = w[0] * n[0] + w[1] * n[1] + w[2] * n[2];
-                    margin_min(&mg, lz);
+                    margin_min(&mg, lz, 2e-6);
                     if (lz > 0.0) {
                         const double th = acos(lz > 1.0 ? 1.0 : lz);
                         double ph = atan2(ly, lx);
                         if (ph < 0.0)
                             ph += 2.0 * ORC_PI;
-                        margin_min(&mg, frac_dist(th / (0.5 * ORC_PI) * mapH));
-                        margin_min(&mg, frac_dist(ph / (2.0 * ORC_PI) * mapW));
+                        margin_min(&mg, frac_dist(th / (0.5 * ORC_PI) * mapH), 2e-4);
+                        margin_min(&mg, frac_dist(ph / (2.0 * ORC_PI) * mapW), 2e-4);
                     }
                 }
                 int ta, tb;
@@ -751,6 +789,7 @@ int orc_mis_indirect(int n_caches, int mapH, int mapW, const float *maps, const 
             margin[p] = mg;
     }
     free(cdf);
+    free(cdf_f);
     return 0;
 }
 

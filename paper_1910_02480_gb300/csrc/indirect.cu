@@ -20,9 +20,9 @@
 // f_r cos R / (n_env pdf_env + n_brdf pdf_brdf).  The uniforms are an input,
 // u[p][s] = (map choice, three for the direction).
 //
-// 1. indirect_setup_kernel: one block per map: its frame and its CDF
-//    (per-thread runs of texels in row-major order, a block scan of the run
-//    totals).
+// 1. indirect_setup_kernel: one thread per map: its frame and its CDF,
+//    summed in row-major order in float32 (the texel choice is taken from
+//    these sums, as in the oracle).
 // 2. indirect_kernel: one thread per pixel over its S samples; the texel of
 //    an environment sample by binary search in the CDF; the result plus the
 //    emission and the direct term when given (Eq. 3).
@@ -34,7 +34,7 @@
 
 namespace drc {
 
-static constexpr int SETUP_THREADS = 256;
+static constexpr int SETUP_THREADS = 128;
 static constexpr int IND_THREADS = 256;
 static constexpr float kPi = 3.14159265358979f;
 
@@ -72,41 +72,31 @@ __device__ __forceinline__ float lum_of(float r, float g, float b) {
   return __fadd_rn(__fadd_rn(__fmul_rn(0.2126f, r), __fmul_rn(0.7152f, g)), __fmul_rn(0.0722f, b));
 }
 
+// One thread per map: its frame and its CDF, summed texel by texel in
+// row-major order with separately rounded float32 operations
+// (luminance (0.2126 R + 0.7152 G) + 0.0722 B, times the row's solid angle,
+// added to the running total).  The texel choice is taken from these sums;
+// they are exactly the float32 sums in that order, so the choice is the one
+// any float32 evaluation in that order takes.
 __global__ void __launch_bounds__(SETUP_THREADS) indirect_setup_kernel(const __grid_constant__ IndirectArgs a) {
-  __shared__ float warp_tot[SETUP_THREADS / 32];
-  const int j = blockIdx.x, tid = threadIdx.x;
-  if (tid == 0) {
-    float3 t, b, n;
-    const bool ok = make_frame(__ldg(a.cnrm + 3 * j), __ldg(a.cnrm + 3 * j + 1), __ldg(a.cnrm + 3 * j + 2), t, b, n);
-    a.frame[3 * j] = make_float4(t.x, t.y, t.z, 0.f);
-    a.frame[3 * j + 1] = make_float4(b.x, b.y, b.z, 0.f);
-    a.frame[3 * j + 2] = make_float4(n.x, n.y, n.z, ok ? 1.f : 0.f);
-  }
-  const int HW = a.H * a.W;
-  const size_t plane = (size_t)HW;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= a.n) return;
+  float3 t, b, n;
+  const bool ok = make_frame(__ldg(a.cnrm + 3 * j), __ldg(a.cnrm + 3 * j + 1), __ldg(a.cnrm + 3 * j + 2), t, b, n);
+  a.frame[3 * j] = make_float4(t.x, t.y, t.z, 0.f);
+  a.frame[3 * j + 1] = make_float4(b.x, b.y, b.z, 0.f);
+  a.frame[3 * j + 2] = make_float4(n.x, n.y, n.z, ok ? 1.f : 0.f);
+  const size_t plane = (size_t)a.H * a.W;
   const float *R = a.maps + (size_t)j * 3 * plane;
-  const int run = (HW + SETUP_THREADS - 1) / SETUP_THREADS;
-  const int e0 = min(tid * run, HW), e1 = min(e0 + run, HW);
-  float local = 0.f;
-  for (int e = e0; e < e1; ++e)
-    local += lum_of(__ldg(R + e), __ldg(R + plane + e), __ldg(R + 2 * plane + e)) * a.omega[e / a.W];
-  // exclusive scan of the run totals over the block
-  const int lane = tid & 31, w = tid >> 5;
-  float x = local;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const float y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) warp_tot[w] = x;
-  __syncthreads();
-  float before = 0.f;
-  for (int q = 0; q < w; ++q) before += warp_tot[q];
-  float acc = before + x - local;
   float *cdf = a.cdf + (size_t)j * plane;
-  for (int e = e0; e < e1; ++e) {
-    acc += lum_of(__ldg(R + e), __ldg(R + plane + e), __ldg(R + 2 * plane + e)) * a.omega[e / a.W];
-    cdf[e] = acc;
+  float acc = 0.f;
+  for (int r = 0; r < a.H; ++r) {
+    const float om = a.omega[r];
+    for (int c = 0; c < a.W; ++c) {
+      const size_t e = (size_t)r * a.W + c;
+      acc = __fadd_rn(acc, __fmul_rn(lum_of(__ldg(R + e), __ldg(R + plane + e), __ldg(R + 2 * plane + e)), om));
+      cdf[e] = acc;
+    }
   }
 }
 
@@ -126,14 +116,14 @@ __global__ void __launch_bounds__(IND_THREADS) indirect_kernel(const __grid_cons
   const float *wb = a.nbr_w + p * a.k;
   for (int s = 0; pix_ok && s < a.S; ++s) {
     const float4 us = __ldg(a.u + p * a.S + s);
-    // the map, by the normalised weights
+    // the map, by the normalised weights (their running float32 sum)
     int j = -1;
     float c = 0.f;
     for (int i = 0; i < a.k; ++i) {
       const int ji = __ldg(nb + i);
       if (ji < 0 || ji >= a.n) continue;  // no neighbour (an index past n is treated alike)
       j = ji;
-      c += __ldg(wb + i);
+      c = __fadd_rn(c, __ldg(wb + i));
       if (us.x < c) break;
     }
     if (j < 0) continue;
@@ -145,7 +135,7 @@ __global__ void __launch_bounds__(IND_THREADS) indirect_kernel(const __grid_cons
     float wx, wy, wz;
     if ((s & 1) == 0) {  // environment: texel by the CDF, direction uniform inside it
       if (!(total > 0.f)) continue;
-      const float target = us.y * total;
+      const float target = __fmul_rn(us.y, total);
       int lo = 0, hi = HW - 1;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
@@ -211,7 +201,9 @@ __global__ void __launch_bounds__(IND_THREADS) indirect_kernel(const __grid_cons
 }
 
 cudaError_t launch_indirect(const IndirectArgs &a, cudaStream_t st, Tracer *tr) {
-  if (a.n > 0) DRC_TRACED(tr, "indirect setup", st, (indirect_setup_kernel<<<a.n, SETUP_THREADS, 0, st>>>(a)));
+  if (a.n > 0)
+    DRC_TRACED(tr, "indirect setup", st,
+               (indirect_setup_kernel<<<(a.n + SETUP_THREADS - 1) / SETUP_THREADS, SETUP_THREADS, 0, st>>>(a)));
   if (a.P > 0) {
     const unsigned blocks = (unsigned)((a.P + IND_THREADS - 1) / IND_THREADS);
     DRC_TRACED(tr, "indirect estimate", st, (indirect_kernel<<<blocks, IND_THREADS, 0, st>>>(a)));

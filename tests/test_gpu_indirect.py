@@ -2,12 +2,13 @@
 sampling between the blended cached maps and the BRDF, Sec. 3.2; plus the
 emission and direct terms) with the FP64 oracle, through the C ABI.
 
-The uniforms are an input, so both sides draw the same samples.  A sample
-takes discrete decisions from floating-point values (the map, the texel of
-an environment sample, the texel a direction falls in, the hemisphere
-tests); the oracle reports per pixel how close its decisions came to a
-boundary, and pixels within 2e-4 of one (where fp32 may rightly decide the
-other way) are left out and counted."""
+The uniforms are an input, so both sides draw the same samples.  The map
+and the environment texel are chosen from running float32 sums that both
+sides form alike.  The other discrete decisions come from continuous values
+(the texel a direction falls in, the hemisphere tests, the frame's up
+vector); the oracle reports per pixel how close they came to a boundary in
+units of their float32 error, and pixels below 1 (where fp32 may rightly
+decide the other way) are left out and counted."""
 import numpy as np
 import pytest
 
@@ -17,7 +18,7 @@ from parity import FP32_TOL, rel_err
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-MARGIN = 2e-4
+MARGIN = 1.0
 
 
 @pytest.fixture(scope="module")
@@ -79,7 +80,7 @@ def _gpu(ctx, c, g, idx, wts, u, alb, emit=None, direct=None):
     return out.cpu().numpy()
 
 
-def _check(got, ref, margin, min_kept=0.97):
+def _check(got, ref, margin, min_kept=0.98):
     ok = margin > MARGIN
     assert ok.mean() >= min_kept, ok.mean()
     err = rel_err(got[ok], ref[ok])
