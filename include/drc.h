@@ -240,6 +240,39 @@ typedef struct {
 drc_status drc_indirect(drc_ctx *ctx, const drc_caches *caches, const drc_gbuffer *gbuf,
                         const drc_indirect_params *params, float *out_rgb, void *stream);
 
+/* The denoiser's input maps traced from cache points (Sec. 3.1-3.3: the
+ * radiance arriving at the first non-specular hit without the direct light,
+ * the distance to what is seen and its normal), in an analytic interior:
+ * the unit box [0,1]^3 of six diffuse walls, an emitting rectangle on the
+ * ceiling z = 1 and diffuse spheres seen from outside.
+ *   Texel (a, b) of cache j takes one ray from pos[j] along polar angle
+ *   (a + 1/2) pi/2H from nrm[j] and azimuth (b + 1/2) 2 pi/W in the cache
+ *   frame of drc_interpolate's LOOKUP mode.  Channel 3 is the distance to the
+ *   first hit, channels 4-6 its normal facing the ray, channels 0-2 the
+ *   radiance leaving it toward the cache without its own emission: a path of
+ *   D bounces, each cosine-weighted about the current normal with uniforms
+ *   u[j][a][b][k] = (u0, u1) (r = sqrt(u0), phi = 2 pi u1), adding the
+ *   throughput times the next hit's emission and multiplying it by that
+ *   hit's albedo.  A texel whose ray hits nothing, or a cache with a zero
+ *   normal, is all zeros.
+ * pos, nrm: device [n][3] (pos strictly inside the box); u: device
+ * [n][H][W][D][2] float32 (8-byte aligned; NULL when D = 0); maps: device
+ * [n][7][H][W] float32, drc_denoise's input layout (linear radiance: denoise
+ * with DRC_F_ENCODE_INPUT).  INVALID_ARG for nsph outside 0..DRC_MAX_SPHERES,
+ * H, W outside 1..4096, D outside 0..64.  Asynchronous on `stream`. */
+#define DRC_MAX_SPHERES 64
+typedef struct {
+  float wall_alb[6][3];  /* albedo of the walls -x, +x, -y, +y, -z, +z */
+  float wall_em[6][3];   /* their emitted radiance */
+  int has_light;         /* the ceiling rectangle below, when nonzero */
+  float light[7];        /* x0, x1, y0, y1 on z = 1, emitted radiance rgb */
+  int nsph;
+  float sph[DRC_MAX_SPHERES][7]; /* centre xyz, radius, albedo rgb */
+} drc_scene;
+
+drc_status drc_gen_maps(drc_ctx *ctx, const drc_scene *scene, int n, const float *pos, const float *nrm, int H,
+                        int W, int D, const float *u, float *maps, void *stream);
+
 /* One frame end to end from host memory: drc_denoise of N maps, then
  * drc_interpolate (IRRADIANCE) of a G-buffer from their payloads, with the
  * uploads and the download inside the call (Sec. 3.3 denoising feeding the

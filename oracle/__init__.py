@@ -83,7 +83,7 @@ def _load():
         lib.orc_mis_indirect.restype = i
         lib.orc_indirect_expected.argtypes = [i, i, i, P, P, l, i, P, P, P, P, i, P]
         lib.orc_indirect_expected.restype = i
-        lib.orc_gen_maps.argtypes = [i, P, P, i, i, P, P, P, i, P, i, P, P]
+        lib.orc_gen_maps.argtypes = [i, P, P, i, i, P, P, P, i, P, i, P, P, P]
         lib.orc_gen_maps.restype = i
         lib.orc_interp.restype = i
         lib.orc_l1_backward.argtypes = [i, P, i, i, i, d, u, P, l, P, P, i, i,
@@ -389,13 +389,16 @@ def indirect_expected(caches, nbr_idx, nbr_w, gnrm, albedo, m=16):
     return out
 
 
-def gen_maps(pos, nrm, H, W, wall_alb, wall_em=None, light=None, spheres=(), D=3, u=None):
+def gen_maps(pos, nrm, H, W, wall_alb, wall_em=None, light=None, spheres=(), D=3, u=None, want_margin=False):
     """Maps [n, 7, H, W] traced from cache points pos [n,3] (inside the unit
     box) with normals nrm [n,3]: radiance leaving the first hit without its
     own emission (D cosine-sampled bounces), distance, hit normal.  wall_alb,
     wall_em: [6,3] for -x, +x, -y, +y, -z, +z; light: (x0, x1, y0, y1, Le
     rgb) on the ceiling; spheres: rows (cx, cy, cz, r, albedo rgb); u:
-    uniforms [n, H, W, D, 2] (default zeros)."""
+    uniforms [n, H, W, D, 2] (default zeros).  With want_margin also
+    [n, H, W]: per texel the smallest margin of its path's discrete
+    decisions in units of their float32 error (below 1: a float evaluation
+    may rightly hit another surface or light)."""
     pos, nrm = _f32(pos), _f32(nrm)
     n = pos.shape[0]
     wa = _f64(wall_alb).reshape(6, 3)
@@ -407,9 +410,10 @@ def gen_maps(pos, nrm, H, W, wall_alb, wall_em=None, light=None, spheres=(), D=3
         raise ValueError("u must be [n, H, W, D, 2]")
     u = np.ascontiguousarray(u[:, :, :, :max(D, 1)])
     out = np.empty((n, 7, H, W))
+    margin = np.empty((n, H, W)) if want_margin else None
     rc = _load().orc_gen_maps(n, _ptr(pos), _ptr(nrm), H, W, _ptr(wa), _ptr(we), _ptr(lt), sp.shape[0], _ptr(sp),
-                              D, _ptr(u), _ptr(out))
+                              D, _ptr(u), _ptr(out), _ptr(margin))
     if rc:
         raise ValueError("oracle gen_maps: points must lie inside the unit box, normals nonzero")
-    return out
+    return (out, margin) if want_margin else out
 

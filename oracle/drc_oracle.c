@@ -879,19 +879,31 @@ typedef struct {
 } orc_scene;
 
 /* nearest hit of the ray o + t d (d unit, t > 0): distance, normal facing
- * the ray, albedo and emission there; 0 when nothing is hit */
+ * the ray, albedo and emission there; 0 when nothing is hit.  mg
+ * (nullable): lowered to the margins of the hit's discrete decisions, in
+ * units of the float32 error the values may carry after a few bounces --
+ * the gap from the nearest surface to the next one along the ray (units
+ * 1e-5), the hit's distance to the ceiling light's border (1e-5), a sphere's
+ * B^2 - C at a grazing ray (1e-6) and, for the next bounce's frame, |n_z| of
+ * a sphere normal against 1 - 1e-6 (2e-6). */
 static int scene_hit(const orc_scene *sc, const double o[3], const double d[3], double *th, double nh[3],
-                     double alb[3], double em[3])
+                     double alb[3], double em[3], double *mg)
 {
-    double best = INFINITY;
+    double best = INFINITY, second = INFINITY;
     int which = -1; /* 0..5 wall, 6 + s sphere s */
     for (int i = 0; i < 3; i++) {
+        double t = -1.0;
+        int w = -1;
         if (d[i] > 0.0) {
-            const double t = (1.0 - o[i]) / d[i];
-            if (t > 1e-12 && t < best) { best = t; which = 2 * i + 1; }
+            t = (1.0 - o[i]) / d[i];
+            w = 2 * i + 1;
         } else if (d[i] < 0.0) {
-            const double t = -o[i] / d[i];
-            if (t > 1e-12 && t < best) { best = t; which = 2 * i; }
+            t = -o[i] / d[i];
+            w = 2 * i;
+        }
+        if (w >= 0 && t > 1e-12) {
+            if (t < best) { second = best; best = t; which = w; }
+            else if (t < second) second = t;
         }
     }
     for (int s = 0; s < sc->nsph; s++) {
@@ -900,13 +912,20 @@ static int scene_hit(const orc_scene *sc, const double o[3], const double d[3], 
         const double B = oc[0] * d[0] + oc[1] * d[1] + oc[2] * d[2];
         const double C = oc[0] * oc[0] + oc[1] * oc[1] + oc[2] * oc[2] - sp[3] * sp[3];
         const double disc = B * B - C;
+        if (mg && C > 0.0 && B < 0.0)
+            margin_min(mg, disc, 1e-6);
         if (C <= 0.0 || disc < 0.0)
             continue; /* seen from outside only */
         const double t = -B - sqrt(disc);
-        if (t > 1e-12 && t < best) { best = t; which = 6 + s; }
+        if (t > 1e-12) {
+            if (t < best) { second = best; best = t; which = 6 + s; }
+            else if (t < second) second = t;
+        }
     }
     if (which < 0)
         return 0;
+    if (mg && second < INFINITY)
+        margin_min(mg, second - best, 1e-5);
     *th = best;
     const double h[3] = {o[0] + best * d[0], o[1] + best * d[1], o[2] + best * d[2]};
     if (which < 6) {
@@ -916,6 +935,11 @@ static int scene_hit(const orc_scene *sc, const double o[3], const double d[3], 
         for (int c = 0; c < 3; c++) {
             alb[c] = sc->wall_alb[3 * which + c];
             em[c] = sc->wall_em[3 * which + c];
+        }
+        if (which == 5 && sc->light && mg) {
+            const double ex = fmin(fabs(h[0] - sc->light[0]), fabs(h[0] - sc->light[1]));
+            const double ey = fmin(fabs(h[1] - sc->light[2]), fabs(h[1] - sc->light[3]));
+            margin_min(mg, fmin(ex, ey), 1e-5);
         }
         if (which == 5 && sc->light && h[0] >= sc->light[0] && h[0] <= sc->light[1] && h[1] >= sc->light[2] &&
             h[1] <= sc->light[3])
@@ -928,13 +952,20 @@ static int scene_hit(const orc_scene *sc, const double o[3], const double d[3], 
             alb[c] = sp[4 + c];
             em[c] = 0.0;
         }
+        if (mg) {
+            const float nf[3] = {(float)nh[0], (float)nh[1], (float)nh[2]};
+            margin_min(mg, frame_margin(nf), 1.0);
+        }
     }
     return 1;
 }
 
+/* margin (nullable, [n][H][W]): per texel the smallest margin of the
+ * decisions along its path (scene_hit), for the comparison with a float32
+ * evaluation: below 1 it may rightly take another surface or light. */
 int orc_gen_maps(int n, const float *pos, const float *nrm, int H, int W, const double *wall_alb,
                  const double *wall_em, const double *light, int nsph, const double *sph, int D, const double *u,
-                 double *maps)
+                 double *maps, double *margin)
 {
     if (n < 0 || H < 1 || W < 1 || D < 0 || nsph < 0)
         return -1;
@@ -963,9 +994,12 @@ int orc_gen_maps(int n, const float *pos, const float *nrm, int H, int W, const 
                 for (int c = 0; c < 3; c++)
                     d[c] = l[0] * t[c] + l[1] * b[c] + l[2] * nn[c];
                 double dist, nh[3], alb[3], em[3];
+                double mgv = 1e30, *mg = margin ? &mgv : NULL;
                 for (int c = 0; c < 7; c++)
                     out[c * plane + e] = 0.0;
-                if (!scene_hit(&sc, x, d, &dist, nh, alb, em))
+                if (margin)
+                    margin[(long)j * plane + e] = 1e30;
+                if (!scene_hit(&sc, x, d, &dist, nh, alb, em, mg))
                     continue;
                 out[3 * plane + e] = dist;
                 for (int c = 0; c < 3; c++)
@@ -985,7 +1019,7 @@ int orc_gen_maps(int n, const float *pos, const float *nrm, int H, int W, const 
                     for (int c = 0; c < 3; c++)
                         dn[c] = rr * cos(phi) * tt[c] + rr * sin(phi) * bb[c] + lz * nc[c];
                     double t2, nh2[3], alb2[3], em2[3];
-                    if (!scene_hit(&sc, o, dn, &t2, nh2, alb2, em2))
+                    if (!scene_hit(&sc, o, dn, &t2, nh2, alb2, em2, mg))
                         break;
                     for (int c = 0; c < 3; c++) {
                         L[c] += thr[c] * em2[c];
@@ -996,6 +1030,8 @@ int orc_gen_maps(int n, const float *pos, const float *nrm, int H, int W, const 
                 }
                 for (int c = 0; c < 3; c++)
                     out[c * plane + e] = L[c];
+                if (margin)
+                    margin[(long)j * plane + e] = mgv;
             }
     }
     return bad ? -1 : 0;

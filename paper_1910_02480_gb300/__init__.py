@@ -70,6 +70,38 @@ class InterpParams(ctypes.Structure):
                 ("delta_rel", ctypes.c_float), ("nbr_out", ctypes.c_void_p), ("nbr_w", ctypes.c_void_p)]
 
 
+class Scene(ctypes.Structure):
+    _fields_ = [("wall_alb", (ctypes.c_float * 3) * 6), ("wall_em", (ctypes.c_float * 3) * 6),
+                ("has_light", ctypes.c_int), ("light", ctypes.c_float * 7), ("nsph", ctypes.c_int),
+                ("sph", (ctypes.c_float * 7) * 64)]
+
+
+def make_scene(wall_alb, wall_em=None, light=None, spheres=()):
+    """A drc_scene: wall albedos / emissions [6,3] (-x, +x, -y, +y, -z,
+    +z), an optional ceiling light (x0, x1, y0, y1, Le rgb) and sphere rows
+    (cx, cy, cz, r, albedo rgb)."""
+    import numpy as np
+    sc = Scene()
+    wa = np.asarray(wall_alb, dtype=np.float32).reshape(6, 3)
+    we = np.zeros((6, 3), np.float32) if wall_em is None else np.asarray(wall_em, dtype=np.float32).reshape(6, 3)
+    for i in range(6):
+        for c in range(3):
+            sc.wall_alb[i][c] = float(wa[i, c])
+            sc.wall_em[i][c] = float(we[i, c])
+    if light is not None:
+        sc.has_light = 1
+        for i, v in enumerate(np.asarray(light, dtype=np.float32).reshape(7)):
+            sc.light[i] = float(v)
+    sp = np.asarray(spheres, dtype=np.float32).reshape(-1, 7) if len(spheres) else np.zeros((0, 7), np.float32)
+    if sp.shape[0] > 64:
+        raise ValueError("at most 64 spheres")
+    sc.nsph = sp.shape[0]
+    for s_ in range(sp.shape[0]):
+        for c in range(7):
+            sc.sph[s_][c] = float(sp[s_, c])
+    return sc
+
+
 class IndirectParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("nbr", ctypes.c_void_p), ("nbr_w", ctypes.c_void_p), ("S", ctypes.c_int),
                 ("u", ctypes.c_void_p), ("albedo", ctypes.c_void_p), ("emit", ctypes.c_void_p),
@@ -108,6 +140,8 @@ def load_library():
     lib.drc_indirect.argtypes = [P, ctypes.POINTER(Caches), ctypes.POINTER(GBuffer), ctypes.POINTER(IndirectParams),
                                  P, P]
     lib.drc_indirect.restype = I
+    lib.drc_gen_maps.argtypes = [P, ctypes.POINTER(Scene), I, P, P, I, I, I, P, P, P]
+    lib.drc_gen_maps.restype = I
     lib.drc_backward.argtypes = [P, P, P, I, I, I, U, P, P, P, P]
     lib.drc_backward.restype = I
     lib.drc_frame_host.argtypes = [P, P, I, I, I, U, ctypes.POINTER(Caches), ctypes.POINTER(GBuffer),
@@ -288,6 +322,20 @@ class Context:
         rc = self._lib.drc_interpolate(self._ctx, ctypes.byref(c), ctypes.byref(g), ctypes.byref(p),
                                        _ptr(out), _stream(stream))
         self._check(rc, "drc_interpolate")
+        return out
+
+    def gen_maps(self, scene, pos, nrm, H, W, u=None, out=None, stream=None):
+        """drc_gen_maps: maps [n,7,H,W] traced from cache points pos / nrm
+        ([n,3] cuda float32) in `scene` (make_scene), with the uniforms u
+        [n,H,W,D,2] of the D bounces (None: D = 0)."""
+        import torch
+        n = int(pos.shape[0])
+        D = 0 if u is None else int(u.shape[3])
+        if out is None:
+            out = torch.empty((n, 7, H, W), dtype=torch.float32, device=pos.device)
+        rc = self._lib.drc_gen_maps(self._ctx, ctypes.byref(scene), n, _ptr(pos), _ptr(nrm), int(H), int(W), D,
+                                    _ptr(u), _ptr(out), _stream(stream))
+        self._check(rc, "drc_gen_maps")
         return out
 
     def indirect(self, maps, cache_nrm, gnrm, width, height, nbr, nbr_w, u, albedo, emit=None, direct=None,

@@ -19,6 +19,7 @@
 #include "head.cuh"
 #include "drc_status.cuh"
 #include "indirect.cuh"
+#include "mapgen.cuh"
 #include "interp.cuh"
 #include "trace.cuh"
 #include "train.cuh"
@@ -1482,6 +1483,38 @@ drc_status drc_indirect(drc_ctx *c, const drc_caches *caches, const drc_gbuffer 
   }
   cudaError_t e = launch_indirect(a, static_cast<cudaStream_t>(stream), &c->tracer);
   if (e != cudaSuccess) return cuda_fail(c, e, "indirect launch");
+  return DRC_OK;
+}
+
+drc_status drc_gen_maps(drc_ctx *c, const drc_scene *scene, int n, const float *pos, const float *nrm, int H,
+                        int W, int D, const float *u, float *maps, void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!scene) return fail(c, DRC_ERR_INVALID_ARG, "scene is NULL");
+  if (scene->nsph < 0 || scene->nsph > DRC_MAX_SPHERES)
+    return fail(c, DRC_ERR_INVALID_ARG, "nsph must be 0..%d", DRC_MAX_SPHERES);
+  if (n < 0 || H < 1 || W < 1 || H > 4096 || W > 4096 || D < 0 || D > 64)
+    return fail(c, DRC_ERR_INVALID_ARG, "need n >= 0, H and W in 1..4096, D in 0..64");
+  if ((long long)n * 7 * H * W >= (1ll << 40)) return fail(c, DRC_ERR_INVALID_ARG, "maps too large");
+  if (n == 0) return DRC_OK;
+  drc_status s;
+  if ((s = check_dev(c, pos, "pos", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, nrm, "nrm", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, maps, "maps", false)) != DRC_OK) return s;
+  if (D > 0 && (s = check_dev(c, u, "u", false)) != DRC_OK) return s;
+  MapGenArgs a;
+  memset(&a, 0, sizeof a);
+  a.scene = *scene;
+  a.n = n;
+  a.H = H;
+  a.W = W;
+  a.D = D;
+  a.pos = pos;
+  a.nrm = nrm;
+  a.u = reinterpret_cast<const float2 *>(u);
+  a.maps = maps;
+  cudaError_t e = launch_gen_maps(a, static_cast<cudaStream_t>(stream), &c->tracer);
+  if (e != cudaSuccess) return cuda_fail(c, e, "map generation launch");
   return DRC_OK;
 }
 

@@ -104,3 +104,23 @@ def test_argument_errors():
         oracle.gen_maps([[0.5, 0.5, 1.5]], [[0.0, 0.0, 1.0]], 4, 4, WHITE)
     with pytest.raises(ValueError):
         oracle.gen_maps([[0.5, 0.5, 0.5]], [[0.0, 0.0, 0.0]], 4, 4, WHITE)
+
+
+def test_margin_flags_rays_into_a_box_edge_and_leaves_the_maps_alone():
+    """The margin output: asking for it changes no map value.  From the box
+    centre with normal +z and W = 4 columns, every column's azimuth is a
+    diagonal (pi/4 + j pi/2), so its rays meet two side walls at the same
+    distance; for the rows below 54.7 degrees from the horizon (polar angle
+    above atan(sqrt 2)) those walls are the nearest surfaces: a tie, margin
+    below 1.  The two upper rows meet the ceiling well before either wall."""
+    H = W = 4
+    light = [0.25, 0.75, 0.25, 0.75, 5.0, 5.0, 5.0]
+    u = np.random.default_rng(7).uniform(size=(1, H, W, 2, 2))
+    a = oracle.gen_maps([[0.5, 0.5, 0.5]], [[0.0, 0.0, 1.0]], H, W, WHITE, light=light, D=2, u=u)
+    b, m = oracle.gen_maps([[0.5, 0.5, 0.5]], [[0.0, 0.0, 1.0]], H, W, WHITE, light=light, D=2, u=u,
+                           want_margin=True)
+    np.testing.assert_array_equal(a, b)
+    _, m0 = oracle.gen_maps([[0.5, 0.5, 0.5]], [[0.0, 0.0, 1.0]], H, W, WHITE, D=0, want_margin=True)
+    assert np.all(m0[0, 2:] < 1.0)   # polar angles 56.25 and 78.75 degrees
+    assert np.all(m0[0, :2] > 100.0)  # 11.25 and 33.75 degrees: the ceiling first
+    assert np.all(m <= m0)            # longer paths only add decisions
