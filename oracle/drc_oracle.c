@@ -884,8 +884,11 @@ typedef struct {
  * units of the float32 error the values may carry after a few bounces --
  * the gap from the nearest surface to the next one along the ray (units
  * 1e-5), the hit's distance to the ceiling light's border (1e-5), a sphere's
- * B^2 - C at a grazing ray (1e-6) and, for the next bounce's frame, |n_z| of
- * a sphere normal against 1 - 1e-6 (2e-6). */
+ * B^2 - C at a grazing ray (1e-4: near tangency the hit point moves by
+ * about the error of B^2 - C over its square root, so the distance and
+ * normal are ill-conditioned there, not only the hit-or-miss decision) and,
+ * for the next bounce's frame, |n_z| of a sphere normal against 1 - 1e-6
+ * (2e-6). */
 static int scene_hit(const orc_scene *sc, const double o[3], const double d[3], double *th, double nh[3],
                      double alb[3], double em[3], double *mg)
 {
@@ -913,7 +916,7 @@ static int scene_hit(const orc_scene *sc, const double o[3], const double d[3], 
         const double C = oc[0] * oc[0] + oc[1] * oc[1] + oc[2] * oc[2] - sp[3] * sp[3];
         const double disc = B * B - C;
         if (mg && C > 0.0 && B < 0.0)
-            margin_min(mg, disc, 1e-6);
+            margin_min(mg, disc, 1e-4);
         if (C <= 0.0 || disc < 0.0)
             continue; /* seen from outside only */
         const double t = -B - sqrt(disc);

@@ -74,12 +74,17 @@ __device__ __forceinline__ bool gen_hit(const drc_scene &sc, float3 o, float3 d,
       }
     }
   }
+  // Spheres: with oc = o - centre and B = oc . d, the ray meets the sphere at
+  // t = -B - sqrt(r^2 - |oc - B d|^2): the discriminant written through the
+  // ray's closest approach, |oc - B d|, rather than as B^2 - (|oc|^2 - r^2),
+  // which in float32 cancels badly for grazing rays.
   for (int s = 0; s < sc.nsph; ++s) {
     const float *sp = sc.sph[s];
     const float ox = o.x - sp[0], oy = o.y - sp[1], oz = o.z - sp[2];
     const float B = ox * d.x + oy * d.y + oz * d.z;
     const float C = ox * ox + oy * oy + oz * oz - sp[3] * sp[3];
-    const float disc = B * B - C;
+    const float px = ox - B * d.x, py = oy - B * d.y, pz = oz - B * d.z;
+    const float disc = sp[3] * sp[3] - (px * px + py * py + pz * pz);
     if (C <= 0.f || disc < 0.f) continue;  // seen from outside only
     const float t = -B - sqrtf(disc);
     if (t > 1e-12f && t < best) {
@@ -104,7 +109,9 @@ __device__ __forceinline__ bool gen_hit(const drc_scene &sc, float3 o, float3 d,
     }
   } else {
     const float *sp = sc.sph[which - 6];
-    h.n = make_float3((hx - sp[0]) / sp[3], (hy - sp[1]) / sp[3], (hz - sp[2]) / sp[3]);
+    // hit - centre = oc + t d (no cancellation against the centre)
+    h.n = make_float3((o.x - sp[0] + best * d.x) / sp[3], (o.y - sp[1] + best * d.y) / sp[3],
+                      (o.z - sp[2] + best * d.z) / sp[3]);
     h.alb = make_float3(sp[4], sp[5], sp[6]);
     h.em = make_float3(0.f, 0.f, 0.f);
   }
