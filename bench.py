@@ -359,6 +359,86 @@ def measure_training_paper(drc, torch, dev, batch=32, pool=512, steps=40):
             "kernel_ms_per_step": {k: round(v, 4) for k, v in sorted(by.items(), key=lambda kv: -kv[1])}}
 
 
+def measure_mapgen_indirect(drc, torch, dev, steps=10, S=8, D=3):
+    """The steps around the denoiser at the benchmark's sizes: tracing the
+    4096 caches' 7 x 32 x 32 input maps in the analytic room (D bounces,
+    drc_gen_maps), and the indirect term of Eq. 3 at 1920 x 1080 from the
+    k = 16 nearest caches' maps by multiple importance sampling with S
+    samples per pixel (drc_indirect, emission and direct term composited).
+    Both are bound by HBM: the map tracer reads its uniforms (n H W D 8 B)
+    and writes the maps (n 7 H W 4 B); the estimator reads u (P S 16 B),
+    the neighbour lists and weights (P k 8 B), normal, albedo, emission and
+    direct light (P 48 B) and writes the image (P 12 B), besides gathering
+    map texels from L2."""
+    from paper_1910_02480_gb300 import synth
+    g = synth.gbuffer(IMG_W, IMG_H, seed=2)
+    c = synth.cache_grid(g, GRID, GRID)
+    n, P, k = GRID * GRID, IMG_W * IMG_H, K_NN
+    rng = np.random.default_rng(21)
+    pos = np.float32(0.02 + 0.96 * c["pos"].astype(np.float64))
+    alb = np.float32([[0.7, 0.2, 0.2], [0.2, 0.7, 0.2], [0.6, 0.6, 0.6], [0.6, 0.6, 0.5], [0.5, 0.5, 0.5],
+                      [0.8, 0.8, 0.8]])
+    scene = drc.make_scene(alb, np.full((6, 3), 0.05, np.float32), [0.3, 0.7, 0.35, 0.65, 8.0, 7.5, 6.0],
+                           [[0.3, 0.3, 0.25, 0.15, 0.9, 0.8, 0.3], [0.7, 0.6, 0.3, 0.2, 0.3, 0.5, 0.9]])
+    ctx = drc.Context(WIDTHS, synth.he_weights(WIDTHS, seed=0), precision="fp32")
+    pd = torch.from_numpy(pos).to(dev)
+    nd = torch.from_numpy(c["nrm"]).to(dev)
+    ud = torch.from_numpy(rng.uniform(size=(n, MAP_H, MAP_W, D, 2)).astype(np.float32)).to(dev)
+    maps = torch.empty((n, 7, MAP_H, MAP_W), device=dev)
+    gd = {"width": IMG_W, "height": IMG_H, "pos": torch.from_numpy(g["pos"]).to(dev),
+          "nrm": torch.from_numpy(g["nrm"]).to(dev)}
+    cd = {"pos": torch.from_numpy(c["pos"]).to(dev), "nrm": nd, "pix": torch.from_numpy(c["pix"]).to(dev),
+          "payload": torch.zeros((n, 3), device=dev)}
+    nbr = torch.empty((P, k), dtype=torch.int32, device=dev)
+    nw = torch.empty((P, k), dtype=torch.float32, device=dev)
+    ctx.interpolate(cd, gd, k, drc.METRIC_WORLD, drc.WP_INVERSE, drc.INTERP_IRRADIANCE,
+                    synth.world_radius(n), nbr_out=nbr, nbr_w=nw)
+    lin = torch.rand((n, 3, MAP_H, MAP_W), device=dev) * 2.0
+    uu = torch.rand((P, S, 4), device=dev)
+    albd = torch.rand((P, 3), device=dev) * 0.7 + 0.2
+    emit = torch.zeros((P, 3), device=dev)
+    direct = torch.rand((P, 3), device=dev)
+    out = torch.empty((P, 3), device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(steps):
+            flush.fill_(float(i))
+            a, b = _events(torch)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ms.append(a.elapsed_time(b))
+        return float(np.mean(ms))
+
+    gen_ms = timed(lambda: ctx.gen_maps(scene, pd, nd, MAP_H, MAP_W, u=ud, out=maps))
+    ind_ms = timed(lambda: ctx.indirect(lin, nd, gd["nrm"], IMG_W, IMG_H, nbr, nw, uu, albd, emit=emit,
+                                        direct=direct, out=out))
+    if ctx.status() != drc.OK:
+        raise RuntimeError("device status after map generation / indirect")
+    peak = json.load(open(PEAKS_FILE))["hbm_gbs"] if os.path.exists(PEAKS_FILE) else 6800.0
+    gen_bytes = n * MAP_H * MAP_W * (D * 8 + 7 * 4)
+    ind_bytes = P * (S * 16 + k * 8 + 48 + 12)
+    ctx.close()
+    return {"gen_maps": {"workload": "%d caches, 7x%dx%d maps, %d bounces, room of 6 walls + ceiling light + 2 "
+                                     "spheres" % (n, MAP_H, MAP_W, D),
+                         "ms": gen_ms, "maps_per_s": n / (gen_ms * 1e-3),
+                         "roofline": {"bound": "hbm", "achieved": gen_bytes / (gen_ms * 1e-3) / 1e9, "peak": peak,
+                                      "unit": "GB/s", "frac": gen_bytes / (gen_ms * 1e-3) / 1e9 / peak,
+                                      "algorithmic_bytes": gen_bytes}},
+            "indirect": {"workload": "%dx%d pixels, k=%d, S=%d samples (MIS env/BRDF), emission + direct "
+                                     "composited" % (IMG_W, IMG_H, k, S),
+                         "ms": ind_ms, "pixels_per_s": P / (ind_ms * 1e-3),
+                         "roofline": {"bound": "hbm", "achieved": ind_bytes / (ind_ms * 1e-3) / 1e9, "peak": peak,
+                                      "unit": "GB/s", "frac": ind_bytes / (ind_ms * 1e-3) / 1e9 / peak,
+                                      "algorithmic_bytes": ind_bytes}}}
+
+
 def unet_flops_per_map(base=64, levels=3, H=32, W=32, cin=7, cout=3):
     """Valid multiply-adds x 2 of the paper-form U-Net on one H x W map: a
     stride-1 3x3 layer with zero padding meets (3H - 2)(3W - 2) in-map taps
@@ -726,6 +806,7 @@ def main():
         extra("training_keep_activations", lambda: measure_training(drc, torch, dev, recompute=False))
         extra("training_paper_settings", lambda: measure_training_paper(drc, torch, dev))
         extra("paper_form_unet", lambda: measure_unet(drc, torch, dev))
+        extra("map_generation_and_indirect", lambda: measure_mapgen_indirect(drc, torch, dev))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         b = cpu_baseline(w, x, g, c, one_thread=True)
         b.pop("step_s", None)

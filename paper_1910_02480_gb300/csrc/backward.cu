@@ -207,16 +207,18 @@ __global__ void __launch_bounds__(256) head_bwd_kernel(const float *__restrict__
 // Tiles: 64 rows (m) x 64 columns (tap-major: col = 9-tap index x Qc + q) per
 // block, 16 pixels of K per step, 4 x 4 outputs per thread; each block sums
 // a range of pixels and adds its tile to dW with atomics (split K).
-// AccT = double (the FP32 path): the 16-pixel partial sums are added with
-// Kahan compensation and the block totals into an fp64 buffer -- L1
-// gradients carry random signs, so these sums cancel heavily and plain fp32
-// accumulation over thousands of pixels loses ~1e-4 of the result.
+// KAHAN (the FP32 path): the 16-pixel partial sums are added with Kahan
+// compensation, and each block writes its tile as (sum, -compensation)
+// pairs to part[split][element]; wgrad_reduce_kernel then adds the splits'
+// pairs in a fixed order, again compensated, into dW -- L1 gradients carry
+// random signs, so these sums cancel heavily and plain fp32 accumulation over
+// thousands of pixels loses ~1e-4 of the result.  Otherwise the tile goes
+// to dW with fp32 atomics.
 constexpr int WG_T = 64, WG_K = 16;
-template <typename ActR, typename ActQ, typename AccT>
+template <typename ActR, typename ActQ, bool KAHAN>
 __global__ void __launch_bounds__(256) wgrad_kernel(const ActR *__restrict__ R, const ActQ *__restrict__ Q, int N,
                                                     int Hb, int Wb, int Mr, int Qc, int Qraw, long long k_per_block,
-                                                    AccT *__restrict__ dW) {
-  constexpr bool KAHAN = sizeof(AccT) == 8;
+                                                    float *__restrict__ dW, float2 *__restrict__ part) {
   __shared__ float As[WG_K][WG_T + 4];
   __shared__ float Bs[WG_K][WG_T + 4];
   const int m0 = blockIdx.x * WG_T, c0 = blockIdx.y * WG_T;
@@ -294,7 +296,8 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const ActR *__restrict__ R, 
       const int tap = col / Qc, q = col - tap * Qc;
       if (q >= Qraw) continue;
       if constexpr (KAHAN)
-        atomicAdd(dW + ((size_t)m * Qraw + q) * 9 + tap, (double)acc[r][s] - (double)comp[r][s]);
+        part[(size_t)blockIdx.z * ((size_t)Mr * Qraw * 9) + ((size_t)m * Qraw + q) * 9 + tap] =
+            make_float2(acc[r][s], -comp[r][s]);
       else
         atomicAdd(dW + ((size_t)m * Qraw + q) * 9 + tap, acc[r][s]);
     }
@@ -305,13 +308,15 @@ __global__ void __launch_bounds__(256) wgrad_kernel(const ActR *__restrict__ R, 
 // 16-byte group of V channels over every L-th pixel of the block's range
 // (G = C / V groups side by side, L = 256 / G pixel lanes, four loads in
 // flight); the L partial rows are then added through shared memory and the
-// block total goes to db with one atomic per channel.  AccT = double (the
-// FP32 path): Kahan-compensated partial sums, totals in fp64.
-template <typename Act, typename AccT>
+// block total goes to db with one atomic per channel.  KAHAN (the FP32
+// path): Kahan-compensated partial sums, and each block's totals as
+// (sum, correction) pairs in part[block][channel], added over the blocks by
+// the compensated reduction.
+template <typename Act, bool KAHAN>
 __global__ void __launch_bounds__(256) colsum_kernel(const Act *__restrict__ T, long long npix, int C, int Craw,
-                                                     long long pix_per_block, AccT *__restrict__ db) {
+                                                     long long pix_per_block, float *__restrict__ db,
+                                                     float2 *__restrict__ part) {
   constexpr int V = 16 / sizeof(Act);
-  constexpr bool KAHAN = sizeof(AccT) == 8;
   extern __shared__ float cs_part[];  // [L][C] sums, then [L][C] compensations
   const int G = C / V, L = 256 / G;
   const int sub = threadIdx.x / G, g = threadIdx.x - sub * G;
@@ -367,19 +372,41 @@ __global__ void __launch_bounds__(256) colsum_kernel(const Act *__restrict__ T, 
   }
   __syncthreads();
   for (int c = threadIdx.x; c < Craw; c += blockDim.x) {
-    AccT t = 0;
-    for (int l = 0; l < L; ++l) {
-      t += (AccT)cs_part[l * C + c];
-      if constexpr (KAHAN) t -= (AccT)cs_part[(L + l) * C + c];
+    if constexpr (KAHAN) {
+      // the lanes' sums, Kahan-added, and their compensations, summed apart
+      float t = 0.f, tc = 0.f, low = 0.f;
+      for (int l = 0; l < L; ++l) {
+        const float y = cs_part[l * C + c] - tc;
+        const float u = t + y;
+        tc = (u - t) - y;
+        t = u;
+        low -= cs_part[(L + l) * C + c];
+      }
+      part[(size_t)blockIdx.x * Craw + c] = make_float2(t, low - tc);
+    } else {
+      float t = 0.f;
+      for (int l = 0; l < L; ++l) t += cs_part[l * C + c];
+      atomicAdd(db + c, t);
     }
-    atomicAdd(db + c, t);
   }
 }
 
-// dweights (fp32) = the fp64 accumulation buffer.
-__global__ void to_f32_kernel(const double *__restrict__ a, long long n, float *__restrict__ out) {
+// out[i] = sum over the S splits of the pairs part[s][i] = (sum, correction):
+// the sums Kahan-added in split order, the corrections summed apart and
+// added at the end.  Deterministic; overwrites out.
+__global__ void compensated_reduce_kernel(const float2 *__restrict__ part, long long n, int S, float *__restrict__ out) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (float)a[i];
+  if (i >= n) return;
+  float s = 0.f, c = 0.f, low = 0.f;
+  for (int k = 0; k < S; ++k) {
+    const float2 v = part[(size_t)k * n + i];
+    const float y = v.x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+    low += v.y;
+  }
+  out[i] = s + (low - c);
 }
 
 // Input gradient: NHWC16 (7 real channels) -> [N][7][H][W], through the log
@@ -438,72 +465,110 @@ cudaError_t launch_head_bwd(const float *g4, const float *Whead, const void *mas
   return cudaGetLastError();
 }
 
-template <typename AccT>
-cudaError_t wgrad_dispatch(const void *R, bool r_bf16, const void *Q, bool q_bf16, int N, int Hb, int Wb, int Mr,
-                           int Qc, int Qraw, AccT *dW, int num_sms, cudaStream_t st) {
-  const long long K = (long long)N * Hb * Wb;
-  if (K == 0) return cudaSuccess;
-  const int gx = (Mr + WG_T - 1) / WG_T, gy = (9 * Qc + WG_T - 1) / WG_T;
-  // enough K splits for about four blocks per SM, at least 256 pixels each
+// Split-K shape of the SIMT weight gradient: enough K splits for about four
+// blocks per SM, at least 256 pixels each.
+static void wgrad_shape(long long K, int Mr, int Qc, int num_sms, int &gx, int &gy, long long &kpb, unsigned &gz) {
+  gx = (Mr + WG_T - 1) / WG_T;
+  gy = (9 * Qc + WG_T - 1) / WG_T;
   long long splits = (4ll * num_sms + gx * gy - 1) / (gx * gy);
   if (splits < 1) splits = 1;
-  long long kpb = (K + splits - 1) / splits;
+  kpb = (K + splits - 1) / splits;
   if (kpb < 256) kpb = 256;
   kpb = (kpb + WG_K - 1) / WG_K * WG_K;
-  const unsigned gz = (unsigned)((K + kpb - 1) / kpb);
+  gz = (unsigned)((K + kpb - 1) / kpb);
+}
+
+size_t wgrad_partial_elems(int N, int Hb, int Wb, int Mr, int Qc, int Qraw, int num_sms) {
+  const long long K = (long long)N * Hb * Wb;
+  if (K == 0) return 0;
+  int gx, gy;
+  long long kpb;
+  unsigned gz;
+  wgrad_shape(K, Mr, Qc, num_sms, gx, gy, kpb, gz);
+  return (size_t)gz * Mr * Qraw * 9;
+}
+
+template <bool KAHAN>
+static cudaError_t wgrad_dispatch(const void *R, bool r_bf16, const void *Q, bool q_bf16, int N, int Hb, int Wb,
+                                  int Mr, int Qc, int Qraw, float *dW, float2 *part, int num_sms, cudaStream_t st) {
+  const long long K = (long long)N * Hb * Wb;
+  if (K == 0) return cudaSuccess;
+  int gx, gy;
+  long long kpb;
+  unsigned gz;
+  wgrad_shape(K, Mr, Qc, num_sms, gx, gy, kpb, gz);
   const dim3 grid(gx, gy, gz);
   using bf = __nv_bfloat16;
   if (r_bf16 && q_bf16)
-    wgrad_kernel<bf, bf, AccT><<<grid, 256, 0, st>>>(static_cast<const bf *>(R), static_cast<const bf *>(Q), N, Hb,
-                                                     Wb, Mr, Qc, Qraw, kpb, dW);
+    wgrad_kernel<bf, bf, KAHAN><<<grid, 256, 0, st>>>(static_cast<const bf *>(R), static_cast<const bf *>(Q), N, Hb,
+                                                      Wb, Mr, Qc, Qraw, kpb, dW, part);
   else if (!r_bf16 && !q_bf16)
-    wgrad_kernel<float, float, AccT><<<grid, 256, 0, st>>>(static_cast<const float *>(R),
-                                                           static_cast<const float *>(Q), N, Hb, Wb, Mr, Qc, Qraw,
-                                                           kpb, dW);
+    wgrad_kernel<float, float, KAHAN><<<grid, 256, 0, st>>>(static_cast<const float *>(R),
+                                                            static_cast<const float *>(Q), N, Hb, Wb, Mr, Qc, Qraw,
+                                                            kpb, dW, part);
   else if (r_bf16)
-    wgrad_kernel<bf, float, AccT><<<grid, 256, 0, st>>>(static_cast<const bf *>(R), static_cast<const float *>(Q), N,
-                                                        Hb, Wb, Mr, Qc, Qraw, kpb, dW);
+    wgrad_kernel<bf, float, KAHAN><<<grid, 256, 0, st>>>(static_cast<const bf *>(R), static_cast<const float *>(Q), N,
+                                                         Hb, Wb, Mr, Qc, Qraw, kpb, dW, part);
   else
-    wgrad_kernel<float, bf, AccT><<<grid, 256, 0, st>>>(static_cast<const float *>(R), static_cast<const bf *>(Q), N,
-                                                        Hb, Wb, Mr, Qc, Qraw, kpb, dW);
+    wgrad_kernel<float, bf, KAHAN><<<grid, 256, 0, st>>>(static_cast<const float *>(R), static_cast<const bf *>(Q), N,
+                                                         Hb, Wb, Mr, Qc, Qraw, kpb, dW, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !KAHAN) return e;
+  const long long n = (long long)Mr * Qraw * 9;
+  compensated_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, n, (int)gz, dW);
   return cudaGetLastError();
 }
 
 cudaError_t launch_wgrad(const void *R, bool r_bf16, const void *Q, bool q_bf16, int N, int Hb, int Wb, int Mr,
-                         int Qc, int Qraw, float *dW, double *dW64, int num_sms, cudaStream_t st) {
-  return dW64 ? wgrad_dispatch<double>(R, r_bf16, Q, q_bf16, N, Hb, Wb, Mr, Qc, Qraw, dW64, num_sms, st)
-              : wgrad_dispatch<float>(R, r_bf16, Q, q_bf16, N, Hb, Wb, Mr, Qc, Qraw, dW, num_sms, st);
+                         int Qc, int Qraw, float *dW, float2 *part, int num_sms, cudaStream_t st) {
+  return part ? wgrad_dispatch<true>(R, r_bf16, Q, q_bf16, N, Hb, Wb, Mr, Qc, Qraw, dW, part, num_sms, st)
+              : wgrad_dispatch<false>(R, r_bf16, Q, q_bf16, N, Hb, Wb, Mr, Qc, Qraw, dW, nullptr, num_sms, st);
 }
 
-cudaError_t launch_colsum(const void *T, bool bf16, long long npix, int C, int Craw, float *db, double *db64,
+static void colsum_shape(long long npix, int C, bool bf16, int num_sms, int &L, long long &ppb, unsigned &blocks) {
+  const int V = bf16 ? 8 : 4;
+  L = 256 / (C / V);
+  ppb = (npix + 2ll * num_sms - 1) / (2ll * num_sms);
+  if (ppb < 4ll * L) ppb = 4ll * L;
+  blocks = (unsigned)((npix + ppb - 1) / ppb);
+}
+
+size_t colsum_partial_elems(long long npix, int C, int Craw, bool bf16, int num_sms) {
+  if (npix == 0) return 0;
+  int L;
+  long long ppb;
+  unsigned blocks;
+  colsum_shape(npix, C, bf16, num_sms, L, ppb, blocks);
+  return (size_t)blocks * Craw;
+}
+
+cudaError_t launch_colsum(const void *T, bool bf16, long long npix, int C, int Craw, float *db, float2 *part,
                           int num_sms, cudaStream_t st) {
   if (npix == 0) return cudaSuccess;
   const int V = bf16 ? 8 : 4;
   if (C % V || C / V > 256) return cudaErrorInvalidValue;
-  const int L = 256 / (C / V);
-  long long ppb = (npix + 2ll * num_sms - 1) / (2ll * num_sms);
-  if (ppb < 4ll * L) ppb = 4ll * L;
-  const unsigned blocks = (unsigned)((npix + ppb - 1) / ppb);
-  const size_t smem = (size_t)(db64 ? 2 : 1) * L * C * sizeof(float);
+  int L;
+  long long ppb;
+  unsigned blocks;
+  colsum_shape(npix, C, bf16, num_sms, L, ppb, blocks);
+  const size_t smem = (size_t)(part ? 2 : 1) * L * C * sizeof(float);
   using bf = __nv_bfloat16;
-  if (db64) {
+  if (part) {
     if (bf16)
-      colsum_kernel<bf, double><<<blocks, 256, smem, st>>>(static_cast<const bf *>(T), npix, C, Craw, ppb, db64);
+      colsum_kernel<bf, true><<<blocks, 256, smem, st>>>(static_cast<const bf *>(T), npix, C, Craw, ppb, db, part);
     else
-      colsum_kernel<float, double><<<blocks, 256, smem, st>>>(static_cast<const float *>(T), npix, C, Craw, ppb,
-                                                              db64);
+      colsum_kernel<float, true><<<blocks, 256, smem, st>>>(static_cast<const float *>(T), npix, C, Craw, ppb, db,
+                                                            part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    compensated_reduce_kernel<<<(unsigned)((Craw + 255) / 256), 256, 0, st>>>(part, Craw, (int)blocks, db);
   } else {
     if (bf16)
-      colsum_kernel<bf, float><<<blocks, 256, smem, st>>>(static_cast<const bf *>(T), npix, C, Craw, ppb, db);
+      colsum_kernel<bf, false><<<blocks, 256, smem, st>>>(static_cast<const bf *>(T), npix, C, Craw, ppb, db, nullptr);
     else
-      colsum_kernel<float, float><<<blocks, 256, smem, st>>>(static_cast<const float *>(T), npix, C, Craw, ppb, db);
+      colsum_kernel<float, false><<<blocks, 256, smem, st>>>(static_cast<const float *>(T), npix, C, Craw, ppb, db,
+                                                             nullptr);
   }
-  return cudaGetLastError();
-}
-
-cudaError_t launch_to_f32(const double *a, long long n, float *out, cudaStream_t st) {
-  if (n == 0) return cudaSuccess;
-  to_f32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a, n, out);
   return cudaGetLastError();
 }
 

@@ -800,8 +800,31 @@ struct TrainBufs {
   float *out = nullptr, *g4 = nullptr;    // network output [N][3][H][W]; dL/dout NHWC4
   void *g8 = nullptr;                     // BF16 contexts: dL/dout as bf16 NHWC8 (the head's weight gradient)
   uint8_t *dx16 = nullptr;                // input gradient NHWC16
-  double *dW64 = nullptr;                 // FP32 path: fp64 accumulation of the weight gradients
+  float2 *part = nullptr;                 // FP32 path: compensated split partials of the weight gradients
 };
+
+// Largest compensated-partials buffer (float2 elements) any weight or bias
+// gradient of drc_backward needs (FP32 path), with the shapes of its calls.
+size_t train_partial_elems(const drc_ctx *c, int N, int H, int W) {
+  const int S = c->cfg.num_stages, c1 = c->cfg.widths[0], ns = c->num_sms;
+  size_t m = 0;
+  auto take = [&](size_t v) { m = v > m ? v : m; };
+  const Layer &Lh = c->layers.back();
+  take(wgrad_partial_elems(N, H >> 1, W >> 1, c1, 4, 3, ns));
+  take(colsum_partial_elems((long long)N * H * W, 4, 3, false, ns));
+  (void)Lh;
+  for (int s2 = 2; s2 <= S; ++s2) {
+    const Layer &F = c->layers[(size_t)(2 * S - s2)];
+    take(wgrad_partial_elems(N, H >> s2, W >> s2, F.Cin, F.Cout, F.Cout, ns));
+    take(colsum_partial_elems((long long)N * (H >> (s2 - 1)) * (W >> (s2 - 1)), F.Cout, F.Cout, false, ns));
+  }
+  for (int s2 = S; s2 >= 1; --s2) {
+    const Layer &F = c->layers[(size_t)(s2 - 1)];
+    take(wgrad_partial_elems(N, H >> s2, W >> s2, F.Cout, F.Cin, F.Cin_raw, ns));
+    take(colsum_partial_elems((long long)N * (H >> s2) * (W >> s2), F.Cout, F.Cout, false, ns));
+  }
+  return m;
+}
 
 size_t train_layout(const drc_ctx *c, int N, int H, int W, bool recompute, void *base, TrainBufs *tb) {
   const int S = c->cfg.num_stages;
@@ -833,7 +856,7 @@ size_t train_layout(const drc_ctx *c, int N, int H, int W, bool recompute, void 
   b.g4 = reinterpret_cast<float *>(take((size_t)N * H * W * 4 * sizeof(float)));
   if (c->prec != PREC_TF32X3) b.g8 = take((size_t)N * H * W * 8 * 2);
   b.dx16 = take((size_t)N * H * W * 16 * eb);
-  if (c->prec == PREC_TF32X3) b.dW64 = reinterpret_cast<double *>(take(c->n_floats * sizeof(double)));
+  if (c->prec == PREC_TF32X3) b.part = reinterpret_cast<float2 *>(take(train_partial_elems(c, N, H, W) * sizeof(float2)));
   if (tb) *tb = b;
   return off;
 }
@@ -842,9 +865,9 @@ size_t train_layout(const drc_ctx *c, int N, int H, int W, bool recompute, void 
 // the tensor cores where both operands are BF16 and the shape fits
 // (wgrad_tc.cu), else the SIMT kernel (fp32 or compensated fp64 sums).
 cudaError_t weight_grad(const drc_ctx *c, const void *R, bool r_bf16, const void *Q, bool q_bf16, int N, int Hb,
-                        int Wb, int Mr, int Qc, int Qraw, float *dW, double *dW64, cudaStream_t st) {
+                        int Wb, int Mr, int Qc, int Qraw, float *dW, float2 *part, cudaStream_t st) {
   EncodeTiledFn enc = encode_tiled();
-  const int form = r_bf16 && q_bf16 && !dW64 && enc && N > 0 ? wgrad_tc_form(Hb, Wb, Mr, Qc) : WGRAD_TC_NONE;
+  const int form = r_bf16 && q_bf16 && !part && enc && N > 0 ? wgrad_tc_form(Hb, Wb, Mr, Qc) : WGRAD_TC_NONE;
   if (form != WGRAD_TC_NONE) {
     const bool narrow = form == WGRAD_TC_NARROW;
     WgradTcArgs a;
@@ -886,7 +909,7 @@ cudaError_t weight_grad(const drc_ctx *c, const void *R, bool r_bf16, const void
       return launch_wgrad_tc(a, form, c->num_sms, st);
     }
   }
-  return launch_wgrad(R, r_bf16, Q, q_bf16, N, Hb, Wb, Mr, Qc, Qraw, dW, dW64, c->num_sms, st);
+  return launch_wgrad(R, r_bf16, Q, q_bf16, N, Hb, Wb, Mr, Qc, Qraw, dW, part, c->num_sms, st);
 }
 
 // ConvArgs of layer L on explicit buffers (input Hin x Win, N maps).
@@ -1559,10 +1582,9 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
   Tracer *tr = &c->tracer;
   if ((e = cudaMemsetAsync(dweights, 0, c->n_floats * sizeof(float), st)) != cudaSuccess)
     return cuda_fail(c, e, "dweights clear");
-  if (b.dW64 && (e = cudaMemsetAsync(b.dW64, 0, c->n_floats * sizeof(double), st)) != cudaSuccess)
-    return cuda_fail(c, e, "dweights clear");
-  double *const w64 = b.dW64;
-  auto o64 = [&](size_t off) -> double * { return w64 ? w64 + off : nullptr; };
+  // FP32: compensated partials, reduced (deterministically) into dweights
+  float2 *const part = b.part;
+  auto opart = [&](size_t) -> float2 * { return part; };
   if (loss && (e = cudaMemsetAsync(loss, 0, sizeof(float), st)) != cudaSuccess) return cuda_fail(c, e, "loss clear");
 
   if ((s = train_forward(c, b, in, N, H, W, flags, false, st)) != DRC_OK) return s;
@@ -1581,10 +1603,10 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
   DRC_TRACED(tr, "wgrad head", st,
              e = weight_grad(c, S >= 2 ? b.t[1] : b.e[1], bf, bf ? b.g8 : (const void *)b.g4, bf, N, H >> 1, W >> 1,
                              c1, bf ? 8 : 4, 3,
-                              dweights + Lh.w_off, o64(Lh.w_off), st));
+                              dweights + Lh.w_off, opart(Lh.w_off), st));
   if (e == cudaSuccess)
     DRC_TRACED(tr, "bgrad head", st,
-               e = launch_colsum(b.g4, false, (long long)N * H * W, 4, 3, dweights + Lh.b_off, o64(Lh.b_off),
+               e = launch_colsum(b.g4, false, (long long)N * H * W, 4, 3, dweights + Lh.b_off, opart(Lh.b_off),
                                  c->num_sms, st));
   if (e != cudaSuccess) return cuda_fail(c, e, "head weight gradient");
 
@@ -1598,10 +1620,10 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
     const std::string wname = std::string("wgrad ") + F.name, bname = std::string("bgrad ") + F.name;
     DRC_TRACED(tr, wname.c_str(), st,
                e = weight_grad(c, tin, bf, b.gzd[s2 - 1], bf, N, H >> s2, W >> s2, F.Cin, F.Cout, F.Cout,
-                                dweights + F.w_off, o64(F.w_off), st));
+                                dweights + F.w_off, opart(F.w_off), st));
     if (e == cudaSuccess)
       DRC_TRACED(tr, bname.c_str(), st,
-                 e = launch_colsum(b.gzd[s2 - 1], bf, npix, F.Cout, F.Cout, dweights + F.b_off, o64(F.b_off),
+                 e = launch_colsum(b.gzd[s2 - 1], bf, npix, F.Cout, F.Cout, dweights + F.b_off, opart(F.b_off),
                                    c->num_sms, st));
     if (e != cudaSuccess) return cuda_fail(c, e, "decoder weight gradient");
     ConvArgs a;
@@ -1630,10 +1652,10 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
     const std::string wname = std::string("wgrad ") + F.name, bname = std::string("bgrad ") + F.name;
     DRC_TRACED(tr, wname.c_str(), st,
                e = weight_grad(c, b.gze[s2], bf, xin, bf, N, H >> s2, W >> s2, F.Cout, F.Cin, F.Cin_raw,
-                                dweights + F.w_off, o64(F.w_off), st));
+                                dweights + F.w_off, opart(F.w_off), st));
     if (e == cudaSuccess)
       DRC_TRACED(tr, bname.c_str(), st,
-                 e = launch_colsum(b.gze[s2], bf, npix, F.Cout, F.Cout, dweights + F.b_off, o64(F.b_off),
+                 e = launch_colsum(b.gze[s2], bf, npix, F.Cout, F.Cout, dweights + F.b_off, opart(F.b_off),
                                    c->num_sms, st));
     if (e != cudaSuccess) return cuda_fail(c, e, "encoder weight gradient");
     if (s2 == 1 && !dinput) break;
@@ -1644,10 +1666,6 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
     plan_operand(D.prec, a, -1);
     DRC_TRACED(tr, D.name, st, e = launch_conv(a, D.prec, c->num_sms, st));
     if (e != cudaSuccess) return cuda_fail(c, e, "encoder data gradient");
-  }
-  if (w64) {
-    DRC_TRACED(tr, "dweights f32", st, e = launch_to_f32(w64, (long long)c->n_floats, dweights, st));
-    if (e != cudaSuccess) return cuda_fail(c, e, "dweights");
   }
   if (dinput) {
     DRC_TRACED(tr, "input grad", st,
