@@ -273,6 +273,18 @@ typedef struct {
 drc_status drc_gen_maps(drc_ctx *ctx, const drc_scene *scene, int n, const float *pos, const float *nrm, int H,
                         int W, int D, const float *u, float *maps, void *stream);
 
+/* Test harness, not a hot path (the paper has no counterpart): the mean L1
+ * loss of the context's network (Sec. 3.3 network, Sec. 4 loss, the loss
+ * drc_backward differentiates with DRC_BWD_L1_TARGET) evaluated in FP64 on
+ * the GPU with the packed weights given in FP64, for central finite
+ * differences of drc_backward's gradient.  weights64: device [n_floats]
+ * double; in: device [N][7][H][W] float; target: device [N][3][H][W];
+ * flags: DRC_F_ENCODE_INPUT or 0; loss64: device double, written.
+ * Allocates its own scratch and synchronises `stream` (slow, direct loops).
+ * INVALID_ARG for shapes drc_backward refuses. */
+drc_status drc_fd_loss64(drc_ctx *ctx, const double *weights64, const float *in, const float *target, int N, int H,
+                         int W, unsigned flags, double *loss64, void *stream);
+
 /* One frame end to end from host memory: drc_denoise of N maps, then
  * drc_interpolate (IRRADIANCE) of a G-buffer from their payloads, with the
  * uploads and the download inside the call (Sec. 3.3 denoising feeding the

@@ -142,6 +142,8 @@ def load_library():
     lib.drc_indirect.restype = I
     lib.drc_gen_maps.argtypes = [P, ctypes.POINTER(Scene), I, P, P, I, I, I, P, P, P]
     lib.drc_gen_maps.restype = I
+    lib.drc_fd_loss64.argtypes = [P, P, P, P, I, I, I, U, P, P]
+    lib.drc_fd_loss64.restype = I
     lib.drc_backward.argtypes = [P, P, P, I, I, I, U, P, P, P, P]
     lib.drc_backward.restype = I
     lib.drc_frame_host.argtypes = [P, P, I, I, I, U, ctypes.POINTER(Caches), ctypes.POINTER(GBuffer),
@@ -323,6 +325,17 @@ class Context:
                                        _ptr(out), _stream(stream))
         self._check(rc, "drc_interpolate")
         return out
+
+    def fd_loss64(self, weights64, x, target, flags=0, stream=None):
+        """drc_fd_loss64 (test harness): the mean L1 loss in FP64 on the GPU
+        for cuda float64 packed weights; returns a cuda float64 scalar."""
+        import torch
+        N, _, H, W = x.shape
+        loss = torch.empty((), dtype=torch.float64, device=x.device)
+        rc = self._lib.drc_fd_loss64(self._ctx, _ptr(weights64), _ptr(x), _ptr(target), N, H, W, flags, _ptr(loss),
+                                     _stream(stream))
+        self._check(rc, "drc_fd_loss64")
+        return loss
 
     def gen_maps(self, scene, pos, nrm, H, W, u=None, out=None, stream=None):
         """drc_gen_maps: maps [n,7,H,W] traced from cache points pos / nrm

@@ -16,6 +16,7 @@
 #include "backward.cuh"
 #include "conv_tc.cuh"
 #include "drc.h"
+#include "fd_harness.cuh"
 #include "head.cuh"
 #include "drc_status.cuh"
 #include "indirect.cuh"
@@ -1539,6 +1540,36 @@ drc_status drc_gen_maps(drc_ctx *c, const drc_scene *scene, int n, const float *
   cudaError_t e = launch_gen_maps(a, static_cast<cudaStream_t>(stream), &c->tracer);
   if (e != cudaSuccess) return cuda_fail(c, e, "map generation launch");
   return DRC_OK;
+}
+
+drc_status drc_fd_loss64(drc_ctx *c, const double *w64, const float *in, const float *target, int N, int H, int W,
+                         unsigned flags, double *loss64, void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  const int S = c->cfg.num_stages;
+  if (flags & ~DRC_F_ENCODE_INPUT) return fail(c, DRC_ERR_INVALID_ARG, "flags: DRC_F_ENCODE_INPUT or 0");
+  if (N < 1) return fail(c, DRC_ERR_INVALID_ARG, "N must be >= 1");
+  if (H < (1 << S) || W < (1 << S) || H % (1 << S) || W % (1 << S))
+    return fail(c, DRC_ERR_INVALID_ARG, "H, W (%d, %d) must be positive multiples of 2^S = %d", H, W, 1 << S);
+  if ((long long)N * H * W * 16 >= (1ll << 31)) return fail(c, DRC_ERR_INVALID_ARG, "too large");
+  drc_status s;
+  if ((s = check_dev(c, w64, "weights64", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, in, "in", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, target, "target", false)) != DRC_OK) return s;
+  if ((s = check_dev(c, loss64, "loss64", false)) != DRC_OK) return s;
+  std::vector<FdLayer> L(c->layers.size());
+  for (size_t i = 0; i < c->layers.size(); ++i) {
+    const Layer &l = c->layers[i];
+    L[i].transposed = l.kind == LK_CONV ? 0 : 1;
+    L[i].Cin = l.kind == LK_CONV ? l.Cin_raw : l.Cin;
+    L[i].Cout = l.Cout;
+    L[i].w_off = l.w_off;
+    L[i].b_off = l.b_off;
+  }
+  cudaError_t e = fd_loss64(L.data(), S, w64, in, target, N, c->cfg.in_channels, H, W,
+                            (flags & DRC_F_ENCODE_INPUT) != 0, c->cfg.exposure, c->cfg.out_relu != 0, loss64,
+                            static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? DRC_OK : cuda_fail(c, e, "fd loss");
 }
 
 drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N, int H, int W, unsigned flags,
