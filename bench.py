@@ -439,6 +439,78 @@ def measure_mapgen_indirect(drc, torch, dev, steps=10, S=8, D=3):
                                       "algorithmic_bytes": ind_bytes}}}
 
 
+def measure_progressive(drc, torch, dev, spacing0=64, passes=4, k=8, S=4, D=3):
+    """Progressive refinement (Sec. 3.2) through every GPU step of the
+    method, per pass on a 1920 x 1080 G-buffer: the pass's new image-plane
+    sample points (drc_pass_points, grid spacing halving from 64 pixels),
+    their 7 x 32 x 32 input maps traced in the analytic room (drc_gen_maps,
+    D bounces), denoised by the benchmark network (log encode in, linear
+    radiance out), the interpolation over every cache so far in the image
+    plane (r = the pass's spacing) giving each pixel's k caches and weights,
+    and the indirect term by multiple importance sampling (S samples)
+    composited with a direct term (drc_indirect).  Times each pass on the
+    device; the point lists are uploaded before the timed region."""
+    from paper_1910_02480_gb300 import synth
+    g = synth.gbuffer(IMG_W, IMG_H, seed=2)
+    P = IMG_W * IMG_H
+    pos_img = torch.from_numpy(np.float32(0.02 + 0.96 * g["pos"].astype(np.float64))).to(dev)
+    nrm_img = torch.from_numpy(g["nrm"]).to(dev)
+    gd = {"width": IMG_W, "height": IMG_H, "pos": pos_img, "nrm": nrm_img}
+    alb = np.float32([[0.7, 0.2, 0.2], [0.2, 0.7, 0.2], [0.6, 0.6, 0.6], [0.6, 0.6, 0.5], [0.5, 0.5, 0.5],
+                      [0.8, 0.8, 0.8]])
+    scene = drc.make_scene(alb, np.full((6, 3), 0.05, np.float32), [0.3, 0.7, 0.35, 0.65, 8.0, 7.5, 6.0])
+    ctx = drc.Context(WIDTHS, synth.he_weights(WIDTHS, seed=0), precision="fp32")
+    pts = [torch.from_numpy(drc.pass_points(IMG_W, IMG_H, spacing0, t)).to(dev) for t in range(passes)]
+    total = sum(int(p_.shape[0]) for p_ in pts)
+    u_gen = torch.rand((total, MAP_H, MAP_W, D, 2), device=dev)
+    u_ind = torch.rand((P, S, 4), device=dev)
+    albd = torch.rand((P, 3), device=dev) * 0.7 + 0.2
+    direct = torch.rand((P, 3), device=dev)
+    maps7 = torch.empty((total, 7, MAP_H, MAP_W), device=dev)
+    lin = torch.empty((total, 3, MAP_H, MAP_W), device=dev)
+    pay = torch.empty((total, 3), device=dev)
+    nbr = torch.empty((P, k), dtype=torch.int32, device=dev)
+    nw = torch.empty((P, k), dtype=torch.float32, device=dev)
+    img = torch.empty((P, 3), device=dev)
+    pix_all = torch.cat(pts).contiguous()
+    idx_all = (pix_all[:, 1].long() * IMG_W + pix_all[:, 0].long())
+    cpos_all = pos_img[idx_all].contiguous()
+    cnrm_all = nrm_img[idx_all].contiguous()
+
+    def run_pass(t, n0, n1):
+        ctx.gen_maps(scene, cpos_all[n0:n1], cnrm_all[n0:n1], MAP_H, MAP_W, u=u_gen[n0:n1], out=maps7[n0:n1])
+        ctx.denoise(maps7[n0:n1], out=lin[n0:n1], payload=pay[n0:n1],
+                    flags=drc.F_ENCODE_INPUT | drc.F_DECODE_OUTPUT)
+        cd = {"pos": cpos_all[:n1], "nrm": cnrm_all[:n1], "pix": pix_all[:n1], "payload": pay[:n1]}
+        ctx.interpolate(cd, gd, k, drc.METRIC_IMAGE, drc.WP_INVERSE, drc.INTERP_IRRADIANCE,
+                        float(spacing0 >> t), nbr_out=nbr, nbr_w=nw)
+        ctx.indirect(lin[:n1], cnrm_all[:n1], nrm_img, IMG_W, IMG_H, nbr, nw, u_ind, albd, direct=direct, out=img)
+
+    bounds, n0 = [], 0
+    for p_ in pts:
+        bounds.append((n0, n0 + int(p_.shape[0])))
+        n0 += int(p_.shape[0])
+    for t, (a0, a1) in enumerate(bounds):  # warm-up of every pass shape
+        run_pass(t, a0, a1)
+    torch.cuda.synchronize()
+    per = []
+    for t, (a0, a1) in enumerate(bounds):
+        ev = _events(torch)
+        ev[0].record()
+        run_pass(t, a0, a1)
+        ev[1].record()
+        torch.cuda.synchronize()
+        per.append(ev[0].elapsed_time(ev[1]))
+    if ctx.status() != drc.OK:
+        raise RuntimeError("device status after the progressive passes")
+    ctx.close()
+    return {"workload": "%dx%d, grid spacing %d halving over %d passes, 7x%dx%d maps (%d bounces), k=%d IMAGE "
+                        "metric, S=%d MIS samples, direct term composited" % (IMG_W, IMG_H, spacing0, passes,
+                                                                             MAP_H, MAP_W, D, k, S),
+            "new_caches_per_pass": [b - a for a, b in bounds], "caches_total": total,
+            "ms_per_pass": [round(v, 4) for v in per], "ms_total": float(sum(per))}
+
+
 def unet_flops_per_map(base=64, levels=3, H=32, W=32, cin=7, cout=3):
     """Valid multiply-adds x 2 of the paper-form U-Net on one H x W map: a
     stride-1 3x3 layer with zero padding meets (3H - 2)(3W - 2) in-map taps
@@ -807,6 +879,7 @@ def main():
         extra("training_paper_settings", lambda: measure_training_paper(drc, torch, dev))
         extra("paper_form_unet", lambda: measure_unet(drc, torch, dev))
         extra("map_generation_and_indirect", lambda: measure_mapgen_indirect(drc, torch, dev))
+        extra("progressive_passes", lambda: measure_progressive(drc, torch, dev))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         b = cpu_baseline(w, x, g, c, one_thread=True)
         b.pop("step_s", None)

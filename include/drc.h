@@ -285,6 +285,21 @@ drc_status drc_gen_maps(drc_ctx *ctx, const drc_scene *scene, int n, const float
 drc_status drc_fd_loss64(drc_ctx *ctx, const double *weights64, const float *in, const float *target, int N, int H,
                          int W, unsigned flags, double *loss64, void *stream);
 
+/* Progressive refinement (Sec. 3.2): the image-plane sample points of pass
+ * `pass` (0, 1, ...).  After each pass the distance between grid points is
+ * reduced by a constant factor, here 2 (a reading: the factor is not
+ * printed); points already evaluated are kept, so pass 0 takes the pixels
+ * (x, y) with x and y multiples of s0 = spacing0, and pass t > 0 those that
+ * are multiples of s_t = spacing0 / 2^t but not both multiples of s_{t-1}.
+ * The interpolation after pass t uses every point so far with
+ * r = s_t (the distance between two grid points).  Host-only, no GPU.
+ * pix: host [max_points][2] int32 (x, y), row-major order of (y, x); *count
+ * receives the number of points (written even when they do not fit, in
+ * which case INVALID_ARG is returned and pix is left partial).  spacing0
+ * must be a power of two; once s_t would drop below 1 a pass has no points.
+ * INVALID_ARG for width or height < 1, pass < 0, NULL count. */
+drc_status drc_pass_points(int width, int height, int spacing0, int pass, int *pix, int max_points, int *count);
+
 /* One frame end to end from host memory: drc_denoise of N maps, then
  * drc_interpolate (IRRADIANCE) of a G-buffer from their payloads, with the
  * uploads and the download inside the call (Sec. 3.3 denoising feeding the

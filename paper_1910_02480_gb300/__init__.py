@@ -144,6 +144,8 @@ def load_library():
     lib.drc_gen_maps.restype = I
     lib.drc_fd_loss64.argtypes = [P, P, P, P, I, I, I, U, P, P]
     lib.drc_fd_loss64.restype = I
+    lib.drc_pass_points.argtypes = [I, I, I, I, P, I, ctypes.POINTER(I)]
+    lib.drc_pass_points.restype = I
     lib.drc_backward.argtypes = [P, P, P, I, I, I, U, P, P, P, P]
     lib.drc_backward.restype = I
     lib.drc_frame_host.argtypes = [P, P, I, I, I, U, ctypes.POINTER(Caches), ctypes.POINTER(GBuffer),
@@ -223,6 +225,23 @@ def _stream(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def pass_points(width, height, spacing0, pass_):
+    """drc_pass_points: the image-plane sample points (int32 [n, 2], x, y)
+    of progressive pass `pass_` on grids halving from spacing0 (Sec. 3.2)."""
+    import numpy as np
+    lib = load_library()
+    cnt = ctypes.c_int(0)
+    rc = lib.drc_pass_points(int(width), int(height), int(spacing0), int(pass_), None, 0, ctypes.byref(cnt))
+    if rc not in (OK, ERR_INVALID_ARG):
+        raise DrcError("drc_pass_points: %s" % STATUS_NAMES.get(rc, rc))
+    pix = np.zeros((max(cnt.value, 1), 2), dtype=np.int32)
+    rc = lib.drc_pass_points(int(width), int(height), int(spacing0), int(pass_),
+                             pix.ctypes.data_as(ctypes.c_void_p), cnt.value, ctypes.byref(cnt))
+    if rc != OK:
+        raise DrcError("drc_pass_points: %s" % STATUS_NAMES.get(rc, rc))
+    return pix[:cnt.value]
 
 
 class Context:

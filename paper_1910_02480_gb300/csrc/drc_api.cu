@@ -1572,6 +1572,30 @@ drc_status drc_fd_loss64(drc_ctx *c, const double *w64, const float *in, const f
   return e == cudaSuccess ? DRC_OK : cuda_fail(c, e, "fd loss");
 }
 
+drc_status drc_pass_points(int width, int height, int spacing0, int pass, int *pix, int max_points, int *count) {
+  if (!count || width < 1 || height < 1 || pass < 0 || spacing0 < 1 || (spacing0 & (spacing0 - 1)) || max_points < 0)
+    return DRC_ERR_INVALID_ARG;
+  *count = 0;
+  if (pass > 30 || (spacing0 >> pass) < 1) return DRC_OK;  // the grid cannot get finer than every pixel
+  const int st = spacing0 >> pass, prev = pass > 0 ? st * 2 : 0;
+  long long n = 0;
+  bool fits = true;
+  for (int y = 0; y < height; y += st)
+    for (int x = 0; x < width; x += st) {
+      if (prev && x % prev == 0 && y % prev == 0) continue;  // an earlier pass's point
+      if (n < max_points && pix) {
+        pix[2 * n] = x;
+        pix[2 * n + 1] = y;
+      } else {
+        fits = false;
+      }
+      ++n;
+    }
+  if (n > 0x7fffffff) return DRC_ERR_INVALID_ARG;
+  *count = (int)n;
+  return fits ? DRC_OK : DRC_ERR_INVALID_ARG;
+}
+
 drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N, int H, int W, unsigned flags,
                         float *dweights, float *dinput, float *loss, void *stream) {
   if (!c) return DRC_ERR_INVALID_ARG;
