@@ -468,7 +468,7 @@ def measure_progressive(drc, torch, dev, spacing0=64, passes=4, k=8, S=4, D=3):
     direct = torch.rand((P, 3), device=dev)
     maps7 = torch.empty((total, 7, MAP_H, MAP_W), device=dev)
     lin = torch.empty((total, 3, MAP_H, MAP_W), device=dev)
-    pay = torch.empty((total, 3), device=dev)
+    pay = torch.zeros((total, 3), device=dev)  # the blend's payloads are not used: the MIS reads the maps
     nbr = torch.empty((P, k), dtype=torch.int32, device=dev)
     nw = torch.empty((P, k), dtype=torch.float32, device=dev)
     img = torch.empty((P, 3), device=dev)
@@ -477,10 +477,18 @@ def measure_progressive(drc, torch, dev, spacing0=64, passes=4, k=8, S=4, D=3):
     cpos_all = pos_img[idx_all].contiguous()
     cnrm_all = nrm_img[idx_all].contiguous()
 
+    # per pass, 16-byte aligned copies of the new caches' points (a slice of an
+    # [n, 3] array is not)
+    cpos_new = [cpos_all[a0:a1].clone() for a0, a1 in
+                [(sum(int(q.shape[0]) for q in pts[:t]), sum(int(q.shape[0]) for q in pts[:t + 1]))
+                 for t in range(passes)]]
+    cnrm_new = [cnrm_all[a0:a1].clone() for a0, a1 in
+                [(sum(int(q.shape[0]) for q in pts[:t]), sum(int(q.shape[0]) for q in pts[:t + 1]))
+                 for t in range(passes)]]
+
     def run_pass(t, n0, n1):
-        ctx.gen_maps(scene, cpos_all[n0:n1], cnrm_all[n0:n1], MAP_H, MAP_W, u=u_gen[n0:n1], out=maps7[n0:n1])
-        ctx.denoise(maps7[n0:n1], out=lin[n0:n1], payload=pay[n0:n1],
-                    flags=drc.F_ENCODE_INPUT | drc.F_DECODE_OUTPUT)
+        ctx.gen_maps(scene, cpos_new[t], cnrm_new[t], MAP_H, MAP_W, u=u_gen[n0:n1], out=maps7[n0:n1])
+        ctx.denoise(maps7[n0:n1], out=lin[n0:n1], flags=drc.F_ENCODE_INPUT | drc.F_DECODE_OUTPUT)
         cd = {"pos": cpos_all[:n1], "nrm": cnrm_all[:n1], "pix": pix_all[:n1], "payload": pay[:n1]}
         ctx.interpolate(cd, gd, k, drc.METRIC_IMAGE, drc.WP_INVERSE, drc.INTERP_IRRADIANCE,
                         float(spacing0 >> t), nbr_out=nbr, nbr_w=nw)

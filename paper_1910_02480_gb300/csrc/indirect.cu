@@ -100,6 +100,10 @@ __global__ void __launch_bounds__(SETUP_THREADS) indirect_setup_kernel(const __g
   }
 }
 
+// KMAX >= k: the pixel's neighbour list and weights are read once into
+// registers (loops over them are unrolled to KMAX with i < k guards), so a
+// sample's map choice costs no memory access.
+template <int KMAX>
 __global__ void __launch_bounds__(IND_THREADS) indirect_kernel(const __grid_constant__ IndirectArgs a) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= a.P) return;
@@ -114,17 +118,32 @@ __global__ void __launch_bounds__(IND_THREADS) indirect_kernel(const __grid_cons
   const float n_env = (float)((a.S + 1) / 2), n_brdf = (float)(a.S / 2);
   const int *nb = a.nbr + p * a.k;
   const float *wb = a.nbr_w + p * a.k;
+  int jn[KMAX];
+  float wn[KMAX];
+#pragma unroll
+  for (int i = 0; i < KMAX; ++i) {
+    jn[i] = -1;
+    wn[i] = 0.f;
+    if (i < a.k) {
+      const int ji = __ldg(nb + i);
+      jn[i] = ji >= 0 && ji < a.n ? ji : -1;  // no neighbour (an index past n is treated alike)
+      wn[i] = __ldg(wb + i);
+    }
+  }
   for (int s = 0; pix_ok && s < a.S; ++s) {
     const float4 us = __ldg(a.u + p * a.S + s);
-    // the map, by the normalised weights (their running float32 sum)
+    // the map, by the normalised weights (their running float32 sum): the
+    // first valid slot whose running sum exceeds u0, else the last valid one
     int j = -1;
     float c = 0.f;
-    for (int i = 0; i < a.k; ++i) {
-      const int ji = __ldg(nb + i);
-      if (ji < 0 || ji >= a.n) continue;  // no neighbour (an index past n is treated alike)
-      j = ji;
-      c = __fadd_rn(c, __ldg(wb + i));
-      if (us.x < c) break;
+    bool done = false;
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {
+      if (!done && jn[i] >= 0) {
+        j = jn[i];
+        c = __fadd_rn(c, wn[i]);
+        done = us.x < c;
+      }
     }
     if (j < 0) continue;
     const float4 f2 = __ldg(a.frame + 3 * j + 2);
@@ -206,7 +225,12 @@ cudaError_t launch_indirect(const IndirectArgs &a, cudaStream_t st, Tracer *tr) 
                (indirect_setup_kernel<<<(a.n + SETUP_THREADS - 1) / SETUP_THREADS, SETUP_THREADS, 0, st>>>(a)));
   if (a.P > 0) {
     const unsigned blocks = (unsigned)((a.P + IND_THREADS - 1) / IND_THREADS);
-    DRC_TRACED(tr, "indirect estimate", st, (indirect_kernel<<<blocks, IND_THREADS, 0, st>>>(a)));
+    if (a.k <= 8)
+      DRC_TRACED(tr, "indirect estimate", st, (indirect_kernel<8><<<blocks, IND_THREADS, 0, st>>>(a)));
+    else if (a.k <= 16)
+      DRC_TRACED(tr, "indirect estimate", st, (indirect_kernel<16><<<blocks, IND_THREADS, 0, st>>>(a)));
+    else
+      DRC_TRACED(tr, "indirect estimate", st, (indirect_kernel<32><<<blocks, IND_THREADS, 0, st>>>(a)));
   }
   return cudaGetLastError();
 }
