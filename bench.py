@@ -164,6 +164,9 @@ def measure_precision(drc, torch, dev, prec, fp32_denoise_ms, autotune=True, ste
     for _ in range(3):
         ctx.denoise(xd, out=out, payload=pay)
     ms = []
+    torch.cuda.synchronize()
+    ctx.read_timing()
+    ctx.set_timing(True)
     for i in range(steps):
         flush.fill_(float(i))
         a, b = _events(torch)
@@ -172,9 +175,28 @@ def measure_precision(drc, torch, dev, prec, fp32_denoise_ms, autotune=True, ste
         b.record()
         torch.cuda.synchronize()
         ms.append(a.elapsed_time(b))
+    ctx.set_timing(False)
+    kt = ctx.read_timing()
     if ctx.status() != drc.OK:
         raise RuntimeError("device status after %s timing" % prec)
     den = float(np.mean(ms))
+    # the tensor-core conv kernel's roofline at this precision: valid-tap
+    # FLOPs over its launches' device time; peaks: the measured bf16 burst,
+    # and for e4m3 that times the nominal fp8 : bf16 ratio (4.5 / 2.25)
+    layer_macs = valid_macs_per_layer(WIDTHS, MAP_H, MAP_W)
+    conv_names = [n for n in layer_macs if n.startswith("conv")]
+    conv_flops = 2.0 * sum(layer_macs[n] for n in conv_names) * N_MAPS
+    conv_ms = sum(kt[n][1] for n in conv_names if n in kt) / steps
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else None
+    bf16_peak = peaks["bf16_tflops"] if peaks else 1900.0
+    peak = bf16_peak * (2.0 if prec == "fp8" else 1.0)
+    achieved = conv_flops / (conv_ms * 1e-3) / 1e12 if conv_ms > 0 else None
+    roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak if achieved else None, "kernel_ms_per_call": conv_ms,
+            "kernel_ms_per_layer": {n: kt[n][1] / steps for n in conv_names if n in kt},
+            "peak_source": ("of measured: bf16 burst %.1f TF/s" % bf16_peak if prec == "bf16" else
+                            "of measured: bf16 burst %.1f TF/s x nominal e4m3/bf16 2" % bf16_peak)
+            if peaks else "of fallback"}
     # error sample: 16 maps of the HDR field, log1p-encoded radiance in
     xs, _ = synth.hemisphere_maps(g["pos"][:16], g["nrm"][:16], H=MAP_H, W=MAP_W, lobe=lobe, seed=5)
     xs = np.ascontiguousarray(xs, dtype=np.float32)
@@ -189,7 +211,7 @@ def measure_precision(drc, torch, dev, prec, fp32_denoise_ms, autotune=True, ste
         err[name] = {"max_rel": float(np.max(np.abs(gv - rv) / den_)),
                      "normwise": float(np.linalg.norm(gv - rv) / np.linalg.norm(rv))}
     ctx.close()
-    return {"denoise_ms": den, "denoise_maps_per_s": N_MAPS / (den * 1e-3),
+    return {"denoise_ms": den, "denoise_maps_per_s": N_MAPS / (den * 1e-3), "roofline": roof,
             "speedup_vs_fp32_denoise": fp32_denoise_ms / den, "error_vs_oracle": err,
             "error_sample": "16 maps 7x32x32, lobes log-uniform 1e-3..1e3, FP64 oracle",
             "calibration": cal_note}
