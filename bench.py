@@ -556,37 +556,81 @@ def unet_flops_per_map(base=64, levels=3, H=32, W=32, cin=7, cout=3):
     return flops + 2.0 * H * W * base * cout
 
 
-def measure_unet(drc, torch, dev, N=256, steps=10):
+def unet_layer_flops(base=64, levels=3, H=32, W=32, cin=7):
+    """Valid FLOPs per map of each 3x3 layer of the paper-form U-Net, keyed by
+    the name the library traces its launch under ("unet conv i", i in
+    execution order: two per encoder level, two per decoder level)."""
+    out, i = {}, 0
+    for lvl in range(levels + 1):
+        h, w, c = H >> lvl, W >> lvl, base << lvl
+        ci = cin if lvl == 0 else base << (lvl - 1)
+        for a, b in ((ci, c), (c, c)):
+            out["unet conv %d" % i] = 2.0 * (3 * h - 2) * (3 * w - 2) * a * b
+            i += 1
+    for lvl in range(levels - 1, -1, -1):
+        h, w, c = H >> lvl, W >> lvl, base << lvl
+        for a, b in ((3 * c, c), (c, c)):
+            out["unet conv %d" % i] = 2.0 * (3 * h - 2) * (3 * w - 2) * a * b
+            i += 1
+    return out
+
+
+def measure_unet(drc, torch, dev, N=4096, steps=5):
     """The paper's own network form (Sec. 3.3: a U-Net, base 64, three
-    downsizing steps, 7.8 M parameters), FP32 on the CUDA cores, on 256
-    synthetic 7 x 32 x 32 maps.  Bound by FP32 FMA issue: the peak is 152 SMs
-    x 128 lanes x 2 FLOP at the 2070 MHz maximum clock."""
+    downsizing steps, 7.8 M parameters) in FP32 on 4096 synthetic 7 x 32 x 32
+    maps: its 3x3 layers on the tensor cores (split-tf32 implicit GEMMs of the
+    conv kernel family).  One step is the whole forward call: BN folding and
+    weight packing, input staging, 16 convolutions, pooling, upsampling, the
+    head.  Activations (about 12 GB) are far larger than L2."""
     from paper_1910_02480_gb300 import synth
     g = synth.gbuffer(N, 1, seed=18)
     x, _ = synth.hemisphere_maps(g["pos"], g["nrm"], H=32, W=32, seed=19)
     xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev)
     ctx = drc.Context([16], synth.he_weights([16]), precision="fp32")
     net = drc.UNet(ctx, synth.unet_params(64, 3, seed=0), 64, 3)
+    out = torch.empty((N, 3, 32, 32), device=dev)
     for _ in range(3):
-        net.forward(xd)
+        net.forward(xd, out=out)
     torch.cuda.synchronize()
-    a, b = _events(torch)
-    a.record()
+    ctx.read_timing()
+    ctx.set_timing(True)
+    ms = []
     for _ in range(steps):
-        net.forward(xd)
-    b.record()
-    torch.cuda.synchronize()
+        a, b = _events(torch)
+        a.record()
+        net.forward(xd, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    ctx.set_timing(False)
+    kt = ctx.read_timing()
     if ctx.status() != drc.OK:
         raise RuntimeError("device status after the U-Net")
-    ms = a.elapsed_time(b) / steps
-    fl = unet_flops_per_map() * N
-    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    ms = float(np.mean(ms))
+    lf = unet_layer_flops()
+    conv_flops = sum(lf.values()) * N
+    conv_ms = sum(kt[n][1] for n in lf if n in kt) / steps
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else None
+    bf16 = peaks["bf16_tflops"] if peaks else 1900.0
+    peak = bf16 * TF32_PER_BF16 / 3.0
+    achieved = conv_flops / (conv_ms * 1e-3) / 1e12 if conv_ms > 0 else None
+    per_layer = {}
+    for n, f in lf.items():
+        if n in kt and kt[n][1] > 0:
+            lms = kt[n][1] / steps
+            per_layer[n] = {"ms": lms, "frac": f * N / (lms * 1e-3) / 1e12 / peak}
+    others = {n: v[1] / steps for n, v in kt.items() if n not in lf}
     ctx.close()
-    return {"workload": "%d maps 7x32x32, U-Net base 64, 3 levels, fp32 CUDA cores" % N, "ms": ms,
-            "maps_per_s": N / (ms * 1e-3), "flops_per_map": fl / N,
-            "roofline": {"bound": "alu", "achieved": fl / (ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                         "frac": fl / (ms * 1e-3) / 1e12 / peak,
-                         "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (nominal unit counts)"}}
+    return {"workload": "%d maps 7x32x32, U-Net base 64, 3 levels (7.8 M parameters), fp32 split-tf32 tensor cores"
+                        % N,
+            "tensor_cores": drc.unet_tensor_cores(64, 3, 32, 32),
+            "ms": ms, "maps_per_s": N / (ms * 1e-3), "flops_per_map": unet_flops_per_map(),
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if achieved else None, "kernel": "conv_tc_kernel (16 launches)",
+                         "kernel_ms_per_call": conv_ms,
+                         "peak_source": ("of measured: bf16 burst %.1f TF/s x nominal tf32/bf16 %.3f / 3 products"
+                                         % (bf16, TF32_PER_BF16)) if peaks else "of fallback"},
+            "per_layer": per_layer, "other_kernels_ms": others}
 
 
 def make_inputs(seed_offset=0):

@@ -414,8 +414,8 @@ drc_status drc_adam_step(drc_ctx *ctx, float *w, const float *grad, float *m,
                          float *v, size_t n, int t, float lr, float beta1,
                          float beta2, float eps, void *stream);
 
-/* The paper's own network form (Sec. 3.3, "Neural network"), FP32 on the
- * CUDA cores: a U-Net.  Levels l = 0..levels have depth base * 2^l.  Each
+/* The paper's own network form (Sec. 3.3, "Neural network") in FP32: a
+ * U-Net.  Levels l = 0..levels have depth base * 2^l.  Each
  * encoder level applies two 3x3 convolutions (stride 1, padding 1), each
  * followed by batch normalisation (inference statistics, eps 1e-5) and
  * LeakyReLU (slope 0.01); 2x2 max pooling leads to the next level.  Each
@@ -438,8 +438,17 @@ drc_status drc_adam_step(drc_ctx *ctx, float *w, const float *grad, float *m,
  *           and every activation), caller-owned.
  * All pointers 16-byte aligned.  Asynchronous on `stream`; INVALID_ARG for a
  * bad shape, a short workspace, host or unaligned pointers.  The two size
- * queries return 0 for shapes the forward pass refuses. */
+ * queries return 0 for shapes the forward pass refuses.
+ * Where drc_unet_tensor_cores is 1 for the shape (base a multiple of 32;
+ * in_ch <= 8 or a multiple of 32; at every level W >> l dividing 128 and
+ * the maps' rows tiling 128-row boxes), the 3x3 layers run on the tensor
+ * cores as implicit GEMMs in the split-tf32 product (three tf32 products,
+ * each tile's K loop accumulated in chunks of 2 K blocks that are added into
+ * an fp32 running sum), with NHWC activations in the workspace; otherwise
+ * on the CUDA cores in plain fp32.  The workspace size covers either. */
 size_t drc_unet_param_count(int in_ch, int out_ch, int base, int levels);
+int drc_unet_tensor_cores(int in_ch, int out_ch, int base, int levels, int H,
+                          int W);
 size_t drc_unet_workspace_bytes(int in_ch, int out_ch, int base, int levels,
                                 int N, int H, int W);
 drc_status drc_unet_forward(drc_ctx *ctx, int in_ch, int out_ch, int base,

@@ -163,6 +163,8 @@ def load_library():
     lib.drc_unet_param_count.restype = SZ
     lib.drc_unet_workspace_bytes.argtypes = [I, I, I, I, I, I, I]
     lib.drc_unet_workspace_bytes.restype = SZ
+    lib.drc_unet_tensor_cores.argtypes = [I, I, I, I, I, I]
+    lib.drc_unet_tensor_cores.restype = I
     lib.drc_unet_forward.argtypes = [P, I, I, I, I, P, P, P, I, I, I, P, SZ, P]
     lib.drc_unet_forward.restype = I
     lib.drc_get_status.argtypes = [P, P]
@@ -643,6 +645,12 @@ def unet_param_count(base=64, levels=3, in_ch=7, out_ch=3):
     """drc_unet_param_count: packed parameters of the paper-form U-Net (0 for
     a shape the forward pass refuses)."""
     return int(load_library().drc_unet_param_count(in_ch, out_ch, base, levels))
+
+
+def unet_tensor_cores(base, levels, H, W, in_ch=7, out_ch=3):
+    """drc_unet_tensor_cores: whether drc_unet_forward runs this shape's 3x3
+    layers on the tensor cores (else on the CUDA cores)."""
+    return bool(load_library().drc_unet_tensor_cores(in_ch, out_ch, base, levels, H, W))
 
 
 class UNet:

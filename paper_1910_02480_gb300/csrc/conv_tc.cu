@@ -77,8 +77,9 @@ static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, 
 
 // With the epilogue's staging buffer where the pipeline keeps at least two
 // stages (and two raw slots where it uses a raw ring); otherwise without.
-__host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode, int ytma) {
-  const int avail = SMEM_BUDGET - SMEM_CTRL - 1024;
+// fold: the accumulation-chunk running sums (BM x BN fp32) come off the top.
+__host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode, int ytma, int fold) {
+  const int avail = SMEM_BUDGET - SMEM_CTRL - 1024 - (fold ? fold_bytes(BN) : 0);
   // the FP32 path, and BF16 stores by TMA: with 16-byte bf16 / e4m3 row
   // chunks the staged per-lane epilogue measured slower than the per-row one
   SmemPlan p = smem_plan_avail(prec, BN, mode, avail - (ytma ? EPI_TMA_BYTES : EPI_STG_BYTES));
@@ -121,11 +122,11 @@ static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, 
   p.raw_slot_bytes = rb;
   return p;
 }
-size_t conv_smem_bytes(int prec, int BN, int mode, int ytma) {
-  const SmemPlan p = smem_plan(prec, BN, mode, ytma);
+size_t conv_smem_bytes(int prec, int BN, int mode, int ytma, int fold) {
+  const SmemPlan p = smem_plan(prec, BN, mode, ytma, fold);
   return (size_t)SMEM_CTRL + 1024 + (size_t)p.stages * stage_bytes(prec, BN, mode) +
          (size_t)p.raw_depth * p.raw_slot_bytes +
-         (p.epi_stage ? (size_t)(ytma ? EPI_TMA_BYTES : EPI_STG_BYTES) : 0);
+         (p.epi_stage ? (size_t)(ytma ? EPI_TMA_BYTES : EPI_STG_BYTES) : 0) + (fold ? (size_t)fold_bytes(BN) : 0);
 }
 
 // Offset of 16-byte chunk q of row r inside a 128-byte-swizzled K-major tile.
@@ -279,6 +280,7 @@ __device__ __forceinline__ void prod_setup(const ConvArgs &a, int M, int t, int 
   const int hw_in = a.Hin * a.Win;
   const int lane = pt & 31, pw = pt >> 5;
   const bool s2 = a.kind == LK_CONV;
+  const int o1 = a.kind == LK_CONV1 ? 1 : 0;  // stride 1: taps at offsets -1..1 from the output pixel
 #pragma unroll
   for (int it = 0; it < 4; ++it) {
     const int r = (lane >> 3) + 4 * pw + 32 * it;
@@ -289,8 +291,8 @@ __device__ __forceinline__ void prod_setup(const ConvArgs &a, int M, int t, int 
     const int i = rem / a.Wrow, j = rem - (rem / a.Wrow) * a.Wrow;
     ri.vrow[it] = v;
     ri.pix_base[it] = n * hw_in;
-    ri.ybase[it] = s2 ? 2 * i - 1 : i;
-    ri.xbase[it] = s2 ? 2 * j - 1 : j;
+    ri.ybase[it] = s2 ? 2 * i - 1 : i - o1;
+    ri.xbase[it] = s2 ? 2 * j - 1 : j - o1;
   }
 }
 
@@ -428,16 +430,18 @@ __device__ __forceinline__ void tma_issue(const ConvArgs &a, const TmaCursor &c,
   constexpr int BKE = KROW_BYTES / T::ELEM;
   if (a.tap_boxes) {
     // taps of 8 channels (FP32: 32 bytes, four per K block; BF16: 16 bytes,
-    // eight per K block) of the stride-2 conv, one box each, tap-major; a slot
-    // past the last tap loads tap 0 again, against B rows packed as zero
+    // eight per K block) of the stride-2 or stride-1 conv, one box each,
+    // tap-major; a slot past the last tap loads tap 0 again, against B rows
+    // packed as zero
     constexpr int TB = 8 * T::ELEM;           // bytes of one tap row
     constexpr int TPB = KROW_BYTES / TB;      // taps per K block
+    const int ry = a.kind == LK_CONV ? 2 * c.r0 : c.r0;
 #pragma unroll
     for (int t = 0; t < TPB; ++t) {
       const int tap = TPB * c.kb + t < c.ntaps ? TPB * c.kb + t : 0;
       const unsigned tb = (unsigned)(c.taps >> (4 * tap)) & 15u;
       const int dy = (int)(tb & 3u), dx = (int)(tb >> 2);
-      tma_load_4d(dst + (uint32_t)(t * BM * TB), &a.tmap, 0, dx - 1, 2 * c.r0 + dy - 1, c.n0, bar);
+      tma_load_4d(dst + (uint32_t)(t * BM * TB), &a.tmap, 0, dx - 1, ry + dy - 1, c.n0, bar);
     }
     return;
   }
@@ -450,6 +454,13 @@ __device__ __forceinline__ void tma_issue(const ConvArgs &a, const TmaCursor &c,
   if (a.kind == LK_CONV) {  // stride-2 box: rows 2 i + dy - 1, cols 2 j + dx - 1
     x = dx - 1;
     y = 2 * c.r0 + dy - 1;
+  } else if (a.kind == LK_CONV1) {  // stride-1 box: rows i + dy - 1, cols j + dx - 1
+    x = dx - 1;
+    y = c.r0 + dy - 1;
+    if (a.x2 && c0 >= a.C1) {  // the channels of the concatenated second input
+      tma_load_4d(dst, &a.tmap2, c0 - a.C1, x, y, c.n0, bar);
+      return;
+    }
   } else {  // decoder phase: rows a + di, cols b + dj
     x = dx;
     y = c.r0 + dy;
@@ -665,6 +676,18 @@ __device__ __forceinline__ void tmem_ld_acc(uint32_t taddr, int BN, float (&v)[1
   }
 }
 
+// Accumulation chunks: add the running sums of columns [c, c+16) of this
+// lane's row (radd = the row's column 0; column stride BM floats).
+template <int PREC>
+__device__ __forceinline__ void add_running(const float *radd, int c, float (&v)[16]) {
+  if constexpr (PREC == PREC_TF32X3) {
+    if (radd) {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) v[e] += radd[(c + e) * BM];
+    }
+  }
+}
+
 // 16 consecutive skip channels as raw 16-byte words (fp32: 4 words, bf16: 2,
 // e4m3: 1).
 template <int PREC>
@@ -707,6 +730,11 @@ __device__ __forceinline__ void store16(uint8_t *yb, const float (&v)[16]) {
   }
 }
 
+// The epilogue's rectifier: ReLU, or LeakyReLU with a.slope in (0, 1).
+__device__ __forceinline__ float act_fn(const ConvArgs &a, float z) {
+  return a.slope != 0.f ? fmaxf(z, a.slope * z) : fmaxf(z, 0.f);
+}
+
 // Zero v[e] where the mask tensor's value is not positive (16 channels at mb).
 template <int PREC>
 __device__ __forceinline__ void apply_mask(const uint8_t *mb, float (&v)[16]) {
@@ -737,9 +765,11 @@ __device__ __forceinline__ void apply_mask(const uint8_t *mb, float (&v)[16]) {
 
 template <int PREC>
 __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int cc, int BN, int col0, bool vrow,
-                                          bool has_skip, const uint4 (&sk)[4], uint8_t *yb, size_t eoff) {
+                                          bool has_skip, const uint4 (&sk)[4], uint8_t *yb, size_t eoff,
+                                          const float *radd) {
   float v[16];
   tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
+  add_running<PREC>(radd, cc * 16, v);
   const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
   const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
 #pragma unroll
@@ -750,7 +780,7 @@ __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int
     for (int e = 0; e < 4; ++e) {
       float z = bsc ? v[4 * e4 + e] * __ldg(bsc + 4 * e4 + e) : v[4 * e4 + e];
       z += bb[e];
-      if (a.relu) z = fmaxf(z, 0.f);
+      if (a.relu) z = act_fn(a, z);
       v[4 * e4 + e] = z;
     }
   }
@@ -870,7 +900,8 @@ __device__ __forceinline__ void st4(void *base, size_t e, float4 v, const float 
 template <int PREC>
 __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, int BN, int n0, int row0,
                                              const PhaseDesc &pd, uint32_t ring, int &box, unsigned long long &w_tfull,
-                                             uint32_t tfull, uint32_t par, unsigned long long &w_ld) {
+                                             uint32_t tfull, uint32_t par, unsigned long long &w_ld,
+                                             const float *radd) {
   const int lane = threadIdx.x & 31;
   const bool convt = a.kind == LK_CONVT;
   // box origin (convT) and this lane's skip row
@@ -907,6 +938,7 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
     const long long tl0 = a.prof ? clock64() : 0;
     tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
     if (a.prof) w_ld += (unsigned long long)(clock64() - tl0);
+    add_running<PREC>(radd, cc * 16, v);
     const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
 #pragma unroll
     for (int e4 = 0; e4 < 4; ++e4) {
@@ -915,7 +947,7 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         float z = v[4 * e4 + e] + bb[e];
-        if (a.relu) z = fmaxf(z, 0.f);
+        if (a.relu) z = act_fn(a, z);
         v[4 * e4 + e] = z;
       }
     }
@@ -962,7 +994,7 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
 template <int PREC>
 __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t taddr, int BN, int n0, size_t ebase,
                                                 bool vrow, float *stg, unsigned long long &w_tfull, uint32_t tfull,
-                                                uint32_t par, unsigned long long &w_ld) {
+                                                uint32_t par, unsigned long long &w_ld, const float *radd) {
   const int lane = threadIdx.x & 31;
   size_t er[4];
   bool vr[4];
@@ -993,6 +1025,7 @@ __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t tadd
     const long long tl0 = a.prof ? clock64() : 0;
     tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
     if (a.prof) w_ld += (unsigned long long)(clock64() - tl0);
+    add_running<PREC>(radd, cc * 16, v);
     const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
     const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
 #pragma unroll
@@ -1003,7 +1036,7 @@ __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t tadd
       for (int e = 0; e < 4; ++e) {
         float z = bsc ? v[4 * e4 + e] * __ldg(bsc + 4 * e4 + e) : v[4 * e4 + e];
         z += bb[e];
-        if (a.relu) z = fmaxf(z, 0.f);
+        if (a.relu) z = act_fn(a, z);
         v[4 * e4 + e] = z;
       }
     }
@@ -1103,68 +1136,72 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
   const uint32_t dBlo = (uint32_t)b_bytes >> 4;
   int stage = 0;
   uint32_t phase = 0;
-  int it = 0;
-  for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x, ++it) {
+  int it = 0;  // accumulator units: tiles, or with a.kfold chunks of a.kfold K blocks of a tile
+  for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
     const TileCoord tc = tile_coord(a, t);
     const int nkb = a.ph[tc.phase].num_kb;
-    const int buf = nbufs == 2 ? (it & 1) : 0;
-    const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
-    if (!pwait(a, w_tempty, smem_u32(&tempty_bar[buf]), par ^ 1)) {
-      ok = false;
-      break;
-    }
-    tc_fence_after();
-    const uint32_t d_tmem = tmem_base + (uint32_t)(buf * acc_cols);
-    const uint32_t c_tmem = d_tmem + (uint32_t)BN;  // correction accumulator (split-tf32)
-    for (int kb = 0; kb < nkb; ++kb) {
-      if (!pwait(a, w_full, smem_u32(&full_bar[stage]), phase)) {
+    const int kf = a.kfold > 0 ? a.kfold : nkb;
+    for (int k0 = 0; ok && k0 < nkb; k0 += kf, ++it) {
+      const int k1 = k0 + kf < nkb ? k0 + kf : nkb;
+      const int buf = nbufs == 2 ? (it & 1) : 0;
+      const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
+      if (!pwait(a, w_tempty, smem_u32(&tempty_bar[buf]), par ^ 1)) {
         ok = false;
         break;
       }
       tc_fence_after();
-      // descriptors: the stage-0 A tile's plus fixed offsets in units of
-      // the start-address field (bytes >> 4); the K step inside the
-      // 128-byte swizzle row adds 32 bytes (2 units).  Keeping this to a
-      // few adds matters: one thread issues every MMA, so its dependent
-      // instruction latency bounds the MMA rate.
-      const uint64_t sd = dA0 + (uint64_t)((uint32_t)stage * dstage);
-      const uint64_t bd0 = dB0 + (uint64_t)((uint32_t)stage * dstage), bd1 = bd0 + dBlo;
-      if constexpr (TS) {
-        // A hi/lo from tensor memory: 8 tf32 columns per K step
-        const uint32_t ta = tmem_base + (uint32_t)(TS_A_COL0 + stage * 64);
-        const uint32_t acc0 = kb != 0;
-        tc_mma_ts_tf32(d_tmem, ta, bd0, idesc, acc0);
-        tc_mma_ts_tf32(c_tmem, ta, bd1, idesc, acc0);
-        tc_mma_ts_tf32(c_tmem, ta + 32, bd0, idesc, 1u);
-#pragma unroll
-        for (int k = 1; k < KROW_BYTES / 32; ++k) {
-          tc_mma_ts_tf32(d_tmem, ta + 8 * k, bd0 + 2 * k, idesc, 1u);
-          tc_mma_ts_tf32(c_tmem, ta + 8 * k, bd1 + 2 * k, idesc, 1u);
-          tc_mma_ts_tf32(c_tmem, ta + 32 + 8 * k, bd0 + 2 * k, idesc, 1u);
+      const uint32_t d_tmem = tmem_base + (uint32_t)(buf * acc_cols);
+      const uint32_t c_tmem = d_tmem + (uint32_t)BN;  // correction accumulator (split-tf32)
+      for (int kb = k0; kb < k1; ++kb) {
+        if (!pwait(a, w_full, smem_u32(&full_bar[stage]), phase)) {
+          ok = false;
+          break;
         }
-      } else {
-        const uint64_t ad1 = sd + dAlo;
-        const uint32_t acc0 = kb != 0;
-        tc_mma<T::KIND>(d_tmem, sd, bd0, idesc, acc0);
-        if constexpr (PREC == PREC_TF32X3) {
-          tc_mma<T::KIND>(c_tmem, sd, bd1, idesc, acc0);
-          tc_mma<T::KIND>(c_tmem, ad1, bd0, idesc, 1u);
-        }
-#pragma unroll
-        for (int k = 1; k < KROW_BYTES / 32; ++k) {
-          tc_mma<T::KIND>(d_tmem, sd + kA * k, bd0 + 2 * k, idesc, 1u);
+        tc_fence_after();
+        // descriptors: the stage-0 A tile's plus fixed offsets in units of
+        // the start-address field (bytes >> 4); the K step inside the
+        // 128-byte swizzle row adds 32 bytes (2 units).  Keeping this to a
+        // few adds matters: one thread issues every MMA, so its dependent
+        // instruction latency bounds the MMA rate.
+        const uint64_t sd = dA0 + (uint64_t)((uint32_t)stage * dstage);
+        const uint64_t bd0 = dB0 + (uint64_t)((uint32_t)stage * dstage), bd1 = bd0 + dBlo;
+        if constexpr (TS) {
+          // A hi/lo from tensor memory: 8 tf32 columns per K step
+          const uint32_t ta = tmem_base + (uint32_t)(TS_A_COL0 + stage * 64);
+          const uint32_t acc0 = kb != k0;
+          tc_mma_ts_tf32(d_tmem, ta, bd0, idesc, acc0);
+          tc_mma_ts_tf32(c_tmem, ta, bd1, idesc, acc0);
+          tc_mma_ts_tf32(c_tmem, ta + 32, bd0, idesc, 1u);
+  #pragma unroll
+          for (int k = 1; k < KROW_BYTES / 32; ++k) {
+            tc_mma_ts_tf32(d_tmem, ta + 8 * k, bd0 + 2 * k, idesc, 1u);
+            tc_mma_ts_tf32(c_tmem, ta + 8 * k, bd1 + 2 * k, idesc, 1u);
+            tc_mma_ts_tf32(c_tmem, ta + 32 + 8 * k, bd0 + 2 * k, idesc, 1u);
+          }
+        } else {
+          const uint64_t ad1 = sd + dAlo;
+          const uint32_t acc0 = kb != k0;
+          tc_mma<T::KIND>(d_tmem, sd, bd0, idesc, acc0);
           if constexpr (PREC == PREC_TF32X3) {
-            tc_mma<T::KIND>(c_tmem, sd + kA * k, bd1 + 2 * k, idesc, 1u);
-            tc_mma<T::KIND>(c_tmem, ad1 + kA * k, bd0 + 2 * k, idesc, 1u);
+            tc_mma<T::KIND>(c_tmem, sd, bd1, idesc, acc0);
+            tc_mma<T::KIND>(c_tmem, ad1, bd0, idesc, 1u);
+          }
+  #pragma unroll
+          for (int k = 1; k < KROW_BYTES / 32; ++k) {
+            tc_mma<T::KIND>(d_tmem, sd + kA * k, bd0 + 2 * k, idesc, 1u);
+            if constexpr (PREC == PREC_TF32X3) {
+              tc_mma<T::KIND>(c_tmem, sd + kA * k, bd1 + 2 * k, idesc, 1u);
+              tc_mma<T::KIND>(c_tmem, ad1 + kA * k, bd0 + 2 * k, idesc, 1u);
+            }
           }
         }
+        tc_commit(smem_u32(&empty_bar[stage]));
+        stage = stage + 1 == stages ? 0 : stage + 1;  // selects, not a branch
+        phase ^= stage == 0 ? 1u : 0u;
       }
-      tc_commit(smem_u32(&empty_bar[stage]));
-      stage = stage + 1 == stages ? 0 : stage + 1;  // selects, not a branch
-      phase ^= stage == 0 ? 1u : 0u;
+      if (!ok) break;
+      tc_commit(smem_u32(&tfull_bar[buf]));
     }
-    if (!ok) break;
-    tc_commit(smem_u32(&tfull_bar[buf]));
   }
 }
 
@@ -1174,7 +1211,7 @@ template <int PREC, bool YTMA>
 __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_constant__ ConvArgs a) {
   using T = PrecTraits<PREC>;
   const int BN = a.BN;
-  const SmemPlan plan = smem_plan(PREC, BN, a.prod_mode, YTMA ? 1 : 0);
+  const SmemPlan plan = smem_plan(PREC, BN, a.prod_mode, YTMA ? 1 : 0, a.kfold > 0 ? 1 : 0);
   const int stages = plan.stages;
   const int a_bytes = BM * KROW_BYTES;
   const int b_bytes = BN * KROW_BYTES;
@@ -1339,10 +1376,47 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     const act_t *skip = reinterpret_cast<const act_t *>(a.skip);
     const int nch = BN / 16;
     float *epi_stg = reinterpret_cast<float *>(data + (size_t)stages * sbytes + (size_t)plan.raw_depth * plan.raw_slot_bytes);
+    // accumulation chunks: this lane's running sums, column c at rsum[c * BM]
+    float *rsum = nullptr;
+    if (PREC == PREC_TF32X3 && a.kfold > 0)
+      rsum = epi_stg + (plan.epi_stage ? (YTMA ? EPI_TMA_BYTES : EPI_STG_BYTES) / 4 : 0) + row;
     int tma_box = 0;  // next box of this warp's TMA staging ring
+    bool failed = false;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++it) {
       const TileCoord tc = tile_coord(a, t);
       const PhaseDesc &pd = a.ph[tc.phase];
+      // every chunk but the last: D + C of the chunk into the running sums,
+      // then the accumulator buffer goes back to the MMA warp
+      const int nkb = pd.num_kb;
+      const int kf = rsum ? a.kfold : nkb;
+      const int nchunk = (nkb + kf - 1) / kf;
+      for (int q = 0; q + 1 < nchunk; ++q, ++it) {
+        const int fbuf = nbufs == 2 ? (it & 1) : 0;
+        const uint32_t fpar = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
+        if (!pwait(a, w_tfull, smem_u32(&tfull_bar[fbuf]), fpar)) {
+          failed = true;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t faddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(fbuf * acc_cols);
+        for (int cc = 0; cc < nch; ++cc) {
+          float v[16];
+          tmem_ld_acc<PREC>(faddr + cc * 16, BN, v);
+          float *r = rsum + cc * 16 * BM;
+          if (q == 0) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) r[e * BM] = v[e];
+          } else {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) r[e * BM] += v[e];
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[fbuf]));
+      }
+      if (failed) break;
+      const float *radd = nchunk > 1 ? rsum : nullptr;
       const int buf = nbufs == 2 ? (it & 1) : 0;
       const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
       const int m = tc.m_tile * BM + row;
@@ -1358,7 +1432,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
         const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
         if (!epi_tile_tma<PREC>(a, taddr, BN, tc.n_tile * BN, tc.m_tile * BM + eq * 32, pd,
                                 smem_u32(epi_stg) + (uint32_t)(eq * EPI_TMA_BOXES * EPI_TMA_BOX_BYTES), tma_box,
-                                w_tfull, smem_u32(&tfull_bar[buf]), par, w_ld))
+                                w_tfull, smem_u32(&tfull_bar[buf]), par, w_ld, radd))
           break;
         tc_fence_before();
         __syncwarp();
@@ -1368,7 +1442,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       if (plan.epi_stage) {
         const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
         if (!epi_tile_staged<PREC>(a, taddr, BN, tc.n_tile * BN, opix * a.Cout, vrow, epi_stg + eq * 32 * 20, w_tfull,
-                                   smem_u32(&tfull_bar[buf]), par, w_ld))
+                                   smem_u32(&tfull_bar[buf]), par, w_ld, radd))
           break;
         tc_fence_before();
         __syncwarp();
@@ -1392,7 +1466,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
           uint4 sk[4];
           if (has_skip) load_skip<PREC>(skip + ebase + cc * 16, sk);
           epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk, yb + cc * 16 * out_elem,
-                          ebase + cc * 16);
+                          ebase + cc * 16, radd);
         }
       } else {
         uint4 sk0[4], sk1[4];
@@ -1404,11 +1478,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
         tc_fence_after();
         for (int cc = 0; cc < nch; cc += 2) {
           epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk0, yb + cc * 16 * out_elem,
-                          ebase + cc * 16);
+                          ebase + cc * 16, nullptr);
           if (has_skip && cc + 2 < nch) load_skip<PREC>(skip + ebase + (cc + 2) * 16, sk0);
           if (cc + 1 < nch) {
             epi_chunk<PREC>(a, taddr, cc + 1, BN, tc.n_tile * BN + (cc + 1) * 16, vrow, has_skip, sk1,
-                            yb + (cc + 1) * 16 * out_elem, ebase + (cc + 1) * 16);
+                            yb + (cc + 1) * 16 * out_elem, ebase + (cc + 1) * 16, nullptr);
             if (has_skip && cc + 3 < nch) load_skip<PREC>(skip + ebase + (cc + 3) * 16, sk1);
           }
         }
@@ -1438,7 +1512,8 @@ cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t s
   const int total = a.num_phases * a.m_tiles * a.n_tiles;
   if (total == 0) return cudaSuccess;
   const int grid = total < num_sms ? total : num_sms;
-  const size_t smem = conv_smem_bytes(prec, a.BN, a.prod_mode, a.y_tma);
+  if (a.kfold < 0 || (a.kfold > 0 && (prec != PREC_TF32X3 || a.BN > KFOLD_MAX_BN))) return cudaErrorInvalidValue;
+  const size_t smem = conv_smem_bytes(prec, a.BN, a.prod_mode, a.y_tma, a.kfold > 0 ? 1 : 0);
   cudaError_t e;
   switch (prec) {
     case PREC_TF32X3:
@@ -1534,7 +1609,7 @@ cudaError_t launch_nchw7_to_nhwc8(const float *in, void *out, long long hw, int 
 __device__ float raw_weight(const PackArgs &p, const PhaseDesc &pd, int col, int k) {
   const int t = k / p.Cin, c = k - (k / p.Cin) * p.Cin;
   if (t >= pd.ntaps || c >= p.Cin_raw) return 0.f;
-  if (p.kind == LK_CONV)  // W[o][c][u][v], tap t = 3u + v
+  if (p.kind == LK_CONV || p.kind == LK_CONV1)  // W[o][c][u][v], tap t = 3u + v
     return p.wraw[((size_t)col * p.Cin_raw + c) * 9 + t];
   // LK_CONVT: W[c][o][u][v] with the phase's kernel tap
   const int co = p.Cout_raw > 0 ? p.Cout_raw : p.Cout;

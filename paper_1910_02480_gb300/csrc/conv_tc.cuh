@@ -13,7 +13,9 @@ namespace drc {
 enum LayerKind {
   LK_CONV = 1,   // encoder conv3x3 s2 p1 on NHWC activations, K = tap*Cin + c
   LK_CONVT = 2,  // decoder convT3x3 s2, one GEMM per output parity phase
-  LK_HEAD = 3    // output convT (3 channels): not a tensor-core GEMM (head.cu)
+  LK_HEAD = 3,   // output convT (3 channels): not a tensor-core GEMM (head.cu)
+  LK_CONV1 = 4   // conv3x3 s1 p1 ("same") on NHWC activations, K = tap*Cin + c; the input may be the
+                 // channel concatenation of two tensors (x: channels [0, C1), x2: the rest)
 };
 
 enum Prec { PREC_TF32X3 = 0, PREC_BF16 = 1, PREC_FP8 = 2 };
@@ -54,6 +56,9 @@ struct ConvArgs {
                      // four per K block, placed tap-major in the raw slot (BM rows x 32 bytes each)
   int kind;
   const void *x;     // input activations, NHWC
+  const void *x2;    // LK_CONV1: second input (NHWC, Cin - C1 channels) concatenated after x, or nullptr
+  int C1;            // LK_CONV1 with x2: channels of x (a multiple of the K block's channels)
+  CUtensorMap tmap2; // LK_CONV1 with x2: A operand view of x2 (TMA modes)
   void *y;           // output activations, NHWC
   const void *skip;  // NHWC skip tensor shaped like y (LK_CONVT), or nullptr
   const uint8_t *B;  // packed B tiles (tf32 hi part for PREC_TF32X3)
@@ -71,6 +76,7 @@ struct ConvArgs {
   int phase_order[4];    // heaviest phase first
   PhaseDesc ph[4];
   int relu;
+  float slope;             // with relu: 0 = ReLU, else LeakyReLU max(z, slope z) (0 < slope < 1)
   const float *out_qinv;   // nullable: store the output as e4m3, column c times out_qinv[c] (the inverse
                            // of the consuming layer's input scale); else in the kernel's activation type
   const float *skip_scale; // FP8 kernel: the e4m3 skip tensor's per-channel scales
@@ -82,6 +88,14 @@ struct ConvArgs {
   void *y2;
   int y2_pre_skip;
   const void *mask;
+  // FP32 accumulation in chunks (0: off): the MMAs of every kfold K blocks of
+  // a tile go into a fresh tensor-memory accumulator, which the epilogue
+  // warps add into an fp32 running sum (round to nearest) while the next
+  // chunk accumulates in the other buffer.  The tensor core's own fp32
+  // accumulation does not round to nearest, so its error grows with the
+  // number of MMAs into one accumulator; deep K (thousands of terms) needs
+  // this to stay at fp32 accuracy.  BN <= KFOLD_MAX_BN.
+  int kfold;
   int *status;
   unsigned long long timeout_ns;
   int debug_stall;
@@ -109,8 +123,13 @@ constexpr int EPI_STG_BYTES = EPI_STG_FLOATS * 4;
 constexpr int EPI_TMA_BOXES = 4;
 constexpr int EPI_TMA_BOX_BYTES = 2048;
 constexpr int EPI_TMA_BYTES = 4 * EPI_TMA_BOXES * EPI_TMA_BOX_BYTES;
-__host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode, int ytma);
-size_t conv_smem_bytes(int prec, int BN, int mode, int ytma);
+// Accumulation chunks (ConvArgs::kfold): the epilogue warps' running sums,
+// [BN][BM] fp32 in shared memory (column-major: a warp's 32 rows of one
+// column are 32 consecutive words).
+constexpr int KFOLD_MAX_BN = 64;
+__host__ __device__ inline int fold_bytes(int BN) { return BM * BN * 4; }
+__host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode, int ytma, int fold = 0);
+size_t conv_smem_bytes(int prec, int BN, int mode, int ytma, int fold = 0);
 
 // Host-side launch / pack entry points (conv_tc.cu).
 cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t st);

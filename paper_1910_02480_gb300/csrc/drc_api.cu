@@ -159,14 +159,14 @@ void plan_store(int prec, ConvArgs &a) {
   const int eb = prec == PREC_TF32X3 ? 4 : 2;
   const CUtensorMapDataType dt = prec == PREC_TF32X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const CUtensorMapSwizzle sw = prec == PREC_TF32X3 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
-  if (a.kind == LK_CONV && a.skip) return;
+  if (a.kind != LK_CONVT && a.skip) return;
   // BF16 decoder phases keep the per-row epilogue (its skip prefetch two
   // chunks ahead measured faster there: d2 0.21 against 0.24 ms)
   if (prec == PREC_BF16 && a.kind == LK_CONVT) return;
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return;
   CUresult r;
-  if (a.kind == LK_CONV) {
+  if (a.kind == LK_CONV || a.kind == LK_CONV1) {
     cuuint64_t dims[2] = {(cuuint64_t)a.Cout, (cuuint64_t)a.M};
     cuuint64_t strides[1] = {(cuuint64_t)a.Cout * eb};
     cuuint32_t box[2] = {16, 32}, estr[2] = {1, 1};
@@ -202,8 +202,12 @@ void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
   // conv over 8 stored channels (the first layer): 32 bytes per tap in FP32
   // (four taps per K block) or 16 in BF16 (eight), each tap its own TMA box;
   // BF16 boxes land in the A tile directly (no-swizzle K-major layout)
-  const bool taps = a.kind == LK_CONV && a.Cin == 8 && (prec == PREC_TF32X3 || prec == PREC_BF16);
+  const bool taps = (a.kind == LK_CONV || a.kind == LK_CONV1) && a.Cin == 8 && !a.x2 &&
+                    (prec == PREC_TF32X3 || prec == PREC_BF16);
   if (Wr > BM || BM % Wr || (!taps && a.Cin % bke)) return;
+  // a concatenated second input: every K block inside one of the two tensors
+  const int C1 = a.x2 ? a.C1 : a.Cin;
+  if (a.x2 && (a.kind != LK_CONV1 || C1 <= 0 || C1 >= a.Cin || C1 % bke)) return;
   const int rows_t = Hr < BM / Wr ? Hr : BM / Wr;
   if ((rows_t * Wr) % Wr || BM % (rows_t * Wr) || (rows_t < Hr && Hr % rows_t)) return;
   const int maps_t = BM / (rows_t * Wr);
@@ -214,9 +218,8 @@ void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
   if (!enc) return;
   const int eb = prec == PREC_TF32X3 ? 4 : (prec == PREC_BF16 ? 2 : 1);  // stored activation bytes
   const int box_c = taps ? a.Cin : KROW_BYTES / eb;                      // channels per box row (128 / 32 bytes)
-  cuuint64_t dims[4] = {(cuuint64_t)a.Cin, (cuuint64_t)a.Win, (cuuint64_t)a.Hin, (cuuint64_t)a.N};
-  cuuint64_t strides[3] = {(cuuint64_t)a.Cin * eb, (cuuint64_t)a.Cin * eb * a.Win,
-                           (cuuint64_t)a.Cin * eb * a.Win * a.Hin};
+  cuuint64_t dims[4] = {(cuuint64_t)C1, (cuuint64_t)a.Win, (cuuint64_t)a.Hin, (cuuint64_t)a.N};
+  cuuint64_t strides[3] = {(cuuint64_t)C1 * eb, (cuuint64_t)C1 * eb * a.Win, (cuuint64_t)C1 * eb * a.Win * a.Hin};
   cuuint32_t box[4] = {(cuuint32_t)box_c, (cuuint32_t)(s2 ? 2 * Wr : Wr), (cuuint32_t)(s2 ? 2 * rows_t : rows_t),
                        (cuuint32_t)maps_t};
   cuuint32_t estr[4] = {1, (cuuint32_t)(s2 ? 2 : 1), (cuuint32_t)(s2 ? 2 : 1), 1};
@@ -227,6 +230,16 @@ void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
                    taps ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return;
+  if (a.x2) {
+    const int C2 = a.Cin - C1;
+    dims[0] = (cuuint64_t)C2;
+    strides[0] = (cuuint64_t)C2 * eb;
+    strides[1] = strides[0] * a.Win;
+    strides[2] = strides[1] * a.Hin;
+    r = enc(&a.tmap2, dt, 4, const_cast<void *>(a.x2), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return;
+  }
   if (force_mode == PROD_CPASYNC) return;
   a.tap_boxes = taps ? 1 : 0;
   if (prec == PREC_TF32X3 && force_mode == PROD_TMA_CONVERT) {
@@ -1796,6 +1809,153 @@ static bool unet_shape_ok(int in_ch, int out_ch, int base, int levels) {
          ((long long)base << levels) <= 4096;
 }
 
+namespace {
+
+// The paper-form U-Net with its 3x3 layers on the tensor cores: each is a
+// stride-1 implicit GEMM of conv_tc_kernel (LK_CONV1) over NHWC fp32
+// activations in the split-tf32 product, with batch normalisation folded
+// into the weights and bias, LeakyReLU in the epilogue, and a decoder's
+// concatenated input read from its two tensors (upsampled deeper features,
+// then the level's encoder output) by two tensor maps -- no copy.  Pooling,
+// upsampling, the input staging and the 1x1 head are NHWC kernels of their
+// own (unet.cu).  Weights are folded and packed on every call (the caller
+// owns the parameters).
+drc_status unet_forward_tc(drc_ctx *c, const UnetShape &u, const float *params, const float *in, float *out, int N,
+                           int H, int W, void *workspace, cudaStream_t st) {
+  Tracer *tr = &c->tracer;
+  UnetTcBufs b;
+  unet_tc_carve(u, N, H, W, static_cast<char *>(workspace), &b);
+  const std::vector<UnetLayer> T = unet_layer_table(u);
+  const int cs = unet_tc_in_channels(u);
+  // the 3x3 layers as GEMM layers, their packed tiles laid out like the
+  // autoencoder's
+  // Accumulation chunks of 2 K blocks (64 input channels x taps) on every
+  // layer: the tensor core's own fp32 accumulation loses about an ulp of the
+  // running sum per MMA, so one accumulator over this network's reductions
+  // (up to 216 K blocks, 6912 terms) measured 1.6e-3 max floored relative
+  // error at the paper-size output (normwise 4.8e-5); folded every 2 K
+  // blocks, 6.4e-5 (2.1e-6).  Chunks on the deep layers only (more than 18
+  // K blocks) still left 1.6e-4 on a smaller network.  The running sums live
+  // in shared memory, which limits the layers to 64-column tiles.
+  constexpr int kFoldKb = 2, kFoldAbove = kFoldKb;
+  std::vector<Layer> Ls;
+  std::vector<int> kfold;
+  for (size_t i = 0; i < T.size(); ++i) {
+    const UnetLayer &d = T[i];
+    if (d.kind == 2) continue;
+    Layer L;
+    memset(&L, 0, sizeof L);
+    L.kind = LK_CONV1;
+    L.prec = PREC_TF32X3;
+    L.Cin_raw = d.cin;
+    L.Cin = i == 0 ? cs : d.cin;
+    L.Cout = d.cout;
+    L.num_phases = 1;
+    PhaseDesc &pd = L.ph[0];
+    pd.ntaps = 9;
+    for (int t = 0; t < 9; ++t) {
+      pd.u[t] = pd.dy[t] = (signed char)(t / 3);
+      pd.v[t] = pd.dx[t] = (signed char)(t % 3);
+    }
+    pd.num_kb = ceil_div(9ll * L.Cin, bke_of(PREC_TF32X3));
+    const bool fold = pd.num_kb > kFoldAbove;
+    kfold.push_back(fold ? kFoldKb : 0);
+    set_bn(L, fold && L.Cout > KFOLD_MAX_BN ? KFOLD_MAX_BN : pick_bn(L.Cout));
+    snprintf(L.name, sizeof L.name, "unet conv %zu", i);
+    Ls.push_back(L);
+  }
+  layout_packs(Ls);
+  cudaError_t e = unet_fold_conv_form(u, params, b.fold, st, tr);
+  if (e != cudaSuccess) return cuda_fail(c, e, "unet fold");
+  for (size_t i = 0; i < Ls.size(); ++i) {
+    const Layer &L = Ls[i];
+    PackArgs p;
+    memset(&p, 0, sizeof p);
+    p.kind = L.kind;
+    p.wraw = b.fold + T[i].dst;
+    p.Cin = L.Cin;
+    p.Cin_raw = L.Cin_raw;
+    p.Cout = L.Cout;
+    p.BN = L.BN;
+    p.n_tiles = L.n_tiles;
+    p.num_phases = 1;
+    p.ph[0] = L.ph[0];
+    p.B = b.B;
+    p.B_lo = b.B_lo;
+    p.total_chunks = (long long)(L.pack_bytes / 16);
+    DRC_TRACED(tr, "weight pack", st, e = launch_pack(p, PREC_TF32X3, st));
+    if (e != cudaSuccess) return cuda_fail(c, e, "unet weight packing");
+  }
+  if ((e = launch_unet_stage_nhwc(in, N, u.cin, (long long)H * W, cs, b.in, st, tr)) != cudaSuccess)
+    return cuda_fail(c, e, "unet input staging");
+  size_t li = 0;
+  // one 3x3 layer: x (and x2 after its C1 channels) at h x w -> y
+  auto conv = [&](const float *x, const float *x2, int C1, int h, int w, float *y) -> drc_status {
+    const Layer &L = Ls[li];
+    ConvArgs a;
+    fill_common(c, L, b.B, b.B_lo, a);
+    a.N = N;
+    a.x = x;
+    a.x2 = x2;
+    a.C1 = x2 ? C1 : 0;
+    a.y = y;
+    a.Hin = a.Hrow = a.Hout = h;
+    a.Win = a.Wrow = a.Wout = w;
+    a.Cin = L.Cin;
+    a.Cout = L.Cout;
+    a.relu = 1;
+    a.slope = 0.01f;  // LeakyReLU
+    a.bias = b.fold + T[li].dst + 9 * (size_t)T[li].cin * T[li].cout;
+    a.M = (int)((long long)N * h * w);
+    a.m_tiles = ceil_div(a.M, BM);
+    a.kfold = kfold[li];
+    plan_operand(PREC_TF32X3, a);
+    if (a.prod_mode == PROD_CPASYNC && x2)
+      return fail(c, DRC_ERR_CUDA, "unet layer %zu: no tensor map for the concatenated input", li);
+    cudaError_t le;
+    DRC_TRACED(tr, L.name, st, le = launch_conv(a, PREC_TF32X3, c->num_sms, st));
+    if (le != cudaSuccess) return cuda_fail(c, le, "unet layer launch");
+    ++li;
+    return DRC_OK;
+  };
+  drc_status s;
+  int ci = cs;
+  const float *x = b.in;
+  for (int l = 0; l <= u.levels; ++l) {
+    const int h = H >> l, w = W >> l, ch = u.base << l;
+    if (l > 0) {
+      if ((e = launch_unet_pool_nhwc(b.enc[l - 1], N, h * 2, w * 2, ci, b.pool[l], st, tr)) != cudaSuccess)
+        return cuda_fail(c, e, "unet pool");
+      x = b.pool[l];
+    }
+    if ((s = conv(x, nullptr, 0, h, w, b.enc_a[l])) != DRC_OK) return s;
+    if ((s = conv(b.enc_a[l], nullptr, 0, h, w, b.enc[l])) != DRC_OK) return s;
+    ci = ch;
+  }
+  const float *d = b.enc[u.levels];
+  for (int l = u.levels - 1; l >= 0; --l) {
+    const int h = H >> l, w = W >> l, ch = u.base << l;
+    if ((e = launch_unet_up_nhwc(d, N, h / 2, w / 2, 2 * ch, b.up[l], st, tr)) != cudaSuccess)
+      return cuda_fail(c, e, "unet upsampling");
+    if ((s = conv(b.up[l], b.enc[l], 2 * ch, h, w, b.dec_a[l])) != DRC_OK) return s;
+    if ((s = conv(b.dec_a[l], nullptr, 0, h, w, b.dec[l])) != DRC_OK) return s;
+    d = b.dec[l];
+  }
+  const UnetLayer &hd = T.back();
+  if ((e = launch_unet_head_nhwc(d, N, (long long)H * W, u.base, b.fold + hd.dst, u.cout, out, st, tr)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "unet head");
+  return DRC_OK;
+}
+
+}  // namespace
+
+int drc_unet_tensor_cores(int in_ch, int out_ch, int base, int levels, int H, int W) {
+  if (!unet_shape_ok(in_ch, out_ch, base, levels) || H < 1 || W < 1 || H % (1 << levels) || W % (1 << levels))
+    return 0;
+  return unet_tc_shape_ok(UnetShape{in_ch, out_ch, base, levels}, H, W) ? 1 : 0;
+}
+
 size_t drc_unet_param_count(int in_ch, int out_ch, int base, int levels) {
   if (!unet_shape_ok(in_ch, out_ch, base, levels)) return 0;
   return unet_param_count(UnetShape{in_ch, out_ch, base, levels});
@@ -1805,7 +1965,11 @@ size_t drc_unet_workspace_bytes(int in_ch, int out_ch, int base, int levels, int
   if (!unet_shape_ok(in_ch, out_ch, base, levels) || N < 0 || H < 1 || W < 1 || H % (1 << levels) ||
       W % (1 << levels))
     return 0;
-  return unet_workspace_bytes(UnetShape{in_ch, out_ch, base, levels}, N, H, W);
+  const UnetShape u{in_ch, out_ch, base, levels};
+  const size_t simt = unet_workspace_bytes(u, N, H, W);
+  if (!unet_tc_shape_ok(u, H, W)) return simt;
+  const size_t tc = unet_tc_carve(u, N, H, W, nullptr, nullptr);
+  return tc > simt ? tc : simt;
 }
 
 drc_status drc_unet_forward(drc_ctx *c, int in_ch, int out_ch, int base, int levels, const float *params,
@@ -1831,6 +1995,8 @@ drc_status drc_unet_forward(drc_ctx *c, int in_ch, int out_ch, int base, int lev
   if ((s = check_dev(c, in, "in", false)) != DRC_OK) return s;
   if ((s = check_dev(c, out, "out", false)) != DRC_OK) return s;
   if ((s = check_dev(c, workspace, "workspace", false)) != DRC_OK) return s;
+  if (unet_tc_shape_ok(u, H, W))
+    return unet_forward_tc(c, u, params, in, out, N, H, W, workspace, static_cast<cudaStream_t>(stream));
   const cudaError_t e = unet_forward(u, params, in, out, N, H, W, workspace, static_cast<cudaStream_t>(stream),
                                      &c->tracer);
   return e == cudaSuccess ? DRC_OK : cuda_fail(c, e, "unet forward");

@@ -46,12 +46,7 @@ constexpr int UCOB = 16;        // output channels per block
 constexpr int UMPB_MAX = 64;    // maps per block at most
 constexpr int UXS_MAX = 9216;   // staged input floats: UCC x maps x (TH + 2) x (TW + 2) <= 8 x 1152
 
-struct LayerDesc {
-  int kind;  // 0: 3x3 convolution, 1: 3x3 transposed convolution, 2: 1x1 head
-  int cin, cout, bn;
-  size_t src;  // first float of the layer in the packed parameters
-  size_t dst;  // first float of its folded weights (bias after them)
-};
+using LayerDesc = UnetLayer;
 
 std::vector<LayerDesc> unet_layers(const UnetShape &u, size_t *n_src, size_t *n_dst) {
   std::vector<LayerDesc> L;
@@ -120,6 +115,9 @@ size_t unet_carve(const UnetShape &u, int N, int H, int W, char *base, UnetBufs 
   return off;
 }
 
+// CONV_FORM: the 3x3 layers' destination is [o][c][u][v] (the tensor-core
+// packer's input); otherwise [c][t][o] (the CUDA-core kernel's).
+template <bool CONV_FORM>
 __global__ void unet_fold_kernel(const float *P, int kind, int cin, int cout, int bn, size_t src, size_t dst,
                                  float *F) {
   const size_t nw = (kind == 2 ? 1 : 9) * (size_t)cin * cout;
@@ -133,6 +131,10 @@ __global__ void unet_fold_kernel(const float *P, int kind, int cin, int cout, in
       if (kind == 2) {  // head: [o][c], unchanged
         o = (int)(e / cin);
         val = Wt[e];
+      } else if (CONV_FORM) {  // destination [o][c][u][v]
+        o = (int)(e / (9 * (size_t)cin));
+        const int c = (int)((e / 9) % cin), t = (int)(e % 9), u = t / 3, v = t - 3 * (t / 3);
+        val = kind == 0 ? Wt[e] : Wt[(((size_t)c * cout + o) * 3 + (2 - u)) * 3 + (2 - v)];
       } else {  // destination [c][t][o], t = 3 u + v
         o = (int)(e % cout);
         const size_t ct = e / cout;
@@ -277,6 +279,98 @@ __global__ void unet_head_kernel(const float *d, int N, int C, int HW, const flo
   }
 }
 
+// ---- tensor-core form: NHWC helpers (one thread per 4 channels of an
+// output pixel, or per pixel) ----
+
+__global__ void unet_stage_nhwc_kernel(const float *in, int N, int cin, long long hw, int cs, float *out) {
+  const long long total = (long long)N * hw;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long n = g / hw, p = g - n * hw;
+    const float *src = in + n * cin * hw + p;
+    float4 *dst = reinterpret_cast<float4 *>(out + g * cs);
+    for (int q = 0; q < cs / 4; ++q) {
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = 4 * q + e < cin ? __ldg(src + (4 * q + e) * hw) : 0.f;
+      dst[q] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+  }
+}
+
+__global__ void unet_pool_nhwc_kernel(const float4 *x, int N, int H, int W, int C4, float4 *y) {
+  const int Ho = H / 2, Wo = W / 2;
+  const long long total = (long long)N * Ho * Wo * C4;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long pix = e / C4;
+    const int c4 = (int)(e - pix * C4);
+    const long long n = pix / ((long long)Ho * Wo);
+    const int r = (int)(pix - n * Ho * Wo), i = r / Wo, j = r - (r / Wo) * Wo;
+    const float4 *s = x + ((n * H + 2 * i) * W + 2 * j) * C4 + c4;
+    const float4 a = __ldg(s), b = __ldg(s + C4), c = __ldg(s + (size_t)W * C4), d = __ldg(s + (size_t)W * C4 + C4);
+    y[e] = make_float4(fmaxf(fmaxf(a.x, b.x), fmaxf(c.x, d.x)), fmaxf(fmaxf(a.y, b.y), fmaxf(c.y, d.y)),
+                       fmaxf(fmaxf(a.z, b.z), fmaxf(c.z, d.z)), fmaxf(fmaxf(a.w, b.w), fmaxf(c.w, d.w)));
+  }
+}
+
+__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float f) {
+  return make_float4((1.f - f) * a.x + f * b.x, (1.f - f) * a.y + f * b.y, (1.f - f) * a.z + f * b.z,
+                     (1.f - f) * a.w + f * b.w);
+}
+
+__global__ void unet_up_nhwc_kernel(const float4 *x, int N, int h, int w, int C4, float4 *y) {
+  const int Ho = 2 * h, Wo = 2 * w;
+  const long long total = (long long)N * Ho * Wo * C4;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long pix = e / C4;
+    const int c4 = (int)(e - pix * C4);
+    const long long n = pix / ((long long)Ho * Wo);
+    const int r = (int)(pix - n * Ho * Wo), p = r / Wo, q = r - (r / Wo) * Wo;
+    int i0, i1, j0, j1;
+    float fi, fj;
+    up_src(p, h, i0, i1, fi);
+    up_src(q, w, j0, j1, fj);
+    const float4 *s = x + n * h * w * C4 + c4;
+    const float4 top = lerp4(__ldg(s + ((size_t)i0 * w + j0) * C4), __ldg(s + ((size_t)i0 * w + j1) * C4), fj);
+    const float4 bot = lerp4(__ldg(s + ((size_t)i1 * w + j0) * C4), __ldg(s + ((size_t)i1 * w + j1) * C4), fj);
+    y[e] = lerp4(top, bot, fi);
+  }
+}
+
+// Output channels in groups of four, each group one pass over the pixel's C
+// channels (C a multiple of 4).
+__global__ void unet_head_nhwc_kernel(const float *d, int N, long long hw, int C, const float *wh, const float *bh,
+                                      int cout, float *out) {
+  const long long total = (long long)N * hw;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const long long n = g / hw, p = g - n * hw;
+    const float4 *dp = reinterpret_cast<const float4 *>(d + g * C);
+    for (int o0 = 0; o0 < cout; o0 += 4) {
+      float acc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[q] = o0 + q < cout ? __ldg(bh + o0 + q) : 0.f;
+      for (int c4 = 0; c4 < C / 4; ++c4) {
+        const float4 v = __ldg(dp + c4);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (o0 + q >= cout) break;
+          const float *wr = wh + (size_t)(o0 + q) * C + 4 * c4;
+          acc[q] = fmaf(__ldg(wr), v.x, acc[q]);
+          acc[q] = fmaf(__ldg(wr + 1), v.y, acc[q]);
+          acc[q] = fmaf(__ldg(wr + 2), v.z, acc[q]);
+          acc[q] = fmaf(__ldg(wr + 3), v.w, acc[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (o0 + q < cout) out[(n * cout + o0 + q) * hw + p] = fmaxf(acc[q], 0.f);
+    }
+  }
+}
+
 unsigned grid_for(size_t work) {
   size_t g = (work + 255) / 256;
   if (g < 1) g = 1;
@@ -320,8 +414,8 @@ cudaError_t unet_forward(const UnetShape &u, const float *params, const float *i
   for (const LayerDesc &d : L) {
     const size_t work = (d.kind == 2 ? 1 : 9) * (size_t)d.cin * d.cout + d.cout;
     DRC_TRACED(tr, "unet fold", st,
-               (unet_fold_kernel<<<grid_for(work), 256, 0, st>>>(params, d.kind, d.cin, d.cout, d.bn, d.src, d.dst,
-                                                                 b.fold)));
+               (unet_fold_kernel<false><<<grid_for(work), 256, 0, st>>>(params, d.kind, d.cin, d.cout, d.bn, d.src,
+                                                                        d.dst, b.fold)));
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   size_t li = 0;
@@ -358,6 +452,101 @@ cudaError_t unet_forward(const UnetShape &u, const float *params, const float *i
   DRC_TRACED(tr, "unet head", st,
              (unet_head_kernel<<<grid_for((size_t)N * H * W), 256, 0, st>>>(d, N, u.base, H * W, wh, bh, u.cout,
                                                                            out)));
+  return cudaGetLastError();
+}
+
+std::vector<UnetLayer> unet_layer_table(const UnetShape &u) { return unet_layers(u, nullptr, nullptr); }
+
+int unet_tc_in_channels(const UnetShape &u) { return u.cin <= 8 ? 8 : u.cin; }
+
+bool unet_tc_shape_ok(const UnetShape &u, int H, int W) {
+  if (u.base % 32 || (u.cin > 8 && u.cin % 32)) return false;
+  for (int l = 0; l <= u.levels; ++l) {
+    const int h = H >> l, w = W >> l;
+    if (h < 1 || w < 1 || w > 128 || 128 % w) return false;
+    const int rows_t = h < 128 / w ? h : 128 / w;
+    if (rows_t < h ? h % rows_t != 0 : 128 % (h * w) != 0) return false;
+  }
+  return true;
+}
+
+size_t unet_tc_pack_bytes(int cin_stored, int cout) {
+  const size_t kb = (9 * (size_t)cin_stored + 31) / 32;  // K blocks of 32 tf32 elements (128 bytes)
+  return kb * (size_t)cout * 128;
+}
+
+size_t unet_tc_carve(const UnetShape &u, int N, int H, int W, char *base, UnetTcBufs *b) {
+  size_t n_dst = 0;
+  const std::vector<LayerDesc> L = unet_layers(u, nullptr, &n_dst);
+  size_t pack = 0;
+  for (const LayerDesc &d : L)
+    if (d.kind != 2) pack += align256(unet_tc_pack_bytes(&d == &L[0] ? unet_tc_in_channels(u) : d.cin, d.cout));
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char * {
+    char *p = base ? base + off : nullptr;
+    off += align256(bytes);
+    return p;
+  };
+  auto takef = [&](size_t floats) { return reinterpret_cast<float *>(take(floats * sizeof(float))); };
+  UnetTcBufs t;
+  t.fold = takef(n_dst);
+  t.B = reinterpret_cast<uint8_t *>(take(pack));
+  t.B_lo = reinterpret_cast<uint8_t *>(take(pack));
+  t.in = takef((size_t)N * H * W * unet_tc_in_channels(u));
+  for (int l = 0; l <= u.levels; ++l) {
+    const size_t px = (size_t)N * (H >> l) * (W >> l);
+    const size_t c = (size_t)u.base << l;
+    t.enc_a[l] = takef(px * c);
+    t.enc[l] = takef(px * c);
+    if (l > 0) t.pool[l] = takef(px * (c / 2));
+    if (l < u.levels) {
+      t.up[l] = takef(px * 2 * c);
+      t.dec_a[l] = takef(px * c);
+      t.dec[l] = takef(px * c);
+    }
+  }
+  if (b) *b = t;
+  return off;
+}
+
+cudaError_t unet_fold_conv_form(const UnetShape &u, const float *params, float *fold, cudaStream_t st, Tracer *tr) {
+  for (const LayerDesc &d : unet_layers(u, nullptr, nullptr)) {
+    const size_t work = (d.kind == 2 ? 1 : 9) * (size_t)d.cin * d.cout + d.cout;
+    DRC_TRACED(tr, "unet fold", st,
+               (unet_fold_kernel<true><<<grid_for(work), 256, 0, st>>>(params, d.kind, d.cin, d.cout, d.bn, d.src,
+                                                                       d.dst, fold)));
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unet_stage_nhwc(const float *in, int N, int cin, long long hw, int cs, float *out,
+                                   cudaStream_t st, Tracer *tr) {
+  DRC_TRACED(tr, "unet stage input", st,
+             (unet_stage_nhwc_kernel<<<grid_for((size_t)N * hw), 256, 0, st>>>(in, N, cin, hw, cs, out)));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unet_pool_nhwc(const float *x, int N, int H, int W, int C, float *y, cudaStream_t st, Tracer *tr) {
+  const size_t work = (size_t)N * (H / 2) * (W / 2) * (C / 4);
+  DRC_TRACED(tr, "unet pool", st,
+             (unet_pool_nhwc_kernel<<<grid_for(work), 256, 0, st>>>(reinterpret_cast<const float4 *>(x), N, H, W,
+                                                                    C / 4, reinterpret_cast<float4 *>(y))));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unet_up_nhwc(const float *x, int N, int h, int w, int C, float *y, cudaStream_t st, Tracer *tr) {
+  const size_t work = (size_t)N * (2 * h) * (2 * w) * (C / 4);
+  DRC_TRACED(tr, "unet up", st,
+             (unet_up_nhwc_kernel<<<grid_for(work), 256, 0, st>>>(reinterpret_cast<const float4 *>(x), N, h, w, C / 4,
+                                                                  reinterpret_cast<float4 *>(y))));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unet_head_nhwc(const float *d, int N, long long hw, int C, const float *wh, int cout, float *out,
+                                  cudaStream_t st, Tracer *tr) {
+  const float *bh = wh + (size_t)cout * C;
+  DRC_TRACED(tr, "unet head", st,
+             (unet_head_nhwc_kernel<<<grid_for((size_t)N * hw), 256, 0, st>>>(d, N, hw, C, wh, bh, cout, out)));
   return cudaGetLastError();
 }
 

@@ -20,6 +20,53 @@ def rel_err(g, o, floor=FLOOR):
     return float(np.max(np.abs(g - o) / den))
 
 
+def unet_float32(params, x, base, levels, cin=7, cout=3):
+    """The paper-form U-Net evaluated in plain IEEE float32 by PyTorch's CPU
+    operators (conv2d, conv_transpose2d, batch_norm, leaky_relu, max_pool2d,
+    bilinear interpolate with half-pixel centres, cat): the error any
+    correct fp32 evaluation carries, the basis of the U-Net's bar."""
+    import torch
+    from paper_1910_02480_gb300 import synth
+    F = torch.nn.functional
+    p = torch.from_numpy(np.ascontiguousarray(params, dtype=np.float32))
+    layers, off = [], 0
+    for kind, ws, nvec in synth.unet_layer_shapes(base, levels, cin, cout):
+        n = int(np.prod(ws))
+        w = p[off:off + n].reshape(ws)
+        off += n
+        co = ws[0] if kind in ("conv", "head") else ws[1]
+        vec = []
+        for _ in range(nvec):
+            vec.append(p[off:off + co])
+            off += co
+        layers.append((kind, w, vec))
+
+    def layer(t, li):
+        kind, w, vec = layers[li]
+        z = (F.conv2d if kind == "conv" else F.conv_transpose2d)(t, w, vec[0], padding=1)
+        if len(vec) == 5:
+            z = F.batch_norm(z, vec[3], vec[4], weight=vec[1], bias=vec[2], training=False, eps=1e-5)
+        return F.leaky_relu(z, 0.01)
+
+    with torch.no_grad():
+        t = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32))
+        li, enc = 0, []
+        for lvl in range(levels + 1):
+            if lvl > 0:
+                t = F.max_pool2d(t, 2)
+            t = layer(layer(t, li), li + 1)
+            li += 2
+            enc.append(t)
+        d = enc[levels]
+        for lvl in range(levels - 1, -1, -1):
+            u = F.interpolate(d, scale_factor=2, mode="bilinear", align_corners=False)
+            d = layer(layer(torch.cat([u, enc[lvl]], 1), li), li + 1)
+            li += 2
+        _, w, vec = layers[li]
+        y = torch.relu(F.conv2d(d, w[:, :, None, None], vec[0]))
+    return y.numpy()
+
+
 def median_rel(g, o, floor=FLOOR):
     g = np.asarray(g, dtype=np.float64)
     o = np.asarray(o, dtype=np.float64)

@@ -98,3 +98,12 @@ def test_unet_size_queries(lib):
     assert ws(1, 20, 32) == 0 and ws(-1, 32, 32) == 0 and ws(1, 32, 32, levels=0) == 0
     assert drc.unet_param_count(64, 7) == 0 and drc.unet_param_count(0, 3) == 0
     assert np.isfinite(ws(1, 32, 32))
+    # which shapes take the tensor cores: whole K blocks of channels and maps
+    # whose rows tile 128-row boxes at every level
+    tc = lambda cin, base, levels, H, W: int(lib.drc_unet_tensor_cores(cin, 3, base, levels, H, W))
+    assert tc(7, 64, 3, 32, 32) == 1 and tc(32, 64, 3, 32, 32) == 1 and tc(7, 32, 2, 32, 16) == 1
+    assert tc(7, 8, 2, 16, 16) == 0    # 8 channels: not a whole K block
+    assert tc(16, 64, 3, 32, 32) == 0  # 16 input channels: neither tap boxes nor whole K blocks
+    assert tc(7, 64, 3, 24, 32) == 0   # 3 x 4 bottleneck: 12-row maps do not tile 128 rows
+    assert tc(7, 64, 1, 256, 256) == 0  # rows wider than a tile
+    assert tc(7, 64, 3, 20, 32) == 0 and tc(7, 64, 0, 32, 32) == 0  # shapes the forward pass refuses

@@ -54,3 +54,16 @@ def test_plain_float32_fails_small_floor_and_passes_ours(widths, N, bias):
     ours = rel_err(out, ref, floor=FLOOR)
     assert small > FP32_TOL, small      # measured 3.9e-4 .. 5.5e-4
     assert ours < 0.25 * FP32_TOL, ours  # measured 7.7e-6 .. 1.0e-5
+
+
+def test_unet_float32_reference_and_its_error():
+    """The plain float32 U-Net that sets the U-Net's bar: it follows the
+    oracle (a wrong layer would miss by orders of magnitude) and its floored
+    error at the paper's size sits below the FP32 bar, near it."""
+    base, levels = 64, 3
+    params = synth.unet_params(base, levels, seed=base + levels)
+    x = np.random.default_rng(2 * 32 + 32).standard_normal((2, 7, 32, 32)).astype(np.float32)
+    ref = oracle.unet_forward(params, x, base, levels)
+    from parity import unet_float32
+    e = rel_err(unet_float32(params, x, base, levels), ref)
+    assert 1e-6 < e < FP32_TOL, e  # measured 6.0e-5
