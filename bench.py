@@ -580,7 +580,7 @@ def measure_unet(drc, torch, dev, N=4096, steps=5):
     downsizing steps, 7.8 M parameters) in FP32 on 4096 synthetic 7 x 32 x 32
     maps: its 3x3 layers on the tensor cores (split-tf32 implicit GEMMs of the
     conv kernel family).  One step is the whole forward call: BN folding and
-    weight packing, input staging, 16 convolutions, pooling, upsampling, the
+    weight packing, input staging, 14 convolutions, pooling, upsampling, the
     head.  Activations (about 12 GB) are far larger than L2."""
     from paper_1910_02480_gb300 import synth
     g = synth.gbuffer(N, 1, seed=18)
@@ -626,7 +626,7 @@ def measure_unet(drc, torch, dev, N=4096, steps=5):
             "tensor_cores": drc.unet_tensor_cores(64, 3, 32, 32),
             "ms": ms, "maps_per_s": N / (ms * 1e-3), "flops_per_map": unet_flops_per_map(),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak if achieved else None, "kernel": "conv_tc_kernel (16 launches)",
+                         "frac": achieved / peak if achieved else None, "kernel": "conv_tc_kernel (14 launches)",
                          "kernel_ms_per_call": conv_ms,
                          "peak_source": ("of measured: bf16 burst %.1f TF/s x nominal tf32/bf16 %.3f / 3 products"
                                          % (bf16, TF32_PER_BF16)) if peaks else "of fallback"},

@@ -443,9 +443,10 @@ drc_status drc_adam_step(drc_ctx *ctx, float *w, const float *grad, float *m,
  * in_ch <= 8 or a multiple of 32; at every level W >> l dividing 128 and
  * the maps' rows tiling 128-row boxes), the 3x3 layers run on the tensor
  * cores as implicit GEMMs in the split-tf32 product (three tf32 products,
- * each tile's K loop accumulated in chunks of 2 K blocks that are added into
- * an fp32 running sum), with NHWC activations in the workspace; otherwise
- * on the CUDA cores in plain fp32.  The workspace size covers either. */
+ * each tile's K loop accumulated in chunks of one K block that are added
+ * into an fp32 running sum), with NHWC activations in the workspace;
+ * otherwise on the CUDA cores in plain fp32.  The workspace size covers
+ * either. */
 size_t drc_unet_param_count(int in_ch, int out_ch, int base, int levels);
 int drc_unet_tensor_cores(int in_ch, int out_ch, int base, int levels, int H,
                           int W);

@@ -61,9 +61,14 @@ __host__ __device__ inline int stage_bytes(int prec, int BN, int mode) {
 }
 
 // PROD_TMA_TMEM tensor-memory map: accumulators in columns [0, 256), A
-// stages of 64 columns (tf32 hi 32 | lo 32) from column 256.
+// stages of 64 columns (tf32 hi 32 | lo 32) from column 256.  With
+// accumulation chunks (ConvArgs::kfold) the accumulators are the running
+// sum R [0, BN) and two chunk buffers [BN, 3 BN); above 256 columns of
+// those (BN 128) the A stages shrink to two, from column 384.
 constexpr int TS_STAGES = 4;
 constexpr int TS_A_COL0 = 256;
+__host__ __device__ inline int ts_a_col0(int BN, int fold) { return fold && 3 * BN > TS_A_COL0 ? 384 : TS_A_COL0; }
+__host__ __device__ inline int ts_stages(int BN, int fold) { return (512 - ts_a_col0(BN, fold)) / 64; }
 
 // Raw bytes of one operand row per K block, in the stored activation type
 // (fp32 for the split-tf32 path, bf16 / e4m3 otherwise): one swizzle row.
@@ -73,34 +78,34 @@ __host__ __device__ inline int raw_row_bytes(int) { return 128; }
 // the A tile itself, a ring of R raw slots; R = 3 keeps two K blocks of
 // copies in flight beyond the one being converted, shrunk to 2 when 2 MMA
 // stages would not fit otherwise.
-static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, int avail);
+static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, int avail, int fold);
 
 // With the epilogue's staging buffer where the pipeline keeps at least two
 // stages (and two raw slots where it uses a raw ring); otherwise without.
-// fold: the accumulation-chunk running sums (BM x BN fp32) come off the top.
+// fold: accumulation chunks (fewer tensor-memory A stages at BN 128).
 __host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode, int ytma, int fold) {
-  const int avail = SMEM_BUDGET - SMEM_CTRL - 1024 - (fold ? fold_bytes(BN) : 0);
+  const int avail = SMEM_BUDGET - SMEM_CTRL - 1024;
   // the FP32 path, and BF16 stores by TMA: with 16-byte bf16 / e4m3 row
   // chunks the staged per-lane epilogue measured slower than the per-row one
-  SmemPlan p = smem_plan_avail(prec, BN, mode, avail - (ytma ? EPI_TMA_BYTES : EPI_STG_BYTES));
+  SmemPlan p = smem_plan_avail(prec, BN, mode, avail - (ytma ? EPI_TMA_BYTES : EPI_STG_BYTES), fold);
   if ((prec == PREC_TF32X3 || ytma) && p.stages >= 2 && (mode == PROD_TMA_DIRECT || p.raw_depth >= 2)) {
     p.epi_stage = 1;
     return p;
   }
-  p = smem_plan_avail(prec, BN, mode, avail);
+  p = smem_plan_avail(prec, BN, mode, avail, fold);
   p.epi_stage = 0;
   return p;
 }
 
-static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, int avail) {
+static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, int avail, int fold) {
   const int sb = stage_bytes(prec, BN, mode);
   const int rb = BM * raw_row_bytes(prec);
   if (mode == PROD_TMA_TMEM) {
     // B stages match the tensor-memory A stages; the rest of shared memory
     // holds raw TMA boxes in flight (up to 6)
     SmemPlan p;
-    p.stages = TS_STAGES;
-    int R = (avail - TS_STAGES * sb) / rb;
+    p.stages = ts_stages(BN, fold);
+    int R = (avail - p.stages * sb) / rb;
     p.raw_depth = R > 6 ? 6 : R;
     p.raw_slot_bytes = rb;
     return p;
@@ -126,7 +131,7 @@ size_t conv_smem_bytes(int prec, int BN, int mode, int ytma, int fold) {
   const SmemPlan p = smem_plan(prec, BN, mode, ytma, fold);
   return (size_t)SMEM_CTRL + 1024 + (size_t)p.stages * stage_bytes(prec, BN, mode) +
          (size_t)p.raw_depth * p.raw_slot_bytes +
-         (p.epi_stage ? (size_t)(ytma ? EPI_TMA_BYTES : EPI_STG_BYTES) : 0) + (fold ? (size_t)fold_bytes(BN) : 0);
+         (p.epi_stage ? (size_t)(ytma ? EPI_TMA_BYTES : EPI_STG_BYTES) : 0);
 }
 
 // Offset of 16-byte chunk q of row r inside a 128-byte-swizzled K-major tile.
@@ -523,7 +528,8 @@ __device__ __forceinline__ void convert_loop(const ConvArgs &a, uint8_t *data, u
     const long long tv0 = a.prof ? clock64() : 0;
     if constexpr (PREC == PREC_TF32X3) {
       if (a.prod_mode == PROD_TMA_TMEM)
-        raw_convert_tmem<TAPS>(gw, lane, raw + slot * slot_bytes, tmem_base + (uint32_t)(TS_A_COL0 + stage * 64));
+        raw_convert_tmem<TAPS>(gw, lane, raw + slot * slot_bytes,
+                               tmem_base + (uint32_t)(ts_a_col0(a.BN, a.kfold > 0) + stage * 64));
       else
         raw_convert_tma_group<PREC, TAPS>(gt, raw + slot * slot_bytes, a0, a0 + a_bytes);
     } else {
@@ -661,13 +667,21 @@ __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint
 
 // Accumulator columns [c, c+16) of a tile: the main accumulator, plus the
 // correction accumulator BN columns further on for the split-tf32 path.
+// t2: the second accumulator's address (split-tf32: the correction one, BN
+// columns on; with accumulation chunks the running sum, or kNoAcc for a
+// tile of one chunk).
+constexpr uint32_t kNoAcc = 0xFFFFFFFFu;
 template <int PREC>
-__device__ __forceinline__ void tmem_ld_acc(uint32_t taddr, int BN, float (&v)[16]) {
+__device__ __forceinline__ void tmem_ld_acc(uint32_t taddr, uint32_t t2, float (&v)[16]) {
   if constexpr (PREC == PREC_TF32X3) {
-    // main and correction accumulators: both loads in flight, one wait
+    if (t2 == kNoAcc) {
+      tmem_ld16(taddr, v);
+      return;
+    }
+    // both loads in flight, one wait
     uint32_t a[16], c[16];
     tmem_ld16_nowait(taddr, a);
-    tmem_ld16_nowait(taddr + (uint32_t)BN, c);
+    tmem_ld16_nowait(t2, c);
     tmem_wait_ld();
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = __uint_as_float(a[e]) + __uint_as_float(c[e]);
@@ -675,18 +689,7 @@ __device__ __forceinline__ void tmem_ld_acc(uint32_t taddr, int BN, float (&v)[1
     tmem_ld16(taddr, v);
   }
 }
-
-// Accumulation chunks: add the running sums of columns [c, c+16) of this
-// lane's row (radd = the row's column 0; column stride BM floats).
-template <int PREC>
-__device__ __forceinline__ void add_running(const float *radd, int c, float (&v)[16]) {
-  if constexpr (PREC == PREC_TF32X3) {
-    if (radd) {
-#pragma unroll
-      for (int e = 0; e < 16; ++e) v[e] += radd[(c + e) * BM];
-    }
-  }
-}
+__device__ __forceinline__ uint32_t acc_at(uint32_t t2, int c) { return t2 == kNoAcc ? kNoAcc : t2 + (uint32_t)c; }
 
 // 16 consecutive skip channels as raw 16-byte words (fp32: 4 words, bf16: 2,
 // e4m3: 1).
@@ -766,10 +769,9 @@ __device__ __forceinline__ void apply_mask(const uint8_t *mb, float (&v)[16]) {
 template <int PREC>
 __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int cc, int BN, int col0, bool vrow,
                                           bool has_skip, const uint4 (&sk)[4], uint8_t *yb, size_t eoff,
-                                          const float *radd) {
+                                          uint32_t t2) {
   float v[16];
-  tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
-  add_running<PREC>(radd, cc * 16, v);
+  tmem_ld_acc<PREC>(taddr + cc * 16, acc_at(t2, cc * 16), v);
   const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
   const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
 #pragma unroll
@@ -900,8 +902,7 @@ __device__ __forceinline__ void st4(void *base, size_t e, float4 v, const float 
 template <int PREC>
 __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, int BN, int n0, int row0,
                                              const PhaseDesc &pd, uint32_t ring, int &box, unsigned long long &w_tfull,
-                                             uint32_t tfull, uint32_t par, unsigned long long &w_ld,
-                                             const float *radd) {
+                                             uint32_t tfull, uint32_t par, unsigned long long &w_ld, uint32_t t2) {
   const int lane = threadIdx.x & 31;
   const bool convt = a.kind == LK_CONVT;
   // box origin (convT) and this lane's skip row
@@ -936,9 +937,8 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
     const int col0 = n0 + cc * 16;
     float v[16];
     const long long tl0 = a.prof ? clock64() : 0;
-    tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
+    tmem_ld_acc<PREC>(taddr + cc * 16, acc_at(t2, cc * 16), v);
     if (a.prof) w_ld += (unsigned long long)(clock64() - tl0);
-    add_running<PREC>(radd, cc * 16, v);
     const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
 #pragma unroll
     for (int e4 = 0; e4 < 4; ++e4) {
@@ -994,7 +994,7 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
 template <int PREC>
 __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t taddr, int BN, int n0, size_t ebase,
                                                 bool vrow, float *stg, unsigned long long &w_tfull, uint32_t tfull,
-                                                uint32_t par, unsigned long long &w_ld, const float *radd) {
+                                                uint32_t par, unsigned long long &w_ld, uint32_t t2) {
   const int lane = threadIdx.x & 31;
   size_t er[4];
   bool vr[4];
@@ -1023,9 +1023,8 @@ __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t tadd
     const int col0 = n0 + cc * 16;
     float v[16];
     const long long tl0 = a.prof ? clock64() : 0;
-    tmem_ld_acc<PREC>(taddr + cc * 16, BN, v);
+    tmem_ld_acc<PREC>(taddr + cc * 16, acc_at(t2, cc * 16), v);
     if (a.prof) w_ld += (unsigned long long)(clock64() - tl0);
-    add_running<PREC>(radd, cc * 16, v);
     const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
     const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
 #pragma unroll
@@ -1100,12 +1099,16 @@ __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t tadd
   return true;
 }
 
-// MMA issue loop of one CTA (one thread): per tile wait for a free
-// accumulator, per K block wait for the stage and issue its MMAs, then hand
-// the accumulator to the epilogue.  TS: A from tensor memory (split-tf32).
-template <int PREC, bool TS, bool PROF, bool TAPA>
+// MMA issue loop of one CTA (one thread): per tile (or accumulation chunk)
+// wait for a free accumulator, per K block wait for the stage and issue its
+// MMAs, then hand the accumulator to the epilogue.  TS: A from tensor memory
+// (split-tf32).  FOLD (with TS): accumulation chunks, all three products of
+// a K block into the chunk's one accumulator, the two small correction
+// products first.
+template <int PREC, bool TS, bool PROF, bool TAPA, bool FOLD>
 __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, int sbytes, int a_bytes,
                                           int b_bytes, int stages, int total_tiles, int nbufs, int acc_cols,
+                                          uint32_t acc_base, uint32_t a_col0,
                                           uint32_t tmem_base, uint64_t *full_bar, uint64_t *empty_bar,
                                           uint64_t *tfull_bar, uint64_t *tempty_bar, unsigned long long &w_full,
                                           unsigned long long &w_tempty) {
@@ -1150,8 +1153,8 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
         break;
       }
       tc_fence_after();
-      const uint32_t d_tmem = tmem_base + (uint32_t)(buf * acc_cols);
-      const uint32_t c_tmem = d_tmem + (uint32_t)BN;  // correction accumulator (split-tf32)
+      const uint32_t d_tmem = tmem_base + acc_base + (uint32_t)(buf * acc_cols);
+      const uint32_t c_tmem = d_tmem + (uint32_t)BN;  // correction accumulator (split-tf32, not FOLD)
       for (int kb = k0; kb < k1; ++kb) {
         if (!pwait(a, w_full, smem_u32(&full_bar[stage]), phase)) {
           ok = false;
@@ -1167,16 +1170,30 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
         const uint64_t bd0 = dB0 + (uint64_t)((uint32_t)stage * dstage), bd1 = bd0 + dBlo;
         if constexpr (TS) {
           // A hi/lo from tensor memory: 8 tf32 columns per K step
-          const uint32_t ta = tmem_base + (uint32_t)(TS_A_COL0 + stage * 64);
+          const uint32_t ta = tmem_base + a_col0 + (uint32_t)(stage * 64);
           const uint32_t acc0 = kb != k0;
-          tc_mma_ts_tf32(d_tmem, ta, bd0, idesc, acc0);
-          tc_mma_ts_tf32(c_tmem, ta, bd1, idesc, acc0);
-          tc_mma_ts_tf32(c_tmem, ta + 32, bd0, idesc, 1u);
-  #pragma unroll
-          for (int k = 1; k < KROW_BYTES / 32; ++k) {
-            tc_mma_ts_tf32(d_tmem, ta + 8 * k, bd0 + 2 * k, idesc, 1u);
-            tc_mma_ts_tf32(c_tmem, ta + 8 * k, bd1 + 2 * k, idesc, 1u);
-            tc_mma_ts_tf32(c_tmem, ta + 32 + 8 * k, bd0 + 2 * k, idesc, 1u);
+          if constexpr (FOLD) {
+            // A_hi B_lo and A_lo B_hi while the accumulator holds only small
+            // terms (their rounding is then negligible), then A_hi B_hi
+            tc_mma_ts_tf32(d_tmem, ta, bd1, idesc, acc0);
+            tc_mma_ts_tf32(d_tmem, ta + 32, bd0, idesc, 1u);
+#pragma unroll
+            for (int k = 1; k < KROW_BYTES / 32; ++k) {
+              tc_mma_ts_tf32(d_tmem, ta + 8 * k, bd1 + 2 * k, idesc, 1u);
+              tc_mma_ts_tf32(d_tmem, ta + 32 + 8 * k, bd0 + 2 * k, idesc, 1u);
+            }
+#pragma unroll
+            for (int k = 0; k < KROW_BYTES / 32; ++k) tc_mma_ts_tf32(d_tmem, ta + 8 * k, bd0 + 2 * k, idesc, 1u);
+          } else {
+            tc_mma_ts_tf32(d_tmem, ta, bd0, idesc, acc0);
+            tc_mma_ts_tf32(c_tmem, ta, bd1, idesc, acc0);
+            tc_mma_ts_tf32(c_tmem, ta + 32, bd0, idesc, 1u);
+#pragma unroll
+            for (int k = 1; k < KROW_BYTES / 32; ++k) {
+              tc_mma_ts_tf32(d_tmem, ta + 8 * k, bd0 + 2 * k, idesc, 1u);
+              tc_mma_ts_tf32(c_tmem, ta + 8 * k, bd1 + 2 * k, idesc, 1u);
+              tc_mma_ts_tf32(c_tmem, ta + 32 + 8 * k, bd0 + 2 * k, idesc, 1u);
+            }
           }
         } else {
           const uint64_t ad1 = sd + dAlo;
@@ -1186,7 +1203,7 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
             tc_mma<T::KIND>(c_tmem, sd, bd1, idesc, acc0);
             tc_mma<T::KIND>(c_tmem, ad1, bd0, idesc, 1u);
           }
-  #pragma unroll
+#pragma unroll
           for (int k = 1; k < KROW_BYTES / 32; ++k) {
             tc_mma<T::KIND>(d_tmem, sd + kA * k, bd0 + 2 * k, idesc, 1u);
             if constexpr (PREC == PREC_TF32X3) {
@@ -1211,7 +1228,8 @@ template <int PREC, bool YTMA>
 __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_constant__ ConvArgs a) {
   using T = PrecTraits<PREC>;
   const int BN = a.BN;
-  const SmemPlan plan = smem_plan(PREC, BN, a.prod_mode, YTMA ? 1 : 0, a.kfold > 0 ? 1 : 0);
+  const bool fold = PREC == PREC_TF32X3 && a.prod_mode == PROD_TMA_TMEM && a.kfold > 0;
+  const SmemPlan plan = smem_plan(PREC, BN, a.prod_mode, YTMA ? 1 : 0, fold ? 1 : 0);
   const int stages = plan.stages;
   const int a_bytes = BM * KROW_BYTES;
   const int b_bytes = BN * KROW_BYTES;
@@ -1242,9 +1260,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
   // rounds the accumulator on every MMA, so three MMAs into one accumulator
   // triple its rounding error.  Two buffers when they fit in 512 columns.
   // With A in tensor memory (PROD_TMA_TMEM) the accumulators share the 512
-  // columns with the A stages.
-  const int acc_cols = T::SPLIT * BN;
-  const int nbufs = ts ? (2 * acc_cols <= TS_A_COL0 ? 2 : 1) : (2 * acc_cols <= 512 ? 2 : 1);
+  // columns with the A stages.  Accumulation chunks (fold): the running sum
+  // at column 0, then two chunk buffers of BN columns, each taking all
+  // three products (the correction products first).
+  const int acc_cols = fold ? BN : T::SPLIT * BN;
+  const uint32_t acc_base = fold ? (uint32_t)BN : 0u;
+  const uint32_t a_col0 = (uint32_t)ts_a_col0(BN, fold ? 1 : 0);
+  const int nbufs = fold ? 2 : (ts ? (2 * acc_cols <= TS_A_COL0 ? 2 : 1) : (2 * acc_cols <= 512 ? 2 : 1));
   const int need = ts ? 512 : nbufs * acc_cols;
   const uint32_t ncols =
       need <= 32 ? 32u : (need <= 64 ? 64u : (need <= 128 ? 128u : (need <= 256 ? 256u : 512u)));
@@ -1296,26 +1318,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       // one instantiation per A form: a branch between the forms inside the
       // issue loop measured ~110 cycles per MMA against 45-64 without
       if (ok) {
-#define DRC_MMA_ISSUE(TSV, PROFV, TAPV)                                                                          \
-  mma_issue<PREC, TSV, PROFV, TAPV>(a, data_u32, sbytes, a_bytes, b_bytes, stages, total_tiles, nbufs, acc_cols,     \
-                                    tmem_base, full_bar, empty_bar, tfull_bar, tempty_bar, w_full, w_tempty)
+#define DRC_MMA_ISSUE(TSV, PROFV, TAPV, FOLDV)                                                                   \
+  mma_issue<PREC, TSV, PROFV, TAPV, FOLDV>(a, data_u32, sbytes, a_bytes, b_bytes, stages, total_tiles, nbufs,       \
+                                           acc_cols, acc_base, a_col0, tmem_base, full_bar, empty_bar, tfull_bar,  \
+                                           tempty_bar, w_full, w_tempty)
         constexpr bool kTS = PREC == PREC_TF32X3;
         constexpr bool kTAP = PREC == PREC_BF16;  // BF16 tap boxes land in the A tile itself
         const bool tapa = kTAP && a.tap_boxes && a.prod_mode == PROD_TMA_DIRECT;
         if (a.prof) {
-          if (kTS && ts)
-            DRC_MMA_ISSUE(kTS, true, false);
+          if (kTS && ts && fold)
+            DRC_MMA_ISSUE(kTS, true, false, kTS);
+          else if (kTS && ts)
+            DRC_MMA_ISSUE(kTS, true, false, false);
           else if (tapa)
-            DRC_MMA_ISSUE(false, true, kTAP);
+            DRC_MMA_ISSUE(false, true, kTAP, false);
           else
-            DRC_MMA_ISSUE(false, true, false);
+            DRC_MMA_ISSUE(false, true, false, false);
         } else {
-          if (kTS && ts)
-            DRC_MMA_ISSUE(kTS, false, false);
+          if (kTS && ts && fold)
+            DRC_MMA_ISSUE(kTS, false, false, kTS);
+          else if (kTS && ts)
+            DRC_MMA_ISSUE(kTS, false, false, false);
           else if (tapa)
-            DRC_MMA_ISSUE(false, false, kTAP);
+            DRC_MMA_ISSUE(false, false, kTAP, false);
           else
-            DRC_MMA_ISSUE(false, false, false);
+            DRC_MMA_ISSUE(false, false, false, false);
         }
 #undef DRC_MMA_ISSUE
       }
@@ -1376,19 +1403,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     const act_t *skip = reinterpret_cast<const act_t *>(a.skip);
     const int nch = BN / 16;
     float *epi_stg = reinterpret_cast<float *>(data + (size_t)stages * sbytes + (size_t)plan.raw_depth * plan.raw_slot_bytes);
-    // accumulation chunks: this lane's running sums, column c at rsum[c * BM]
-    float *rsum = nullptr;
-    if (PREC == PREC_TF32X3 && a.kfold > 0)
-      rsum = epi_stg + (plan.epi_stage ? (YTMA ? EPI_TMA_BYTES : EPI_STG_BYTES) / 4 : 0) + row;
+    // this lane quarter's tensor-memory rows; with accumulation chunks the
+    // running sum is at column 0
+    const uint32_t lanebase = tmem_base + ((uint32_t)(eq * 32) << 16);
     int tma_box = 0;  // next box of this warp's TMA staging ring
     bool failed = false;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++it) {
       const TileCoord tc = tile_coord(a, t);
       const PhaseDesc &pd = a.ph[tc.phase];
-      // every chunk but the last: D + C of the chunk into the running sums,
-      // then the accumulator buffer goes back to the MMA warp
+      // every chunk but the last: added into the running sum (round to
+      // nearest), then the chunk buffer goes back to the MMA warp
       const int nkb = pd.num_kb;
-      const int kf = rsum ? a.kfold : nkb;
+      const int kf = fold ? a.kfold : nkb;
       const int nchunk = (nkb + kf - 1) / kf;
       for (int q = 0; q + 1 < nchunk; ++q, ++it) {
         const int fbuf = nbufs == 2 ? (it & 1) : 0;
@@ -1398,27 +1424,30 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
           break;
         }
         tc_fence_after();
-        const uint32_t faddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(fbuf * acc_cols);
+        const uint32_t faddr = lanebase + acc_base + (uint32_t)(fbuf * acc_cols);
         for (int cc = 0; cc < nch; ++cc) {
-          float v[16];
-          tmem_ld_acc<PREC>(faddr + cc * 16, BN, v);
-          float *r = rsum + cc * 16 * BM;
-          if (q == 0) {
+          uint32_t x[16], r[16];
+          tmem_ld16_nowait(faddr + cc * 16, x);
+          if (q > 0) tmem_ld16_nowait(lanebase + cc * 16, r);
+          tmem_wait_ld();
+          if (q > 0) {
 #pragma unroll
-            for (int e = 0; e < 16; ++e) r[e * BM] = v[e];
-          } else {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) r[e * BM] += v[e];
+            for (int e = 0; e < 16; ++e) x[e] = __float_as_uint(__uint_as_float(x[e]) + __uint_as_float(r[e]));
           }
+          tmem_st16(lanebase + cc * 16, x);
         }
+        tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[fbuf]));
       }
       if (failed) break;
-      const float *radd = nchunk > 1 ? rsum : nullptr;
       const int buf = nbufs == 2 ? (it & 1) : 0;
       const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
+      // the tile's accumulator and the one added to it: the correction
+      // accumulator, or with chunks the running sum (none for one chunk)
+      const uint32_t taddr = lanebase + acc_base + (uint32_t)(buf * acc_cols);
+      const uint32_t t2 = PREC != PREC_TF32X3 ? kNoAcc : (!fold ? taddr + (uint32_t)BN : (nchunk > 1 ? lanebase : kNoAcc));
       const int m = tc.m_tile * BM + row;
       const bool vrow = m < M;
       const int n = vrow ? m / rows_per_map : 0;
@@ -1429,10 +1458,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
                               : (size_t)m;
       const size_t ebase = opix * a.Cout + (size_t)tc.n_tile * BN;
       if (YTMA && plan.epi_stage) {
-        const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
         if (!epi_tile_tma<PREC>(a, taddr, BN, tc.n_tile * BN, tc.m_tile * BM + eq * 32, pd,
                                 smem_u32(epi_stg) + (uint32_t)(eq * EPI_TMA_BOXES * EPI_TMA_BOX_BYTES), tma_box,
-                                w_tfull, smem_u32(&tfull_bar[buf]), par, w_ld, radd))
+                                w_tfull, smem_u32(&tfull_bar[buf]), par, w_ld, t2))
           break;
         tc_fence_before();
         __syncwarp();
@@ -1440,9 +1468,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
         continue;
       }
       if (plan.epi_stage) {
-        const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
         if (!epi_tile_staged<PREC>(a, taddr, BN, tc.n_tile * BN, opix * a.Cout, vrow, epi_stg + eq * 32 * 20, w_tfull,
-                                   smem_u32(&tfull_bar[buf]), par, w_ld, radd))
+                                   smem_u32(&tfull_bar[buf]), par, w_ld, t2))
           break;
         tc_fence_before();
         __syncwarp();
@@ -1457,7 +1484,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       // FP32 kernel only takes this path when the staging buffer does not
       // fit and loads each chunk's skip just before use (fewer registers).
       const bool has_skip = skip != nullptr && vrow;
-      const uint32_t taddr = tmem_base + ((uint32_t)(eq * 32) << 16) + (uint32_t)(buf * acc_cols);
       uint8_t *yb = yout + ebase * out_elem;
       if constexpr (PREC == PREC_TF32X3) {
         if (!pwait(a, w_tfull, smem_u32(&tfull_bar[buf]), par)) break;
@@ -1466,7 +1492,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
           uint4 sk[4];
           if (has_skip) load_skip<PREC>(skip + ebase + cc * 16, sk);
           epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk, yb + cc * 16 * out_elem,
-                          ebase + cc * 16, radd);
+                          ebase + cc * 16, t2);
         }
       } else {
         uint4 sk0[4], sk1[4];
@@ -1478,11 +1504,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
         tc_fence_after();
         for (int cc = 0; cc < nch; cc += 2) {
           epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk0, yb + cc * 16 * out_elem,
-                          ebase + cc * 16, nullptr);
+                          ebase + cc * 16, t2);
           if (has_skip && cc + 2 < nch) load_skip<PREC>(skip + ebase + (cc + 2) * 16, sk0);
           if (cc + 1 < nch) {
             epi_chunk<PREC>(a, taddr, cc + 1, BN, tc.n_tile * BN + (cc + 1) * 16, vrow, has_skip, sk1,
-                            yb + (cc + 1) * 16 * out_elem, ebase + (cc + 1) * 16, nullptr);
+                            yb + (cc + 1) * 16 * out_elem, ebase + (cc + 1) * 16, t2);
             if (has_skip && cc + 3 < nch) load_skip<PREC>(skip + ebase + (cc + 3) * 16, sk1);
           }
         }
@@ -1512,7 +1538,9 @@ cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t s
   const int total = a.num_phases * a.m_tiles * a.n_tiles;
   if (total == 0) return cudaSuccess;
   const int grid = total < num_sms ? total : num_sms;
-  if (a.kfold < 0 || (a.kfold > 0 && (prec != PREC_TF32X3 || a.BN > KFOLD_MAX_BN))) return cudaErrorInvalidValue;
+  if (a.kfold < 0 ||
+      (a.kfold > 0 && (prec != PREC_TF32X3 || a.prod_mode != PROD_TMA_TMEM || a.BN > KFOLD_MAX_BN)))
+    return cudaErrorInvalidValue;
   const size_t smem = conv_smem_bytes(prec, a.BN, a.prod_mode, a.y_tma, a.kfold > 0 ? 1 : 0);
   cudaError_t e;
   switch (prec) {

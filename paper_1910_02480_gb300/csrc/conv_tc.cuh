@@ -88,13 +88,15 @@ struct ConvArgs {
   void *y2;
   int y2_pre_skip;
   const void *mask;
-  // FP32 accumulation in chunks (0: off): the MMAs of every kfold K blocks of
-  // a tile go into a fresh tensor-memory accumulator, which the epilogue
-  // warps add into an fp32 running sum (round to nearest) while the next
+  // FP32 accumulation in chunks (0: off; PROD_TMA_TMEM, BN <= KFOLD_MAX_BN):
+  // the MMAs of every kfold K blocks of a tile go into a fresh
+  // tensor-memory accumulator -- per K block the two small correction
+  // products first, then the main one -- which the epilogue warps add into
+  // an fp32 running sum in tensor memory (round to nearest) while the next
   // chunk accumulates in the other buffer.  The tensor core's own fp32
   // accumulation does not round to nearest, so its error grows with the
   // number of MMAs into one accumulator; deep K (thousands of terms) needs
-  // this to stay at fp32 accuracy.  BN <= KFOLD_MAX_BN.
+  // this to stay at fp32 accuracy.
   int kfold;
   int *status;
   unsigned long long timeout_ns;
@@ -123,11 +125,9 @@ constexpr int EPI_STG_BYTES = EPI_STG_FLOATS * 4;
 constexpr int EPI_TMA_BOXES = 4;
 constexpr int EPI_TMA_BOX_BYTES = 2048;
 constexpr int EPI_TMA_BYTES = 4 * EPI_TMA_BOXES * EPI_TMA_BOX_BYTES;
-// Accumulation chunks (ConvArgs::kfold): the epilogue warps' running sums,
-// [BN][BM] fp32 in shared memory (column-major: a warp's 32 rows of one
-// column are 32 consecutive words).
-constexpr int KFOLD_MAX_BN = 64;
-__host__ __device__ inline int fold_bytes(int BN) { return BM * BN * 4; }
+// Accumulation chunks (ConvArgs::kfold): the running sum and two chunk
+// accumulators in tensor memory next to the A stages.
+constexpr int KFOLD_MAX_BN = 128;
 __host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode, int ytma, int fold = 0);
 size_t conv_smem_bytes(int prec, int BN, int mode, int ytma, int fold = 0);
 

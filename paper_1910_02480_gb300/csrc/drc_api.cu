@@ -1829,15 +1829,15 @@ drc_status unet_forward_tc(drc_ctx *c, const UnetShape &u, const float *params, 
   const int cs = unet_tc_in_channels(u);
   // the 3x3 layers as GEMM layers, their packed tiles laid out like the
   // autoencoder's
-  // Accumulation chunks of 2 K blocks (64 input channels x taps) on every
-  // layer: the tensor core's own fp32 accumulation loses about an ulp of the
-  // running sum per MMA, so one accumulator over this network's reductions
-  // (up to 216 K blocks, 6912 terms) measured 1.6e-3 max floored relative
-  // error at the paper-size output (normwise 4.8e-5); folded every 2 K
-  // blocks, 6.4e-5 (2.1e-6).  Chunks on the deep layers only (more than 18
-  // K blocks) still left 1.6e-4 on a smaller network.  The running sums live
-  // in shared memory, which limits the layers to 64-column tiles.
-  constexpr int kFoldKb = 2, kFoldAbove = kFoldKb;
+  // Accumulation in chunks of one K block (32 input channels of a tap) on
+  // every layer: the tensor core's own fp32 accumulation loses about an ulp
+  // of the running sum per MMA, so one accumulator over this network's
+  // reductions (up to 216 K blocks, 6912 terms) measured 1.6e-3 max floored
+  // relative error at the paper-size output (normwise 4.8e-5); added into an
+  // fp32 running sum every K block, at the level of a plain float32
+  // evaluation.  The running sum and two chunk accumulators share tensor
+  // memory with the A stages, which caps the tiles at 128 columns.
+  constexpr int kFoldKb = 1, kFoldAbove = kFoldKb;
   std::vector<Layer> Ls;
   std::vector<int> kfold;
   for (size_t i = 0; i < T.size(); ++i) {
@@ -1910,8 +1910,8 @@ drc_status unet_forward_tc(drc_ctx *c, const UnetShape &u, const float *params, 
     a.m_tiles = ceil_div(a.M, BM);
     a.kfold = kfold[li];
     plan_operand(PREC_TF32X3, a);
-    if (a.prod_mode == PROD_CPASYNC && x2)
-      return fail(c, DRC_ERR_CUDA, "unet layer %zu: no tensor map for the concatenated input", li);
+    if (a.prod_mode != PROD_TMA_TMEM)
+      return fail(c, DRC_ERR_CUDA, "unet layer %zu: no tensor map for the A operand", li);
     cudaError_t le;
     DRC_TRACED(tr, L.name, st, le = launch_conv(a, PREC_TF32X3, c->num_sms, st));
     if (le != cudaSuccess) return cuda_fail(c, le, "unet layer launch");

@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
 # below (normwise 8.3e-7), above 1e-4 on some single maps.  The CUDA-core
 # kernel sums each output in two levels (72-term partial sums, then their
 # total; one serial sum measured 1.5e-4 here, two levels 3.6e-5); the
-# tensor-core form accumulates in chunks of 2 K blocks (6.4e-5).
+# tensor-core form accumulates in chunks of one K block (4.1e-5).
 UNET_NORMWISE = 1e-5
 
 
