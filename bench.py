@@ -575,7 +575,7 @@ def unet_layer_flops(base=64, levels=3, H=32, W=32, cin=7):
     return out
 
 
-def measure_unet(drc, torch, dev, N=4096, steps=5):
+def measure_unet(drc, torch, dev, N=4096, steps=5, warmup=3):
     """The paper's own network form (Sec. 3.3: a U-Net, base 64, three
     downsizing steps, 7.8 M parameters) in FP32 on 4096 synthetic 7 x 32 x 32
     maps: its 3x3 layers on the tensor cores (split-tf32 implicit GEMMs of the
@@ -589,7 +589,7 @@ def measure_unet(drc, torch, dev, N=4096, steps=5):
     ctx = drc.Context([16], synth.he_weights([16]), precision="fp32")
     net = drc.UNet(ctx, synth.unet_params(64, 3, seed=0), 64, 3)
     out = torch.empty((N, 3, 32, 32), device=dev)
-    for _ in range(3):
+    for _ in range(warmup):
         net.forward(xd, out=out)
     torch.cuda.synchronize()
     ctx.read_timing()
@@ -773,6 +773,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="default tile widths instead of drc_autotune")
     ap.add_argument("--maps", type=int, default=N_MAPS, help="maps per step (profiling of smaller cases)")
     ap.add_argument("--frame", default="%dx%d" % (IMG_W, IMG_H), help="G-buffer WxH (profiling)")
+    ap.add_argument("--unet-only", type=int, default=0, metavar="N",
+                    help="only the paper-form U-Net on N maps (profiling): one JSON line, --steps timed forwards")
     args = ap.parse_args()
     set_workload(args.maps, args.frame)
 
@@ -788,6 +790,10 @@ def main():
     from paper_1910_02480_gb300 import build, synth
     build.build()
     torch.cuda.set_device(local)
+    if args.unet_only > 0:
+        print(json.dumps(measure_unet(drc, torch, torch.device("cuda", local), N=args.unet_only,
+                                      steps=max(1, args.steps), warmup=max(1, args.warmup))))
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

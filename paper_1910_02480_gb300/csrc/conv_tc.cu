@@ -671,10 +671,10 @@ __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint
 // columns on; with accumulation chunks the running sum, or kNoAcc for a
 // tile of one chunk).
 constexpr uint32_t kNoAcc = 0xFFFFFFFFu;
-template <int PREC>
+template <int PREC, bool FOLD>
 __device__ __forceinline__ void tmem_ld_acc(uint32_t taddr, uint32_t t2, float (&v)[16]) {
   if constexpr (PREC == PREC_TF32X3) {
-    if (t2 == kNoAcc) {
+    if (FOLD && t2 == kNoAcc) {
       tmem_ld16(taddr, v);
       return;
     }
@@ -689,7 +689,13 @@ __device__ __forceinline__ void tmem_ld_acc(uint32_t taddr, uint32_t t2, float (
     tmem_ld16(taddr, v);
   }
 }
-__device__ __forceinline__ uint32_t acc_at(uint32_t t2, int c) { return t2 == kNoAcc ? kNoAcc : t2 + (uint32_t)c; }
+template <bool FOLD>
+__device__ __forceinline__ uint32_t acc_at(uint32_t t2, int c) {
+  if constexpr (FOLD)
+    return t2 == kNoAcc ? kNoAcc : t2 + (uint32_t)c;
+  else
+    return t2 + (uint32_t)c;
+}
 
 // 16 consecutive skip channels as raw 16-byte words (fp32: 4 words, bf16: 2,
 // e4m3: 1).
@@ -733,9 +739,15 @@ __device__ __forceinline__ void store16(uint8_t *yb, const float (&v)[16]) {
   }
 }
 
-// The epilogue's rectifier: ReLU, or LeakyReLU with a.slope in (0, 1).
+// The epilogue's rectifier: ReLU, or in the U-Net form (FOLD) LeakyReLU
+// max(z, a.slope z), a.slope in [0, 1).  Compile-time: a select per element
+// measured 5-40 % on the autoencoder's epilogue-bound layers.
+template <bool FOLD>
 __device__ __forceinline__ float act_fn(const ConvArgs &a, float z) {
-  return a.slope != 0.f ? fmaxf(z, a.slope * z) : fmaxf(z, 0.f);
+  if constexpr (FOLD)
+    return fmaxf(z, a.slope * z);
+  else
+    return fmaxf(z, 0.f);
 }
 
 // Zero v[e] where the mask tensor's value is not positive (16 channels at mb).
@@ -766,12 +778,12 @@ __device__ __forceinline__ void apply_mask(const uint8_t *mb, float (&v)[16]) {
   }
 }
 
-template <int PREC>
+template <int PREC, bool FOLD>
 __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int cc, int BN, int col0, bool vrow,
                                           bool has_skip, const uint4 (&sk)[4], uint8_t *yb, size_t eoff,
                                           uint32_t t2) {
   float v[16];
-  tmem_ld_acc<PREC>(taddr + cc * 16, acc_at(t2, cc * 16), v);
+  tmem_ld_acc<PREC, FOLD>(taddr + cc * 16, acc_at<FOLD>(FOLD ? t2 : taddr + (uint32_t)BN, cc * 16), v);
   const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
   const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
 #pragma unroll
@@ -782,7 +794,7 @@ __device__ __forceinline__ void epi_chunk(const ConvArgs &a, uint32_t taddr, int
     for (int e = 0; e < 4; ++e) {
       float z = bsc ? v[4 * e4 + e] * __ldg(bsc + 4 * e4 + e) : v[4 * e4 + e];
       z += bb[e];
-      if (a.relu) z = act_fn(a, z);
+      if (a.relu) z = act_fn<FOLD>(a, z);
       v[4 * e4 + e] = z;
     }
   }
@@ -899,7 +911,7 @@ __device__ __forceinline__ void st4(void *base, size_t e, float4 v, const float 
 // rows x Wrow columns, i.e. a box of the output with element strides 2 in H
 // and W starting at (2 i0 + oy, ox); the skip add reads each lane's own row
 // (prefetched one chunk ahead, as in the other epilogues).
-template <int PREC>
+template <int PREC, bool FOLD>
 __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, int BN, int n0, int row0,
                                              const PhaseDesc &pd, uint32_t ring, int &box, unsigned long long &w_tfull,
                                              uint32_t tfull, uint32_t par, unsigned long long &w_ld, uint32_t t2) {
@@ -937,7 +949,7 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
     const int col0 = n0 + cc * 16;
     float v[16];
     const long long tl0 = a.prof ? clock64() : 0;
-    tmem_ld_acc<PREC>(taddr + cc * 16, acc_at(t2, cc * 16), v);
+    tmem_ld_acc<PREC, FOLD>(taddr + cc * 16, acc_at<FOLD>(FOLD ? t2 : taddr + (uint32_t)BN, cc * 16), v);
     if (a.prof) w_ld += (unsigned long long)(clock64() - tl0);
     const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
 #pragma unroll
@@ -947,7 +959,7 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         float z = v[4 * e4 + e] + bb[e];
-        if (a.relu) z = act_fn(a, z);
+        if (a.relu) z = act_fn<FOLD>(a, z);
         v[4 * e4 + e] = z;
       }
     }
@@ -991,7 +1003,7 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
   return true;
 }
 
-template <int PREC>
+template <int PREC, bool FOLD>
 __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t taddr, int BN, int n0, size_t ebase,
                                                 bool vrow, float *stg, unsigned long long &w_tfull, uint32_t tfull,
                                                 uint32_t par, unsigned long long &w_ld, uint32_t t2) {
@@ -1023,7 +1035,7 @@ __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t tadd
     const int col0 = n0 + cc * 16;
     float v[16];
     const long long tl0 = a.prof ? clock64() : 0;
-    tmem_ld_acc<PREC>(taddr + cc * 16, acc_at(t2, cc * 16), v);
+    tmem_ld_acc<PREC, FOLD>(taddr + cc * 16, acc_at<FOLD>(FOLD ? t2 : taddr + (uint32_t)BN, cc * 16), v);
     if (a.prof) w_ld += (unsigned long long)(clock64() - tl0);
     const float *bsc = a.bscale ? a.bscale + col0 : nullptr;
     const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
@@ -1035,7 +1047,7 @@ __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t tadd
       for (int e = 0; e < 4; ++e) {
         float z = bsc ? v[4 * e4 + e] * __ldg(bsc + 4 * e4 + e) : v[4 * e4 + e];
         z += bb[e];
-        if (a.relu) z = act_fn(a, z);
+        if (a.relu) z = act_fn<FOLD>(a, z);
         v[4 * e4 + e] = z;
       }
     }
@@ -1143,9 +1155,10 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
   for (int t = blockIdx.x; ok && t < total_tiles; t += gridDim.x) {
     const TileCoord tc = tile_coord(a, t);
     const int nkb = a.ph[tc.phase].num_kb;
-    const int kf = a.kfold > 0 ? a.kfold : nkb;
-    for (int k0 = 0; ok && k0 < nkb; k0 += kf, ++it) {
-      const int k1 = k0 + kf < nkb ? k0 + kf : nkb;
+    // FOLD: one accumulator unit per a.kfold K blocks; else the whole tile
+    int k0 = 0;
+    do {
+      const int k1 = FOLD ? (k0 + a.kfold < nkb ? k0 + a.kfold : nkb) : nkb;
       const int buf = nbufs == 2 ? (it & 1) : 0;
       const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
       if (!pwait(a, w_tempty, smem_u32(&tempty_bar[buf]), par ^ 1)) {
@@ -1218,17 +1231,21 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
       }
       if (!ok) break;
       tc_commit(smem_u32(&tfull_bar[buf]));
-    }
+      ++it;
+      k0 = k1;
+    } while (FOLD && k0 < nkb);
   }
 }
 
 // YTMA: the FP32 encoder form whose epilogue stores tiles by TMA (a.y_tma),
 // compiled apart so that the other layers carry none of its code.
-template <int PREC, bool YTMA>
+// FOLD: the U-Net form -- accumulation chunks and LeakyReLU (TF32X3 with A
+// in tensor memory only), compiled apart like YTMA.
+template <int PREC, bool YTMA, bool FOLD>
 __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_constant__ ConvArgs a) {
   using T = PrecTraits<PREC>;
   const int BN = a.BN;
-  const bool fold = PREC == PREC_TF32X3 && a.prod_mode == PROD_TMA_TMEM && a.kfold > 0;
+  constexpr bool fold = FOLD;
   const SmemPlan plan = smem_plan(PREC, BN, a.prod_mode, YTMA ? 1 : 0, fold ? 1 : 0);
   const int stages = plan.stages;
   const int a_bytes = BM * KROW_BYTES;
@@ -1326,7 +1343,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
         constexpr bool kTAP = PREC == PREC_BF16;  // BF16 tap boxes land in the A tile itself
         const bool tapa = kTAP && a.tap_boxes && a.prod_mode == PROD_TMA_DIRECT;
         if (a.prof) {
-          if (kTS && ts && fold)
+          if constexpr (FOLD)
             DRC_MMA_ISSUE(kTS, true, false, kTS);
           else if (kTS && ts)
             DRC_MMA_ISSUE(kTS, true, false, false);
@@ -1335,7 +1352,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
           else
             DRC_MMA_ISSUE(false, true, false, false);
         } else {
-          if (kTS && ts && fold)
+          if constexpr (FOLD)
             DRC_MMA_ISSUE(kTS, false, false, kTS);
           else if (kTS && ts)
             DRC_MMA_ISSUE(kTS, false, false, false);
@@ -1413,9 +1430,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       const PhaseDesc &pd = a.ph[tc.phase];
       // every chunk but the last: added into the running sum (round to
       // nearest), then the chunk buffer goes back to the MMA warp
-      const int nkb = pd.num_kb;
-      const int kf = fold ? a.kfold : nkb;
-      const int nchunk = (nkb + kf - 1) / kf;
+      int nchunk = 1;
+      if constexpr (FOLD) {
+      nchunk = (pd.num_kb + a.kfold - 1) / a.kfold;
       for (int q = 0; q + 1 < nchunk; ++q, ++it) {
         const int fbuf = nbufs == 2 ? (it & 1) : 0;
         const uint32_t fpar = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
@@ -1441,6 +1458,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
         __syncwarp();
         if (lane == 0) mbar_arrive(smem_u32(&tempty_bar[fbuf]));
       }
+      }
       if (failed) break;
       const int buf = nbufs == 2 ? (it & 1) : 0;
       const uint32_t par = (uint32_t)((nbufs == 2 ? (it >> 1) : it) & 1);
@@ -1458,7 +1476,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
                               : (size_t)m;
       const size_t ebase = opix * a.Cout + (size_t)tc.n_tile * BN;
       if (YTMA && plan.epi_stage) {
-        if (!epi_tile_tma<PREC>(a, taddr, BN, tc.n_tile * BN, tc.m_tile * BM + eq * 32, pd,
+        if (!epi_tile_tma<PREC, FOLD>(a, taddr, BN, tc.n_tile * BN, tc.m_tile * BM + eq * 32, pd,
                                 smem_u32(epi_stg) + (uint32_t)(eq * EPI_TMA_BOXES * EPI_TMA_BOX_BYTES), tma_box,
                                 w_tfull, smem_u32(&tfull_bar[buf]), par, w_ld, t2))
           break;
@@ -1468,7 +1486,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
         continue;
       }
       if (plan.epi_stage) {
-        if (!epi_tile_staged<PREC>(a, taddr, BN, tc.n_tile * BN, opix * a.Cout, vrow, epi_stg + eq * 32 * 20, w_tfull,
+        if (!epi_tile_staged<PREC, FOLD>(a, taddr, BN, tc.n_tile * BN, opix * a.Cout, vrow, epi_stg + eq * 32 * 20, w_tfull,
                                    smem_u32(&tfull_bar[buf]), par, w_ld, t2))
           break;
         tc_fence_before();
@@ -1491,7 +1509,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
         for (int cc = 0; cc < nch; ++cc) {
           uint4 sk[4];
           if (has_skip) load_skip<PREC>(skip + ebase + cc * 16, sk);
-          epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk, yb + cc * 16 * out_elem,
+          epi_chunk<PREC, FOLD>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk, yb + cc * 16 * out_elem,
                           ebase + cc * 16, t2);
         }
       } else {
@@ -1503,11 +1521,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
         if (!pwait(a, w_tfull, smem_u32(&tfull_bar[buf]), par)) break;
         tc_fence_after();
         for (int cc = 0; cc < nch; cc += 2) {
-          epi_chunk<PREC>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk0, yb + cc * 16 * out_elem,
+          epi_chunk<PREC, FOLD>(a, taddr, cc, BN, tc.n_tile * BN + cc * 16, vrow, has_skip, sk0, yb + cc * 16 * out_elem,
                           ebase + cc * 16, t2);
           if (has_skip && cc + 2 < nch) load_skip<PREC>(skip + ebase + (cc + 2) * 16, sk0);
           if (cc + 1 < nch) {
-            epi_chunk<PREC>(a, taddr, cc + 1, BN, tc.n_tile * BN + (cc + 1) * 16, vrow, has_skip, sk1,
+            epi_chunk<PREC, FOLD>(a, taddr, cc + 1, BN, tc.n_tile * BN + (cc + 1) * 16, vrow, has_skip, sk1,
                             yb + (cc + 1) * 16 * out_elem, ebase + (cc + 1) * 16, t2);
             if (has_skip && cc + 3 < nch) load_skip<PREC>(skip + ebase + (cc + 3) * 16, sk1);
           }
@@ -1534,50 +1552,37 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
   }
 }
 
+template <int PREC, bool YTMA, bool FOLD>
+static cudaError_t launch_form(const ConvArgs &a, int grid, size_t smem, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<PREC, YTMA, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  conv_tc_kernel<PREC, YTMA, FOLD><<<grid, NUM_THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t st) {
   const int total = a.num_phases * a.m_tiles * a.n_tiles;
   if (total == 0) return cudaSuccess;
   const int grid = total < num_sms ? total : num_sms;
-  if (a.kfold < 0 ||
-      (a.kfold > 0 && (prec != PREC_TF32X3 || a.prod_mode != PROD_TMA_TMEM || a.BN > KFOLD_MAX_BN)))
+  // the U-Net form: accumulation chunks, LeakyReLU (its slope only there)
+  const bool fold = a.kfold > 0;
+  if (a.kfold < 0 || (fold && (prec != PREC_TF32X3 || a.prod_mode != PROD_TMA_TMEM || a.BN > KFOLD_MAX_BN)) ||
+      (!fold && a.slope != 0.f))
     return cudaErrorInvalidValue;
-  const size_t smem = conv_smem_bytes(prec, a.BN, a.prod_mode, a.y_tma, a.kfold > 0 ? 1 : 0);
-  cudaError_t e;
+  const size_t smem = conv_smem_bytes(prec, a.BN, a.prod_mode, a.y_tma, fold ? 1 : 0);
   switch (prec) {
     case PREC_TF32X3:
-      if (a.y_tma) {
-        e = cudaFuncSetAttribute(conv_tc_kernel<PREC_TF32X3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        conv_tc_kernel<PREC_TF32X3, true><<<grid, NUM_THREADS, smem, st>>>(a);
-      } else {
-        e = cudaFuncSetAttribute(conv_tc_kernel<PREC_TF32X3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        conv_tc_kernel<PREC_TF32X3, false><<<grid, NUM_THREADS, smem, st>>>(a);
-      }
-      break;
+      if (fold) return a.y_tma ? launch_form<PREC_TF32X3, true, true>(a, grid, smem, st)
+                               : launch_form<PREC_TF32X3, false, true>(a, grid, smem, st);
+      return a.y_tma ? launch_form<PREC_TF32X3, true, false>(a, grid, smem, st)
+                     : launch_form<PREC_TF32X3, false, false>(a, grid, smem, st);
     case PREC_BF16:
-      if (a.y_tma) {
-        e = cudaFuncSetAttribute(conv_tc_kernel<PREC_BF16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        conv_tc_kernel<PREC_BF16, true><<<grid, NUM_THREADS, smem, st>>>(a);
-      } else {
-        e = cudaFuncSetAttribute(conv_tc_kernel<PREC_BF16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
-        if (e != cudaSuccess) return e;
-        conv_tc_kernel<PREC_BF16, false><<<grid, NUM_THREADS, smem, st>>>(a);
-      }
-      break;
+      return a.y_tma ? launch_form<PREC_BF16, true, false>(a, grid, smem, st)
+                     : launch_form<PREC_BF16, false, false>(a, grid, smem, st);
     default:
-      e = cudaFuncSetAttribute(conv_tc_kernel<PREC_FP8, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-      if (e != cudaSuccess) return e;
-      conv_tc_kernel<PREC_FP8, false><<<grid, NUM_THREADS, smem, st>>>(a);
-      break;
+      return launch_form<PREC_FP8, false, false>(a, grid, smem, st);
   }
-  return cudaGetLastError();
 }
 
 // ------------------------------------------------------ first-layer input
