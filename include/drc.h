@@ -474,6 +474,67 @@ const char *drc_last_error(drc_ctx *ctx);
  * the paper. */
 drc_status drc_autotune(drc_ctx *ctx, int N, int H, int W);
 
+/* drc_autotune with a persistent cache: `path` is a text file of JSON lines,
+ * one per tuned case, keyed by the GPU (name, SM count, compute capability),
+ * the network (channels, widths, out_relu, exposure), the precision and the
+ * batch shape N x H x W.  If the file holds an entry for this case (the last
+ * valid one wins), its tile widths and A paths are applied without timing
+ * and *from_cache (nullable) is set to 1; otherwise drc_autotune runs and
+ * its choice is appended as a new line (a missing file is created).  An
+ * entry whose choices do not fit this context's layers is ignored.  Lines
+ * are appended with one write each, so processes sharing the file may add
+ * duplicate entries but do not interleave them.  Synchronises the device.
+ * INVALID_ARG for a bad shape, an empty path or a file that cannot be
+ * written.  No counterpart in the paper. */
+drc_status drc_autotune_cached(drc_ctx *ctx, int N, int H, int W,
+                               const char *path, int *from_cache);
+
+/* Checkpoints (Sec. 4: the trained network is saved and loaded again by the
+ * renderer): the context's current fp32 weights and, optionally, the Adam
+ * state of a training run, in one file -- a line of JSON header (format,
+ * version, the network: in/out channels, widths, out_relu, exposure; the
+ * float count, whether Adam state follows, its step count, the payload size
+ * and its 64-bit FNV-1a checksum) followed by the little-endian fp32 arrays:
+ * weights [n], then adam_m [n] and adam_v [n] when present (n =
+ * drc_weight_count).
+ *   save: adam_m / adam_v are device pointers of n floats, both given or
+ *         both NULL; adam_step >= 0 is stored with them.  Reads the weights
+ *         and state on `stream` and synchronises it; writes a temporary file
+ *         renamed over `path`.
+ *   load: checks the header against the context's network (precision may
+ *         differ: the weights are the fp32 masters) and the checksum, makes
+ *         the weights current as drc_set_weights from host memory does,
+ *         and, when adam_m / adam_v are given, uploads the state into them
+ *         and stores the step in *adam_step (nullable).  Asking for Adam
+ *         state from a file without it is INVALID_ARG.
+ * INVALID_ARG for a file that cannot be read or written, is not a
+ * checkpoint, belongs to another network or is damaged; UNSUPPORTED for a
+ * newer format version. */
+drc_status drc_save_checkpoint(drc_ctx *ctx, const char *path,
+                               const float *adam_m, const float *adam_v,
+                               int adam_step, void *stream);
+drc_status drc_load_checkpoint(drc_ctx *ctx, const char *path, float *adam_m,
+                               float *adam_v, int *adam_step, void *stream);
+
+/* Copy the context's current fp32 weights (drc_weight_count floats, the
+ * layout drc_create takes) into `out`: device memory (asynchronous on
+ * `stream`) when out_on_device, else host memory (synchronises `stream`).
+ * INVALID_ARG before any weights were set. */
+drc_status drc_get_weights(drc_ctx *ctx, float *out, int out_on_device,
+                           void *stream);
+
+/* Cap the device memory the context allocates from now on -- its packed
+ * weights, workspaces, interpolation and training scratch, plans and
+ * staging buffers -- at `bytes` in total (0: no cap, the default).  A call
+ * that would need more returns DRC_ERR_OOM before allocating, with the
+ * sizes in drc_last_error, and leaves the context usable (raising the cap
+ * lets the same call succeed).  Memory the caller passes in (inputs,
+ * outputs, drc_unet_forward's workspace) is not counted.  A cap below the
+ * current use only refuses later growth.  No counterpart in the paper. */
+drc_status drc_set_memory_limit(drc_ctx *ctx, size_t bytes);
+/* Bytes of device memory the context holds now. */
+size_t drc_memory_in_use(const drc_ctx *ctx);
+
 /* FP8 e4m3 contexts: measure the network's activations on a representative
  * batch (in, N, H, W, flags as drc_denoise) and set every layer's
  * per-input-channel scales to the channel's maximum / 448 with one binade of

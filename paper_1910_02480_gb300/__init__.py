@@ -190,6 +190,18 @@ def load_library():
     lib.drc_autotune.restype = I
     lib.drc_describe_layer.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]
     lib.drc_describe_layer.restype = I
+    lib.drc_autotune_cached.argtypes = [P, I, I, I, ctypes.c_char_p, ctypes.POINTER(I)]
+    lib.drc_autotune_cached.restype = I
+    lib.drc_save_checkpoint.argtypes = [P, ctypes.c_char_p, P, P, I, P]
+    lib.drc_save_checkpoint.restype = I
+    lib.drc_load_checkpoint.argtypes = [P, ctypes.c_char_p, P, P, ctypes.POINTER(I), P]
+    lib.drc_load_checkpoint.restype = I
+    lib.drc_set_memory_limit.argtypes = [P, ctypes.c_size_t]
+    lib.drc_set_memory_limit.restype = I
+    lib.drc_memory_in_use.argtypes = [P]
+    lib.drc_memory_in_use.restype = ctypes.c_size_t
+    lib.drc_get_weights.argtypes = [P, P, I, P]
+    lib.drc_get_weights.restype = I
     lib.drc_plan_destroy.argtypes = [P]
     lib.drc_plan_destroy.restype = I
     _lib = lib
@@ -502,10 +514,52 @@ class Context:
         N, C, H, W = x.shape
         self._check(self._lib.drc_calibrate(self._ctx, _ptr(x), N, H, W, flags, _stream(stream)), "drc_calibrate")
 
-    def autotune(self, N, H, W):
+    def autotune(self, N, H, W, cache=None):
         """Time each conv layer's tile candidates for N maps of H x W and keep
-        the fastest for later denoise calls (synchronises)."""
-        self._check(self._lib.drc_autotune(self._ctx, int(N), int(H), int(W)), "drc_autotune")
+        the fastest for later denoise calls (synchronises).  cache: path of
+        a JSON-lines tile cache (drc_autotune_cached) -- a hit applies the
+        stored choice without timing.  Returns True on a cache hit."""
+        if cache is None:
+            self._check(self._lib.drc_autotune(self._ctx, int(N), int(H), int(W)), "drc_autotune")
+            return False
+        hit = ctypes.c_int(0)
+        self._check(self._lib.drc_autotune_cached(self._ctx, int(N), int(H), int(W), os.fsencode(cache),
+                                                  ctypes.byref(hit)), "drc_autotune_cached")
+        return bool(hit.value)
+
+    def save_checkpoint(self, path, adam_m=None, adam_v=None, adam_step=0, stream=None):
+        """drc_save_checkpoint: the current weights (and the Adam state, cuda
+        float32 tensors of n_weights, when given) to one file."""
+        self._check(self._lib.drc_save_checkpoint(self._ctx, os.fsencode(path), _ptr(adam_m) if adam_m is not None
+                                                  else None, _ptr(adam_v) if adam_v is not None else None,
+                                                  int(adam_step), _stream(stream)), "drc_save_checkpoint")
+
+    def load_checkpoint(self, path, adam_m=None, adam_v=None, stream=None):
+        """drc_load_checkpoint: make the file's weights current (and fill the
+        Adam state tensors when given); returns the stored Adam step."""
+        step = ctypes.c_int(0)
+        self._check(self._lib.drc_load_checkpoint(self._ctx, os.fsencode(path), _ptr(adam_m) if adam_m is not None
+                                                  else None, _ptr(adam_v) if adam_v is not None else None,
+                                                  ctypes.byref(step), _stream(stream)), "drc_load_checkpoint")
+        return step.value
+
+    def get_weights(self, out=None, stream=None):
+        """drc_get_weights: the current fp32 weights, into `out` (a cuda
+        float32 tensor of n_weights) or as a new numpy array."""
+        if out is not None:
+            self._check(self._lib.drc_get_weights(self._ctx, _ptr(out), 1, _stream(stream)), "drc_get_weights")
+            return out
+        w = np.empty(self.n_weights, dtype=np.float32)
+        self._check(self._lib.drc_get_weights(self._ctx, w.ctypes.data, 0, _stream(stream)), "drc_get_weights")
+        return w
+
+    def set_memory_limit(self, nbytes):
+        """drc_set_memory_limit: cap the device memory this context allocates
+        (0: no cap)."""
+        self._check(self._lib.drc_set_memory_limit(self._ctx, int(nbytes)), "drc_set_memory_limit")
+
+    def memory_in_use(self):
+        return int(self._lib.drc_memory_in_use(self._ctx))
 
     def describe_layer(self, layer):
         bn, path = ctypes.c_int(0), ctypes.c_int(0)
@@ -639,6 +693,15 @@ class Trainer:
                            stream=stream)
         self.ctx.set_weights(self.w, stream=stream)
         return loss
+
+    def save(self, path, stream=None):
+        """Checkpoint of the run: the weights and the Adam state and step."""
+        self.ctx.save_checkpoint(path, self.m, self.v, self.t, stream=stream)
+
+    def load(self, path, stream=None):
+        """Resume from save(): weights, Adam state and step."""
+        self.t = self.ctx.load_checkpoint(path, self.m, self.v, stream=stream)
+        self.ctx.get_weights(out=self.w, stream=stream)
 
 
 def unet_param_count(base=64, levels=3, in_ch=7, out_ch=3):

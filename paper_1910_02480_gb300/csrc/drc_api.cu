@@ -3,6 +3,7 @@
 // autoencoder (Sec. 3.3) and of the interpolation (Sec. 3.2).
 #include <cuda_runtime.h>
 
+#include <cerrno>
 #include <cmath>
 #include <cstdarg>
 #include <cstdlib>
@@ -11,6 +12,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "backward.cuh"
@@ -21,6 +23,7 @@
 #include "drc_status.cuh"
 #include "indirect.cuh"
 #include "mapgen.cuh"
+#include "persist.cuh"
 #include "interp.cuh"
 #include "trace.cuh"
 #include "train.cuh"
@@ -98,6 +101,11 @@ struct drc_ctx {
   size_t fmaps_n = 0, fgbuf_p = 0;
   cudaStream_t fcopy = nullptr;
   cudaEvent_t fev_maps = nullptr, fev_gbuf = nullptr, fev_maps_free = nullptr, fev_gbuf_free = nullptr;
+  // device memory the context owns (ctx_malloc / ctx_free), under an
+  // optional limit (drc_set_memory_limit; 0 = none)
+  std::unordered_map<void *, size_t> allocs;
+  size_t mem_used = 0, mem_limit = 0;
+  size_t refused = 0;  // bytes of the last request the limit refused (0: the last failure was CUDA's)
 };
 
 namespace {
@@ -117,8 +125,49 @@ drc_status fail(drc_ctx *c, drc_status s, const char *fmt, ...) {
 
 drc_status cuda_fail(drc_ctx *c, cudaError_t e, const char *what) {
   cudaGetLastError();
+  if (e == cudaErrorMemoryAllocation && c && c->refused) {
+    const size_t r = c->refused;
+    c->refused = 0;
+    return fail(c, DRC_ERR_OOM, "%s: %zu bytes requested with %zu in use exceed the context's memory limit of %zu bytes",
+                what, r, c->mem_used, c->mem_limit);
+  }
   if (e == cudaErrorMemoryAllocation) return fail(c, DRC_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
   return fail(c, DRC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Device memory owned by the context: counted, and refused (as
+// cudaErrorMemoryAllocation, before cudaMalloc is called) where it would take
+// the context past its limit.
+cudaError_t ctx_malloc_raw(drc_ctx *c, void **p, size_t bytes) {
+  *p = nullptr;
+  if (c->mem_limit && c->mem_used + bytes > c->mem_limit) {
+    c->refused = bytes;
+    return cudaErrorMemoryAllocation;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  c->allocs[*p] = bytes;
+  c->mem_used += bytes;
+  return cudaSuccess;
+}
+template <class T>
+cudaError_t ctx_malloc(drc_ctx *c, T **p, size_t bytes) {
+  void *v = nullptr;
+  const cudaError_t e = ctx_malloc_raw(c, &v, bytes);
+  *p = static_cast<T *>(v);
+  return e;
+}
+void ctx_free(drc_ctx *c, void *p) {
+  if (!p) return;
+  auto it = c->allocs.find(p);
+  if (it != c->allocs.end()) {
+    c->mem_used -= it->second;
+    c->allocs.erase(it);
+  }
+  cudaFree(p);
 }
 
 // cuTensorMapEncodeTiled, looked up once through the runtime (no link
@@ -503,10 +552,10 @@ size_t act_bytes_for(const drc_ctx *c, long long N, int H, int W) {
 drc_status ensure_act(drc_ctx *c, long long N, int H, int W) {
   const size_t need = act_bytes_for(c, N, H, W);
   if (need <= c->act_bytes) return DRC_OK;
-  if (c->d_act) cudaFree(c->d_act);
+  if (c->d_act) ctx_free(c, c->d_act);
   c->d_act = nullptr;
   c->act_bytes = 0;
-  cudaError_t e = cudaMalloc(&c->d_act, need);
+  cudaError_t e = ctx_malloc(c, &c->d_act, need);
   if (e != cudaSuccess) return cuda_fail(c, e, "activation workspace");
   c->act_bytes = need;
   return DRC_OK;
@@ -792,8 +841,8 @@ void plan_dgrad_layers(drc_ctx *c) {
 drc_status ensure_dgrad_pack(drc_ctx *c, cudaStream_t st) {
   if (c->dlayers.empty()) {
     plan_dgrad_layers(c);
-    cudaError_t e = cudaMalloc(&c->d_dpack, c->dpack_total);
-    if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&c->d_dpack_lo, c->dpack_total);
+    cudaError_t e = ctx_malloc(c, &c->d_dpack, c->dpack_total);
+    if (e == cudaSuccess && c->prec == PREC_TF32X3) e = ctx_malloc(c, &c->d_dpack_lo, c->dpack_total);
     if (e != cudaSuccess) {
       c->dlayers.clear();
       return cuda_fail(c, e, "data-gradient operands");
@@ -1033,10 +1082,10 @@ namespace {
 void plan_free(drc_plan *p) {
   if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->graph) cudaGraphDestroy(p->graph);
-  for (uint8_t *b : p->pack) cudaFree(b);
-  for (uint8_t *b : p->pack_lo) cudaFree(b);
-  cudaFree(p->d_act);
-  cudaFree(p->d_slots);
+  for (uint8_t *b : p->pack) ctx_free(p->ctx, b);
+  for (uint8_t *b : p->pack_lo) ctx_free(p->ctx, b);
+  ctx_free(p->ctx, p->d_act);
+  ctx_free(p->ctx, p->d_slots);
   cudaGetLastError();
   delete p;
 }
@@ -1116,8 +1165,8 @@ drc_status autotune_layers(drc_ctx *c, std::vector<Layer> &Ls, std::vector<int> 
   }
   uint8_t *B = nullptr, *B_lo = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  cudaError_t e = cudaMalloc(&B, scratch);
-  if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&B_lo, scratch);
+  cudaError_t e = ctx_malloc(c, &B, scratch);
+  if (e == cudaSuccess && c->prec == PREC_TF32X3) e = ctx_malloc(c, &B_lo, scratch);
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   drc_status s = e == cudaSuccess ? DRC_OK : cuda_fail(c, e, "autotune scratch");
@@ -1148,8 +1197,8 @@ drc_status autotune_layers(drc_ctx *c, std::vector<Layer> &Ls, std::vector<int> 
     modes[li] = best_mode;
   }
   cudaStreamSynchronize(st);
-  cudaFree(B);
-  cudaFree(B_lo);
+  ctx_free(c, B);
+  ctx_free(c, B_lo);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaGetLastError();
@@ -1193,21 +1242,21 @@ drc_status drc_create(const drc_config *cfg, const float *weights_host, size_t n
   }
   plan_layers(c);
   c->modes.assign(c->layers.size(), -1);
-  e = cudaMalloc(&c->d_wraw, c->n_floats * sizeof(float));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_pack, c->pack_total);
-  if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&c->d_pack_lo, c->pack_total);
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_status, sizeof(int));
+  e = ctx_malloc(c, &c->d_wraw, c->n_floats * sizeof(float));
+  if (e == cudaSuccess) e = ctx_malloc(c, &c->d_pack, c->pack_total);
+  if (e == cudaSuccess && c->prec == PREC_TF32X3) e = ctx_malloc(c, &c->d_pack_lo, c->pack_total);
+  if (e == cudaSuccess) e = ctx_malloc(c, &c->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_zero, 1024 * sizeof(float));
+  if (e == cudaSuccess) e = ctx_malloc(c, &c->d_zero, 1024 * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(c->d_zero, 0, 1024 * sizeof(float));
   if (e == cudaSuccess && c->prec == PREC_FP8) {
     // activation scales start at 1 (values up to the e4m3 maximum, 448)
     // until drc_calibrate measures the network's activations
     c->h_inscale.assign(c->n_scales, 1.0f);
-    e = cudaMalloc(&c->d_inscale, c->n_scales * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_qinv, c->n_scales * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_bscale, c->n_bscales * sizeof(float));
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_amax, c->n_bscales * sizeof(unsigned));
+    e = ctx_malloc(c, &c->d_inscale, c->n_scales * sizeof(float));
+    if (e == cudaSuccess) e = ctx_malloc(c, &c->d_qinv, c->n_scales * sizeof(float));
+    if (e == cudaSuccess) e = ctx_malloc(c, &c->d_bscale, c->n_bscales * sizeof(float));
+    if (e == cudaSuccess) e = ctx_malloc(c, &c->d_amax, c->n_bscales * sizeof(unsigned));
     if (e == cudaSuccess)
       e = cudaMemcpy(c->d_inscale, c->h_inscale.data(), c->n_scales * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -1274,28 +1323,28 @@ drc_status drc_set_weights(drc_ctx *c, const float *weights, int weights_on_devi
 
 drc_status drc_destroy(drc_ctx *c) {
   if (!c) return DRC_ERR_INVALID_ARG;
-  cudaFree(c->d_wraw);
-  cudaFree(c->d_pack);
-  cudaFree(c->d_pack_lo);
-  cudaFree(c->d_bscale);
-  cudaFree(c->d_inscale);
-  cudaFree(c->d_dpack);
-  cudaFree(c->d_dpack_lo);
-  cudaFree(c->d_train);
-  cudaFree(c->d_zero);
-  cudaFree(c->d_qinv);
-  cudaFree(c->d_amax);
-  cudaFree(c->d_act);
-  cudaFree(c->d_iscratch);
-  cudaFree(c->d_indscratch);
-  cudaFree(c->d_status);
-  cudaFree(c->d_prof);
-  cudaFree(c->d_fmaps);
-  cudaFree(c->d_fout);
-  cudaFree(c->d_fpay);
-  cudaFree(c->d_fgpos);
-  cudaFree(c->d_fgnrm);
-  cudaFree(c->d_frgb);
+  ctx_free(c, c->d_wraw);
+  ctx_free(c, c->d_pack);
+  ctx_free(c, c->d_pack_lo);
+  ctx_free(c, c->d_bscale);
+  ctx_free(c, c->d_inscale);
+  ctx_free(c, c->d_dpack);
+  ctx_free(c, c->d_dpack_lo);
+  ctx_free(c, c->d_train);
+  ctx_free(c, c->d_zero);
+  ctx_free(c, c->d_qinv);
+  ctx_free(c, c->d_amax);
+  ctx_free(c, c->d_act);
+  ctx_free(c, c->d_iscratch);
+  ctx_free(c, c->d_indscratch);
+  ctx_free(c, c->d_status);
+  ctx_free(c, c->d_prof);
+  ctx_free(c, c->d_fmaps);
+  ctx_free(c, c->d_fout);
+  ctx_free(c, c->d_fpay);
+  ctx_free(c, c->d_fgpos);
+  ctx_free(c, c->d_fgnrm);
+  ctx_free(c, c->d_frgb);
   for (cudaEvent_t e : {c->fev_maps, c->fev_gbuf, c->fev_maps_free, c->fev_gbuf_free})
     if (e) cudaEventDestroy(e);
   if (c->fcopy) cudaStreamDestroy(c->fcopy);
@@ -1338,7 +1387,10 @@ drc_status drc_denoise(drc_ctx *c, const float *in, float *out, float *payload, 
   const bool prof = std::getenv("DRC_PROFILE_WAITS") != nullptr;
   if (prof) {
     const size_t pb = c->layers.size() * PROF_SLOTS * sizeof(unsigned long long);
-    if (!c->d_prof && cudaMalloc(&c->d_prof, pb) != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "prof");
+    if (!c->d_prof) {
+      const cudaError_t pe = ctx_malloc(c, &c->d_prof, pb);
+      if (pe != cudaSuccess) return cuda_fail(c, pe, "wait-time counters");
+    }
     cudaMemsetAsync(c->d_prof, 0, pb, st);
   }
   if ((s = refresh_head_weights(c, st)) != DRC_OK) return s;
@@ -1414,10 +1466,10 @@ drc_status drc_interpolate(drc_ctx *c, const drc_caches *caches, const drc_gbuff
   const size_t grid_bytes = (interp_scratch_bytes(caches->n, prm->k) + 255) & ~(size_t)255;
   const size_t need = grid_bytes + (order ? interp_order_bytes(P, caches->n) : 0);
   if (need > c->iscratch_bytes) {
-    if (c->d_iscratch) cudaFree(c->d_iscratch);
+    if (c->d_iscratch) ctx_free(c, c->d_iscratch);
     c->d_iscratch = nullptr;
     c->iscratch_bytes = 0;
-    cudaError_t e = cudaMalloc(&c->d_iscratch, need);
+    cudaError_t e = ctx_malloc(c, &c->d_iscratch, need);
     if (e != cudaSuccess) return cuda_fail(c, e, "interpolation scratch");
     c->iscratch_bytes = need;
   }
@@ -1488,10 +1540,10 @@ drc_status drc_indirect(drc_ctx *c, const drc_caches *caches, const drc_gbuffer 
   a.W = caches->W;
   const size_t need = indirect_scratch_bytes(a.n, a.H, a.W);
   if (need > c->indscratch_bytes) {
-    if (c->d_indscratch) cudaFree(c->d_indscratch);
+    if (c->d_indscratch) ctx_free(c, c->d_indscratch);
     c->d_indscratch = nullptr;
     c->indscratch_bytes = 0;
-    cudaError_t e = cudaMalloc(&c->d_indscratch, need);
+    cudaError_t e = ctx_malloc(c, &c->d_indscratch, need);
     if (e != cudaSuccess) return cuda_fail(c, e, "indirect scratch");
     c->indscratch_bytes = need;
   }
@@ -1638,10 +1690,10 @@ drc_status drc_backward(drc_ctx *c, const float *in, const float *target, int N,
   const size_t need = train_layout(c, N, H, W, recompute, nullptr, nullptr);
   cudaError_t e;
   if (need > c->train_bytes) {
-    cudaFree(c->d_train);
+    ctx_free(c, c->d_train);
     c->d_train = nullptr;
     c->train_bytes = 0;
-    if ((e = cudaMalloc(&c->d_train, need)) != cudaSuccess) return cuda_fail(c, e, "training workspace");
+    if ((e = ctx_malloc(c, &c->d_train, need)) != cudaSuccess) return cuda_fail(c, e, "training workspace");
     c->train_bytes = need;
   }
   TrainBufs b;
@@ -1861,7 +1913,7 @@ drc_status unet_forward_tc(drc_ctx *c, const UnetShape &u, const float *params, 
     const bool fold = pd.num_kb > kFoldAbove;
     kfold.push_back(fold ? kFoldKb : 0);
     set_bn(L, fold && L.Cout > KFOLD_MAX_BN ? KFOLD_MAX_BN : pick_bn(L.Cout));
-    snprintf(L.name, sizeof L.name, "unet conv %zu", i);
+    snprintf(L.name, sizeof L.name, "unet conv %d", (int)i);
     Ls.push_back(L);
   }
   layout_packs(Ls);
@@ -2023,26 +2075,26 @@ drc_status drc_frame_host(drc_ctx *c, const float *maps_host, int N, int H, int 
   // staging, copy stream and events (first use / growth)
   const size_t map_floats = (size_t)7 * H * W;
   if ((size_t)N * map_floats > c->fmaps_n) {
-    cudaFree(c->d_fmaps);
-    cudaFree(c->d_fout);
-    cudaFree(c->d_fpay);
+    ctx_free(c, c->d_fmaps);
+    ctx_free(c, c->d_fout);
+    ctx_free(c, c->d_fpay);
     c->d_fmaps = c->d_fout = c->d_fpay = nullptr;
     c->fmaps_n = 0;
-    if ((e = cudaMalloc(&c->d_fmaps, (size_t)N * map_floats * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_fout, (size_t)N * 3 * H * W * 4)) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_fpay, (size_t)N * 3 * 4)) != cudaSuccess)
+    if ((e = ctx_malloc(c, &c->d_fmaps, (size_t)N * map_floats * 4)) != cudaSuccess ||
+        (e = ctx_malloc(c, &c->d_fout, (size_t)N * 3 * H * W * 4)) != cudaSuccess ||
+        (e = ctx_malloc(c, &c->d_fpay, (size_t)N * 3 * 4)) != cudaSuccess)
       return cuda_fail(c, e, "frame staging");
     c->fmaps_n = (size_t)N * map_floats;
   }
   if ((size_t)P > c->fgbuf_p) {
-    cudaFree(c->d_fgpos);
-    cudaFree(c->d_fgnrm);
-    cudaFree(c->d_frgb);
+    ctx_free(c, c->d_fgpos);
+    ctx_free(c, c->d_fgnrm);
+    ctx_free(c, c->d_frgb);
     c->d_fgpos = c->d_fgnrm = c->d_frgb = nullptr;
     c->fgbuf_p = 0;
-    if ((e = cudaMalloc(&c->d_fgpos, (size_t)P * 12)) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_fgnrm, (size_t)P * 12)) != cudaSuccess ||
-        (e = cudaMalloc(&c->d_frgb, (size_t)P * 12)) != cudaSuccess)
+    if ((e = ctx_malloc(c, &c->d_fgpos, (size_t)P * 12)) != cudaSuccess ||
+        (e = ctx_malloc(c, &c->d_fgnrm, (size_t)P * 12)) != cudaSuccess ||
+        (e = ctx_malloc(c, &c->d_frgb, (size_t)P * 12)) != cudaSuccess)
       return cuda_fail(c, e, "frame staging");
     c->fgbuf_p = (size_t)P;
   }
@@ -2116,6 +2168,71 @@ drc_status drc_get_status(drc_ctx *c, void *stream) {
 
 const char *drc_last_error(drc_ctx *c) { return c ? c->err.c_str() : "NULL context"; }
 
+drc_status drc_set_memory_limit(drc_ctx *c, size_t bytes) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  c->mem_limit = bytes;
+  return DRC_OK;
+}
+
+size_t drc_memory_in_use(const drc_ctx *c) { return c ? c->mem_used : 0; }
+
+drc_status drc_get_weights(drc_ctx *c, float *out, int out_on_device, void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!out) return fail(c, DRC_ERR_INVALID_ARG, "out is NULL");
+  if (!c->weights_set) return fail(c, DRC_ERR_INVALID_ARG, "weights were never set");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if (out_on_device) {
+    if (!is_device_ptr(out, c->device))
+      return fail(c, DRC_ERR_INVALID_ARG, "out_on_device set but out is not device memory");
+    e = cudaMemcpyAsync(out, c->d_wraw, c->n_floats * sizeof(float), cudaMemcpyDeviceToDevice, st);
+  } else {
+    e = cudaMemcpyAsync(out, c->d_wraw, c->n_floats * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  return e == cudaSuccess ? DRC_OK : cuda_fail(c, e, "weight read-back");
+}
+
+
+
+namespace {
+
+// Make per-layer tile widths and A paths current: lay the packed operands
+// out again (a larger buffer where the new widths pad more) and repack.
+drc_status apply_tiles(drc_ctx *c, std::vector<Layer> &Ls, const std::vector<int> &modes, cudaStream_t st) {
+  drc_status s = DRC_OK;
+  cudaError_t e;
+  {
+    const size_t need = layout_packs(Ls);
+    if (need > c->pack_total) {  // a narrower tile can pad the packed image differently
+      uint8_t *B = nullptr, *B_lo = nullptr;
+      e = ctx_malloc(c, &B, need);
+      if (e == cudaSuccess && c->prec == PREC_TF32X3) e = ctx_malloc(c, &B_lo, need);
+      if (e != cudaSuccess) {
+        ctx_free(c, B);
+        s = cuda_fail(c, e, "autotune operands");
+      } else {
+        cudaStreamSynchronize(st);
+        ctx_free(c, c->d_pack);
+        ctx_free(c, c->d_pack_lo);
+        c->d_pack = B;
+        c->d_pack_lo = B_lo;
+        c->pack_total = need;
+      }
+    }
+  }
+  if (s == DRC_OK) {
+    c->layers = Ls;
+    c->modes = modes;
+    s = pack_all(c, st);
+  }
+  return s;
+}
+
+}  // namespace
+
 drc_status drc_autotune(drc_ctx *c, int N, int H, int W) {
   if (!c) return DRC_ERR_INVALID_ARG;
   c->err.clear();
@@ -2134,30 +2251,7 @@ drc_status drc_autotune(drc_ctx *c, int N, int H, int W) {
   std::vector<Layer> Ls = c->layers;
   std::vector<int> modes = c->modes;
   s = autotune_layers(c, Ls, modes, ch, st);
-  if (s == DRC_OK) {
-    const size_t need = layout_packs(Ls);
-    if (need > c->pack_total) {  // a narrower tile can pad the packed image differently
-      uint8_t *B = nullptr, *B_lo = nullptr;
-      e = cudaMalloc(&B, need);
-      if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&B_lo, need);
-      if (e != cudaSuccess) {
-        cudaFree(B);
-        s = cuda_fail(c, e, "autotune operands");
-      } else {
-        cudaStreamSynchronize(st);
-        cudaFree(c->d_pack);
-        cudaFree(c->d_pack_lo);
-        c->d_pack = B;
-        c->d_pack_lo = B_lo;
-        c->pack_total = need;
-      }
-    }
-  }
-  if (s == DRC_OK) {
-    c->layers = Ls;
-    c->modes = modes;
-    s = pack_all(c, st);
-  }
+  if (s == DRC_OK) s = apply_tiles(c, Ls, modes, st);
   if (s == DRC_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) s = cuda_fail(c, e, "autotune");
   cudaStreamDestroy(st);
   return s;
@@ -2178,7 +2272,7 @@ drc_status drc_calibrate(drc_ctx *c, const float *in, int N, int H, int W, unsig
   if ((s = check_dev(c, in, "in", false)) != DRC_OK) return s;
   if ((s = ensure_act(c, N, H, W)) != DRC_OK) return s;
   float *out = nullptr;
-  cudaError_t e = cudaMalloc(&out, (size_t)N * 3 * H * W * sizeof(float));
+  cudaError_t e = ctx_malloc(c, &out, (size_t)N * 3 * H * W * sizeof(float));
   if (e != cudaSuccess) return cuda_fail(c, e, "calibration output");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Chain ch;
@@ -2225,7 +2319,7 @@ drc_status drc_calibrate(drc_ctx *c, const float *in, int N, int H, int W, unsig
     ++c->weights_version;
   }
   cudaStreamSynchronize(st);
-  cudaFree(out);
+  ctx_free(c, out);
   cudaGetLastError();
   return s;
 }
@@ -2267,9 +2361,9 @@ drc_status drc_plan_create(drc_ctx *c, const drc_size_class *classes, int n_clas
     act_off[k] = act_total;
     act_total += (act_bytes_for(c, classes[k].max_maps, classes[k].H, classes[k].W) + 255) & ~(size_t)255;
   }
-  cudaError_t e = cudaMalloc(&p->d_act, act_total);
+  cudaError_t e = ctx_malloc(c, &p->d_act, act_total);
   if (e == cudaSuccess) e = cudaMemset(p->d_act, 0, act_total);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_slots, n_classes * sizeof(PassSlot));
+  if (e == cudaSuccess) e = ctx_malloc(c, &p->d_slots, n_classes * sizeof(PassSlot));
   if (e == cudaSuccess) e = cudaMemset(p->d_slots, 0, n_classes * sizeof(PassSlot));
   if (e != cudaSuccess) {
     drc_status s = cuda_fail(c, e, "plan buffers");
@@ -2290,8 +2384,8 @@ drc_status drc_plan_create(drc_ctx *c, const drc_size_class *classes, int n_clas
     if (flags & DRC_PLAN_AUTOTUNE) s = autotune_layers(c, p->layers[k], p->modes[k], p->chains[k], cs);
     if (s != DRC_OK) break;
     const size_t bytes = layout_packs(p->layers[k]);
-    e = cudaMalloc(&p->pack[k], bytes);
-    if (e == cudaSuccess && c->prec == PREC_TF32X3) e = cudaMalloc(&p->pack_lo[k], bytes);
+    e = ctx_malloc(c, &p->pack[k], bytes);
+    if (e == cudaSuccess && c->prec == PREC_TF32X3) e = ctx_malloc(c, &p->pack_lo[k], bytes);
     if (e != cudaSuccess) s = cuda_fail(c, e, "plan operands");
   }
   if (s == DRC_OK) s = plan_pack(p, cs);
@@ -2401,3 +2495,206 @@ drc_status drc_read_timing(drc_ctx *c, drc_kernel_time *out, int capacity, int *
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- checkpoint
+namespace {
+
+const char *prec_name(int prec) { return prec == PREC_TF32X3 ? "fp32" : (prec == PREC_BF16 ? "bf16" : "fp8"); }
+
+// The architecture part of a header: what a checkpoint or a tile choice is
+// tied to (precision is not part of it: the weights are fp32 masters).
+std::string arch_json(const drc_config &g) {
+  std::string w;
+  for (int i = 0; i < g.num_stages; ++i) w += (i ? "," : "") + std::to_string(g.widths[i]);
+  char buf[256];
+  snprintf(buf, sizeof buf, "\"in_channels\": %d, \"out_channels\": %d, \"widths\": [%s], \"out_relu\": %d, "
+                            "\"exposure\": %.9g",
+           g.in_channels, g.out_channels, w.c_str(), g.out_relu ? 1 : 0, (double)g.exposure);
+  return buf;
+}
+
+// Whether header h describes the same network as g; *why says how it differs.
+bool arch_matches(const FlatJson &h, const drc_config &g, std::string *why) {
+  double ic = -1, oc = -1, orl = -1, ex = -1;
+  std::vector<double> w;
+  if (!h.num("in_channels", &ic) || !h.num("out_channels", &oc) || !h.num("out_relu", &orl) ||
+      !h.num("exposure", &ex) || !h.nums("widths", &w)) {
+    *why = "header lacks the network description";
+    return false;
+  }
+  bool same = (int)ic == g.in_channels && (int)oc == g.out_channels && (int)w.size() == g.num_stages &&
+              ((int)orl != 0) == (g.out_relu != 0) && (float)ex == g.exposure;
+  for (size_t i = 0; same && i < w.size(); ++i) same = (int)w[i] == g.widths[i];
+  if (!same) *why = "it was written for another network (channels, widths, out_relu or exposure differ)";
+  return same;
+}
+
+}  // namespace
+
+drc_status drc_save_checkpoint(drc_ctx *c, const char *path, const float *adam_m, const float *adam_v,
+                               int adam_step, void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!path || !*path) return fail(c, DRC_ERR_INVALID_ARG, "path is empty");
+  if (!c->weights_set) return fail(c, DRC_ERR_INVALID_ARG, "weights were never set");
+  if ((adam_m == nullptr) != (adam_v == nullptr))
+    return fail(c, DRC_ERR_INVALID_ARG, "adam_m and adam_v must both be given or both be NULL");
+  if (adam_step < 0) return fail(c, DRC_ERR_INVALID_ARG, "adam_step must be >= 0");
+  drc_status s;
+  if (adam_m && ((s = check_dev(c, adam_m, "adam_m", false)) != DRC_OK || (s = check_dev(c, adam_v, "adam_v", false)) != DRC_OK))
+    return s;
+  const size_t n = c->n_floats;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<float> w(n), m(adam_m ? n : 0), v(adam_v ? n : 0);
+  cudaError_t e = cudaMemcpyAsync(w.data(), c->d_wraw, n * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && adam_m) e = cudaMemcpyAsync(m.data(), adam_m, n * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && adam_v) e = cudaMemcpyAsync(v.data(), adam_v, n * 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "checkpoint read-back");
+  uint64_t h = fnv1a64(w.data(), n * 4);
+  if (adam_m) h = fnv1a64(v.data(), n * 4, fnv1a64(m.data(), n * 4, h));
+  char head[160];
+  snprintf(head, sizeof head, "\"n_floats\": %zu, \"adam\": %d, \"adam_step\": %d, \"payload_bytes\": %zu, "
+                              "\"fnv1a64\": \"%016llx\"}",
+           n, adam_m ? 1 : 0, adam_step, n * 4 * (adam_m ? 3 : 1), (unsigned long long)h);
+  const std::string header = "{\"format\": \"drc-checkpoint\", \"version\": 1, " + arch_json(c->cfg) + ", " + head;
+  std::vector<std::pair<const void *, size_t>> blobs{{w.data(), n * 4}};
+  if (adam_m) {
+    blobs.push_back({m.data(), n * 4});
+    blobs.push_back({v.data(), n * 4});
+  }
+  if (!write_file_atomic(path, header, blobs))
+    return fail(c, DRC_ERR_INVALID_ARG, "cannot write %s: %s", path, strerror(errno));
+  return DRC_OK;
+}
+
+drc_status drc_load_checkpoint(drc_ctx *c, const char *path, float *adam_m, float *adam_v, int *adam_step,
+                               void *stream) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (!path || !*path) return fail(c, DRC_ERR_INVALID_ARG, "path is empty");
+  if ((adam_m == nullptr) != (adam_v == nullptr))
+    return fail(c, DRC_ERR_INVALID_ARG, "adam_m and adam_v must both be given or both be NULL");
+  drc_status s;
+  if (adam_m && ((s = check_dev(c, adam_m, "adam_m", false)) != DRC_OK || (s = check_dev(c, adam_v, "adam_v", false)) != DRC_OK))
+    return s;
+  std::string data;
+  if (!read_file(path, &data)) return fail(c, DRC_ERR_INVALID_ARG, "cannot read %s: %s", path, strerror(errno));
+  const size_t nl = data.find('\n');
+  FlatJson h;
+  std::string fmt;
+  double ver = 0, nf = 0, has_adam = 0, step = 0, pbytes = 0;
+  std::string sum, why;
+  if (nl == std::string::npos || !parse_flat_json(data.substr(0, nl), &h) || !h.str("format", &fmt) ||
+      fmt != "drc-checkpoint" || !h.num("version", &ver) || !h.num("n_floats", &nf) || !h.num("adam", &has_adam) ||
+      !h.num("adam_step", &step) || !h.num("payload_bytes", &pbytes) || !h.str("fnv1a64", &sum))
+    return fail(c, DRC_ERR_INVALID_ARG, "%s is not a checkpoint of this library", path);
+  if ((int)ver != 1) return fail(c, DRC_ERR_UNSUPPORTED, "%s: checkpoint version %d", path, (int)ver);
+  if (!arch_matches(h, c->cfg, &why)) return fail(c, DRC_ERR_INVALID_ARG, "%s: %s", path, why.c_str());
+  const size_t n = c->n_floats;
+  const size_t want = n * 4 * (has_adam != 0 ? 3 : 1);
+  if ((size_t)nf != n || (size_t)pbytes != want || data.size() - nl - 1 != want)
+    return fail(c, DRC_ERR_INVALID_ARG, "%s: payload of %zu bytes, %zu expected", path, data.size() - nl - 1, want);
+  const char *pay = data.data() + nl + 1;
+  char hex[17];
+  snprintf(hex, sizeof hex, "%016llx", (unsigned long long)fnv1a64(pay, want));
+  if (sum != hex) return fail(c, DRC_ERR_INVALID_ARG, "%s: checksum mismatch (the file is damaged)", path);
+  if (adam_m && has_adam == 0) return fail(c, DRC_ERR_INVALID_ARG, "%s holds no optimizer state", path);
+  std::vector<float> w(n);
+  memcpy(w.data(), pay, n * 4);
+  if ((s = drc_set_weights(c, w.data(), 0, stream)) != DRC_OK) return s;
+  if (adam_m) {
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(adam_m, pay + n * 4, n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(adam_v, pay + 2 * n * 4, n * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host copy is freed on return
+    if (e != cudaSuccess) return cuda_fail(c, e, "optimizer state upload");
+  }
+  if (adam_step) *adam_step = (int)step;
+  return DRC_OK;
+}
+
+// ----------------------------------------------------------- autotune cache
+drc_status drc_autotune_cached(drc_ctx *c, int N, int H, int W, const char *path, int *from_cache) {
+  if (!c) return DRC_ERR_INVALID_ARG;
+  c->err.clear();
+  if (from_cache) *from_cache = 0;
+  if (!path || !*path) return fail(c, DRC_ERR_INVALID_ARG, "path is empty");
+  cudaDeviceProp prop;
+  cudaError_t e = cudaGetDeviceProperties(&prop, c->device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device properties");
+  const int cc = prop.major * 10 + prop.minor;
+  // the entries of this device, network, precision and batch shape
+  std::string data;
+  if (read_file(path, &data)) {
+    std::vector<Layer> best;
+    std::vector<int> best_modes;
+    size_t pos = 0;
+    while (pos < data.size()) {
+      size_t end = data.find('\n', pos);
+      if (end == std::string::npos) end = data.size();
+      const std::string line = data.substr(pos, end - pos);
+      pos = end + 1;
+      FlatJson j;
+      std::string fmt, dev, prec, why;
+      double sms = 0, jcc = 0;
+      std::vector<double> shape, tn, ap;
+      if (!parse_flat_json(line, &j) || !j.str("format", &fmt) || fmt != "drc-autotune" || !j.str("device", &dev) ||
+          !j.num("sms", &sms) || !j.num("cc", &jcc) || !j.str("precision", &prec) || !j.nums("shape", &shape) ||
+          !j.nums("tile_n", &tn) || !j.nums("a_path", &ap))
+        continue;  // not an entry (or damaged): skipped
+      if (dev != prop.name || (int)sms != c->num_sms || (int)jcc != cc || prec != prec_name(c->prec) ||
+          shape.size() != 3 || (int)shape[0] != N || (int)shape[1] != H || (int)shape[2] != W ||
+          !arch_matches(j, c->cfg, &why) || tn.size() != c->layers.size() || ap.size() != c->layers.size())
+        continue;
+      // the choices must be ones drc_autotune can make for these layers
+      std::vector<Layer> Ls = c->layers;
+      std::vector<int> modes(Ls.size(), -1);
+      bool ok = true;
+      for (size_t li = 0; ok && li < Ls.size(); ++li) {
+        if (Ls[li].kind == LK_HEAD) continue;
+        const int bn = (int)tn[li], mode = (int)ap[li];
+        bool bn_ok = false;
+        for (int cand : bn_candidates(Ls[li])) bn_ok = bn_ok || cand == bn;
+        const bool mode_ok = mode == -1 || (c->prec == PREC_TF32X3 && mode == PROD_TMA_CONVERT && bn <= 128) ||
+                             (c->prec == PREC_TF32X3 && mode == PROD_CPASYNC && Ls[li].kind == LK_CONV && Ls[li].Cin == 8);
+        ok = bn_ok && mode_ok;
+        if (ok) {
+          set_bn(Ls[li], bn);
+          modes[li] = mode;
+        }
+      }
+      if (ok) {  // the last valid entry wins
+        best = Ls;
+        best_modes = modes;
+      }
+    }
+    if (!best.empty()) {
+      drc_status s = ensure_act(c, N, H, W);
+      if (s != DRC_OK) return s;
+      if (!c->weights_set) return fail(c, DRC_ERR_INVALID_ARG, "weights were never set");
+      cudaStream_t st = nullptr;
+      if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(c, e, "autotune stream");
+      s = apply_tiles(c, best, best_modes, st);
+      if (s == DRC_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) s = cuda_fail(c, e, "autotune cache");
+      cudaStreamDestroy(st);
+      if (s == DRC_OK && from_cache) *from_cache = 1;
+      return s;
+    }
+  }
+  drc_status s = drc_autotune(c, N, H, W);
+  if (s != DRC_OK) return s;
+  std::string tn, ap;
+  for (size_t li = 0; li < c->layers.size(); ++li) {
+    tn += (li ? "," : "") + std::to_string(c->layers[li].kind == LK_HEAD ? 0 : c->layers[li].BN);
+    ap += (li ? "," : "") + std::to_string(c->modes[li]);
+  }
+  char buf[256];
+  snprintf(buf, sizeof buf, "\"sms\": %d, \"cc\": %d, \"precision\": \"%s\", \"shape\": [%d,%d,%d], ", c->num_sms, cc,
+           prec_name(c->prec), N, H, W);
+  const std::string line = "{\"format\": \"drc-autotune\", \"version\": 1, \"device\": " + json_quote(prop.name) +
+                           ", " + buf + arch_json(c->cfg) + ", \"tile_n\": [" + tn + "], \"a_path\": [" + ap + "]}";
+  if (!append_line(path, line)) return fail(c, DRC_ERR_INVALID_ARG, "cannot append to %s: %s", path, strerror(errno));
+  return DRC_OK;
+}
