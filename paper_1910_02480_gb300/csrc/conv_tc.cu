@@ -66,6 +66,7 @@ __host__ __device__ inline int stage_bytes(int prec, int BN, int mode) {
 // sum R [0, BN) and two chunk buffers [BN, 3 BN); above 256 columns of
 // those (BN 128) the A stages shrink to two, from column 384.
 constexpr int TS_STAGES = 4;
+constexpr int RAW_MAX = 6;  // raw TMA slots at most (the control block's barrier arrays); 8 measured no faster
 constexpr int TS_A_COL0 = 256;
 __host__ __device__ inline int ts_a_col0(int BN, int fold) { return fold && 3 * BN > TS_A_COL0 ? 384 : TS_A_COL0; }
 __host__ __device__ inline int ts_stages(int BN, int fold) { return (512 - ts_a_col0(BN, fold)) / 64; }
@@ -102,11 +103,11 @@ static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, 
   const int rb = BM * raw_row_bytes(prec);
   if (mode == PROD_TMA_TMEM) {
     // B stages match the tensor-memory A stages; the rest of shared memory
-    // holds raw TMA boxes in flight (up to 6)
+    // holds raw TMA boxes in flight (up to RAW_MAX)
     SmemPlan p;
     p.stages = ts_stages(BN, fold);
     int R = (avail - p.stages * sb) / rb;
-    p.raw_depth = R > 6 ? 6 : R;
+    p.raw_depth = R > RAW_MAX ? RAW_MAX : R;
     p.raw_slot_bytes = rb;
     return p;
   }
@@ -1262,9 +1263,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
   uint64_t *tfull_bar = empty_bar + 8;                       // [2]
   uint64_t *tempty_bar = tfull_bar + 2;                      // [2]
   uint64_t *stall_bar = tempty_bar + 2;                      // [1]
-  uint64_t *raw_full = stall_bar + 1;                        // [6]
-  uint64_t *raw_empty = raw_full + 6;                        // [6]
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(raw_empty + 6);
+  uint64_t *raw_full = stall_bar + 1;                        // [RAW_MAX]
+  uint64_t *raw_empty = raw_full + RAW_MAX;                  // [RAW_MAX]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(raw_empty + RAW_MAX);
+  static_assert((8 + 8 + 2 + 2 + 1 + 2 * RAW_MAX) * 8 + 4 <= SMEM_CTRL, "control block");
   const uint32_t base_u32 = smem_u32(smem_raw);
   const uint32_t data_u32 = (base_u32 + SMEM_CTRL + 1023u) & ~1023u;
   uint8_t *data = smem_raw + (data_u32 - base_u32);
