@@ -435,12 +435,12 @@ __device__ __forceinline__ void tma_issue(const ConvArgs &a, const TmaCursor &c,
   using T = PrecTraits<PREC>;
   constexpr int BKE = KROW_BYTES / T::ELEM;
   if (a.tap_boxes) {
-    // taps of 8 channels (FP32: 32 bytes, four per K block; BF16: 16 bytes,
-    // eight per K block) of the stride-2 or stride-1 conv, one box each,
-    // tap-major; a slot past the last tap loads tap 0 again, against B rows
-    // packed as zero
-    constexpr int TB = 8 * T::ELEM;           // bytes of one tap row
-    constexpr int TPB = KROW_BYTES / TB;      // taps per K block
+    // taps narrower than a K block -- 8 channels (FP32: 32 bytes, four per K
+    // block; BF16: 16 bytes, eight), or 64 e4m3 channels (64 bytes, two) --
+    // of the stride-2 or stride-1 conv, one box each, tap-major; a slot past
+    // the last tap loads tap 0 again, against B rows packed as zero
+    constexpr int TB = PREC == PREC_FP8 ? 64 : 8 * T::ELEM;  // bytes of one tap row (Cin 64 / 8)
+    constexpr int TPB = KROW_BYTES / TB;                      // taps per K block
     const int ry = a.kind == LK_CONV ? 2 * c.r0 : c.r0;
 #pragma unroll
     for (int t = 0; t < TPB; ++t) {
@@ -912,7 +912,9 @@ __device__ __forceinline__ void st4(void *base, size_t e, float4 v, const float 
 // rows x Wrow columns, i.e. a box of the output with element strides 2 in H
 // and W starting at (2 i0 + oy, ox); the skip add reads each lane's own row
 // (prefetched one chunk ahead, as in the other epilogues).
-template <int PREC, bool FOLD>
+// E4: the tile is stored as e4m3 with a.out_qinv (FP8 contexts' encoder
+// outputs), compiled apart.
+template <int PREC, bool FOLD, bool E4>
 __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, int BN, int n0, int row0,
                                              const PhaseDesc &pd, uint32_t ring, int &box, unsigned long long &w_tfull,
                                              uint32_t tfull, uint32_t par, unsigned long long &w_ld, uint32_t t2) {
@@ -953,6 +955,10 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
     tmem_ld_acc<PREC, FOLD>(taddr + cc * 16, acc_at<FOLD>(FOLD ? t2 : taddr + (uint32_t)BN, cc * 16), v);
     if (a.prof) w_ld += (unsigned long long)(clock64() - tl0);
     const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
+    if constexpr (PREC == PREC_FP8) {  // dequantise with the output columns' weight scales
+#pragma unroll
+      for (int e = 0; e < 16; ++e) v[e] *= __ldg(a.bscale + col0 + e);
+    }
 #pragma unroll
     for (int e4 = 0; e4 < 4; ++e4) {
       const float4 b = __ldg(bias4 + e4);
@@ -978,7 +984,16 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
     box = box + 1 == EPI_TMA_BOXES ? 0 : box + 1;
     if (lane == 0) bulk_wait_read<EPI_TMA_BOXES - 1>();
     __syncwarp();
-    if constexpr (PREC == PREC_BF16) {
+    if constexpr (E4) {
+      // e4m3 with the consuming layer's inverse input scales: 16-byte rows,
+      // no swizzle (a quarter warp's eight rows are 128 contiguous bytes)
+      const float *qi = a.out_qinv + col0;
+      float q[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) q[e] = v[e] * __ldg(qi + e);
+      sts128u(stg + (uint32_t)(lane * 16), pack_e4m3x4(q[0], q[1], q[2], q[3]), pack_e4m3x4(q[4], q[5], q[6], q[7]),
+              pack_e4m3x4(q[8], q[9], q[10], q[11]), pack_e4m3x4(q[12], q[13], q[14], q[15]));
+    } else if constexpr (PREC == PREC_BF16) {
       // 32-byte rows, 32-byte swizzle: 16-byte chunk h at h ^ ((r / 4) % 2)
 #pragma unroll
       for (int h = 0; h < 2; ++h)
@@ -1142,11 +1157,16 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
   };
   bool ok = true;
   const uint32_t idesc = make_idesc(T::KIND, BM, BN);
-  // TAPA (BF16 tap boxes): A is K-major without swizzle, 2 KB per 8-element
+  // TAPA, BF16 tap boxes: A is K-major without swizzle, 2 KB per 8-element
   // K group (one tap box), 128 bytes per 8-row group; a 16-element K step
-  // spans two groups (4096 bytes = 256 units)
-  const uint64_t dA0 = TAPA ? make_sdesc_kmajor_plain(data_u32, BM * 16, 128) : make_sdesc_sw128(data_u32);
+  // spans two groups (4096 bytes = 256 units).  TAPA, FP8 tap boxes of 64
+  // channels: two 64-byte-swizzled boxes of 8 KB (512 units) per K block, two
+  // 32-element K steps in each (+2 units).
+  constexpr bool TAP8 = TAPA && PREC == PREC_FP8;
+  const uint64_t dA0 = TAP8 ? make_sdesc_sw64(data_u32)
+                            : (TAPA ? make_sdesc_kmajor_plain(data_u32, BM * 16, 128) : make_sdesc_sw128(data_u32));
   constexpr uint32_t kA = TAPA ? 256u : 2u;
+  auto a_step = [&](int k) -> uint32_t { return TAP8 ? (uint32_t)((k >> 1) * 512 + (k & 1) * 2) : kA * (uint32_t)k; };
   const uint32_t dstage = (uint32_t)sbytes >> 4, dAlo = (uint32_t)a_bytes >> 4;
   const uint64_t dB0 = make_sdesc_sw128(data_u32 + (uint32_t)(TS ? 0 : T::SPLIT * a_bytes));
   const uint32_t dBlo = (uint32_t)b_bytes >> 4;
@@ -1219,7 +1239,7 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
           }
 #pragma unroll
           for (int k = 1; k < KROW_BYTES / 32; ++k) {
-            tc_mma<T::KIND>(d_tmem, sd + kA * k, bd0 + 2 * k, idesc, 1u);
+            tc_mma<T::KIND>(d_tmem, sd + a_step(k), bd0 + 2 * k, idesc, 1u);
             if constexpr (PREC == PREC_TF32X3) {
               tc_mma<T::KIND>(c_tmem, sd + kA * k, bd1 + 2 * k, idesc, 1u);
               tc_mma<T::KIND>(c_tmem, ad1 + kA * k, bd0 + 2 * k, idesc, 1u);
@@ -1242,7 +1262,7 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
 // compiled apart so that the other layers carry none of its code.
 // FOLD: the U-Net form -- accumulation chunks and LeakyReLU (TF32X3 with A
 // in tensor memory only), compiled apart like YTMA.
-template <int PREC, bool YTMA, bool FOLD>
+template <int PREC, bool YTMA, bool FOLD, bool E4>
 __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_constant__ ConvArgs a) {
   using T = PrecTraits<PREC>;
   const int BN = a.BN;
@@ -1342,7 +1362,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
                                            acc_cols, acc_base, a_col0, tmem_base, full_bar, empty_bar, tfull_bar,  \
                                            tempty_bar, w_full, w_tempty)
         constexpr bool kTS = PREC == PREC_TF32X3;
-        constexpr bool kTAP = PREC == PREC_BF16;  // BF16 tap boxes land in the A tile itself
+        constexpr bool kTAP = PREC == PREC_BF16 || PREC == PREC_FP8;  // tap boxes land in the A tile itself
         const bool tapa = kTAP && a.tap_boxes && a.prod_mode == PROD_TMA_DIRECT;
         if (a.prof) {
           if constexpr (FOLD)
@@ -1478,7 +1498,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
                               : (size_t)m;
       const size_t ebase = opix * a.Cout + (size_t)tc.n_tile * BN;
       if (YTMA && plan.epi_stage) {
-        if (!epi_tile_tma<PREC, FOLD>(a, taddr, BN, tc.n_tile * BN, tc.m_tile * BM + eq * 32, pd,
+        if (!epi_tile_tma<PREC, FOLD, E4>(a, taddr, BN, tc.n_tile * BN, tc.m_tile * BM + eq * 32, pd,
                                 smem_u32(epi_stg) + (uint32_t)(eq * EPI_TMA_BOXES * EPI_TMA_BOX_BYTES), tma_box,
                                 w_tfull, smem_u32(&tfull_bar[buf]), par, w_ld, t2))
           break;
@@ -1554,12 +1574,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
   }
 }
 
-template <int PREC, bool YTMA, bool FOLD>
+template <int PREC, bool YTMA, bool FOLD, bool E4 = false>
 static cudaError_t launch_form(const ConvArgs &a, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<PREC, YTMA, FOLD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<PREC, YTMA, FOLD, E4>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  conv_tc_kernel<PREC, YTMA, FOLD><<<grid, NUM_THREADS, smem, st>>>(a);
+  conv_tc_kernel<PREC, YTMA, FOLD, E4><<<grid, NUM_THREADS, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1580,10 +1600,12 @@ cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t s
       return a.y_tma ? launch_form<PREC_TF32X3, true, false>(a, grid, smem, st)
                      : launch_form<PREC_TF32X3, false, false>(a, grid, smem, st);
     case PREC_BF16:
+      if (a.y_tma && a.out_qinv) return launch_form<PREC_BF16, true, false, true>(a, grid, smem, st);
       return a.y_tma ? launch_form<PREC_BF16, true, false>(a, grid, smem, st)
                      : launch_form<PREC_BF16, false, false>(a, grid, smem, st);
-    default:
-      return launch_form<PREC_FP8, false, false>(a, grid, smem, st);
+    default:  // FP8 TMA stores are always e4m3
+      return a.y_tma ? launch_form<PREC_FP8, true, false, true>(a, grid, smem, st)
+                     : launch_form<PREC_FP8, false, false>(a, grid, smem, st);
   }
 }
 

@@ -201,13 +201,21 @@ EncodeTiledFn encode_tiled() {
 // the output as a 2-D tensor [M][Cout] with 16-column x 32-row boxes.
 void plan_store(int prec, ConvArgs &a) {
   a.y_tma = 0;
-  if ((prec != PREC_TF32X3 && prec != PREC_BF16) || a.y2 || a.mask || a.amax || a.out_qinv || a.bscale ||
-      a.BN % 16 || a.Cout % 8)
+  if (a.y2 || a.mask || a.amax || a.BN % 16 || a.Cout % 8) return;
+  // e4m3 outputs (FP8 contexts: quantised for the consuming layer) of the
+  // encoder convs, from the BF16 first layer or an FP8 layer: 16-byte rows,
+  // no swizzle
+  const bool e4m3 = a.out_qinv != nullptr;
+  if (e4m3 ? (prec == PREC_TF32X3 || a.kind != LK_CONV || (prec == PREC_FP8) != (a.bscale != nullptr))
+           : (prec == PREC_FP8 || a.bscale))
     return;
   // fp32: 64-byte box rows, 64-byte swizzle; bf16: 32-byte rows, 32-byte swizzle
-  const int eb = prec == PREC_TF32X3 ? 4 : 2;
-  const CUtensorMapDataType dt = prec == PREC_TF32X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const CUtensorMapSwizzle sw = prec == PREC_TF32X3 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
+  const int eb = e4m3 ? 1 : (prec == PREC_TF32X3 ? 4 : 2);
+  const CUtensorMapDataType dt = e4m3 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                      : (prec == PREC_TF32X3 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                                             : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16);
+  const CUtensorMapSwizzle sw = e4m3 ? CU_TENSOR_MAP_SWIZZLE_NONE
+                                     : (prec == PREC_TF32X3 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
   if (a.kind != LK_CONVT && a.skip) return;
   // BF16 decoder phases keep the per-row epilogue (its skip prefetch two
   // chunks ahead measured faster there: d2 0.21 against 0.24 ms)
@@ -250,9 +258,12 @@ void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
   const int Wr = a.Wrow, Hr = a.Hrow;
   // conv over 8 stored channels (the first layer): 32 bytes per tap in FP32
   // (four taps per K block) or 16 in BF16 (eight), each tap its own TMA box;
-  // BF16 boxes land in the A tile directly (no-swizzle K-major layout)
-  const bool taps = (a.kind == LK_CONV || a.kind == LK_CONV1) && a.Cin == 8 && !a.x2 &&
-                    (prec == PREC_TF32X3 || prec == PREC_BF16);
+  // BF16 boxes land in the A tile directly (no-swizzle K-major layout).  FP8
+  // conv over 64 channels: 64-byte taps, two per K block, 64-byte swizzle,
+  // straight into the A tile.
+  const bool conv = (a.kind == LK_CONV || a.kind == LK_CONV1) && !a.x2;
+  const bool taps8 = conv && prec == PREC_FP8 && a.Cin == 64;  // the kernel's FP8 tap width
+  const bool taps = (conv && a.Cin == 8 && (prec == PREC_TF32X3 || prec == PREC_BF16)) || taps8;
   if (Wr > BM || BM % Wr || (!taps && a.Cin % bke)) return;
   // a concatenated second input: every K block inside one of the two tensors
   const int C1 = a.x2 ? a.C1 : a.Cin;
@@ -276,7 +287,8 @@ void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
                                 : (prec == PREC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8);
   CUresult r = enc(&a.tmap, dt,
                    4, const_cast<void *>(a.x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   taps ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   taps8 ? CU_TENSOR_MAP_SWIZZLE_64B : (taps ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B),
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return;
   if (a.x2) {

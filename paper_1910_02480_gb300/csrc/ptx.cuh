@@ -227,6 +227,18 @@ __device__ __forceinline__ uint64_t make_sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
+// The same for rows of 64 bytes stored with the 64-byte swizzle: 8-row atoms
+// of 512 bytes (stride byte offset), atoms 512-byte aligned.
+__device__ __forceinline__ uint64_t make_sdesc_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+  d |= (uint64_t)1 << 16;                    // leading byte offset (unused here), 16 B
+  d |= (uint64_t)(512 >> 4) << 32;           // stride byte offset: 8 rows x 64 B
+  d |= (uint64_t)1 << 46;                    // descriptor version (fixed 0b001)
+  d |= (uint64_t)4 << 61;                    // swizzle mode: 64-byte
+  return d;
+}
+
 // Shared-memory matrix descriptor for a K-major operand without swizzle:
 // core matrices of 8 rows x 16 bytes, LBO = distance between core matrices
 // along K, SBO = distance between 8-row groups along M/N.
