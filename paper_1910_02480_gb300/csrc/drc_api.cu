@@ -1113,15 +1113,53 @@ drc_status plan_capture(drc_plan *p, cudaStream_t cs) {
   p->exec = nullptr;
   p->graph = nullptr;
   p->kernels_per_launch = 0;
-  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
-  if (e != cudaSuccess) return cuda_fail(c, e, "begin capture");
+  // The size classes are independent chains: each class after the first is
+  // captured on a stream of its own, forked from and joined back into the
+  // capture stream, so that the graph runs them concurrently and one class's
+  // layers fill the SMs the other's tail leaves idle.
+  const size_t ncls = p->cls.size();
+  std::vector<cudaStream_t> side(ncls > 1 ? ncls - 1 : 0, nullptr);
+  std::vector<cudaEvent_t> done(side.size(), nullptr);
+  cudaEvent_t fork = nullptr;
+  cudaError_t e = cudaSuccess;
+  for (size_t k = 0; e == cudaSuccess && k < side.size(); ++k) {
+    e = cudaStreamCreateWithFlags(&side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&done[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess && !side.empty()) e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  auto release = [&]() {
+    for (cudaStream_t x : side)
+      if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t x : done)
+      if (x) cudaEventDestroy(x);
+    if (fork) cudaEventDestroy(fork);
+  };
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(c, e, "plan streams");
+  }
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(c, e, "begin capture");
+  }
   drc_status cap = DRC_OK;
-  for (size_t k = 0; cap == DRC_OK && k < p->cls.size(); ++k) {
+  if (fork) {
+    cudaEventRecord(fork, cs);
+    for (cudaStream_t x : side) cudaStreamWaitEvent(x, fork, 0);
+  }
+  for (size_t k = 0; cap == DRC_OK && k < ncls; ++k) {
+    cudaStream_t sk = k == 0 ? cs : side[k - 1];
     cap = run_chain(c, p->layers[k], p->pack[k], p->pack_lo[k], &p->modes[k], p->chains[k], nullptr, nullptr,
-                    nullptr, 0, cs, nullptr, nullptr);
+                    nullptr, 0, sk, nullptr, nullptr);
     p->kernels_per_launch += 1 + (int)p->layers[k].size();
   }
+  for (size_t k = 0; k < side.size(); ++k) {  // join (also after a failure: capture must end on one stream)
+    cudaEventRecord(done[k], side[k]);
+    cudaStreamWaitEvent(cs, done[k], 0);
+  }
   e = cudaStreamEndCapture(cs, &p->graph);
+  release();
   if (cap != DRC_OK) return cap;
   if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
   if ((e = cudaGraphInstantiate(&p->exec, p->graph, 0)) != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
