@@ -946,6 +946,13 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
     }
   };
   if (skp) load_sk(0);
+  // the fused 1x1 head (U-Net form): this lane's pixel's outputs, from the bias
+  const bool head = FOLD && a.head_w != nullptr;
+  float hacc[KHEAD_MAX];
+  if constexpr (FOLD) {
+#pragma unroll
+    for (int o = 0; o < KHEAD_MAX; ++o) hacc[o] = head && o < a.head_cout ? __ldg(a.head_w + a.head_cout * a.Cout + o) : 0.f;
+  }
   if (!pwait(a, w_tfull, tfull, par)) return false;
   tc_fence_after();
   for (int cc = 0; cc < BN / 16; ++cc) {
@@ -979,6 +986,18 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
         v[4 * e4 + 3] += sk[e4].w;
       }
       if (cc + 1 < BN / 16) load_sk(cc + 1);
+    }
+    if constexpr (FOLD) {
+      if (head) {  // this chunk's 16 channels into the head's dot products; y is not stored
+#pragma unroll
+        for (int o = 0; o < KHEAD_MAX; ++o) {
+          if (o >= a.head_cout) break;
+          const float *wo = a.head_w + (size_t)o * a.Cout + col0;
+#pragma unroll
+          for (int e = 0; e < 16; ++e) hacc[o] = fmaf(__ldg(wo + e), v[e], hacc[o]);
+        }
+        continue;
+      }
     }
     const uint32_t stg = ring + (uint32_t)(box * EPI_TMA_BOX_BYTES);
     box = box + 1 == EPI_TMA_BOXES ? 0 : box + 1;
@@ -1014,6 +1033,13 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
       else
         tma_store_2d(&a.ymap, stg, col0, row0);
       bulk_commit();
+    }
+  }
+  if constexpr (FOLD) {
+    if (head && vrow) {
+#pragma unroll
+      for (int o = 0; o < KHEAD_MAX; ++o)
+        if (o < a.head_cout) a.head_out[((size_t)n * a.head_cout + o) * rows_per_map + rem] = fmaxf(hacc[o], 0.f);
     }
   }
   return true;
@@ -1590,7 +1616,9 @@ cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t s
   // the U-Net form: accumulation chunks, LeakyReLU (its slope only there)
   const bool fold = a.kfold > 0;
   if (a.kfold < 0 || (fold && (prec != PREC_TF32X3 || a.prod_mode != PROD_TMA_TMEM || a.BN > KFOLD_MAX_BN)) ||
-      (!fold && a.slope != 0.f))
+      (!fold && a.slope != 0.f) ||
+      (a.head_w && (!fold || !a.y_tma || a.kind == LK_CONVT || a.n_tiles != 1 || a.head_cout < 1 ||
+                    a.head_cout > KHEAD_MAX || !a.head_out)))
     return cudaErrorInvalidValue;
   const size_t smem = conv_smem_bytes(prec, a.BN, a.prod_mode, a.y_tma, fold ? 1 : 0);
   switch (prec) {

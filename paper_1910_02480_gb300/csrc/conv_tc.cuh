@@ -98,6 +98,13 @@ struct ConvArgs {
   // number of MMAs into one accumulator; deep K (thousands of terms) needs
   // this to stay at fp32 accuracy.
   int kfold;
+  // U-Net form with the whole output row in one tile (n_tiles 1) and TMA
+  // stores: the network's 1x1 head fused into the epilogue -- out[n][o][pixel]
+  // = ReLU(head_w[o] . y + head_b[o]) for o < head_cout (<= KHEAD_MAX), head_w
+  // [head_cout][Cout] then head_b; y itself is not stored (nullptr: off)
+  const float *head_w;
+  float *head_out;  // [N][head_cout][Hout * Wout]
+  int head_cout;
   int *status;
   unsigned long long timeout_ns;
   int debug_stall;
@@ -128,6 +135,7 @@ constexpr int EPI_TMA_BYTES = 4 * EPI_TMA_BOXES * EPI_TMA_BOX_BYTES;
 // Accumulation chunks (ConvArgs::kfold): the running sum and two chunk
 // accumulators in tensor memory next to the A stages.
 constexpr int KFOLD_MAX_BN = 128;
+constexpr int KHEAD_MAX = 4;  // head outputs the fused epilogue keeps in registers
 __host__ __device__ SmemPlan smem_plan(int prec, int BN, int mode, int ytma, int fold = 0);
 size_t conv_smem_bytes(int prec, int BN, int mode, int ytma, int fold = 0);
 

@@ -1991,7 +1991,9 @@ drc_status unet_forward_tc(drc_ctx *c, const UnetShape &u, const float *params, 
   if ((e = launch_unet_stage_nhwc(in, N, u.cin, (long long)H * W, cs, b.in, st, tr)) != cudaSuccess)
     return cuda_fail(c, e, "unet input staging");
   size_t li = 0;
-  // one 3x3 layer: x (and x2 after its C1 channels) at h x w -> y
+  bool head_fused = false;
+  // one 3x3 layer: x (and x2 after its C1 channels) at h x w -> y; the last
+  // one takes the 1x1 head into its epilogue where its tile holds whole rows
   auto conv = [&](const float *x, const float *x2, int C1, int h, int w, float *y) -> drc_status {
     const Layer &L = Ls[li];
     ConvArgs a;
@@ -2014,6 +2016,12 @@ drc_status unet_forward_tc(drc_ctx *c, const UnetShape &u, const float *params, 
     plan_operand(PREC_TF32X3, a);
     if (a.prod_mode != PROD_TMA_TMEM)
       return fail(c, DRC_ERR_CUDA, "unet layer %zu: no tensor map for the A operand", li);
+    if (li + 1 == Ls.size() && a.y_tma && a.n_tiles == 1 && u.cout <= KHEAD_MAX) {
+      a.head_w = b.fold + T.back().dst;  // [cout][base], then the bias
+      a.head_out = out;
+      a.head_cout = u.cout;
+      head_fused = true;
+    }
     cudaError_t le;
     DRC_TRACED(tr, L.name, st, le = launch_conv(a, PREC_TF32X3, c->num_sms, st));
     if (le != cudaSuccess) return cuda_fail(c, le, "unet layer launch");
@@ -2044,8 +2052,8 @@ drc_status unet_forward_tc(drc_ctx *c, const UnetShape &u, const float *params, 
     d = b.dec[l];
   }
   const UnetLayer &hd = T.back();
-  if ((e = launch_unet_head_nhwc(d, N, (long long)H * W, u.base, b.fold + hd.dst, u.cout, out, st, tr)) !=
-      cudaSuccess)
+  if (!head_fused &&
+      (e = launch_unet_head_nhwc(d, N, (long long)H * W, u.base, b.fold + hd.dst, u.cout, out, st, tr)) != cudaSuccess)
     return cuda_fail(c, e, "unet head");
   return DRC_OK;
 }
