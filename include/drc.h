@@ -469,7 +469,12 @@ const char *drc_last_error(drc_ctx *ctx);
  * layer's tile width (GEMM N per tile: its output channels, or half of them)
  * and, for FP32, its A-operand path are timed on the context's own workspace
  * and the fastest kept for every later drc_denoise (results stay within the
- * precision's tolerance).
+ * precision's tolerance).  FP32 decoder layers of at most 64 output channels
+ * also time their phase-pair form: the four output parities of the stride-2
+ * transposed conv as two GEMMs, each holding the parities (p, 0) and (p, 1)
+ * of one output row side by side in a 2 Cout-column tile over the union of
+ * their input taps (a tap one of the two parities lacks has zero weights
+ * there).
  * Synchronises the device; grows the workspace to N maps.  No counterpart in
  * the paper. */
 drc_status drc_autotune(drc_ctx *ctx, int N, int H, int W);
@@ -546,8 +551,10 @@ size_t drc_memory_in_use(const drc_ctx *ctx);
 drc_status drc_calibrate(drc_ctx *ctx, const float *in, int N, int H, int W,
                          unsigned flags, void *stream);
 
-/* The tile width (0 for the head) and A-operand path (-1 default, 1 TMA +
- * producer conversion) drc_denoise uses for one layer (0 .. 2S-1). */
+/* The tile width (0 for the head) and A-operand path (-1 default, 0
+ * per-thread gathers, 1 TMA + producer conversion, 8 phase pairs -- see
+ * drc_autotune; the tile width is then the unpaired fallback's) drc_denoise
+ * uses for one layer (0 .. 2S-1). */
 drc_status drc_describe_layer(drc_ctx *ctx, int layer, int *bn, int *a_path);
 
 /* ---- Plans: progressive passes with uneven batches ------------------------

@@ -204,6 +204,11 @@ __device__ __forceinline__ void sts128u(uint32_t addr, uint32_t x, uint32_t y, u
 __device__ __forceinline__ void sts128f(uint32_t addr, float x, float y, float z, float w) {
   asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(x), "f"(y), "f"(z), "f"(w) : "memory");
 }
+__device__ __forceinline__ float4 lds128f(uint32_t addr) {
+  float4 v;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr) : "memory");
+  return v;
+}
 __device__ __forceinline__ uint4 lds128(const void *p) {
   uint4 v;
   asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
@@ -912,12 +917,17 @@ __device__ __forceinline__ void st4(void *base, size_t e, float4 v, const float 
 // rows x Wrow columns, i.e. a box of the output with element strides 2 in H
 // and W starting at (2 i0 + oy, ox); the skip add reads each lane's own row
 // (prefetched one chunk ahead, as in the other epilogues).
-// E4: the tile is stored as e4m3 with a.out_qinv (FP8 contexts' encoder
-// outputs), compiled apart.
-template <int PREC, bool FOLD, bool E4>
+// EPI (compiled apart): EPI_E4 stores the tile as e4m3 with a.out_qinv (FP8
+// contexts' encoder outputs); EPI_SKIP is the FP32 decoder form, whose skip
+// comes by TMA when a.skip_tma; EPI_PAIR is EPI_SKIP for a phase pair,
+// columns [Cout, 2 Cout) at the second output parity.
+enum EpiForm { EPI_PLAIN = 0, EPI_E4 = 1, EPI_PAIR = 2, EPI_SKIP = 3 };
+template <int PREC, bool FOLD, int EPI>
 __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, int BN, int n0, int row0,
                                              const PhaseDesc &pd, uint32_t ring, int &box, unsigned long long &w_tfull,
-                                             uint32_t tfull, uint32_t par, unsigned long long &w_ld, uint32_t t2) {
+                                             uint32_t tfull, uint32_t par, unsigned long long &w_ld, uint32_t t2,
+                                             uint32_t skbar, uint32_t &skpar) {
+  constexpr bool E4 = EPI == EPI_E4;
   const int lane = threadIdx.x & 31;
   const bool convt = a.kind == LK_CONVT;
   // box origin (convT) and this lane's skip row
@@ -928,21 +938,59 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
   const int n = m / rows_per_map, rem = m - n * rows_per_map;
   const int i = rem / a.Wrow, j = rem - (rem / a.Wrow) * a.Wrow;
   const size_t sbase = (((size_t)n * a.Hout + (2 * i + pd.oy)) * a.Wout + (2 * j + pd.ox)) * a.Cout + n0;
+  // a phase pair (one tile, n0 = 0): columns [Cout, 2 Cout) are the output
+  // parity (oy2, ox2), whose skip element is dsk past the first phase's
+  constexpr bool pr = EPI == EPI_PAIR;
+  const int dsk = pr ? ((pd.oy2 - pd.oy) * a.Wout + (pd.ox2 - pd.ox) - 1) * a.Cout : 0;
+  // skip boxes by TMA (a.skip_tma): chunk cc's box of the ring, (box0 + cc)
+  // mod EPI_TMA_BOXES, is loaded on that box's barrier -- the first
+  // EPI_TMA_BOXES - 1 before the accumulator is waited for, each later one
+  // once the store of the chunk before it has read its box -- and the chunk
+  // adds the skip from there and stores the sum from the same box
+  constexpr bool SKT = PREC == PREC_TF32X3 && !FOLD && (EPI == EPI_SKIP || EPI == EPI_PAIR);
+  const bool skt = SKT && a.skip_tma;
+  const int nch = BN / 16;
+  const int box0 = box;
+  auto issue_skip = [&](int cc) {  // lane 0
+    const int b = (box0 + cc) % EPI_TMA_BOXES, c0 = n0 + cc * 16;
+    const bool u = pr && c0 >= a.Cout;
+    const uint32_t bar = skbar + 8u * (uint32_t)b;
+    mbar_arrive_expect_tx(bar, EPI_TMA_BOX_BYTES);
+    tma_load_4d(ring + (uint32_t)(b * EPI_TMA_BOX_BYTES), &a.ymap, u ? c0 - a.Cout : c0, u ? pd.ox2 : pd.ox,
+                2 * bi0 + (u ? pd.oy2 : pd.oy), bn0, bar);
+  };
+  // after a failed wait: the loads still in flight, chunks [c1, c2), land
+  // before the kernel returns (bounded waits, their failures only latched)
+  auto drain_skip = [&](int c1, int c2) {
+    if (lane == 0)
+      for (int cc = c1; cc < c2 && cc < nch; ++cc) {
+        const int b = (box0 + cc) % EPI_TMA_BOXES;
+        mbar_wait(skbar + 8u * (uint32_t)b, (skpar >> b) & 1u, a.timeout_ns, a.status, ERR_TIMEOUT);
+        skpar ^= 1u << b;
+      }
+  };
+  if constexpr (SKT) {
+    if (skt && lane == 0) {
+      bulk_wait_read<0>();  // every box's last store has read it
+      for (int cc = 0; cc < nch && cc < EPI_TMA_BOXES - 1; ++cc) issue_skip(cc);
+    }
+  }
   using act_t = typename PrecTraits<PREC>::act_t;
-  const act_t *skp = a.skip && vrow ? reinterpret_cast<const act_t *>(a.skip) + sbase : nullptr;
+  const act_t *skp = a.skip && vrow && !skt ? reinterpret_cast<const act_t *>(a.skip) + sbase : nullptr;
   float4 sk[4];
   // 16 skip values of chunk cc (fp32: four 16-byte loads; bf16: two)
   auto load_sk = [&](int cc) {
+    const act_t *sp = skp + cc * 16 + (cc * 16 >= a.Cout ? dsk : 0);
     if constexpr (PREC == PREC_BF16) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(skp + cc * 16) + h);
+        const uint4 u = __ldg(reinterpret_cast<const uint4 *>(sp) + h);
         sk[2 * h] = make_float4(bf16_lo(u.x), bf16_hi(u.x), bf16_lo(u.y), bf16_hi(u.y));
         sk[2 * h + 1] = make_float4(bf16_lo(u.z), bf16_hi(u.z), bf16_lo(u.w), bf16_hi(u.w));
       }
     } else {
 #pragma unroll
-      for (int e4 = 0; e4 < 4; ++e4) sk[e4] = __ldg(reinterpret_cast<const float4 *>(skp + cc * 16) + e4);
+      for (int e4 = 0; e4 < 4; ++e4) sk[e4] = __ldg(reinterpret_cast<const float4 *>(sp) + e4);
     }
   };
   if (skp) load_sk(0);
@@ -953,15 +1001,20 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
 #pragma unroll
     for (int o = 0; o < KHEAD_MAX; ++o) hacc[o] = head && o < a.head_cout ? __ldg(a.head_w + a.head_cout * a.Cout + o) : 0.f;
   }
-  if (!pwait(a, w_tfull, tfull, par)) return false;
+  if (!pwait(a, w_tfull, tfull, par)) {
+    if (skt) drain_skip(0, EPI_TMA_BOXES - 1);
+    return false;
+  }
   tc_fence_after();
-  for (int cc = 0; cc < BN / 16; ++cc) {
+  for (int cc = 0; cc < nch; ++cc) {
     const int col0 = n0 + cc * 16;
     float v[16];
     const long long tl0 = a.prof ? clock64() : 0;
     tmem_ld_acc<PREC, FOLD>(taddr + cc * 16, acc_at<FOLD>(FOLD ? t2 : taddr + (uint32_t)BN, cc * 16), v);
     if (a.prof) w_ld += (unsigned long long)(clock64() - tl0);
-    const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + col0);
+    const bool up = pr && col0 >= a.Cout;  // the pair's second phase
+    const int ch0 = up ? col0 - a.Cout : col0;
+    const float4 *bias4 = reinterpret_cast<const float4 *>(a.bias + ch0);
     if constexpr (PREC == PREC_FP8) {  // dequantise with the output columns' weight scales
 #pragma unroll
       for (int e = 0; e < 16; ++e) v[e] *= __ldg(a.bscale + col0 + e);
@@ -986,6 +1039,25 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
         v[4 * e4 + 3] += sk[e4].w;
       }
       if (cc + 1 < BN / 16) load_sk(cc + 1);
+    }
+    if constexpr (SKT) {
+      if (skt) {  // this chunk's skip box (the waits count as the epilogue's input waits)
+        const uint32_t bar = skbar + 8u * (uint32_t)box;
+        if (!pwait(a, w_tfull, bar, (skpar >> box) & 1u)) {
+          drain_skip(cc + 1, cc + EPI_TMA_BOXES - 1);
+          return false;
+        }
+        skpar ^= 1u << box;
+        const uint32_t sb = ring + (uint32_t)(box * EPI_TMA_BOX_BYTES) + (uint32_t)(lane * 64);
+#pragma unroll
+        for (int e4 = 0; e4 < 4; ++e4) {
+          const float4 k = lds128f(sb + (uint32_t)((e4 ^ ((lane >> 1) & 3)) << 4));
+          v[4 * e4] += k.x;
+          v[4 * e4 + 1] += k.y;
+          v[4 * e4 + 2] += k.z;
+          v[4 * e4 + 3] += k.w;
+        }
+      }
     }
     if constexpr (FOLD) {
       if (head) {  // this chunk's 16 channels into the head's dot products; y is not stored
@@ -1029,10 +1101,16 @@ __device__ __forceinline__ bool epi_tile_tma(const ConvArgs &a, uint32_t taddr, 
     __syncwarp();
     if (lane == 0) {
       if (convt)
-        tma_store_4d(&a.ymap, stg, col0, pd.ox, 2 * bi0 + pd.oy, bn0);
+        tma_store_4d(&a.ymap, stg, ch0, up ? pd.ox2 : pd.ox, 2 * bi0 + (up ? pd.oy2 : pd.oy), bn0);
       else
         tma_store_2d(&a.ymap, stg, col0, row0);
       bulk_commit();
+      if constexpr (SKT) {
+        if (skt && cc + EPI_TMA_BOXES - 1 < nch) {  // into the box of chunk cc - 1, once its store has read it
+          bulk_wait_read<1>();
+          issue_skip(cc + EPI_TMA_BOXES - 1);
+        }
+      }
     }
   }
   if constexpr (FOLD) {
@@ -1288,7 +1366,7 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
 // compiled apart so that the other layers carry none of its code.
 // FOLD: the U-Net form -- accumulation chunks and LeakyReLU (TF32X3 with A
 // in tensor memory only), compiled apart like YTMA.
-template <int PREC, bool YTMA, bool FOLD, bool E4>
+template <int PREC, bool YTMA, bool FOLD, int EPI>
 __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_constant__ ConvArgs a) {
   using T = PrecTraits<PREC>;
   const int BN = a.BN;
@@ -1311,8 +1389,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
   uint64_t *stall_bar = tempty_bar + 2;                      // [1]
   uint64_t *raw_full = stall_bar + 1;                        // [RAW_MAX]
   uint64_t *raw_empty = raw_full + RAW_MAX;                  // [RAW_MAX]
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(raw_empty + RAW_MAX);
-  static_assert((8 + 8 + 2 + 2 + 1 + 2 * RAW_MAX) * 8 + 4 <= SMEM_CTRL, "control block");
+  uint64_t *skip_bar = raw_empty + RAW_MAX;                  // [4 * EPI_TMA_BOXES]
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(skip_bar + 4 * EPI_TMA_BOXES);
+  static_assert((8 + 8 + 2 + 2 + 1 + 2 * RAW_MAX + 4 * EPI_TMA_BOXES) * 8 + 4 <= SMEM_CTRL, "control block");
   const uint32_t base_u32 = smem_u32(smem_raw);
   const uint32_t data_u32 = (base_u32 + SMEM_CTRL + 1023u) & ~1023u;
   uint8_t *data = smem_raw + (data_u32 - base_u32);
@@ -1361,6 +1440,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       mbar_init(smem_u32(&raw_full[r]), 1);                        // the TMA thread's arrive
       mbar_init(smem_u32(&raw_empty[r]), 4);                      // one arrive per warp of the converting group
     }
+    for (int b = 0; b < 4 * EPI_TMA_BOXES; ++b) mbar_init(smem_u32(&skip_bar[b]), 1);  // the epilogue lane's arrive
     fence_mbar_init();
   }
   tc_fence_before();
@@ -1471,7 +1551,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     // this lane quarter's tensor-memory rows; with accumulation chunks the
     // running sum is at column 0
     const uint32_t lanebase = tmem_base + ((uint32_t)(eq * 32) << 16);
-    int tma_box = 0;  // next box of this warp's TMA staging ring
+    int tma_box = 0;      // next box of this warp's TMA staging ring
+    uint32_t skpar = 0;   // per box: parity of its next skip load
     bool failed = false;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x, ++it) {
       const TileCoord tc = tile_coord(a, t);
@@ -1524,9 +1605,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
                               : (size_t)m;
       const size_t ebase = opix * a.Cout + (size_t)tc.n_tile * BN;
       if (YTMA && plan.epi_stage) {
-        if (!epi_tile_tma<PREC, FOLD, E4>(a, taddr, BN, tc.n_tile * BN, tc.m_tile * BM + eq * 32, pd,
+        if (!epi_tile_tma<PREC, FOLD, EPI>(a, taddr, BN, tc.n_tile * BN, tc.m_tile * BM + eq * 32, pd,
                                 smem_u32(epi_stg) + (uint32_t)(eq * EPI_TMA_BOXES * EPI_TMA_BOX_BYTES), tma_box,
-                                w_tfull, smem_u32(&tfull_bar[buf]), par, w_ld, t2))
+                                w_tfull, smem_u32(&tfull_bar[buf]), par, w_ld, t2,
+                                smem_u32(&skip_bar[eq * EPI_TMA_BOXES]), skpar))
           break;
         tc_fence_before();
         __syncwarp();
@@ -1600,12 +1682,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
   }
 }
 
-template <int PREC, bool YTMA, bool FOLD, bool E4 = false>
+template <int PREC, bool YTMA, bool FOLD, int EPI = EPI_PLAIN>
 static cudaError_t launch_form(const ConvArgs &a, int grid, size_t smem, cudaStream_t st) {
-  cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<PREC, YTMA, FOLD, E4>,
+  cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<PREC, YTMA, FOLD, EPI>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  conv_tc_kernel<PREC, YTMA, FOLD, E4><<<grid, NUM_THREADS, smem, st>>>(a);
+  conv_tc_kernel<PREC, YTMA, FOLD, EPI><<<grid, NUM_THREADS, smem, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -1620,19 +1702,28 @@ cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t s
       (a.head_w && (!fold || !a.y_tma || a.kind == LK_CONVT || a.n_tiles != 1 || a.head_cout < 1 ||
                     a.head_cout > KHEAD_MAX || !a.head_out)))
     return cudaErrorInvalidValue;
+  // phase pairs: every phase of the launch, through the TMA-store epilogue
+  // of the FP32 kernel, one tile of 2 Cout columns
+  const bool pair = a.kind == LK_CONVT && a.num_phases > 0 && a.ph[0].pair;
+  for (int p = 0; p < a.num_phases; ++p)
+    if ((a.ph[p].pair != 0) != pair) return cudaErrorInvalidValue;
+  if (pair && (prec != PREC_TF32X3 || fold || !a.y_tma || a.n_tiles != 1 || a.BN != 2 * a.Cout))
+    return cudaErrorInvalidValue;
   const size_t smem = conv_smem_bytes(prec, a.BN, a.prod_mode, a.y_tma, fold ? 1 : 0);
   switch (prec) {
     case PREC_TF32X3:
       if (fold) return a.y_tma ? launch_form<PREC_TF32X3, true, true>(a, grid, smem, st)
                                : launch_form<PREC_TF32X3, false, true>(a, grid, smem, st);
+      if (pair) return launch_form<PREC_TF32X3, true, false, EPI_PAIR>(a, grid, smem, st);
+      if (a.y_tma && a.skip_tma) return launch_form<PREC_TF32X3, true, false, EPI_SKIP>(a, grid, smem, st);
       return a.y_tma ? launch_form<PREC_TF32X3, true, false>(a, grid, smem, st)
                      : launch_form<PREC_TF32X3, false, false>(a, grid, smem, st);
     case PREC_BF16:
-      if (a.y_tma && a.out_qinv) return launch_form<PREC_BF16, true, false, true>(a, grid, smem, st);
+      if (a.y_tma && a.out_qinv) return launch_form<PREC_BF16, true, false, EPI_E4>(a, grid, smem, st);
       return a.y_tma ? launch_form<PREC_BF16, true, false>(a, grid, smem, st)
                      : launch_form<PREC_BF16, false, false>(a, grid, smem, st);
     default:  // FP8 TMA stores are always e4m3
-      return a.y_tma ? launch_form<PREC_FP8, true, false, true>(a, grid, smem, st)
+      return a.y_tma ? launch_form<PREC_FP8, true, false, EPI_E4>(a, grid, smem, st)
                      : launch_form<PREC_FP8, false, false>(a, grid, smem, st);
   }
 }
@@ -1698,6 +1789,12 @@ __device__ float raw_weight(const PackArgs &p, const PhaseDesc &pd, int col, int
     return p.wraw[((size_t)col * p.Cin_raw + c) * 9 + t];
   // LK_CONVT: W[c][o][u][v] with the phase's kernel tap
   const int co = p.Cout_raw > 0 ? p.Cout_raw : p.Cout;
+  if (pd.pair) {  // columns [co, 2 co): the pair's second phase
+    const bool up = col >= co;
+    const int o = up ? col - co : col, u = up ? pd.u2[t] : pd.u[t], v = up ? pd.v2[t] : pd.v[t];
+    if (u < 0 || v < 0 || o >= co) return 0.f;
+    return p.wraw[(((size_t)c * co + o) * 3 + u) * 3 + v];
+  }
   if (col >= co) return 0.f;
   return p.wraw[(((size_t)c * co + col) * 3 + pd.u[t]) * 3 + pd.v[t]];
 }

@@ -32,8 +32,19 @@ struct PhaseDesc {
   int oy, ox;        // output parity (LK_CONVT); 0 otherwise
   long long b_off;   // byte offset of this phase's packed B tiles
   signed char dy[9], dx[9];  // input pixel offset of each tap, from the row's base pixel
-  signed char u[9], v[9];    // kernel tap (row, col) of each tap (weight packing)
+  signed char u[9], v[9];    // kernel tap (row, col) of each tap (weight packing); -1: none (pair)
+  // LK_CONVT phase pair (pair = 1): columns [Cout, 2 Cout) of the GEMM are a
+  // second output parity (oy2, ox2) with kernel taps (u2, v2) over the same
+  // input taps (the union of the two phases' taps; -1 where that phase has
+  // no weight for the tap)
+  int pair, oy2, ox2;
+  signed char u2[9], v2[9];
 };
+// drc_describe_layer / autotune codes of a decoder layer run as phase pairs:
+// A in tensor memory (the default path), or in shared memory (TMA + producer
+// conversion; the tensor memory then holds two accumulator buffers)
+constexpr int A_PATH_PAIRED = 8;
+constexpr int A_PATH_PAIRED_SMEM = 9;
 
 // How the A operand reaches shared memory.
 enum ProdMode {
@@ -51,6 +62,8 @@ struct ConvArgs {
                      // [N][Hout][Wout][Cout] with element strides {1, 2, 2, 1}, box {16, 2 Wrow, 2 rw, mw}
   int y_tma;         // FP32 without training outputs: tiles stored by TMA from shared memory
   int y_rw, y_mw;    // LK_CONVT: phase rows and maps per 32-row box (Wrow * y_rw * y_mw = 32)
+  int skip_tma;      // y_tma FP32 decoder whose skip is its output (in place): the epilogue reads the
+                     // skip boxes through ymap by TMA, into the staging boxes the stores then read
   int prod_mode;
   int tap_boxes;     // TMA modes, FP32 with 8 stored input channels (32 bytes per tap): one box per tap,
                      // four per K block, placed tap-major in the raw slot (BM rows x 32 bytes each)

@@ -61,6 +61,12 @@ struct drc_ctx {
   int prec = PREC_TF32X3;
   size_t n_floats = 0;
   std::vector<Layer> layers;  // conv_1..conv_S, convT_S..convT_2, head
+  // per layer: the FP32 decoder layer as two GEMMs of phase pairs (kind 0:
+  // none), its own packed operands; used where drc_autotune picks a
+  // phase-pair path (A_PATH_PAIRED, A_PATH_PAIRED_SMEM)
+  std::vector<Layer> players;
+  uint8_t *d_ppack = nullptr, *d_ppack_lo = nullptr;
+  size_t ppack_total = 0;
   std::vector<int> modes;     // per layer: A-operand path chosen by drc_autotune (-1 = default)
   std::vector<Layer> dlayers; // data-gradient GEMMs of conv_1..conv_S, convT_S..convT_2 (training)
   uint8_t *d_dpack = nullptr, *d_dpack_lo = nullptr;
@@ -201,6 +207,7 @@ EncodeTiledFn encode_tiled() {
 // the output as a 2-D tensor [M][Cout] with 16-column x 32-row boxes.
 void plan_store(int prec, ConvArgs &a) {
   a.y_tma = 0;
+  a.skip_tma = 0;
   if (a.y2 || a.mask || a.amax || a.BN % 16 || a.Cout % 8) return;
   // e4m3 outputs (FP8 contexts: quantised for the consuming layer) of the
   // encoder convs, from the BF16 first layer or an FP8 layer: 16-byte rows,
@@ -247,7 +254,10 @@ void plan_store(int prec, ConvArgs &a) {
   } else {
     return;
   }
-  if (r == CUDA_SUCCESS) a.y_tma = 1;
+  if (r == CUDA_SUCCESS) {
+    a.y_tma = 1;
+    a.skip_tma = a.kind == LK_CONVT && prec == PREC_TF32X3 && a.skip && a.skip == a.y && !a.skip_scale;
+  }
 }
 
 void plan_operand(int prec, ConvArgs &a, int force_mode = -1) {
@@ -464,6 +474,47 @@ void plan_layers(drc_ctx *c) {
     finish(L);
   }
   c->pack_total = layout_packs(c->layers);
+  // FP32 decoder layers whose two phases of one output row fit a 128-column
+  // tile: phases (0,0)+(0,1) over their two input taps, (1,0)+(1,1) over four
+  c->players.assign(c->layers.size(), Layer());
+  for (size_t li = 0; li < c->layers.size(); ++li) {
+    const Layer &L = c->layers[li];
+    if (L.kind != LK_CONVT || L.prec != PREC_TF32X3 || 2 * L.Cout > 128 || L.Cout % 16) continue;
+    Layer P = L;
+    snprintf(P.name, sizeof P.name, "%s", L.name);
+    set_bn(P, 2 * L.Cout);
+    P.n_tiles = 1;
+    P.num_phases = 2;
+    for (int q = 0; q < 2; ++q) {
+      const PhaseDesc &lo = L.ph[2 * q], &hi = L.ph[2 * q + 1];  // (q, 0) and (q, 1)
+      PhaseDesc pd;
+      memset(&pd, 0, sizeof pd);
+      pd.pair = 1;
+      pd.oy = lo.oy;
+      pd.ox = lo.ox;
+      pd.oy2 = hi.oy;
+      pd.ox2 = hi.ox;
+      for (int t = 0; t < hi.ntaps; ++t) {  // the second phase's taps hold the first's
+        pd.dy[t] = hi.dy[t];
+        pd.dx[t] = hi.dx[t];
+        pd.u2[t] = hi.u[t];
+        pd.v2[t] = hi.v[t];
+        pd.u[t] = pd.v[t] = -1;
+        for (int s = 0; s < lo.ntaps; ++s)
+          if (lo.dy[s] == hi.dy[t] && lo.dx[s] == hi.dx[t]) {
+            pd.u[t] = lo.u[s];
+            pd.v[t] = lo.v[s];
+          }
+      }
+      pd.ntaps = hi.ntaps;
+      pd.num_kb = ceil_div((long long)pd.ntaps * L.Cin, bke_of(L.prec));
+      P.ph[q] = pd;
+    }
+    P.phase_order[0] = 1;  // four taps first
+    P.phase_order[1] = 0;
+    c->players[li] = P;
+  }
+  c->ppack_total = layout_packs(c->players);
   c->n_scales = sc;
   c->n_bscales = bs;
 }
@@ -550,7 +601,16 @@ drc_status pack_layers(drc_ctx *c, const std::vector<Layer> &Ls, uint8_t *B, uin
   return DRC_OK;
 }
 
-drc_status pack_all(drc_ctx *c, cudaStream_t st) { return pack_layers(c, c->layers, c->d_pack, c->d_pack_lo, st); }
+drc_status pack_all(drc_ctx *c, cudaStream_t st) {
+  drc_status s = pack_layers(c, c->layers, c->d_pack, c->d_pack_lo, st);
+  if (s == DRC_OK && c->ppack_total) {
+    std::vector<Layer> pl;
+    for (const Layer &P : c->players)
+      if (P.kind == LK_CONVT) pl.push_back(P);
+    s = pack_layers(c, pl, c->d_ppack, c->d_ppack_lo, st);
+  }
+  return s;
+}
 
 size_t act_bytes_for(const drc_ctx *c, long long N, int H, int W) {
   // the first layer's NHWC input (8 channels), then e_1 .. e_S
@@ -684,6 +744,19 @@ void conv_args_for(const drc_ctx *c, const std::vector<Layer> &Ls, const Layer &
   plan_operand(L.prec, a, force_mode);
 }
 
+bool is_paired(int mode) { return mode == A_PATH_PAIRED || mode == A_PATH_PAIRED_SMEM; }
+
+// ConvArgs of decoder layer li of the context's own table as its two GEMMs of
+// phase pairs (mode A_PATH_PAIRED or A_PATH_PAIRED_SMEM); false where the
+// layer has no paired form or its output tiles do not fit the TMA-store
+// epilogue the pairs need.
+bool paired_args(const drc_ctx *c, size_t li, const Chain &ch, int mode, ConvArgs &a) {
+  if (li >= c->players.size() || c->players[li].kind != LK_CONVT || !is_paired(mode)) return false;
+  const bool smem = mode == A_PATH_PAIRED_SMEM;
+  conv_args_for(c, c->layers, c->players[li], li, ch, c->d_ppack, c->d_ppack_lo, smem ? PROD_TMA_CONVERT : -1, a);
+  return a.y_tma && a.prod_mode == (smem ? PROD_TMA_CONVERT : PROD_TMA_TMEM);
+}
+
 // Enqueue the whole network over one chain: input staging, S encoder convs,
 // S-1 decoder convTs, the head.  tr: launch tracer (nullptr while capturing a
 // graph); prof: wait-time counters per layer, or nullptr.
@@ -728,7 +801,9 @@ drc_status run_chain(drc_ctx *c, const std::vector<Layer> &layers, const uint8_t
       continue;
     }
     ConvArgs a;
-    conv_args_for(c, layers, L, li, ch, B, B_lo, modes ? (*modes)[li] : -1, a);
+    // phase-pair paths: the context's own layers only (plans keep their tiles)
+    const bool paired = modes && &layers == &c->layers && paired_args(c, li, ch, (*modes)[li], a);
+    if (!paired) conv_args_for(c, layers, L, li, ch, B, B_lo, modes ? (*modes)[li] : -1, a);
     a.debug_stall = debug_stall && li == 0;
     if (prof) a.prof = prof + li * PROF_SLOTS;
     DRC_TRACED(tr, L.name, st, e = launch_conv(a, L.prec, c->num_sms, st));
@@ -1177,17 +1252,14 @@ drc_status plan_pack(drc_plan *p, cudaStream_t st) {
   return DRC_OK;
 }
 
-// Time one conv layer of a chain (min of 3 launches after one warm-up).
-drc_status time_layer(drc_ctx *c, const std::vector<Layer> &Ls, const Layer &L, size_t li, const Chain &ch,
-                      const uint8_t *B, const uint8_t *B_lo, int mode, cudaStream_t st, cudaEvent_t e0,
-                      cudaEvent_t e1, float *best_ms) {
-  ConvArgs a;
-  conv_args_for(c, Ls, L, li, ch, B, B_lo, mode, a);
+// Time one conv launch (min of 3 launches after one warm-up).
+drc_status time_args(drc_ctx *c, ConvArgs &a, int prec, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1,
+                     float *best_ms) {
   a.count = nullptr;
   float best = 1e30f;
   for (int r = 0; r < 4; ++r) {
     cudaEventRecord(e0, st);
-    cudaError_t e = launch_conv(a, L.prec, c->num_sms, st);
+    cudaError_t e = launch_conv(a, prec, c->num_sms, st);
     cudaEventRecord(e1, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "autotune launch");
     if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return cuda_fail(c, e, "autotune sync");
@@ -1199,10 +1271,19 @@ drc_status time_layer(drc_ctx *c, const std::vector<Layer> &Ls, const Layer &L, 
   return DRC_OK;
 }
 
+drc_status time_layer(drc_ctx *c, const std::vector<Layer> &Ls, const Layer &L, size_t li, const Chain &ch,
+                      const uint8_t *B, const uint8_t *B_lo, int mode, cudaStream_t st, cudaEvent_t e0,
+                      cudaEvent_t e1, float *best_ms) {
+  ConvArgs a;
+  conv_args_for(c, Ls, L, li, ch, B, B_lo, mode, a);
+  return time_args(c, a, L.prec, st, e0, e1, best_ms);
+}
+
 // Pick each conv layer's tile width (and, split-tf32, the A-operand path) by
-// timing the candidates on a chain's full-size buffers.
+// timing the candidates on a chain's full-size buffers.  pairs: the chain is
+// the context's own, whose decoder layers may also run as phase pairs.
 drc_status autotune_layers(drc_ctx *c, std::vector<Layer> &Ls, std::vector<int> &modes, const Chain &ch,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool pairs = false) {
   size_t scratch = 0;
   for (const Layer &L : Ls) {
     if (L.kind == LK_HEAD) continue;
@@ -1242,6 +1323,16 @@ drc_status autotune_layers(drc_ctx *c, std::vector<Layer> &Ls, std::vector<int> 
         }
       }
       if (s != DRC_OK) break;
+    }
+    for (int pm : {A_PATH_PAIRED, A_PATH_PAIRED_SMEM}) {
+      ConvArgs pa;
+      if (s != DRC_OK || !pairs || !paired_args(c, li, ch, pm, pa)) continue;
+      float ms = 0.f;
+      s = time_args(c, pa, Ls[li].prec, st, e0, e1, &ms);
+      if (s == DRC_OK && ms < best) {  // the unpaired tile width stays the fallback
+        best = ms;
+        best_mode = pm;
+      }
     }
     set_bn(Ls[li], best_bn);
     modes[li] = best_mode;
@@ -1295,6 +1386,8 @@ drc_status drc_create(const drc_config *cfg, const float *weights_host, size_t n
   e = ctx_malloc(c, &c->d_wraw, c->n_floats * sizeof(float));
   if (e == cudaSuccess) e = ctx_malloc(c, &c->d_pack, c->pack_total);
   if (e == cudaSuccess && c->prec == PREC_TF32X3) e = ctx_malloc(c, &c->d_pack_lo, c->pack_total);
+  if (e == cudaSuccess && c->ppack_total) e = ctx_malloc(c, &c->d_ppack, c->ppack_total);
+  if (e == cudaSuccess && c->ppack_total) e = ctx_malloc(c, &c->d_ppack_lo, c->ppack_total);
   if (e == cudaSuccess) e = ctx_malloc(c, &c->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
   if (e == cudaSuccess) e = ctx_malloc(c, &c->d_zero, 1024 * sizeof(float));
@@ -1376,6 +1469,8 @@ drc_status drc_destroy(drc_ctx *c) {
   ctx_free(c, c->d_wraw);
   ctx_free(c, c->d_pack);
   ctx_free(c, c->d_pack_lo);
+  ctx_free(c, c->d_ppack);
+  ctx_free(c, c->d_ppack_lo);
   ctx_free(c, c->d_bscale);
   ctx_free(c, c->d_inscale);
   ctx_free(c, c->d_dpack);
@@ -2308,7 +2403,7 @@ drc_status drc_autotune(drc_ctx *c, int N, int H, int W) {
   carve_chain(c, c->d_act, N, H, W, ch);
   std::vector<Layer> Ls = c->layers;
   std::vector<int> modes = c->modes;
-  s = autotune_layers(c, Ls, modes, ch, st);
+  s = autotune_layers(c, Ls, modes, ch, st, true);
   if (s == DRC_OK) s = apply_tiles(c, Ls, modes, st);
   if (s == DRC_OK && (e = cudaStreamSynchronize(st)) != cudaSuccess) s = cuda_fail(c, e, "autotune");
   cudaStreamDestroy(st);
@@ -2715,7 +2810,8 @@ drc_status drc_autotune_cached(drc_ctx *c, int N, int H, int W, const char *path
         bool bn_ok = false;
         for (int cand : bn_candidates(Ls[li])) bn_ok = bn_ok || cand == bn;
         const bool mode_ok = mode == -1 || (c->prec == PREC_TF32X3 && mode == PROD_TMA_CONVERT && bn <= 128) ||
-                             (c->prec == PREC_TF32X3 && mode == PROD_CPASYNC && Ls[li].kind == LK_CONV && Ls[li].Cin == 8);
+                             (c->prec == PREC_TF32X3 && mode == PROD_CPASYNC && Ls[li].kind == LK_CONV && Ls[li].Cin == 8) ||
+                             (is_paired(mode) && li < c->players.size() && c->players[li].kind == LK_CONVT);
         ok = bn_ok && mode_ok;
         if (ok) {
           set_bn(Ls[li], bn);

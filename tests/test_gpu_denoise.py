@@ -225,3 +225,51 @@ def test_autotuned_context_keeps_parity(drc, precision):
         assert rel_err(g, oracle.forward(w, x.cpu().numpy(), widths)) <= FP32_TOL
     print("max |tuned - untuned| / rms:", np.max(np.abs(g - ref)) / np.sqrt(np.mean(ref * ref)))
     assert rel_err(g, ref) <= (1e-6 if precision == "fp32" else 1e-2)
+
+
+PAIR_CASES = [
+    # widths, N, H, W: decoder layers of <= 64 output channels run as phase pairs
+    ([32, 64, 128], 5, 32, 32),     # d3 (64 channels, 128-column pairs), d2 (32, 64-column pairs); ragged M
+    ([64, 128, 256], 9, 32, 32),    # d2 only (d3 has 128 channels)
+    ([16, 32, 48, 64], 3, 64, 64),  # d4 .. d2: 48, 32 and 16 channels (96, 64, 32 columns)
+]
+
+
+@pytest.mark.parametrize("mode", [8, 9])
+@pytest.mark.parametrize("widths,N,H,W", PAIR_CASES)
+def test_phase_pairs_match_oracle(drc, widths, N, H, W, mode, tmp_path):
+    """Decoder layers forced onto the phase-pair form (A path 8: A in tensor
+    memory, 9: in shared memory; applied through a tile cache entry) keep the
+    oracle's FP32 bar, and agree with the one-GEMM-per-parity form: the pair
+    adds zero-weight taps only, whole K blocks of exact zero products."""
+    import json
+    w = synth.he_weights(widths, seed=5, bias=True)
+    x = torch.from_numpy(_maps(N, H, W, seed=7)).cuda()
+    S = len(widths)
+    base = drc.Context(widths, w, precision="fp32")
+    ref = base.denoise(x).cpu().numpy()
+    cache = str(tmp_path / "tiles.jsonl")
+    assert base.autotune(N, H, W, cache=cache) is False
+    entry = json.loads(open(cache).read().splitlines()[-1])
+    tiles = [base.describe_layer(li) for li in range(2 * S)]
+    entry["tile_n"] = [t[0] for t in tiles]
+    entry["a_path"] = [-1] * (2 * S)
+    paired = []
+    for li in range(S, 2 * S - 1):  # convT d_S .. d_2
+        cout = widths[2 * S - 2 - li]
+        if 2 * cout <= 128 and cout % 16 == 0:
+            entry["a_path"][li] = mode
+            paired.append(li)
+    assert paired
+    with open(cache, "a") as f:
+        f.write(json.dumps(entry) + "\n")
+    ctx = drc.Context(widths, w, precision="fp32")
+    assert ctx.autotune(N, H, W, cache=cache) is True
+    assert [ctx.describe_layer(li)[1] for li in paired] == [mode] * len(paired)
+    g = ctx.denoise(x).cpu().numpy()
+    assert ctx.status() == drc.OK
+    err = rel_err(g, oracle.forward(w, x.cpu().numpy(), widths))
+    d = np.max(np.abs(g - ref)) / np.sqrt(np.mean(ref * ref))
+    print("pairs on layers %s: max rel %.3e vs oracle, max |paired - unpaired| / rms %.3e" % (paired, err, d))
+    assert err <= FP32_TOL
+    assert rel_err(g, ref) <= 1e-6
