@@ -771,6 +771,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the precision and uneven-batching lines")
     ap.add_argument("--no-autotune", action="store_true", help="default tile widths instead of drc_autotune")
+    ap.add_argument("--tile-cache", default=None, metavar="PATH",
+                    help="drc_autotune_cached file: reuse the tiles a previous run chose for this shape (profiling "
+                         "runs replay the plain run's choice instead of timing under the profiler)")
     ap.add_argument("--maps", type=int, default=N_MAPS, help="maps per step (profiling of smaller cases)")
     ap.add_argument("--frame", default="%dx%d" % (IMG_W, IMG_H), help="G-buffer WxH (profiling)")
     ap.add_argument("--unet-only", type=int, default=0, metavar="N",
@@ -802,8 +805,8 @@ def main():
     w, x, g, c = make_inputs(seed_offset=rank)
     dev = torch.device("cuda", local)
     ctx = drc.Context(WIDTHS, w, precision=args.precision, max_maps=N_MAPS, max_hw=MAP_H * MAP_W)
-    if not args.no_autotune:
-        ctx.autotune(N_MAPS, MAP_H, MAP_W)  # setup: per-layer tile choice for this batch shape
+    if not args.no_autotune:  # setup: per-layer tile choice for this batch shape
+        ctx.autotune(N_MAPS, MAP_H, MAP_W, cache=args.tile_cache)
     tiles = [ctx.describe_layer(li) for li in range(2 * len(WIDTHS))]
     xd = torch.from_numpy(x).to(dev)
     gd = {"width": IMG_W, "height": IMG_H, "pos": torch.from_numpy(g["pos"]).to(dev),
