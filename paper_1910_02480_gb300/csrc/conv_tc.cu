@@ -122,6 +122,11 @@ static __host__ __device__ SmemPlan smem_plan_avail(int prec, int BN, int mode, 
   while (R > 2 && avail - R * rb < 2 * sb) --R;
   int st = (avail - R * rb) / sb;
   if (st > 8) st = 8;
+  // what the stages leave over: more raw boxes in flight
+  if (mode == PROD_TMA_CONVERT) {
+    R += (avail - R * rb - st * sb) / rb;
+    if (R > RAW_MAX) R = RAW_MAX;
+  }
   SmemPlan p;
   p.stages = st;
   p.raw_depth = R;
