@@ -475,7 +475,9 @@ const char *drc_last_error(drc_ctx *ctx);
  * of one output row side by side in a 2 Cout-column tile over the union of
  * their input taps (a tap one of the two parities lacks has zero weights
  * there).
- * Synchronises the device; grows the workspace to N maps.  No counterpart in
+ * Synchronises the device first (calls in flight on any stream finish before
+ * the timing launches reuse the workspace) and at the end; grows the
+ * workspace to N maps.  No counterpart in
  * the paper. */
 drc_status drc_autotune(drc_ctx *ctx, int N, int H, int W);
 

@@ -2394,10 +2394,14 @@ drc_status drc_autotune(drc_ctx *c, int N, int H, int W) {
       (long long)N * H * W * 7 >= (1ll << 31))
     return fail(c, DRC_ERR_INVALID_ARG, "autotune shape N=%d H=%d W=%d is not a valid denoise batch", N, H, W);
   if (!c->weights_set) return fail(c, DRC_ERR_INVALID_ARG, "weights were never set");
+  // the timing launches write the context's workspace and the repack its
+  // packed operands: calls still in flight on any stream finish first
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_fail(c, e, "device synchronize");
   drc_status s = ensure_act(c, N, H, W);
   if (s != DRC_OK) return s;
   cudaStream_t st = nullptr;
-  cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(c, e, "autotune stream");
   Chain ch;
   carve_chain(c, c->d_act, N, H, W, ch);
@@ -2503,6 +2507,9 @@ drc_status drc_plan_create(drc_ctx *c, const drc_size_class *classes, int n_clas
     if (q.max_maps < 1 || (long long)q.max_maps * q.H * q.W * 7 >= (1ll << 31))
       return fail(c, DRC_ERR_INVALID_ARG, "class %d: max_maps must be >= 1 and max_maps*7*H*W < 2^31", k);
   }
+  // the plan packs from the context's weights on its own stream: updates in
+  // flight on any stream land first
+  if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(c, cudaGetLastError(), "device synchronize");
   drc_plan *p = new (std::nothrow) drc_plan();
   if (!p) return fail(c, DRC_ERR_OOM, "plan");
   p->ctx = c;
@@ -2824,6 +2831,8 @@ drc_status drc_autotune_cached(drc_ctx *c, int N, int H, int W, const char *path
       }
     }
     if (!best.empty()) {
+      // the repack rewrites operands that calls in flight may be reading
+      if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(c, e, "device synchronize");
       drc_status s = ensure_act(c, N, H, W);
       if (s != DRC_OK) return s;
       if (!c->weights_set) return fail(c, DRC_ERR_INVALID_ARG, "weights were never set");
