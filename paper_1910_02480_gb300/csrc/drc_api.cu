@@ -2533,6 +2533,9 @@ drc_status drc_plan_create(drc_ctx *c, const drc_size_class *classes, int n_clas
   p->chains.resize(n_classes);
   p->layers.assign(n_classes, c->layers);
   p->modes.assign(n_classes, c->modes);
+  for (auto &m : p->modes)  // plans keep the four-GEMM decoders (their own tiles and packing)
+    for (int &x : m)
+      if (is_paired(x)) x = -1;
   p->pack.assign(n_classes, nullptr);
   p->pack_lo.assign(n_classes, nullptr);
   cudaStream_t cs = nullptr;
