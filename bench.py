@@ -138,7 +138,7 @@ def _events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def measure_precision(drc, torch, dev, prec, fp32_denoise_ms, autotune=True, steps=20):
+def measure_precision(drc, torch, dev, prec, fp32_denoise_ms, autotune=True, steps=20, tile_cache=None):
     """Denoise-only throughput of another precision at the benchmark's size,
     its speedup over the FP32 path, and its error against the FP64 oracle on
     a sample of high-dynamic-range maps (lobes log-uniform in 1e-3..1e3)."""
@@ -156,7 +156,7 @@ def measure_precision(drc, torch, dev, prec, fp32_denoise_ms, autotune=True, ste
         ctx.calibrate(torch.from_numpy(np.ascontiguousarray(xc, dtype=np.float32)).to(dev))
         cal_note = "256 maps of the HDR field (not the error sample), drc_calibrate"
     if autotune:
-        ctx.autotune(N_MAPS, MAP_H, MAP_W)
+        ctx.autotune(N_MAPS, MAP_H, MAP_W, cache=tile_cache)
     xd = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(dev)
     out = torch.empty((N_MAPS, 3, MAP_H, MAP_W), device=dev)
     pay = torch.empty((N_MAPS, 3), device=dev)
@@ -212,7 +212,7 @@ def measure_precision(drc, torch, dev, prec, fp32_denoise_ms, autotune=True, ste
                      "normwise": float(np.linalg.norm(gv - rv) / np.linalg.norm(rv))}
     ctx.close()
     return {"denoise_ms": den, "denoise_maps_per_s": N_MAPS / (den * 1e-3), "roofline": roof,
-            "speedup_vs_fp32_denoise": fp32_denoise_ms / den, "error_vs_oracle": err,
+            "speedup_vs_fp32_denoise": fp32_denoise_ms / den if fp32_denoise_ms else None, "error_vs_oracle": err,
             "error_sample": "16 maps 7x32x32, lobes log-uniform 1e-3..1e3, FP64 oracle",
             "calibration": cal_note}
 
@@ -776,6 +776,9 @@ def main():
                          "runs replay the plain run's choice instead of timing under the profiler)")
     ap.add_argument("--maps", type=int, default=N_MAPS, help="maps per step (profiling of smaller cases)")
     ap.add_argument("--frame", default="%dx%d" % (IMG_W, IMG_H), help="G-buffer WxH (profiling)")
+    ap.add_argument("--precision-only", default=None, choices=["bf16", "fp8"],
+                    help="only the BF16 or FP8 denoise line (precision_variants) at --maps, --steps timed calls "
+                         "(profiling of those conv kernels)")
     ap.add_argument("--unet-only", type=int, default=0, metavar="N",
                     help="only the paper-form U-Net on N maps (profiling): one JSON line, --steps timed forwards")
     args = ap.parse_args()
@@ -796,6 +799,11 @@ def main():
     if args.unet_only > 0:
         print(json.dumps(measure_unet(drc, torch, torch.device("cuda", local), N=args.unet_only,
                                       steps=max(1, args.steps), warmup=max(1, args.warmup))))
+        return
+    if args.precision_only:
+        r = measure_precision(drc, torch, torch.device("cuda", local), args.precision_only, None,
+                              autotune=not args.no_autotune, steps=max(1, args.steps), tile_cache=args.tile_cache)
+        print(json.dumps(dict(r, precision=args.precision_only, maps=N_MAPS)))
         return
     dist = None
     if world > 1:
