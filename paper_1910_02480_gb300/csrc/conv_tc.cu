@@ -396,6 +396,27 @@ __device__ __forceinline__ void raw_convert_tma_group(int gt, const uint8_t *slo
   }
 }
 
+// PROD_TMA_CONVERT, split-tf32 over whole K-block boxes (the raw slot is
+// already a 128-byte-swizzled K-major tile): the MMAs read A_hi from the raw
+// slot itself -- the tensor core takes the top 19 bits of each fp32 element,
+// i.e. A truncated to tf32 -- so only A_lo = A - trunc_tf32(A), exact in
+// fp32, is written, into the stage's lo tile.
+__device__ __forceinline__ void raw_convert_lo(int gt, const uint8_t *slot, uint8_t *a1) {
+  const int lane = gt & 31, gw = gt >> 5, q = lane & 7;
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int r = (lane >> 3) + 4 * gw + 16 * it;
+    const uint32_t off = swz(r, q);
+    const uint4 u = lds128(slot + off);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+    uint32_t l[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      l[e] = __float_as_uint(__uint_as_float(w[e]) - __uint_as_float(w[e] & 0xFFFFE000u));
+    sts128(a1 + off, l[0], l[1], l[2], l[3]);
+  }
+}
+
 // PROD_TMA_TMEM step 2: the warp's lane quarter (rows 32 q .. 32 q + 31,
 // q = warp % 4) of the whole K block goes from the raw slot, split into tf32
 // hi/lo, into the A stage's tensor-memory columns [0, 32) (hi) and
@@ -515,7 +536,7 @@ __device__ __noinline__ void tma_issue_loop(const ConvArgs &a, uint32_t raw_u32,
 
 // PROD_TMA_CONVERT / PROD_TMA_TMEM producer loop (TAPS: the raw slots hold
 // tap boxes, see tma_issue).
-template <int PREC, bool TAPS>
+template <int PREC, bool TAPS, bool HI>
 __device__ __forceinline__ void convert_loop(const ConvArgs &a, uint8_t *data, uint8_t *raw, uint64_t *full_bar,
                                              uint64_t *empty_bar, uint64_t *raw_full, uint64_t *raw_empty,
                                              int stages, int sbytes, int R, int slot_bytes, int total_kb,
@@ -531,6 +552,8 @@ __device__ __forceinline__ void convert_loop(const ConvArgs &a, uint8_t *data, u
   // converted at any time.  K block j uses raw slot j % R and MMA stage
   // j % stages; the barrier parities follow from j.
   const int g = (pt >> 5) >> 2, gw = (pt >> 5) & 3, gt = pt & 127;
+  // A_hi read by the MMAs from the raw slot, which their commit releases
+  const bool hiraw = HI && PREC == PREC_TF32X3 && !TAPS && a.hi_raw;
   for (int jc = g; jc < total_kb; jc += 2) {
     const int slot = jc % R, stage = jc % stages;
     if (!pwait(a, w_copy, smem_u32(&raw_full[slot]), (uint32_t)((jc / R) & 1))) break;
@@ -541,6 +564,8 @@ __device__ __forceinline__ void convert_loop(const ConvArgs &a, uint8_t *data, u
       if (a.prod_mode == PROD_TMA_TMEM)
         raw_convert_tmem<TAPS>(gw, lane, raw + slot * slot_bytes,
                                tmem_base + (uint32_t)(ts_a_col0(a.BN, a.kfold > 0) + stage * 64));
+      else if (HI && hiraw)
+        raw_convert_lo(gt, raw + slot * slot_bytes, a0 + a_bytes);
       else
         raw_convert_tma_group<PREC, TAPS>(gt, raw + slot * slot_bytes, a0, a0 + a_bytes);
     } else {
@@ -556,13 +581,15 @@ __device__ __forceinline__ void convert_loop(const ConvArgs &a, uint8_t *data, u
     }
     if (lane == 0) {
       mbar_arrive(smem_u32(&full_bar[stage]));
-      mbar_arrive(smem_u32(&raw_empty[slot]));
+      if (!(HI && hiraw)) mbar_arrive(smem_u32(&raw_empty[slot]));
     }
   }
 }
 
-// Producer warps.  `raw` is the raw ring (unused in PROD_TMA_DIRECT).
-template <int PREC>
+// Producer warps.  `raw` is the raw ring (unused in PROD_TMA_DIRECT).  HI:
+// the decoder forms, where a.hi_raw may send A_hi to the MMAs from the raw
+// slot (compiled apart, so the encoders' producers carry none of it).
+template <int PREC, bool HI>
 __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint8_t *raw, uint64_t *full_bar,
                                           uint64_t *empty_bar, uint64_t *raw_full, uint64_t *raw_empty, int stages,
                                           int sbytes, int R, int slot_bytes, int M, int total_tiles,
@@ -605,10 +632,10 @@ __device__ __noinline__ void run_producer(const ConvArgs &a, uint8_t *data, uint
     }
   } else if (a.prod_mode == PROD_TMA_CONVERT || a.prod_mode == PROD_TMA_TMEM) {
     if (a.tap_boxes)
-      convert_loop<PREC, true>(a, data, raw, full_bar, empty_bar, raw_full, raw_empty, stages, sbytes, R, slot_bytes,
+      convert_loop<PREC, true, HI>(a, data, raw, full_bar, empty_bar, raw_full, raw_empty, stages, sbytes, R, slot_bytes,
                                total_kb, tmem_base, w_empty, w_copy, w_conv, w_fence);
     else
-      convert_loop<PREC, false>(a, data, raw, full_bar, empty_bar, raw_full, raw_empty, stages, sbytes, R, slot_bytes,
+      convert_loop<PREC, false, HI>(a, data, raw, full_bar, empty_bar, raw_full, raw_empty, stages, sbytes, R, slot_bytes,
                                 total_kb, tmem_base, w_empty, w_copy, w_conv, w_fence);
   } else {
     // PROD_CPASYNC
@@ -1242,13 +1269,14 @@ __device__ __forceinline__ bool epi_tile_staged(const ConvArgs &a, uint32_t tadd
 // (split-tf32).  FOLD (with TS): accumulation chunks, all three products of
 // a K block into the chunk's one accumulator, the two small correction
 // products first.
-template <int PREC, bool TS, bool PROF, bool TAPA, bool FOLD>
+template <int PREC, bool TS, bool PROF, bool TAPA, bool FOLD, bool HIRAW>
 __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, int sbytes, int a_bytes,
                                           int b_bytes, int stages, int total_tiles, int nbufs, int acc_cols,
                                           uint32_t acc_base, uint32_t a_col0,
                                           uint32_t tmem_base, uint64_t *full_bar, uint64_t *empty_bar,
                                           uint64_t *tfull_bar, uint64_t *tempty_bar, unsigned long long &w_full,
-                                          unsigned long long &w_tempty) {
+                                          unsigned long long &w_tempty, uint32_t raw_u32, int R, int slot_bytes,
+                                          uint64_t *raw_empty) {
   using T = PrecTraits<PREC>;
   const int BN = a.BN;
   const unsigned long long tmo = a.timeout_ns;
@@ -1279,6 +1307,10 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
   const uint32_t dstage = (uint32_t)sbytes >> 4, dAlo = (uint32_t)a_bytes >> 4;
   const uint64_t dB0 = make_sdesc_sw128(data_u32 + (uint32_t)(TS ? 0 : T::SPLIT * a_bytes));
   const uint32_t dBlo = (uint32_t)b_bytes >> 4;
+  // HIRAW: A_hi is K block j's raw slot (j mod R), released by the commit
+  const uint64_t dR0 = make_sdesc_sw128(raw_u32);
+  const uint32_t dslot = (uint32_t)slot_bytes >> 4;
+  int rslot = 0;
   int stage = 0;
   uint32_t phase = 0;
   int it = 0;  // accumulator units: tiles, or with a.kfold chunks of a.kfold K blocks of a tile
@@ -1340,7 +1372,19 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
           }
         } else {
           const uint64_t ad1 = sd + dAlo;
+          const uint64_t ah = HIRAW ? dR0 + (uint64_t)((uint32_t)rslot * dslot) : sd;
           const uint32_t acc0 = kb != k0;
+          if constexpr (HIRAW) {
+            tc_mma<T::KIND>(d_tmem, ah, bd0, idesc, acc0);
+            tc_mma<T::KIND>(c_tmem, ah, bd1, idesc, acc0);
+            tc_mma<T::KIND>(c_tmem, ad1, bd0, idesc, 1u);
+#pragma unroll
+            for (int k = 1; k < KROW_BYTES / 32; ++k) {
+              tc_mma<T::KIND>(d_tmem, ah + 2u * k, bd0 + 2 * k, idesc, 1u);
+              tc_mma<T::KIND>(c_tmem, ah + 2u * k, bd1 + 2 * k, idesc, 1u);
+              tc_mma<T::KIND>(c_tmem, ad1 + 2u * k, bd0 + 2 * k, idesc, 1u);
+            }
+          } else {
           tc_mma<T::KIND>(d_tmem, sd, bd0, idesc, acc0);
           if constexpr (PREC == PREC_TF32X3) {
             tc_mma<T::KIND>(c_tmem, sd, bd1, idesc, acc0);
@@ -1354,8 +1398,13 @@ __device__ __forceinline__ void mma_issue(const ConvArgs &a, uint32_t data_u32, 
               tc_mma<T::KIND>(c_tmem, ad1 + kA * k, bd0 + 2 * k, idesc, 1u);
             }
           }
+          }
         }
         tc_commit(smem_u32(&empty_bar[stage]));
+        if constexpr (HIRAW) {
+          tc_commit(smem_u32(&raw_empty[rslot]));
+          rslot = rslot + 1 == R ? 0 : rslot + 1;
+        }
         stage = stage + 1 == stages ? 0 : stage + 1;  // selects, not a branch
         phase ^= stage == 0 ? 1u : 0u;
       }
@@ -1443,7 +1492,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
     mbar_init(smem_u32(stall_bar), 1);
     for (int r = 0; r < plan.raw_depth; ++r) {
       mbar_init(smem_u32(&raw_full[r]), 1);                        // the TMA thread's arrive
-      mbar_init(smem_u32(&raw_empty[r]), 4);                      // one arrive per warp of the converting group
+      // one arrive per warp of the converting group, or the MMAs' commit where
+      // they read A_hi from the raw slot
+      mbar_init(smem_u32(&raw_empty[r]), a.hi_raw ? 1u : 4u);
     }
     for (int b = 0; b < 4 * EPI_TMA_BOXES; ++b) mbar_init(smem_u32(&skip_bar[b]), 1);  // the epilogue lane's arrive
     fence_mbar_init();
@@ -1468,31 +1519,40 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       // one instantiation per A form: a branch between the forms inside the
       // issue loop measured ~110 cycles per MMA against 45-64 without
       if (ok) {
-#define DRC_MMA_ISSUE(TSV, PROFV, TAPV, FOLDV)                                                                   \
-  mma_issue<PREC, TSV, PROFV, TAPV, FOLDV>(a, data_u32, sbytes, a_bytes, b_bytes, stages, total_tiles, nbufs,       \
-                                           acc_cols, acc_base, a_col0, tmem_base, full_bar, empty_bar, tfull_bar,  \
-                                           tempty_bar, w_full, w_tempty)
+#define DRC_MMA_ISSUE(TSV, PROFV, TAPV, FOLDV, HIV)                                                              \
+  mma_issue<PREC, TSV, PROFV, TAPV, FOLDV, HIV>(a, data_u32, sbytes, a_bytes, b_bytes, stages, total_tiles, nbufs,  \
+                                                acc_cols, acc_base, a_col0, tmem_base, full_bar, empty_bar,         \
+                                                tfull_bar, tempty_bar, w_full, w_tempty,                            \
+                                                smem_u32(data + stages * sbytes), plan.raw_depth,                  \
+                                                plan.raw_slot_bytes, raw_empty)
         constexpr bool kTS = PREC == PREC_TF32X3;
         constexpr bool kTAP = PREC == PREC_BF16 || PREC == PREC_FP8;  // tap boxes land in the A tile itself
         const bool tapa = kTAP && a.tap_boxes && a.prod_mode == PROD_TMA_DIRECT;
+        // the decoder forms only (the encoders' form carries none of its code)
+        constexpr bool kHI = kTS && (EPI == EPI_SKIP || EPI == EPI_PAIR);
+        const bool hiraw = kHI && a.hi_raw;
         if (a.prof) {
           if constexpr (FOLD)
-            DRC_MMA_ISSUE(kTS, true, false, kTS);
+            DRC_MMA_ISSUE(kTS, true, false, kTS, false);
           else if (kTS && ts)
-            DRC_MMA_ISSUE(kTS, true, false, false);
+            DRC_MMA_ISSUE(kTS, true, false, false, false);
           else if (tapa)
-            DRC_MMA_ISSUE(false, true, kTAP, false);
+            DRC_MMA_ISSUE(false, true, kTAP, false, false);
+          else if (hiraw)
+            DRC_MMA_ISSUE(false, true, false, false, kHI);
           else
-            DRC_MMA_ISSUE(false, true, false, false);
+            DRC_MMA_ISSUE(false, true, false, false, false);
         } else {
           if constexpr (FOLD)
-            DRC_MMA_ISSUE(kTS, false, false, kTS);
+            DRC_MMA_ISSUE(kTS, false, false, kTS, false);
           else if (kTS && ts)
-            DRC_MMA_ISSUE(kTS, false, false, false);
+            DRC_MMA_ISSUE(kTS, false, false, false, false);
           else if (tapa)
-            DRC_MMA_ISSUE(false, false, kTAP, false);
+            DRC_MMA_ISSUE(false, false, kTAP, false, false);
+          else if (hiraw)
+            DRC_MMA_ISSUE(false, false, false, false, kHI);
           else
-            DRC_MMA_ISSUE(false, false, false, false);
+            DRC_MMA_ISSUE(false, false, false, false, false);
         }
 #undef DRC_MMA_ISSUE
       }
@@ -1537,7 +1597,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1) conv_tc_kernel(const __grid_co
       tma_issue_loop<PREC>(a, smem_u32(data + stages * sbytes), raw_full, raw_empty, plan.raw_depth,
                            plan.raw_slot_bytes, total_tiles);
   } else if (warp >= PROD_WARP0) {
-    run_producer<PREC>(a, data, data + stages * sbytes, full_bar, empty_bar, raw_full, raw_empty, stages, sbytes,
+    run_producer<PREC, PREC == PREC_TF32X3 && (EPI == EPI_SKIP || EPI == EPI_PAIR)>(a, data, data + stages * sbytes, full_bar, empty_bar, raw_full, raw_empty, stages, sbytes,
                        plan.raw_depth, plan.raw_slot_bytes, M, total_tiles, tmem_base);
   } else if (warp >= EPI_WARP0 && warp < EPI_WARP0 + 4) {
     // ------------------------------------------------------------ epilogue
@@ -1715,14 +1775,25 @@ cudaError_t launch_conv(const ConvArgs &a, int prec, int num_sms, cudaStream_t s
   if (pair && (prec != PREC_TF32X3 || fold || !a.y_tma || a.n_tiles != 1 || a.BN != 2 * a.Cout))
     return cudaErrorInvalidValue;
   const size_t smem = conv_smem_bytes(prec, a.BN, a.prod_mode, a.y_tma, fold ? 1 : 0);
+  if (a.hi_raw) return cudaErrorInvalidValue;  // launch_conv's own decision
   switch (prec) {
-    case PREC_TF32X3:
+    case PREC_TF32X3: {
       if (fold) return a.y_tma ? launch_form<PREC_TF32X3, true, true>(a, grid, smem, st)
                                : launch_form<PREC_TF32X3, false, true>(a, grid, smem, st);
+      // the decoder forms: A_hi from the raw slot where A is in shared memory
+      // over whole K-block boxes
+      const bool dec = pair || (a.y_tma && a.skip_tma);
+      if (dec && a.prod_mode == PROD_TMA_CONVERT && !a.tap_boxes) {
+        ConvArgs b = a;
+        b.hi_raw = 1;
+        return pair ? launch_form<PREC_TF32X3, true, false, EPI_PAIR>(b, grid, smem, st)
+                    : launch_form<PREC_TF32X3, true, false, EPI_SKIP>(b, grid, smem, st);
+      }
       if (pair) return launch_form<PREC_TF32X3, true, false, EPI_PAIR>(a, grid, smem, st);
       if (a.y_tma && a.skip_tma) return launch_form<PREC_TF32X3, true, false, EPI_SKIP>(a, grid, smem, st);
       return a.y_tma ? launch_form<PREC_TF32X3, true, false>(a, grid, smem, st)
                      : launch_form<PREC_TF32X3, false, false>(a, grid, smem, st);
+    }
     case PREC_BF16:
       if (a.y_tma && a.out_qinv) return launch_form<PREC_BF16, true, false, EPI_E4>(a, grid, smem, st);
       return a.y_tma ? launch_form<PREC_BF16, true, false>(a, grid, smem, st)

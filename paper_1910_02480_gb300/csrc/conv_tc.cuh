@@ -62,6 +62,8 @@ struct ConvArgs {
                      // [N][Hout][Wout][Cout] with element strides {1, 2, 2, 1}, box {16, 2 Wrow, 2 rw, mw}
   int y_tma;         // FP32 without training outputs: tiles stored by TMA from shared memory
   int y_rw, y_mw;    // LK_CONVT: phase rows and maps per 32-row box (Wrow * y_rw * y_mw = 32)
+  int hi_raw;        // set by launch_conv: split-tf32 with A in shared memory over whole K-block boxes in the
+                     // decoder forms -- the MMAs read A_hi from the raw slot, the producers write only A_lo
   int skip_tma;      // y_tma FP32 decoder whose skip is its output (in place): the epilogue reads the
                      // skip boxes through ymap by TMA, into the staging boxes the stores then read
   int prod_mode;

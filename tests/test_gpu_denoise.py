@@ -223,8 +223,12 @@ def test_autotuned_context_keeps_parity(drc, precision):
     assert ctx.status() == drc.OK
     if precision == "fp32":
         assert rel_err(g, oracle.forward(w, x.cpu().numpy(), widths)) <= FP32_TOL
-    print("max |tuned - untuned| / rms:", np.max(np.abs(g - ref)) / np.sqrt(np.mean(ref * ref)))
-    assert rel_err(g, ref) <= (1e-6 if precision == "fp32" else 1e-2)
+    d = np.max(np.abs(g - ref)) / np.sqrt(np.mean(ref * ref))
+    print("max |tuned - untuned| / rms:", d)
+    if precision == "fp32":  # the A paths differ at most in the split of A's tf32 parts (see the pair tests)
+        assert d <= 1e-5
+    else:
+        assert rel_err(g, ref) <= 1e-2
 
 
 PAIR_CASES = [
@@ -239,19 +243,25 @@ PAIR_CASES = [
 @pytest.mark.parametrize("widths,N,H,W", PAIR_CASES)
 def test_phase_pairs_match_oracle(drc, widths, N, H, W, mode, tmp_path):
     """Decoder layers forced onto the phase-pair form (A path 8: A in tensor
-    memory, 9: in shared memory; applied through a tile cache entry) keep the
-    oracle's FP32 bar, and agree with the one-GEMM-per-parity form: the pair
-    adds zero-weight taps only, whole K blocks of exact zero products."""
+    memory, 9: in shared memory; applied through a tile cache entry, every
+    other layer on its default tiles) keep the oracle's FP32 bar, and agree
+    with the one-GEMM-per-parity form.  With A in tensor memory the pair adds
+    zero-weight taps only, whole K blocks of exact zero products: bit for bit.
+    With A in shared memory the decoder forms split A as trunc_tf32(A) (read
+    by the MMAs from the TMA box itself) + the tf32 remainder, where the
+    tensor-memory form rounds both parts to nearest; per product the two
+    splits' errors differ by about 2^-20 relative, so the outputs differ by
+    far less than 1e-5 of their rms."""
     import json
     w = synth.he_weights(widths, seed=5, bias=True)
     x = torch.from_numpy(_maps(N, H, W, seed=7)).cuda()
     S = len(widths)
     base = drc.Context(widths, w, precision="fp32")
     ref = base.denoise(x).cpu().numpy()
+    tiles = [base.describe_layer(li) for li in range(2 * S)]  # the defaults ref ran with
     cache = str(tmp_path / "tiles.jsonl")
     assert base.autotune(N, H, W, cache=cache) is False
     entry = json.loads(open(cache).read().splitlines()[-1])
-    tiles = [base.describe_layer(li) for li in range(2 * S)]
     entry["tile_n"] = [t[0] for t in tiles]
     entry["a_path"] = [-1] * (2 * S)
     paired = []
@@ -272,16 +282,22 @@ def test_phase_pairs_match_oracle(drc, widths, N, H, W, mode, tmp_path):
     d = np.max(np.abs(g - ref)) / np.sqrt(np.mean(ref * ref))
     print("pairs on layers %s: max rel %.3e vs oracle, max |paired - unpaired| / rms %.3e" % (paired, err, d))
     assert err <= FP32_TOL
-    assert rel_err(g, ref) <= 1e-6
+    if mode == 8:
+        assert np.array_equal(g, ref)
+    else:
+        assert d <= 1e-5
 
 
 def test_phase_pairs_full_size(drc, tmp_path):
     """The benchmark's batch (4096 maps of 7x32x32, widths 64/128/256) with d2
     forced onto its phase pairs with A in shared memory (the path the
     autotuner picks there): every output equals the four-GEMM form's bit for
-    bit, and sampled maps meet the oracle's FP32 bar.  The four-GEMM result
-    is still in flight when drc_autotune starts on the same context: the
-    tuner's timing launches, which reuse the workspace, wait for it."""
+    bit but for the split of A (shared-memory A truncates its tf32 high part,
+    see test_phase_pairs_match_oracle: within 1e-5 of the rms), and sampled
+    maps meet the oracle's FP32 bar.  The four-GEMM result is still in flight
+    when drc_autotune starts on the same context: the tuner's timing
+    launches, which reuse the workspace, wait for it (a race there corrupted
+    whole maps, far beyond this bound)."""
     import json
     widths, N = [64, 128, 256], 4096
     w = synth.he_weights(widths, seed=8, bias=True)
@@ -308,8 +324,8 @@ def test_phase_pairs_full_size(drc, tmp_path):
     o = oracle.forward(w, x[idx], widths)
     err = rel_err(out.cpu().numpy()[idx], o)
     err_ref = rel_err(ref.cpu().numpy()[idx], o)
-    diff = (out != ref).reshape(N, -1).any(dim=1).nonzero().flatten().cpu().numpy()
-    print("d2 phase pairs, 4096 maps: max rel %.3e (four GEMMs: %.3e) on the sampled maps; %d maps differ, first %s"
-          % (err, err_ref, len(diff), diff[:8]))
+    d = ((out - ref).abs().max() / ref.pow(2).mean().sqrt()).item()
+    print("d2 phase pairs, 4096 maps: max rel %.3e (four GEMMs: %.3e) on the sampled maps; max |paired - four GEMMs|"
+          " / rms %.3e" % (err, err_ref, d))
     assert err <= FP32_TOL and err_ref <= FP32_TOL
-    assert torch.equal(out, ref)
+    assert d <= 1e-5
