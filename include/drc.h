@@ -474,7 +474,7 @@ const char *drc_last_error(drc_ctx *ctx);
  * transposed conv as two GEMMs, each holding the parities (p, 0) and (p, 1)
  * of one output row side by side in a 2 Cout-column tile over the union of
  * their input taps (a tap one of the two parities lacks has zero weights
- * there).
+ * there), with A in tensor memory or in shared memory.
  * Synchronises the device first (calls in flight on any stream finish before
  * the timing launches reuse the workspace) and at the end; grows the
  * workspace to N maps.  No counterpart in
@@ -554,9 +554,9 @@ drc_status drc_calibrate(drc_ctx *ctx, const float *in, int N, int H, int W,
                          unsigned flags, void *stream);
 
 /* The tile width (0 for the head) and A-operand path (-1 default, 0
- * per-thread gathers, 1 TMA + producer conversion, 8 phase pairs -- see
- * drc_autotune; the tile width is then the unpaired fallback's) drc_denoise
- * uses for one layer (0 .. 2S-1). */
+ * per-thread gathers, 1 TMA + producer conversion, 8 / 9 phase pairs with A
+ * in tensor / shared memory -- see drc_autotune; the tile width is then the
+ * unpaired fallback's) drc_denoise uses for one layer (0 .. 2S-1). */
 drc_status drc_describe_layer(drc_ctx *ctx, int layer, int *bn, int *a_path);
 
 /* ---- Plans: progressive passes with uneven batches ------------------------
